@@ -1,0 +1,6 @@
+"""FP64 CPU oracle of the ReaxFF timestep -- test infrastructure only.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline / reference legs use it.
+"""
+from oracle.reaxff_oracle import (TERMS, Model, build_lists, far_list_bruteforce,  # noqa: F401
+                                  far_list_cells, half_mask, kinetic, pcg, sort_key, taper, verlet)
