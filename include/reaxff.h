@@ -1,0 +1,201 @@
+/*
+ * reaxff.h -- C ABI of the GB300 (sm_103a) ReaxFF timestep library (libreaxff.so).
+ *
+ * One ReaxFF molecular-dynamics timestep (paper Sec. 2.1 and Fig. 1: bonded,
+ * non-bonded and charge-equilibration interactions summed into per-atom forces)
+ * runs here as hand-written CUDA kernels on one GPU:
+ *   (a) cell-binned far-neighbour list, bond list and hydrogen-bond list (Sec. 3.3,
+ *       "Neighbor and Interaction Lists"; Table 2 "Write Lists" / "Init. Forces"),
+ *   (b) uncorrected -> corrected bond orders (Sec. 3.3 "Pairwise Interactions";
+ *       Table 2 "Bond Orders"),
+ *   (c) bonded terms: bond, lone pair, over/under-coordination, valence angle
+ *       (+penalty, coalition), torsion (+conjugation), hydrogen bond (Sec. 2.1;
+ *       Sec. 3.3 "Three-body Interactions"; Table 2 "3-body" / "4-body"),
+ *   (d) tapered, shielded van der Waals and Coulomb terms (Sec. 3.3, Algorithm 2),
+ *   (e) QEq: two Jacobi-preconditioned CG solves sharing the tapered H matrix,
+ *       iterated concurrently (Sec. 3.3 "QEq"),
+ *   (f) the dE/dBO chain rule into atom forces (Table 2 "Aggregate Forces") and
+ *       velocity Verlet (Sec. 4.1: dt = 0.1 fs).
+ *
+ * Units: energy kcal/mol, length Angstrom, charge e, mass amu, time fs,
+ *        force kcal/(mol A), velocity A/fs.
+ * Boxes are orthorhombic and periodic; every box length must exceed r_nb.
+ *
+ * Ownership: every pointer argument is owned by the caller and only read or written
+ * during the call. Host-pointer functions copy in/out; the context owns all device
+ * memory it allocates. Functions suffixed _dev take device pointers and a
+ * cudaStream_t (passed as void*) and enqueue work on that stream.
+ *
+ * Errors: every int-returning function returns REAXFF_OK (0) or a negative code;
+ * reaxff_last_error() gives a text description. Nothing aborts the process.
+ * The library is not thread-safe per context (one host thread per context).
+ */
+#ifndef REAXFF_H
+#define REAXFF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define REAXFF_MAXT 8       /* maximum number of atom types */
+#define REAXFF_NTERMS 13    /* energy terms, in this order: */
+/* 0 bond, 1 lp, 2 over, 3 under, 4 val, 5 pen, 6 coa, 7 tors, 8 conj, 9 hbond,
+   10 vdw, 11 coul, 12 pol */
+
+enum {
+  REAXFF_OK = 0,
+  REAXFF_E_INVALID = -1,        /* bad argument, parameter or size */
+  REAXFF_E_CUDA = -2,           /* a CUDA runtime call failed (text has the CUDA error) */
+  REAXFF_E_CAPACITY = -3,       /* a list overflowed even after the internal regrow */
+  REAXFF_E_NOT_CONVERGED = -4,  /* QEq hit qeq_max_iter; charges still returned */
+  REAXFF_E_TIMEOUT = -5,        /* a device-side wait hit its spin limit */
+  REAXFF_E_NAN = -6,            /* non-finite positions, forces or energies */
+  REAXFF_E_STATE = -7           /* call out of order (e.g. no positions set) */
+};
+
+enum { REAXFF_FP64 = 0, REAXFF_MIXED = 1 };                  /* options.precision */
+enum { REAXFF_WARM_EXTRAP = 0, REAXFF_WARM_ZERO = 1, REAXFF_WARM_MLP = 2 };
+enum { REAXFF_LIST_FAR = 0, REAXFF_LIST_BOND = 1, REAXFF_LIST_HBOND = 2 };
+
+/* Force-field parameters (tables indexed by atom type). Per-pair tables are
+ * symmetric; per-triple tables are [i][j=centre][k], symmetric in i<->k; torsion
+ * tables are [j][k] for the central bond; H-bond tables are [X][Z] (X bonded to
+ * the H atom, Z the acceptor). The functional forms that read them are listed in
+ * each kernel's header comment. */
+typedef struct {
+  int32_t ntypes;
+  int32_t hb[REAXFF_MAXT];          /* 0 none, 1 H-bond donor hydrogen, 2 acceptor */
+  double mass[REAXFF_MAXT], val[REAXFF_MAXT], vale[REAXFF_MAXT], valboc[REAXFF_MAXT],
+      valang[REAXFF_MAXT], p_lp2[REAXFF_MAXT], p_ovun2[REAXFF_MAXT], p_ovun5[REAXFF_MAXT],
+      p_val3[REAXFF_MAXT], p_val5[REAXFF_MAXT], chi[REAXFF_MAXT], eta[REAXFF_MAXT],
+      gamma_t[REAXFF_MAXT];
+  double r0s[REAXFF_MAXT][REAXFF_MAXT], r0p[REAXFF_MAXT][REAXFF_MAXT],
+      r0pp[REAXFF_MAXT][REAXFF_MAXT], p_bo1[REAXFF_MAXT][REAXFF_MAXT],
+      p_bo2[REAXFF_MAXT][REAXFF_MAXT], p_bo3[REAXFF_MAXT][REAXFF_MAXT],
+      p_bo4[REAXFF_MAXT][REAXFF_MAXT], p_bo5[REAXFF_MAXT][REAXFF_MAXT],
+      p_bo6[REAXFF_MAXT][REAXFF_MAXT], p_boc3[REAXFF_MAXT][REAXFF_MAXT],
+      p_boc4[REAXFF_MAXT][REAXFF_MAXT], p_boc5[REAXFF_MAXT][REAXFF_MAXT],
+      ovc[REAXFF_MAXT][REAXFF_MAXT], v13[REAXFF_MAXT][REAXFF_MAXT],
+      De_s[REAXFF_MAXT][REAXFF_MAXT], De_p[REAXFF_MAXT][REAXFF_MAXT],
+      De_pp[REAXFF_MAXT][REAXFF_MAXT], p_be1[REAXFF_MAXT][REAXFF_MAXT],
+      p_be2[REAXFF_MAXT][REAXFF_MAXT], p_ovun1[REAXFF_MAXT][REAXFF_MAXT],
+      vdw_D[REAXFF_MAXT][REAXFF_MAXT], vdw_rv[REAXFF_MAXT][REAXFF_MAXT],
+      vdw_alpha[REAXFF_MAXT][REAXFF_MAXT], vdw_gw[REAXFF_MAXT][REAXFF_MAXT],
+      gamma[REAXFF_MAXT][REAXFF_MAXT];
+  double th00[REAXFF_MAXT][REAXFF_MAXT][REAXFF_MAXT], p_val1[REAXFF_MAXT][REAXFF_MAXT][REAXFF_MAXT],
+      p_val2[REAXFF_MAXT][REAXFF_MAXT][REAXFF_MAXT], p_val4[REAXFF_MAXT][REAXFF_MAXT][REAXFF_MAXT],
+      p_val7[REAXFF_MAXT][REAXFF_MAXT][REAXFF_MAXT], p_pen1[REAXFF_MAXT][REAXFF_MAXT][REAXFF_MAXT],
+      p_coa1[REAXFF_MAXT][REAXFF_MAXT][REAXFF_MAXT];
+  double V1[REAXFF_MAXT][REAXFF_MAXT], V2[REAXFF_MAXT][REAXFF_MAXT], V3[REAXFF_MAXT][REAXFF_MAXT],
+      p_tor1[REAXFF_MAXT][REAXFF_MAXT], p_cot1[REAXFF_MAXT][REAXFF_MAXT];
+  double r0hb[REAXFF_MAXT][REAXFF_MAXT], p_hb1[REAXFF_MAXT][REAXFF_MAXT],
+      p_hb2[REAXFF_MAXT][REAXFF_MAXT], p_hb3[REAXFF_MAXT][REAXFF_MAXT];
+  double p_boc1, p_boc2, p_lp1, p_ovun3, p_ovun4, p_ovun6, p_ovun7, p_ovun8, p_val6, p_val8,
+      p_val9, p_val10, p_pen2, p_pen3, p_pen4, p_coa2, p_coa3, p_coa4, p_tor2, p_tor3, p_tor4,
+      p_cot2, p_vdW1, k_e;
+} reaxff_params;
+
+typedef struct {
+  double r_nb;        /* nonbonded / QEq cutoff (A), 10 in the paper's setup (Sec. 4.2) */
+  double r_bond;      /* bond-candidate cutoff (A) */
+  double r_hb;        /* hydrogen-bond partner cutoff (A) */
+  double bo_cut;      /* bond kept when BO'sig+BO'pi+BO'pp >= bo_cut */
+  double thb_cut;     /* valence-angle / torsion bond-order threshold */
+  double thb_cutsq;   /* valence-angle product threshold */
+  double hb_bo_min;   /* minimum H-X bond order of an H-bond */
+  double qeq_tol;     /* QEq relative residual ||b - Hx|| / ||b|| per system */
+  int32_t qeq_max_iter;
+  int32_t precision;  /* REAXFF_FP64 or REAXFF_MIXED (FP32 interaction math, FP64 sums) */
+  int32_t warm_start; /* REAXFF_WARM_* */
+  int32_t term_mask;  /* bit t set = energy term t contributes to forces (0 = all) */
+  double capacity_margin; /* list capacity headroom factor (>= 1; 0 = default 1.35) */
+} reaxff_options;
+
+typedef struct reaxff_ctx reaxff_ctx;
+
+/* Layout checks for language bindings: sizes of the two structs and the byte offset
+ * of a named field (returns -1 for an unknown name). */
+int64_t reaxff_sizeof_params(void);
+int64_t reaxff_sizeof_options(void);
+int64_t reaxff_params_offset(const char* field);
+
+/* Create a context for one periodic system of n atoms with the given types
+ * (int32[n], each < params->ntypes) and box (double[3], A). Copies params and
+ * options; allocates device memory sized from the density. *out receives the
+ * context (NULL on error). */
+int reaxff_create(const reaxff_params* params, const int32_t* types, int64_t n,
+                  const double box[3], const reaxff_options* options, reaxff_ctx** out);
+
+/* Create a context for nrep independent replicas (uneven sizes allowed) that run
+ * together, one kernel launch per stage: replica r owns atoms
+ * [rep_offsets[r], rep_offsets[r+1]) (int64[nrep+1], rep_offsets[0] = 0) and box
+ * boxes[3r..3r+2]. No interaction crosses replicas; QEq and energies are per replica. */
+int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t* rep_offsets,
+                        const int32_t* types, const double* boxes,
+                        const reaxff_options* options, reaxff_ctx** out);
+
+void reaxff_destroy(reaxff_ctx* ctx);
+const char* reaxff_last_error(const reaxff_ctx* ctx);
+int64_t reaxff_num_atoms(const reaxff_ctx* ctx);
+int32_t reaxff_num_replicas(const reaxff_ctx* ctx);
+
+/* Positions x (double[n*3], row-major xyz, A) and velocities v (double[n*3], A/fs,
+ * NULL = zero). Positions are wrapped into [0, L). Resets the QEq history. */
+int reaxff_set_state(reaxff_ctx* ctx, const double* x, const double* v);
+/* Copy out positions, velocities (double[n*3]) and charges (double[n]); any may be NULL. */
+int reaxff_get_state(reaxff_ctx* ctx, double* x, double* v, double* q);
+
+/* (a) Build the far-neighbour, bond and H-bond lists for the current positions.
+ * On overflow the library grows the list and rebuilds once; then E_CAPACITY. */
+int reaxff_build_lists(reaxff_ctx* ctx);
+
+/* Export a list built by reaxff_build_lists / reaxff_forces / reaxff_step in original
+ * atom ids: entries (i[k], j[k], shift[3k..3k+2]) with the image shift s in {-1,0,1}^3
+ * such that the neighbour is x_j + s*L. FAR and HBOND are directed (every ordered
+ * pair), BOND is directed (both directions). capacity = length of i/j (shift has
+ * 3*capacity); *count receives the entry count; E_INVALID if capacity < count
+ * (*count is still set). Pass capacity 0 and NULL arrays to query the count. */
+int reaxff_get_lists(reaxff_ctx* ctx, int32_t which, int64_t capacity, int64_t* count,
+                     int32_t* i, int32_t* j, int8_t* shift);
+
+/* (b) Bond orders of the directed bond list after reaxff_forces: per entry the
+ * shifted uncorrected total BO' and the corrected BO, BO_pi, BO_pipi (double[count]),
+ * in the order of reaxff_get_lists(BOND). Same capacity rules. */
+int reaxff_get_bond_orders(reaxff_ctx* ctx, int64_t capacity, int64_t* count, double* bo_prime,
+                           double* bo, double* bo_pi, double* bo_pipi);
+
+/* (e) QEq at the current positions (builds lists): charges q (double[n] or NULL) and
+ * CG iteration counts of the s and t systems (int32[nrep] each, or NULL). Returns
+ * E_NOT_CONVERGED when a system hit qeq_max_iter (q is still written). */
+int reaxff_qeq(reaxff_ctx* ctx, double* q_out, int32_t* iters_s, int32_t* iters_t);
+
+/* (a)-(f) Forces at the current positions: lists, QEq, all terms, chain rule.
+ * F: double[n*3]; E: double[nrep*13] per-replica energy terms; virial: double[nrep*6]
+ * per replica, (xx, yy, zz, xy, xz, yz) of W_ab = -dE/d(strain_ab). Any may be NULL. */
+int reaxff_forces(reaxff_ctx* ctx, double* F, double* E, double* virial);
+
+/* Same with caller-fixed charges q (double[n]); QEq is skipped. */
+int reaxff_forces_fixed_q(reaxff_ctx* ctx, const double* q, double* F, double* E,
+                          double* virial);
+
+/* nsteps velocity-Verlet steps of dt_fs. Each step rebuilds lists, solves QEq and
+ * recomputes forces. E_tot (double[nsteps*nrep] or NULL) receives the total
+ * (potential + kinetic) energy per step and replica. */
+int reaxff_step(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot);
+
+/* Kernel launches issued by the last reaxff_step call (for launch accounting). */
+int64_t reaxff_last_launch_count(const reaxff_ctx* ctx);
+
+/* ---- device-pointer variants (no host copies; enqueue on `stream`) ---------------- */
+int reaxff_set_state_dev(reaxff_ctx* ctx, const double* x_dev, const double* v_dev, void* stream);
+int reaxff_get_state_dev(reaxff_ctx* ctx, double* x_dev, double* v_dev, double* q_dev, void* stream);
+/* Runs nsteps on `stream`; no host synchronisation unless a list overflows.
+ * E_tot_dev: double[nsteps*nrep] on the device, or NULL. */
+int reaxff_step_dev(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REAXFF_H */

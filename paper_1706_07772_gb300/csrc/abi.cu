@@ -1,0 +1,843 @@
+// C ABI of the library (include/reaxff.h): context, device memory plan, stage
+// orchestration of one timestep, list-overflow regrow, error reporting.
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "reax_internal.cuh"
+
+std::string cuda_err_str(cudaError_t e) { return std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e); }
+
+namespace {
+struct DevBuf {
+  std::vector<void*> ptrs;
+  cudaError_t err = cudaSuccess;
+  template <typename T> T* alloc(size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      err = e;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+  void* alloc_bytes(size_t bytes) { return alloc<char>(bytes); }
+  void free_all() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+}  // namespace
+
+struct reaxff_ctx {
+  std::string err;
+  int n = 0, nrep = 0;
+  reaxff_params hp;
+  reaxff_options ho;
+  bool fp64 = true;
+  unsigned mask = 0x1fff;
+  int nsm = 0;
+  cudaStream_t st = nullptr;
+  int64_t launches = 0;
+  bool have_pos = false, forces_valid = false, lists_valid = false;
+  float far_margin = 0.f;
+  std::vector<int64_t> h_rep_off;
+  std::vector<double> h_box;
+  std::vector<int> h_types;
+  // device memory: fixed part and list part (re-allocated on regrow)
+  DevBuf fixed, lists;
+  DParams<double>* Pd = nullptr;
+  DParams<float>* Pf = nullptr;
+  Sys sys{};
+  Cells cells{};
+  FarList far{};
+  BondList bond{};
+  HbList hb{};
+  AtomQ aq{};
+  Accum acc{};
+  rx::QeqState Q{};
+  double *F_out = nullptr, *E_rep = nullptr, *vir_rep = nullptr, *ke_rep = nullptr, *Etot_dev = nullptr;
+  int Etot_cap = 0;
+  double *chi_t = nullptr, *eta_t = nullptr, *mass_t = nullptr;
+  int* h_err_pinned = nullptr;
+  int cap_far = 0, cap_bond = 0, cap_hb = 0;
+};
+
+namespace {
+
+#define CK(call)                                                        \
+  do {                                                                  \
+    cudaError_t e__ = (call);                                           \
+    if (e__ != cudaSuccess) {                                           \
+      ctx->err = std::string(#call) + " -> " + cuda_err_str(e__);       \
+      return REAXFF_E_CUDA;                                             \
+    }                                                                   \
+  } while (0)
+
+int fail(reaxff_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+template <typename R> void fill_params(DParams<R>& d, const reaxff_params& p, const reaxff_options& o) {
+  memset(&d, 0, sizeof(d));
+  d.nt = p.ntypes;
+  for (int a = 0; a < MAXT; ++a) {
+    d.hb[a] = p.hb[a];
+    d.mass[a] = (R)p.mass[a]; d.val[a] = (R)p.val[a]; d.vale[a] = (R)p.vale[a];
+    d.valboc[a] = (R)p.valboc[a]; d.valang[a] = (R)p.valang[a]; d.p_lp2[a] = (R)p.p_lp2[a];
+    d.p_ovun2[a] = (R)p.p_ovun2[a]; d.p_ovun5[a] = (R)p.p_ovun5[a]; d.p_val3[a] = (R)p.p_val3[a];
+    d.p_val5[a] = (R)p.p_val5[a]; d.chi[a] = (R)p.chi[a]; d.eta[a] = (R)p.eta[a];
+    for (int b = 0; b < MAXT; ++b) {
+      const int k = a * MAXT + b;
+#define PP(f) d.f[k] = (R)p.f[a][b]
+      PP(r0s); PP(r0p); PP(r0pp); PP(p_bo1); PP(p_bo2); PP(p_bo3); PP(p_bo4); PP(p_bo5); PP(p_bo6);
+      PP(p_boc3); PP(p_boc4); PP(p_boc5); PP(ovc); PP(v13); PP(De_s); PP(De_p); PP(De_pp);
+      PP(p_be1); PP(p_be2); PP(p_ovun1); PP(vdw_D); PP(vdw_rv); PP(vdw_alpha);
+      PP(V1); PP(V2); PP(V3); PP(p_tor1); PP(p_cot1); PP(r0hb); PP(p_hb1); PP(p_hb2); PP(p_hb3);
+#undef PP
+      d.vdw_gw_pow[k] = (R)std::pow(p.vdw_gw[a][b], -p.p_vdW1);
+      d.r0s_lo[k] = (R)(p.r0s[a][b] - (double)(R)p.r0s[a][b]);
+      d.r0p_lo[k] = (R)(p.r0p[a][b] - (double)(R)p.r0p[a][b]);
+      d.r0pp_lo[k] = (R)(p.r0pp[a][b] - (double)(R)p.r0pp[a][b]);
+      d.gamma_m3[k] = (R)std::pow(p.gamma[a][b], -3.0);
+      for (int c = 0; c < MAXT; ++c) {
+        const int t3 = (a * MAXT + b) * MAXT + c;
+        d.th00[t3] = (R)p.th00[a][b][c]; d.p_val1[t3] = (R)p.p_val1[a][b][c];
+        d.p_val2[t3] = (R)p.p_val2[a][b][c]; d.p_val4[t3] = (R)p.p_val4[a][b][c];
+        d.p_val7[t3] = (R)p.p_val7[a][b][c]; d.p_pen1[t3] = (R)p.p_pen1[a][b][c];
+        d.p_coa1[t3] = (R)p.p_coa1[a][b][c];
+      }
+    }
+  }
+#define PG(f) d.f = (R)p.f
+  PG(p_boc1); PG(p_boc2); PG(p_lp1); PG(p_ovun3); PG(p_ovun4); PG(p_ovun6); PG(p_ovun7); PG(p_ovun8);
+  PG(p_val6); PG(p_val8); PG(p_val9); PG(p_val10); PG(p_pen2); PG(p_pen3); PG(p_pen4); PG(p_coa2);
+  PG(p_coa3); PG(p_coa4); PG(p_tor2); PG(p_tor3); PG(p_tor4); PG(p_cot2); PG(p_vdW1); PG(k_e);
+#undef PG
+  d.r_nb = (R)o.r_nb; d.r_bond = (R)o.r_bond; d.r_hb = (R)o.r_hb; d.bo_cut = (R)o.bo_cut;
+  d.thb_cut = (R)o.thb_cut; d.thb_cutsq = (R)o.thb_cutsq; d.hb_bo_min = (R)o.hb_bo_min;
+}
+
+int round_up(double v, int m) { return (int)((std::ceil(v) + m - 1) / m) * m; }
+
+// allocate the three lists at the current capacities
+int alloc_lists(reaxff_ctx* ctx) {
+  ctx->lists.free_all();
+  DevBuf& B = ctx->lists;
+  const size_t n = ctx->n;
+  const size_t rs = ctx->fp64 ? sizeof(double) : sizeof(float);
+  FarList& f = ctx->far;
+  f.cap = ctx->cap_far;
+  f.cnt = B.alloc<int>(n);
+  f.j = B.alloc<int>(n * f.cap);
+  f.s = B.alloc<uint8_t>(n * f.cap);
+  f.H = B.alloc_bytes(n * f.cap * rs);
+  BondList& b = ctx->bond;
+  b.cap = ctx->cap_bond;
+  const size_t nb = n * b.cap;
+  b.cnt = B.alloc<int>(n);
+  b.j = B.alloc<int>(nb);
+  b.s = B.alloc<uint8_t>(nb);
+  b.mirror = B.alloc<int>(nb);
+  b.canon = B.alloc<int>(nb);
+  b.ncanon = B.alloc<int>(1);
+  void** rfields[] = {&b.dx, &b.dy, &b.dz, &b.r, &b.bo, &b.bo_pi, &b.bo_pp};
+  for (void** p : rfields) *p = B.alloc_bytes(nb * rs);
+  double** bofields[] = {&b.bop, &b.bopi, &b.bopp, &b.dbop, &b.dbopi, &b.dbopp};
+  for (double** p : bofields) *p = B.alloc<double>(nb);
+  void** dfields[] = {&b.f1, &b.fo, &b.ft, &b.df1, &b.dfo_bo, &b.dft_bo, &b.dfo_d};   // FP64 in both modes
+  for (void** p : dfields) *p = B.alloc_bytes(nb * sizeof(double));
+  b.dEdBOp = B.alloc<double>(nb);
+  b.dEdBOpi = B.alloc<double>(nb);
+  b.dEdBOpp = B.alloc<double>(nb);
+  b.cdbo = B.alloc<unsigned long long>(nb);
+  b.cdbopi = B.alloc<unsigned long long>(nb);
+  b.cdbopp = B.alloc<unsigned long long>(nb);
+  HbList& h = ctx->hb;
+  h.cap = ctx->cap_hb;
+  h.cnt = B.alloc<int>(n);
+  h.j = B.alloc<int>(n * h.cap);
+  h.s = B.alloc<uint8_t>(n * h.cap);
+  if (B.err != cudaSuccess) return fail(ctx, REAXFF_E_CUDA, "list allocation: " + cuda_err_str(B.err));
+  ctx->lists_valid = false;
+  return REAXFF_OK;
+}
+
+rx::Launch launch_of(reaxff_ctx* ctx) { return rx::Launch{ctx->st, &ctx->launches}; }
+
+int read_err(reaxff_ctx* ctx, int* flags) {
+  CK(cudaMemcpyAsync(ctx->h_err_pinned, ctx->sys.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  *flags = *ctx->h_err_pinned;
+  return REAXFF_OK;
+}
+
+int build_lists_impl(reaxff_ctx* ctx) {
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    rx::Launch L = launch_of(ctx);
+    CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
+    CK(cudaMemsetAsync(ctx->bond.ncanon, 0, sizeof(int), ctx->st));
+    rx::cells_build(L, ctx->sys, ctx->cells);
+    if (ctx->fp64) {
+      rx::far_list<double>(L, ctx->sys, ctx->cells, ctx->far, ctx->Pd, ctx->far_margin);
+      rx::bond_list<double>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pd, ctx->Pd);
+    } else {
+      rx::far_list<float>(L, ctx->sys, ctx->cells, ctx->far, ctx->Pf, ctx->far_margin);
+      rx::bond_list<float>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pf, ctx->Pd);
+    }
+    rx::bond_mirror(L, ctx->sys, ctx->bond);
+    rx::bo_prime64(L, ctx->sys, ctx->bond, ctx->aq, ctx->Pd, ctx->n * ctx->bond.cap);
+    CK(cudaGetLastError());
+    int flags = 0;
+    int rc = read_err(ctx, &flags);
+    if (rc) return rc;
+    if (flags & ERR_NAN) return fail(ctx, REAXFF_E_NAN, "non-finite value while building lists");
+    if (!(flags & (ERR_CAP_FAR | ERR_CAP_BOND | ERR_CAP_HB))) {
+      ctx->lists_valid = true;
+      return REAXFF_OK;
+    }
+    if (attempt == 2) break;
+    if (flags & ERR_CAP_FAR) ctx->cap_far = round_up(ctx->cap_far * 1.5, 32);
+    if (flags & ERR_CAP_BOND) ctx->cap_bond = round_up(ctx->cap_bond * 1.5, 8);
+    if (flags & ERR_CAP_HB) ctx->cap_hb = round_up(ctx->cap_hb * 1.5, 32);
+    int r2 = alloc_lists(ctx);
+    if (r2) return r2;
+  }
+  return fail(ctx, REAXFF_E_CAPACITY, "neighbour list capacity exceeded after regrow");
+}
+
+template <typename R> const DParams<R>* params_of(reaxff_ctx* ctx);
+template <> const DParams<double>* params_of<double>(reaxff_ctx* ctx) { return ctx->Pd; }
+template <> const DParams<float>* params_of<float>(reaxff_ctx* ctx) { return ctx->Pf; }
+
+int qeq_impl(reaxff_ctx* ctx) {
+  rx::Launch L = launch_of(ctx);
+  int rc = ctx->fp64 ? rx::qeq_solve<double>(L, ctx->sys, ctx->far, ctx->Q, ctx->Pd, ctx->chi_t, ctx->eta_t,
+                                             ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start)
+                     : rx::qeq_solve<float>(L, ctx->sys, ctx->far, ctx->Q, ctx->Pf, ctx->chi_t, ctx->eta_t,
+                                            ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start);
+  if (rc) {
+    cudaError_t e = cudaGetLastError();
+    return fail(ctx, REAXFF_E_CUDA, "cooperative QEq launch failed: " + cuda_err_str(e));
+  }
+  rx::qeq_push_history(L, ctx->n, ctx->Q);
+  return REAXFF_OK;
+}
+
+template <typename R> void terms_impl(reaxff_ctx* ctx) {
+  rx::Launch L = launch_of(ctx);
+  const DParams<R>* P = params_of<R>(ctx);
+  rx::bo_correct<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->Pd);
+  rx::atom_terms<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  rx::over_under_bond<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  rx::s_gather<R>(L, ctx->sys, ctx->bond, ctx->aq);
+  rx::angles<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  rx::torsions<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  rx::hbonds<R>(L, ctx->sys, ctx->bond, ctx->hb, ctx->acc, P, ctx->mask);
+  rx::nonbonded<R>(L, ctx->sys, ctx->far, ctx->acc, P, ctx->mask);
+  rx::chain_rule<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc);
+}
+
+int zero_accumulators(reaxff_ctx* ctx) {
+  const size_t n = ctx->n, nb = n * ctx->bond.cap;
+  CK(cudaMemsetAsync(ctx->sys.fx, 0, 3 * n * sizeof(unsigned long long), ctx->st));
+  CK(cudaMemsetAsync(ctx->bond.cdbo, 0, nb * sizeof(unsigned long long), ctx->st));
+  CK(cudaMemsetAsync(ctx->bond.cdbopi, 0, nb * sizeof(unsigned long long), ctx->st));
+  CK(cudaMemsetAsync(ctx->bond.cdbopp, 0, nb * sizeof(unsigned long long), ctx->st));
+  CK(cudaMemsetAsync(ctx->aq.cddelta, 0, n * sizeof(unsigned long long), ctx->st));
+  CK(cudaMemsetAsync(ctx->acc.e, 0, NTERMS * n * sizeof(double), ctx->st));
+  CK(cudaMemsetAsync(ctx->acc.vir, 0, 6 * n * sizeof(double), ctx->st));
+  return REAXFF_OK;
+}
+
+// lists -> (QEq) -> all terms -> chain rule; energies reduced into E_rep / vir_rep
+int forces_impl(reaxff_ctx* ctx, bool solve_q) {
+  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  int rc = build_lists_impl(ctx);
+  if (rc) return rc;
+  rc = zero_accumulators(ctx);
+  if (rc) return rc;
+  if (solve_q) {
+    rc = qeq_impl(ctx);
+    if (rc) return rc;
+  }
+  if (ctx->fp64) terms_impl<double>(ctx);
+  else terms_impl<float>(ctx);
+  rx::reduce_energies(launch_of(ctx), ctx->sys, ctx->acc, ctx->E_rep, ctx->vir_rep);
+  CK(cudaGetLastError());
+  ctx->forces_valid = true;
+  return REAXFF_OK;
+}
+
+int check_flags(reaxff_ctx* ctx, bool allow_nc) {
+  int flags = 0;
+  int rc = read_err(ctx, &flags);
+  if (rc) return rc;
+  if (flags & ERR_TIMEOUT) return fail(ctx, REAXFF_E_TIMEOUT, "a device-side wait hit its spin limit");
+  if (flags & ERR_NAN) return fail(ctx, REAXFF_E_NAN, "non-finite or out-of-range value in forces/energies");
+  if (flags & (ERR_CAP_FAR | ERR_CAP_BOND | ERR_CAP_HB))
+    return fail(ctx, REAXFF_E_CAPACITY, "list capacity exceeded");
+  if ((flags & ERR_CG) && !allow_nc) return fail(ctx, REAXFF_E_NOT_CONVERGED, "QEq reached qeq_max_iter");
+  if (flags & ERR_CG) {
+    ctx->err = "QEq reached qeq_max_iter";
+    return REAXFF_E_NOT_CONVERGED;
+  }
+  return REAXFF_OK;
+}
+
+int validate(const reaxff_params* p, const reaxff_options* o, std::string& msg) {
+  if (!p || !o) { msg = "null params/options"; return REAXFF_E_INVALID; }
+  if (p->ntypes < 1 || p->ntypes > MAXT) { msg = "ntypes out of range"; return REAXFF_E_INVALID; }
+  if (!(o->r_nb > 0 && o->r_bond > 0 && o->r_hb > 0 && o->r_bond <= o->r_nb && o->r_hb <= o->r_nb)) {
+    msg = "cutoffs must satisfy 0 < r_bond, r_hb <= r_nb"; return REAXFF_E_INVALID;
+  }
+  if (!(o->bo_cut > 0 && o->qeq_tol > 0 && o->qeq_max_iter > 0)) { msg = "bo_cut, qeq_tol, qeq_max_iter must be > 0"; return REAXFF_E_INVALID; }
+  if (o->precision != REAXFF_FP64 && o->precision != REAXFF_MIXED) { msg = "unknown precision"; return REAXFF_E_INVALID; }
+  if (o->warm_start < 0 || o->warm_start > REAXFF_WARM_MLP) { msg = "unknown warm_start"; return REAXFF_E_INVALID; }
+  for (int a = 0; a < p->ntypes; ++a)
+    if (!(p->mass[a] > 0 && p->eta[a] > 0)) { msg = "mass and eta must be > 0"; return REAXFF_E_INVALID; }
+  return REAXFF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t reaxff_sizeof_params(void) { return (int64_t)sizeof(reaxff_params); }
+int64_t reaxff_sizeof_options(void) { return (int64_t)sizeof(reaxff_options); }
+
+int64_t reaxff_params_offset(const char* field) {
+  if (!field) return -1;
+#define OFS(f) if (!strcmp(field, #f)) return (int64_t)offsetof(reaxff_params, f);
+  OFS(ntypes) OFS(hb) OFS(mass) OFS(val) OFS(vale) OFS(valboc) OFS(valang) OFS(p_lp2) OFS(p_ovun2)
+  OFS(p_ovun5) OFS(p_val3) OFS(p_val5) OFS(chi) OFS(eta) OFS(gamma_t) OFS(r0s) OFS(r0p) OFS(r0pp)
+  OFS(p_bo1) OFS(p_bo2) OFS(p_bo3) OFS(p_bo4) OFS(p_bo5) OFS(p_bo6) OFS(p_boc3) OFS(p_boc4) OFS(p_boc5)
+  OFS(ovc) OFS(v13) OFS(De_s) OFS(De_p) OFS(De_pp) OFS(p_be1) OFS(p_be2) OFS(p_ovun1) OFS(vdw_D)
+  OFS(vdw_rv) OFS(vdw_alpha) OFS(vdw_gw) OFS(gamma) OFS(th00) OFS(p_val1) OFS(p_val2) OFS(p_val4)
+  OFS(p_val7) OFS(p_pen1) OFS(p_coa1) OFS(V1) OFS(V2) OFS(V3) OFS(p_tor1) OFS(p_cot1) OFS(r0hb)
+  OFS(p_hb1) OFS(p_hb2) OFS(p_hb3) OFS(p_boc1) OFS(p_boc2) OFS(p_lp1) OFS(p_ovun3) OFS(p_ovun4)
+  OFS(p_ovun6) OFS(p_ovun7) OFS(p_ovun8) OFS(p_val6) OFS(p_val8) OFS(p_val9) OFS(p_val10) OFS(p_pen2)
+  OFS(p_pen3) OFS(p_pen4) OFS(p_coa2) OFS(p_coa3) OFS(p_coa4) OFS(p_tor2) OFS(p_tor3) OFS(p_tor4)
+  OFS(p_cot2) OFS(p_vdW1) OFS(k_e)
+#undef OFS
+  return -1;
+}
+
+const char* reaxff_last_error(const reaxff_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+int64_t reaxff_num_atoms(const reaxff_ctx* ctx) { return ctx ? ctx->n : 0; }
+int32_t reaxff_num_replicas(const reaxff_ctx* ctx) { return ctx ? ctx->nrep : 0; }
+int64_t reaxff_last_launch_count(const reaxff_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t* rep_offsets,
+                        const int32_t* types, const double* boxes, const reaxff_options* options,
+                        reaxff_ctx** out) {
+  if (!out) return REAXFF_E_INVALID;
+  *out = nullptr;
+  std::string msg;
+  int v = validate(params, options, msg);
+  if (v) return v;
+  if (nrep < 1 || !rep_offsets || !types || !boxes || rep_offsets[0] != 0) return REAXFF_E_INVALID;
+  for (int r = 0; r < nrep; ++r) {
+    if (rep_offsets[r + 1] <= rep_offsets[r]) return REAXFF_E_INVALID;
+    for (int d = 0; d < 3; ++d)
+      if (!(boxes[3 * r + d] > options->r_nb)) return REAXFF_E_INVALID;
+  }
+  const int64_t n64 = rep_offsets[nrep];
+  if (n64 > (int64_t)1 << 30) return REAXFF_E_INVALID;
+  for (int64_t i = 0; i < n64; ++i)
+    if (types[i] < 0 || types[i] >= params->ntypes) return REAXFF_E_INVALID;
+
+  reaxff_ctx* ctx = new reaxff_ctx();
+  ctx->n = (int)n64;
+  ctx->nrep = nrep;
+  ctx->hp = *params;
+  ctx->ho = *options;
+  ctx->fp64 = options->precision == REAXFF_FP64;
+  ctx->mask = options->term_mask ? (unsigned)options->term_mask : 0x1fffu;
+  ctx->h_rep_off.assign(rep_offsets, rep_offsets + nrep + 1);
+  ctx->h_box.assign(boxes, boxes + 3 * nrep);
+  ctx->h_types.assign(types, types + n64);
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev);
+  int coop = 0;
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking);
+  if (ce != cudaSuccess || !coop) {
+    delete ctx;
+    return REAXFF_E_CUDA;
+  }
+  const int n = ctx->n;
+  // ---- capacities from the densest replica
+  double rho = 0, lmax = 0;
+  for (int r = 0; r < nrep; ++r) {
+    double vol = boxes[3 * r] * boxes[3 * r + 1] * boxes[3 * r + 2];
+    rho = std::max(rho, (double)(rep_offsets[r + 1] - rep_offsets[r]) / vol);
+    for (int d = 0; d < 3; ++d) lmax = std::max(lmax, boxes[3 * r + d]);
+  }
+  const double margin = options->capacity_margin >= 1.0 ? options->capacity_margin : 1.35;
+  const double sph = 4.0 / 3.0 * M_PI;
+  ctx->cap_far = std::max(64, round_up(margin * sph * std::pow(options->r_nb, 3) * rho + 16, 32));
+  ctx->cap_bond = 24;
+  ctx->cap_hb = std::max(32, round_up(margin * sph * std::pow(options->r_hb, 3) * rho + 16, 32));
+  const double u = std::ldexp(1.0, -24);
+  ctx->far_margin = (float)(32.0 * u * (lmax * options->r_nb + options->r_nb * options->r_nb));
+  // ---- cells per replica
+  std::vector<int> nc(3 * nrep), cell_off(nrep + 1, 0);
+  for (int r = 0; r < nrep; ++r) {
+    int tot = 1;
+    for (int d = 0; d < 3; ++d) {
+      nc[3 * r + d] = std::max(1, (int)std::floor(boxes[3 * r + d] / options->r_nb));
+      tot *= nc[3 * r + d];
+    }
+    cell_off[r + 1] = cell_off[r] + tot;
+  }
+  const int ncell = cell_off[nrep];
+  // ---- fixed allocations
+  DevBuf& B = ctx->fixed;
+  ctx->Pd = B.alloc<DParams<double>>(1);
+  ctx->Pf = B.alloc<DParams<float>>(1);
+  Sys& s = ctx->sys;
+  s.n = n;
+  s.nrep = nrep;
+  int* type_d = B.alloc<int>(n);
+  int* rep_d = B.alloc<int>(n);
+  double* box_d = B.alloc<double>(3 * nrep);
+  int64_t* off_d = B.alloc<int64_t>(nrep + 1);
+  float* boxh_d = B.alloc<float>(3 * nrep);
+  float* boxl_d = B.alloc<float>(3 * nrep);
+  s.type = type_d; s.rep = rep_d; s.box = box_d; s.rep_off = off_d; s.boxh = boxh_d; s.boxl = boxl_d;
+  s.x = B.alloc<double>(n); s.y = B.alloc<double>(n); s.z = B.alloc<double>(n);
+  s.xh = B.alloc<float>(n); s.yh = B.alloc<float>(n); s.zh = B.alloc<float>(n);
+  s.xl = B.alloc<float>(n); s.yl = B.alloc<float>(n); s.zl = B.alloc<float>(n);
+  s.vx = B.alloc<double>(n); s.vy = B.alloc<double>(n); s.vz = B.alloc<double>(n);
+  unsigned long long* facc = B.alloc<unsigned long long>(3 * (size_t)n);
+  s.fx = facc; s.fy = facc ? facc + n : nullptr; s.fz = facc ? facc + 2 * (size_t)n : nullptr;
+  s.q = B.alloc<double>(n);
+  s.err = B.alloc<int>(1);
+  Cells& c = ctx->cells;
+  int* nc_d = B.alloc<int>(3 * nrep);
+  int* coff_d = B.alloc<int>(nrep + 1);
+  c.nc = nc_d; c.cell_off = coff_d; c.ncell_total = ncell;
+  c.count = B.alloc<int>(ncell); c.start = B.alloc<int>(ncell + 1); c.cursor = B.alloc<int>(ncell);
+  c.atoms = B.alloc<int>(n); c.atom_cell = B.alloc<int>(n); c.tmp = B.alloc<int>(n);
+  AtomQ& a = ctx->aq;
+  double** aqf[] = {&a.dp, &a.dpboc, &a.sumbo, &a.delta, &a.dang, &a.nlp, &a.dnlp, &a.dlp, &a.dd,
+                    &a.prodexp, &a.sbo2, &a.dsbo2, &a.sbo_fac, &a.cds, &a.A};
+  for (double** p : aqf) *p = B.alloc<double>(n);
+  a.cddelta = B.alloc<unsigned long long>(n);
+  ctx->acc.e = B.alloc<double>((size_t)NTERMS * n);
+  ctx->acc.vir = B.alloc<double>(6 * (size_t)n);
+  ctx->F_out = B.alloc<double>(3 * (size_t)n);
+  ctx->E_rep = B.alloc<double>(NTERMS * nrep);
+  ctx->vir_rep = B.alloc<double>(6 * nrep);
+  ctx->ke_rep = B.alloc<double>(nrep);
+  ctx->chi_t = B.alloc<double>(MAXT);
+  ctx->eta_t = B.alloc<double>(MAXT);
+  ctx->mass_t = B.alloc<double>(MAXT);
+  // ---- QEq state and chunking (chunks never straddle replicas)
+  rx::QeqState& Q = ctx->Q;
+  Q.grid = rx::qeq_grid_size(ctx->nsm);
+  double** qf[] = {&Q.s, &Q.t, &Q.r_s, &Q.r_t, &Q.p_s, &Q.p_t, &Q.w_s, &Q.w_t, &Q.z_s, &Q.z_t};
+  for (double** p : qf) *p = B.alloc<double>(n);
+  Q.u_s = Q.u_t = nullptr;
+  Q.hist_s = B.alloc<double>(4 * (size_t)n);
+  Q.hist_t = B.alloc<double>(3 * (size_t)n);
+  Q.nhist = 0;
+  const int rows = std::max(8, (int)((n + Q.grid - 1) / Q.grid));
+  std::vector<int> clo, crep, rchunk(nrep + 1, 0);
+  for (int r = 0; r < nrep; ++r) {
+    rchunk[r] = (int)crep.size();
+    for (int64_t i = rep_offsets[r]; i < rep_offsets[r + 1]; i += rows) {
+      clo.push_back((int)i);
+      crep.push_back(r);
+    }
+  }
+  rchunk[nrep] = (int)crep.size();
+  Q.nchunk = (int)crep.size();
+  clo.push_back(n);
+  int* clo_d = B.alloc<int>(clo.size());
+  int* crep_d = B.alloc<int>(crep.size());
+  int* rchunk_d = B.alloc<int>(nrep + 1);
+  Q.chunk_lo = clo_d; Q.chunk_rep = crep_d; Q.rep_chunk = rchunk_d;
+  Q.part = B.alloc<double>((size_t)Q.nchunk * 8);
+  Q.red = B.alloc<double>((size_t)nrep * 8);
+  Q.scal = B.alloc<double>((size_t)nrep * 16 + 1);
+  Q.iters = B.alloc<int>(2 * nrep);
+  Q.bar = B.alloc<GridBar>(1);
+  if (B.err != cudaSuccess) {
+    std::string m = "allocation: " + cuda_err_str(B.err);
+    B.free_all();
+    cudaStreamDestroy(ctx->st);
+    delete ctx;
+    (void)m;
+    return REAXFF_E_CUDA;
+  }
+  if (cudaMallocHost(&ctx->h_err_pinned, sizeof(int)) != cudaSuccess) {
+    B.free_all();
+    delete ctx;
+    return REAXFF_E_CUDA;
+  }
+  // ---- uploads
+  DParams<double> hd;
+  DParams<float> hf;
+  fill_params<double>(hd, *params, *options);
+  fill_params<float>(hf, *params, *options);
+  std::vector<int> rep_h(n);
+  for (int r = 0; r < nrep; ++r)
+    for (int64_t i = rep_offsets[r]; i < rep_offsets[r + 1]; ++i) rep_h[i] = r;
+  std::vector<float> bh(3 * nrep), bl(3 * nrep);
+  for (int k = 0; k < 3 * nrep; ++k) {
+    bh[k] = (float)boxes[k];
+    bl[k] = (float)(boxes[k] - (double)bh[k]);
+  }
+  double chi[MAXT], eta[MAXT], mass[MAXT];
+  for (int t = 0; t < MAXT; ++t) { chi[t] = params->chi[t]; eta[t] = params->eta[t]; mass[t] = params->mass[t]; }
+  cudaError_t e = cudaSuccess;
+#define UP(dst, src, bytes) if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice)
+  UP(ctx->Pd, &hd, sizeof(hd));
+  UP(ctx->Pf, &hf, sizeof(hf));
+  UP(type_d, types, n * sizeof(int));
+  UP(rep_d, rep_h.data(), n * sizeof(int));
+  UP(box_d, boxes, 3 * nrep * sizeof(double));
+  UP(off_d, rep_offsets, (nrep + 1) * sizeof(int64_t));
+  UP(boxh_d, bh.data(), 3 * nrep * sizeof(float));
+  UP(boxl_d, bl.data(), 3 * nrep * sizeof(float));
+  UP(nc_d, nc.data(), 3 * nrep * sizeof(int));
+  UP(coff_d, cell_off.data(), (nrep + 1) * sizeof(int));
+  UP(clo_d, clo.data(), clo.size() * sizeof(int));
+  UP(crep_d, crep.data(), crep.size() * sizeof(int));
+  UP(rchunk_d, rchunk.data(), (nrep + 1) * sizeof(int));
+  UP(ctx->chi_t, chi, sizeof(chi));
+  UP(ctx->eta_t, eta, sizeof(eta));
+  UP(ctx->mass_t, mass, sizeof(mass));
+#undef UP
+  if (e == cudaSuccess) e = cudaMemset(s.vx, 0, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(s.vy, 0, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(s.vz, 0, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(s.q, 0, n * sizeof(double));
+  if (e != cudaSuccess) {
+    B.free_all();
+    delete ctx;
+    return REAXFF_E_CUDA;
+  }
+  if (alloc_lists(ctx)) {
+    ctx->lists.free_all();
+    B.free_all();
+    delete ctx;
+    return REAXFF_E_CUDA;
+  }
+  *out = ctx;
+  return REAXFF_OK;
+}
+
+int reaxff_create(const reaxff_params* params, const int32_t* types, int64_t n, const double box[3],
+                  const reaxff_options* options, reaxff_ctx** out) {
+  if (n < 1 || !box) return REAXFF_E_INVALID;
+  int64_t off[2] = {0, n};
+  return reaxff_create_batch(params, 1, off, types, box, options, out);
+}
+
+void reaxff_destroy(reaxff_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  ctx->lists.free_all();
+  ctx->fixed.free_all();
+  if (ctx->h_err_pinned) cudaFreeHost(ctx->h_err_pinned);
+  if (ctx->st) cudaStreamDestroy(ctx->st);
+  delete ctx;
+}
+
+static int set_state_common(reaxff_ctx* ctx, const double* x, const double* v, cudaMemcpyKind kind,
+                            cudaStream_t user) {
+  const int n = ctx->n;
+  // positions arrive interleaved xyz; de-interleave into SoA with wrap
+  std::vector<double> hx, hv;
+  const double* xs = x;
+  const double* vs = v;
+  if (kind == cudaMemcpyDeviceToHost || kind == cudaMemcpyDeviceToDevice) {
+    hx.resize(3 * (size_t)n);
+    CK(cudaMemcpyAsync(hx.data(), x, 3 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, user));
+    if (v) {
+      hv.resize(3 * (size_t)n);
+      CK(cudaMemcpyAsync(hv.data(), v, 3 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, user));
+    }
+    CK(cudaStreamSynchronize(user));
+    xs = hx.data();
+    vs = v ? hv.data() : nullptr;
+  }
+  std::vector<double> soa(3 * (size_t)n), vsoa(3 * (size_t)n, 0.0);
+  for (int r = 0; r < ctx->nrep; ++r) {
+    for (int64_t i = ctx->h_rep_off[r]; i < ctx->h_rep_off[r + 1]; ++i) {
+      for (int d = 0; d < 3; ++d) {
+        double p = xs[3 * i + d];
+        if (!std::isfinite(p)) return fail(ctx, REAXFF_E_NAN, "non-finite position");
+        const double L = ctx->h_box[3 * r + d];
+        p = std::fmod(p, L);
+        if (p < 0) p += L;
+        if (p >= L) p -= L;
+        soa[d * (size_t)n + i] = p;
+        if (vs) vsoa[d * (size_t)n + i] = vs[3 * i + d];
+      }
+    }
+  }
+  CK(cudaMemcpyAsync(ctx->sys.x, soa.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->sys.y, soa.data() + n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->sys.z, soa.data() + 2 * (size_t)n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->sys.vx, vsoa.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->sys.vy, vsoa.data() + n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->sys.vz, vsoa.data() + 2 * (size_t)n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->have_pos = true;
+  ctx->forces_valid = false;
+  ctx->lists_valid = false;
+  ctx->Q.nhist = 0;
+  return REAXFF_OK;
+}
+
+int reaxff_set_state(reaxff_ctx* ctx, const double* x, const double* v) {
+  if (!ctx || !x) return REAXFF_E_INVALID;
+  return set_state_common(ctx, x, v, cudaMemcpyHostToHost, ctx->st);
+}
+
+int reaxff_set_state_dev(reaxff_ctx* ctx, const double* x_dev, const double* v_dev, void* stream) {
+  if (!ctx || !x_dev) return REAXFF_E_INVALID;
+  return set_state_common(ctx, x_dev, v_dev, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+}
+
+static int get_soa3(reaxff_ctx* ctx, const double* a, const double* b, const double* c, double* out) {
+  const int n = ctx->n;
+  std::vector<double> t(3 * (size_t)n);
+  CK(cudaMemcpyAsync(t.data(), a, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(t.data() + n, b, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(t.data() + 2 * (size_t)n, c, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int i = 0; i < n; ++i)
+    for (int d = 0; d < 3; ++d) out[3 * (size_t)i + d] = t[d * (size_t)n + i];
+  return REAXFF_OK;
+}
+
+int reaxff_get_state(reaxff_ctx* ctx, double* x, double* v, double* q) {
+  if (!ctx) return REAXFF_E_INVALID;
+  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  int rc;
+  if (x && (rc = get_soa3(ctx, ctx->sys.x, ctx->sys.y, ctx->sys.z, x))) return rc;
+  if (v && (rc = get_soa3(ctx, ctx->sys.vx, ctx->sys.vy, ctx->sys.vz, v))) return rc;
+  if (q) {
+    CK(cudaMemcpyAsync(q, ctx->sys.q, ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  return REAXFF_OK;
+}
+
+int reaxff_get_state_dev(reaxff_ctx* ctx, double* x_dev, double* v_dev, double* q_dev, void* stream) {
+  if (!ctx) return REAXFF_E_INVALID;
+  std::vector<double> tmp(3 * (size_t)ctx->n);
+  int rc;
+  if (x_dev) {
+    if ((rc = get_soa3(ctx, ctx->sys.x, ctx->sys.y, ctx->sys.z, tmp.data()))) return rc;
+    CK(cudaMemcpyAsync(x_dev, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+  }
+  if (v_dev) {
+    if ((rc = get_soa3(ctx, ctx->sys.vx, ctx->sys.vy, ctx->sys.vz, tmp.data()))) return rc;
+    CK(cudaMemcpyAsync(v_dev, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+  }
+  if (q_dev) {
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaMemcpyAsync(q_dev, ctx->sys.q, ctx->n * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  }
+  return REAXFF_OK;
+}
+
+int reaxff_build_lists(reaxff_ctx* ctx) {
+  if (!ctx) return REAXFF_E_INVALID;
+  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  return build_lists_impl(ctx);
+}
+
+int reaxff_get_lists(reaxff_ctx* ctx, int32_t which, int64_t capacity, int64_t* count, int32_t* i_out,
+                     int32_t* j_out, int8_t* shift) {
+  if (!ctx || !count) return REAXFF_E_INVALID;
+  if (!ctx->lists_valid) return fail(ctx, REAXFF_E_STATE, "lists not built");
+  const int n = ctx->n;
+  int cap;
+  const int *cnt_d, *j_d;
+  const uint8_t* s_d;
+  if (which == REAXFF_LIST_FAR) { cap = ctx->far.cap; cnt_d = ctx->far.cnt; j_d = ctx->far.j; s_d = ctx->far.s; }
+  else if (which == REAXFF_LIST_BOND) { cap = ctx->bond.cap; cnt_d = ctx->bond.cnt; j_d = ctx->bond.j; s_d = ctx->bond.s; }
+  else if (which == REAXFF_LIST_HBOND) { cap = ctx->hb.cap; cnt_d = ctx->hb.cnt; j_d = ctx->hb.j; s_d = ctx->hb.s; }
+  else return fail(ctx, REAXFF_E_INVALID, "unknown list");
+  std::vector<int> cnt(n);
+  CK(cudaMemcpyAsync(cnt.data(), cnt_d, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  int64_t tot = 0;
+  for (int i = 0; i < n; ++i) tot += cnt[i];
+  *count = tot;
+  if (capacity == 0 && !i_out) return REAXFF_OK;
+  if (capacity < tot || !i_out || !j_out || !shift) return fail(ctx, REAXFF_E_INVALID, "output capacity too small");
+  std::vector<int> jj((size_t)n * cap);
+  std::vector<uint8_t> ss((size_t)n * cap);
+  CK(cudaMemcpyAsync(jj.data(), j_d, jj.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(ss.data(), s_d, ss.size(), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  int64_t k = 0;
+  for (int i = 0; i < n; ++i)
+    for (int m = 0; m < cnt[i]; ++m) {
+      const size_t e = (size_t)i * cap + m;
+      i_out[k] = i;
+      j_out[k] = jj[e];
+      const int c = ss[e];
+      shift[3 * k + 0] = (int8_t)(c / 9 - 1);
+      shift[3 * k + 1] = (int8_t)((c / 3) % 3 - 1);
+      shift[3 * k + 2] = (int8_t)(c % 3 - 1);
+      ++k;
+    }
+  return REAXFF_OK;
+}
+
+int reaxff_get_bond_orders(reaxff_ctx* ctx, int64_t capacity, int64_t* count, double* bo_prime, double* bo,
+                           double* bo_pi, double* bo_pipi) {
+  if (!ctx || !count) return REAXFF_E_INVALID;
+  if (!ctx->forces_valid) return fail(ctx, REAXFF_E_STATE, "call reaxff_forces first");
+  const int n = ctx->n, cap = ctx->bond.cap;
+  std::vector<int> cnt(n);
+  CK(cudaMemcpyAsync(cnt.data(), ctx->bond.cnt, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  int64_t tot = 0;
+  for (int i = 0; i < n; ++i) tot += cnt[i];
+  *count = tot;
+  if (capacity == 0 && !bo) return REAXFF_OK;
+  if (capacity < tot) return fail(ctx, REAXFF_E_INVALID, "output capacity too small");
+  void* src[4] = {ctx->bond.bop, ctx->bond.bo, ctx->bond.bo_pi, ctx->bond.bo_pp};
+  double* dst[4] = {bo_prime, bo, bo_pi, bo_pipi};
+  for (int f = 0; f < 4; ++f) {
+    if (!dst[f]) continue;
+    const bool dbl = ctx->fp64 || f == 0;          // BO' is FP64 in both modes
+    std::vector<char> buf((size_t)n * cap * (dbl ? 8 : 4));
+    CK(cudaMemcpyAsync(buf.data(), src[f], buf.size(), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    int64_t k = 0;
+    for (int i = 0; i < n; ++i)
+      for (int m = 0; m < cnt[i]; ++m) {
+        const size_t e = (size_t)i * cap + m;
+        dst[f][k++] = dbl ? ((double*)buf.data())[e] : (double)((float*)buf.data())[e];
+      }
+  }
+  return REAXFF_OK;
+}
+
+int reaxff_qeq(reaxff_ctx* ctx, double* q_out, int32_t* iters_s, int32_t* iters_t) {
+  if (!ctx) return REAXFF_E_INVALID;
+  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  int rc = build_lists_impl(ctx);
+  if (rc) return rc;
+  rc = qeq_impl(ctx);
+  if (rc) return rc;
+  int frc = check_flags(ctx, true);
+  if (frc && frc != REAXFF_E_NOT_CONVERGED) return frc;
+  std::vector<int> it(2 * ctx->nrep);
+  CK(cudaMemcpyAsync(it.data(), ctx->Q.iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (q_out) CK(cudaMemcpyAsync(q_out, ctx->sys.q, ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int r = 0; r < ctx->nrep; ++r) {
+    if (iters_s) iters_s[r] = it[2 * r];
+    if (iters_t) iters_t[r] = it[2 * r + 1];
+  }
+  return frc;
+}
+
+static int copy_outputs(reaxff_ctx* ctx, double* F, double* E, double* virial) {
+  if (F) {
+    rx::finalize_forces(launch_of(ctx), ctx->sys, ctx->F_out);
+    CK(cudaMemcpyAsync(F, ctx->F_out, 3 * (size_t)ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  }
+  if (E) CK(cudaMemcpyAsync(E, ctx->E_rep, NTERMS * ctx->nrep * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  if (virial) CK(cudaMemcpyAsync(virial, ctx->vir_rep, 6 * ctx->nrep * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return REAXFF_OK;
+}
+
+int reaxff_forces(reaxff_ctx* ctx, double* F, double* E, double* virial) {
+  if (!ctx) return REAXFF_E_INVALID;
+  int rc = forces_impl(ctx, true);
+  if (rc) return rc;
+  int frc = check_flags(ctx, true);
+  if (frc && frc != REAXFF_E_NOT_CONVERGED) return frc;
+  rc = copy_outputs(ctx, F, E, virial);
+  return rc ? rc : frc;
+}
+
+int reaxff_forces_fixed_q(reaxff_ctx* ctx, const double* q, double* F, double* E, double* virial) {
+  if (!ctx || !q) return REAXFF_E_INVALID;
+  CK(cudaMemcpyAsync(ctx->sys.q, q, ctx->n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  int rc = forces_impl(ctx, false);
+  if (rc) return rc;
+  rc = check_flags(ctx, false);
+  if (rc) return rc;
+  return copy_outputs(ctx, F, E, virial);
+}
+
+static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev) {
+  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  ctx->launches = 0;
+  int rc;
+  if (!ctx->forces_valid) {
+    if ((rc = forces_impl(ctx, true))) return rc;
+  }
+  rx::Launch L = launch_of(ctx);
+  for (int st = 0; st < nsteps; ++st) {
+    rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 1);
+    if ((rc = forces_impl(ctx, true))) return rc;
+    rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 0);
+    if (Etot_dev) {
+      rx::kinetic(L, ctx->sys, ctx->mass_t, ctx->ke_rep);
+      rx::etot_combine(L, ctx->nrep, ctx->E_rep, ctx->ke_rep, Etot_dev + (size_t)st * ctx->nrep);
+    }
+  }
+  CK(cudaGetLastError());
+  return check_flags(ctx, false);
+}
+
+int reaxff_step(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot) {
+  if (!ctx || nsteps < 0 || !(dt_fs > 0)) return REAXFF_E_INVALID;
+  double* dev = nullptr;
+  if (E_tot && nsteps > 0) {
+    if (ctx->Etot_cap < nsteps * ctx->nrep) {
+      if (ctx->Etot_dev) cudaFree(ctx->Etot_dev);
+      ctx->Etot_dev = nullptr;
+      CK(cudaMalloc(&ctx->Etot_dev, (size_t)nsteps * ctx->nrep * sizeof(double)));
+      ctx->Etot_cap = nsteps * ctx->nrep;
+    }
+    dev = ctx->Etot_dev;
+  }
+  int rc = step_impl(ctx, nsteps, dt_fs, dev);
+  if (rc) return rc;
+  if (E_tot && nsteps > 0) {
+    CK(cudaMemcpyAsync(E_tot, dev, (size_t)nsteps * ctx->nrep * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  return REAXFF_OK;
+}
+
+int reaxff_step_dev(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot_dev, void* stream) {
+  if (!ctx || nsteps < 0 || !(dt_fs > 0)) return REAXFF_E_INVALID;
+  cudaEvent_t ev;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(ev, (cudaStream_t)stream));
+  CK(cudaStreamWaitEvent(ctx->st, ev, 0));
+  int rc = step_impl(ctx, nsteps, dt_fs, E_tot_dev);
+  CK(cudaEventRecord(ev, ctx->st));
+  CK(cudaStreamWaitEvent((cudaStream_t)stream, ev, 0));
+  cudaEventDestroy(ev);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,741 @@
+// (b) bond-order correction and (c) bonded terms, with their dE/dBO and dE/dDelta parts.
+//
+// Paper: Sec. 2.1 (bond orders, lone pair, over/under-coordination, valence angle,
+// torsion, conjugation, H-bond), Sec. 3.3 "Pairwise Interactions" (bond-order correction,
+// bond energy), "Three-body Interactions" (angles identified per central atom) and the
+// 4-body terms built on top of the bonds (Table 2 "Bond Orders", "3-body", "4-body").
+//
+// GPU form: every per-interaction derivative is split into (1) a geometric part,
+// applied at once as forces (and virial) through dE/d(interaction vectors), and (2)
+// dE/dBO, dE/dBO_pi, dE/dBO_pipi per bond entry and dE/d(sum BO) per atom, accumulated
+// in int64 fixed point and turned into forces by the chain-rule pass (forces.cu).
+// Warp per central atom (angles, H-bonds) or per central bond (torsions): lanes
+// enumerate the pairs of the centre's bonds, so skewed per-atom work stays inside one
+// warp's loop instead of one thread's.
+//
+// Functional forms (energy kcal/mol; symbols as in the parameter tables):
+//  BO correction  f1 = (A_i + A_j)/2, A_x = (V_x + f2)/(V_x + f2 + f3),
+//                 f2 = e^{-p_boc1 D'_i} + e^{-p_boc1 D'_j},
+//                 f3 = -(1/p_boc2) ln((e^{-p_boc2 D'_i} + e^{-p_boc2 D'_j})/2),
+//                 f4 = 1/(1 + e^{-p_boc3 (p_boc4 BO'^2 - D'boc_i) + p_boc5}) (f5 with j),
+//                 BO = BO' f1 f4 f5, BO_pi = BO'_pi f1^2 f4 f5, BO_pp = BO'_pp f1^2 f4 f5
+//  bond           -De_s BOs e^{p_be1 (1 - BOs^p_be2)} - De_p BO_pi - De_pp BO_pp
+//  lone pair      p_lp2 Dlp / (1 + e^{-75 Dlp}),  n_lp = e^{-p_lp1 (2 + De - 2T)^2} - T,
+//                 T = trunc(De/2), Dlp = (Vale - Val)/2 - n_lp
+//  over           (sum p_ovun1 De_s BO) Dlpc/(Dlpc + Val + 1e-8) / (1 + e^{p_ovun2 Dlpc})
+//  under          -p_ovun5 (1 - e^{p_ovun6 Dlpc}) / (1 + e^{-p_ovun2 Dlpc})
+//                 / (1 + p_ovun7 e^{p_ovun8 S}),  Dlpc = D - Dlp/(1 + p_ovun3 e^{p_ovun4 S}),
+//                 S = sum_j (D_j - Dlp_j)(BO_pi + BO_pp)
+//  valence        f7(BO_ij) f7(BO_jk) f8(Dang_j) p_val1 (1 - e^{-p_val2 (th0 - th)^2})
+//  penalty        p_pen1 f9(D_j) e^{-p_pen2 (BO_ij - 2)^2} e^{-p_pen2 (BO_jk - 2)^2}
+//  coalition      p_coa1/(1 + e^{p_coa2 Dang_j}) e^{-p_coa3 (SBO_i - BO_ij)^2}
+//                 e^{-p_coa3 (SBO_k - BO_jk)^2} e^{-p_coa4 (BO_ij - 1.5)^2} e^{-p_coa4 (BO_jk - 1.5)^2}
+//  torsion        f10 sin th1 sin th2 [V1 (1 + cos w)/2 + V2 e^{p_tor1 (2 - BO_pi,jk - f11)^2}
+//                 (1 - cos 2w)/2 + V3 (1 + cos 3w)/2]
+//  conjugation    p_cot1 prod e^{-p_cot2 (BO - 1.5)^2} [1 + (cos^2 w - 1) sin th1 sin th2]
+//  H-bond         p_hb1 (1 - e^{-p_hb2 BO_XH}) e^{-p_hb3 (r0/r + r/r0 - 2)} sin^4(th/2)
+#include "reax_internal.cuh"
+
+namespace {
+
+inline unsigned grid_for(long long threads, int block) { return (unsigned)((threads + block - 1) / block); }
+
+template <typename R> __device__ __forceinline__ R wbit(unsigned mask, int t) {
+  return ((mask >> t) & 1u) ? R(1) : R(0);
+}
+
+// ------------------------------------------------------------------ BO correction
+// The correction factors feed dE/dDelta' (a sum of large, partly cancelling terms per
+// atom), so they are evaluated and stored in FP64 in both precision modes; BO, BO_pi and
+// BO_pp are stored in the path's precision R.
+template <typename R>
+__global__ void k_bo_correct(Sys s, BondList bl, AtomQ aq, const DParams<double>* __restrict__ P) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const int ti = s.type[i];
+  const int nb = bl.cnt[i];
+  const double* BOp = bl.bop;
+  const double* BOpi = bl.bopi;
+  const double* BOpp = bl.bopp;
+  R* bo = (R*)bl.bo; R* bo_pi = (R*)bl.bo_pi; R* bo_pp = (R*)bl.bo_pp;
+  double* f1a = (double*)bl.f1; double* foa = (double*)bl.fo; double* fta = (double*)bl.ft;
+  double* df1a = (double*)bl.df1; double* dfoba = (double*)bl.dfo_bo; double* dftba = (double*)bl.dft_bo;
+  double* dfoda = (double*)bl.dfo_d;
+  const double dpo = aq.dp[i], dpbo = aq.dpboc[i];
+  for (int k = 0; k < nb; ++k) {
+    const int e = i * bl.cap + k;
+    const int j = bl.j[e];
+    const int tj = s.type[j];
+    const int pt = ti * MAXT + tj;
+    const bool own_lo = (i < j) || (i == j && bl.s[e] > 13);
+    const double dpt = aq.dp[j], dptb = aq.dpboc[j];
+    const double bp = BOp[e];
+    double f1 = 1.0, df1 = 0.0;
+    if (P->ovc[pt] > 0.0) {
+      const double dlo = own_lo ? dpo : dpt, dhi = own_lo ? dpt : dpo;
+      const double vlo = own_lo ? P->val[ti] : P->val[tj], vhi = own_lo ? P->val[tj] : P->val[ti];
+      const double e1lo = exp(-P->p_boc1 * dlo), e1hi = exp(-P->p_boc1 * dhi);
+      const double f2 = e1lo + e1hi;
+      const double e2lo = exp(-P->p_boc2 * dlo), e2hi = exp(-P->p_boc2 * dhi);
+      const double ssum = e2lo + e2hi;
+      const double f3 = -(1.0 / P->p_boc2) * log(0.5 * ssum);
+      const double dlo_den = vlo + f2 + f3, dhi_den = vhi + f2 + f3;
+      f1 = 0.5 * ((vlo + f2) / dlo_den + (vhi + f2) / dhi_den);
+      const double df2 = -P->p_boc1 * (own_lo ? e1lo : e1hi);
+      const double df3 = (own_lo ? e2lo : e2hi) / ssum;
+      const double dAlo = (f3 * df2 - (vlo + f2) * df3) / (dlo_den * dlo_den);
+      const double dAhi = (f3 * df2 - (vhi + f2) * df3) / (dhi_den * dhi_den);
+      df1 = 0.5 * (dAlo + dAhi);
+    }
+    double fo = 1.0, ft = 1.0, dfo_bo = 0.0, dft_bo = 0.0, dfo_d = 0.0;
+    if (P->v13[pt] > 0.0) {
+      const double p3 = P->p_boc3[pt], p4 = P->p_boc4[pt], p5 = P->p_boc5[pt];
+      double sdo, sdt;
+      sig_pair<double>(-p3 * (p4 * bp * bp - dpbo) + p5, fo, sdo);
+      sig_pair<double>(-p3 * (p4 * bp * bp - dptb) + p5, ft, sdt);
+      dfo_bo = 2.0 * p3 * p4 * bp * sdo;
+      dft_bo = 2.0 * p3 * p4 * bp * sdt;
+      dfo_d = -p3 * sdo;
+    }
+    const double flo = own_lo ? fo : ft, fhi = own_lo ? ft : fo;
+    const double F = f1 * flo * fhi;
+    const double G = f1 * f1 * flo * fhi;
+    bo[e] = (R)(bp * F);
+    bo_pi[e] = (R)(BOpi[e] * G);
+    bo_pp[e] = (R)(BOpp[e] * G);
+    f1a[e] = f1; foa[e] = fo; fta[e] = ft; df1a[e] = df1;
+    dfoba[e] = dfo_bo; dftba[e] = dft_bo; dfoda[e] = dfo_d;
+  }
+}
+
+// ------------------------------------------------------------------ atom terms + lone pair
+template <typename R>
+__global__ void k_atom_terms(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<R>* __restrict__ P,
+                             unsigned mask) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const int ti = s.type[i];
+  const int nb = bl.cnt[i];
+  const R* bo = (const R*)bl.bo;
+  const R* bo_pi = (const R*)bl.bo_pi;
+  const R* bo_pp = (const R*)bl.bo_pp;
+  double sumbo = 0, pisum = 0, sum8 = 0;                 // sums in FP64
+  for (int k = 0; k < nb; ++k) {
+    const int e = i * bl.cap + k;
+    const R b = bo[e];
+    const R b2 = b * b, b4 = b2 * b2;
+    sumbo += (double)b;
+    pisum += (double)(bo_pi[e] + bo_pp[e]);
+    sum8 += (double)(b4 * b4);
+  }
+  const double delta = sumbo - (double)P->val[ti];
+  const double dele = sumbo - (double)P->vale[ti];
+  const double dang = sumbo - (double)P->valang[ti];
+  const double T = trunc(dele * 0.5);
+  const R el = (R)(2.0 + dele - 2.0 * T);
+  const R enlp = m_exp(-P->p_lp1 * el * el);
+  const double nlp = (double)enlp - T;
+  const R dnlp = R(-2) * P->p_lp1 * el * enlp;
+  const double dlp = 0.5 * ((double)P->vale[ti] - (double)P->val[ti]) - nlp;
+  R sg, sgd;
+  sig_pair<R>(R(-75) * (R)dlp, sg, sgd);                  // 1/(1+e^{-75 dlp})
+  const R elp = P->p_lp2[ti] * (R)dlp * sg;
+  const R delp = P->p_lp2[ti] * (sg + R(75) * (R)dlp * sgd);
+  fix_add(aq.cddelta + i, (double)(wbit<R>(mask, T_LP) * delp * (-dnlp)), s.err);
+  const R prodexp = m_exp(-(R)sum8);
+  const double sbo_fac = -dang - (double)P->p_val8 * nlp;
+  const R sbo = (R)(pisum + (1.0 - (double)prodexp) * sbo_fac);
+  R sbo2, dsbo2;
+  const R p9 = P->p_val9;
+  if (sbo <= R(0)) {
+    sbo2 = 0; dsbo2 = 0;
+  } else if (sbo < R(1)) {
+    sbo2 = m_pow(sbo, p9);
+    dsbo2 = p9 * m_pow(sbo, p9 - R(1));
+  } else if (sbo < R(2)) {
+    sbo2 = R(2) - m_pow(R(2) - sbo, p9);
+    dsbo2 = p9 * m_pow(R(2) - sbo, p9 - R(1));
+  } else {
+    sbo2 = 2; dsbo2 = 0;
+  }
+  aq.sumbo[i] = sumbo;
+  aq.delta[i] = delta;
+  aq.dang[i] = dang;
+  aq.nlp[i] = nlp;
+  aq.dnlp[i] = dnlp;
+  aq.dlp[i] = dlp;
+  aq.dd[i] = delta - dlp;
+  aq.prodexp[i] = prodexp;
+  aq.sbo2[i] = sbo2;
+  aq.dsbo2[i] = dsbo2;
+  aq.sbo_fac[i] = sbo_fac;
+  acc.e[T_LP * s.n + i] = elp;
+}
+
+// ------------------------------------------------------------------ over/under + bond energy
+template <typename R>
+__global__ void k_over_under_bond(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<R>* __restrict__ P,
+                                  unsigned mask) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const int ti = s.type[i];
+  const int nb = bl.cnt[i];
+  const R* bo = (const R*)bl.bo;
+  const R* bo_pi = (const R*)bl.bo_pi;
+  const R* bo_pp = (const R*)bl.bo_pp;
+  double S = 0, sov = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int e = i * bl.cap + k;
+    const int j = bl.j[e];
+    const int pt = ti * MAXT + s.type[j];
+    S += aq.dd[j] * (double)(bo_pi[e] + bo_pp[e]);
+    sov += (double)(P->p_ovun1[pt] * P->De_s[pt] * bo[e]);
+  }
+  const double delta = aq.delta[i], dlp = aq.dlp[i];
+  const R dnlp = (R)aq.dnlp[i];
+  const R V = P->val[ti];
+  const R e4 = m_expc(P->p_ovun4 * (R)S);
+  const R den = R(1) + P->p_ovun3 * e4;
+  const R dlpc = (R)(delta - dlp / (double)den);
+  const R ddlpc_dS = (R)dlp * P->p_ovun3 * P->p_ovun4 * e4 / (den * den);
+  // over
+  const R gd = dlpc + V + R(1e-8);
+  const R g = dlpc / gd;
+  const R dg = (V + R(1e-8)) / (gd * gd);
+  const R p2 = P->p_ovun2[ti];
+  R s1, s1d;
+  sig_pair<R>(p2 * dlpc, s1, s1d);                     // 1/(1+e^{p2 dlpc})
+  const R ds1 = -p2 * s1d;
+  const R eover = (R)sov * g * s1;
+  const R deover = (R)sov * (dg * s1 + g * ds1);
+  // under
+  const R em6 = m_expm1(P->p_ovun6 * dlpc);            // e^{p6 dlpc} - 1
+  const R e6 = em6 + R(1);
+  R s2, s2d;
+  sig_pair<R>(-p2 * dlpc, s2, s2d);                    // 1/(1+e^{-p2 dlpc})
+  const R ds2 = p2 * s2d;
+  const R e8 = m_expc(P->p_ovun8 * (R)S);
+  const R h = R(1) / (R(1) + P->p_ovun7 * e8);
+  const R dh = -h * h * P->p_ovun7 * P->p_ovun8 * e8;
+  const R p5 = P->p_ovun5[ti];
+  const R eunder = p5 * em6 * s2 * h;
+  const R deunder = -p5 * (-P->p_ovun6 * e6 * s2 + (-em6) * ds2) * h;
+  const R deunder_S = p5 * em6 * s2 * dh;
+  const R wo = wbit<R>(mask, T_OVER), wu = wbit<R>(mask, T_UNDER);
+  const R cdlpc = wo * deover + wu * deunder;
+  const R cds = cdlpc * ddlpc_dS + wu * deunder_S;
+  fix_add(aq.cddelta + i, (double)(cdlpc * (R(1) + dnlp / den)), s.err);
+  aq.cds[i] = cds;
+  acc.e[T_OVER * s.n + i] = eover;
+  acc.e[T_UNDER * s.n + i] = eunder;
+  const R dov_dsum = wo * g * s1;
+  // bond energy on the canonical half of i's row
+  const R wb = wbit<R>(mask, T_BOND);
+  double ebond = 0.0;
+  for (int k = 0; k < nb; ++k) {
+    const int e = i * bl.cap + k;
+    const int j = bl.j[e];
+    const int pt = ti * MAXT + s.type[j];
+    const R cdd = (R)aq.dd[j];
+    R cb = dov_dsum * P->p_ovun1[pt] * P->De_s[pt];
+    R cpi = cds * cdd, cpp = cds * cdd;
+    if ((i < j) || (i == j && bl.s[e] > 13)) {
+      const R b = bo[e], bpi = bo_pi[e], bpp = bo_pp[e];
+      const R bs = b - bpi - bpp;
+      R es = 0, des = 0;
+      if (bs > R(0)) {
+        const R pw = m_pow(bs, P->p_be2[pt]);
+        const R ex = m_exp(P->p_be1[pt] * (R(1) - pw));
+        es = -P->De_s[pt] * bs * ex;
+        des = -P->De_s[pt] * ex * (R(1) - P->p_be1[pt] * P->p_be2[pt] * pw);
+      }
+      ebond += (double)(es - P->De_p[pt] * bpi - P->De_pp[pt] * bpp);
+      cb += wb * des;
+      cpi += wb * (-des - P->De_p[pt]);
+      cpp += wb * (-des - P->De_pp[pt]);
+    }
+    fix_add(bl.cdbo + e, (double)cb, s.err);
+    fix_add(bl.cdbopi + e, (double)cpi, s.err);
+    fix_add(bl.cdbopp + e, (double)cpp, s.err);
+  }
+  acc.e[T_BOND * s.n + i] = ebond;
+}
+
+// dE/dS_i reaches neighbour j through D_j - Dlp_j: gathered by j over its own row
+template <typename R>
+__global__ void k_s_gather(Sys s, BondList bl, AtomQ aq) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const int nb = bl.cnt[i];
+  const R* bo_pi = (const R*)bl.bo_pi;
+  const R* bo_pp = (const R*)bl.bo_pp;
+  double acc = 0.0;
+  for (int k = 0; k < nb; ++k) {
+    const int e = i * bl.cap + k;
+    acc += aq.cds[bl.j[e]] * (double)(bo_pi[e] + bo_pp[e]);
+  }
+  fix_add(aq.cddelta + i, acc * (1.0 + aq.dnlp[i]), s.err);
+}
+
+// ------------------------------------------------------------------ geometry helpers
+template <typename R> struct Vec3 { R x, y, z; };
+template <typename R> __device__ __forceinline__ R dot3(const Vec3<R>& a, const Vec3<R>& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <typename R> __device__ __forceinline__ Vec3<R> lin2(R a, const Vec3<R>& u, R b, const Vec3<R>& v) {
+  return Vec3<R>{a * u.x + b * v.x, a * u.y + b * v.y, a * u.z + b * v.z};
+}
+template <typename R> __device__ __forceinline__ Vec3<R> cross3(const Vec3<R>& a, const Vec3<R>& b) {
+  return Vec3<R>{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+// cross product with each component a correctly-rounded difference of products
+template <typename R> __device__ __forceinline__ Vec3<R> cross_acc(const Vec3<R>& a, const Vec3<R>& b) {
+  return Vec3<R>{diff_prod(a.y, b.z, a.z, b.y), diff_prod(a.z, b.x, a.x, b.z), diff_prod(a.x, b.y, a.y, b.x)};
+}
+template <typename R>
+__device__ __forceinline__ Vec3<R> load_vec(const BondList& bl, int e) {
+  return Vec3<R>{((const R*)bl.dx)[e], ((const R*)bl.dy)[e], ((const R*)bl.dz)[e]};
+}
+__device__ __forceinline__ void force_add(const Sys& s, int a, double fx, double fy, double fz) {
+  fix_add(s.fx + a, fx, s.err);
+  fix_add(s.fy + a, fy, s.err);
+  fix_add(s.fz + a, fz, s.err);
+}
+// virial W_ab -= g_a v_b (xx yy zz xy xz yz)
+template <typename R>
+__device__ __forceinline__ void vir_sub(double* w, const Vec3<R>& g, const Vec3<R>& v) {
+  w[0] -= (double)(g.x * v.x); w[1] -= (double)(g.y * v.y); w[2] -= (double)(g.z * v.z);
+  w[3] -= (double)(g.x * v.y); w[4] -= (double)(g.x * v.z); w[5] -= (double)(g.y * v.z);
+}
+// f9-type function (2 + e^{-a D}) / (1 + e^{-a D} + e^{b D}) and its D-derivative,
+// written with u = e^{-aD}/den, v = e^{bD}/den in [0, 1] so no intermediate overflows:
+// df/dD = (a u - 2 b v)/den - (a + b) u v
+template <typename R> __device__ __forceinline__ void f9fun(R a, R b, R D, R& f, R& df) {
+  const R e3 = m_expc(-a * D), e4 = m_expc(b * D);
+  const R den = R(1) + e3 + e4;
+  const R u = e3 / den, v = e4 / den;
+  f = R(2) / den + u;
+  df = (a * u - R(2) * b * v) / den - (a + b) * u * v;
+}
+
+// ------------------------------------------------------------------ valence angles
+template <typename R>
+__global__ void k_angles(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<R>* __restrict__ P,
+                         unsigned mask) {
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (j >= s.n) return;
+  const int nb = bl.cnt[j];
+  if (nb < 2) return;
+  const int tj = s.type[j];
+  const R* bo = (const R*)bl.bo;
+  const R dang = (R)aq.dang[j], delta = (R)aq.delta[j];
+  const R sbo2 = (R)aq.sbo2[j];
+  const R wv = wbit<R>(mask, T_VAL), wp = wbit<R>(mask, T_PEN), wc = wbit<R>(mask, T_COA);
+  // centre-only factors
+  const R pv5 = P->p_val5[tj];
+  const R e6 = m_expc(P->p_val6 * dang);
+  const R ex2 = m_exp(-P->p_val10 * (R(2) - sbo2));
+  const R dth0_dsbo2 = ex2 * P->p_val10;              // times th00
+  R f9, df9;
+  f9fun<R>(P->p_pen3, P->p_pen4, delta, f9, df9);
+  R scoa, scoad;
+  sig_pair<R>(P->p_coa2 * dang, scoa, scoad);
+  double eval = 0, epen = 0, ecoa = 0, cdsbo = 0, cdd = 0;
+  double fj[3] = {0, 0, 0}, w[6] = {0, 0, 0, 0, 0, 0};
+  const int npair = nb * (nb - 1) / 2;
+  for (int p = lane; p < npair; p += 32) {
+    int a = 0, rem = p;
+    while (rem >= nb - 1 - a) { rem -= nb - 1 - a; ++a; }
+    const int b = a + 1 + rem;
+    const int ea = j * bl.cap + a, eb = j * bl.cap + b;
+    const R BOa = bo[ea], BOb = bo[eb];
+    if (!(BOa > P->thb_cut && BOb > P->thb_cut && BOa * BOb > P->thb_cutsq)) continue;
+    const int i = bl.j[ea], k = bl.j[eb];
+    const int ti = s.type[i], tk = s.type[k];
+    const int t3 = (ti * MAXT + tj) * MAXT + tk;
+    const Vec3<R> u = load_vec<R>(bl, ea), v = load_vec<R>(bl, eb);
+    const R L1 = dot3(u, u), L2 = dot3(v, v);
+    // theta = atan2(|u x v|, u.v): accurate at every angle; d theta/du = (u x n^)/|u|^2,
+    // d theta/dv = (n^ x v)/|v|^2 with n^ = (u x v)/|u x v|
+    const Vec3<R> nrm = cross_acc(u, v);
+    const R nn = m_sqrt(dot3(nrm, nrm));
+    const R th = m_atan2(nn, dot3(u, v));
+    const bool cok = nn > R(0);
+    // valence
+    const R th00 = P->th00[t3];
+    const R th0 = R(3.14159265358979323846) - th00 * (R(1) - ex2);
+    const R pv3 = P->p_val3[tj], pv4 = P->p_val4[t3];
+    const R pa = m_pow(BOa, pv4), pb = m_pow(BOb, pv4);
+    const R ea7 = m_exp(-pv3 * pa), eb7 = m_exp(-pv3 * pb);
+    const R f7a = -m_expm1(-pv3 * pa), f7b = -m_expm1(-pv3 * pb);
+    const R df7a = ea7 * pv3 * pv4 * pa / BOa, df7b = eb7 * pv3 * pv4 * pb / BOb;
+    // f8 = pv5 - (pv5 - 1)(2 + e6)/(1 + e6 + e7); with u = e6/den, v = e7/den:
+    // d[(2 + e6)/den]/dDang = (2 p7 v - p6 u)/den + (p6 + p7) u v
+    const R p7 = P->p_val7[t3];
+    const R e7 = m_expc(-p7 * dang);
+    const R den8 = R(1) + e6 + e7;
+    const R u8 = e6 / den8, v8 = e7 / den8;
+    const R f8 = pv5 - (pv5 - R(1)) * (R(2) / den8 + u8);
+    const R df8 = -(pv5 - R(1)) * ((R(2) * p7 * v8 - P->p_val6 * u8) / den8 + (P->p_val6 + p7) * u8 * v8);
+    const R pv1 = P->p_val1[t3], pv2 = P->p_val2[t3];
+    const R D = th0 - th;
+    const R exv = m_exp(-pv2 * D * D);
+    const R gth = -m_expm1(-pv2 * D * D);
+    const R Cv = f7a * f7b * f8 * pv1;
+    const R ev = Cv * gth;
+    const R dEdD = Cv * exv * R(2) * pv2 * D;          // d/dD of Cv (1 - e^{-pv2 D^2})
+    const R dEv_dth = -dEdD;
+    const R dEv_dsbo2 = dEdD * th00 * dth0_dsbo2;
+    // penalty
+    const R pp2 = P->p_pen2;
+    const R ga = m_exp(-pp2 * (BOa - R(2)) * (BOa - R(2))), gb = m_exp(-pp2 * (BOb - R(2)) * (BOb - R(2)));
+    const R ep = P->p_pen1[t3] * f9 * ga * gb;
+    // coalition
+    const R sbi = (R)(aq.sumbo[i] - (double)BOa), sbk = (R)(aq.sumbo[k] - (double)BOb);
+    const R pc3 = P->p_coa3, pc4 = P->p_coa4;
+    const R ec = P->p_coa1[t3] * scoa * m_exp(-pc3 * sbi * sbi) * m_exp(-pc3 * sbk * sbk) *
+                 m_exp(-pc4 * (BOa - R(1.5)) * (BOa - R(1.5))) * m_exp(-pc4 * (BOb - R(1.5)) * (BOb - R(1.5)));
+    eval += (double)ev;
+    epen += (double)ep;
+    ecoa += (double)ec;
+    // bond-order and Delta derivatives
+    const R dBOa = wv * df7a * f7b * f8 * pv1 * gth + wp * ep * (R(-2) * pp2 * (BOa - R(2))) +
+                   wc * ec * (R(2) * pc3 * sbi - R(2) * pc4 * (BOa - R(1.5)));
+    const R dBOb = wv * f7a * df7b * f8 * pv1 * gth + wp * ep * (R(-2) * pp2 * (BOb - R(2))) +
+                   wc * ec * (R(2) * pc3 * sbk - R(2) * pc4 * (BOb - R(1.5)));
+    fix_add(bl.cdbo + ea, (double)dBOa, s.err);
+    fix_add(bl.cdbo + eb, (double)dBOb, s.err);
+    fix_add(aq.cddelta + i, (double)(wc * ec * (R(-2) * pc3 * sbi)), s.err);
+    fix_add(aq.cddelta + k, (double)(wc * ec * (R(-2) * pc3 * sbk)), s.err);
+    cdd += (double)(wv * f7a * f7b * df8 * pv1 * gth + wp * P->p_pen1[t3] * df9 * ga * gb +
+                    wc * (scoa > R(0) ? -ec * P->p_coa2 * scoad / scoa : R(0)));
+    cdsbo += (double)(wv * dEv_dsbo2);
+    // geometry: E depends on cos(theta) only through the valence term
+    if (cok) {
+      const R gt = wv * dEv_dth / nn;
+      const Vec3<R> cu = cross3(u, nrm), cv = cross3(nrm, v);
+      const Vec3<R> gu = Vec3<R>{gt * cu.x / L1, gt * cu.y / L1, gt * cu.z / L1};
+      const Vec3<R> gv = Vec3<R>{gt * cv.x / L2, gt * cv.y / L2, gt * cv.z / L2};
+      force_add(s, i, -(double)gu.x, -(double)gu.y, -(double)gu.z);
+      force_add(s, k, -(double)gv.x, -(double)gv.y, -(double)gv.z);
+      fj[0] += (double)(gu.x + gv.x); fj[1] += (double)(gu.y + gv.y); fj[2] += (double)(gu.z + gv.z);
+      vir_sub(w, gu, u);
+      vir_sub(w, gv, v);
+    }
+  }
+  eval = warp_sum(eval); epen = warp_sum(epen); ecoa = warp_sum(ecoa);
+  cdsbo = warp_sum(cdsbo); cdd = warp_sum(cdd);
+  for (int q = 0; q < 3; ++q) fj[q] = warp_sum(fj[q]);
+  for (int q = 0; q < 6; ++q) w[q] = warp_sum(w[q]);
+  cdsbo *= aq.dsbo2[j];                                // dE/dSBO
+  const double prod = aq.prodexp[j];
+  if (lane == 0) {
+    acc.e[T_VAL * s.n + j] = eval;
+    acc.e[T_PEN * s.n + j] = epen;
+    acc.e[T_COA * s.n + j] = ecoa;
+    force_add(s, j, fj[0], fj[1], fj[2]);
+    const double dsbo_dsum = -(1.0 - prod) * (1.0 + (double)P->p_val8 * aq.dnlp[j]);
+    fix_add(aq.cddelta + j, cdd + cdsbo * dsbo_dsum, s.err);
+    for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
+  }
+  // SBO depends on every bond of j: distribute dE/dSBO over j's row
+  if (cdsbo != 0.0) {
+    const double fac = aq.sbo_fac[j];
+    for (int k = lane; k < nb; k += 32) {
+      const int e = j * bl.cap + k;
+      const double b = (double)bo[e];
+      const double b2 = b * b, b4 = b2 * b2;
+      fix_add(bl.cdbopi + e, cdsbo, s.err);
+      fix_add(bl.cdbopp + e, cdsbo, s.err);
+      fix_add(bl.cdbo + e, cdsbo * prod * 8.0 * b4 * b2 * b * fac, s.err);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ torsion + conjugation
+template <typename R>
+__global__ void k_torsions(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<R>* __restrict__ P,
+                           unsigned mask) {
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (j >= s.n) return;
+  const int nbj = bl.cnt[j];
+  if (nbj < 2) return;
+  const R* bo = (const R*)bl.bo;
+  const R* bo_pi = (const R*)bl.bo_pi;
+  const R wt = wbit<R>(mask, T_TORS), wcj = wbit<R>(mask, T_CONJ);
+  const int tj = s.type[j];
+  double etor = 0, econ = 0, fj[3] = {0, 0, 0}, w[6] = {0, 0, 0, 0, 0, 0}, cddj = 0;
+  for (int cb = 0; cb < nbj; ++cb) {
+    const int ejk = j * bl.cap + cb;
+    const int k = bl.j[ejk];
+    const int codejk = bl.s[ejk];
+    if (!((j < k) || (j == k && codejk > 13))) continue;
+    const R BO2 = bo[ejk];
+    if (!(BO2 > P->thb_cut)) continue;
+    const int nbk = bl.cnt[k];
+    if (nbk < 2) continue;
+    const int ekj = bl.mirror[ejk];
+    if (ekj / bl.cap != k) continue;                 // mirror missing (flagged by the list pass)
+    const int tk = s.type[k];
+    const int pt = tj * MAXT + tk;
+    const R V1 = P->V1[pt], V2 = P->V2[pt], V3 = P->V3[pt], pt1 = P->p_tor1[pt], pc1 = P->p_cot1[pt];
+    const R pt2 = P->p_tor2, pc2 = P->p_cot2;
+    const R BOpi2 = bo_pi[ejk];
+    const R Dsum = (R)(aq.dang[j] + aq.dang[k]);
+    R f11, df11;
+    f9fun<R>(P->p_tor3, P->p_tor4, Dsum, f11, df11);
+    const R xb = R(2) - BOpi2 - f11;
+    const R ex = m_exp(pt1 * xb * xb);
+    const R g2 = -m_expm1(-pt2 * BO2), dg2 = pt2 * m_exp(-pt2 * BO2);
+    const R h2 = m_exp(-pc2 * (BO2 - R(1.5)) * (BO2 - R(1.5)));
+    const Vec3<R> u2 = load_vec<R>(bl, ejk);
+    const R L2 = dot3(u2, u2), l2 = m_sqrt(L2);
+    int sjk[3];
+    shift_decode(codejk, sjk[0], sjk[1], sjk[2]);
+    double fk[3] = {0, 0, 0}, cddk = 0, cdbo2 = 0, cdbopi2 = 0;
+    const int ntot = (nbj - 1) * (nbk - 1);
+    for (int p = lane; p < ntot; p += 32) {
+      int ia = p / (nbk - 1), ic = p % (nbk - 1);
+      const int ea = j * bl.cap + ia + (j * bl.cap + ia >= ejk ? 1 : 0);
+      int ec = k * bl.cap + ic;
+      if (ec >= ekj) ++ec;
+      const int i = bl.j[ea], l = bl.j[ec];
+      if (i == l) {
+        int si[3], sl[3];
+        shift_decode(bl.s[ea], si[0], si[1], si[2]);
+        shift_decode(bl.s[ec], sl[0], sl[1], sl[2]);
+        if (si[0] == sjk[0] + sl[0] && si[1] == sjk[1] + sl[1] && si[2] == sjk[2] + sl[2]) continue;
+      }
+      const R BO1 = bo[ea], BO3 = bo[ec];
+      if (!(BO1 * BO2 * BO3 > P->thb_cut)) continue;
+      const Vec3<R> u1 = load_vec<R>(bl, ea), u3 = load_vec<R>(bl, ec);
+      // Well-conditioned torsion geometry: n1 = u1 x u2, n2 = u3 x u2, A = |n1|, B = |n2|,
+      // P = n1.n2, V = u3.n1 (L2 V^2 = A^2 B^2 - P^2), D0 = l1 l2^2 l3. Then
+      //   s1 s2 = A B / D0 = S,  s1 s2 cos w = P / D0 = C,  s1 s2 cos^3 w = P^3/(A^2 B^2 D0) = M,
+      //   s1 s2 (1 - cos^2 w) = V^2 / (A B l1 l3) = Y,
+      //   E_tors = f10 [V1 (S + C)/2 + V2 e Y + V3 (S + 4M - 3C)/2],  E_conj = K (1 - Y).
+      const Vec3<R> n1 = cross_acc(u1, u2), n2 = cross_acc(u3, u2);
+      const R A2 = dot3(n1, n1), B2 = dot3(n2, n2);
+      const R L1 = dot3(u1, u1), L3 = dot3(u3, u3);
+      const R l1 = m_sqrt(L1), l3 = m_sqrt(L3);
+      const R Am = m_sqrt(A2), Bm = m_sqrt(B2);
+      if (!(Am > R(1e-10) * l1 * l2 && Bm > R(1e-10) * l2 * l3)) continue;   // collinear: sin th ~ 0
+      const R Pn = dot3(n1, n2);
+      const R Vt = dot3(u3, n1);
+      const R D0 = l1 * L2 * l3;
+      const R cw = rclamp(Pn / (Am * Bm), R(-1), R(1));
+      const R S = Am * Bm / D0, Cc = Pn / D0, M = cw * cw * Cc, Y = Vt * Vt / (Am * Bm * l1 * l3);
+      // energy
+      const R g1 = -m_expm1(-pt2 * BO1), g3 = -m_expm1(-pt2 * BO3);
+      const R dg1 = pt2 * m_exp(-pt2 * BO1), dg3 = pt2 * m_exp(-pt2 * BO3);
+      const R f10 = g1 * g2 * g3;
+      const R Tsum = R(0.5) * V1 * (S + Cc) + V2 * ex * Y + R(0.5) * V3 * (S + R(4) * M - R(3) * Cc);
+      const R h1 = m_exp(-pc2 * (BO1 - R(1.5)) * (BO1 - R(1.5)));
+      const R h3 = m_exp(-pc2 * (BO3 - R(1.5)) * (BO3 - R(1.5)));
+      const R K = pc1 * h1 * h2 * h3;
+      const R et = f10 * Tsum;
+      const R ecj = K * (R(1) - Y);
+      etor += (double)et;
+      econ += (double)ecj;
+      // non-geometric derivatives
+      const R dBO1 = wt * dg1 * g2 * g3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO1 - R(1.5)));
+      const R dBO3 = wt * g1 * g2 * dg3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO3 - R(1.5)));
+      const R dBO2 = wt * g1 * dg2 * g3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO2 - R(1.5)));
+      const R dTdx = V2 * Y * ex * pt1 * R(2) * xb;   // d Tsum / d xb
+      const R dpi = wt * f10 * dTdx * R(-1);
+      const R dD = wt * f10 * dTdx * (-df11);
+      fix_add(bl.cdbo + ea, (double)dBO1, s.err);
+      fix_add(bl.cdbo + ec, (double)dBO3, s.err);
+      cdbo2 += (double)dBO2;
+      cdbopi2 += (double)dpi;
+      cddj += (double)dD;
+      cddk += (double)dD;
+      // geometric derivatives through (A, B, P, V, l1, l2, l3)
+      const R dES = wt * f10 * R(0.5) * (V1 + V3);
+      const R dEC = wt * f10 * (R(0.5) * V1 - R(1.5) * V3);
+      const R dEM = wt * f10 * R(2) * V3;
+      const R dEY = wt * f10 * V2 * ex - wcj * K;
+      const R gA = (dES * S - R(2) * dEM * M - dEY * Y) / Am;
+      const R gB = (dES * S - R(2) * dEM * M - dEY * Y) / Bm;
+      const R gP = (dEC + dEM * R(3) * cw * cw) / D0;
+      const R gV = dEY * R(2) * Vt / (Am * Bm * l1 * l3);
+      const R T0 = dES * S + dEC * Cc + dEM * M;
+      const R gl1 = -(T0 + dEY * Y) / L1;             // per unit of u1 (d l1 / d u1 = u1 / l1)
+      const R gl2 = R(-2) * T0 / L2;
+      const R gl3 = -(T0 + dEY * Y) / L3;
+      const R iA = gA / Am, iB = gB / Bm;
+      // dA/du1 = (u2 x n1)/A, dA/du2 = (n1 x u1)/A, dB/du3 = (u2 x n2)/B, dB/du2 = (n2 x u3)/B
+      // dP/du1 = u2 x n2, dP/du2 = n2 x u1 + n1 x u3, dP/du3 = u2 x n1
+      // dV/du1 = u2 x u3, dV/du2 = u3 x u1, dV/du3 = n1
+      const Vec3<R> u2n1 = cross3(u2, n1), u2n2 = cross3(u2, n2), u2u3 = cross3(u2, u3);
+      const Vec3<R> n1u1 = cross3(n1, u1), n2u3 = cross3(n2, u3), n2u1 = cross3(n2, u1), n1u3 = cross3(n1, u3);
+      const Vec3<R> u3u1 = cross3(u3, u1);
+      Vec3<R> gg1, gg2, gg3;
+      gg1.x = iA * u2n1.x + gP * u2n2.x + gV * u2u3.x + gl1 * u1.x;
+      gg1.y = iA * u2n1.y + gP * u2n2.y + gV * u2u3.y + gl1 * u1.y;
+      gg1.z = iA * u2n1.z + gP * u2n2.z + gV * u2u3.z + gl1 * u1.z;
+      gg2.x = iA * n1u1.x + iB * n2u3.x + gP * (n2u1.x + n1u3.x) + gV * u3u1.x + gl2 * u2.x;
+      gg2.y = iA * n1u1.y + iB * n2u3.y + gP * (n2u1.y + n1u3.y) + gV * u3u1.y + gl2 * u2.y;
+      gg2.z = iA * n1u1.z + iB * n2u3.z + gP * (n2u1.z + n1u3.z) + gV * u3u1.z + gl2 * u2.z;
+      gg3.x = iB * u2n2.x + gP * u2n1.x + gV * n1.x + gl3 * u3.x;
+      gg3.y = iB * u2n2.y + gP * u2n1.y + gV * n1.y + gl3 * u3.y;
+      gg3.z = iB * u2n2.z + gP * u2n1.z + gV * n1.z + gl3 * u3.z;
+      force_add(s, i, -(double)gg1.x, -(double)gg1.y, -(double)gg1.z);
+      force_add(s, l, -(double)gg3.x, -(double)gg3.y, -(double)gg3.z);
+      fj[0] += (double)(gg1.x + gg2.x); fj[1] += (double)(gg1.y + gg2.y); fj[2] += (double)(gg1.z + gg2.z);
+      fk[0] += (double)(gg3.x - gg2.x); fk[1] += (double)(gg3.y - gg2.y); fk[2] += (double)(gg3.z - gg2.z);
+      vir_sub(w, gg1, u1);
+      vir_sub(w, gg2, u2);
+      vir_sub(w, gg3, u3);
+    }
+    for (int q = 0; q < 3; ++q) fk[q] = warp_sum(fk[q]);
+    cddk = warp_sum(cddk);
+    cdbo2 = warp_sum(cdbo2);
+    cdbopi2 = warp_sum(cdbopi2);
+    if (lane == 0) {
+      force_add(s, k, fk[0], fk[1], fk[2]);
+      fix_add(aq.cddelta + k, cddk, s.err);
+      fix_add(bl.cdbo + ejk, cdbo2, s.err);
+      fix_add(bl.cdbopi + ejk, cdbopi2, s.err);
+    }
+  }
+  etor = warp_sum(etor); econ = warp_sum(econ); cddj = warp_sum(cddj);
+  for (int q = 0; q < 3; ++q) fj[q] = warp_sum(fj[q]);
+  for (int q = 0; q < 6; ++q) w[q] = warp_sum(w[q]);
+  if (lane == 0) {
+    acc.e[T_TORS * s.n + j] = etor;
+    acc.e[T_CONJ * s.n + j] = econ;
+    force_add(s, j, fj[0], fj[1], fj[2]);
+    fix_add(aq.cddelta + j, cddj, s.err);
+    for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
+  }
+}
+
+// ------------------------------------------------------------------ hydrogen bonds
+template <typename R>
+__global__ void k_hbonds(Sys s, BondList bl, HbList hl, Accum acc, const DParams<R>* __restrict__ P,
+                         unsigned mask) {
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (j >= s.n) return;
+  const int tj = s.type[j];
+  if (P->hb[tj] != 1) return;
+  const int nb = bl.cnt[j], nz = hl.cnt[j];
+  const R* bo = (const R*)bl.bo;
+  const R wh = wbit<R>(mask, T_HB);
+  const int r = s.rep[j];
+  double ehb = 0, fj[3] = {0, 0, 0}, w[6] = {0, 0, 0, 0, 0, 0};
+  for (int a = 0; a < nb; ++a) {
+    const int ea = j * bl.cap + a;
+    const int x = bl.j[ea];
+    const int tx = s.type[x];
+    const R BO = bo[ea];
+    if (P->hb[tx] != 2 || !(BO >= P->hb_bo_min)) continue;
+    const int codea = bl.s[ea];
+    const Vec3<R> u = load_vec<R>(bl, ea);
+    const R Lu = dot3(u, u), lu = m_sqrt(Lu);
+    double cdb = 0, fx[3] = {0, 0, 0};
+    for (int zz = lane; zz < nz; zz += 32) {
+      const int ez = j * hl.cap + zz;
+      const int z = hl.j[ez];
+      const int codez = hl.s[ez];
+      if (z == x && codez == codea) continue;
+      const int tz = s.type[z];
+      const int pt = tx * MAXT + tz;
+      Vec3<R> v;
+      PairVec<R>::get(s, j, z, codez, r, v.x, v.y, v.z);
+      const R Lv = dot3(v, v), lv = m_sqrt(Lv), A = dot3(u, v);
+      const R cr = A / (lu * lv);
+      const bool cok = cr > R(-1) && cr < R(1);
+      const R c = rclamp(cr, R(-1), R(1));
+      const R r0 = P->r0hb[pt];
+      const R eb = m_exp(-P->p_hb2[pt] * BO);
+      const R er = m_exp(-P->p_hb3[pt] * (r0 / lv + lv / r0 - R(2)));
+      const R hs = R(0.5) * (R(1) - c);
+      const R s4 = hs * hs;
+      const R ph1 = P->p_hb1[pt];
+      const R omeb = -m_expm1(-P->p_hb2[pt] * BO);
+      const R e = ph1 * omeb * er * s4;
+      ehb += (double)e;
+      cdb += (double)(wh * ph1 * P->p_hb2[pt] * eb * er * s4);
+      const R dEdr = wh * e * (-P->p_hb3[pt]) * (-r0 / Lv + R(1) / r0);
+      const R dEdc = cok ? wh * ph1 * omeb * er * (-hs) : R(0);
+      const R dEdA = dEdc / (lu * lv);
+      const R dEdLu = dEdc * (-c / (R(2) * Lu));
+      const R dEdLv = dEdc * (-c / (R(2) * Lv)) + dEdr / (R(2) * lv);
+      const Vec3<R> gu = lin2(dEdA, v, R(2) * dEdLu, u);
+      const Vec3<R> gv = lin2(dEdA, u, R(2) * dEdLv, v);
+      force_add(s, z, -(double)gv.x, -(double)gv.y, -(double)gv.z);
+      fx[0] -= (double)gu.x; fx[1] -= (double)gu.y; fx[2] -= (double)gu.z;
+      fj[0] += (double)(gu.x + gv.x); fj[1] += (double)(gu.y + gv.y); fj[2] += (double)(gu.z + gv.z);
+      vir_sub(w, gu, u);
+      vir_sub(w, gv, v);
+    }
+    cdb = warp_sum(cdb);
+    for (int q = 0; q < 3; ++q) fx[q] = warp_sum(fx[q]);
+    if (lane == 0) {
+      fix_add(bl.cdbo + ea, cdb, s.err);
+      force_add(s, x, fx[0], fx[1], fx[2]);
+    }
+  }
+  ehb = warp_sum(ehb);
+  for (int q = 0; q < 3; ++q) fj[q] = warp_sum(fj[q]);
+  for (int q = 0; q < 6; ++q) w[q] = warp_sum(w[q]);
+  if (lane == 0) {
+    acc.e[T_HB * s.n + j] = ehb;
+    force_add(s, j, fj[0], fj[1], fj[2]);
+    for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
+  }
+}
+
+}  // namespace
+
+namespace rx {
+
+template <typename R> void bo_correct(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<double>* P) {
+  k_bo_correct<R><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a, P);
+  *L.count += 1;
+}
+template <typename R>
+void atom_terms(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P, unsigned mask) {
+  k_atom_terms<R><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a, acc, P, mask);
+  *L.count += 1;
+}
+template <typename R>
+void over_under_bond(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P, unsigned mask) {
+  k_over_under_bond<R><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a, acc, P, mask);
+  *L.count += 1;
+}
+template <typename R> void s_gather(const Launch& L, Sys s, BondList b, AtomQ a) {
+  k_s_gather<R><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a);
+  *L.count += 1;
+}
+template <typename R>
+void angles(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P, unsigned mask) {
+  k_angles<R><<<grid_for((long long)s.n * 32, 128), 128, 0, L.st>>>(s, b, a, acc, P, mask);
+  *L.count += 1;
+}
+template <typename R>
+void torsions(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P, unsigned mask) {
+  k_torsions<R><<<grid_for((long long)s.n * 32, 128), 128, 0, L.st>>>(s, b, a, acc, P, mask);
+  *L.count += 1;
+}
+template <typename R>
+void hbonds(const Launch& L, Sys s, BondList b, HbList h, Accum acc, const DParams<R>* P, unsigned mask) {
+  k_hbonds<R><<<grid_for((long long)s.n * 32, 128), 128, 0, L.st>>>(s, b, h, acc, P, mask);
+  *L.count += 1;
+}
+
+#define INST(R)                                                                                           \
+  template void bo_correct<R>(const Launch&, Sys, BondList, AtomQ, const DParams<double>*);               \
+  template void atom_terms<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned);   \
+  template void over_under_bond<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned); \
+  template void s_gather<R>(const Launch&, Sys, BondList, AtomQ);                                         \
+  template void angles<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned);       \
+  template void torsions<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned);     \
+  template void hbonds<R>(const Launch&, Sys, BondList, HbList, Accum, const DParams<R>*, unsigned);
+INST(double)
+INST(float)
+}  // namespace rx

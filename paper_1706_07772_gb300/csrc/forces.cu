@@ -1,0 +1,201 @@
+// (f) dE/dBO chain rule into atom forces, force finalisation, energy/virial
+// reductions and velocity Verlet.
+//
+// Paper: Table 2 "Aggregate Forces" (bond-order derivatives turned into atom forces),
+// Sec. 3.1 (energies reduced system-wide, forces summed per atom; data privatisation
+// replaced here by owner-computes), Sec. 4.1 (velocity-Verlet MD, dt = 0.1 fs).
+//
+// Chain rule (per bond, totals over both directed entries; BO, BO_pi, BO_pp are
+// functions of BO' = BO'sig + BO'pi + BO'pp, BO'pi, BO'pp, Delta'_i and Delta'_j):
+//   C   = dE/dBO (both entries) + dE/dsumBO_i + dE/dsumBO_j,  C_pi, C_pp likewise
+//   dE/dBO'      = C (F + BO' dF/dBO') + (C_pi BO'pi + C_pp BO'pp) dG/dBO'
+//   dE/dBO'pi    = C_pi G,   dE/dBO'pp = C_pp G        (F = f1 f4 f5, G = f1^2 f4 f5)
+//   A_i          = sum over i's bonds of dE/dDelta'_i
+//   dE/dr_ij     = (dE/dBO' + A_i + A_j) dBO'/dr + dE/dBO'pi dBO'pi/dr + dE/dBO'pp dBO'pp/dr
+// Pass 1 (atom i over its row) forms the per-entry coefficients and A_i; pass 2 (atom i
+// over its row) gathers F_i = sum_j dE/dr_ij (x_j - x_i)/r -- owner computes, no atomics.
+#include "reax_internal.cuh"
+
+namespace {
+
+inline unsigned grid_for(long long threads, int block) { return (unsigned)((threads + block - 1) / block); }
+
+template <typename R>
+__global__ void k_chain1(Sys s, BondList bl, AtomQ aq) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const int nb = bl.cnt[i];
+  const double* BOp = bl.bop;
+  const double* BOpi = bl.bopi;
+  const double* BOpp = bl.bopp;
+  const double* F1 = (const double*)bl.f1; const double* FO = (const double*)bl.fo;
+  const double* FT = (const double*)bl.ft; const double* DF1 = (const double*)bl.df1;
+  const double* DFOB = (const double*)bl.dfo_bo; const double* DFTB = (const double*)bl.dft_bo;
+  const double* DFOD = (const double*)bl.dfo_d;
+  const long long cdi = (long long)aq.cddelta[i];
+  double A = 0.0;
+  for (int k = 0; k < nb; ++k) {
+    const int e = i * bl.cap + k;
+    const int m = bl.mirror[e];
+    const int j = bl.j[e];
+    const bool own_lo = (i < j) || (i == j && bl.s[e] > 13);
+    // exact integer sums: identical in both directions
+    const double C = (double)((long long)bl.cdbo[e] + (long long)bl.cdbo[m] + cdi + (long long)aq.cddelta[j]) * FIX_INV;
+    const double Cpi = (double)((long long)bl.cdbopi[e] + (long long)bl.cdbopi[m]) * FIX_INV;
+    const double Cpp = (double)((long long)bl.cdbopp[e] + (long long)bl.cdbopp[m]) * FIX_INV;
+    const double bp = BOp[e], bpi = BOpi[e], bpp = BOpp[e];
+    const double f1 = (double)F1[e], fo = (double)FO[e], ft = (double)FT[e];
+    const double dfo_bo = (double)DFOB[e], dft_bo = (double)DFTB[e];
+    const double flo = own_lo ? fo : ft, fhi = own_lo ? ft : fo;
+    const double dflo = own_lo ? dfo_bo : dft_bo, dfhi = own_lo ? dft_bo : dfo_bo;
+    const double F = f1 * flo * fhi;
+    const double G = f1 * f1 * flo * fhi;
+    const double d45 = dflo * fhi + flo * dfhi;
+    const double dFdB = f1 * d45, dGdB = f1 * f1 * d45;
+    const double piw = Cpi * bpi + Cpp * bpp;
+    bl.dEdBOp[e] = C * (F + bp * dFdB) + piw * dGdB;
+    bl.dEdBOpi[e] = Cpi * G;
+    bl.dEdBOpp[e] = Cpp * G;
+    const double df1 = (double)DF1[e], dfo_d = (double)DFOD[e];
+    const double dFdD = df1 * fo * ft + f1 * dfo_d * ft;
+    const double dGdD = 2.0 * f1 * df1 * fo * ft + f1 * f1 * dfo_d * ft;
+    A += C * bp * dFdD + piw * dGdD;
+  }
+  aq.A[i] = A;
+}
+
+template <typename R>
+__global__ void k_chain2(Sys s, BondList bl, AtomQ aq, Accum acc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const int nb = bl.cnt[i];
+  const R* DX = (const R*)bl.dx; const R* DY = (const R*)bl.dy; const R* DZ = (const R*)bl.dz;
+  const R* RR = (const R*)bl.r;
+  const double* DB = bl.dbop; const double* DBPI = bl.dbopi; const double* DBPP = bl.dbopp;
+  const double Ai = aq.A[i];
+  double fx = 0, fy = 0, fz = 0, w[6] = {0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < nb; ++k) {
+    const int e = i * bl.cap + k;
+    const int j = bl.j[e];
+    const bool own_lo = (i < j) || (i == j && bl.s[e] > 13);
+    const double Aj = aq.A[j];
+    const double Asum = own_lo ? Ai + Aj : Aj + Ai;
+    const double c = (bl.dEdBOp[e] + Asum) * DB[e] + bl.dEdBOpi[e] * DBPI[e] + bl.dEdBOpp[e] * DBPP[e];
+    const double dx = (double)DX[e], dy = (double)DY[e], dz = (double)DZ[e];
+    const double cr = c / (double)RR[e];
+    fx += cr * dx; fy += cr * dy; fz += cr * dz;
+    const double hc = -0.5 * cr;
+    w[0] += hc * dx * dx; w[1] += hc * dy * dy; w[2] += hc * dz * dz;
+    w[3] += hc * dx * dy; w[4] += hc * dx * dz; w[5] += hc * dy * dz;
+  }
+  fix_add(s.fx + i, fx, s.err);
+  fix_add(s.fy + i, fy, s.err);
+  fix_add(s.fz + i, fz, s.err);
+  for (int q = 0; q < 6; ++q) acc.vir[q * s.n + i] += w[q];
+}
+
+__global__ void k_finalize(Sys s, double* F) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  F[3 * i + 0] = fix_get(s.fx + i);
+  F[3 * i + 1] = fix_get(s.fy + i);
+  F[3 * i + 2] = fix_get(s.fz + i);
+}
+
+// block (r, q): sum over replica r's atoms of e[q] (q < NTERMS) or vir[q - NTERMS]
+__global__ void k_reduce(Sys s, Accum acc, double* E_rep, double* vir_rep) {
+  const int r = blockIdx.x, q = blockIdx.y;
+  const double* src = q < NTERMS ? acc.e + (size_t)q * s.n : acc.vir + (size_t)(q - NTERMS) * s.n;
+  const int64_t lo = s.rep_off[r], hi = s.rep_off[r + 1];
+  double v = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v += src[i];
+  __shared__ double sh[32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    if (!isfinite(t)) atomicOr(s.err, ERR_NAN);
+    if (q < NTERMS) E_rep[r * NTERMS + q] = t;
+    else vir_rep[r * 6 + (q - NTERMS)] = t;
+  }
+}
+
+__global__ void k_kick_drift(Sys s, const double* mass_t, double dt, int drift) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const double c = 0.5 * dt * 4.184e-4 / mass_t[s.type[i]];
+  double vx = s.vx[i] + c * fix_get(s.fx + i);
+  double vy = s.vy[i] + c * fix_get(s.fy + i);
+  double vz = s.vz[i] + c * fix_get(s.fz + i);
+  s.vx[i] = vx; s.vy[i] = vy; s.vz[i] = vz;
+  if (drift) {
+    const double* L = s.box + 3 * s.rep[i];
+    double p[3] = {s.x[i] + dt * vx, s.y[i] + dt * vy, s.z[i] + dt * vz};
+    for (int d = 0; d < 3; ++d) {
+      if (p[d] < 0.0) p[d] += L[d];
+      if (p[d] >= L[d]) p[d] -= L[d];
+    }
+    if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) atomicOr(s.err, ERR_NAN);
+    s.x[i] = p[0]; s.y[i] = p[1]; s.z[i] = p[2];
+  }
+}
+
+__global__ void k_kinetic(Sys s, const double* mass_t, double* ke_rep) {
+  const int r = blockIdx.x;
+  const int64_t lo = s.rep_off[r], hi = s.rep_off[r + 1];
+  double v = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    v += mass_t[s.type[i]] * (s.vx[i] * s.vx[i] + s.vy[i] * s.vy[i] + s.vz[i] * s.vz[i]);
+  __shared__ double sh[32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    ke_rep[r] = 0.5 * t / 4.184e-4;
+  }
+}
+
+__global__ void k_etot(int nrep, const double* E_rep, const double* ke, double* out) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrep) return;
+  double t = 0.0;
+  for (int q = 0; q < NTERMS; ++q) t += E_rep[r * NTERMS + q];
+  out[r] = t + ke[r];
+}
+
+}  // namespace
+
+namespace rx {
+void etot_combine(const Launch& L, int nrep, const double* E_rep, const double* ke, double* out) {
+  k_etot<<<(nrep + 127) / 128, 128, 0, L.st>>>(nrep, E_rep, ke, out);
+  *L.count += 1;
+}
+template <typename R> void chain_rule(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc) {
+  k_chain1<R><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a);
+  k_chain2<R><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a, acc);
+  *L.count += 2;
+}
+template void chain_rule<double>(const Launch&, Sys, BondList, AtomQ, Accum);
+template void chain_rule<float>(const Launch&, Sys, BondList, AtomQ, Accum);
+
+void finalize_forces(const Launch& L, Sys s, double* F) {
+  k_finalize<<<grid_for(s.n, 256), 256, 0, L.st>>>(s, F);
+  *L.count += 1;
+}
+void reduce_energies(const Launch& L, Sys s, Accum acc, double* E_rep, double* vir_rep) {
+  k_reduce<<<dim3(s.nrep, NTERMS + 6), 256, 0, L.st>>>(s, acc, E_rep, vir_rep);
+  *L.count += 1;
+}
+void verlet_kick_drift(const Launch& L, Sys s, const double* mass_t, double dt, int drift) {
+  k_kick_drift<<<grid_for(s.n, 256), 256, 0, L.st>>>(s, mass_t, dt, drift);
+  *L.count += 1;
+}
+void kinetic(const Launch& L, Sys s, const double* mass_t, double* ke_rep) {
+  k_kinetic<<<s.nrep, 256, 0, L.st>>>(s, mass_t, ke_rep);
+  *L.count += 1;
+}
+}  // namespace rx

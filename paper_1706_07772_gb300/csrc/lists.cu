@@ -1,0 +1,404 @@
+// (a) Cell binning, far-neighbour list (+ QEq H entries), bond list (+ BO'), H-bond list.
+//
+// Paper: Sec. 3.3 "Neighbor and Interaction Lists" (own far list with distances, compact
+// adjacency rows, bond and H-bond lists generated from one pass over the neighbour
+// list) and Sec. 3.2 (spatial order of atoms). GPU form: the cell grid is binned with a
+// count -> scan -> scatter and a per-cell rank sort (deterministic order, no slot locks);
+// one warp builds one atom's row: 27 stencil cells with image shifts, 32 candidates per
+// ballot, warp-compacted writes. Membership is decided exactly as the FP64 definition
+// (d = (xj - xi) + s*L, r^2 = (dx*dx + dy*dy) + dz*dz, r^2 < R^2) using an FP32 filter
+// with a proven error margin and FP64 only inside the margin.
+#include "reax_internal.cuh"
+
+namespace {
+
+__global__ void k_cell_assign(Sys s, Cells c) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  int r = s.rep[i];
+  const double* L = s.box + 3 * r;
+  const int* nc = c.nc + 3 * r;
+  double p[3] = {s.x[i], s.y[i], s.z[i]};
+  int cc[3];
+  for (int d = 0; d < 3; ++d) {
+    int k = (int)floor(p[d] / L[d] * (double)nc[d]);
+    cc[d] = k < 0 ? 0 : (k >= nc[d] ? nc[d] - 1 : k);
+  }
+  int cell = c.cell_off[r] + (cc[2] * nc[1] + cc[1]) * nc[0] + cc[0];
+  c.atom_cell[i] = cell;
+  atomicAdd(&c.count[cell], 1);
+  // float hi/lo copies of the positions
+  float h;
+  h = (float)s.x[i]; s.xh[i] = h; s.xl[i] = (float)(s.x[i] - (double)h);
+  h = (float)s.y[i]; s.yh[i] = h; s.yl[i] = (float)(s.y[i] - (double)h);
+  h = (float)s.z[i]; s.zh[i] = h; s.zl[i] = (float)(s.z[i] - (double)h);
+}
+
+// single-block exclusive scan over cell counts
+__global__ void k_cell_scan(Cells c) {
+  __shared__ int carry;
+  __shared__ int warp_tot[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < c.ncell_total; base += blockDim.x) {
+    int k = base + threadIdx.x;
+    int v = k < c.ncell_total ? c.count[k] : 0;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      int nw = blockDim.x >> 5;
+      int t = lane < nw ? warp_tot[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += u;
+      }
+      if (lane < nw) warp_tot[lane] = t;   // inclusive warp totals
+    }
+    __syncthreads();
+    int excl = carry + (w > 0 ? warp_tot[w - 1] : 0) + incl - v;
+    if (k < c.ncell_total) {
+      c.start[k] = excl;
+      c.cursor[k] = excl;
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) c.start[c.ncell_total] = carry;
+}
+
+__global__ void k_cell_scatter(Sys s, Cells c, int* tmp) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  int slot = atomicAdd(&c.cursor[c.atom_cell[i]], 1);
+  tmp[slot] = i;
+}
+
+// per cell: order atoms by index (rank = number of smaller indices in the cell)
+__global__ void k_cell_sort(Cells c, const int* tmp) {
+  int cell = blockIdx.x;
+  int a = c.start[cell], b = c.start[cell + 1];
+  for (int k = a + threadIdx.x; k < b; k += blockDim.x) {
+    int me = tmp[k];
+    int rank = 0;
+    for (int m = a; m < b; ++m) rank += tmp[m] < me;
+    c.atoms[a + rank] = me;
+  }
+}
+
+// decide r^2 < R2 exactly (FP64 definition) from an FP32 estimate with error bound `margin`
+__device__ __forceinline__ bool in_range(const Sys& s, int i, int j, int code, int r, float r2f, float R2f,
+                                         float margin, double R2) {
+  if (r2f < R2f - margin) return true;
+  if (r2f > R2f + margin) return false;
+  return r2_exact(s, i, j, code, r) < R2;
+}
+
+template <typename R>
+__global__ void k_far_list(Sys s, Cells c, FarList f, const DParams<R>* __restrict__ P, float margin) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= s.n) return;
+  const int i = warp;
+  const int r = s.rep[i];
+  const int* nc = c.nc + 3 * r;
+  const float* Lh = s.boxh + 3 * r;
+  const double Rc = (double)P->r_nb;
+  const double R2 = Rc * Rc;
+  const float R2f = (float)R2;
+  int cell = c.atom_cell[i] - c.cell_off[r];
+  int ci[3] = {cell % nc[0], (cell / nc[0]) % nc[1], cell / (nc[0] * nc[1])};
+  float xi = s.xh[i], yi = s.yh[i], zi = s.zh[i];
+  const int ti = s.type[i];
+  int count = 0;
+  const int base_row = i * f.cap;
+  R* H = (R*)f.H;
+  for (int o = 0; o < 27; ++o) {
+    int oc[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+    int t[3], sh[3];
+    for (int d = 0; d < 3; ++d) {
+      int v = ci[d] + oc[d];
+      sh[d] = v < 0 ? -1 : (v >= nc[d] ? 1 : 0);
+      t[d] = v - sh[d] * nc[d];
+    }
+    int code = (sh[0] + 1) * 9 + (sh[1] + 1) * 3 + (sh[2] + 1);
+    int cid = c.cell_off[r] + (t[2] * nc[1] + t[1]) * nc[0] + t[0];
+    int a = c.start[cid], b = c.start[cid + 1];
+    float ox = sh[0] * Lh[0], oy = sh[1] * Lh[1], oz = sh[2] * Lh[2];
+    for (int base = a; base < b; base += 32) {
+      int k = base + lane;
+      bool ok = false;
+      int j = -1;
+      if (k < b) {
+        j = c.atoms[k];
+        float dx = (s.xh[j] - xi) + ox, dy = (s.yh[j] - yi) + oy, dz = (s.zh[j] - zi) + oz;
+        float r2f = dx * dx + dy * dy + dz * dz;
+        ok = !(j == i && code == 13) && in_range(s, i, j, code, r, r2f, R2f, margin, R2);
+      }
+      unsigned m = __ballot_sync(0xffffffffu, ok);
+      int pos = count + __popc(m & ((1u << lane) - 1u));
+      if (ok && pos < f.cap) {
+        f.j[base_row + pos] = j;
+        f.s[base_row + pos] = (uint8_t)code;
+        R dx, dy, dz;
+        PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
+        R rr = m_sqrt(dx * dx + dy * dy + dz * dz);
+        R tap, dtap;
+        taper<R>(rr, P->r_nb, tap, dtap);
+        R g3 = P->gamma_m3[ti * MAXT + s.type[j]];
+        H[base_row + pos] = tap * P->k_e / m_cbrt(rr * rr * rr + g3);
+      }
+      count += __popc(m);
+    }
+  }
+  if (lane == 0) {
+    f.cnt[i] = count < f.cap ? count : f.cap;
+    if (count > f.cap) atomicOr(s.err, ERR_CAP_FAR);
+  }
+}
+
+// BO' components and their r-derivatives: sigma carries the (1 + bo_cut) factor.
+// (r/r0)^p = exp(p log1p((r - r0)/r0)); in FP32 r and r0 are float-float so the
+// difference r - r0 keeps full relative precision (steep exponents p ~ 10-40 amplify
+// any relative error of r/r0 by p).
+template <typename R>
+__device__ __forceinline__ R pow_ratio(R rh, R rl, R r0h, R r0l, R p) {
+  const R u = ((rh - r0h) + (rl - r0l)) / r0h;
+  return m_exp(p * m_log1p(u));
+}
+template <typename R>
+__device__ __forceinline__ void bo_prime(const DParams<R>* P, int pt, R r, R rl, R& bs, R& bp, R& bpp, R& dbs,
+                                         R& dbp, R& dbpp) {
+  bs = bp = bpp = dbs = dbp = dbpp = R(0);
+  R r0 = P->r0s[pt];
+  if (r0 > R(0)) {
+    R tt = pow_ratio<R>(r, rl, r0, P->r0s_lo[pt], P->p_bo2[pt]);
+    bs = (R(1) + P->bo_cut) * m_exp(P->p_bo1[pt] * tt);
+    dbs = bs * P->p_bo1[pt] * P->p_bo2[pt] * tt / r;
+  }
+  r0 = P->r0p[pt];
+  if (r0 > R(0)) {
+    R tt = pow_ratio<R>(r, rl, r0, P->r0p_lo[pt], P->p_bo4[pt]);
+    bp = m_exp(P->p_bo3[pt] * tt);
+    dbp = bp * P->p_bo3[pt] * P->p_bo4[pt] * tt / r;
+  }
+  r0 = P->r0pp[pt];
+  if (r0 > R(0)) {
+    R tt = pow_ratio<R>(r, rl, r0, P->r0pp_lo[pt], P->p_bo6[pt]);
+    bpp = m_exp(P->p_bo5[pt] * tt);
+    dbpp = bpp * P->p_bo5[pt] * P->p_bo6[pt] * tt / r;
+  }
+}
+
+// exact FP64 bond membership (used directly in FP64 mode, in the ambiguous band in FP32)
+__device__ __forceinline__ bool bond_member_exact(const Sys& s, const DParams<double>* Pd, int i, int j,
+                                                  int code, int r, int pt) {
+  double r2 = r2_exact(s, i, j, code, r);
+  if (!(r2 < Pd->r_bond * Pd->r_bond)) return false;
+  double rr = sqrt(r2);
+  double bs, bp, bpp, a, b, c;
+  bo_prime<double>(Pd, pt, rr, 0.0, bs, bp, bpp, a, b, c);
+  return bs + bp + bpp >= Pd->bo_cut;
+}
+
+template <typename R>
+__global__ void k_bond_list(Sys s, FarList f, BondList bl, HbList hl, AtomQ aq,
+                            const DParams<R>* __restrict__ P, const DParams<double>* __restrict__ Pd) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= s.n) return;
+  const int i = warp;
+  const int r = s.rep[i];
+  const int ti = s.type[i];
+  const bool is_h = P->hb[ti] == 1;
+  const int nf = f.cnt[i];
+  const int frow = i * f.cap, brow = i * bl.cap, hrow = i * hl.cap;
+  R* bdx = (R*)bl.dx; R* bdy = (R*)bl.dy; R* bdz = (R*)bl.dz; R* br = (R*)bl.r;
+  const double rb2 = Pd->r_bond * Pd->r_bond, rh2 = Pd->r_hb * Pd->r_hb;
+  int nb = 0, nh = 0;
+  for (int base = 0; base < nf; base += 32) {
+    int k = base + lane;
+    bool isb = false, ish = false;
+    int j = 0, code = 0;
+    R dx = 0, dy = 0, dz = 0, rr = 0, bs = 0, bp = 0, bpp = 0, dbs = 0, dbp = 0, dbpp = 0;
+    if (k < nf) {
+      j = f.j[frow + k];
+      code = f.s[frow + k];
+      R rlo = 0;
+      if (sizeof(R) == 8) {
+        PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
+      } else {
+        int sx, sy, sz;
+        shift_decode(code, sx, sy, sz);
+        const float* Lh = s.boxh + 3 * r;
+        const float* Ll = s.boxl + 3 * r;
+        float dh[3], dl[3], rh, rl;
+        pv_comp_ff(s.xh[j], s.xh[i], s.xl[j], s.xl[i], sx, Lh[0], Ll[0], dh[0], dl[0]);
+        pv_comp_ff(s.yh[j], s.yh[i], s.yl[j], s.yl[i], sy, Lh[1], Ll[1], dh[1], dl[1]);
+        pv_comp_ff(s.zh[j], s.zh[i], s.zl[j], s.zl[i], sz, Lh[2], Ll[2], dh[2], dl[2]);
+        norm_ff(dh, dl, rh, rl);
+        dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
+        rr = (R)rh;
+        rlo = (R)rl;
+      }
+      R r2 = dx * dx + dy * dy + dz * dz;
+      const int pt = ti * MAXT + s.type[j];
+      if (sizeof(R) == 8) {
+        // FP64 path: the computed r^2 is the defining value up to contraction; use the
+        // exact form for the decision
+        double r2e = r2_exact(s, i, j, code, r);
+        if (r2e < rb2) {
+          rr = m_sqrt(r2);
+          bo_prime<R>(P, pt, rr, R(0), bs, bp, bpp, dbs, dbp, dbpp);
+          isb = (double)(bs + bp + bpp) >= Pd->bo_cut;
+        }
+        if (is_h && P->hb[s.type[j]] == 2) ish = r2e < rh2;
+      } else {
+        // FP32 path: |r2 - r2_exact| <= ~1e-6 relative (hi/lo positions); 1e-4 margins
+        float r2f = (float)r2;
+        if (r2f < (float)rb2 * 1.0001f) {
+          bo_prime<R>(P, pt, rr, rlo, bs, bp, bpp, dbs, dbp, dbpp);
+          R tot = bs + bp + bpp;
+          bool clear = r2f < (float)rb2 * 0.9999f && fabsf((float)(tot - P->bo_cut)) > 1e-3f * (float)P->bo_cut;
+          isb = clear ? tot >= P->bo_cut : bond_member_exact(s, Pd, i, j, code, r, pt);
+        }
+        if (is_h && P->hb[s.type[j]] == 2) {
+          float m = (float)rh2 * 1e-4f;
+          ish = r2f < (float)rh2 - m ? true : (r2f > (float)rh2 + m ? false : r2_exact(s, i, j, code, r) < rh2);
+        }
+      }
+    }
+    unsigned mb = __ballot_sync(0xffffffffu, isb);
+    int pos = nb + __popc(mb & ((1u << lane) - 1u));
+    if (isb && pos < bl.cap) {
+      int e = brow + pos;
+      bl.j[e] = j;
+      bl.s[e] = (uint8_t)code;
+      bdx[e] = dx; bdy[e] = dy; bdz[e] = dz; br[e] = rr;
+      if ((i < j) || (i == j && code > 13)) bl.canon[atomicAdd(bl.ncanon, 1)] = e;
+    }
+    nb += __popc(mb);
+    unsigned mh = __ballot_sync(0xffffffffu, ish);
+    int hp = nh + __popc(mh & ((1u << lane) - 1u));
+    if (ish && hp < hl.cap) {
+      hl.j[hrow + hp] = j;
+      hl.s[hrow + hp] = (uint8_t)code;
+    }
+    nh += __popc(mh);
+  }
+  if (lane == 0) {
+    bl.cnt[i] = nb < bl.cap ? nb : bl.cap;
+    hl.cnt[i] = nh < hl.cap ? nh : hl.cap;
+    if (nb > bl.cap) atomicOr(s.err, ERR_CAP_BOND);
+    if (nh > hl.cap) atomicOr(s.err, ERR_CAP_HB);
+  }
+}
+
+__global__ void k_bond_mirror(Sys s, BondList bl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  int nb = bl.cnt[i];
+  for (int k = 0; k < nb; ++k) {
+    int e = i * bl.cap + k;
+    int j = bl.j[e];
+    int want = 26 - (int)bl.s[e];
+    int found = -1;
+    int nj = bl.cnt[j];
+    for (int m = 0; m < nj; ++m) {
+      int e2 = j * bl.cap + m;
+      if (bl.j[e2] == i && (int)bl.s[e2] == want) {
+        found = e2;
+        break;
+      }
+    }
+    if (found < 0) {
+      atomicOr(s.err, ERR_CAP_BOND);
+      found = e;
+    }
+    bl.mirror[e] = found;
+  }
+}
+
+// FP64 BO' of each unordered bond (thread per bond), written to both directed entries
+__global__ void k_bo_prime64(Sys s, BondList bl, const DParams<double>* __restrict__ P) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= *bl.ncanon) return;
+  const int e = bl.canon[t];
+  const int i = e / bl.cap;
+  const int j = bl.j[e];
+  const int code = bl.s[e];
+  double dx, dy, dz;
+  PairVec<double>::get(s, i, j, code, s.rep[i], dx, dy, dz);
+  const double r = sqrt(dx * dx + dy * dy + dz * dz);
+  double bs, bp, bpp, dbs, dbp, dbpp;
+  bo_prime<double>(P, s.type[i] * MAXT + s.type[j], r, 0.0, bs, bp, bpp, dbs, dbp, dbpp);
+  const int m = bl.mirror[e];
+  const double tot = bs + bp + bpp - P->bo_cut;
+  bl.bop[e] = tot; bl.bopi[e] = bp; bl.bopp[e] = bpp;
+  bl.dbop[e] = dbs + dbp + dbpp; bl.dbopi[e] = dbp; bl.dbopp[e] = dbpp;
+  bl.bop[m] = tot; bl.bopi[m] = bp; bl.bopp[m] = bpp;
+  bl.dbop[m] = dbs + dbp + dbpp; bl.dbopi[m] = dbp; bl.dbopp[m] = dbpp;
+}
+
+// Delta'_i = sum BO'_ij - Val_i and Delta'boc_i (FP64, in row order)
+__global__ void k_delta_prime(Sys s, BondList bl, AtomQ aq, const DParams<double>* __restrict__ P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  double sum = 0.0;
+  for (int k = 0; k < bl.cnt[i]; ++k) sum += bl.bop[i * bl.cap + k];
+  aq.dp[i] = sum - P->val[s.type[i]];
+  aq.dpboc[i] = sum - P->valboc[s.type[i]];
+}
+
+inline unsigned grid_for(long long threads, int block) { return (unsigned)((threads + block - 1) / block); }
+
+}  // namespace
+
+namespace rx {
+
+void cells_build(const Launch& L, Sys s, Cells c) {
+  cudaMemsetAsync(c.count, 0, sizeof(int) * c.ncell_total, L.st);
+  k_cell_assign<<<grid_for(s.n, 256), 256, 0, L.st>>>(s, c);
+  k_cell_scan<<<1, 1024, 0, L.st>>>(c);
+  k_cell_scatter<<<grid_for(s.n, 256), 256, 0, L.st>>>(s, c, c.tmp);
+  k_cell_sort<<<c.ncell_total, 128, 0, L.st>>>(c, c.tmp);
+  *L.count += 4;
+}
+
+template <typename R>
+void far_list(const Launch& L, Sys s, Cells c, FarList f, const DParams<R>* P, float margin) {
+  k_far_list<R><<<grid_for((long long)s.n * 32, 256), 256, 0, L.st>>>(s, c, f, P, margin);
+  *L.count += 1;
+}
+
+template <typename R>
+void bond_list(const Launch& L, Sys s, FarList f, BondList b, HbList h, AtomQ a, const DParams<R>* P,
+               const DParams<double>* Pd) {
+  k_bond_list<R><<<grid_for((long long)s.n * 32, 256), 256, 0, L.st>>>(s, f, b, h, a, P, Pd);
+  *L.count += 1;
+}
+
+void bond_mirror(const Launch& L, Sys s, BondList b) {
+  k_bond_mirror<<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b);
+  *L.count += 1;
+}
+
+void bo_prime64(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<double>* Pd, int n_canon_max) {
+  k_bo_prime64<<<grid_for(n_canon_max, 128), 128, 0, L.st>>>(s, b, Pd);
+  k_delta_prime<<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a, Pd);
+  *L.count += 2;
+}
+
+template void far_list<double>(const Launch&, Sys, Cells, FarList, const DParams<double>*, float);
+template void far_list<float>(const Launch&, Sys, Cells, FarList, const DParams<float>*, float);
+template void bond_list<double>(const Launch&, Sys, FarList, BondList, HbList, AtomQ, const DParams<double>*,
+                                const DParams<double>*);
+template void bond_list<float>(const Launch&, Sys, FarList, BondList, HbList, AtomQ, const DParams<float>*,
+                               const DParams<double>*);
+}  // namespace rx

@@ -1,0 +1,391 @@
+// Internal declarations of the ReaxFF GB300 library: device data layout, device
+// helpers (fixed-point accumulation, warp reductions, bounded grid barrier) and the
+// kernel launch entry points shared between translation units.
+//
+// Layout in HBM (all per-atom data structure-of-arrays, atoms in input order):
+//   positions/velocities   double x[n], y[n], z[n], vx.., with float copies xf.. for
+//                          list filtering
+//   far list (ELL)         row i at [i*cap_far, i*cap_far + far_cnt[i]): int32 j,
+//                          uint8 image-shift code, H value (QEq matrix entry, type R)
+//   bond list (ELL)        row i at [i*cap_bond, ...): j, shift, mirror entry index,
+//                          geometry, BO' parts and their r-derivatives, corrected BO
+//                          parts and the correction derivatives (type R), dE/dBO
+//                          accumulators (int64 fixed point)
+//   H-bond list (ELL)      row i (H atoms only) at [i*cap_hb, ...): j, shift
+// Forces, dE/dBO and dE/dDelta are accumulated as int64 fixed point (2^-32 quanta):
+// integer addition is associative, so every result is bitwise reproducible.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "reaxff.h"
+
+#define MAXT REAXFF_MAXT
+#define NTERMS REAXFF_NTERMS
+
+enum { T_BOND = 0, T_LP, T_OVER, T_UNDER, T_VAL, T_PEN, T_COA, T_TORS, T_CONJ, T_HB, T_VDW,
+       T_COUL, T_POL };
+
+// error flag bits (device-side, read by the host after a stage)
+enum { ERR_CAP_FAR = 1, ERR_CAP_BOND = 2, ERR_CAP_HB = 4, ERR_TIMEOUT = 8, ERR_NAN = 16,
+       ERR_CG = 32 };
+
+constexpr double FIX_SCALE = 4294967296.0;         // 2^32
+constexpr double FIX_INV = 1.0 / 4294967296.0;
+constexpr double FIX_LIMIT = 1.0e9;                // |value| beyond this -> ERR_NAN
+
+// ------------------------------------------------------------------ parameters
+template <typename R>
+struct DParams {
+  int nt;
+  int hb[MAXT];
+  R mass[MAXT], val[MAXT], vale[MAXT], valboc[MAXT], valang[MAXT], p_lp2[MAXT], p_ovun2[MAXT],
+      p_ovun5[MAXT], p_val3[MAXT], p_val5[MAXT], chi[MAXT], eta[MAXT];
+  R r0s[MAXT * MAXT], r0p[MAXT * MAXT], r0pp[MAXT * MAXT], p_bo1[MAXT * MAXT], p_bo2[MAXT * MAXT],
+      p_bo3[MAXT * MAXT], p_bo4[MAXT * MAXT], p_bo5[MAXT * MAXT], p_bo6[MAXT * MAXT],
+      p_boc3[MAXT * MAXT], p_boc4[MAXT * MAXT], p_boc5[MAXT * MAXT], ovc[MAXT * MAXT],
+      v13[MAXT * MAXT], De_s[MAXT * MAXT], De_p[MAXT * MAXT], De_pp[MAXT * MAXT],
+      p_be1[MAXT * MAXT], p_be2[MAXT * MAXT], p_ovun1[MAXT * MAXT], vdw_D[MAXT * MAXT],
+      vdw_rv[MAXT * MAXT], vdw_alpha[MAXT * MAXT], vdw_gw_pow[MAXT * MAXT],  // gw^-p_vdW1
+      gamma_m3[MAXT * MAXT];                                                 // gamma^-3
+  R th00[MAXT * MAXT * MAXT], p_val1[MAXT * MAXT * MAXT], p_val2[MAXT * MAXT * MAXT],
+      p_val4[MAXT * MAXT * MAXT], p_val7[MAXT * MAXT * MAXT], p_pen1[MAXT * MAXT * MAXT],
+      p_coa1[MAXT * MAXT * MAXT];
+  R r0s_lo[MAXT * MAXT], r0p_lo[MAXT * MAXT], r0pp_lo[MAXT * MAXT];   // r0 - R(r0) (float-float)
+  R V1[MAXT * MAXT], V2[MAXT * MAXT], V3[MAXT * MAXT], p_tor1[MAXT * MAXT], p_cot1[MAXT * MAXT];
+  R r0hb[MAXT * MAXT], p_hb1[MAXT * MAXT], p_hb2[MAXT * MAXT], p_hb3[MAXT * MAXT];
+  R p_boc1, p_boc2, p_lp1, p_ovun3, p_ovun4, p_ovun6, p_ovun7, p_ovun8, p_val6, p_val8, p_val9,
+      p_val10, p_pen2, p_pen3, p_pen4, p_coa2, p_coa3, p_coa4, p_tor2, p_tor3, p_tor4, p_cot2,
+      p_vdW1, k_e;
+  // options needed inside kernels
+  R r_nb, r_bond, r_hb, bo_cut, thb_cut, thb_cutsq, hb_bo_min;
+};
+
+// ------------------------------------------------------------------ device views
+struct Sys {                   // per-atom and per-replica state
+  int n, nrep;
+  const int* type;
+  const int* rep;              // replica of each atom
+  const double* box;           // [nrep*3]
+  const int64_t* rep_off;      // [nrep+1]
+  const float* boxh;           // [nrep*3] float(L)
+  const float* boxl;           // [nrep*3] float(L - float(L))
+  double *x, *y, *z;
+  float *xh, *yh, *zh;         // float(x)
+  float *xl, *yl, *zl;         // float(x - float(x))
+  double *vx, *vy, *vz;
+  unsigned long long *fx, *fy, *fz;   // fixed-point force accumulators
+  double* q;
+  int* err;
+};
+
+struct Cells {
+  const int* nc;               // [nrep*3]
+  const int* cell_off;         // [nrep+1] first cell of each replica
+  int ncell_total;
+  int* count;                  // [ncell_total]
+  int* start;                  // [ncell_total+1]
+  int* cursor;                 // [ncell_total]
+  int* atoms;                  // [n] atoms sorted by cell
+  int* atom_cell;              // [n]
+  int* tmp;                    // [n] scatter scratch
+};
+
+struct FarList {
+  int cap;
+  int* cnt;                    // [n]
+  int* j;                      // [n*cap]
+  uint8_t* s;                  // [n*cap]
+  void* H;                     // [n*cap] of R: QEq matrix off-diagonal entries
+};
+
+struct BondList {
+  int cap;
+  int* cnt;
+  int* j;
+  uint8_t* s;
+  int* mirror;                 // global entry index of the reverse entry
+  int* canon;                  // compact list of canonical entries (one per unordered bond)
+  int* ncanon;                 // its length (device counter)
+  // geometry (arrays of R, [n*cap])
+  void *dx, *dy, *dz, *r;
+  // BO' (shifted total), pi, pipi and their r-derivatives: FP64 in both modes, because the
+  // correction f1 depends on Delta' = sum BO' - Val through e^{-p_boc1 Delta'} (p_boc1 ~ 50)
+  double *bop, *bopi, *bopp, *dbop, *dbopi, *dbopp;
+  void *bo, *bo_pi, *bo_pp;                            // corrected
+  void *f1, *fo, *ft, *df1, *dfo_bo, *dft_bo, *dfo_d;  // correction factors and partials
+  double *dEdBOp, *dEdBOpi, *dEdBOpp;                  // chain-rule coefficients
+  unsigned long long *cdbo, *cdbopi, *cdbopp;          // dE/dBO accumulators (fixed point)
+};
+
+struct HbList {
+  int cap;
+  int* cnt;
+  int* j;
+  uint8_t* s;
+};
+
+struct AtomQ {                 // per-atom bond-order quantities (double)
+  double *dp, *dpboc;          // Delta', Delta'boc
+  double *sumbo, *delta, *dang, *nlp, *dnlp, *dlp, *dd;   // dd = Delta - Delta_lp
+  double *prodexp, *sbo2, *dsbo2, *sbo_fac;               // sbo_fac = -Delta_ang - p_val8 nlp
+  double *cds, *A;             // dE/dS, chain-rule dE/dDelta'
+  unsigned long long* cddelta; // dE/d(sum BO) accumulator (fixed point)
+};
+
+struct Accum {                 // per-atom energies and virial (owner-written, double)
+  double* e;                   // [NTERMS*n]
+  double* vir;                 // [6*n]
+};
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ long long fix_of(double v, int* err) {
+  if (!(fabs(v) < FIX_LIMIT)) {
+    atomicOr(err, ERR_NAN);
+    return 0;
+  }
+  return __double2ll_rn(v * FIX_SCALE);
+}
+__device__ __forceinline__ void fix_add(unsigned long long* p, double v, int* err) {
+  long long f = fix_of(v, err);
+  if (f != 0) atomicAdd(p, (unsigned long long)f);
+}
+__device__ __forceinline__ double fix_get(const unsigned long long* p) {
+  return (double)(long long)(*p) * FIX_INV;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void shift_decode(int code, int& sx, int& sy, int& sz) {
+  sx = code / 9 - 1;
+  sy = (code / 3) % 3 - 1;
+  sz = code % 3 - 1;
+}
+
+// precision-generic math wrappers
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float m_pow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_cbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ float m_cbrt(float x) { return cbrtf(x); }
+__device__ __forceinline__ double m_acos(double x) { return acos(x); }
+__device__ __forceinline__ float m_acos(float x) { return acosf(x); }
+__device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
+// exp with the argument capped so FP32 never overflows to inf (inf*0 -> NaN in the
+// derivative products); the cap is far beyond any value that changes an FP64 result
+template <typename R> __device__ __forceinline__ R exp_cap_arg();
+template <> __device__ __forceinline__ double exp_cap_arg<double>() { return 700.0; }
+template <> __device__ __forceinline__ float exp_cap_arg<float>() { return 80.0f; }
+template <typename R> __device__ __forceinline__ R m_expc(R x) {
+  return m_exp(x < exp_cap_arg<R>() ? x : exp_cap_arg<R>());
+}
+template <typename R> __device__ __forceinline__ R rclamp(R x, R lo, R hi) {
+  return x < lo ? lo : (x > hi ? hi : x);
+}
+// 1 / (1 + exp(u)) and its derivative -s(1-s), overflow-safe
+template <typename R> __device__ __forceinline__ R sig_neg(R u) {
+  return R(1) / (R(1) + m_expc(u));
+}
+// s = 1/(1 + e^u) and sd = s (1 - s) = e^u s^2 without the cancellation of 1 - s
+template <typename R> __device__ __forceinline__ void sig_pair(R u, R& s, R& sd) {
+  const R e = m_expc(u);
+  s = R(1) / (R(1) + e);
+  sd = e * s * s;
+}
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
+__device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
+// a*b - c*d with one rounding error (fma-based; Kahan's difference of products)
+__device__ __forceinline__ double diff_prod(double a, double b, double c, double d) { return a * b - c * d; }
+__device__ __forceinline__ float diff_prod(float a, float b, float c, float d) {
+  const float w = __fmul_rn(c, d);
+  const float e = __fmaf_rn(-c, d, w);
+  const float f = __fmaf_rn(a, b, -w);
+  return f + e;
+}
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+
+// taper Tap(x) = 20x^7 - 70x^6 + 84x^5 - 35x^4 + 1 and dTap/dr, x = r/R
+template <typename R> __device__ __forceinline__ void taper(R r, R Rc, R& t, R& dt) {
+  R x = r / Rc;
+  R x2 = x * x, x3 = x2 * x;
+  t = ((((R(20) * x - R(70)) * x + R(84)) * x - R(35)) * x2 * x2) + R(1);
+  dt = ((((R(140) * x - R(420)) * x + R(420)) * x - R(140)) * x3) / Rc;
+}
+
+// Image vector d = (x_j - x_i) + s*L of a list entry (shift code 0..26).
+// FP64: the defining arithmetic. FP32: hi/lo float positions with an error-free
+// difference of the hi parts, so d is within ~1 ulp of its own magnitude (not of L).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+template <typename R> struct PairVec;
+template <> struct PairVec<double> {
+  static __device__ __forceinline__ void get(const Sys& s, int i, int j, int code, int r, double& dx,
+                                             double& dy, double& dz) {
+    int sx, sy, sz;
+    shift_decode(code, sx, sy, sz);
+    const double* L = s.box + 3 * r;
+    dx = __dadd_rn(__dsub_rn(s.x[j], s.x[i]), sx == 0 ? 0.0 : (sx > 0 ? L[0] : -L[0]));
+    dy = __dadd_rn(__dsub_rn(s.y[j], s.y[i]), sy == 0 ? 0.0 : (sy > 0 ? L[1] : -L[1]));
+    dz = __dadd_rn(__dsub_rn(s.z[j], s.z[i]), sz == 0 ? 0.0 : (sz > 0 ? L[2] : -L[2]));
+  }
+};
+__device__ __forceinline__ float pv_comp(float hj, float hi, float lj, float li, int sgn, float Lh,
+                                         float Ll) {
+  float d, e;
+  two_sum(hj, -hi, d, e);
+  float a = sgn == 0 ? d : __fadd_rn(d, sgn > 0 ? Lh : -Lh);
+  float t = __fadd_rn(__fadd_rn(e, __fsub_rn(lj, li)), sgn == 0 ? 0.0f : (sgn > 0 ? Ll : -Ll));
+  return __fadd_rn(a, t);
+}
+// float-float image vector: d = dh + dl with |dl| <= ulp(dh)/2 (error-free transforms)
+__device__ __forceinline__ void pv_comp_ff(float hj, float hi, float lj, float li, int sgn, float Lh, float Ll,
+                                           float& dh, float& dl) {
+  float d, e;
+  two_sum(hj, -hi, d, e);
+  float a, e2;
+  if (sgn == 0) { a = d; e2 = 0.0f; }
+  else two_sum(d, sgn > 0 ? Lh : -Lh, a, e2);
+  const float t = __fadd_rn(__fadd_rn(__fadd_rn(e, e2), __fsub_rn(lj, li)), sgn == 0 ? 0.0f : (sgn > 0 ? Ll : -Ll));
+  two_sum(a, t, dh, dl);
+}
+// float-float |d|: r = rh + rl from exact squares (fma) and one Newton correction
+__device__ __forceinline__ void norm_ff(const float* dh, const float* dl, float& rh, float& rl) {
+  float sh = 0.0f, sl = 0.0f;
+  for (int c = 0; c < 3; ++c) {
+    const float p = __fmul_rn(dh[c], dh[c]);
+    const float pe = __fmaf_rn(dh[c], dh[c], -p);
+    float t, te;
+    two_sum(sh, p, t, te);
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(te, __fadd_rn(pe, 2.0f * dh[c] * dl[c])));
+  }
+  float s, se;
+  two_sum(sh, sl, s, se);
+  rh = sqrtf(s);
+  const float q = __fmul_rn(rh, rh);
+  const float qe = __fmaf_rn(rh, rh, -q);
+  rl = (((s - q) - qe) + se) / (2.0f * rh);
+}
+
+template <> struct PairVec<float> {
+  static __device__ __forceinline__ void get(const Sys& s, int i, int j, int code, int r, float& dx,
+                                             float& dy, float& dz) {
+    int sx, sy, sz;
+    shift_decode(code, sx, sy, sz);
+    const float* Lh = s.boxh + 3 * r;
+    const float* Ll = s.boxl + 3 * r;
+    dx = pv_comp(s.xh[j], s.xh[i], s.xl[j], s.xl[i], sx, Lh[0], Ll[0]);
+    dy = pv_comp(s.yh[j], s.yh[i], s.yl[j], s.yl[i], sy, Lh[1], Ll[1]);
+    dz = pv_comp(s.zh[j], s.zh[i], s.zl[j], s.zl[i], sz, Lh[2], Ll[2]);
+  }
+};
+// r^2 exactly as the list definition fixes it (FP64, no contraction)
+__device__ __forceinline__ double r2_exact(const Sys& s, int i, int j, int code, int r) {
+  double dx, dy, dz;
+  PairVec<double>::get(s, i, j, code, r, dx, dy, dz);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// ------------------------------------------------------------------ bounded grid barrier
+// Used only inside cooperative launches (all blocks co-resident). Sense via a
+// generation counter; gives up after `limit` polls, sets ERR_TIMEOUT and returns false.
+struct GridBar {
+  unsigned int arrive;
+  unsigned int gen;
+};
+constexpr long long BAR_SPIN_LIMIT = 20000000LL;    // ~1-2 s of polling (64 ns sleeps)
+
+// ------------------------------------------------------------------ host side
+struct reaxff_ctx_impl;
+std::string cuda_err_str(cudaError_t e);
+
+// kernel entry points (host launch wrappers), defined in the .cu files
+namespace rx {
+struct Launch {
+  cudaStream_t st;
+  int64_t* count;              // launch counter
+};
+// lists.cu
+void cells_build(const Launch& L, Sys s, Cells c);
+template <typename R>
+void far_list(const Launch& L, Sys s, Cells c, FarList f, const DParams<R>* P, float margin);
+template <typename R>
+void bond_list(const Launch& L, Sys s, FarList f, BondList b, HbList h, AtomQ a, const DParams<R>* P,
+               const DParams<double>* Pd);
+void bond_mirror(const Launch& L, Sys s, BondList b);
+void bo_prime64(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<double>* Pd, int n_canon_max);
+// bonded.cu
+template <typename R>
+void bo_correct(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<double>* P);
+template <typename R>
+void atom_terms(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P,
+                unsigned mask);
+template <typename R>
+void over_under_bond(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P,
+                     unsigned mask);
+template <typename R>
+void s_gather(const Launch& L, Sys s, BondList b, AtomQ a);
+template <typename R>
+void angles(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P, unsigned mask);
+template <typename R>
+void torsions(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P,
+              unsigned mask);
+template <typename R>
+void hbonds(const Launch& L, Sys s, BondList b, HbList h, Accum acc, const DParams<R>* P,
+            unsigned mask);
+// nonbonded.cu
+template <typename R>
+void nonbonded(const Launch& L, Sys s, FarList f, Accum acc, const DParams<R>* P, unsigned mask);
+// forces.cu
+template <typename R>
+void chain_rule(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc);
+void finalize_forces(const Launch& L, Sys s, double* F);
+void reduce_energies(const Launch& L, Sys s, Accum acc, double* E_rep, double* vir_rep);
+void verlet_kick_drift(const Launch& L, Sys s, const double* mass_t, double dt, int drift);
+void kinetic(const Launch& L, Sys s, const double* mass_t, double* ke_rep);
+void etot_combine(const Launch& L, int nrep, const double* E_rep, const double* ke, double* out);
+// qeq.cu
+struct QeqState {
+  double *s, *t;               // solutions
+  double *hist_s, *hist_t;     // [4*n] previous solutions (ring)
+  int nhist, hist_pos;
+  double *r_s, *r_t, *p_s, *p_t, *w_s, *w_t, *z_s, *z_t, *u_s, *u_t;
+  double* part;                // chunk partials
+  double* red;                 // per-replica reductions
+  double* scal;                // per-replica scalars
+  int* chunk_rep;              // replica of each chunk
+  int* chunk_lo;               // first atom of each chunk [nchunk+1]
+  int* rep_chunk;              // first chunk of each replica [nrep+1]
+  int nchunk;
+  int* iters;                  // [2*nrep]
+  GridBar* bar;
+  int grid;                    // cooperative grid size
+};
+template <typename R>
+int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* P, const double* chi,
+              const double* eta, double tol, int max_iter, int warm);
+void qeq_push_history(const Launch& L, int n, QeqState& Q);
+int qeq_grid_size(int nsm);
+}  // namespace rx

@@ -1,0 +1,284 @@
+"""Python binding of libreaxff.so (include/reaxff.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels. The module-level functions carry
+the C names; `ReaxFF` wraps one context. Loading fails loudly when the library is
+missing (build it with `python -m paper_1706_07772_gb300.build`).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+MAXT = 8
+NTERMS = 13
+TERMS = ("bond", "lp", "over", "under", "val", "pen", "coa", "tors", "conj", "hbond", "vdw", "coul", "pol")
+OK, E_INVALID, E_CUDA, E_CAPACITY, E_NOT_CONVERGED, E_TIMEOUT, E_NAN, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7
+FP64, MIXED = 0, 1
+WARM_EXTRAP, WARM_ZERO, WARM_MLP = 0, 1, 2
+LIST_FAR, LIST_BOND, LIST_HBOND = 0, 1, 2
+
+_PER_TYPE = ("mass", "val", "vale", "valboc", "valang", "p_lp2", "p_ovun2", "p_ovun5", "p_val3", "p_val5",
+             "chi", "eta", "gamma_t")
+_PER_PAIR = ("r0s", "r0p", "r0pp", "p_bo1", "p_bo2", "p_bo3", "p_bo4", "p_bo5", "p_bo6", "p_boc3", "p_boc4",
+             "p_boc5", "ovc", "v13", "De_s", "De_p", "De_pp", "p_be1", "p_be2", "p_ovun1", "vdw_D", "vdw_rv",
+             "vdw_alpha", "vdw_gw", "gamma")
+_PER_TRIPLE = ("th00", "p_val1", "p_val2", "p_val4", "p_val7", "p_pen1", "p_coa1")
+_PER_PAIR2 = ("V1", "V2", "V3", "p_tor1", "p_cot1", "r0hb", "p_hb1", "p_hb2", "p_hb3")
+_GENERAL = ("p_boc1", "p_boc2", "p_lp1", "p_ovun3", "p_ovun4", "p_ovun6", "p_ovun7", "p_ovun8", "p_val6",
+            "p_val8", "p_val9", "p_val10", "p_pen2", "p_pen3", "p_pen4", "p_coa2", "p_coa3", "p_coa4",
+            "p_tor2", "p_tor3", "p_tor4", "p_cot2", "p_vdW1", "k_e")
+
+_D8 = C.c_double * MAXT
+_D88 = _D8 * MAXT
+_D888 = _D88 * MAXT
+
+
+class Params(C.Structure):
+    _fields_ = ([("ntypes", C.c_int32), ("hb", C.c_int32 * MAXT)] + [(k, _D8) for k in _PER_TYPE]
+                + [(k, _D88) for k in _PER_PAIR] + [(k, _D888) for k in _PER_TRIPLE]
+                + [(k, _D88) for k in _PER_PAIR2] + [(k, C.c_double) for k in _GENERAL])
+
+
+class Options(C.Structure):
+    _fields_ = [("r_nb", C.c_double), ("r_bond", C.c_double), ("r_hb", C.c_double), ("bo_cut", C.c_double),
+                ("thb_cut", C.c_double), ("thb_cutsq", C.c_double), ("hb_bo_min", C.c_double),
+                ("qeq_tol", C.c_double), ("qeq_max_iter", C.c_int32), ("precision", C.c_int32),
+                ("warm_start", C.c_int32), ("term_mask", C.c_int32), ("capacity_margin", C.c_double)]
+
+
+class ReaxFFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("reaxff error %d: %s" % (code, msg))
+        self.code = code
+
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libreaxff.so")
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libreaxff.so and check the struct layouts against the library's own."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libreaxff.so not built: run `python -m paper_1706_07772_gb300.build` (%s)" % path)
+    lib = C.CDLL(path)
+    vp, i32, i64, dp, ip32, ip64 = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+    sig = {
+        "reaxff_sizeof_params": (i64, []), "reaxff_sizeof_options": (i64, []),
+        "reaxff_params_offset": (i64, [C.c_char_p]),
+        "reaxff_create": (C.c_int, [C.POINTER(Params), ip32, i64, dp, C.POINTER(Options), C.POINTER(vp)]),
+        "reaxff_create_batch": (C.c_int, [C.POINTER(Params), i32, ip64, ip32, dp, C.POINTER(Options), C.POINTER(vp)]),
+        "reaxff_destroy": (None, [vp]), "reaxff_last_error": (C.c_char_p, [vp]),
+        "reaxff_num_atoms": (i64, [vp]), "reaxff_num_replicas": (i32, [vp]),
+        "reaxff_set_state": (C.c_int, [vp, dp, dp]), "reaxff_get_state": (C.c_int, [vp, dp, dp, dp]),
+        "reaxff_build_lists": (C.c_int, [vp]),
+        "reaxff_get_lists": (C.c_int, [vp, i32, i64, ip64, ip32, ip32, C.POINTER(C.c_int8)]),
+        "reaxff_get_bond_orders": (C.c_int, [vp, i64, ip64, dp, dp, dp, dp]),
+        "reaxff_qeq": (C.c_int, [vp, dp, ip32, ip32]),
+        "reaxff_forces": (C.c_int, [vp, dp, dp, dp]),
+        "reaxff_forces_fixed_q": (C.c_int, [vp, dp, dp, dp, dp]),
+        "reaxff_step": (C.c_int, [vp, i32, C.c_double, dp]),
+        "reaxff_last_launch_count": (i64, [vp]),
+        "reaxff_set_state_dev": (C.c_int, [vp, vp, vp, vp]),
+        "reaxff_get_state_dev": (C.c_int, [vp, vp, vp, vp, vp]),
+        "reaxff_step_dev": (C.c_int, [vp, i32, C.c_double, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if lib.reaxff_sizeof_params() != C.sizeof(Params) or lib.reaxff_sizeof_options() != C.sizeof(Options):
+        raise ImportError("reaxff struct size mismatch between binding and library")
+    for name, _ in Params._fields_:
+        if lib.reaxff_params_offset(name.encode()) != getattr(Params, name).offset:
+            raise ImportError("reaxff_params field offset mismatch: " + name)
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def make_params(p: dict) -> Params:
+    """Pack a parameter dict (numpy tables, types 0..ntypes-1) into the C struct."""
+    P = Params()
+    nt = int(p["ntypes"])
+    P.ntypes = nt
+    for t in range(nt):
+        P.hb[t] = int(p["hb"][t])
+    for k in _PER_TYPE:
+        arr = getattr(P, k)
+        for t in range(nt):
+            arr[t] = float(p[k][t])
+    for k in _PER_PAIR + _PER_PAIR2:
+        arr = getattr(P, k)
+        v = np.asarray(p[k], float)
+        for a in range(nt):
+            for b in range(nt):
+                arr[a][b] = v[a, b]
+    for k in _PER_TRIPLE:
+        arr = getattr(P, k)
+        v = np.asarray(p[k], float)
+        for a in range(nt):
+            for b in range(nt):
+                for c in range(nt):
+                    arr[a][b][c] = v[a, b, c]
+    for k in _GENERAL:
+        setattr(P, k, float(p[k]))
+    return P
+
+
+def make_options(o: dict, precision=FP64, warm_start=WARM_EXTRAP, term_mask=0, capacity_margin=0.0) -> Options:
+    O = Options()
+    for k in ("r_nb", "r_bond", "r_hb", "bo_cut", "thb_cut", "thb_cutsq", "hb_bo_min", "qeq_tol"):
+        setattr(O, k, float(o[k]))
+    O.qeq_max_iter = int(o.get("qeq_max_iter", 200))
+    O.precision = int(precision)
+    O.warm_start = int(warm_start)
+    O.term_mask = int(term_mask)
+    O.capacity_margin = float(capacity_margin)
+    return O
+
+
+def term_mask(*names) -> int:
+    m = 0
+    for nm in names:
+        m |= 1 << TERMS.index(nm)
+    return m
+
+
+# ------------------------------------------------------------------ C-named wrappers
+def reaxff_create(params: Params, types, box, options: Options):
+    lib = load()
+    t = np.ascontiguousarray(types, np.int32)
+    b = np.ascontiguousarray(box, np.float64)
+    h = C.c_void_p()
+    rc = lib.reaxff_create(C.byref(params), t.ctypes.data_as(C.POINTER(C.c_int32)), len(t), _dp(b),
+                           C.byref(options), C.byref(h))
+    if rc != OK:
+        raise ReaxFFError(rc, "reaxff_create failed")
+    return h
+
+
+def reaxff_create_batch(params: Params, rep_offsets, types, boxes, options: Options):
+    lib = load()
+    off = np.ascontiguousarray(rep_offsets, np.int64)
+    t = np.ascontiguousarray(types, np.int32)
+    b = np.ascontiguousarray(boxes, np.float64).reshape(-1)
+    h = C.c_void_p()
+    rc = lib.reaxff_create_batch(C.byref(params), len(off) - 1, off.ctypes.data_as(C.POINTER(C.c_int64)),
+                                 t.ctypes.data_as(C.POINTER(C.c_int32)), _dp(b), C.byref(options), C.byref(h))
+    if rc != OK:
+        raise ReaxFFError(rc, "reaxff_create_batch failed")
+    return h
+
+
+class ReaxFF:
+    """One library context (single system or a batch of replicas)."""
+
+    def __init__(self, params: dict, types, box, options: dict, precision=FP64, warm_start=WARM_EXTRAP,
+                 term_mask=0, rep_offsets=None, capacity_margin=0.0):
+        self.lib = load()
+        P = make_params(params)
+        O = make_options(options, precision, warm_start, term_mask, capacity_margin)
+        self.types = np.ascontiguousarray(types, np.int32)
+        if rep_offsets is None:
+            self.h = reaxff_create(P, self.types, np.asarray(box, float).reshape(3), O)
+        else:
+            self.h = reaxff_create_batch(P, rep_offsets, self.types, np.asarray(box, float), O)
+        self.n = int(self.lib.reaxff_num_atoms(self.h))
+        self.nrep = int(self.lib.reaxff_num_replicas(self.h))
+
+    def _check(self, rc, allow=()):
+        if rc != OK and rc not in allow:
+            raise ReaxFFError(rc, self.lib.reaxff_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.reaxff_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, x, v=None):
+        x = np.ascontiguousarray(x, np.float64).reshape(self.n, 3)
+        v = None if v is None else np.ascontiguousarray(v, np.float64).reshape(self.n, 3)
+        self._check(self.lib.reaxff_set_state(self.h, _dp(x), _dp(v)))
+
+    def get_state(self):
+        x = np.empty((self.n, 3))
+        v = np.empty((self.n, 3))
+        q = np.empty(self.n)
+        self._check(self.lib.reaxff_get_state(self.h, _dp(x), _dp(v), _dp(q)))
+        return x, v, q
+
+    def build_lists(self):
+        self._check(self.lib.reaxff_build_lists(self.h))
+
+    def get_lists(self, which):
+        cnt = C.c_int64()
+        self._check(self.lib.reaxff_get_lists(self.h, which, 0, C.byref(cnt), None, None, None))
+        m = cnt.value
+        i = np.empty(m, np.int32)
+        j = np.empty(m, np.int32)
+        s = np.empty((m, 3), np.int8)
+        self._check(self.lib.reaxff_get_lists(self.h, which, m, C.byref(cnt), i.ctypes.data_as(C.POINTER(C.c_int32)),
+                                              j.ctypes.data_as(C.POINTER(C.c_int32)),
+                                              s.ctypes.data_as(C.POINTER(C.c_int8))))
+        return i, j, s
+
+    def get_bond_orders(self):
+        cnt = C.c_int64()
+        self._check(self.lib.reaxff_get_bond_orders(self.h, 0, C.byref(cnt), None, None, None, None))
+        m = cnt.value
+        out = {k: np.empty(m) for k in ("bo_prime", "bo", "bo_pi", "bo_pp")}
+        self._check(self.lib.reaxff_get_bond_orders(self.h, m, C.byref(cnt), _dp(out["bo_prime"]), _dp(out["bo"]),
+                                                    _dp(out["bo_pi"]), _dp(out["bo_pp"])))
+        return out
+
+    def qeq(self):
+        q = np.empty(self.n)
+        its = np.empty(self.nrep, np.int32)
+        itt = np.empty(self.nrep, np.int32)
+        rc = self._check(self.lib.reaxff_qeq(self.h, _dp(q), its.ctypes.data_as(C.POINTER(C.c_int32)),
+                                             itt.ctypes.data_as(C.POINTER(C.c_int32))), allow=(E_NOT_CONVERGED,))
+        return q, its, itt, rc == OK
+
+    def forces(self, q=None):
+        F = np.empty((self.n, 3))
+        E = np.empty((self.nrep, NTERMS))
+        W = np.empty((self.nrep, 6))
+        if q is None:
+            self._check(self.lib.reaxff_forces(self.h, _dp(F), _dp(E), _dp(W)), allow=(E_NOT_CONVERGED,))
+        else:
+            qq = np.ascontiguousarray(q, np.float64)
+            self._check(self.lib.reaxff_forces_fixed_q(self.h, _dp(qq), _dp(F), _dp(E), _dp(W)))
+        return F, E, W
+
+    def step(self, nsteps, dt_fs=0.1, energies=True):
+        et = np.empty((max(nsteps, 1), self.nrep)) if energies else None
+        self._check(self.lib.reaxff_step(self.h, int(nsteps), float(dt_fs), _dp(et)))
+        return et[:nsteps] if energies else None
+
+    def step_dev(self, nsteps, dt_fs, etot_dev_ptr, stream_ptr):
+        self._check(self.lib.reaxff_step_dev(self.h, int(nsteps), float(dt_fs), C.c_void_p(etot_dev_ptr),
+                                             C.c_void_p(stream_ptr)))
+
+    def last_launch_count(self):
+        return int(self.lib.reaxff_last_launch_count(self.h))
+
+
+def virial_matrix(w6):
+    """(xx, yy, zz, xy, xz, yz) -> symmetric 3x3."""
+    xx, yy, zz, xy, xz, yz = w6
+    return np.array([[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]])
