@@ -1,0 +1,365 @@
+"""Benchmark: ReaxFF MD timesteps on the synthetic 32,480-atom CHNO crystal (atom-steps/s).
+
+Default (no flags): 1 GPU, the mixed-precision path (FP32 interaction math, FP64 sums)
+with the extrapolated QEq warm start at QEq tolerance 1e-6, dt = 0.1 fs, lists rebuilt
+and QEq solved every step. One JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload petn32k|petn1m|petn464] [--precision mixed|fp64]
+
+A step is one velocity-Verlet step of the whole path (lists, QEq, all energy terms,
+chain rule, integration). `value` times K device-resident steps with CUDA events, the
+L2 cache flushed (a 256 MB write) before each timed step. `e2e` times the same steps
+through the host API (positions and velocities uploaded, state and energy downloaded
+every step). For N > 1 every rank runs its own independent system (weak scaling,
+no collective on the data path). `--impl reference` times the FP64 CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s (32K & 1M atoms), mixed+warm-start vs FP64 at equal force error"
+UNIT = "atom-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="petn32k")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--dt", type=float, default=0.1)
+    ap.add_argument("--no-extras", action="store_true", help="skip fp64 compare, e2e and cpu baseline")
+    return ap.parse_args()
+
+
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.samples = []
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p.get("hbm_gbs", 6800.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------------------------------
+# algorithmic cost model of the timed stages (per launch), from the list sizes
+# ---------------------------------------------------------------------------------------
+def stage_costs(ctx, n, prec_bytes, qeq_iters):
+    """Algorithmic bytes per launch of the memory-bound stages:
+      far_list  : write j (4 B) + image code (1 B) + H entry (R) per full-list entry
+      qeq       : per CG iteration one read of H (index 4 B + value R) for both systems plus
+                  ~12 FP64 vector streams of n (z, p, w, x, r per system, read or written)
+      nonbonded : read j + code per entry (positions and charges are cache resident)
+    """
+    import paper_1706_07772_gb300.reaxff as rx
+    nfar = ctx.get_lists(rx.LIST_FAR)[0].size
+    it = max(1, int(qeq_iters))
+    return {
+        "far_list": {"bytes": nfar * (5 + prec_bytes), "entries": nfar},
+        "qeq": {"bytes": it * (nfar * (4 + prec_bytes) + 12 * 8 * n * 2), "iters": it},
+        "nonbonded": {"bytes": nfar * 5, "entries": nfar},
+    }
+
+
+def run_ours(a, rank, world):
+    import torch
+
+    import paper_1706_07772_gb300.reaxff as rx
+    import synth
+    from paper_1706_07772_gb300 import build as B
+    if rank == 0:
+        B.build()
+    barrier(world)
+    rx.load()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    P = synth.make_params()
+    w = synth.workload(a.workload, seed=rank)
+    n = len(w["x"])
+    prec = rx.MIXED if a.precision == "mixed" else rx.FP64
+    ctx = rx.ReaxFF(P, w["types"], w["box"], w["options"], precision=prec, warm_start=rx.WARM_EXTRAP)
+    ctx.set_state(w["x"], w["v"])
+    stream = torch.cuda.current_stream(dev)
+    etot = torch.zeros(max(a.steps, 1), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # warm-up
+    for _ in range(a.warmup):
+        ctx.step_dev(1, a.dt, etot.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    ctx.profile_enable(True)
+    launches = 0
+    ms_total = 0.0
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.25)
+    for k in range(a.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step_dev(1, a.dt, etot.data_ptr() + 8 * k, stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms_total += e0.elapsed_time(e1)
+        launches += ctx.last_launch_count()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    its, itt = ctx.last_qeq_iters()
+    ms_step = max_over_ranks(ms_total / max(a.steps, 1), world)
+    value = world * n / (ms_step * 1e-3)
+    et = etot.cpu().numpy()[: a.steps]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == rx.MIXED else "f64", "data": "synthetic",
+        "config": {"workload": a.workload, "atoms": n, "atoms_per_gpu": n, "precision": a.precision,
+                   "warm_start": "extrapolated", "qeq_tol": w["options"]["qeq_tol"], "dt_fs": a.dt,
+                   "lists": "rebuilt every step", "l2": "flushed (256 MB write) before each timed step",
+                   "parallelism": "independent system per GPU" if world > 1 else "single GPU"},
+        "clocks": clocks.summary(),
+        "gpu_launches": launches,
+        "qeq_iters_last": [int(its[0]), int(itt[0])],
+        "nve_rel_drift": float(np.abs(et - et[0]).max() / abs(et[0])) if len(et) > 1 else None,
+    }
+    stages = {k: {"ms_per_step": v[0] / max(a.steps, 1), "launches": v[1]} for k, v in prof.items() if v[1] > 0}
+    out["stages"] = {k: round(v["ms_per_step"], 4) for k, v in sorted(stages.items(), key=lambda t: -t[1]["ms_per_step"])}
+    # roofline of the dominant stage
+    pk = peaks()
+    costs = stage_costs(ctx, n, 4 if prec == rx.MIXED else 8, int(its[0]) + 0)
+    dom = max(stages, key=lambda k: stages[k]["ms_per_step"])
+    out["roofline"] = roofline(dom, stages, costs, pk, prec)
+    out["_ctx"] = ctx
+    out["_w"] = w
+    out["_P"] = P
+    return out
+
+
+def roofline(dom, stages, costs, pk, prec):
+    st = stages[dom]
+    per_launch_ms = st["ms_per_step"] * 1.0   # one launch of each stage per step
+    if dom in costs:
+        byts = costs[dom]["bytes"]
+        ach = byts / (per_launch_ms * 1e-3) / 1e9
+        return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"],
+                "algorithmic_bytes_per_launch": byts}
+    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None}
+
+
+def e2e(ctx, w, steps, dt):
+    """Host-API steps: upload x, v (pinned not needed for correctness; numpy buffers),
+    one step, download x, v, q and the energy; wall clock around the whole loop."""
+    x, v, q = ctx.get_state()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.set_state(x, v)
+        e = ctx.step(1, dt)
+        x, v, q = ctx.get_state()
+    t = time.perf_counter() - t0
+    n = ctx.n
+    return {"value": n * steps / t, "unit": UNIT, "h2d_bytes_per_step": 48 * n,
+            "d2h_bytes_per_step": 56 * n + 8, "steps": steps}
+
+
+def cpu_oracle_step(P, w):
+    """One oracle MD step (lists, QEq to the workload tolerance, energy + forces, Verlet
+    update) on the host cores. Returns (seconds, threads, model, lists)."""
+    import torch
+
+    import oracle
+    m = oracle.Model(P, w["types"], w["box"], w["options"])
+    t0 = time.perf_counter()
+    out = m.forces(w["x"])
+    mass = P["mass"][w["types"]]
+    v = w["v"] + 0.5 * 0.1 * oracle.reaxff_oracle.ACC_CONV * out["F"] / mass[:, None]
+    np.mod(w["x"] + 0.1 * v, w["box"])
+    t = time.perf_counter() - t0
+    return t, torch.get_num_threads(), m, out["lists"]
+
+
+def oracle_reference_forces(m, L, w):
+    """Oracle forces at the start state with QEq converged to 1e-10 (error reference)."""
+    q = m.qeq(w["x"], L, tol=1e-10)["q"]
+    return m.energy(w["x"], q, L)["F"]
+
+
+def run_reference(a, rank, world):
+    """The oracle as the reference arm: each step one oracle MD step on a bounded sample
+    of the workload (the 4x3x2-cell piece of the same crystal, 1,392 atoms)."""
+    if rank != 0:
+        return None
+    import torch
+
+    import oracle
+    import synth
+    P = synth.make_params()
+    types, x, box = synth.crystal((4, 3, 2), seed=0)
+    opts = dict(synth.OPTIONS_DEFAULT)
+    m = oracle.Model(P, types, box, opts)
+    v = synth.velocities(types, 300.0, seed=1)
+    for _ in range(min(a.warmup, 1)):
+        m.forces(x)
+    t0 = time.perf_counter()
+    x, v, F, et = oracle.verlet(m, x, v, a.dt, a.steps, F=m.forces(x)["F"])
+    t = time.perf_counter() - t0
+    n = len(types)
+    val = n * a.steps / t
+    return {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * t / max(a.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": a.workload, "sample": "4x3x2 cells of the same crystal (%d atoms)" % n},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": "%d oracle MD steps on %d atoms" % (a.steps, n)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    rank, world = dist_setup(a.gpus)
+    if a.impl == "reference":
+        out = run_reference(a, rank, world)
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    out = run_ours(a, rank, world)
+    ctx, w, P = out.pop("_ctx"), out.pop("_w"), out.pop("_P")
+    if rank == 0 and not a.no_extras:
+        import paper_1706_07772_gb300.reaxff as rx
+        import torch
+        # FP64 GPU path on the same workload (the comparison the metric names)
+        if a.precision == "mixed":
+            c64 = rx.ReaxFF(P, w["types"], w["box"], w["options"], precision=rx.FP64)
+            c64.set_state(w["x"], w["v"])
+            st = torch.cuda.current_stream()
+            et = torch.zeros(64, dtype=torch.float64, device="cuda")
+            c64.step_dev(2, a.dt, et.data_ptr(), st.cuda_stream)
+            torch.cuda.synchronize()
+            k64 = max(3, min(10, a.steps // 5))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            c64.step_dev(k64, a.dt, et.data_ptr(), st.cuda_stream)
+            e1.record(st)
+            e1.synchronize()
+            ms64 = e0.elapsed_time(e1) / k64
+            out["compare"] = {"fp64_value": ctx.n / (ms64 * 1e-3), "fp64_ms_per_step": ms64,
+                              "mixed_over_fp64": (ms64 / out["ms_per_step"])}
+        # end to end through the host API
+        out["e2e"] = e2e(ctx, w, max(5, min(20, a.steps // 5)), a.dt)
+        # CPU baseline (oracle) and force error of both GPU paths at the same state
+        t, cores, m, L = cpu_oracle_step(P, w)
+        nat = len(w["x"])
+        out["cpu_baseline"] = {"value": nat / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": "1 oracle MD step on the full %s (%d atoms), %.1f s" % (a.workload, nat, t)}
+        Fo = oracle_reference_forces(m, L, w)
+        rms = float(np.sqrt((Fo ** 2).mean()))
+        ferr = {}
+        for name, prec in (("mixed", rx.MIXED), ("fp64", rx.FP64)):
+            c = rx.ReaxFF(P, w["types"], w["box"], w["options"], precision=prec)
+            c.set_state(w["x"], w["v"])
+            F, E, W = c.forces()
+            ferr[name] = float(np.abs(F - Fo).max() / rms)
+            c.close()
+        out["force_error_max_over_rms"] = ferr
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

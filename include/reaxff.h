@@ -142,7 +142,9 @@ int64_t reaxff_num_atoms(const reaxff_ctx* ctx);
 int32_t reaxff_num_replicas(const reaxff_ctx* ctx);
 
 /* Positions x (double[n*3], row-major xyz, A) and velocities v (double[n*3], A/fs,
- * NULL = zero). Positions are wrapped into [0, L). Resets the QEq history. */
+ * NULL = zero). Positions are wrapped into [0, L). The QEq solution history used for
+ * the extrapolated initial guess is kept (it only changes the starting point of CG,
+ * never the converged charges); reaxff_reset_qeq_history() clears it. */
 int reaxff_set_state(reaxff_ctx* ctx, const double* x, const double* v);
 /* Copy out positions, velocities (double[n*3]) and charges (double[n]); any may be NULL. */
 int reaxff_get_state(reaxff_ctx* ctx, double* x, double* v, double* q);
@@ -187,6 +189,22 @@ int reaxff_step(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot);
 
 /* Kernel launches issued by the last reaxff_step call (for launch accounting). */
 int64_t reaxff_last_launch_count(const reaxff_ctx* ctx);
+
+/* CG iteration counts of the most recent QEq solve (int32[nrep] each, or NULL). */
+int reaxff_last_qeq_iters(reaxff_ctx* ctx, int32_t* iters_s, int32_t* iters_t);
+
+/* Forget the QEq solution history (the next solve starts from zero). */
+void reaxff_reset_qeq_history(reaxff_ctx* ctx);
+
+/* Per-stage timing with CUDA events recorded on the context's stream around every
+ * kernel group (cells, far_list, bond_list, bo_prime64, qeq, bo_correct, atom_terms,
+ * over_under_bond, s_gather, angles, torsions, hbonds, nonbonded, chain_rule, verlet,
+ * reduce). enable(1) also zeroes the totals. read() fills ms[] (accumulated
+ * milliseconds) and calls[] (timed launches) for up to nstage stages and returns the
+ * number of stages; stage_name() gives each stage's name. */
+void reaxff_profile_enable(reaxff_ctx* ctx, int32_t on);
+int32_t reaxff_profile_read(reaxff_ctx* ctx, int32_t nstage, double* ms, int64_t* calls);
+const char* reaxff_stage_name(int32_t stage);
 
 /* ---- device-pointer variants (no host copies; enqueue on `stream`) ---------------- */
 int reaxff_set_state_dev(reaxff_ctx* ctx, const double* x_dev, const double* v_dev, void* stream);

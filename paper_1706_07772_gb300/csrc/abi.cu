@@ -66,6 +66,12 @@ struct reaxff_ctx {
   double *chi_t = nullptr, *eta_t = nullptr, *mass_t = nullptr;
   int* h_err_pinned = nullptr;
   int cap_far = 0, cap_bond = 0, cap_hb = 0;
+  // per-stage CUDA-event timing (reaxff_profile_*)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_pending;   // (stage, index of start event; end = +1)
+  double stage_ms[32] = {0};
+  int64_t stage_calls[32] = {0};
 };
 
 namespace {
@@ -171,6 +177,46 @@ int alloc_lists(reaxff_ctx* ctx) {
 
 rx::Launch launch_of(reaxff_ctx* ctx) { return rx::Launch{ctx->st, &ctx->launches}; }
 
+const char* const STAGE_NAMES[] = {"cells", "far_list", "bond_list", "bo_prime64", "qeq", "bo_correct",
+                                   "atom_terms", "over_under_bond", "s_gather", "angles", "torsions",
+                                   "hbonds", "nonbonded", "chain_rule", "verlet", "reduce"};
+constexpr int NSTAGES = 16;
+
+// scoped event pair around one stage (only when profiling is on)
+struct Stage {
+  reaxff_ctx* ctx;
+  int id, idx = -1;
+  Stage(reaxff_ctx* c, int s) : ctx(c), id(s) {
+    if (!ctx->prof) return;
+    const size_t need = 2 * (ctx->ev_pending.size() + 1);
+    while (ctx->ev_pool.size() < need) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      ctx->ev_pool.push_back(e);
+    }
+    idx = (int)(2 * ctx->ev_pending.size());
+    cudaEventRecord(ctx->ev_pool[idx], ctx->st);
+  }
+  ~Stage() {
+    if (idx < 0) return;
+    cudaEventRecord(ctx->ev_pool[idx + 1], ctx->st);
+    ctx->ev_pending.push_back({id, idx});
+  }
+};
+
+void collect_profile(reaxff_ctx* ctx) {
+  if (ctx->ev_pending.empty()) return;
+  cudaStreamSynchronize(ctx->st);
+  for (auto& p : ctx->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev_pool[p.second], ctx->ev_pool[p.second + 1]) == cudaSuccess) {
+      ctx->stage_ms[p.first] += ms;
+      ctx->stage_calls[p.first] += 1;
+    }
+  }
+  ctx->ev_pending.clear();
+}
+
 int read_err(reaxff_ctx* ctx, int* flags) {
   CK(cudaMemcpyAsync(ctx->h_err_pinned, ctx->sys.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
@@ -183,16 +229,16 @@ int build_lists_impl(reaxff_ctx* ctx) {
     rx::Launch L = launch_of(ctx);
     CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
     CK(cudaMemsetAsync(ctx->bond.ncanon, 0, sizeof(int), ctx->st));
-    rx::cells_build(L, ctx->sys, ctx->cells);
+    { Stage st(ctx, 0); rx::cells_build(L, ctx->sys, ctx->cells); }
     if (ctx->fp64) {
-      rx::far_list<double>(L, ctx->sys, ctx->cells, ctx->far, ctx->Pd, ctx->far_margin);
-      rx::bond_list<double>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pd, ctx->Pd);
+      { Stage st(ctx, 1); rx::far_list<double>(L, ctx->sys, ctx->cells, ctx->far, ctx->Pd, ctx->far_margin); }
+      { Stage st(ctx, 2); rx::bond_list<double>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pd, ctx->Pd); }
     } else {
-      rx::far_list<float>(L, ctx->sys, ctx->cells, ctx->far, ctx->Pf, ctx->far_margin);
-      rx::bond_list<float>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pf, ctx->Pd);
+      { Stage st(ctx, 1); rx::far_list<float>(L, ctx->sys, ctx->cells, ctx->far, ctx->Pf, ctx->far_margin); }
+      { Stage st(ctx, 2); rx::bond_list<float>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pf, ctx->Pd); }
     }
-    rx::bond_mirror(L, ctx->sys, ctx->bond);
-    rx::bo_prime64(L, ctx->sys, ctx->bond, ctx->aq, ctx->Pd, ctx->n * ctx->bond.cap);
+    { Stage st(ctx, 2); rx::bond_mirror(L, ctx->sys, ctx->bond); }
+    { Stage st(ctx, 3); rx::bo_prime64(L, ctx->sys, ctx->bond, ctx->aq, ctx->Pd, ctx->n * ctx->bond.cap); }
     CK(cudaGetLastError());
     int flags = 0;
     int rc = read_err(ctx, &flags);
@@ -218,6 +264,7 @@ template <> const DParams<float>* params_of<float>(reaxff_ctx* ctx) { return ctx
 
 int qeq_impl(reaxff_ctx* ctx) {
   rx::Launch L = launch_of(ctx);
+  Stage stg(ctx, 4);
   int rc = ctx->fp64 ? rx::qeq_solve<double>(L, ctx->sys, ctx->far, ctx->Q, ctx->Pd, ctx->chi_t, ctx->eta_t,
                                              ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start)
                      : rx::qeq_solve<float>(L, ctx->sys, ctx->far, ctx->Q, ctx->Pf, ctx->chi_t, ctx->eta_t,
@@ -233,15 +280,15 @@ int qeq_impl(reaxff_ctx* ctx) {
 template <typename R> void terms_impl(reaxff_ctx* ctx) {
   rx::Launch L = launch_of(ctx);
   const DParams<R>* P = params_of<R>(ctx);
-  rx::bo_correct<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->Pd);
-  rx::atom_terms<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
-  rx::over_under_bond<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
-  rx::s_gather<R>(L, ctx->sys, ctx->bond, ctx->aq);
-  rx::angles<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
-  rx::torsions<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
-  rx::hbonds<R>(L, ctx->sys, ctx->bond, ctx->hb, ctx->acc, P, ctx->mask);
-  rx::nonbonded<R>(L, ctx->sys, ctx->far, ctx->acc, P, ctx->mask);
-  rx::chain_rule<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc);
+  { Stage st(ctx, 5); rx::bo_correct<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->Pd); }
+  { Stage st(ctx, 6); rx::atom_terms<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
+  { Stage st(ctx, 7); rx::over_under_bond<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
+  { Stage st(ctx, 8); rx::s_gather<R>(L, ctx->sys, ctx->bond, ctx->aq); }
+  { Stage st(ctx, 9); rx::angles<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
+  { Stage st(ctx, 10); rx::torsions<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
+  { Stage st(ctx, 11); rx::hbonds<R>(L, ctx->sys, ctx->bond, ctx->hb, ctx->acc, P, ctx->mask); }
+  { Stage st(ctx, 12); rx::nonbonded<R>(L, ctx->sys, ctx->far, ctx->acc, P, ctx->mask); }
+  { Stage st(ctx, 13); rx::chain_rule<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc); }
 }
 
 int zero_accumulators(reaxff_ctx* ctx) {
@@ -269,7 +316,7 @@ int forces_impl(reaxff_ctx* ctx, bool solve_q) {
   }
   if (ctx->fp64) terms_impl<double>(ctx);
   else terms_impl<float>(ctx);
-  rx::reduce_energies(launch_of(ctx), ctx->sys, ctx->acc, ctx->E_rep, ctx->vir_rep);
+  { Stage st(ctx, 15); rx::reduce_energies(launch_of(ctx), ctx->sys, ctx->acc, ctx->E_rep, ctx->vir_rep); }
   CK(cudaGetLastError());
   ctx->forces_valid = true;
   return REAXFF_OK;
@@ -547,6 +594,8 @@ int reaxff_create(const reaxff_params* params, const int32_t* types, int64_t n, 
 void reaxff_destroy(reaxff_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->Etot_dev) cudaFree(ctx->Etot_dev);
   ctx->lists.free_all();
   ctx->fixed.free_all();
   if (ctx->h_err_pinned) cudaFreeHost(ctx->h_err_pinned);
@@ -597,7 +646,6 @@ static int set_state_common(reaxff_ctx* ctx, const double* x, const double* v, c
   ctx->have_pos = true;
   ctx->forces_valid = false;
   ctx->lists_valid = false;
-  ctx->Q.nhist = 0;
   return REAXFF_OK;
 }
 
@@ -794,8 +842,9 @@ static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev) {
   }
   rx::Launch L = launch_of(ctx);
   for (int st = 0; st < nsteps; ++st) {
-    rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 1);
+    { Stage sg(ctx, 14); rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 1); }
     if ((rc = forces_impl(ctx, true))) return rc;
+    Stage sg(ctx, 14);
     rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 0);
     if (Etot_dev) {
       rx::kinetic(L, ctx->sys, ctx->mass_t, ctx->ke_rep);
@@ -803,7 +852,9 @@ static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev) {
     }
   }
   CK(cudaGetLastError());
-  return check_flags(ctx, false);
+  rc = check_flags(ctx, false);
+  collect_profile(ctx);
+  return rc;
 }
 
 int reaxff_step(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot) {
@@ -825,6 +876,42 @@ int reaxff_step(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot) {
     CK(cudaStreamSynchronize(ctx->st));
   }
   return REAXFF_OK;
+}
+
+int reaxff_last_qeq_iters(reaxff_ctx* ctx, int32_t* iters_s, int32_t* iters_t) {
+  if (!ctx) return REAXFF_E_INVALID;
+  std::vector<int> it(2 * ctx->nrep);
+  CK(cudaMemcpyAsync(it.data(), ctx->Q.iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int r = 0; r < ctx->nrep; ++r) {
+    if (iters_s) iters_s[r] = it[2 * r];
+    if (iters_t) iters_t[r] = it[2 * r + 1];
+  }
+  return REAXFF_OK;
+}
+
+void reaxff_reset_qeq_history(reaxff_ctx* ctx) {
+  if (ctx) ctx->Q.nhist = 0;
+}
+
+void reaxff_profile_enable(reaxff_ctx* ctx, int32_t on) {
+  if (!ctx) return;
+  ctx->prof = on != 0;
+  for (int s = 0; s < 32; ++s) { ctx->stage_ms[s] = 0; ctx->stage_calls[s] = 0; }
+}
+
+int32_t reaxff_profile_read(reaxff_ctx* ctx, int32_t nstage, double* ms, int64_t* calls) {
+  if (!ctx) return 0;
+  collect_profile(ctx);
+  for (int s = 0; s < nstage && s < NSTAGES; ++s) {
+    if (ms) ms[s] = ctx->stage_ms[s];
+    if (calls) calls[s] = ctx->stage_calls[s];
+  }
+  return NSTAGES;
+}
+
+const char* reaxff_stage_name(int32_t stage) {
+  return (stage >= 0 && stage < NSTAGES) ? STAGE_NAMES[stage] : "";
 }
 
 int reaxff_step_dev(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot_dev, void* stream) {

@@ -86,6 +86,12 @@ def load(path: str = LIB_PATH):
         "reaxff_set_state_dev": (C.c_int, [vp, vp, vp, vp]),
         "reaxff_get_state_dev": (C.c_int, [vp, vp, vp, vp, vp]),
         "reaxff_step_dev": (C.c_int, [vp, i32, C.c_double, vp, vp]),
+        "reaxff_reset_qeq_history": (None, [vp]),
+        "reaxff_last_qeq_iters": (C.c_int, [vp, ip32, ip32]),
+        "reaxff_profile_enable": (None, [vp, i32]),
+        "reaxff_profile_read": (i32, [vp, i32, dp, ip64]),
+        "reaxff_stage_name": (C.c_char_p, [i32]),
+        "reaxff_probe_fma_gflops": (C.c_double, [C.c_int, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -276,6 +282,31 @@ class ReaxFF:
 
     def last_launch_count(self):
         return int(self.lib.reaxff_last_launch_count(self.h))
+
+    def reset_qeq_history(self):
+        self.lib.reaxff_reset_qeq_history(self.h)
+
+    def last_qeq_iters(self):
+        its = np.empty(self.nrep, np.int32)
+        itt = np.empty(self.nrep, np.int32)
+        self._check(self.lib.reaxff_last_qeq_iters(self.h, its.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                   itt.ctypes.data_as(C.POINTER(C.c_int32))))
+        return its, itt
+
+    def profile_enable(self, on=True):
+        self.lib.reaxff_profile_enable(self.h, 1 if on else 0)
+
+    def profile_read(self):
+        """{stage name: (accumulated ms, timed launches)} from the CUDA-event stage timers."""
+        ms = np.zeros(32)
+        calls = np.zeros(32, np.int64)
+        k = self.lib.reaxff_profile_read(self.h, 32, _dp(ms), calls.ctypes.data_as(C.POINTER(C.c_int64)))
+        return {self.lib.reaxff_stage_name(i).decode(): (float(ms[i]), int(calls[i])) for i in range(k)}
+
+
+def probe_fma_gflops(fp64: bool, iters: int = 0) -> float:
+    """Measured FMA throughput of the current GPU (GFLOP/s) from reaxff_probe_fma_gflops."""
+    return float(load().reaxff_probe_fma_gflops(1 if fp64 else 0, int(iters)))
 
 
 def virial_matrix(w6):
