@@ -61,6 +61,7 @@ struct reaxff_ctx {
   AtomQ aq{};
   Accum acc{};
   rx::QeqState Q{};
+  rx::RedPlan red{};
   double *F_out = nullptr, *E_rep = nullptr, *vir_rep = nullptr, *ke_rep = nullptr, *Etot_dev = nullptr;
   int Etot_cap = 0;
   double *chi_t = nullptr, *eta_t = nullptr, *mass_t = nullptr;
@@ -280,7 +281,7 @@ int qeq_impl(reaxff_ctx* ctx) {
 template <typename R> void terms_impl(reaxff_ctx* ctx) {
   rx::Launch L = launch_of(ctx);
   const DParams<R>* P = params_of<R>(ctx);
-  { Stage st(ctx, 5); rx::bo_correct<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->Pd); }
+  { Stage st(ctx, 5); rx::bo_correct<R>(L, ctx->sys, ctx->bond, ctx->aq, P); }
   { Stage st(ctx, 6); rx::atom_terms<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
   { Stage st(ctx, 7); rx::over_under_bond<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
   { Stage st(ctx, 8); rx::s_gather<R>(L, ctx->sys, ctx->bond, ctx->aq); }
@@ -304,7 +305,7 @@ int zero_accumulators(reaxff_ctx* ctx) {
 }
 
 // lists -> (QEq) -> all terms -> chain rule; energies reduced into E_rep / vir_rep
-int forces_impl(reaxff_ctx* ctx, bool solve_q) {
+int forces_impl(reaxff_ctx* ctx, bool solve_q, bool reduce = true) {
   if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
   int rc = build_lists_impl(ctx);
   if (rc) return rc;
@@ -316,7 +317,10 @@ int forces_impl(reaxff_ctx* ctx, bool solve_q) {
   }
   if (ctx->fp64) terms_impl<double>(ctx);
   else terms_impl<float>(ctx);
-  { Stage st(ctx, 15); rx::reduce_energies(launch_of(ctx), ctx->sys, ctx->acc, ctx->E_rep, ctx->vir_rep); }
+  if (reduce) {
+    Stage st(ctx, 15);
+    rx::reduce_energies(launch_of(ctx), ctx->sys, ctx->acc, ctx->mass_t, ctx->red, ctx->E_rep, ctx->vir_rep, ctx->ke_rep);
+  }
   CK(cudaGetLastError());
   ctx->forces_valid = true;
   return REAXFF_OK;
@@ -494,6 +498,8 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   double** qf[] = {&Q.s, &Q.t, &Q.r_s, &Q.r_t, &Q.p_s, &Q.p_t, &Q.w_s, &Q.w_t, &Q.z_s, &Q.z_t};
   for (double** p : qf) *p = B.alloc<double>(n);
   Q.u_s = Q.u_t = nullptr;
+  Q.zf_s = B.alloc<float>(n);
+  Q.zf_t = B.alloc<float>(n);
   Q.hist_s = B.alloc<double>(4 * (size_t)n);
   Q.hist_t = B.alloc<double>(3 * (size_t)n);
   Q.nhist = 0;
@@ -514,6 +520,20 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   int* rchunk_d = B.alloc<int>(nrep + 1);
   Q.chunk_lo = clo_d; Q.chunk_rep = crep_d; Q.rep_chunk = rchunk_d;
   Q.part = B.alloc<double>((size_t)Q.nchunk * 8);
+  // reduction chunks (<= 4096 atoms each, per replica)
+  std::vector<int> rlo, rrep(nrep + 1, 0);
+  for (int r = 0; r < nrep; ++r) {
+    rrep[r] = (int)rlo.size();
+    for (int64_t i = rep_offsets[r]; i < rep_offsets[r + 1]; i += 4096) rlo.push_back((int)i);
+  }
+  rrep[nrep] = (int)rlo.size();
+  ctx->red.nchunk = (int)rlo.size();
+  rlo.push_back(n);
+  int* rlo_d = B.alloc<int>(rlo.size());
+  int* rrep_d = B.alloc<int>(nrep + 1);
+  ctx->red.chunk_lo = rlo_d;
+  ctx->red.rep_chunk = rrep_d;
+  ctx->red.part = B.alloc<double>((size_t)ctx->red.nchunk * 20);
   Q.red = B.alloc<double>((size_t)nrep * 8);
   Q.scal = B.alloc<double>((size_t)nrep * 16 + 1);
   Q.iters = B.alloc<int>(2 * nrep);
@@ -561,6 +581,8 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   UP(clo_d, clo.data(), clo.size() * sizeof(int));
   UP(crep_d, crep.data(), crep.size() * sizeof(int));
   UP(rchunk_d, rchunk.data(), (nrep + 1) * sizeof(int));
+  UP(rlo_d, rlo.data(), rlo.size() * sizeof(int));
+  UP(rrep_d, rrep.data(), (nrep + 1) * sizeof(int));
   UP(ctx->chi_t, chi, sizeof(chi));
   UP(ctx->eta_t, eta, sizeof(eta));
   UP(ctx->mass_t, mass, sizeof(mass));
@@ -843,11 +865,11 @@ static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev) {
   rx::Launch L = launch_of(ctx);
   for (int st = 0; st < nsteps; ++st) {
     { Stage sg(ctx, 14); rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 1); }
-    if ((rc = forces_impl(ctx, true))) return rc;
-    Stage sg(ctx, 14);
-    rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 0);
+    if ((rc = forces_impl(ctx, true, false))) return rc;
+    { Stage sg(ctx, 14); rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 0); }
+    Stage sg(ctx, 15);
+    rx::reduce_energies(L, ctx->sys, ctx->acc, ctx->mass_t, ctx->red, ctx->E_rep, ctx->vir_rep, ctx->ke_rep);
     if (Etot_dev) {
-      rx::kinetic(L, ctx->sys, ctx->mass_t, ctx->ke_rep);
       rx::etot_combine(L, ctx->nrep, ctx->E_rep, ctx->ke_rep, Etot_dev + (size_t)st * ctx->nrep);
     }
   }

@@ -45,11 +45,10 @@ template <typename R> __device__ __forceinline__ R wbit(unsigned mask, int t) {
 }
 
 // ------------------------------------------------------------------ BO correction
-// The correction factors feed dE/dDelta' (a sum of large, partly cancelling terms per
-// atom), so they are evaluated and stored in FP64 in both precision modes; BO, BO_pi and
-// BO_pp are stored in the path's precision R.
+// Evaluated in the path's precision R from FP64 Delta' and BO'; the factors and their
+// partials are stored in FP64 for the chain rule, BO, BO_pi and BO_pp in R.
 template <typename R>
-__global__ void k_bo_correct(Sys s, BondList bl, AtomQ aq, const DParams<double>* __restrict__ P) {
+__global__ void k_bo_correct(Sys s, BondList bl, AtomQ aq, const DParams<R>* __restrict__ P) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
   const int ti = s.type[i];
@@ -61,46 +60,50 @@ __global__ void k_bo_correct(Sys s, BondList bl, AtomQ aq, const DParams<double>
   double* f1a = (double*)bl.f1; double* foa = (double*)bl.fo; double* fta = (double*)bl.ft;
   double* df1a = (double*)bl.df1; double* dfoba = (double*)bl.dfo_bo; double* dftba = (double*)bl.dft_bo;
   double* dfoda = (double*)bl.dfo_d;
-  const double dpo = aq.dp[i], dpbo = aq.dpboc[i];
+  const R dpo = (R)aq.dp[i], dpbo = (R)aq.dpboc[i];
   for (int k = 0; k < nb; ++k) {
     const int e = i * bl.cap + k;
     const int j = bl.j[e];
     const int tj = s.type[j];
     const int pt = ti * MAXT + tj;
     const bool own_lo = (i < j) || (i == j && bl.s[e] > 13);
-    const double dpt = aq.dp[j], dptb = aq.dpboc[j];
-    const double bp = BOp[e];
-    double f1 = 1.0, df1 = 0.0;
-    if (P->ovc[pt] > 0.0) {
-      const double dlo = own_lo ? dpo : dpt, dhi = own_lo ? dpt : dpo;
-      const double vlo = own_lo ? P->val[ti] : P->val[tj], vhi = own_lo ? P->val[tj] : P->val[ti];
-      const double e1lo = exp(-P->p_boc1 * dlo), e1hi = exp(-P->p_boc1 * dhi);
-      const double f2 = e1lo + e1hi;
-      const double e2lo = exp(-P->p_boc2 * dlo), e2hi = exp(-P->p_boc2 * dhi);
-      const double ssum = e2lo + e2hi;
-      const double f3 = -(1.0 / P->p_boc2) * log(0.5 * ssum);
-      const double dlo_den = vlo + f2 + f3, dhi_den = vhi + f2 + f3;
-      f1 = 0.5 * ((vlo + f2) / dlo_den + (vhi + f2) / dhi_den);
-      const double df2 = -P->p_boc1 * (own_lo ? e1lo : e1hi);
-      const double df3 = (own_lo ? e2lo : e2hi) / ssum;
-      const double dAlo = (f3 * df2 - (vlo + f2) * df3) / (dlo_den * dlo_den);
-      const double dAhi = (f3 * df2 - (vhi + f2) * df3) / (dhi_den * dhi_den);
-      df1 = 0.5 * (dAlo + dAhi);
+    const R dpt = (R)aq.dp[j], dptb = (R)aq.dpboc[j];
+    const R bp = (R)BOp[e];
+    R f1 = 1, df1 = 0;
+    if (P->ovc[pt] > R(0)) {
+      const R dlo = own_lo ? dpo : dpt, dhi = own_lo ? dpt : dpo;
+      const R vlo = own_lo ? P->val[ti] : P->val[tj], vhi = own_lo ? P->val[tj] : P->val[ti];
+      const R e1lo = m_expc(-P->p_boc1 * dlo), e1hi = m_expc(-P->p_boc1 * dhi);
+      const R f2 = e1lo + e1hi;
+      // f3 = -(1/p_boc2) ln((e^a + e^b)/2), a,b = -p_boc2 D'; as a log-sum-exp so that
+      // neither underflow (both exponentials 0) nor overflow reaches the log or df3
+      const R ga = -P->p_boc2 * dlo, gb = -P->p_boc2 * dhi;
+      const R gm = ga > gb ? ga : gb;
+      const R wlo = m_exp(ga - gm), whi = m_exp(gb - gm);
+      const R wsum = wlo + whi;
+      const R f3 = -(R(1) / P->p_boc2) * (gm + m_log(R(0.5) * wsum));
+      const R dlo_den = vlo + f2 + f3, dhi_den = vhi + f2 + f3;
+      f1 = R(0.5) * ((vlo + f2) / dlo_den + (vhi + f2) / dhi_den);
+      const R df2 = -P->p_boc1 * (own_lo ? e1lo : e1hi);
+      const R df3 = (own_lo ? wlo : whi) / wsum;
+      const R dAlo = (f3 * df2 - (vlo + f2) * df3) / (dlo_den * dlo_den);
+      const R dAhi = (f3 * df2 - (vhi + f2) * df3) / (dhi_den * dhi_den);
+      df1 = R(0.5) * (dAlo + dAhi);
     }
-    double fo = 1.0, ft = 1.0, dfo_bo = 0.0, dft_bo = 0.0, dfo_d = 0.0;
-    if (P->v13[pt] > 0.0) {
-      const double p3 = P->p_boc3[pt], p4 = P->p_boc4[pt], p5 = P->p_boc5[pt];
-      double sdo, sdt;
-      sig_pair<double>(-p3 * (p4 * bp * bp - dpbo) + p5, fo, sdo);
-      sig_pair<double>(-p3 * (p4 * bp * bp - dptb) + p5, ft, sdt);
-      dfo_bo = 2.0 * p3 * p4 * bp * sdo;
-      dft_bo = 2.0 * p3 * p4 * bp * sdt;
+    R fo = 1, ft = 1, dfo_bo = 0, dft_bo = 0, dfo_d = 0;
+    if (P->v13[pt] > R(0)) {
+      const R p3 = P->p_boc3[pt], p4 = P->p_boc4[pt], p5 = P->p_boc5[pt];
+      R sdo, sdt;
+      sig_pair<R>(-p3 * (p4 * bp * bp - dpbo) + p5, fo, sdo);
+      sig_pair<R>(-p3 * (p4 * bp * bp - dptb) + p5, ft, sdt);
+      dfo_bo = R(2) * p3 * p4 * bp * sdo;
+      dft_bo = R(2) * p3 * p4 * bp * sdt;
       dfo_d = -p3 * sdo;
     }
     const double flo = own_lo ? fo : ft, fhi = own_lo ? ft : fo;
-    const double F = f1 * flo * fhi;
-    const double G = f1 * f1 * flo * fhi;
-    bo[e] = (R)(bp * F);
+    const double F = (double)f1 * flo * fhi;
+    const double G = (double)f1 * f1 * flo * fhi;
+    bo[e] = (R)(BOp[e] * F);
     bo_pi[e] = (R)(BOpi[e] * G);
     bo_pp[e] = (R)(BOpp[e] * G);
     f1a[e] = f1; foa[e] = fo; fta[e] = ft; df1a[e] = df1;
@@ -694,7 +697,7 @@ __global__ void k_hbonds(Sys s, BondList bl, HbList hl, Accum acc, const DParams
 
 namespace rx {
 
-template <typename R> void bo_correct(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<double>* P) {
+template <typename R> void bo_correct(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<R>* P) {
   k_bo_correct<R><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a, P);
   *L.count += 1;
 }
@@ -729,7 +732,7 @@ void hbonds(const Launch& L, Sys s, BondList b, HbList h, Accum acc, const DPara
 }
 
 #define INST(R)                                                                                           \
-  template void bo_correct<R>(const Launch&, Sys, BondList, AtomQ, const DParams<double>*);               \
+  template void bo_correct<R>(const Launch&, Sys, BondList, AtomQ, const DParams<R>*);                    \
   template void atom_terms<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned);   \
   template void over_under_bond<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned); \
   template void s_gather<R>(const Launch&, Sys, BondList, AtomQ);                                         \

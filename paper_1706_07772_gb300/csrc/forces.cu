@@ -102,13 +102,21 @@ __global__ void k_finalize(Sys s, double* F) {
   F[3 * i + 2] = fix_get(s.fz + i);
 }
 
-// block (r, q): sum over replica r's atoms of e[q] (q < NTERMS) or vir[q - NTERMS]
-__global__ void k_reduce(Sys s, Accum acc, double* E_rep, double* vir_rep) {
-  const int r = blockIdx.x, q = blockIdx.y;
-  const double* src = q < NTERMS ? acc.e + (size_t)q * s.n : acc.vir + (size_t)(q - NTERMS) * s.n;
-  const int64_t lo = s.rep_off[r], hi = s.rep_off[r + 1];
+// Per-replica sums of the 13 energy terms, 6 virial components and the kinetic energy
+// (NQ_RED quantities): pass 1, block (chunk, q) sums one chunk of <= RED_CHUNK atoms of one
+// replica; pass 2, one warp per (replica, q) sums that replica's chunk partials in order.
+// Both passes have a fixed reduction order, so the sums are bitwise reproducible.
+constexpr int NQ_RED = NTERMS + 7;
+__device__ __forceinline__ double red_value(const Sys& s, const Accum& acc, const double* mass_t, int q, int64_t i) {
+  if (q < NTERMS) return acc.e[(size_t)q * s.n + i];
+  if (q < NTERMS + 6) return acc.vir[(size_t)(q - NTERMS) * s.n + i];
+  const double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
+  return 0.5 * mass_t[s.type[i]] * (vx * vx + vy * vy + vz * vz) / 4.184e-4;
+}
+__global__ void k_reduce1(Sys s, Accum acc, const double* mass_t, const int* chunk_lo, double* part) {
+  const int c = blockIdx.x, q = blockIdx.y;
   double v = 0.0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v += src[i];
+  for (int64_t i = chunk_lo[c] + threadIdx.x; i < chunk_lo[c + 1]; i += blockDim.x) v += red_value(s, acc, mass_t, q, i);
   __shared__ double sh[32];
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
@@ -116,9 +124,23 @@ __global__ void k_reduce(Sys s, Accum acc, double* E_rep, double* vir_rep) {
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    if (!isfinite(t)) atomicOr(s.err, ERR_NAN);
-    if (q < NTERMS) E_rep[r * NTERMS + q] = t;
-    else vir_rep[r * 6 + (q - NTERMS)] = t;
+    part[(size_t)c * NQ_RED + q] = t;
+  }
+}
+__global__ void k_reduce2(Sys s, const int* rep_chunk, const double* part, double* E_rep, double* vir_rep, double* ke_rep,
+                          double* etot) {
+  const int pq = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (pq >= s.nrep * NQ_RED) return;
+  const int r = pq / NQ_RED, q = pq % NQ_RED;
+  double v = 0.0;
+  for (int c = rep_chunk[r] + lane; c < rep_chunk[r + 1]; c += 32) v += part[(size_t)c * NQ_RED + q];
+  v = warp_sum(v);
+  if (lane == 0) {
+    if (!isfinite(v)) atomicOr(s.err, ERR_NAN);
+    if (q < NTERMS) E_rep[r * NTERMS + q] = v;
+    else if (q < NTERMS + 6) vir_rep[r * 6 + (q - NTERMS)] = v;
+    else ke_rep[r] = v;
   }
 }
 
@@ -139,23 +161,6 @@ __global__ void k_kick_drift(Sys s, const double* mass_t, double dt, int drift) 
     }
     if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) atomicOr(s.err, ERR_NAN);
     s.x[i] = p[0]; s.y[i] = p[1]; s.z[i] = p[2];
-  }
-}
-
-__global__ void k_kinetic(Sys s, const double* mass_t, double* ke_rep) {
-  const int r = blockIdx.x;
-  const int64_t lo = s.rep_off[r], hi = s.rep_off[r + 1];
-  double v = 0.0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
-    v += mass_t[s.type[i]] * (s.vx[i] * s.vx[i] + s.vy[i] * s.vy[i] + s.vz[i] * s.vz[i]);
-  __shared__ double sh[32];
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    ke_rep[r] = 0.5 * t / 4.184e-4;
   }
 }
 
@@ -186,16 +191,16 @@ void finalize_forces(const Launch& L, Sys s, double* F) {
   k_finalize<<<grid_for(s.n, 256), 256, 0, L.st>>>(s, F);
   *L.count += 1;
 }
-void reduce_energies(const Launch& L, Sys s, Accum acc, double* E_rep, double* vir_rep) {
-  k_reduce<<<dim3(s.nrep, NTERMS + 6), 256, 0, L.st>>>(s, acc, E_rep, vir_rep);
-  *L.count += 1;
+void reduce_energies(const Launch& L, Sys s, Accum acc, const double* mass_t, const RedPlan& rp, double* E_rep,
+                     double* vir_rep, double* ke_rep) {
+  k_reduce1<<<dim3(rp.nchunk, NQ_RED), 256, 0, L.st>>>(s, acc, mass_t, rp.chunk_lo, rp.part);
+  const int warps = s.nrep * NQ_RED;
+  k_reduce2<<<(warps + 7) / 8, 256, 0, L.st>>>(s, rp.rep_chunk, rp.part, E_rep, vir_rep, ke_rep, nullptr);
+  *L.count += 2;
 }
 void verlet_kick_drift(const Launch& L, Sys s, const double* mass_t, double dt, int drift) {
   k_kick_drift<<<grid_for(s.n, 256), 256, 0, L.st>>>(s, mass_t, dt, drift);
   *L.count += 1;
 }
-void kinetic(const Launch& L, Sys s, const double* mass_t, double* ke_rep) {
-  k_kinetic<<<s.nrep, 256, 0, L.st>>>(s, mass_t, ke_rep);
-  *L.count += 1;
-}
+
 }  // namespace rx

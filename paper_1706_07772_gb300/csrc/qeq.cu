@@ -36,6 +36,7 @@ struct CG {
   int cap;
   const double *eta, *chi;                 // per type (double)
   double *xs, *xt, *rs, *rt, *zs, *zt, *ps, *pt, *ws, *wt;
+  float *zsf, *ztf;                        // FP32 copies of z for the FP32-arithmetic SpMV
   double* q;
   double* part;                            // [nchunk*NQ]
   double* red;                             // [nrep*NQ]
@@ -121,18 +122,34 @@ __device__ __forceinline__ void block_partials(double* vals, double* part, int c
   __syncthreads();
 }
 
-// (H v)_i for the two systems, warp per row
+// (H v)_i for the two systems, warp per row. FP64 path: FP64 products and sums. Mixed
+// path: H and v in FP32, FP32 products and per-lane partial sums (about 13 terms per
+// lane), lanes combined in FP64 -- FP64 work per row drops from 2 per entry to ~10.
 template <typename R>
-__device__ __forceinline__ void spmv_row(const CG<R>& a, int i, const double* vs, const double* vt, double& hs,
-                                         double& ht) {
+__device__ __forceinline__ void spmv_row(const CG<R>& a, int i, const double* vs, const double* vt, const float* vsf,
+                                         const float* vtf, double& hs, double& ht) {
   const int lane = threadIdx.x & 31;
   const int row = i * a.cap, nf = a.cnt[i];
-  double s1 = 0.0, t1 = 0.0;
-  for (int k = lane; k < nf; k += 32) {
-    const int j = a.col[row + k];
-    const double h = (double)a.H[row + k];
-    s1 += h * __ldcg(&vs[j]);
-    t1 += h * __ldcg(&vt[j]);
+  double s1, t1;
+  if (sizeof(R) == 4) {
+    float sf = 0.0f, tf = 0.0f;
+    for (int k = lane; k < nf; k += 32) {
+      const int j = a.col[row + k];
+      const float h = (float)a.H[row + k];
+      sf = fmaf(h, __ldcg(&vsf[j]), sf);
+      tf = fmaf(h, __ldcg(&vtf[j]), tf);
+    }
+    s1 = (double)sf;
+    t1 = (double)tf;
+  } else {
+    s1 = 0.0;
+    t1 = 0.0;
+    for (int k = lane; k < nf; k += 32) {
+      const int j = a.col[row + k];
+      const double h = (double)a.H[row + k];
+      s1 += h * __ldcg(&vs[j]);
+      t1 += h * __ldcg(&vt[j]);
+    }
   }
   s1 = warp_sum(s1);
   t1 = warp_sum(t1);
@@ -148,12 +165,19 @@ __global__ void __launch_bounds__(256) k_cg(CG<R> a) {
   double* red = a.red;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* S = a.scal;
-  // ---------------- init: r = b - H x, z = r/eta, p = w = 0
+  // ---------------- init: r = b - H x, z = r/eta, p = w = 0 (x copied to FP32 first)
+  for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x)
+    for (int i = a.chunk_lo[c] + threadIdx.x; i < a.chunk_lo[c + 1]; i += blockDim.x) {
+      a.zsf[i] = (float)a.xs[i];
+      a.ztf[i] = (float)a.xt[i];
+    }
+  bool ok0 = barrier_reduce(a.bar, a.err, []() {});
+  if (!ok0) return;
   for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x) {
     double v[NQ] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int i = a.chunk_lo[c] + wid; i < a.chunk_lo[c + 1]; i += nw) {
       double hs, ht;
-      spmv_row(a, i, a.xs, a.xt, hs, ht);
+      spmv_row(a, i, a.xs, a.xt, a.zsf, a.ztf, hs, ht);
       if (lane == 0) {
         const double bs = -a.chi[a.type[i]], bt = -1.0, e = a.eta[a.type[i]];
         const double rs = bs - hs, rt = bt - ht;
@@ -186,6 +210,16 @@ __global__ void __launch_bounds__(256) k_cg(CG<R> a) {
       S[a.nrep * NS] = act;
     }
   });
+  // z in FP32 for the first iteration's SpMV: written only after every block has finished
+  // the initial SpMV (which read x from the same buffer), published by one more barrier
+  if (ok) {
+    for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x)
+      for (int i = a.chunk_lo[c] + threadIdx.x; i < a.chunk_lo[c + 1]; i += blockDim.x) {
+        a.zsf[i] = (float)a.zs[i];
+        a.ztf[i] = (float)a.zt[i];
+      }
+    ok = barrier_reduce(a.bar, a.err, []() {});
+  }
   int it = 0;
   while (ok && ldS(&S[a.nrep * NS]) > 0.0 && it < a.max_iter) {
     ++it;
@@ -197,7 +231,7 @@ __global__ void __launch_bounds__(256) k_cg(CG<R> a) {
       double v[NQ] = {0, 0, 0, 0, 0, 0, 0, 0};
       for (int i = a.chunk_lo[c] + wid; i < a.chunk_lo[c + 1]; i += nw) {
         double us, ut;
-        spmv_row(a, i, a.zs, a.zt, us, ut);
+        spmv_row(a, i, a.zs, a.zt, a.zsf, a.ztf, us, ut);
         if (lane == 0) {
           if (as) {
             const double p = a.zs[i] + bes * a.ps[i], w = us + bes * a.ws[i];
@@ -231,14 +265,16 @@ __global__ void __launch_bounds__(256) k_cg(CG<R> a) {
         if (as) {
           a.xs[i] += als * a.ps[i];
           const double r = a.rs[i] - als * a.ws[i];
-          a.rs[i] = r; a.zs[i] = r / e;
-          v[0] += r * r / e; v[2] += r * r;
+          const double z = r / e;
+          a.rs[i] = r; a.zs[i] = z; a.zsf[i] = (float)z;
+          v[0] += r * z; v[2] += r * r;
         }
         if (at) {
           a.xt[i] += alt * a.pt[i];
           const double r = a.rt[i] - alt * a.wt[i];
-          a.rt[i] = r; a.zt[i] = r / e;
-          v[1] += r * r / e; v[3] += r * r;
+          const double z = r / e;
+          a.rt[i] = r; a.zt[i] = z; a.ztf[i] = (float)z;
+          v[1] += r * z; v[3] += r * r;
         }
       }
       block_partials(v, a.part, c);
@@ -331,6 +367,7 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   a.eta = eta; a.chi = chi;
   a.xs = Q.s; a.xt = Q.t; a.rs = Q.r_s; a.rt = Q.r_t; a.zs = Q.z_s; a.zt = Q.z_t;
   a.ps = Q.p_s; a.pt = Q.p_t; a.ws = Q.w_s; a.wt = Q.w_t;
+  a.zsf = Q.zf_s; a.ztf = Q.zf_t;
   a.q = s.q; a.part = Q.part; a.red = Q.red; a.scal = Q.scal;
   a.chunk_lo = Q.chunk_lo; a.chunk_rep = Q.chunk_rep; a.rep_chunk = Q.rep_chunk;
   a.iters = Q.iters; a.bar = Q.bar; a.err = s.err;

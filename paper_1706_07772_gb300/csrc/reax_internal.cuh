@@ -338,7 +338,7 @@ void bond_mirror(const Launch& L, Sys s, BondList b);
 void bo_prime64(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<double>* Pd, int n_canon_max);
 // bonded.cu
 template <typename R>
-void bo_correct(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<double>* P);
+void bo_correct(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<R>* P);
 template <typename R>
 void atom_terms(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P,
                 unsigned mask);
@@ -362,9 +362,15 @@ void nonbonded(const Launch& L, Sys s, FarList f, Accum acc, const DParams<R>* P
 template <typename R>
 void chain_rule(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc);
 void finalize_forces(const Launch& L, Sys s, double* F);
-void reduce_energies(const Launch& L, Sys s, Accum acc, double* E_rep, double* vir_rep);
+struct RedPlan {                // chunks (<= 4096 atoms, never straddling replicas) for reductions
+  int nchunk;
+  int* chunk_lo;               // [nchunk+1]
+  int* rep_chunk;              // [nrep+1]
+  double* part;                // [nchunk*20]
+};
+void reduce_energies(const Launch& L, Sys s, Accum acc, const double* mass_t, const RedPlan& rp, double* E_rep,
+                     double* vir_rep, double* ke_rep);
 void verlet_kick_drift(const Launch& L, Sys s, const double* mass_t, double dt, int drift);
-void kinetic(const Launch& L, Sys s, const double* mass_t, double* ke_rep);
 void etot_combine(const Launch& L, int nrep, const double* E_rep, const double* ke, double* out);
 // qeq.cu
 struct QeqState {
@@ -372,6 +378,7 @@ struct QeqState {
   double *hist_s, *hist_t;     // [4*n] previous solutions (ring)
   int nhist, hist_pos;
   double *r_s, *r_t, *p_s, *p_t, *w_s, *w_t, *z_s, *z_t, *u_s, *u_t;
+  float *zf_s, *zf_t;          // FP32 copies of z (mixed-path SpMV)
   double* part;                // chunk partials
   double* red;                 // per-replica reductions
   double* scal;                // per-replica scalars
