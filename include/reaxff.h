@@ -213,6 +213,36 @@ int reaxff_get_state_dev(reaxff_ctx* ctx, double* x_dev, double* v_dev, double* 
  * E_tot_dev: double[nsteps*nrep] on the device, or NULL. */
 int reaxff_step_dev(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot_dev, void* stream);
 
+/* ---- allocation-free far-list builder ----------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory while they run: applications that hand out all GPU memory
+ * from their own pool and forbid runtime allocation, latency-bound loops where the
+ * device-wide synchronisation of cudaMalloc/cudaFree would stall other work, and
+ * plug-ins whose host framework must account for every allocation. It builds the same
+ * cell-binned far-neighbour list and QEq H entries as reaxff_build_lists (FP64 path)
+ * for one periodic system, without a context and without allocating: its scratch (cell
+ * grid, FP32 position copies, sorted atoms, parameter block; about 2.9 MB) is one
+ * file-scope __device__ array that every GPU loading the library keeps until exit.
+ *
+ * Limits: n <= 65536 atoms and at most 16384 cells (cell edge >= r_nb); larger inputs
+ * are rejected with REAXFF_E_INVALID. Inputs (device pointers): types int32[n],
+ * positions x, y, z double[n] each (already wrapped into [0, L)). Outputs (device
+ * pointers, caller-allocated): cnt int32[n] (entries per row, at most cap),
+ * j int32[n*cap] and shift uint8[n*cap] (image code (sx+1)*9 + (sy+1)*3 + (sz+1)) and
+ * H double[n*cap], row i at [i*cap, i*cap + cnt[i]). Returns REAXFF_E_CAPACITY when a
+ * row had more than cap neighbours (that row is truncated). params/options and box are
+ * host pointers. Work is enqueued on `stream`; the call waits for it to finish.
+ * *err_msg (if not NULL) receives a static description of any error.
+ * The first call on each device looks up the scratch array's device address (once per
+ * device, with that device current); make that first call before any stream capture.
+ * All calls share the one scratch array and each call clears what must start at zero;
+ * calls that overlap on the GPU (several streams or host threads) race on it. */
+int reaxff_far_list_noalloc(const reaxff_params* params, const reaxff_options* options,
+                            const int32_t* types_dev, const double* x_dev, const double* y_dev,
+                            const double* z_dev, int64_t n, const double box[3], int32_t cap,
+                            int32_t* cnt_dev, int32_t* j_dev, uint8_t* shift_dev, double* H_dev,
+                            void* stream, const char** err_msg);
+
 #ifdef __cplusplus
 }
 #endif

@@ -133,6 +133,15 @@ template <typename R> void fill_params(DParams<R>& d, const reaxff_params& p, co
 
 int round_up(double v, int m) { return (int)((std::ceil(v) + m - 1) / m) * m; }
 
+}  // namespace
+
+// parameter tables in FP64 device layout (used by the allocation-free list builder)
+void rx_fill_params_double(DParams<double>& d, const reaxff_params& p, const reaxff_options& o) {
+  fill_params<double>(d, p, o);
+}
+
+namespace {
+
 // allocate the three lists at the current capacities
 int alloc_lists(reaxff_ctx* ctx) {
   ctx->lists.free_all();
