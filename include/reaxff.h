@@ -111,6 +111,10 @@ typedef struct {
   int32_t warm_start; /* REAXFF_WARM_* */
   int32_t term_mask;  /* bit t set = energy term t contributes to forces (0 = all) */
   double capacity_margin; /* list capacity headroom factor (>= 1; 0 = default 1.35) */
+  double skin;        /* Verlet skin (A) of the neighbour candidate list, rebuilt on the device
+                         only when an atom has moved more than skin/2; the far list is still
+                         filtered exactly (r < r_nb) every step. 0 = default 1.0 A,
+                         negative = no candidate list (cell stencil every step). */
 } reaxff_options;
 
 typedef struct reaxff_ctx reaxff_ctx;

@@ -66,7 +66,11 @@ struct reaxff_ctx {
   int Etot_cap = 0;
   double *chi_t = nullptr, *eta_t = nullptr, *mass_t = nullptr;
   int* h_err_pinned = nullptr;
-  int cap_far = 0, cap_bond = 0, cap_hb = 0;
+  int cap_far = 0, cap_bond = 0, cap_hb = 0, cap_near = 0, cap_cand = 0;
+  float near_margin = 0.f;
+  bool use_skin = true;
+  double skin = 1.0;
+  CandList cand{};
   // per-stage CUDA-event timing (reaxff_profile_*)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -154,6 +158,13 @@ int alloc_lists(reaxff_ctx* ctx) {
   f.j = B.alloc<int>(n * f.cap);
   f.s = B.alloc<uint8_t>(n * f.cap);
   f.H = B.alloc_bytes(n * f.cap * rs);
+  f.capn = ctx->cap_near;
+  f.cntn = B.alloc<int>(n);
+  f.jn = B.alloc<int>(n * f.capn);
+  f.sn = B.alloc<uint8_t>(n * f.capn);
+  f.Hn = B.alloc_bytes(n * f.capn * rs);
+  f.r2_nb = ctx->ho.r_nb * ctx->ho.r_nb;
+  f.r2_bond = ctx->ho.r_bond * ctx->ho.r_bond;
   BondList& b = ctx->bond;
   b.cap = ctx->cap_bond;
   const size_t nb = n * b.cap;
@@ -175,6 +186,11 @@ int alloc_lists(reaxff_ctx* ctx) {
   b.cdbo = B.alloc<unsigned long long>(nb);
   b.cdbopi = B.alloc<unsigned long long>(nb);
   b.cdbopp = B.alloc<unsigned long long>(nb);
+  CandList& cl = ctx->cand;
+  cl.cap = ctx->cap_cand;
+  cl.cnt = B.alloc<int>(n);
+  cl.j = B.alloc<int>(n * (size_t)cl.cap);
+  cl.s = B.alloc<uint8_t>(n * (size_t)cl.cap);
   HbList& h = ctx->hb;
   h.cap = ctx->cap_hb;
   h.cnt = B.alloc<int>(n);
@@ -239,13 +255,29 @@ int build_lists_impl(reaxff_ctx* ctx) {
     rx::Launch L = launch_of(ctx);
     CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
     CK(cudaMemsetAsync(ctx->bond.ncanon, 0, sizeof(int), ctx->st));
+    if (ctx->use_skin) {
+      // Verlet-skin candidates (rebuilt on the device only when an atom moved > skin/2),
+      // filtered exactly every step into the near/far rows
+      { Stage st(ctx, 0);
+        rx::positions_f32(L, ctx->sys);
+        rx::skin_check(L, ctx->sys, ctx->cand);
+        rx::cand_build(L, ctx->sys, ctx->cells, ctx->cand); }
+      if (ctx->fp64) {
+        { Stage st(ctx, 1); rx::cand_filter<double>(L, ctx->sys, ctx->cand, ctx->far, ctx->Pd, ctx->far_margin, ctx->near_margin); }
+        { Stage st(ctx, 2); rx::bond_list<double>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pd, ctx->Pd); }
+      } else {
+        { Stage st(ctx, 1); rx::cand_filter<float>(L, ctx->sys, ctx->cand, ctx->far, ctx->Pf, ctx->far_margin, ctx->near_margin); }
+        { Stage st(ctx, 2); rx::bond_list<float>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pf, ctx->Pd); }
+      }
+    } else {
     { Stage st(ctx, 0); rx::cells_build(L, ctx->sys, ctx->cells); }
     if (ctx->fp64) {
-      { Stage st(ctx, 1); rx::far_list<double>(L, ctx->sys, ctx->cells, ctx->far, ctx->Pd, ctx->far_margin); }
+      { Stage st(ctx, 1); rx::far_list_split<double>(L, ctx->sys, ctx->cells, ctx->far, ctx->Pd, ctx->far_margin, ctx->near_margin); }
       { Stage st(ctx, 2); rx::bond_list<double>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pd, ctx->Pd); }
     } else {
-      { Stage st(ctx, 1); rx::far_list<float>(L, ctx->sys, ctx->cells, ctx->far, ctx->Pf, ctx->far_margin); }
+      { Stage st(ctx, 1); rx::far_list_split<float>(L, ctx->sys, ctx->cells, ctx->far, ctx->Pf, ctx->far_margin, ctx->near_margin); }
       { Stage st(ctx, 2); rx::bond_list<float>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pf, ctx->Pd); }
+    }
     }
     { Stage st(ctx, 2); rx::bond_mirror(L, ctx->sys, ctx->bond); }
     { Stage st(ctx, 3); rx::bo_prime64(L, ctx->sys, ctx->bond, ctx->aq, ctx->Pd, ctx->n * ctx->bond.cap); }
@@ -254,16 +286,19 @@ int build_lists_impl(reaxff_ctx* ctx) {
     int rc = read_err(ctx, &flags);
     if (rc) return rc;
     if (flags & ERR_NAN) return fail(ctx, REAXFF_E_NAN, "non-finite value while building lists");
-    if (!(flags & (ERR_CAP_FAR | ERR_CAP_BOND | ERR_CAP_HB))) {
+    if (!(flags & (ERR_CAP_FAR | ERR_CAP_BOND | ERR_CAP_HB | ERR_CAP_NEAR | ERR_CAP_CAND))) {
       ctx->lists_valid = true;
       return REAXFF_OK;
     }
     if (attempt == 2) break;
     if (flags & ERR_CAP_FAR) ctx->cap_far = round_up(ctx->cap_far * 1.5, 32);
+    if (flags & ERR_CAP_NEAR) ctx->cap_near = round_up(ctx->cap_near * 1.5, 32);
+    if (flags & ERR_CAP_CAND) ctx->cap_cand = round_up(ctx->cap_cand * 1.5, 32);
     if (flags & ERR_CAP_BOND) ctx->cap_bond = round_up(ctx->cap_bond * 1.5, 8);
     if (flags & ERR_CAP_HB) ctx->cap_hb = round_up(ctx->cap_hb * 1.5, 32);
     int r2 = alloc_lists(ctx);
     if (r2) return r2;
+    CK(cudaMemsetAsync(ctx->sys.rebuild, 1, sizeof(int), ctx->st));   // candidates were reallocated
   }
   return fail(ctx, REAXFF_E_CAPACITY, "neighbour list capacity exceeded after regrow");
 }
@@ -341,7 +376,7 @@ int check_flags(reaxff_ctx* ctx, bool allow_nc) {
   if (rc) return rc;
   if (flags & ERR_TIMEOUT) return fail(ctx, REAXFF_E_TIMEOUT, "a device-side wait hit its spin limit");
   if (flags & ERR_NAN) return fail(ctx, REAXFF_E_NAN, "non-finite or out-of-range value in forces/energies");
-  if (flags & (ERR_CAP_FAR | ERR_CAP_BOND | ERR_CAP_HB))
+  if (flags & (ERR_CAP_FAR | ERR_CAP_BOND | ERR_CAP_HB | ERR_CAP_NEAR | ERR_CAP_CAND))
     return fail(ctx, REAXFF_E_CAPACITY, "list capacity exceeded");
   if ((flags & ERR_CG) && !allow_nc) return fail(ctx, REAXFF_E_NOT_CONVERGED, "QEq reached qeq_max_iter");
   if (flags & ERR_CG) {
@@ -360,6 +395,7 @@ int validate(const reaxff_params* p, const reaxff_options* o, std::string& msg) 
   if (!(o->bo_cut > 0 && o->qeq_tol > 0 && o->qeq_max_iter > 0)) { msg = "bo_cut, qeq_tol, qeq_max_iter must be > 0"; return REAXFF_E_INVALID; }
   if (o->precision != REAXFF_FP64 && o->precision != REAXFF_MIXED) { msg = "unknown precision"; return REAXFF_E_INVALID; }
   if (o->warm_start < 0 || o->warm_start > REAXFF_WARM_MLP) { msg = "unknown warm_start"; return REAXFF_E_INVALID; }
+  if (!std::isfinite(o->skin) || o->skin > 5.0) { msg = "skin must be finite and <= 5 A"; return REAXFF_E_INVALID; }
   for (int a = 0; a < p->ntypes; ++a)
     if (!(p->mass[a] > 0 && p->eta[a] > 0)) { msg = "mass and eta must be > 0"; return REAXFF_E_INVALID; }
   return REAXFF_OK;
@@ -443,11 +479,21 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   }
   const double margin = options->capacity_margin >= 1.0 ? options->capacity_margin : 1.35;
   const double sph = 4.0 / 3.0 * M_PI;
-  ctx->cap_far = std::max(64, round_up(margin * sph * std::pow(options->r_nb, 3) * rho + 16, 32));
+  ctx->cap_far = std::max(64, round_up(margin * sph * (std::pow(options->r_nb, 3) - std::pow(options->r_bond, 3)) * rho + 16, 32));
+  ctx->cap_near = std::max(32, round_up(margin * sph * std::pow(options->r_bond, 3) * rho + 16, 32));
+  ctx->use_skin = !(options->skin < 0.0);
+  ctx->skin = options->skin > 0.0 ? options->skin : 1.0;
+  ctx->cap_cand = std::max(64, round_up(margin * sph * std::pow(options->r_nb + ctx->skin, 3) * rho + 16, 32));
   ctx->cap_bond = 24;
   ctx->cap_hb = std::max(32, round_up(margin * sph * std::pow(options->r_hb, 3) * rho + 16, 32));
   const double u = std::ldexp(1.0, -24);
   ctx->far_margin = (float)(32.0 * u * (lmax * options->r_nb + options->r_nb * options->r_nb));
+  ctx->near_margin = (float)(32.0 * u * (lmax * options->r_bond + options->r_bond * options->r_bond));
+  {
+    const double rc = options->r_nb + ctx->skin;
+    ctx->cand.rc2 = (float)(rc * rc + 64.0 * u * (lmax * rc + rc * rc));
+    ctx->cand.half_skin2 = 0.25 * ctx->skin * ctx->skin;
+  }
   // ---- cells per replica
   std::vector<int> nc(3 * nrep), cell_off(nrep + 1, 0);
   for (int r = 0; r < nrep; ++r) {
@@ -480,7 +526,11 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   unsigned long long* facc = B.alloc<unsigned long long>(3 * (size_t)n);
   s.fx = facc; s.fy = facc ? facc + n : nullptr; s.fz = facc ? facc + 2 * (size_t)n : nullptr;
   s.q = B.alloc<double>(n);
+  s.qf = B.alloc<float>(n);
   s.err = B.alloc<int>(1);
+  s.img = B.alloc<int>(3 * (size_t)n);
+  s.xb = B.alloc<double>(3 * (size_t)n);
+  s.rebuild = B.alloc<int>(1);
   Cells& c = ctx->cells;
   int* nc_d = B.alloc<int>(3 * nrep);
   int* coff_d = B.alloc<int>(nrep + 1);
@@ -501,6 +551,8 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   ctx->chi_t = B.alloc<double>(MAXT);
   ctx->eta_t = B.alloc<double>(MAXT);
   ctx->mass_t = B.alloc<double>(MAXT);
+  double* ieta_d = B.alloc<double>(MAXT);
+  ctx->Q.ieta = ieta_d;
   // ---- QEq state and chunking (chunks never straddle replicas)
   rx::QeqState& Q = ctx->Q;
   Q.grid = rx::qeq_grid_size(ctx->nsm);
@@ -573,8 +625,11 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
     bh[k] = (float)boxes[k];
     bl[k] = (float)(boxes[k] - (double)bh[k]);
   }
-  double chi[MAXT], eta[MAXT], mass[MAXT];
-  for (int t = 0; t < MAXT; ++t) { chi[t] = params->chi[t]; eta[t] = params->eta[t]; mass[t] = params->mass[t]; }
+  double chi[MAXT], eta[MAXT], mass[MAXT], ieta[MAXT];
+  for (int t = 0; t < MAXT; ++t) {
+    chi[t] = params->chi[t]; eta[t] = params->eta[t]; mass[t] = params->mass[t];
+    ieta[t] = params->eta[t] > 0 ? 1.0 / params->eta[t] : 0.0;
+  }
   cudaError_t e = cudaSuccess;
 #define UP(dst, src, bytes) if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice)
   UP(ctx->Pd, &hd, sizeof(hd));
@@ -595,11 +650,15 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   UP(ctx->chi_t, chi, sizeof(chi));
   UP(ctx->eta_t, eta, sizeof(eta));
   UP(ctx->mass_t, mass, sizeof(mass));
+  UP(ieta_d, ieta, sizeof(ieta));
 #undef UP
   if (e == cudaSuccess) e = cudaMemset(s.vx, 0, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(s.vy, 0, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(s.vz, 0, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(s.q, 0, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(s.qf, 0, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s.img, 0, 3 * (size_t)n * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(s.rebuild, 1, sizeof(int));
   if (e != cudaSuccess) {
     B.free_all();
     delete ctx;
@@ -673,6 +732,8 @@ static int set_state_common(reaxff_ctx* ctx, const double* x, const double* v, c
   CK(cudaMemcpyAsync(ctx->sys.vx, vsoa.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->sys.vy, vsoa.data() + n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->sys.vz, vsoa.data() + 2 * (size_t)n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(ctx->sys.img, 0, 3 * (size_t)n * sizeof(int), ctx->st));
+  CK(cudaMemsetAsync(ctx->sys.rebuild, 1, sizeof(int), ctx->st));     // new positions: rebuild candidates
   CK(cudaStreamSynchronize(ctx->st));
   ctx->have_pos = true;
   ctx->forces_valid = false;
@@ -747,38 +808,50 @@ int reaxff_get_lists(reaxff_ctx* ctx, int32_t which, int64_t capacity, int64_t* 
   if (!ctx || !count) return REAXFF_E_INVALID;
   if (!ctx->lists_valid) return fail(ctx, REAXFF_E_STATE, "lists not built");
   const int n = ctx->n;
-  int cap;
-  const int *cnt_d, *j_d;
-  const uint8_t* s_d;
-  if (which == REAXFF_LIST_FAR) { cap = ctx->far.cap; cnt_d = ctx->far.cnt; j_d = ctx->far.j; s_d = ctx->far.s; }
-  else if (which == REAXFF_LIST_BOND) { cap = ctx->bond.cap; cnt_d = ctx->bond.cnt; j_d = ctx->bond.j; s_d = ctx->bond.s; }
-  else if (which == REAXFF_LIST_HBOND) { cap = ctx->hb.cap; cnt_d = ctx->hb.cnt; j_d = ctx->hb.j; s_d = ctx->hb.s; }
-  else return fail(ctx, REAXFF_E_INVALID, "unknown list");
-  std::vector<int> cnt(n);
-  CK(cudaMemcpyAsync(cnt.data(), cnt_d, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
+  struct Part { int cap; const int* cnt; const int* j; const uint8_t* s; };
+  std::vector<Part> parts;
+  if (which == REAXFF_LIST_FAR) {
+    parts.push_back({ctx->far.capn, ctx->far.cntn, ctx->far.jn, ctx->far.sn});
+    parts.push_back({ctx->far.cap, ctx->far.cnt, ctx->far.j, ctx->far.s});
+  } else if (which == REAXFF_LIST_BOND) {
+    parts.push_back({ctx->bond.cap, ctx->bond.cnt, ctx->bond.j, ctx->bond.s});
+  } else if (which == REAXFF_LIST_HBOND) {
+    parts.push_back({ctx->hb.cap, ctx->hb.cnt, ctx->hb.j, ctx->hb.s});
+  } else {
+    return fail(ctx, REAXFF_E_INVALID, "unknown list");
+  }
+  std::vector<std::vector<int>> cnts(parts.size(), std::vector<int>(n));
   int64_t tot = 0;
-  for (int i = 0; i < n; ++i) tot += cnt[i];
+  for (size_t p = 0; p < parts.size(); ++p) {
+    CK(cudaMemcpyAsync(cnts[p].data(), parts[p].cnt, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int i = 0; i < n; ++i) tot += cnts[p][i];
+  }
   *count = tot;
   if (capacity == 0 && !i_out) return REAXFF_OK;
   if (capacity < tot || !i_out || !j_out || !shift) return fail(ctx, REAXFF_E_INVALID, "output capacity too small");
-  std::vector<int> jj((size_t)n * cap);
-  std::vector<uint8_t> ss((size_t)n * cap);
-  CK(cudaMemcpyAsync(jj.data(), j_d, jj.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaMemcpyAsync(ss.data(), s_d, ss.size(), cudaMemcpyDeviceToHost, ctx->st));
+  std::vector<std::vector<int>> jj(parts.size());
+  std::vector<std::vector<uint8_t>> ss(parts.size());
+  for (size_t p = 0; p < parts.size(); ++p) {
+    jj[p].resize((size_t)n * parts[p].cap);
+    ss[p].resize((size_t)n * parts[p].cap);
+    CK(cudaMemcpyAsync(jj[p].data(), parts[p].j, jj[p].size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(ss[p].data(), parts[p].s, ss[p].size(), cudaMemcpyDeviceToHost, ctx->st));
+  }
   CK(cudaStreamSynchronize(ctx->st));
   int64_t k = 0;
   for (int i = 0; i < n; ++i)
-    for (int m = 0; m < cnt[i]; ++m) {
-      const size_t e = (size_t)i * cap + m;
-      i_out[k] = i;
-      j_out[k] = jj[e];
-      const int c = ss[e];
-      shift[3 * k + 0] = (int8_t)(c / 9 - 1);
-      shift[3 * k + 1] = (int8_t)((c / 3) % 3 - 1);
-      shift[3 * k + 2] = (int8_t)(c % 3 - 1);
-      ++k;
-    }
+    for (size_t p = 0; p < parts.size(); ++p)
+      for (int m = 0; m < cnts[p][i]; ++m) {
+        const size_t e = (size_t)i * parts[p].cap + m;
+        i_out[k] = i;
+        j_out[k] = jj[p][e];
+        const int c = ss[p][e];
+        shift[3 * k + 0] = (int8_t)(c / 9 - 1);
+        shift[3 * k + 1] = (int8_t)((c / 3) % 3 - 1);
+        shift[3 * k + 2] = (int8_t)(c % 3 - 1);
+        ++k;
+      }
   return REAXFF_OK;
 }
 
@@ -857,6 +930,7 @@ int reaxff_forces(reaxff_ctx* ctx, double* F, double* E, double* virial) {
 int reaxff_forces_fixed_q(reaxff_ctx* ctx, const double* q, double* F, double* E, double* virial) {
   if (!ctx || !q) return REAXFF_E_INVALID;
   CK(cudaMemcpyAsync(ctx->sys.q, q, ctx->n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  rx::charges_to_f32(launch_of(ctx), ctx->sys);
   int rc = forces_impl(ctx, false);
   if (rc) return rc;
   rc = check_flags(ctx, false);

@@ -144,7 +144,7 @@ __global__ void k_atom_terms(Sys s, BondList bl, AtomQ aq, Accum acc, const DPar
   sig_pair<R>(R(-75) * (R)dlp, sg, sgd);                  // 1/(1+e^{-75 dlp})
   const R elp = P->p_lp2[ti] * (R)dlp * sg;
   const R delp = P->p_lp2[ti] * (sg + R(75) * (R)dlp * sgd);
-  fix_add(aq.cddelta + i, (double)(wbit<R>(mask, T_LP) * delp * (-dnlp)), s.err);
+  fix_add(aq.cddelta + i, wbit<R>(mask, T_LP) * delp * (-dnlp), s.err);
   const R prodexp = m_exp(-(R)sum8);
   const double sbo_fac = -dang - (double)P->p_val8 * nlp;
   const R sbo = (R)(pisum + (1.0 - (double)prodexp) * sbo_fac);
@@ -227,7 +227,7 @@ __global__ void k_over_under_bond(Sys s, BondList bl, AtomQ aq, Accum acc, const
   const R wo = wbit<R>(mask, T_OVER), wu = wbit<R>(mask, T_UNDER);
   const R cdlpc = wo * deover + wu * deunder;
   const R cds = cdlpc * ddlpc_dS + wu * deunder_S;
-  fix_add(aq.cddelta + i, (double)(cdlpc * (R(1) + dnlp / den)), s.err);
+  fix_add(aq.cddelta + i, cdlpc * (R(1) + dnlp / den), s.err);
   aq.cds[i] = cds;
   acc.e[T_OVER * s.n + i] = eover;
   acc.e[T_UNDER * s.n + i] = eunder;
@@ -257,9 +257,9 @@ __global__ void k_over_under_bond(Sys s, BondList bl, AtomQ aq, Accum acc, const
       cpi += wb * (-des - P->De_p[pt]);
       cpp += wb * (-des - P->De_pp[pt]);
     }
-    fix_add(bl.cdbo + e, (double)cb, s.err);
-    fix_add(bl.cdbopi + e, (double)cpi, s.err);
-    fix_add(bl.cdbopp + e, (double)cpp, s.err);
+    fix_add(bl.cdbo + e, cb, s.err);
+    fix_add(bl.cdbopi + e, cpi, s.err);
+    fix_add(bl.cdbopp + e, cpp, s.err);
   }
   acc.e[T_BOND * s.n + i] = ebond;
 }
@@ -299,16 +299,17 @@ template <typename R>
 __device__ __forceinline__ Vec3<R> load_vec(const BondList& bl, int e) {
   return Vec3<R>{((const R*)bl.dx)[e], ((const R*)bl.dy)[e], ((const R*)bl.dz)[e]};
 }
-__device__ __forceinline__ void force_add(const Sys& s, int a, double fx, double fy, double fz) {
+template <typename R>
+__device__ __forceinline__ void force_add(const Sys& s, int a, R fx, R fy, R fz) {
   fix_add(s.fx + a, fx, s.err);
   fix_add(s.fy + a, fy, s.err);
   fix_add(s.fz + a, fz, s.err);
 }
-// virial W_ab -= g_a v_b (xx yy zz xy xz yz)
+// virial W_ab -= g_a v_b (xx yy zz xy xz yz), per-lane partial in the path precision
 template <typename R>
-__device__ __forceinline__ void vir_sub(double* w, const Vec3<R>& g, const Vec3<R>& v) {
-  w[0] -= (double)(g.x * v.x); w[1] -= (double)(g.y * v.y); w[2] -= (double)(g.z * v.z);
-  w[3] -= (double)(g.x * v.y); w[4] -= (double)(g.x * v.z); w[5] -= (double)(g.y * v.z);
+__device__ __forceinline__ void vir_sub(R* w, const Vec3<R>& g, const Vec3<R>& v) {
+  w[0] -= g.x * v.x; w[1] -= g.y * v.y; w[2] -= g.z * v.z;
+  w[3] -= g.x * v.y; w[4] -= g.x * v.z; w[5] -= g.y * v.z;
 }
 // f9-type function (2 + e^{-a D}) / (1 + e^{-a D} + e^{b D}) and its D-derivative,
 // written with u = e^{-aD}/den, v = e^{bD}/den in [0, 1] so no intermediate overflows:
@@ -344,8 +345,8 @@ __global__ void k_angles(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<
   f9fun<R>(P->p_pen3, P->p_pen4, delta, f9, df9);
   R scoa, scoad;
   sig_pair<R>(P->p_coa2 * dang, scoa, scoad);
-  double eval = 0, epen = 0, ecoa = 0, cdsbo = 0, cdd = 0;
-  double fj[3] = {0, 0, 0}, w[6] = {0, 0, 0, 0, 0, 0};
+  R l_eval = 0, l_epen = 0, l_ecoa = 0, l_cdsbo = 0, l_cdd = 0;    // per-lane partials
+  R l_fj[3] = {0, 0, 0}, l_w[6] = {0, 0, 0, 0, 0, 0};
   const int npair = nb * (nb - 1) / 2;
   for (int p = lane; p < npair; p += 32) {
     int a = 0, rem = p;
@@ -399,45 +400,47 @@ __global__ void k_angles(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<
     const R pc3 = P->p_coa3, pc4 = P->p_coa4;
     const R ec = P->p_coa1[t3] * scoa * m_exp(-pc3 * sbi * sbi) * m_exp(-pc3 * sbk * sbk) *
                  m_exp(-pc4 * (BOa - R(1.5)) * (BOa - R(1.5))) * m_exp(-pc4 * (BOb - R(1.5)) * (BOb - R(1.5)));
-    eval += (double)ev;
-    epen += (double)ep;
-    ecoa += (double)ec;
+    l_eval += ev;
+    l_epen += ep;
+    l_ecoa += ec;
     // bond-order and Delta derivatives
     const R dBOa = wv * df7a * f7b * f8 * pv1 * gth + wp * ep * (R(-2) * pp2 * (BOa - R(2))) +
                    wc * ec * (R(2) * pc3 * sbi - R(2) * pc4 * (BOa - R(1.5)));
     const R dBOb = wv * f7a * df7b * f8 * pv1 * gth + wp * ep * (R(-2) * pp2 * (BOb - R(2))) +
                    wc * ec * (R(2) * pc3 * sbk - R(2) * pc4 * (BOb - R(1.5)));
-    fix_add(bl.cdbo + ea, (double)dBOa, s.err);
-    fix_add(bl.cdbo + eb, (double)dBOb, s.err);
-    fix_add(aq.cddelta + i, (double)(wc * ec * (R(-2) * pc3 * sbi)), s.err);
-    fix_add(aq.cddelta + k, (double)(wc * ec * (R(-2) * pc3 * sbk)), s.err);
-    cdd += (double)(wv * f7a * f7b * df8 * pv1 * gth + wp * P->p_pen1[t3] * df9 * ga * gb +
-                    wc * (scoa > R(0) ? -ec * P->p_coa2 * scoad / scoa : R(0)));
-    cdsbo += (double)(wv * dEv_dsbo2);
+    fix_add(bl.cdbo + ea, dBOa, s.err);
+    fix_add(bl.cdbo + eb, dBOb, s.err);
+    fix_add(aq.cddelta + i, wc * ec * (R(-2) * pc3 * sbi), s.err);
+    fix_add(aq.cddelta + k, wc * ec * (R(-2) * pc3 * sbk), s.err);
+    l_cdd += wv * f7a * f7b * df8 * pv1 * gth + wp * P->p_pen1[t3] * df9 * ga * gb +
+             wc * (scoa > R(0) ? -ec * P->p_coa2 * scoad / scoa : R(0));
+    l_cdsbo += wv * dEv_dsbo2;
     // geometry: E depends on cos(theta) only through the valence term
     if (cok) {
       const R gt = wv * dEv_dth / nn;
       const Vec3<R> cu = cross3(u, nrm), cv = cross3(nrm, v);
       const Vec3<R> gu = Vec3<R>{gt * cu.x / L1, gt * cu.y / L1, gt * cu.z / L1};
       const Vec3<R> gv = Vec3<R>{gt * cv.x / L2, gt * cv.y / L2, gt * cv.z / L2};
-      force_add(s, i, -(double)gu.x, -(double)gu.y, -(double)gu.z);
-      force_add(s, k, -(double)gv.x, -(double)gv.y, -(double)gv.z);
-      fj[0] += (double)(gu.x + gv.x); fj[1] += (double)(gu.y + gv.y); fj[2] += (double)(gu.z + gv.z);
-      vir_sub(w, gu, u);
-      vir_sub(w, gv, v);
+      force_add<R>(s, i, -gu.x, -gu.y, -gu.z);
+      force_add<R>(s, k, -gv.x, -gv.y, -gv.z);
+      l_fj[0] += gu.x + gv.x; l_fj[1] += gu.y + gv.y; l_fj[2] += gu.z + gv.z;
+      vir_sub(l_w, gu, u);
+      vir_sub(l_w, gv, v);
     }
   }
-  eval = warp_sum(eval); epen = warp_sum(epen); ecoa = warp_sum(ecoa);
-  cdsbo = warp_sum(cdsbo); cdd = warp_sum(cdd);
-  for (int q = 0; q < 3; ++q) fj[q] = warp_sum(fj[q]);
-  for (int q = 0; q < 6; ++q) w[q] = warp_sum(w[q]);
+  const double eval = warp_sum_d(l_eval), epen = warp_sum_d(l_epen), ecoa = warp_sum_d(l_ecoa);
+  double cdsbo = warp_sum_d(l_cdsbo);
+  const double cdd = warp_sum_d(l_cdd);
+  double fj[3], w[6];
+  for (int q = 0; q < 3; ++q) fj[q] = warp_sum_d(l_fj[q]);
+  for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(l_w[q]);
   cdsbo *= aq.dsbo2[j];                                // dE/dSBO
   const double prod = aq.prodexp[j];
   if (lane == 0) {
     acc.e[T_VAL * s.n + j] = eval;
     acc.e[T_PEN * s.n + j] = epen;
     acc.e[T_COA * s.n + j] = ecoa;
-    force_add(s, j, fj[0], fj[1], fj[2]);
+    force_add<double>(s, j, fj[0], fj[1], fj[2]);
     const double dsbo_dsum = -(1.0 - prod) * (1.0 + (double)P->p_val8 * aq.dnlp[j]);
     fix_add(aq.cddelta + j, cdd + cdsbo * dsbo_dsum, s.err);
     for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
@@ -469,7 +472,7 @@ __global__ void k_torsions(Sys s, BondList bl, AtomQ aq, Accum acc, const DParam
   const R* bo_pi = (const R*)bl.bo_pi;
   const R wt = wbit<R>(mask, T_TORS), wcj = wbit<R>(mask, T_CONJ);
   const int tj = s.type[j];
-  double etor = 0, econ = 0, fj[3] = {0, 0, 0}, w[6] = {0, 0, 0, 0, 0, 0}, cddj = 0;
+  R l_etor = 0, l_econ = 0, l_fj[3] = {0, 0, 0}, l_w[6] = {0, 0, 0, 0, 0, 0}, l_cddj = 0;
   for (int cb = 0; cb < nbj; ++cb) {
     const int ejk = j * bl.cap + cb;
     const int k = bl.j[ejk];
@@ -497,7 +500,7 @@ __global__ void k_torsions(Sys s, BondList bl, AtomQ aq, Accum acc, const DParam
     const R L2 = dot3(u2, u2), l2 = m_sqrt(L2);
     int sjk[3];
     shift_decode(codejk, sjk[0], sjk[1], sjk[2]);
-    double fk[3] = {0, 0, 0}, cddk = 0, cdbo2 = 0, cdbopi2 = 0;
+    R l_fk[3] = {0, 0, 0}, l_cddk = 0, l_cdbo2 = 0, l_cdbopi2 = 0;
     const int ntot = (nbj - 1) * (nbk - 1);
     for (int p = lane; p < ntot; p += 32) {
       int ia = p / (nbk - 1), ic = p % (nbk - 1);
@@ -540,8 +543,8 @@ __global__ void k_torsions(Sys s, BondList bl, AtomQ aq, Accum acc, const DParam
       const R K = pc1 * h1 * h2 * h3;
       const R et = f10 * Tsum;
       const R ecj = K * (R(1) - Y);
-      etor += (double)et;
-      econ += (double)ecj;
+      l_etor += et;
+      l_econ += ecj;
       // non-geometric derivatives
       const R dBO1 = wt * dg1 * g2 * g3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO1 - R(1.5)));
       const R dBO3 = wt * g1 * g2 * dg3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO3 - R(1.5)));
@@ -549,12 +552,12 @@ __global__ void k_torsions(Sys s, BondList bl, AtomQ aq, Accum acc, const DParam
       const R dTdx = V2 * Y * ex * pt1 * R(2) * xb;   // d Tsum / d xb
       const R dpi = wt * f10 * dTdx * R(-1);
       const R dD = wt * f10 * dTdx * (-df11);
-      fix_add(bl.cdbo + ea, (double)dBO1, s.err);
-      fix_add(bl.cdbo + ec, (double)dBO3, s.err);
-      cdbo2 += (double)dBO2;
-      cdbopi2 += (double)dpi;
-      cddj += (double)dD;
-      cddk += (double)dD;
+      fix_add(bl.cdbo + ea, dBO1, s.err);
+      fix_add(bl.cdbo + ec, dBO3, s.err);
+      l_cdbo2 += dBO2;
+      l_cdbopi2 += dpi;
+      l_cddj += dD;
+      l_cddk += dD;
       // geometric derivatives through (A, B, P, V, l1, l2, l3)
       const R dES = wt * f10 * R(0.5) * (V1 + V3);
       const R dEC = wt * f10 * (R(0.5) * V1 - R(1.5) * V3);
@@ -585,32 +588,34 @@ __global__ void k_torsions(Sys s, BondList bl, AtomQ aq, Accum acc, const DParam
       gg3.x = iB * u2n2.x + gP * u2n1.x + gV * n1.x + gl3 * u3.x;
       gg3.y = iB * u2n2.y + gP * u2n1.y + gV * n1.y + gl3 * u3.y;
       gg3.z = iB * u2n2.z + gP * u2n1.z + gV * n1.z + gl3 * u3.z;
-      force_add(s, i, -(double)gg1.x, -(double)gg1.y, -(double)gg1.z);
-      force_add(s, l, -(double)gg3.x, -(double)gg3.y, -(double)gg3.z);
-      fj[0] += (double)(gg1.x + gg2.x); fj[1] += (double)(gg1.y + gg2.y); fj[2] += (double)(gg1.z + gg2.z);
-      fk[0] += (double)(gg3.x - gg2.x); fk[1] += (double)(gg3.y - gg2.y); fk[2] += (double)(gg3.z - gg2.z);
-      vir_sub(w, gg1, u1);
-      vir_sub(w, gg2, u2);
-      vir_sub(w, gg3, u3);
+      force_add<R>(s, i, -gg1.x, -gg1.y, -gg1.z);
+      force_add<R>(s, l, -gg3.x, -gg3.y, -gg3.z);
+      l_fj[0] += gg1.x + gg2.x; l_fj[1] += gg1.y + gg2.y; l_fj[2] += gg1.z + gg2.z;
+      l_fk[0] += gg3.x - gg2.x; l_fk[1] += gg3.y - gg2.y; l_fk[2] += gg3.z - gg2.z;
+      vir_sub(l_w, gg1, u1);
+      vir_sub(l_w, gg2, u2);
+      vir_sub(l_w, gg3, u3);
     }
-    for (int q = 0; q < 3; ++q) fk[q] = warp_sum(fk[q]);
-    cddk = warp_sum(cddk);
-    cdbo2 = warp_sum(cdbo2);
-    cdbopi2 = warp_sum(cdbopi2);
+    double fk[3];
+    for (int q = 0; q < 3; ++q) fk[q] = warp_sum_d(l_fk[q]);
+    const double cddk = warp_sum_d(l_cddk);
+    const double cdbo2 = warp_sum_d(l_cdbo2);
+    const double cdbopi2 = warp_sum_d(l_cdbopi2);
     if (lane == 0) {
-      force_add(s, k, fk[0], fk[1], fk[2]);
+      force_add<double>(s, k, fk[0], fk[1], fk[2]);
       fix_add(aq.cddelta + k, cddk, s.err);
       fix_add(bl.cdbo + ejk, cdbo2, s.err);
       fix_add(bl.cdbopi + ejk, cdbopi2, s.err);
     }
   }
-  etor = warp_sum(etor); econ = warp_sum(econ); cddj = warp_sum(cddj);
-  for (int q = 0; q < 3; ++q) fj[q] = warp_sum(fj[q]);
-  for (int q = 0; q < 6; ++q) w[q] = warp_sum(w[q]);
+  const double etor = warp_sum_d(l_etor), econ = warp_sum_d(l_econ), cddj = warp_sum_d(l_cddj);
+  double fj[3], w[6];
+  for (int q = 0; q < 3; ++q) fj[q] = warp_sum_d(l_fj[q]);
+  for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(l_w[q]);
   if (lane == 0) {
     acc.e[T_TORS * s.n + j] = etor;
     acc.e[T_CONJ * s.n + j] = econ;
-    force_add(s, j, fj[0], fj[1], fj[2]);
+    force_add<double>(s, j, fj[0], fj[1], fj[2]);
     fix_add(aq.cddelta + j, cddj, s.err);
     for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
   }
@@ -629,7 +634,7 @@ __global__ void k_hbonds(Sys s, BondList bl, HbList hl, Accum acc, const DParams
   const R* bo = (const R*)bl.bo;
   const R wh = wbit<R>(mask, T_HB);
   const int r = s.rep[j];
-  double ehb = 0, fj[3] = {0, 0, 0}, w[6] = {0, 0, 0, 0, 0, 0};
+  R l_ehb = 0, l_fj[3] = {0, 0, 0}, l_w[6] = {0, 0, 0, 0, 0, 0};
   for (int a = 0; a < nb; ++a) {
     const int ea = j * bl.cap + a;
     const int x = bl.j[ea];
@@ -639,7 +644,7 @@ __global__ void k_hbonds(Sys s, BondList bl, HbList hl, Accum acc, const DParams
     const int codea = bl.s[ea];
     const Vec3<R> u = load_vec<R>(bl, ea);
     const R Lu = dot3(u, u), lu = m_sqrt(Lu);
-    double cdb = 0, fx[3] = {0, 0, 0};
+    R l_cdb = 0, l_fx[3] = {0, 0, 0};
     for (int zz = lane; zz < nz; zz += 32) {
       const int ez = j * hl.cap + zz;
       const int z = hl.j[ez];
@@ -661,8 +666,8 @@ __global__ void k_hbonds(Sys s, BondList bl, HbList hl, Accum acc, const DParams
       const R ph1 = P->p_hb1[pt];
       const R omeb = -m_expm1(-P->p_hb2[pt] * BO);
       const R e = ph1 * omeb * er * s4;
-      ehb += (double)e;
-      cdb += (double)(wh * ph1 * P->p_hb2[pt] * eb * er * s4);
+      l_ehb += e;
+      l_cdb += wh * ph1 * P->p_hb2[pt] * eb * er * s4;
       const R dEdr = wh * e * (-P->p_hb3[pt]) * (-r0 / Lv + R(1) / r0);
       const R dEdc = cok ? wh * ph1 * omeb * er * (-hs) : R(0);
       const R dEdA = dEdc / (lu * lv);
@@ -670,25 +675,27 @@ __global__ void k_hbonds(Sys s, BondList bl, HbList hl, Accum acc, const DParams
       const R dEdLv = dEdc * (-c / (R(2) * Lv)) + dEdr / (R(2) * lv);
       const Vec3<R> gu = lin2(dEdA, v, R(2) * dEdLu, u);
       const Vec3<R> gv = lin2(dEdA, u, R(2) * dEdLv, v);
-      force_add(s, z, -(double)gv.x, -(double)gv.y, -(double)gv.z);
-      fx[0] -= (double)gu.x; fx[1] -= (double)gu.y; fx[2] -= (double)gu.z;
-      fj[0] += (double)(gu.x + gv.x); fj[1] += (double)(gu.y + gv.y); fj[2] += (double)(gu.z + gv.z);
-      vir_sub(w, gu, u);
-      vir_sub(w, gv, v);
+      force_add<R>(s, z, -gv.x, -gv.y, -gv.z);
+      l_fx[0] -= gu.x; l_fx[1] -= gu.y; l_fx[2] -= gu.z;
+      l_fj[0] += gu.x + gv.x; l_fj[1] += gu.y + gv.y; l_fj[2] += gu.z + gv.z;
+      vir_sub(l_w, gu, u);
+      vir_sub(l_w, gv, v);
     }
-    cdb = warp_sum(cdb);
-    for (int q = 0; q < 3; ++q) fx[q] = warp_sum(fx[q]);
+    const double cdb = warp_sum_d(l_cdb);
+    double fx[3];
+    for (int q = 0; q < 3; ++q) fx[q] = warp_sum_d(l_fx[q]);
     if (lane == 0) {
       fix_add(bl.cdbo + ea, cdb, s.err);
-      force_add(s, x, fx[0], fx[1], fx[2]);
+      force_add<double>(s, x, fx[0], fx[1], fx[2]);
     }
   }
-  ehb = warp_sum(ehb);
-  for (int q = 0; q < 3; ++q) fj[q] = warp_sum(fj[q]);
-  for (int q = 0; q < 6; ++q) w[q] = warp_sum(w[q]);
+  const double ehb = warp_sum_d(l_ehb);
+  double fj[3], w[6];
+  for (int q = 0; q < 3; ++q) fj[q] = warp_sum_d(l_fj[q]);
+  for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(l_w[q]);
   if (lane == 0) {
     acc.e[T_HB * s.n + j] = ehb;
-    force_add(s, j, fj[0], fj[1], fj[2]);
+    force_add<double>(s, j, fj[0], fj[1], fj[2]);
     for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
   }
 }

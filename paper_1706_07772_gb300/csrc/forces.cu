@@ -156,8 +156,8 @@ __global__ void k_kick_drift(Sys s, const double* mass_t, double dt, int drift) 
     const double* L = s.box + 3 * s.rep[i];
     double p[3] = {s.x[i] + dt * vx, s.y[i] + dt * vy, s.z[i] + dt * vz};
     for (int d = 0; d < 3; ++d) {
-      if (p[d] < 0.0) p[d] += L[d];
-      if (p[d] >= L[d]) p[d] -= L[d];
+      if (p[d] < 0.0) { p[d] += L[d]; s.img[3 * i + d] -= 1; }
+      if (p[d] >= L[d]) { p[d] -= L[d]; s.img[3 * i + d] += 1; }
     }
     if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) atomicOr(s.err, ERR_NAN);
     s.x[i] = p[0]; s.y[i] = p[1]; s.z[i] = p[2];

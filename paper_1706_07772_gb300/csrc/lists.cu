@@ -12,9 +12,11 @@
 
 namespace {
 
+template <bool COND>
 __global__ void k_cell_assign(Sys s, Cells c) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
+  if (COND && *s.rebuild == 0) return;
   int r = s.rep[i];
   const double* L = s.box + 3 * r;
   const int* nc = c.nc + 3 * r;
@@ -35,7 +37,9 @@ __global__ void k_cell_assign(Sys s, Cells c) {
 }
 
 // single-block exclusive scan over cell counts
-__global__ void k_cell_scan(Cells c) {
+template <bool COND>
+__global__ void k_cell_scan(Cells c, const int* rebuild) {
+  if (COND && *rebuild == 0) return;
   __shared__ int carry;
   __shared__ int warp_tot[32];
   if (threadIdx.x == 0) carry = 0;
@@ -73,15 +77,19 @@ __global__ void k_cell_scan(Cells c) {
   if (threadIdx.x == 0) c.start[c.ncell_total] = carry;
 }
 
+template <bool COND>
 __global__ void k_cell_scatter(Sys s, Cells c, int* tmp) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
+  if (COND && *s.rebuild == 0) return;
   int slot = atomicAdd(&c.cursor[c.atom_cell[i]], 1);
   tmp[slot] = i;
 }
 
 // per cell: order atoms by index (rank = number of smaller indices in the cell)
-__global__ void k_cell_sort(Cells c, const int* tmp) {
+template <bool COND>
+__global__ void k_cell_sort(Cells c, const int* tmp, const int* rebuild) {
+  if (COND && *rebuild == 0) return;
   int cell = blockIdx.x;
   int a = c.start[cell], b = c.start[cell + 1];
   for (int k = a + threadIdx.x; k < b; k += blockDim.x) {
@@ -163,6 +171,91 @@ __global__ void k_far_list(Sys s, Cells c, FarList f, const DParams<R>* __restri
   }
 }
 
+// Context-path far list: the same candidates and exact membership as k_far_list, each
+// accepted entry written to the near part (r < r_bond, exact FP64 decision in the band)
+// or the far part of its row.
+template <typename R>
+__global__ void k_far_list_split(Sys s, Cells c, FarList f, const DParams<R>* __restrict__ P, float margin,
+                                 float margin_near, double R2, double Rb2) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= s.n) return;
+  const int i = warp;
+  const int r = s.rep[i];
+  const int* nc = c.nc + 3 * r;
+  const float* Lh = s.boxh + 3 * r;
+  const float R2f = (float)R2;        // R2, Rb2 come precomputed (no FP64 work in the loop)
+  const float Rb2f = (float)Rb2;
+  int cell = c.atom_cell[i] - c.cell_off[r];
+  int ci[3] = {cell % nc[0], (cell / nc[0]) % nc[1], cell / (nc[0] * nc[1])};
+  float xi = s.xh[i], yi = s.yh[i], zi = s.zh[i];
+  const int ti = s.type[i];
+  int cntn = 0, cntf = 0;
+  const int rown = i * f.capn, rowf = i * f.cap;
+  R* Hn = (R*)f.Hn;
+  R* Hf = (R*)f.H;
+  for (int o = 0; o < 27; ++o) {
+    int oc[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+    int t[3], sh[3];
+    for (int d = 0; d < 3; ++d) {
+      int v = ci[d] + oc[d];
+      sh[d] = v < 0 ? -1 : (v >= nc[d] ? 1 : 0);
+      t[d] = v - sh[d] * nc[d];
+    }
+    int code = (sh[0] + 1) * 9 + (sh[1] + 1) * 3 + (sh[2] + 1);
+    int cid = c.cell_off[r] + (t[2] * nc[1] + t[1]) * nc[0] + t[0];
+    int a = c.start[cid], b = c.start[cid + 1];
+    float ox = sh[0] * Lh[0], oy = sh[1] * Lh[1], oz = sh[2] * Lh[2];
+    for (int base = a; base < b; base += 32) {
+      int k = base + lane;
+      bool ok = false, near = false;
+      int j = -1;
+      if (k < b) {
+        j = c.atoms[k];
+        float dx = (s.xh[j] - xi) + ox, dy = (s.yh[j] - yi) + oy, dz = (s.zh[j] - zi) + oz;
+        float r2f = dx * dx + dy * dy + dz * dz;
+        ok = !(j == i && code == 13) && in_range(s, i, j, code, r, r2f, R2f, margin, R2);
+        if (ok) near = in_range(s, i, j, code, r, r2f, Rb2f, margin_near, Rb2);
+      }
+      const unsigned mn = __ballot_sync(0xffffffffu, ok && near);
+      const unsigned mf = __ballot_sync(0xffffffffu, ok && !near);
+      const unsigned below = (1u << lane) - 1u;
+      if (ok) {
+        R dx, dy, dz;
+        PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
+        const R rr = m_sqrt(dx * dx + dy * dy + dz * dz);
+        R tap, dtap;
+        taper<R>(rr, P->r_nb, tap, dtap);
+        const R g3 = P->gamma_m3[ti * MAXT + s.type[j]];
+        const R sh3 = rr * rr * rr + g3;
+        if (near) {
+          const int pos = cntn + __popc(mn & below);
+          if (pos < f.capn) {
+            f.jn[rown + pos] = j;
+            f.sn[rown + pos] = (uint8_t)code;
+            Hn[rown + pos] = tap * P->k_e / m_cbrt(sh3);
+          }
+        } else {
+          const int pos = cntf + __popc(mf & below);
+          if (pos < f.cap) {
+            f.j[rowf + pos] = j;
+            f.s[rowf + pos] = (uint8_t)code;
+            Hf[rowf + pos] = tap * P->k_e * f_pow(sh3, R(-1) / R(3));
+          }
+        }
+      }
+      cntn += __popc(mn);
+      cntf += __popc(mf);
+    }
+  }
+  if (lane == 0) {
+    f.cntn[i] = cntn < f.capn ? cntn : f.capn;
+    f.cnt[i] = cntf < f.cap ? cntf : f.cap;
+    if (cntn > f.capn) atomicOr(s.err, ERR_CAP_NEAR);
+    if (cntf > f.cap) atomicOr(s.err, ERR_CAP_FAR);
+  }
+}
+
 // BO' components and their r-derivatives: sigma carries the (1 + bo_cut) factor.
 // (r/r0)^p = exp(p log1p((r - r0)/r0)); in FP32 r and r0 are float-float so the
 // difference r - r0 keeps full relative precision (steep exponents p ~ 10-40 amplify
@@ -217,22 +310,27 @@ __global__ void k_bond_list(Sys s, FarList f, BondList bl, HbList hl, AtomQ aq,
   const int r = s.rep[i];
   const int ti = s.type[i];
   const bool is_h = P->hb[ti] == 1;
-  const int nf = f.cnt[i];
-  const int frow = i * f.cap, brow = i * bl.cap, hrow = i * hl.cap;
+  const int brow = i * bl.cap, hrow = i * hl.cap;
   R* bdx = (R*)bl.dx; R* bdy = (R*)bl.dy; R* bdz = (R*)bl.dz; R* br = (R*)bl.r;
-  const double rb2 = Pd->r_bond * Pd->r_bond, rh2 = Pd->r_hb * Pd->r_hb;
+  const double rh2 = Pd->r_hb * Pd->r_hb;
   int nb = 0, nh = 0;
-  for (int base = 0; base < nf; base += 32) {
+  // near part: every entry has r < r_bond (decided exactly by the far-list pass)
+  const int nn = f.cntn[i];
+  const int frow = i * f.capn;
+  for (int base = 0; base < nn; base += 32) {
     int k = base + lane;
     bool isb = false, ish = false;
     int j = 0, code = 0;
-    R dx = 0, dy = 0, dz = 0, rr = 0, bs = 0, bp = 0, bpp = 0, dbs = 0, dbp = 0, dbpp = 0;
-    if (k < nf) {
-      j = f.j[frow + k];
-      code = f.s[frow + k];
-      R rlo = 0;
+    R dx = 0, dy = 0, dz = 0, rr = 0;
+    if (k < nn) {
+      j = f.jn[frow + k];
+      code = f.sn[frow + k];
+      const int pt = ti * MAXT + s.type[j];
+      R bs, bp, bpp, dbs, dbp, dbpp;
       if (sizeof(R) == 8) {
         PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
+        rr = m_sqrt(dx * dx + dy * dy + dz * dz);
+        isb = bond_member_exact(s, Pd, i, j, code, r, pt);
       } else {
         int sx, sy, sz;
         shift_decode(code, sx, sy, sz);
@@ -245,52 +343,62 @@ __global__ void k_bond_list(Sys s, FarList f, BondList bl, HbList hl, AtomQ aq,
         norm_ff(dh, dl, rh, rl);
         dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
         rr = (R)rh;
-        rlo = (R)rl;
+        bo_prime<R>(P, pt, rr, (R)rl, bs, bp, bpp, dbs, dbp, dbpp);
+        const R tot = bs + bp + bpp;
+        const bool clear = fabsf((float)(tot - P->bo_cut)) > 1e-3f * (float)P->bo_cut;
+        isb = clear ? tot >= P->bo_cut : bond_member_exact(s, Pd, i, j, code, r, pt);
       }
-      R r2 = dx * dx + dy * dy + dz * dz;
-      const int pt = ti * MAXT + s.type[j];
-      if (sizeof(R) == 8) {
-        // FP64 path: the computed r^2 is the defining value up to contraction; use the
-        // exact form for the decision
-        double r2e = r2_exact(s, i, j, code, r);
-        if (r2e < rb2) {
-          rr = m_sqrt(r2);
-          bo_prime<R>(P, pt, rr, R(0), bs, bp, bpp, dbs, dbp, dbpp);
-          isb = (double)(bs + bp + bpp) >= Pd->bo_cut;
-        }
-        if (is_h && P->hb[s.type[j]] == 2) ish = r2e < rh2;
-      } else {
-        // FP32 path: |r2 - r2_exact| <= ~1e-6 relative (hi/lo positions); 1e-4 margins
-        float r2f = (float)r2;
-        if (r2f < (float)rb2 * 1.0001f) {
-          bo_prime<R>(P, pt, rr, rlo, bs, bp, bpp, dbs, dbp, dbpp);
-          R tot = bs + bp + bpp;
-          bool clear = r2f < (float)rb2 * 0.9999f && fabsf((float)(tot - P->bo_cut)) > 1e-3f * (float)P->bo_cut;
-          isb = clear ? tot >= P->bo_cut : bond_member_exact(s, Pd, i, j, code, r, pt);
-        }
-        if (is_h && P->hb[s.type[j]] == 2) {
-          float m = (float)rh2 * 1e-4f;
-          ish = r2f < (float)rh2 - m ? true : (r2f > (float)rh2 + m ? false : r2_exact(s, i, j, code, r) < rh2);
-        }
-      }
+      ish = is_h && P->hb[s.type[j]] == 2;               // r < r_bond <= r_hb
     }
-    unsigned mb = __ballot_sync(0xffffffffu, isb);
-    int pos = nb + __popc(mb & ((1u << lane) - 1u));
+    const unsigned mb = __ballot_sync(0xffffffffu, isb);
+    const int pos = nb + __popc(mb & ((1u << lane) - 1u));
     if (isb && pos < bl.cap) {
-      int e = brow + pos;
+      const int e = brow + pos;
       bl.j[e] = j;
       bl.s[e] = (uint8_t)code;
       bdx[e] = dx; bdy[e] = dy; bdz[e] = dz; br[e] = rr;
       if ((i < j) || (i == j && code > 13)) bl.canon[atomicAdd(bl.ncanon, 1)] = e;
     }
     nb += __popc(mb);
-    unsigned mh = __ballot_sync(0xffffffffu, ish);
-    int hp = nh + __popc(mh & ((1u << lane) - 1u));
+    const unsigned mh = __ballot_sync(0xffffffffu, ish);
+    const int hp = nh + __popc(mh & ((1u << lane) - 1u));
     if (ish && hp < hl.cap) {
       hl.j[hrow + hp] = j;
       hl.s[hrow + hp] = (uint8_t)code;
     }
     nh += __popc(mh);
+  }
+  // far part: H-bond partners with r_bond <= r < r_hb (H atoms only)
+  if (is_h) {
+    const int nfa = f.cnt[i];
+    const int frw = i * f.cap;
+    for (int base = 0; base < nfa; base += 32) {
+      int k = base + lane;
+      bool ish = false;
+      int j = 0, code = 0;
+      if (k < nfa) {
+        j = f.j[frw + k];
+        code = f.s[frw + k];
+        if (P->hb[s.type[j]] == 2) {
+          if (sizeof(R) == 8) {
+            ish = r2_exact(s, i, j, code, r) < rh2;
+          } else {
+            R dx, dy, dz;
+            PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
+            const float r2f = (float)(dx * dx + dy * dy + dz * dz);
+            const float m = (float)rh2 * 1e-4f;
+            ish = r2f < (float)rh2 - m ? true : (r2f > (float)rh2 + m ? false : r2_exact(s, i, j, code, r) < rh2);
+          }
+        }
+      }
+      const unsigned mh = __ballot_sync(0xffffffffu, ish);
+      const int hp = nh + __popc(mh & ((1u << lane) - 1u));
+      if (ish && hp < hl.cap) {
+        hl.j[hrow + hp] = j;
+        hl.s[hrow + hp] = (uint8_t)code;
+      }
+      nh += __popc(mh);
+    }
   }
   if (lane == 0) {
     bl.cnt[i] = nb < bl.cap ? nb : bl.cap;
@@ -323,6 +431,167 @@ __global__ void k_bond_mirror(Sys s, BondList bl) {
     }
     bl.mirror[e] = found;
   }
+}
+
+// float hi/lo copies of the positions (every step)
+__global__ void k_pos_f32(Sys s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  float h;
+  h = (float)s.x[i]; s.xh[i] = h; s.xl[i] = (float)(s.x[i] - (double)h);
+  h = (float)s.y[i]; s.yh[i] = h; s.yl[i] = (float)(s.y[i] - (double)h);
+  h = (float)s.z[i]; s.zh[i] = h; s.zl[i] = (float)(s.z[i] - (double)h);
+}
+
+// displacement since the last build, |(x + img L) - xb|, against skin/2
+__global__ void k_skin_check(Sys s, CandList cl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const double* L = s.box + 3 * s.rep[i];
+  const double p[3] = {s.x[i], s.y[i], s.z[i]};
+  double d2 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double dd = (p[d] + s.img[3 * i + d] * L[d]) - s.xb[3 * i + d];
+    d2 += dd * dd;
+  }
+  if (!(d2 <= cl.half_skin2)) atomicOr(s.rebuild, 1);
+}
+
+// candidate rows: every (j, image) within r_nb + skin (FP32 with a margin: a superset),
+// built from the cell stencil; resets the atom's reference position and crossings
+__global__ void k_cand_build(Sys s, Cells c, CandList cl) {
+  if (*s.rebuild == 0) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= s.n) return;
+  const int i = warp;
+  const int r = s.rep[i];
+  const int* nc = c.nc + 3 * r;
+  const float* Lh = s.boxh + 3 * r;
+  int cell = c.atom_cell[i] - c.cell_off[r];
+  int ci[3] = {cell % nc[0], (cell / nc[0]) % nc[1], cell / (nc[0] * nc[1])};
+  const float xi = s.xh[i], yi = s.yh[i], zi = s.zh[i];
+  int count = 0;
+  const int row = i * cl.cap;
+  for (int o = 0; o < 27; ++o) {
+    int oc[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+    int t[3], sh[3];
+    for (int d = 0; d < 3; ++d) {
+      int v = ci[d] + oc[d];
+      sh[d] = v < 0 ? -1 : (v >= nc[d] ? 1 : 0);
+      t[d] = v - sh[d] * nc[d];
+    }
+    const int code = (sh[0] + 1) * 9 + (sh[1] + 1) * 3 + (sh[2] + 1);
+    const int cid = c.cell_off[r] + (t[2] * nc[1] + t[1]) * nc[0] + t[0];
+    const int a = c.start[cid], b = c.start[cid + 1];
+    const float ox = sh[0] * Lh[0], oy = sh[1] * Lh[1], oz = sh[2] * Lh[2];
+    for (int base = a; base < b; base += 32) {
+      const int k = base + lane;
+      bool ok = false;
+      int j = -1;
+      if (k < b) {
+        j = c.atoms[k];
+        const float dx = (s.xh[j] - xi) + ox, dy = (s.yh[j] - yi) + oy, dz = (s.zh[j] - zi) + oz;
+        ok = !(j == i && code == 13) && dx * dx + dy * dy + dz * dz < cl.rc2;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      const int pos = count + __popc(m & ((1u << lane) - 1u));
+      if (ok && pos < cl.cap) {
+        cl.j[row + pos] = j;
+        cl.s[row + pos] = (uint8_t)code;
+      }
+      count += __popc(m);
+    }
+  }
+  if (lane == 0) {
+    cl.cnt[i] = count < cl.cap ? count : cl.cap;
+    if (count > cl.cap) atomicOr(s.err, ERR_CAP_CAND);
+  }
+  if (lane < 3) {
+    s.xb[3 * i + lane] = lane == 0 ? s.x[i] : (lane == 1 ? s.y[i] : s.z[i]);
+    s.img[3 * i + lane] = 0;
+  }
+}
+
+// every step: exact membership (same rule as the stencil far list) over the candidates;
+// image shift corrected by the box crossings since the build
+template <typename R>
+__global__ void k_cand_filter(Sys s, CandList cl, FarList f, const DParams<R>* __restrict__ P, float margin,
+                              float margin_near, double R2, double Rb2) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= s.n) return;
+  const int i = warp;
+  const int r = s.rep[i];
+  const float* Lh = s.boxh + 3 * r;
+  const float R2f = (float)R2, Rb2f = (float)Rb2;
+  const float xi = s.xh[i], yi = s.yh[i], zi = s.zh[i];
+  const int ii0 = s.img[3 * i], ii1 = s.img[3 * i + 1], ii2 = s.img[3 * i + 2];
+  const int ti = s.type[i];
+  const int nc = cl.cnt[i], crow = i * cl.cap;
+  int cntn = 0, cntf = 0;
+  const int rown = i * f.capn, rowf = i * f.cap;
+  R* Hn = (R*)f.Hn;
+  R* Hf = (R*)f.H;
+  for (int base = 0; base < nc; base += 32) {
+    const int k = base + lane;
+    bool ok = false, near = false;
+    int j = -1, code = 13;
+    if (k < nc) {
+      j = cl.j[crow + k];
+      int sx, sy, sz;
+      shift_decode(cl.s[crow + k], sx, sy, sz);
+      sx += s.img[3 * j] - ii0;
+      sy += s.img[3 * j + 1] - ii1;
+      sz += s.img[3 * j + 2] - ii2;
+      if (sx >= -1 && sx <= 1 && sy >= -1 && sy <= 1 && sz >= -1 && sz <= 1) {
+        code = (sx + 1) * 9 + (sy + 1) * 3 + (sz + 1);
+        const float dx = (s.xh[j] - xi) + sx * Lh[0], dy = (s.yh[j] - yi) + sy * Lh[1];
+        const float dz = (s.zh[j] - zi) + sz * Lh[2];
+        const float r2f = dx * dx + dy * dy + dz * dz;
+        ok = !(j == i && code == 13) && in_range(s, i, j, code, r, r2f, R2f, margin, R2);
+        if (ok) near = in_range(s, i, j, code, r, r2f, Rb2f, margin_near, Rb2);
+      }
+    }
+    const unsigned mn = __ballot_sync(0xffffffffu, ok && near);
+    const unsigned mf = __ballot_sync(0xffffffffu, ok && !near);
+    const unsigned below = (1u << lane) - 1u;
+    if (ok) {
+      R dx, dy, dz;
+      PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
+      const R rr = m_sqrt(dx * dx + dy * dy + dz * dz);
+      R tap, dtap;
+      taper<R>(rr, P->r_nb, tap, dtap);
+      const R sh3 = rr * rr * rr + P->gamma_m3[ti * MAXT + s.type[j]];
+      if (near) {
+        const int pos = cntn + __popc(mn & below);
+        if (pos < f.capn) {
+          f.jn[rown + pos] = j;
+          f.sn[rown + pos] = (uint8_t)code;
+          Hn[rown + pos] = tap * P->k_e / m_cbrt(sh3);
+        }
+      } else {
+        const int pos = cntf + __popc(mf & below);
+        if (pos < f.cap) {
+          f.j[rowf + pos] = j;
+          f.s[rowf + pos] = (uint8_t)code;
+          Hf[rowf + pos] = tap * P->k_e * f_pow(sh3, R(-1) / R(3));
+        }
+      }
+    }
+    cntn += __popc(mn);
+    cntf += __popc(mf);
+  }
+  if (lane == 0) {
+    f.cntn[i] = cntn < f.capn ? cntn : f.capn;
+    f.cnt[i] = cntf < f.cap ? cntf : f.cap;
+    if (cntn > f.capn) atomicOr(s.err, ERR_CAP_NEAR);
+    if (cntf > f.cap) atomicOr(s.err, ERR_CAP_FAR);
+  }
+}
+
+__global__ void k_rebuild_done(Sys s) {
+  if (threadIdx.x == 0) *s.rebuild = 0;
 }
 
 // FP64 BO' of each unordered bond (thread per bond), written to both directed entries
@@ -364,12 +633,42 @@ namespace rx {
 
 void cells_build(const Launch& L, Sys s, Cells c) {
   cudaMemsetAsync(c.count, 0, sizeof(int) * c.ncell_total, L.st);
-  k_cell_assign<<<grid_for(s.n, 256), 256, 0, L.st>>>(s, c);
-  k_cell_scan<<<1, 1024, 0, L.st>>>(c);
-  k_cell_scatter<<<grid_for(s.n, 256), 256, 0, L.st>>>(s, c, c.tmp);
-  k_cell_sort<<<c.ncell_total, 128, 0, L.st>>>(c, c.tmp);
+  k_cell_assign<false><<<grid_for(s.n, 256), 256, 0, L.st>>>(s, c);
+  k_cell_scan<false><<<1, 1024, 0, L.st>>>(c, nullptr);
+  k_cell_scatter<false><<<grid_for(s.n, 256), 256, 0, L.st>>>(s, c, c.tmp);
+  k_cell_sort<false><<<c.ncell_total, 128, 0, L.st>>>(c, c.tmp, nullptr);
   *L.count += 4;
 }
+
+void positions_f32(const Launch& L, Sys s) {
+  k_pos_f32<<<grid_for(s.n, 256), 256, 0, L.st>>>(s);
+  *L.count += 1;
+}
+
+void skin_check(const Launch& L, Sys s, CandList cl) {
+  k_skin_check<<<grid_for(s.n, 256), 256, 0, L.st>>>(s, cl);
+  *L.count += 1;
+}
+
+void cand_build(const Launch& L, Sys s, Cells c, CandList cl) {
+  cudaMemsetAsync(c.count, 0, sizeof(int) * c.ncell_total, L.st);
+  k_cell_assign<true><<<grid_for(s.n, 256), 256, 0, L.st>>>(s, c);
+  k_cell_scan<true><<<1, 1024, 0, L.st>>>(c, s.rebuild);
+  k_cell_scatter<true><<<grid_for(s.n, 256), 256, 0, L.st>>>(s, c, c.tmp);
+  k_cell_sort<true><<<c.ncell_total, 128, 0, L.st>>>(c, c.tmp, s.rebuild);
+  k_cand_build<<<grid_for((long long)s.n * 32, 256), 256, 0, L.st>>>(s, c, cl);
+  *L.count += 5;
+}
+
+template <typename R>
+void cand_filter(const Launch& L, Sys s, CandList cl, FarList f, const DParams<R>* P, float margin, float margin_near) {
+  k_cand_filter<R><<<grid_for((long long)s.n * 32, 256), 256, 0, L.st>>>(s, cl, f, P, margin, margin_near, f.r2_nb,
+                                                                         f.r2_bond);
+  k_rebuild_done<<<1, 32, 0, L.st>>>(s);
+  *L.count += 2;
+}
+template void cand_filter<double>(const Launch&, Sys, CandList, FarList, const DParams<double>*, float, float);
+template void cand_filter<float>(const Launch&, Sys, CandList, FarList, const DParams<float>*, float, float);
 
 template <typename R>
 void far_list(const Launch& L, Sys s, Cells c, FarList f, const DParams<R>* P, float margin) {
@@ -378,9 +677,28 @@ void far_list(const Launch& L, Sys s, Cells c, FarList f, const DParams<R>* P, f
 }
 
 template <typename R>
+void far_list_split(const Launch& L, Sys s, Cells c, FarList f, const DParams<R>* P, float margin,
+                    float margin_near) {
+  k_far_list_split<R><<<grid_for((long long)s.n * 32, 256), 256, 0, L.st>>>(s, c, f, P, margin, margin_near,
+                                                                           f.r2_nb, f.r2_bond);
+  *L.count += 1;
+}
+
+template <typename R>
 void bond_list(const Launch& L, Sys s, FarList f, BondList b, HbList h, AtomQ a, const DParams<R>* P,
                const DParams<double>* Pd) {
   k_bond_list<R><<<grid_for((long long)s.n * 32, 256), 256, 0, L.st>>>(s, f, b, h, a, P, Pd);
+  *L.count += 1;
+}
+
+namespace {
+__global__ void k_q_to_f32(Sys s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < s.n) s.qf[i] = (float)s.q[i];
+}
+}  // namespace
+void charges_to_f32(const Launch& L, Sys s) {
+  k_q_to_f32<<<grid_for(s.n, 256), 256, 0, L.st>>>(s);
   *L.count += 1;
 }
 
@@ -397,6 +715,8 @@ void bo_prime64(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<doubl
 
 template void far_list<double>(const Launch&, Sys, Cells, FarList, const DParams<double>*, float);
 template void far_list<float>(const Launch&, Sys, Cells, FarList, const DParams<float>*, float);
+template void far_list_split<double>(const Launch&, Sys, Cells, FarList, const DParams<double>*, float, float);
+template void far_list_split<float>(const Launch&, Sys, Cells, FarList, const DParams<float>*, float, float);
 template void bond_list<double>(const Launch&, Sys, FarList, BondList, HbList, AtomQ, const DParams<double>*,
                                 const DParams<double>*);
 template void bond_list<float>(const Launch&, Sys, FarList, BondList, HbList, AtomQ, const DParams<float>*,

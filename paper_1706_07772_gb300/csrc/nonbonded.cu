@@ -17,6 +17,57 @@ namespace {
 
 inline unsigned grid_for(long long threads, int block) { return (unsigned)((threads + block - 1) / block); }
 
+template <typename R> struct QLoad;
+template <> struct QLoad<double> {
+  static __device__ __forceinline__ double get(const Sys& s, int j) { return s.q[j]; }
+};
+template <> struct QLoad<float> {
+  static __device__ __forceinline__ float get(const Sys& s, int j) { return s.qf[j]; }
+};
+
+// one directed pair: accumulates energies, force on i and half the pair virial.
+// FAST selects the MUFU-based pow/exp (used for pairs beyond r_bond in FP32).
+template <typename R, bool FAST, typename A>
+__device__ __forceinline__ void nb_pair(const Sys& s, const DParams<R>* __restrict__ P, int i, int j, int code, int r,
+                                        int ti, R qi, R wv, R wc, A& ev, A& ec, A& fx, A& fy, A& fz, A* w) {
+  R dx, dy, dz;
+  PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
+  const R r2 = dx * dx + dy * dy + dz * dz;
+  const R rr = m_sqrt(r2);
+  R tap, dtap;
+  taper<R>(rr, P->r_nb, tap, dtap);
+  const int pt = ti * MAXT + s.type[j];
+  const R pv = P->p_vdW1, ipv = R(1) / P->p_vdW1;
+  // van der Waals
+  const R rp = FAST ? f_pow(rr, pv) : m_pow(rr, pv);
+  const R base = rp + P->vdw_gw_pow[pt];
+  const R f13 = FAST ? f_pow(base, ipv) : m_pow(base, ipv);
+  const R df13 = f13 * rp / (rr * base);
+  const R al = P->vdw_alpha[pt], rv = P->vdw_rv[pt], D = P->vdw_D[pt];
+  const R xr = R(1) - f13 / rv;
+  const R E1 = FAST ? f_exp(al * xr) : m_exp(al * xr);
+  const R E2 = FAST ? f_exp(R(0.5) * al * xr) : m_exp(R(0.5) * al * xr);
+  const R evp = D * (E1 - R(2) * E2);
+  const R devp = -(D * al / rv) * (E1 - E2);
+  // Coulomb
+  const R sh3 = r2 * rr + P->gamma_m3[pt];
+  const R ish = FAST ? f_pow(sh3, R(-1) / R(3)) : R(1) / m_cbrt(sh3);
+  const R kq = P->k_e * qi * QLoad<R>::get(s, j);
+  const R ecp = kq * ish;
+  const R decp = -kq * r2 * ish * ish * ish * ish;
+  ev += (A)(tap * evp);
+  ec += (A)(tap * ecp);
+  const R de = wv * (dtap * evp + tap * devp * df13) + wc * (dtap * ecp + tap * decp);
+  const R c = de / rr;                                // F_i += (dE/dr) d/r
+  fx += (A)(c * dx);
+  fy += (A)(c * dy);
+  fz += (A)(c * dz);
+  // half of W_ab = -dE/dr d_a d_b / r for this direction
+  const R hc = R(-0.5) * c;
+  w[0] += (A)(hc * dx * dx); w[1] += (A)(hc * dy * dy); w[2] += (A)(hc * dz * dz);
+  w[3] += (A)(hc * dx * dy); w[4] += (A)(hc * dx * dz); w[5] += (A)(hc * dy * dz);
+}
+
 template <typename R>
 __global__ void k_nonbonded(Sys s, FarList f, Accum acc, const DParams<R>* __restrict__ P, unsigned mask) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -24,54 +75,25 @@ __global__ void k_nonbonded(Sys s, FarList f, Accum acc, const DParams<R>* __res
   if (i >= s.n) return;
   const int ti = s.type[i];
   const int r = s.rep[i];
-  const int nf = f.cnt[i];
-  const int row = i * f.cap;
-  const R qi = (R)s.q[i];
+  const R qi = QLoad<R>::get(s, i);
   const R wv = ((mask >> T_VDW) & 1u) ? R(1) : R(0);
   const R wc = ((mask >> T_COUL) & 1u) ? R(1) : R(0);
-  const R pv = P->p_vdW1, ipv = R(1) / P->p_vdW1;
-  double ev = 0, ec = 0, fx = 0, fy = 0, fz = 0, w[6] = {0, 0, 0, 0, 0, 0};
-  for (int k = lane; k < nf; k += 32) {
-    const int j = f.j[row + k];
-    const int code = f.s[row + k];
-    R dx, dy, dz;
-    PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
-    const R r2 = dx * dx + dy * dy + dz * dz;
-    const R rr = m_sqrt(r2);
-    R tap, dtap;
-    taper<R>(rr, P->r_nb, tap, dtap);
-    const int pt = ti * MAXT + s.type[j];
-    // van der Waals
-    const R rp = m_pow(rr, pv);
-    const R base = rp + P->vdw_gw_pow[pt];
-    const R f13 = m_pow(base, ipv);
-    const R df13 = f13 * rp / (rr * base);
-    const R al = P->vdw_alpha[pt], rv = P->vdw_rv[pt], D = P->vdw_D[pt];
-    const R xr = R(1) - f13 / rv;
-    const R E1 = m_exp(al * xr), E2 = m_exp(R(0.5) * al * xr);
-    const R evp = D * (E1 - R(2) * E2);
-    const R devp = -(D * al / rv) * (E1 - E2);
-    // Coulomb
-    const R sh3 = r2 * rr + P->gamma_m3[pt];
-    const R sh = m_cbrt(sh3);
-    const R kq = P->k_e * qi * (R)s.q[j];
-    const R ecp = kq / sh;
-    const R decp = -kq * r2 / (sh3 * sh);
-    ev += (double)(tap * evp);
-    ec += (double)(tap * ecp);
-    const R de = wv * (dtap * evp + tap * devp * df13) + wc * (dtap * ecp + tap * decp);
-    const R c = de / rr;                                // F_i += (dE/dr) d/r
-    fx += (double)(c * dx);
-    fy += (double)(c * dy);
-    fz += (double)(c * dz);
-    // half of W_ab = -dE/dr d_a d_b / r for this direction
-    const double hc = -0.5 * (double)c;
-    w[0] += hc * (double)(dx * dx); w[1] += hc * (double)(dy * dy); w[2] += hc * (double)(dz * dz);
-    w[3] += hc * (double)(dx * dy); w[4] += hc * (double)(dx * dz); w[5] += hc * (double)(dy * dz);
-  }
-  ev = warp_sum(ev); ec = warp_sum(ec);
-  fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
-  for (int q = 0; q < 6; ++q) w[q] = warp_sum(w[q]);
+  // near part (r < r_bond): accurate math; per-lane sums in the path precision kept apart
+  // from the far part (the near forces are ~100x larger; mixing would round the far ones away)
+  R nev = 0, nec = 0, nfx = 0, nfy = 0, nfz = 0, nw[6] = {0, 0, 0, 0, 0, 0};
+  const int nn = f.cntn[i], rown = i * f.capn;
+  for (int k = lane; k < nn; k += 32)
+    nb_pair<R, false, R>(s, P, i, f.jn[rown + k], f.sn[rown + k], r, ti, qi, wv, wc, nev, nec, nfx, nfy, nfz, nw);
+  // far part (r_bond <= r < r_nb): MUFU pow/exp in FP32
+  R lev = 0, lec = 0, lfx = 0, lfy = 0, lfz = 0, lw[6] = {0, 0, 0, 0, 0, 0};
+  const int nfa = f.cnt[i], rowf = i * f.cap;
+  for (int k = lane; k < nfa; k += 32)
+    nb_pair<R, true, R>(s, P, i, f.j[rowf + k], f.s[rowf + k], r, ti, qi, wv, wc, lev, lec, lfx, lfy, lfz, lw);
+  const double ev = warp_sum_d(nev) + warp_sum_d(lev), ec = warp_sum_d(nec) + warp_sum_d(lec);
+  const double fx = warp_sum_d(nfx) + warp_sum_d(lfx), fy = warp_sum_d(nfy) + warp_sum_d(lfy);
+  const double fz = warp_sum_d(nfz) + warp_sum_d(lfz);
+  double w[6];
+  for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(nw[q]) + warp_sum_d(lw[q]);
   if (lane == 0) {
     acc.e[T_VDW * s.n + i] = 0.5 * ev;
     acc.e[T_COUL * s.n + i] = 0.5 * ec;

@@ -34,10 +34,15 @@ struct CG {
   const int* col;
   const R* H;
   int cap;
-  const double *eta, *chi;                 // per type (double)
+  const int* cntn;                         // near part of each row
+  const int* coln;
+  const R* Hn;
+  int capn;
+  const double *eta, *chi, *ieta;          // per type (double); ieta = 1/eta
   double *xs, *xt, *rs, *rt, *zs, *zt, *ps, *pt, *ws, *wt;
   float *zsf, *ztf;                        // FP32 copies of z for the FP32-arithmetic SpMV
   double* q;
+  float* qf;
   double* part;                            // [nchunk*NQ]
   double* red;                             // [nrep*NQ]
   double* scal;                            // [nrep*NS + 1]
@@ -92,26 +97,42 @@ __device__ bool barrier_reduce(GridBar* bar, int* err, F reduce) {
   return ok;
 }
 
-// last-block reduction of chunk partials into red[r*NQ+q] (warp per (replica, slot))
+// last-block reduction of chunk partials into red[r*NQ+q]: one warp per replica, each
+// lane sums whole chunks (all NQ slots, contiguous) in a fixed order, then the lanes are
+// combined by a fixed butterfly (deterministic)
 template <typename R>
 __device__ void reduce_parts(const CG<R>& a, double* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int pq = wid; pq < a.nrep * NQ; pq += nw) {
-    const int r = pq / NQ, qq = pq % NQ;
-    double v = 0.0;
-    for (int c = a.rep_chunk[r] + lane; c < a.rep_chunk[r + 1]; c += 32) v += __ldcg(&a.part[c * NQ + qq]);
-    v = warp_sum(v);
-    if (lane == 0) red[pq] = v;
+  for (int r = wid; r < a.nrep; r += nw) {
+    double v[NQ] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int c = a.rep_chunk[r] + lane; c < a.rep_chunk[r + 1]; c += 32) {
+      const double2* src = (const double2*)(a.part + (size_t)c * NQ);
+#pragma unroll
+      for (int q = 0; q < NQ / 2; ++q) {
+        const double2 t = __ldcg(src + q);
+        v[2 * q] += t.x;
+        v[2 * q + 1] += t.y;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
+    if (lane < NQ) {
+      double o = v[0];
+#pragma unroll
+      for (int q = 1; q < NQ; ++q) o = lane == q ? v[q] : o;
+      red[r * NQ + lane] = o;
+    }
   }
   __syncthreads();
 }
 
-// block-level partial sums of NQ values -> part[chunk*NQ + q] (fixed reduction order)
+// block-level partial sums of NQ values held by lane 0 of each warp (the lane that does
+// the row's scalar work) -> part[chunk*NQ + q], summed over warps in a fixed order
 __device__ __forceinline__ void block_partials(double* vals, double* part, int chunk) {
   __shared__ double sh[32][NQ];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int q = 0; q < NQ; ++q) vals[q] = warp_sum(vals[q]);
   if (lane == 0)
+#pragma unroll
     for (int q = 0; q < NQ; ++q) sh[wid][q] = vals[q];
   __syncthreads();
   if (threadIdx.x < NQ) {
@@ -126,33 +147,50 @@ __device__ __forceinline__ void block_partials(double* vals, double* part, int c
 // path: H and v in FP32, FP32 products and per-lane partial sums (about 13 terms per
 // lane), lanes combined in FP64 -- FP64 work per row drops from 2 per entry to ~10.
 template <typename R>
-__device__ __forceinline__ void spmv_row(const CG<R>& a, int i, const double* vs, const double* vt, const float* vsf,
-                                         const float* vtf, double& hs, double& ht) {
+__device__ __forceinline__ void spmv_part(const int* cnt, const int* col, const R* H, int cap, int i, const double* vs,
+                                          const double* vt, const float* vsf, const float* vtf, double& s1, double& t1) {
   const int lane = threadIdx.x & 31;
-  const int row = i * a.cap, nf = a.cnt[i];
-  double s1, t1;
+  const int row = i * cap, nf = cnt[i];
   if (sizeof(R) == 4) {
+    // each lane takes 4 consecutive entries per pass (one int4 + one float4 load: rows start
+    // at multiples of 32 entries, so 16-byte aligned), then 4 independent gathers of z
     float sf = 0.0f, tf = 0.0f;
-    for (int k = lane; k < nf; k += 32) {
-      const int j = a.col[row + k];
-      const float h = (float)a.H[row + k];
-      sf = fmaf(h, __ldcg(&vsf[j]), sf);
-      tf = fmaf(h, __ldcg(&vtf[j]), tf);
+    const int4* c4 = (const int4*)(col + row);
+    const float4* h4 = (const float4*)((const float*)H + row);
+    for (int k = 4 * lane; k < nf; k += 128) {
+      const int4 cc = __ldg(c4 + (k >> 2));
+      const float4 hh = __ldg(h4 + (k >> 2));
+      const int jj[4] = {cc.x, cc.y, cc.z, cc.w};
+      const float hv[4] = {hh.x, hh.y, hh.z, hh.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (k + u < nf) {
+          sf = fmaf(hv[u], __ldcg(&vsf[jj[u]]), sf);
+          tf = fmaf(hv[u], __ldcg(&vtf[jj[u]]), tf);
+        }
+      }
     }
-    s1 = (double)sf;
-    t1 = (double)tf;
+    s1 += (double)warp_sumf(sf);       // FP32 row reduction (H itself is FP32 here)
+    t1 += (double)warp_sumf(tf);
   } else {
-    s1 = 0.0;
-    t1 = 0.0;
     for (int k = lane; k < nf; k += 32) {
-      const int j = a.col[row + k];
-      const double h = (double)a.H[row + k];
+      const int j = col[row + k];
+      const double h = (double)H[row + k];
       s1 += h * __ldcg(&vs[j]);
       t1 += h * __ldcg(&vt[j]);
     }
   }
-  s1 = warp_sum(s1);
-  t1 = warp_sum(t1);
+}
+template <typename R>
+__device__ __forceinline__ void spmv_row(const CG<R>& a, int i, const double* vs, const double* vt, const float* vsf,
+                                         const float* vtf, double& hs, double& ht) {
+  double s1 = 0.0, t1 = 0.0;
+  spmv_part<R>(a.cntn, a.coln, a.Hn, a.capn, i, vs, vt, vsf, vtf, s1, t1);
+  spmv_part<R>(a.cnt, a.col, a.H, a.cap, i, vs, vt, vsf, vtf, s1, t1);
+  if (sizeof(R) == 8) {
+    s1 = warp_sum(s1);
+    t1 = warp_sum(t1);
+  }
   const double d = a.eta[a.type[i]];
   hs = s1 + d * __ldcg(&vs[i]);
   ht = t1 + d * __ldcg(&vt[i]);
@@ -161,7 +199,7 @@ __device__ __forceinline__ void spmv_row(const CG<R>& a, int i, const double* vs
 __device__ __forceinline__ double ldS(const double* p) { return __ldcg(p); }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_cg(CG<R> a) {
+__global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
   double* red = a.red;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* S = a.scal;
@@ -260,19 +298,20 @@ __global__ void __launch_bounds__(256) k_cg(CG<R> a) {
       const bool as = ldS(sr + S_ACT_S) > 0, at = ldS(sr + S_ACT_T) > 0;
       const double als = ldS(sr + S_AL_S), alt = ldS(sr + S_AL_T);
       double v[NQ] = {0, 0, 0, 0, 0, 0, 0, 0};
-      for (int i = a.chunk_lo[c] + threadIdx.x; i < a.chunk_lo[c + 1]; i += blockDim.x) {
-        const double e = a.eta[a.type[i]];
+      for (int i = a.chunk_lo[c] + wid; i < a.chunk_lo[c + 1]; i += nw) {
+        if (lane != 0) continue;
+        const double ie = a.ieta[a.type[i]];
         if (as) {
           a.xs[i] += als * a.ps[i];
           const double r = a.rs[i] - als * a.ws[i];
-          const double z = r / e;
+          const double z = r * ie;
           a.rs[i] = r; a.zs[i] = z; a.zsf[i] = (float)z;
           v[0] += r * z; v[2] += r * r;
         }
         if (at) {
           a.xt[i] += alt * a.pt[i];
           const double r = a.rt[i] - alt * a.wt[i];
-          const double z = r / e;
+          const double z = r * ie;
           a.rt[i] = r; a.zt[i] = z; a.ztf[i] = (float)z;
           v[1] += r * z; v[3] += r * r;
         }
@@ -310,7 +349,8 @@ __global__ void __launch_bounds__(256) k_cg(CG<R> a) {
   // ---------------- charges: mu = sum s / sum t per replica, q = s - mu t
   for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x) {
     double v[NQ] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = a.chunk_lo[c] + threadIdx.x; i < a.chunk_lo[c + 1]; i += blockDim.x) {
+    for (int i = a.chunk_lo[c] + wid; i < a.chunk_lo[c + 1]; i += nw) {
+      if (lane != 0) continue;
       v[0] += a.xs[i];
       v[1] += a.xt[i];
     }
@@ -323,7 +363,11 @@ __global__ void __launch_bounds__(256) k_cg(CG<R> a) {
   if (!ok) return;
   for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x) {
     const double mu = ldS(&S[a.chunk_rep[c] * NS + S_MU]);
-    for (int i = a.chunk_lo[c] + threadIdx.x; i < a.chunk_lo[c + 1]; i += blockDim.x) a.q[i] = a.xs[i] - mu * a.xt[i];
+    for (int i = a.chunk_lo[c] + threadIdx.x; i < a.chunk_lo[c + 1]; i += blockDim.x) {
+      const double qi = a.xs[i] - mu * a.xt[i];
+      a.q[i] = qi;
+      a.qf[i] = (float)qi;
+    }
   }
 }
 
@@ -364,16 +408,18 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   a.tol2 = tol * tol;
   a.type = s.type; a.rep = s.rep;
   a.cnt = f.cnt; a.col = f.j; a.H = (const R*)f.H; a.cap = f.cap;
+  a.cntn = f.cntn; a.coln = f.jn; a.Hn = (const R*)f.Hn; a.capn = f.capn;
   a.eta = eta; a.chi = chi;
   a.xs = Q.s; a.xt = Q.t; a.rs = Q.r_s; a.rt = Q.r_t; a.zs = Q.z_s; a.zt = Q.z_t;
   a.ps = Q.p_s; a.pt = Q.p_t; a.ws = Q.w_s; a.wt = Q.w_t;
   a.zsf = Q.zf_s; a.ztf = Q.zf_t;
-  a.q = s.q; a.part = Q.part; a.red = Q.red; a.scal = Q.scal;
+  a.q = s.q; a.qf = s.qf; a.part = Q.part; a.red = Q.red; a.scal = Q.scal;
+  a.ieta = Q.ieta;
   a.chunk_lo = Q.chunk_lo; a.chunk_rep = Q.chunk_rep; a.rep_chunk = Q.rep_chunk;
   a.iters = Q.iters; a.bar = Q.bar; a.err = s.err;
   cudaMemsetAsync(Q.bar, 0, sizeof(GridBar), L.st);
   void* args[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_cg<R>, dim3(Q.grid), dim3(256), args, 0, L.st);
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_cg<R>, dim3(Q.grid), dim3(1024), args, 0, L.st);
   *L.count += 2;
   return e == cudaSuccess ? 0 : -1;
 }
@@ -393,9 +439,9 @@ void qeq_push_history(const Launch& L, int n, QeqState& Q) {
 
 int qeq_grid_size(int nsm) {
   int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_cg<double>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_cg<double>, 1024, 0);
   int per_f = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, (const void*)k_cg<float>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, (const void*)k_cg<float>, 1024, 0);
   if (per_f < per) per = per_f;
   if (per < 1) per = 1;
   return nsm * per;

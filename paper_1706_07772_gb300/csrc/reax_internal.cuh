@@ -31,7 +31,7 @@ enum { T_BOND = 0, T_LP, T_OVER, T_UNDER, T_VAL, T_PEN, T_COA, T_TORS, T_CONJ, T
 
 // error flag bits (device-side, read by the host after a stage)
 enum { ERR_CAP_FAR = 1, ERR_CAP_BOND = 2, ERR_CAP_HB = 4, ERR_TIMEOUT = 8, ERR_NAN = 16,
-       ERR_CG = 32 };
+       ERR_CG = 32, ERR_CAP_NEAR = 64, ERR_CAP_CAND = 128 };
 
 constexpr double FIX_SCALE = 4294967296.0;         // 2^32
 constexpr double FIX_INV = 1.0 / 4294967296.0;
@@ -79,7 +79,21 @@ struct Sys {                   // per-atom and per-replica state
   double *vx, *vy, *vz;
   unsigned long long *fx, *fy, *fz;   // fixed-point force accumulators
   double* q;
+  float* qf;                   // FP32 copy of q (mixed-path nonbonded)
   int* err;
+  int* img;                    // [3n] box crossings since the last candidate-list build
+  double* xb;                  // [3n] wrapped positions at the last candidate-list build
+  int* rebuild;                // device flag: rebuild the candidate list this step
+};
+
+// Verlet-skin candidate list: every (j, image) within r_nb + skin at the last build
+struct CandList {
+  int cap;
+  int* cnt;
+  int* j;
+  uint8_t* s;
+  float rc2;                   // (r_nb + skin)^2 plus a rounding margin
+  double half_skin2;           // (skin / 2)^2: rebuild when an atom moved farther
 };
 
 struct Cells {
@@ -94,12 +108,21 @@ struct Cells {
   int* tmp;                    // [n] scatter scratch
 };
 
+// Far list. Context path: every row is split into a near part (r < r_bond, the bond
+// candidates; capn, cntn, jn, sn, Hn) and a far part (r_bond <= r < r_nb; cap, cnt, j, s,
+// H). The allocation-free builder fills only the single (unsplit) part.
 struct FarList {
   int cap;
   int* cnt;                    // [n]
   int* j;                      // [n*cap]
   uint8_t* s;                  // [n*cap]
   void* H;                     // [n*cap] of R: QEq matrix off-diagonal entries
+  int capn;
+  int* cntn;
+  int* jn;
+  uint8_t* sn;
+  void* Hn;
+  double r2_nb, r2_bond;       // squared cutoffs (precomputed on the host)
 };
 
 struct BondList {
@@ -153,6 +176,15 @@ __device__ __forceinline__ void fix_add(unsigned long long* p, double v, int* er
   long long f = fix_of(v, err);
   if (f != 0) atomicAdd(p, (unsigned long long)f);
 }
+// FP32 value -> fixed point without FP64 instructions: v * 2^32 is exact in FP32
+__device__ __forceinline__ void fix_add(unsigned long long* p, float v, int* err) {
+  if (!(fabsf(v) < (float)FIX_LIMIT)) {
+    atomicOr(err, ERR_NAN);
+    return;
+  }
+  const long long f = __float2ll_rn(v * 4294967296.0f);
+  if (f != 0) atomicAdd(p, (unsigned long long)f);
+}
 __device__ __forceinline__ double fix_get(const unsigned long long* p) {
   return (double)(long long)(*p) * FIX_INV;
 }
@@ -162,6 +194,27 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// Deterministic warp sum of FP32 lane partials in float-float (TwoSum) arithmetic: only
+// FP32 instructions (GB300 runs FP64 at 1/64 of the FP32 rate, and an FP64 butterfly
+// costs 5 FP64 adds in every lane); exact to ~2^-48 of the partials. The same value
+// in every lane (the error term of a TwoSum is unique, so the butterfly is symmetric).
+__device__ __forceinline__ double warp_sum_ff(float v) {
+  float hi = v, lo = 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = __fadd_rn(hi, ohi);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(ohi, bb));
+    lo = __fadd_rn(__fadd_rn(lo, olo), e);
+    hi = s;
+  }
+  return (double)hi + (double)lo;
+}
+// warp sum of a per-lane partial in the path precision, combined to FP64
+__device__ __forceinline__ double warp_sum_d(float v) { return warp_sum_ff(v); }
+__device__ __forceinline__ double warp_sum_d(double v) { return warp_sum(v); }
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -189,6 +242,12 @@ __device__ __forceinline__ double m_acos(double x) { return acos(x); }
 __device__ __forceinline__ float m_acos(float x) { return acosf(x); }
 __device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
 __device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
+// MUFU-based fast variants (FP32) for far pairs whose contributions are small; the
+// FP64 path keeps the accurate functions
+__device__ __forceinline__ double f_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float f_pow(float x, float y) { return __powf(x, y); }
+__device__ __forceinline__ double f_exp(double x) { return exp(x); }
+__device__ __forceinline__ float f_exp(float x) { return __expf(x); }
 // exp with the argument capped so FP32 never overflows to inf (inf*0 -> NaN in the
 // derivative products); the cap is far beyond any value that changes an FP64 result
 template <typename R> __device__ __forceinline__ R exp_cap_arg();
@@ -332,6 +391,17 @@ void cells_build(const Launch& L, Sys s, Cells c);
 template <typename R>
 void far_list(const Launch& L, Sys s, Cells c, FarList f, const DParams<R>* P, float margin);
 template <typename R>
+void far_list_split(const Launch& L, Sys s, Cells c, FarList f, const DParams<R>* P, float margin,
+                    float margin_near);
+void charges_to_f32(const Launch& L, Sys s);
+// skin list: float position copies (every step), displacement check, conditional cell
+// binning + candidate build, exact per-step filter into the near/far rows
+void positions_f32(const Launch& L, Sys s);
+void skin_check(const Launch& L, Sys s, CandList cl);
+void cand_build(const Launch& L, Sys s, Cells c, CandList cl);
+template <typename R>
+void cand_filter(const Launch& L, Sys s, CandList cl, FarList f, const DParams<R>* P, float margin, float margin_near);
+template <typename R>
 void bond_list(const Launch& L, Sys s, FarList f, BondList b, HbList h, AtomQ a, const DParams<R>* P,
                const DParams<double>* Pd);
 void bond_mirror(const Launch& L, Sys s, BondList b);
@@ -379,6 +449,7 @@ struct QeqState {
   int nhist, hist_pos;
   double *r_s, *r_t, *p_s, *p_t, *w_s, *w_t, *z_s, *z_t, *u_s, *u_t;
   float *zf_s, *zf_t;          // FP32 copies of z (mixed-path SpMV)
+  const double* ieta;          // 1/eta per type
   double* part;                // chunk partials
   double* red;                 // per-replica reductions
   double* scal;                // per-replica scalars

@@ -45,7 +45,8 @@ class Options(C.Structure):
     _fields_ = [("r_nb", C.c_double), ("r_bond", C.c_double), ("r_hb", C.c_double), ("bo_cut", C.c_double),
                 ("thb_cut", C.c_double), ("thb_cutsq", C.c_double), ("hb_bo_min", C.c_double),
                 ("qeq_tol", C.c_double), ("qeq_max_iter", C.c_int32), ("precision", C.c_int32),
-                ("warm_start", C.c_int32), ("term_mask", C.c_int32), ("capacity_margin", C.c_double)]
+                ("warm_start", C.c_int32), ("term_mask", C.c_int32), ("capacity_margin", C.c_double),
+                ("skin", C.c_double)]
 
 
 class ReaxFFError(RuntimeError):
@@ -139,7 +140,8 @@ def make_params(p: dict) -> Params:
     return P
 
 
-def make_options(o: dict, precision=FP64, warm_start=WARM_EXTRAP, term_mask=0, capacity_margin=0.0) -> Options:
+def make_options(o: dict, precision=FP64, warm_start=WARM_EXTRAP, term_mask=0, capacity_margin=0.0,
+                 skin=0.0) -> Options:
     O = Options()
     for k in ("r_nb", "r_bond", "r_hb", "bo_cut", "thb_cut", "thb_cutsq", "hb_bo_min", "qeq_tol"):
         setattr(O, k, float(o[k]))
@@ -148,6 +150,7 @@ def make_options(o: dict, precision=FP64, warm_start=WARM_EXTRAP, term_mask=0, c
     O.warm_start = int(warm_start)
     O.term_mask = int(term_mask)
     O.capacity_margin = float(capacity_margin)
+    O.skin = float(o.get("skin", skin))
     return O
 
 
@@ -188,10 +191,10 @@ class ReaxFF:
     """One library context (single system or a batch of replicas)."""
 
     def __init__(self, params: dict, types, box, options: dict, precision=FP64, warm_start=WARM_EXTRAP,
-                 term_mask=0, rep_offsets=None, capacity_margin=0.0):
+                 term_mask=0, rep_offsets=None, capacity_margin=0.0, skin=0.0):
         self.lib = load()
         P = make_params(params)
-        O = make_options(options, precision, warm_start, term_mask, capacity_margin)
+        O = make_options(options, precision, warm_start, term_mask, capacity_margin, skin)
         self.types = np.ascontiguousarray(types, np.int32)
         if rep_offsets is None:
             self.h = reaxff_create(P, self.types, np.asarray(box, float).reshape(3), O)

@@ -268,3 +268,28 @@ def test_batched_replicas_match_single_runs(rx, params):
         assert np.allclose(Eb[r], E[0], rtol=1e-9, atol=1e-8)
         c.close()
     cb.close()
+
+
+@pytest.mark.parametrize("skin", [0.02, 1.0, -1.0])
+def test_lists_stay_exact_along_md(rx, params, skin):
+    """After MD steps that move atoms across box faces (hot start) the far, bond and
+    H-bond lists of the running context equal the oracle's lists at the final positions,
+    with the skin candidate list rebuilt often (0.02 A), rarely (1 A) or not used (< 0)."""
+    w = synth.workload("cluster300", temperature=3000.0)
+    n = len(w["x"])
+    c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=1, skin=skin)
+    c.set_state(w["x"], w["v"])
+    c.step(30, 0.5)
+    x, _, _ = c.get_state()
+    L = oracle.build_lists(x, w["types"], w["box"], params, w["options"])
+    B = L["bond"]
+    want = {
+        rx.LIST_FAR: keyset(L["far"]["i"], L["far"]["j"], L["far"]["s"], n),
+        rx.LIST_BOND: keyset(np.concatenate([B["i"], B["j"]]), np.concatenate([B["j"], B["i"]]),
+                             np.concatenate([B["s"], -B["s"]]), n),
+        rx.LIST_HBOND: keyset(L["hbond"]["i"], L["hbond"]["j"], L["hbond"]["s"], n),
+    }
+    for which, k in want.items():
+        got = keyset(*c.get_lists(which), n)
+        assert np.array_equal(got, k), which
+    c.close()
