@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "reax_internal.cuh"
@@ -556,11 +557,9 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   // ---- QEq state and chunking (chunks never straddle replicas)
   rx::QeqState& Q = ctx->Q;
   Q.grid = rx::qeq_grid_size(ctx->nsm);
-  double** qf[] = {&Q.s, &Q.t, &Q.r_s, &Q.r_t, &Q.p_s, &Q.p_t, &Q.w_s, &Q.w_t, &Q.z_s, &Q.z_t};
-  for (double** p : qf) *p = B.alloc<double>(n);
-  Q.u_s = Q.u_t = nullptr;
-  Q.zf_s = B.alloc<float>(n);
-  Q.zf_t = B.alloc<float>(n);
+  Q.s = B.alloc<double>(n);
+  Q.t = B.alloc<double>(n);
+  Q.zg = B.alloc<double>(2 * (size_t)n);
   Q.hist_s = B.alloc<double>(4 * (size_t)n);
   Q.hist_t = B.alloc<double>(3 * (size_t)n);
   Q.nhist = 0;
@@ -580,7 +579,20 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   int* crep_d = B.alloc<int>(crep.size());
   int* rchunk_d = B.alloc<int>(nrep + 1);
   Q.chunk_lo = clo_d; Q.chunk_rep = crep_d; Q.rep_chunk = rchunk_d;
-  Q.part = B.alloc<double>((size_t)Q.nchunk * 8);
+  Q.part = B.alloc<double>((size_t)Q.nchunk * 2 * 8);
+  {
+    // rows per block (block b owns chunks b, b + grid, ...); shared memory when it fits
+    std::vector<int> rowsb(Q.grid, 0);
+    for (int c = 0; c < Q.nchunk; ++c) rowsb[c % Q.grid] += clo[c + 1] - clo[c];
+    Q.rows_blk = *std::max_element(rowsb.begin(), rowsb.end());
+    const size_t sc = (size_t)(nrep * rx::QEQ_SCAL_PER_REP + 4) * sizeof(double);
+    const size_t st = (size_t)rx::QEQ_NV_STATE * Q.rows_blk * sizeof(double);
+    Q.scal_smem = sc <= (size_t)rx::QEQ_SMEM_MAX / 2;
+    Q.state_smem = (Q.scal_smem ? sc : 0) + st <= (size_t)rx::QEQ_SMEM_MAX;
+    Q.smem_bytes = (int)((Q.scal_smem ? sc : 0) + (Q.state_smem ? st : 0));
+    Q.scal = Q.scal_smem ? nullptr : B.alloc<double>((size_t)Q.grid * (nrep * rx::QEQ_SCAL_PER_REP + 4));
+    Q.state = Q.state_smem ? nullptr : B.alloc<double>((size_t)Q.grid * rx::QEQ_NV_STATE * Q.rows_blk);
+  }
   // reduction chunks (<= 4096 atoms each, per replica)
   std::vector<int> rlo, rrep(nrep + 1, 0);
   for (int r = 0; r < nrep; ++r) {
@@ -595,8 +607,6 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   ctx->red.chunk_lo = rlo_d;
   ctx->red.rep_chunk = rrep_d;
   ctx->red.part = B.alloc<double>((size_t)ctx->red.nchunk * 20);
-  Q.red = B.alloc<double>((size_t)nrep * 8);
-  Q.scal = B.alloc<double>((size_t)nrep * 16 + 1);
   Q.iters = B.alloc<int>(2 * nrep);
   Q.bar = B.alloc<GridBar>(1);
   if (B.err != cudaSuccess) {

@@ -10,27 +10,41 @@
 // GPU form: one persistent cooperative kernel runs the whole solve. Per iteration:
 //   A: u = H z (both systems in one read of H), p = z + beta p, w = u + beta w, p.w
 //   B: x += alpha p, r -= alpha w, z = r / eta, r.z and r.r
-// (w = H p is carried as H z + beta w, so H is read once per iteration.) Each phase ends
-// in a grid barrier whose last-arriving block reduces the per-chunk partial dot products
-// per replica in a fixed order (deterministic) and publishes alpha, beta and the
-// convergence flags. Convergence per system and replica: ||r||_2 <= tol ||b||_2; a
-// converged system freezes while the other continues. Barrier waits are bounded.
+// (w = H p is carried as H z + beta w, so H is read once per iteration.) Each phase writes
+// per-chunk partial dot products and ends in a grid barrier; after it every block reduces
+// all partials itself, in one fixed order, so every block holds bit-identical alpha, beta
+// and convergence flags without a second synchronisation (the partials are double-
+// buffered: a block that runs ahead writes the other buffer). Convergence per system and
+// replica: ||r||_2 <= tol ||b||_2; a converged system freezes while the other continues.
+// Barrier waits are bounded.
+//
+// GB300 runs FP64 at 1/64 of the FP32 rate: about two FP64 operations per clock per SM,
+// so one FP64 warp instruction holds the SM's FP64 pipe for ~16 cycles whatever its active
+// lanes. The kernel therefore keeps FP64 to the per-row vector updates, packed densely
+// (thread t <-> row t of the block, so ~rows/32 warps issue them), and to a few
+// multi-value warp reductions; the SpMV itself runs in the path precision with its row
+// sums left in shared memory until the dense update reads them.
 #include "reax_internal.cuh"
 
 namespace {
 
-constexpr int NQ = 8;          // partial sums per chunk
+constexpr int NQ = 8;          // partial-sum slots per chunk
 constexpr int NS = 16;         // scalars per replica
 // scalar slots per replica
 enum { S_RHO_S = 0, S_RHO_T, S_AL_S, S_AL_T, S_BE_S, S_BE_T, S_BB_S, S_BB_T, S_ACT_S, S_ACT_T, S_MU };
+// row state of a block (doubles per row; U holds the SpMV row sums as two values of the
+// path type)
+enum { V_XS = 0, V_XT, V_RS, V_RT, V_PS, V_PT, V_WS, V_WT, V_ZS, V_ZT, V_ETA, V_IETA, V_U, V_U2, NV_STATE };
+static_assert(NV_STATE == rx::QEQ_NV_STATE, "row state layout");
+static_assert(NS + NQ == rx::QEQ_SCAL_PER_REP, "scalar layout");
+constexpr int MAXC = 32;       // chunk bounds cached in shared memory per block
 
 template <typename R>
 struct CG {
   int n, nrep, nchunk, max_iter;
   double tol2;
   const int* type;
-  const int* rep;
-  const int* cnt;
+  const int* cnt;                          // far part of each row (r_bond <= r < r_nb)
   const int* col;
   const R* H;
   int cap;
@@ -39,13 +53,15 @@ struct CG {
   const R* Hn;
   int capn;
   const double *eta, *chi, *ieta;          // per type (double); ieta = 1/eta
-  double *xs, *xt, *rs, *rt, *zs, *zt, *ps, *pt, *ws, *wt;
-  float *zsf, *ztf;                        // FP32 copies of z for the FP32-arithmetic SpMV
+  double *xs, *xt;                         // initial guess in, solutions out
+  void* zg;                                // interleaved (s, t) SpMV operand: float2 or double2
   double* q;
   float* qf;
-  double* part;                            // [nchunk*NQ]
-  double* red;                             // [nrep*NQ]
-  double* scal;                            // [nrep*NS + 1]
+  double* part;                            // [2][NQ][nchunk] chunk partials, two buffers
+  double* scal;                            // [grid][nrep*(NS+NQ)+4] scalars, unless in shared memory
+  double* state;                           // [grid][NV_STATE][rows_blk] row state, unless in shared memory
+  int rows_blk;                            // most rows any block owns
+  int scal_smem, state_smem;               // 1: kept in dynamic shared memory
   const int* chunk_lo;                     // [nchunk+1] rows
   const int* chunk_rep;                    // [nchunk]
   const int* rep_chunk;                    // [nrep+1] chunk ranges per replica
@@ -54,321 +70,476 @@ struct CG {
   int* err;
 };
 
-// grid barrier; the last block to arrive runs `reduce` (whole block) before releasing
-template <typename F>
-__device__ bool barrier_reduce(GridBar* bar, int* err, F reduce) {
-  __shared__ int s_last;
-  __shared__ unsigned s_gen;
+// bounded grid barrier (all blocks co-resident: cooperative launch)
+__device__ bool grid_barrier(GridBar* bar, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned g = *((volatile unsigned*)&bar->gen);
+    const unsigned g = *((volatile unsigned*)&bar->gen);
     __threadfence();
-    unsigned a = atomicAdd(&bar->arrive, 1u);
-    s_last = (a == gridDim.x - 1);
-    s_gen = g;
-  }
-  __syncthreads();
-  bool ok = true;
-  if (s_last) {
-    __threadfence();
-    reduce();
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    const unsigned arrived = atomicAdd(&bar->arrive, 1u);
+    if (arrived == gridDim.x - 1) {
       bar->arrive = 0;
       __threadfence();
       atomicAdd(&bar->gen, 1u);
-    }
-  } else {
-    if (threadIdx.x == 0) {
+    } else {
       long long spins = 0;
-      while (*((volatile unsigned*)&bar->gen) == s_gen) {
+      while (*((volatile unsigned*)&bar->gen) == g) {
         if (++spins > BAR_SPIN_LIMIT) {
           atomicOr(err, ERR_TIMEOUT);
           break;
         }
-        __nanosleep(64);
-      }
-      __threadfence();
-    }
-  }
-  __syncthreads();
-  if (*((volatile int*)err) & ERR_TIMEOUT) ok = false;
-  return ok;
-}
-
-// last-block reduction of chunk partials into red[r*NQ+q]: one warp per replica, each
-// lane sums whole chunks (all NQ slots, contiguous) in a fixed order, then the lanes are
-// combined by a fixed butterfly (deterministic)
-template <typename R>
-__device__ void reduce_parts(const CG<R>& a, double* red) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = wid; r < a.nrep; r += nw) {
-    double v[NQ] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int c = a.rep_chunk[r] + lane; c < a.rep_chunk[r + 1]; c += 32) {
-      const double2* src = (const double2*)(a.part + (size_t)c * NQ);
-#pragma unroll
-      for (int q = 0; q < NQ / 2; ++q) {
-        const double2 t = __ldcg(src + q);
-        v[2 * q] += t.x;
-        v[2 * q + 1] += t.y;
+        __nanosleep(32);
       }
     }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
-    if (lane < NQ) {
-      double o = v[0];
-#pragma unroll
-      for (int q = 1; q < NQ; ++q) o = lane == q ? v[q] : o;
-      red[r * NQ + lane] = o;
-    }
+    __threadfence();
   }
   __syncthreads();
+  return !(*((volatile int*)err) & ERR_TIMEOUT);
 }
 
-// block-level partial sums of NQ values held by lane 0 of each warp (the lane that does
-// the row's scalar work) -> part[chunk*NQ + q], summed over warps in a fixed order
-__device__ __forceinline__ void block_partials(double* vals, double* part, int chunk) {
-  __shared__ double sh[32][NQ];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) sh[wid][q] = vals[q];
-  __syncthreads();
-  if (threadIdx.x < NQ) {
-    double v = 0.0;
-    for (int w = 0; w < nw; ++w) v += sh[w][threadIdx.x];
-    part[chunk * NQ + threadIdx.x] = v;
-  }
-  __syncthreads();
-}
-
-// (H v)_i for the two systems, warp per row. FP64 path: FP64 products and sums. Mixed
-// path: H and v in FP32, FP32 products and per-lane partial sums (about 13 terms per
-// lane), lanes combined in FP64 -- FP64 work per row drops from 2 per entry to ~10.
-template <typename R>
-__device__ __forceinline__ void spmv_part(const int* cnt, const int* col, const R* H, int cap, int i, const double* vs,
-                                          const double* vt, const float* vsf, const float* vtf, double& s1, double& t1) {
+// Sum NVP values (a power of two) over the 32 lanes with NVP - 1 + 5 - log2(NVP) FP64 adds
+// per lane instead of 5 NVP: each exchange step halves the values a lane keeps (the lower
+// lane of a pair keeps the first half, the upper the second), then plain butterflies
+// finish. Returns the total of slot `slot`, the same on all 32/NVP lanes of a group (IEEE
+// addition commutes, so partners agree bit for bit). Fixed order: deterministic.
+template <int NVP>
+__device__ __forceinline__ double warp_reduce_multi(double* v, int& slot) {
   const int lane = threadIdx.x & 31;
-  const int row = i * cap, nf = cnt[i];
-  if (sizeof(R) == 4) {
-    // each lane takes 4 consecutive entries per pass (one int4 + one float4 load: rows start
-    // at multiples of 32 entries, so 16-byte aligned), then 4 independent gathers of z
-    float sf = 0.0f, tf = 0.0f;
-    const int4* c4 = (const int4*)(col + row);
-    const float4* h4 = (const float4*)((const float*)H + row);
-    for (int k = 4 * lane; k < nf; k += 128) {
-      const int4 cc = __ldg(c4 + (k >> 2));
-      const float4 hh = __ldg(h4 + (k >> 2));
-      const int jj[4] = {cc.x, cc.y, cc.z, cc.w};
-      const float hv[4] = {hh.x, hh.y, hh.z, hh.w};
+  slot = 0;
+  int s = 16;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (k + u < nf) {
-          sf = fmaf(hv[u], __ldcg(&vsf[jj[u]]), sf);
-          tf = fmaf(hv[u], __ldcg(&vtf[jj[u]]), tf);
-        }
-      }
+  for (int c = NVP; c > 1; c >>= 1, s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int k = 0; k < c / 2; ++k) {
+      const double send = up ? v[k] : v[k + c / 2];
+      const double keep = up ? v[k + c / 2] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, s);
     }
-    s1 += (double)warp_sumf(sf);       // FP32 row reduction (H itself is FP32 here)
-    t1 += (double)warp_sumf(tf);
-  } else {
-    for (int k = lane; k < nf; k += 32) {
-      const int j = col[row + k];
-      const double h = (double)H[row + k];
-      s1 += h * __ldcg(&vs[j]);
-      t1 += h * __ldcg(&vt[j]);
-    }
+    slot = 2 * slot + (up ? 1 : 0);
   }
+  double t = v[0];
+#pragma unroll
+  for (; s > 0; s >>= 1) t += __shfl_xor_sync(0xffffffffu, t, s);
+  return t;
 }
-template <typename R>
-__device__ __forceinline__ void spmv_row(const CG<R>& a, int i, const double* vs, const double* vt, const float* vsf,
-                                         const float* vtf, double& hs, double& ht) {
-  double s1 = 0.0, t1 = 0.0;
-  spmv_part<R>(a.cntn, a.coln, a.Hn, a.capn, i, vs, vt, vsf, vtf, s1, t1);
-  spmv_part<R>(a.cnt, a.col, a.H, a.cap, i, vs, vt, vsf, vtf, s1, t1);
-  if (sizeof(R) == 8) {
-    s1 = warp_sum(s1);
-    t1 = warp_sum(t1);
+template <int NV> struct Pow2 { static constexpr int v = NV <= 1 ? 1 : NV <= 2 ? 2 : NV <= 4 ? 4 : 8; };
+
+// per-replica totals of the first NV slots of partial buffer pb -> red[r*NQ + q]: one warp
+// per replica, lane l sums chunks l, l+32, ... in order, then one multi-value butterfly
+// (every block computes bit-identical totals)
+template <int NV, typename R>
+__device__ __forceinline__ void reduce_parts(const CG<R>& a, int pb, double* red) {
+  constexpr int NVP = Pow2<NV>::v;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* P = a.part + (size_t)pb * NQ * a.nchunk;
+  for (int r = wid; r < a.nrep; r += nw) {
+    double v[NVP];
+#pragma unroll
+    for (int q = 0; q < NVP; ++q) v[q] = 0.0;
+    for (int c = a.rep_chunk[r] + lane; c < a.rep_chunk[r + 1]; c += 32)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) v[q] += __ldcg(P + (size_t)q * a.nchunk + c);
+    int slot;
+    const double t = warp_reduce_multi<NVP>(v, slot);
+    if ((lane & (32 / NVP - 1)) == 0 && slot < NV) red[r * NQ + slot] = t;
   }
-  const double d = a.eta[a.type[i]];
-  hs = s1 + d * __ldcg(&vs[i]);
-  ht = t1 + d * __ldcg(&vt[i]);
+  __syncthreads();
 }
 
-__device__ __forceinline__ double ldS(const double* p) { return __ldcg(p); }
+// chunk partial sums of NV per-thread values -> part[pb][q][chunk]. Threads hold values
+// only for rows t < nr (dense map), so warps past the last row contribute zeros without
+// arithmetic; warp totals are combined by warp 0 in warp order (deterministic).
+template <int NV, typename R>
+__device__ __forceinline__ void block_sum(const CG<R>& a, double* v, int nr, int pb, int chunk) {
+  constexpr int NVP = Pow2<NV>::v;
+  __shared__ double sh[32][NVP];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double w[NVP];
+#pragma unroll
+  for (int q = 0; q < NVP; ++q) w[q] = q < NV ? v[q] : 0.0;
+  if (wid * 32 < nr) {
+    int slot;
+    const double t = warp_reduce_multi<NVP>(w, slot);
+    if ((lane & (32 / NVP - 1)) == 0) sh[wid][slot] = t;
+  } else if (lane < NVP) {
+    sh[wid][lane] = 0.0;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    double u[NVP];
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NVP; ++q) u[q] = lane < nw ? sh[lane][q] : 0.0;
+    int slot;
+    const double t = warp_reduce_multi<NVP>(u, slot);
+    if ((lane & (32 / NVP - 1)) == 0 && slot < NV) a.part[((size_t)pb * NQ + slot) * a.nchunk + chunk] = t;
+  }
+  __syncthreads();
+}
+
+// (H v)_i for the two systems, warp per row, both right-hand sides gathered in one load of
+// the interleaved copy zg[j] = (v_s[j], v_t[j]). Lane l takes entries l, l+32, l+64, l+96 of
+// each 128-entry group: the column and H loads of a group are coalesced, and the gathers of
+// one load instruction fall on 32 consecutive list entries (a few neighbouring cells, so a
+// few cache lines). The next group's column/H loads are issued before this group's
+// multiply-adds. Padding lanes gather zg[i] with h = 0 (adds an exact zero).
+// FP64 path: FP64 products and sums. Mixed path: H and zg in FP32, FP32 products and
+// per-lane partial sums (about 13 terms per lane), lanes combined by an FP32 butterfly.
+template <typename R> struct G2;
+template <> struct G2<float> { using T = float2; };
+template <> struct G2<double> { using T = double2; };
+
+__device__ __forceinline__ float fmaR(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaR(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float warp_total(float v) { return warp_sumf(v); }
+__device__ __forceinline__ double warp_total(double v) { return warp_sum(v); }
+
+// streamed matrix loads: read-only for the kernel's lifetime, kept out of L1 (the L1 holds
+// the gathered vector)
+__device__ __forceinline__ int ld_stream(const int* p) {
+  int v;
+  asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p) {
+  double v;
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
+template <typename R>
+__device__ __forceinline__ void spmv_part(const int* cnt, const int* col, const R* H, int cap, int i,
+                                          const typename G2<R>::T* zg, R& sf, R& tf) {
+  using T = typename G2<R>::T;
+  const int lane = threadIdx.x & 31;
+  const int* cr = col + (size_t)i * cap;
+  const R* hr = H + (size_t)i * cap;
+  const int nf = ld_stream(cnt + i);
+  int j[4];
+  R h[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int k = lane + 32 * u;
+    j[u] = i;
+    h[u] = R(0);
+    if (k < nf) {
+      j[u] = ld_stream(cr + k);
+      h[u] = ld_stream(hr + k);
+    }
+  }
+  for (int k0 = 0; k0 < nf; k0 += 128) {
+    T z[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) z[u] = zg[j[u]];
+    int jn[4];
+    R hn[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + 128 + lane + 32 * u;
+      jn[u] = i;
+      hn[u] = R(0);
+      if (k < nf) {
+        jn[u] = ld_stream(cr + k);
+        hn[u] = ld_stream(hr + k);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      sf = fmaR(h[u], z[u].x, sf);
+      tf = fmaR(h[u], z[u].y, tf);
+      j[u] = jn[u];
+      h[u] = hn[u];
+    }
+  }
+}
+
+// where a block keeps its per-replica scalars and the CG vectors of its rows: shared
+// memory when they fit (the host decides), else a block-private global region. Either way
+// only this block reads or writes them, so no value crosses blocks except through zg and
+// the chunk partials.
+struct Blk {
+  double* S;                   // [nrep*NS + 4] scalars, then [nrep*NQ] reduced totals
+  double* red;
+  double* st;                  // [NV_STATE][rows] row state (structure of arrays)
+  int rows;
+  __device__ __forceinline__ double& v(int k, int li) const { return st[k * rows + li]; }
+  template <typename R>
+  __device__ __forceinline__ R* u(int sys) const { return (R*)(st + V_U * rows) + sys * rows; }
+};
+
+// off-diagonal SpMV of the chunk's rows into this block's U arrays (path precision). Warp w
+// owns a contiguous run of rows (neighbouring atoms, so its gathers share cache lines).
+template <typename R>
+__device__ __forceinline__ void spmv_chunk(const CG<R>& a, const Blk& B, int lo, int hi, int off) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int rpw = (hi - lo + nw - 1) / nw;
+  const int wlo = lo + wid * rpw, whi = min(hi, wlo + rpw);
+  const typename G2<R>::T* zg = (const typename G2<R>::T*)a.zg;
+  R* us = B.u<R>(0);
+  R* ut = B.u<R>(1);
+  for (int i = wlo; i < whi; ++i) {
+    R sf = 0, tf = 0;
+    spmv_part<R>(a.cntn, a.coln, a.Hn, a.capn, i, zg, sf, tf);
+    spmv_part<R>(a.cnt, a.col, a.H, a.cap, i, zg, sf, tf);
+    sf = warp_total(sf);
+    tf = warp_total(tf);
+    if (lane == 0) {
+      us[off + i - lo] = sf;
+      ut[off + i - lo] = tf;
+    }
+  }
+}
+
+template <typename R>
+struct Chunks {
+  int lo[MAXC], hi[MAXC], rep[MAXC];
+};
+template <typename R>
+__device__ __forceinline__ void chunk_of(const CG<R>& a, const Chunks<R>& C, int k, int c, int& lo, int& hi,
+                                         int& rep) {
+  if (k < MAXC) {
+    lo = C.lo[k]; hi = C.hi[k]; rep = C.rep[k];
+  } else {
+    lo = a.chunk_lo[c]; hi = a.chunk_lo[c + 1]; rep = a.chunk_rep[c];
+  }
+}
+// f(chunk, lo, hi, rep, local offset of the chunk's first row in this block's state)
+template <typename R, typename F>
+__device__ __forceinline__ void for_chunks(const CG<R>& a, const Chunks<R>& C, F&& f) {
+  int off = 0, k = 0;
+  for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x, ++k) {
+    int lo, hi, rep;
+    chunk_of(a, C, k, c, lo, hi, rep);
+    f(c, lo, hi, rep, off);
+    off += hi - lo;
+  }
+}
+// dense row map: thread t takes rows lo + t, lo + t + blockDim.x, ...
+template <typename F>
+__device__ __forceinline__ void for_rows(int lo, int hi, F&& f) {
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) f(i);
+}
+
+template <typename R>
+__device__ __forceinline__ void put_zg(const CG<R>& a, int i, double s, double t) {
+  using T = typename G2<R>::T;
+  T v;
+  v.x = (R)s;
+  v.y = (R)t;
+  ((T*)a.zg)[i] = v;
+}
+
+// total of the active flags over replicas -> S[nrep*NS] (thread 0, after the block's
+// scalar updates; fenced by __syncthreads on both sides)
+__device__ __forceinline__ void count_active(double* S, int nrep) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double act = 0;
+    for (int r = 0; r < nrep; ++r) act += S[r * NS + S_ACT_S] + S[r * NS + S_ACT_T];
+    S[nrep * NS] = act;
+  }
+  __syncthreads();
+}
 
 template <typename R>
 __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
-  double* red = a.red;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* S = a.scal;
-  // ---------------- init: r = b - H x, z = r/eta, p = w = 0 (x copied to FP32 first)
-  for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x)
-    for (int i = a.chunk_lo[c] + threadIdx.x; i < a.chunk_lo[c + 1]; i += blockDim.x) {
-      a.zsf[i] = (float)a.xs[i];
-      a.ztf[i] = (float)a.xt[i];
+  extern __shared__ double dsm[];
+  __shared__ Chunks<R> C;
+  Blk B;
+  const int sc = a.nrep * (NS + NQ) + 4;
+  B.S = a.scal_smem ? dsm : a.scal + (size_t)blockIdx.x * sc;
+  B.red = B.S + a.nrep * NS + 4;
+  B.rows = a.rows_blk;
+  B.st = a.state_smem ? dsm + (a.scal_smem ? sc : 0) : a.state + (size_t)blockIdx.x * NV_STATE * a.rows_blk;
+  for (int k = threadIdx.x; k < MAXC; k += blockDim.x) {
+    const int c = blockIdx.x + k * gridDim.x;
+    if (c < a.nchunk) {
+      C.lo[k] = a.chunk_lo[c]; C.hi[k] = a.chunk_lo[c + 1]; C.rep[k] = a.chunk_rep[c];
     }
-  bool ok0 = barrier_reduce(a.bar, a.err, []() {});
-  if (!ok0) return;
-  for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x) {
-    double v[NQ] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = a.chunk_lo[c] + wid; i < a.chunk_lo[c + 1]; i += nw) {
-      double hs, ht;
-      spmv_row(a, i, a.xs, a.xt, a.zsf, a.ztf, hs, ht);
-      if (lane == 0) {
-        const double bs = -a.chi[a.type[i]], bt = -1.0, e = a.eta[a.type[i]];
-        const double rs = bs - hs, rt = bt - ht;
-        a.rs[i] = rs; a.rt[i] = rt;
-        a.zs[i] = rs / e; a.zt[i] = rt / e;
-        a.ps[i] = 0; a.pt[i] = 0; a.ws[i] = 0; a.wt[i] = 0;
-        v[0] += rs * rs / e; v[1] += rt * rt / e;   // r.z
-        v[2] += rs * rs; v[3] += rt * rt;           // r.r
-        v[4] += bs * bs; v[5] += bt * bt;           // b.b
-      }
-    }
-    block_partials(v, a.part, c);
   }
-  bool ok = barrier_reduce(a.bar, a.err, [&]() {
-    reduce_parts(a, red);
-    for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
-      double* sr = S + r * NS;
-      const double* rd = red + r * NQ;
-      sr[S_RHO_S] = rd[0]; sr[S_RHO_T] = rd[1];
-      sr[S_BB_S] = rd[4]; sr[S_BB_T] = rd[5];
-      sr[S_BE_S] = 0; sr[S_BE_T] = 0;
-      sr[S_ACT_S] = rd[2] > a.tol2 * rd[4] ? 1.0 : 0.0;
-      sr[S_ACT_T] = rd[3] > a.tol2 * rd[5] ? 1.0 : 0.0;
-      a.iters[2 * r] = 0; a.iters[2 * r + 1] = 0;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double act = 0;
-      for (int r = 0; r < a.nrep; ++r) act += S[r * NS + S_ACT_S] + S[r * NS + S_ACT_T];
-      S[a.nrep * NS] = act;
-    }
+  const bool lead = blockIdx.x == 0;
+  int pb = 0;
+  double* S = B.S;
+  double* red = B.red;
+  // ---------------- init: eta, 1/eta and x into the row state; x into zg
+  __syncthreads();
+  for_chunks(a, C, [&](int, int lo, int hi, int, int off) {
+    for_rows(lo, hi, [&](int i) {
+      const int li = off + i - lo;
+      const int t = a.type[i];
+      const double e = a.eta[t], ie = a.ieta[t], xs = a.xs[i], xt = a.xt[i];
+      B.v(V_ETA, li) = e; B.v(V_IETA, li) = ie;
+      B.v(V_XS, li) = xs; B.v(V_XT, li) = xt;
+      put_zg(a, i, xs, xt);
+    });
   });
-  // z in FP32 for the first iteration's SpMV: written only after every block has finished
-  // the initial SpMV (which read x from the same buffer), published by one more barrier
-  if (ok) {
-    for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x)
-      for (int i = a.chunk_lo[c] + threadIdx.x; i < a.chunk_lo[c + 1]; i += blockDim.x) {
-        a.zsf[i] = (float)a.zs[i];
-        a.ztf[i] = (float)a.zt[i];
-      }
-    ok = barrier_reduce(a.bar, a.err, []() {});
+  if (!grid_barrier(a.bar, a.err)) return;
+  // r = b - H x, z = r/eta, p = w = 0
+  for_chunks(a, C, [&](int c, int lo, int hi, int, int off) {
+    spmv_chunk(a, B, lo, hi, off);
+    __syncthreads();
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    const R* us = B.u<R>(0);
+    const R* ut = B.u<R>(1);
+    for_rows(lo, hi, [&](int i) {
+      const int li = off + i - lo;
+      const double e = B.v(V_ETA, li), ie = B.v(V_IETA, li);
+      const double hs = (double)us[li] + e * B.v(V_XS, li);
+      const double ht = (double)ut[li] + e * B.v(V_XT, li);
+      const double bs = -a.chi[a.type[i]], bt = -1.0;
+      const double rs = bs - hs, rt = bt - ht;
+      B.v(V_RS, li) = rs; B.v(V_RT, li) = rt;
+      B.v(V_ZS, li) = rs * ie; B.v(V_ZT, li) = rt * ie;
+      B.v(V_PS, li) = 0; B.v(V_PT, li) = 0; B.v(V_WS, li) = 0; B.v(V_WT, li) = 0;
+      v[0] += rs * rs * ie; v[1] += rt * rt * ie;   // r.z
+      v[2] += rs * rs; v[3] += rt * rt;             // r.r
+      v[4] += bs * bs; v[5] += bt * bt;             // b.b
+    });
+    block_sum<6>(a, v, hi - lo, pb, c);
+  });
+  if (!grid_barrier(a.bar, a.err)) return;
+  reduce_parts<6>(a, pb, red);
+  pb ^= 1;
+  for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
+    double* sr = S + r * NS;
+    const double* rd = red + r * NQ;
+    sr[S_RHO_S] = rd[0]; sr[S_RHO_T] = rd[1];
+    sr[S_BB_S] = rd[4]; sr[S_BB_T] = rd[5];
+    sr[S_BE_S] = 0; sr[S_BE_T] = 0;
+    sr[S_ACT_S] = rd[2] > a.tol2 * rd[4] ? 1.0 : 0.0;
+    sr[S_ACT_T] = rd[3] > a.tol2 * rd[5] ? 1.0 : 0.0;
+    if (lead) { a.iters[2 * r] = 0; a.iters[2 * r + 1] = 0; }
   }
+  count_active(S, a.nrep);
+  // z into zg for the first iteration's SpMV: every block has finished the initial SpMV
+  // (which gathered x from the same buffer) -- the barrier above -- and the next barrier
+  // publishes it
+  for_chunks(a, C, [&](int, int lo, int hi, int, int off) {
+    for_rows(lo, hi, [&](int i) {
+      const int li = off + i - lo;
+      put_zg(a, i, B.v(V_ZS, li), B.v(V_ZT, li));
+    });
+  });
+  if (!grid_barrier(a.bar, a.err)) return;
   int it = 0;
-  while (ok && ldS(&S[a.nrep * NS]) > 0.0 && it < a.max_iter) {
+  while (S[a.nrep * NS] > 0.0 && it < a.max_iter) {
     ++it;
     // ---------------- A: u = H z; p = z + beta p; w = u + beta w; p.w
-    for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x) {
-      const double* sr = S + a.chunk_rep[c] * NS;
-      const bool as = ldS(sr + S_ACT_S) > 0, at = ldS(sr + S_ACT_T) > 0;
-      const double bes = ldS(sr + S_BE_S), bet = ldS(sr + S_BE_T);
-      double v[NQ] = {0, 0, 0, 0, 0, 0, 0, 0};
-      for (int i = a.chunk_lo[c] + wid; i < a.chunk_lo[c + 1]; i += nw) {
-        double us, ut;
-        spmv_row(a, i, a.zs, a.zt, a.zsf, a.ztf, us, ut);
-        if (lane == 0) {
-          if (as) {
-            const double p = a.zs[i] + bes * a.ps[i], w = us + bes * a.ws[i];
-            a.ps[i] = p; a.ws[i] = w; v[0] += p * w;
-          }
-          if (at) {
-            const double p = a.zt[i] + bet * a.pt[i], w = ut + bet * a.wt[i];
-            a.pt[i] = p; a.wt[i] = w; v[1] += p * w;
-          }
-        }
-      }
-      block_partials(v, a.part, c);
-    }
-    ok = barrier_reduce(a.bar, a.err, [&]() {
-      reduce_parts(a, red);
-      for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
-        double* sr = S + r * NS;
-        sr[S_AL_S] = sr[S_ACT_S] > 0 ? sr[S_RHO_S] / red[r * NQ + 0] : 0.0;
-        sr[S_AL_T] = sr[S_ACT_T] > 0 ? sr[S_RHO_T] / red[r * NQ + 1] : 0.0;
-      }
-    });
-    if (!ok) break;
-    // ---------------- B: x += alpha p; r -= alpha w; z = r / eta; r.z, r.r
-    for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x) {
-      const double* sr = S + a.chunk_rep[c] * NS;
-      const bool as = ldS(sr + S_ACT_S) > 0, at = ldS(sr + S_ACT_T) > 0;
-      const double als = ldS(sr + S_AL_S), alt = ldS(sr + S_AL_T);
-      double v[NQ] = {0, 0, 0, 0, 0, 0, 0, 0};
-      for (int i = a.chunk_lo[c] + wid; i < a.chunk_lo[c + 1]; i += nw) {
-        if (lane != 0) continue;
-        const double ie = a.ieta[a.type[i]];
+    for_chunks(a, C, [&](int c, int lo, int hi, int rep, int off) {
+      spmv_chunk(a, B, lo, hi, off);
+      __syncthreads();
+      const double* sr = S + rep * NS;
+      const bool as = sr[S_ACT_S] > 0, at = sr[S_ACT_T] > 0;
+      const double bes = sr[S_BE_S], bet = sr[S_BE_T];
+      const R* us = B.u<R>(0);
+      const R* ut = B.u<R>(1);
+      double v[2] = {0, 0};
+      for_rows(lo, hi, [&](int i) {
+        const int li = off + i - lo;
+        const double e = B.v(V_ETA, li);
         if (as) {
-          a.xs[i] += als * a.ps[i];
-          const double r = a.rs[i] - als * a.ws[i];
-          const double z = r * ie;
-          a.rs[i] = r; a.zs[i] = z; a.zsf[i] = (float)z;
-          v[0] += r * z; v[2] += r * r;
+          const double z = B.v(V_ZS, li);
+          const double p = z + bes * B.v(V_PS, li), w = (double)us[li] + e * z + bes * B.v(V_WS, li);
+          B.v(V_PS, li) = p; B.v(V_WS, li) = w; v[0] += p * w;
         }
         if (at) {
-          a.xt[i] += alt * a.pt[i];
-          const double r = a.rt[i] - alt * a.wt[i];
-          const double z = r * ie;
-          a.rt[i] = r; a.zt[i] = z; a.ztf[i] = (float)z;
-          v[1] += r * z; v[3] += r * r;
+          const double z = B.v(V_ZT, li);
+          const double p = z + bet * B.v(V_PT, li), w = (double)ut[li] + e * z + bet * B.v(V_WT, li);
+          B.v(V_PT, li) = p; B.v(V_WT, li) = w; v[1] += p * w;
         }
-      }
-      block_partials(v, a.part, c);
-    }
-    ok = barrier_reduce(a.bar, a.err, [&]() {
-      reduce_parts(a, red);
-      for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
-        double* sr = S + r * NS;
-        if (sr[S_ACT_S] > 0) {
-          a.iters[2 * r] += 1;
-          sr[S_BE_S] = red[r * NQ + 0] / sr[S_RHO_S];
-          sr[S_RHO_S] = red[r * NQ + 0];
-          if (!(red[r * NQ + 2] > a.tol2 * sr[S_BB_S])) sr[S_ACT_S] = 0.0;
-        }
-        if (sr[S_ACT_T] > 0) {
-          a.iters[2 * r + 1] += 1;
-          sr[S_BE_T] = red[r * NQ + 1] / sr[S_RHO_T];
-          sr[S_RHO_T] = red[r * NQ + 1];
-          if (!(red[r * NQ + 3] > a.tol2 * sr[S_BB_T])) sr[S_ACT_T] = 0.0;
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double act = 0;
-        for (int r = 0; r < a.nrep; ++r) act += S[r * NS + S_ACT_S] + S[r * NS + S_ACT_T];
-        S[a.nrep * NS] = act;
-      }
+      });
+      block_sum<2>(a, v, hi - lo, pb, c);
     });
-  }
-  if (ok && ldS(&S[a.nrep * NS]) > 0.0 && blockIdx.x == 0 && threadIdx.x == 0)
-    atomicOr(a.err, ERR_CG);
-  if (!ok) return;
-  // ---------------- charges: mu = sum s / sum t per replica, q = s - mu t
-  for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x) {
-    double v[NQ] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = a.chunk_lo[c] + wid; i < a.chunk_lo[c + 1]; i += nw) {
-      if (lane != 0) continue;
-      v[0] += a.xs[i];
-      v[1] += a.xt[i];
+    if (!grid_barrier(a.bar, a.err)) return;
+    reduce_parts<2>(a, pb, red);
+    pb ^= 1;
+    for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
+      double* sr = S + r * NS;
+      sr[S_AL_S] = sr[S_ACT_S] > 0 ? sr[S_RHO_S] / red[r * NQ + 0] : 0.0;
+      sr[S_AL_T] = sr[S_ACT_T] > 0 ? sr[S_RHO_T] / red[r * NQ + 1] : 0.0;
     }
-    block_partials(v, a.part, c);
+    __syncthreads();
+    // ---------------- B: x += alpha p; r -= alpha w; z = r / eta; r.z, r.r
+    for_chunks(a, C, [&](int c, int lo, int hi, int rep, int off) {
+      const double* sr = S + rep * NS;
+      const bool as = sr[S_ACT_S] > 0, at = sr[S_ACT_T] > 0;
+      const double als = sr[S_AL_S], alt = sr[S_AL_T];
+      double v[4] = {0, 0, 0, 0};
+      for_rows(lo, hi, [&](int i) {
+        const int li = off + i - lo;
+        const double ie = B.v(V_IETA, li);
+        double zs = B.v(V_ZS, li), zt = B.v(V_ZT, li);
+        if (as) {
+          B.v(V_XS, li) += als * B.v(V_PS, li);
+          const double r = B.v(V_RS, li) - als * B.v(V_WS, li);
+          zs = r * ie;
+          B.v(V_RS, li) = r; B.v(V_ZS, li) = zs;
+          v[0] += r * zs; v[2] += r * r;
+        }
+        if (at) {
+          B.v(V_XT, li) += alt * B.v(V_PT, li);
+          const double r = B.v(V_RT, li) - alt * B.v(V_WT, li);
+          zt = r * ie;
+          B.v(V_RT, li) = r; B.v(V_ZT, li) = zt;
+          v[1] += r * zt; v[3] += r * r;
+        }
+        put_zg(a, i, zs, zt);
+      });
+      block_sum<4>(a, v, hi - lo, pb, c);
+    });
+    if (!grid_barrier(a.bar, a.err)) return;
+    reduce_parts<4>(a, pb, red);
+    pb ^= 1;
+    for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
+      double* sr = S + r * NS;
+      if (sr[S_ACT_S] > 0) {
+        if (lead) a.iters[2 * r] += 1;
+        sr[S_BE_S] = red[r * NQ + 0] / sr[S_RHO_S];
+        sr[S_RHO_S] = red[r * NQ + 0];
+        if (!(red[r * NQ + 2] > a.tol2 * sr[S_BB_S])) sr[S_ACT_S] = 0.0;
+      }
+      if (sr[S_ACT_T] > 0) {
+        if (lead) a.iters[2 * r + 1] += 1;
+        sr[S_BE_T] = red[r * NQ + 1] / sr[S_RHO_T];
+        sr[S_RHO_T] = red[r * NQ + 1];
+        if (!(red[r * NQ + 3] > a.tol2 * sr[S_BB_T])) sr[S_ACT_T] = 0.0;
+      }
+    }
+    count_active(S, a.nrep);
   }
-  ok = barrier_reduce(a.bar, a.err, [&]() {
-    reduce_parts(a, red);
-    for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) S[r * NS + S_MU] = red[r * NQ + 0] / red[r * NQ + 1];
+  if (S[a.nrep * NS] > 0.0 && lead && threadIdx.x == 0) atomicOr(a.err, ERR_CG);
+  // ---------------- solutions out; mu = sum s / sum t per replica, q = s - mu t
+  for_chunks(a, C, [&](int c, int lo, int hi, int, int off) {
+    double v[2] = {0, 0};
+    for_rows(lo, hi, [&](int i) {
+      const int li = off + i - lo;
+      const double xs = B.v(V_XS, li), xt = B.v(V_XT, li);
+      a.xs[i] = xs;
+      a.xt[i] = xt;
+      v[0] += xs;
+      v[1] += xt;
+    });
+    block_sum<2>(a, v, hi - lo, pb, c);
   });
-  if (!ok) return;
-  for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x) {
-    const double mu = ldS(&S[a.chunk_rep[c] * NS + S_MU]);
-    for (int i = a.chunk_lo[c] + threadIdx.x; i < a.chunk_lo[c + 1]; i += blockDim.x) {
-      const double qi = a.xs[i] - mu * a.xt[i];
+  if (!grid_barrier(a.bar, a.err)) return;
+  reduce_parts<2>(a, pb, red);
+  for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) S[r * NS + S_MU] = red[r * NQ + 0] / red[r * NQ + 1];
+  __syncthreads();
+  for_chunks(a, C, [&](int, int lo, int hi, int rep, int off) {
+    const double mu = S[rep * NS + S_MU];
+    for_rows(lo, hi, [&](int i) {
+      const int li = off + i - lo;
+      const double qi = B.v(V_XS, li) - mu * B.v(V_XT, li);
       a.q[i] = qi;
       a.qf[i] = (float)qi;
-    }
-  }
+    });
+  });
 }
 
 // initial guess: Lagrange extrapolation of the solution history (cubic for s from 4
@@ -406,20 +577,20 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   CG<R> a;
   a.n = s.n; a.nrep = s.nrep; a.nchunk = Q.nchunk; a.max_iter = max_iter;
   a.tol2 = tol * tol;
-  a.type = s.type; a.rep = s.rep;
+  a.type = s.type;
   a.cnt = f.cnt; a.col = f.j; a.H = (const R*)f.H; a.cap = f.cap;
   a.cntn = f.cntn; a.coln = f.jn; a.Hn = (const R*)f.Hn; a.capn = f.capn;
   a.eta = eta; a.chi = chi;
-  a.xs = Q.s; a.xt = Q.t; a.rs = Q.r_s; a.rt = Q.r_t; a.zs = Q.z_s; a.zt = Q.z_t;
-  a.ps = Q.p_s; a.pt = Q.p_t; a.ws = Q.w_s; a.wt = Q.w_t;
-  a.zsf = Q.zf_s; a.ztf = Q.zf_t;
-  a.q = s.q; a.qf = s.qf; a.part = Q.part; a.red = Q.red; a.scal = Q.scal;
+  a.xs = Q.s; a.xt = Q.t;
+  a.zg = Q.zg;
+  a.q = s.q; a.qf = s.qf; a.part = Q.part; a.scal = Q.scal; a.state = Q.state;
+  a.rows_blk = Q.rows_blk; a.scal_smem = Q.scal_smem; a.state_smem = Q.state_smem;
   a.ieta = Q.ieta;
   a.chunk_lo = Q.chunk_lo; a.chunk_rep = Q.chunk_rep; a.rep_chunk = Q.rep_chunk;
   a.iters = Q.iters; a.bar = Q.bar; a.err = s.err;
   cudaMemsetAsync(Q.bar, 0, sizeof(GridBar), L.st);
   void* args[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_cg<R>, dim3(Q.grid), dim3(1024), args, 0, L.st);
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_cg<R>, dim3(Q.grid), dim3(1024), args, Q.smem_bytes, L.st);
   *L.count += 2;
   return e == cudaSuccess ? 0 : -1;
 }
@@ -438,10 +609,12 @@ void qeq_push_history(const Launch& L, int n, QeqState& Q) {
 }
 
 int qeq_grid_size(int nsm) {
+  cudaFuncSetAttribute((const void*)k_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, QEQ_SMEM_MAX);
+  cudaFuncSetAttribute((const void*)k_cg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, QEQ_SMEM_MAX);
   int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_cg<double>, 1024, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_cg<double>, 1024, QEQ_SMEM_MAX);
   int per_f = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, (const void*)k_cg<float>, 1024, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, (const void*)k_cg<float>, 1024, QEQ_SMEM_MAX);
   if (per_f < per) per = per_f;
   if (per < 1) per = 1;
   return nsm * per;

@@ -443,16 +443,24 @@ void reduce_energies(const Launch& L, Sys s, Accum acc, const double* mass_t, co
 void verlet_kick_drift(const Launch& L, Sys s, const double* mass_t, double dt, int drift);
 void etot_combine(const Launch& L, int nrep, const double* E_rep, const double* ke, double* out);
 // qeq.cu
+// QEq solver state. The cooperative kernel keeps each block's per-replica scalars and the
+// CG vectors of its rows in dynamic shared memory when they fit in QEQ_SMEM_MAX bytes,
+// else in block-private global regions (scal, state).
+constexpr int QEQ_SMEM_MAX = 200 * 1024;
+constexpr int QEQ_NV_STATE = 14;             // doubles per row of CG state
+constexpr int QEQ_SCAL_PER_REP = 24;         // doubles per replica of scalars + reductions
 struct QeqState {
   double *s, *t;               // solutions
   double *hist_s, *hist_t;     // [4*n] previous solutions (ring)
   int nhist, hist_pos;
-  double *r_s, *r_t, *p_s, *p_t, *w_s, *w_t, *z_s, *z_t, *u_s, *u_t;
-  float *zf_s, *zf_t;          // FP32 copies of z (mixed-path SpMV)
+  void* zg;                    // interleaved (s, t) copy of the SpMV operand: float2 or double2
   const double* ieta;          // 1/eta per type
-  double* part;                // chunk partials
-  double* red;                 // per-replica reductions
-  double* scal;                // per-replica scalars
+  double* part;                // chunk partials [2][8][nchunk]
+  double* scal;                // [grid][nrep*24+4] per-block scalars (when not in shared memory)
+  double* state;               // [grid][14][rows_blk] per-block row state (when not in shared memory)
+  int rows_blk;                // most rows one block owns
+  int scal_smem, state_smem;   // 1: held in dynamic shared memory
+  int smem_bytes;              // dynamic shared memory of the launch
   int* chunk_rep;              // replica of each chunk
   int* chunk_lo;               // first atom of each chunk [nchunk+1]
   int* rep_chunk;              // first chunk of each replica [nrep+1]
