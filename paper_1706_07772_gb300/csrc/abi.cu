@@ -557,12 +557,12 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   // ---- QEq state and chunking (chunks never straddle replicas)
   rx::QeqState& Q = ctx->Q;
   Q.grid = rx::qeq_grid_size(ctx->nsm);
-  Q.s = B.alloc<double>(n);
-  Q.t = B.alloc<double>(n);
   Q.zg = B.alloc<double>(2 * (size_t)n);
   Q.hist_s = B.alloc<double>(4 * (size_t)n);
   Q.hist_t = B.alloc<double>(3 * (size_t)n);
   Q.nhist = 0;
+  Q.hpos_s = 0;
+  Q.hpos_t = 0;
   const int rows = std::max(8, (int)((n + Q.grid - 1) / Q.grid));
   std::vector<int> clo, crep, rchunk(nrep + 1, 0);
   for (int r = 0; r < nrep; ++r) {

@@ -53,7 +53,11 @@ struct CG {
   const R* Hn;
   int capn;
   const double *eta, *chi, *ieta;          // per type (double); ieta = 1/eta
-  double *xs, *xt;                         // initial guess in, solutions out
+  // solution history, newest first (s: 4 slots, t: 3); nh usable entries; the new
+  // solutions go to outs/outt (the ring slot of the oldest entry, read only at init)
+  const double *h0s, *h1s, *h2s, *h3s, *h0t, *h1t, *h2t;
+  int nh;
+  double *outs, *outt;
   void* zg;                                // interleaved (s, t) SpMV operand: float2 or double2
   double* q;
   float* qf;
@@ -367,13 +371,23 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
   int pb = 0;
   double* S = B.S;
   double* red = B.red;
-  // ---------------- init: eta, 1/eta and x into the row state; x into zg
+  // ---------------- init: eta, 1/eta and the initial guess into the row state; guess into
+  // zg. Guess: Lagrange extrapolation of the solution history (cubic for s from 4 points,
+  // quadratic for t from 3; lower order while the history is short; 0 without one)
   __syncthreads();
   for_chunks(a, C, [&](int, int lo, int hi, int, int off) {
     for_rows(lo, hi, [&](int i) {
       const int li = off + i - lo;
       const int t = a.type[i];
-      const double e = a.eta[t], ie = a.ieta[t], xs = a.xs[i], xt = a.xt[i];
+      double xs = 0.0, xt = 0.0;
+      if (a.nh >= 4) xs = 4 * a.h0s[i] - 6 * a.h1s[i] + 4 * a.h2s[i] - a.h3s[i];
+      else if (a.nh == 3) xs = 3 * a.h0s[i] - 3 * a.h1s[i] + a.h2s[i];
+      else if (a.nh == 2) xs = 2 * a.h0s[i] - a.h1s[i];
+      else if (a.nh == 1) xs = a.h0s[i];
+      if (a.nh >= 3) xt = 3 * a.h0t[i] - 3 * a.h1t[i] + a.h2t[i];
+      else if (a.nh == 2) xt = 2 * a.h0t[i] - a.h1t[i];
+      else if (a.nh == 1) xt = a.h0t[i];
+      const double e = a.eta[t], ie = a.ieta[t];
       B.v(V_ETA, li) = e; B.v(V_IETA, li) = ie;
       B.v(V_XS, li) = xs; B.v(V_XT, li) = xt;
       put_zg(a, i, xs, xt);
@@ -520,8 +534,8 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
     for_rows(lo, hi, [&](int i) {
       const int li = off + i - lo;
       const double xs = B.v(V_XS, li), xt = B.v(V_XT, li);
-      a.xs[i] = xs;
-      a.xt[i] = xt;
+      a.outs[i] = xs;
+      a.outt[i] = xt;
       v[0] += xs;
       v[1] += xt;
     });
@@ -542,25 +556,6 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
   });
 }
 
-// initial guess: Lagrange extrapolation of the solution history (cubic for s from 4
-// points, quadratic for t from 3; lower order while the history is short; 0 without one)
-__global__ void k_warm(int n, int nh, double* xs, double* xt, const double* h0s, const double* h1s,
-                       const double* h2s, const double* h3s, const double* h0t, const double* h1t,
-                       const double* h2t) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double s = 0, t = 0;
-  if (nh >= 4) s = 4 * h0s[i] - 6 * h1s[i] + 4 * h2s[i] - h3s[i];
-  else if (nh == 3) s = 3 * h0s[i] - 3 * h1s[i] + h2s[i];
-  else if (nh == 2) s = 2 * h0s[i] - h1s[i];
-  else if (nh == 1) s = h0s[i];
-  if (nh >= 3) t = 3 * h0t[i] - 3 * h1t[i] + h2t[i];
-  else if (nh == 2) t = 2 * h0t[i] - h1t[i];
-  else if (nh == 1) t = h0t[i];
-  xs[i] = s;
-  xt[i] = t;
-}
-
 }  // namespace
 
 namespace rx {
@@ -569,11 +564,9 @@ template <typename R>
 int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* P, const double* chi,
               const double* eta, double tol, int max_iter, int warm) {
   (void)P;
-  const int nh = warm == REAXFF_WARM_EXTRAP ? Q.nhist : 0;
-  k_warm<<<(s.n + 255) / 256, 256, 0, L.st>>>(s.n, nh, Q.s, Q.t, Q.hist_s + 0 * (size_t)s.n,
-                                              Q.hist_s + 1 * (size_t)s.n, Q.hist_s + 2 * (size_t)s.n,
-                                              Q.hist_s + 3 * (size_t)s.n, Q.hist_t + 0 * (size_t)s.n,
-                                              Q.hist_t + 1 * (size_t)s.n, Q.hist_t + 2 * (size_t)s.n);
+  const size_t n = (size_t)s.n;
+  auto hs = [&](int k) { return Q.hist_s + (size_t)((Q.hpos_s - k + 8) % 4) * n; };   // k = 0: newest
+  auto ht = [&](int k) { return Q.hist_t + (size_t)((Q.hpos_t - k + 6) % 3) * n; };
   CG<R> a;
   a.n = s.n; a.nrep = s.nrep; a.nchunk = Q.nchunk; a.max_iter = max_iter;
   a.tol2 = tol * tol;
@@ -581,7 +574,10 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   a.cnt = f.cnt; a.col = f.j; a.H = (const R*)f.H; a.cap = f.cap;
   a.cntn = f.cntn; a.coln = f.jn; a.Hn = (const R*)f.Hn; a.capn = f.capn;
   a.eta = eta; a.chi = chi;
-  a.xs = Q.s; a.xt = Q.t;
+  a.h0s = hs(0); a.h1s = hs(1); a.h2s = hs(2); a.h3s = hs(3);
+  a.h0t = ht(0); a.h1t = ht(1); a.h2t = ht(2);
+  a.nh = warm == REAXFF_WARM_EXTRAP ? Q.nhist : 0;
+  a.outs = hs(-1); a.outt = ht(-1);                    // the oldest slots
   a.zg = Q.zg;
   a.q = s.q; a.qf = s.qf; a.part = Q.part; a.scal = Q.scal; a.state = Q.state;
   a.rows_blk = Q.rows_blk; a.scal_smem = Q.scal_smem; a.state_smem = Q.state_smem;
@@ -595,16 +591,12 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   return e == cudaSuccess ? 0 : -1;
 }
 
-// shift the history: newest solution becomes h0 (pointer rotation, one copy)
+// the solve wrote its solutions into the oldest ring slots: advance the newest-slot index
 void qeq_push_history(const Launch& L, int n, QeqState& Q) {
-  // rotate slots 3 <- 2 <- 1 <- 0 by copying (4 small device copies)
-  cudaMemcpyAsync(Q.hist_s + 3 * (size_t)n, Q.hist_s + 2 * (size_t)n, n * sizeof(double), cudaMemcpyDeviceToDevice, L.st);
-  cudaMemcpyAsync(Q.hist_s + 2 * (size_t)n, Q.hist_s + 1 * (size_t)n, n * sizeof(double), cudaMemcpyDeviceToDevice, L.st);
-  cudaMemcpyAsync(Q.hist_s + 1 * (size_t)n, Q.hist_s + 0 * (size_t)n, n * sizeof(double), cudaMemcpyDeviceToDevice, L.st);
-  cudaMemcpyAsync(Q.hist_s + 0 * (size_t)n, Q.s, n * sizeof(double), cudaMemcpyDeviceToDevice, L.st);
-  cudaMemcpyAsync(Q.hist_t + 2 * (size_t)n, Q.hist_t + 1 * (size_t)n, n * sizeof(double), cudaMemcpyDeviceToDevice, L.st);
-  cudaMemcpyAsync(Q.hist_t + 1 * (size_t)n, Q.hist_t + 0 * (size_t)n, n * sizeof(double), cudaMemcpyDeviceToDevice, L.st);
-  cudaMemcpyAsync(Q.hist_t + 0 * (size_t)n, Q.t, n * sizeof(double), cudaMemcpyDeviceToDevice, L.st);
+  (void)L;
+  (void)n;
+  Q.hpos_s = (Q.hpos_s + 1) % 4;
+  Q.hpos_t = (Q.hpos_t + 1) % 3;
   Q.nhist = Q.nhist < 4 ? Q.nhist + 1 : 4;
 }
 

@@ -450,9 +450,10 @@ constexpr int QEQ_SMEM_MAX = 200 * 1024;
 constexpr int QEQ_NV_STATE = 14;             // doubles per row of CG state
 constexpr int QEQ_SCAL_PER_REP = 24;         // doubles per replica of scalars + reductions
 struct QeqState {
-  double *s, *t;               // solutions
-  double *hist_s, *hist_t;     // [4*n] previous solutions (ring)
-  int nhist, hist_pos;
+  double *hist_s, *hist_t;     // [4*n], [3*n] solution rings (s, t); the solver writes each
+                               // new solution into the oldest slot
+  int nhist;                   // usable history entries (0..4)
+  int hpos_s, hpos_t;          // ring slot of the newest s and t
   void* zg;                    // interleaved (s, t) copy of the SpMV operand: float2 or double2
   const double* ieta;          // 1/eta per type
   double* part;                // chunk partials [2][8][nchunk]
