@@ -1,8 +1,10 @@
 """Benchmark: ReaxFF MD timesteps on the synthetic 32,480-atom CHNO crystal (atom-steps/s).
 
 Default (no flags): 1 GPU, the mixed-precision path (FP32 interaction math, FP64 sums)
-with the extrapolated QEq warm start at QEq tolerance 1e-6, dt = 0.1 fs, lists rebuilt
-and QEq solved every step. One JSON line on rank 0.
+with the extrapolated QEq warm start at QEq tolerance 1e-6, dt = 0.1 fs, QEq solved every
+step; the neighbour lists come from a Verlet-skin candidate list (rebuilt once an atom has
+moved more than half the 1 A skin) filtered to the exact cutoffs every step. One JSON line
+on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workload petn32k|petn1m|petn464] [--precision mixed|fp64]
@@ -136,8 +138,9 @@ def peaks():
 def stage_costs(ctx, n, prec_bytes, qeq_iters):
     """Algorithmic bytes per launch of the memory-bound stages:
       far_list  : write j (4 B) + image code (1 B) + H entry (R) per full-list entry
-      qeq       : per CG iteration one read of H (index 4 B + value R) for both systems plus
-                  ~12 FP64 vector streams of n (z, p, w, x, r per system, read or written)
+      qeq       : one read of H (index 4 B + value R) for both systems per SpMV: the
+                  initial residual plus one per CG iteration (the CG vectors live in
+                  shared memory; the gathered operand is cache resident)
       nonbonded : read j + code per entry (positions and charges are cache resident)
     """
     import paper_1706_07772_gb300.reaxff as rx
@@ -145,7 +148,7 @@ def stage_costs(ctx, n, prec_bytes, qeq_iters):
     it = max(1, int(qeq_iters))
     return {
         "far_list": {"bytes": nfar * (5 + prec_bytes), "entries": nfar},
-        "qeq": {"bytes": it * (nfar * (4 + prec_bytes) + 12 * 8 * n * 2), "iters": it},
+        "qeq": {"bytes": (it + 1) * nfar * (4 + prec_bytes), "iters": it},
         "nonbonded": {"bytes": nfar * 5, "entries": nfar},
     }
 
@@ -209,7 +212,8 @@ def run_ours(a, rank, world):
         "dtype": "f32+f64" if prec == rx.MIXED else "f64", "data": "synthetic",
         "config": {"workload": a.workload, "atoms": n, "atoms_per_gpu": n, "precision": a.precision,
                    "warm_start": "extrapolated", "qeq_tol": w["options"]["qeq_tol"], "dt_fs": a.dt,
-                   "lists": "rebuilt every step", "l2": "flushed (256 MB write) before each timed step",
+                   "lists": "Verlet-skin candidates (1 A skin, rebuilt on displacement > skin/2), exact cutoff filter every step",
+                   "l2": "flushed (256 MB write) before each timed step",
                    "parallelism": "independent system per GPU" if world > 1 else "single GPU"},
         "clocks": clocks.summary(),
         "gpu_launches": launches,
@@ -243,14 +247,21 @@ def roofline(dom, stages, costs, pk, prec):
 
 
 def e2e(ctx, w, steps, dt):
-    """Host-API steps: upload x, v (pinned not needed for correctness; numpy buffers),
-    one step, download x, v, q and the energy; wall clock around the whole loop."""
+    """Host-API steps: upload x, v from pinned host buffers, one step, download x, v, q and
+    the energy into pinned buffers; wall clock around the whole loop."""
+    import torch
+    n = ctx.n
+    pin = {k: torch.empty(shape, dtype=torch.float64, pin_memory=True)
+           for k, shape in (("x", (n, 3)), ("v", (n, 3)), ("q", (n,)))}
+    xh, vh, qh = (pin[k].numpy() for k in ("x", "v", "q"))
     x, v, q = ctx.get_state()
+    xh[:] = x
+    vh[:] = v
     t0 = time.perf_counter()
     for _ in range(steps):
-        ctx.set_state(x, v)
+        ctx.set_state(xh, vh)
         e = ctx.step(1, dt)
-        x, v, q = ctx.get_state()
+        ctx.get_state(out=(xh, vh, qh))
     t = time.perf_counter() - t0
     n = ctx.n
     return {"value": n * steps / t, "unit": UNIT, "h2d_bytes_per_step": 48 * n,

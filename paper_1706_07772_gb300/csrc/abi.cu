@@ -543,6 +543,8 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
                     &a.prodexp, &a.sbo2, &a.dsbo2, &a.sbo_fac, &a.cds, &a.A};
   for (double** p : aqf) *p = B.alloc<double>(n);
   a.cddelta = B.alloc<unsigned long long>(n);
+  a.sumbo_f = B.alloc<float>(n);
+  a.dang_f = B.alloc<float>(n);
   ctx->acc.e = B.alloc<double>((size_t)NTERMS * n);
   ctx->acc.vir = B.alloc<double>(6 * (size_t)n);
   ctx->F_out = B.alloc<double>(3 * (size_t)n);

@@ -164,6 +164,8 @@ __global__ void k_atom_terms(Sys s, BondList bl, AtomQ aq, Accum acc, const DPar
   aq.sumbo[i] = sumbo;
   aq.delta[i] = delta;
   aq.dang[i] = dang;
+  aq.sumbo_f[i] = (float)sumbo;
+  aq.dang_f[i] = (float)dang;
   aq.nlp[i] = nlp;
   aq.dnlp[i] = dnlp;
   aq.dlp[i] = dlp;
@@ -396,7 +398,14 @@ __global__ void k_angles(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<
     const R ga = m_exp(-pp2 * (BOa - R(2)) * (BOa - R(2))), gb = m_exp(-pp2 * (BOb - R(2)) * (BOb - R(2)));
     const R ep = P->p_pen1[t3] * f9 * ga * gb;
     // coalition
-    const R sbi = (R)(aq.sumbo[i] - (double)BOa), sbk = (R)(aq.sumbo[k] - (double)BOb);
+    R sbi, sbk;
+    if constexpr (sizeof(R) == 4) {
+      sbi = aq.sumbo_f[i] - BOa;
+      sbk = aq.sumbo_f[k] - BOb;
+    } else {
+      sbi = (R)(aq.sumbo[i] - (double)BOa);
+      sbk = (R)(aq.sumbo[k] - (double)BOb);
+    }
     const R pc3 = P->p_coa3, pc4 = P->p_coa4;
     const R ec = P->p_coa1[t3] * scoa * m_exp(-pc3 * sbi * sbi) * m_exp(-pc3 * sbk * sbk) *
                  m_exp(-pc4 * (BOa - R(1.5)) * (BOa - R(1.5))) * m_exp(-pc4 * (BOb - R(1.5)) * (BOb - R(1.5)));
@@ -428,33 +437,74 @@ __global__ void k_angles(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<
       vir_sub(l_w, gv, v);
     }
   }
-  const double eval = warp_sum_d(l_eval), epen = warp_sum_d(l_epen), ecoa = warp_sum_d(l_ecoa);
-  double cdsbo = warp_sum_d(l_cdsbo);
-  const double cdd = warp_sum_d(l_cdd);
-  double fj[3], w[6];
-  for (int q = 0; q < 3; ++q) fj[q] = warp_sum_d(l_fj[q]);
-  for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(l_w[q]);
-  cdsbo *= aq.dsbo2[j];                                // dE/dSBO
-  const double prod = aq.prodexp[j];
-  if (lane == 0) {
-    acc.e[T_VAL * s.n + j] = eval;
-    acc.e[T_PEN * s.n + j] = epen;
-    acc.e[T_COA * s.n + j] = ecoa;
-    force_add<double>(s, j, fj[0], fj[1], fj[2]);
-    const double dsbo_dsum = -(1.0 - prod) * (1.0 + (double)P->p_val8 * aq.dnlp[j]);
-    fix_add(aq.cddelta + j, cdd + cdsbo * dsbo_dsum, s.err);
-    for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
-  }
-  // SBO depends on every bond of j: distribute dE/dSBO over j's row
-  if (cdsbo != 0.0) {
-    const double fac = aq.sbo_fac[j];
-    for (int k = lane; k < nb; k += 32) {
-      const int e = j * bl.cap + k;
-      const double b = (double)bo[e];
-      const double b2 = b * b, b4 = b2 * b2;
-      fix_add(bl.cdbopi + e, cdsbo, s.err);
-      fix_add(bl.cdbopp + e, cdsbo, s.err);
-      fix_add(bl.cdbo + e, cdsbo * prod * 8.0 * b4 * b2 * b * fac, s.err);
+  if constexpr (sizeof(R) == 4) {
+    // float-float warp totals (FP32 only); then lane q handles value q, so each FP64
+    // conversion or update below is one warp instruction for all values
+    constexpr int NVA = 14;   // 0-2 E_val, E_pen, E_coa; 3-5 F_j; 6-11 virial; 12 dE/dSBO2; 13 dE/dDelta
+    float hi[NVA] = {l_eval, l_epen, l_ecoa, l_fj[0], l_fj[1], l_fj[2], l_w[0], l_w[1], l_w[2], l_w[3], l_w[4],
+                     l_w[5], l_cdsbo, l_cdd};
+    float lo[NVA];
+#pragma unroll
+    for (int q = 0; q < NVA; ++q) {
+      lo[q] = 0.0f;
+      warp_sum_ff2(hi[q], lo[q]);
+    }
+    float h, l;
+    lane_pick<NVA>(hi, lo, lane, h, l);
+    const double d = (double)h + (double)l;
+    const double cdsbo = ((double)hi[12] + (double)lo[12]) * aq.dsbo2[j];   // dE/dSBO
+    const double prod = aq.prodexp[j];
+    if (lane < 3) {
+      acc.e[(T_VAL + lane) * s.n + j] = d;
+    } else if (lane < 6) {
+      fix_add_ff((lane == 3 ? s.fx : lane == 4 ? s.fy : s.fz) + j, h, l, s.err);
+    } else if (lane < 12) {
+      acc.vir[(lane - 6) * s.n + j] += d;
+    } else if (lane == 13) {
+      const double dsbo_dsum = -(1.0 - prod) * (1.0 + (double)P->p_val8 * aq.dnlp[j]);
+      fix_add(aq.cddelta + j, d + cdsbo * dsbo_dsum, s.err);
+    }
+    // SBO depends on every bond of j: distribute dE/dSBO over j's row (FP32 terms)
+    if (cdsbo != 0.0) {
+      const float cf = (float)cdsbo, pf = (float)prod, ff = (float)aq.sbo_fac[j];
+      for (int k = lane; k < nb; k += 32) {
+        const int e = j * bl.cap + k;
+        const float b = bo[e];
+        const float b2 = b * b, b4 = b2 * b2;
+        fix_add(bl.cdbopi + e, cf, s.err);
+        fix_add(bl.cdbopp + e, cf, s.err);
+        fix_add(bl.cdbo + e, cf * pf * 8.0f * b4 * b2 * b * ff, s.err);
+      }
+    }
+  } else {
+    const double eval = warp_sum_d(l_eval), epen = warp_sum_d(l_epen), ecoa = warp_sum_d(l_ecoa);
+    double cdsbo = warp_sum_d(l_cdsbo);
+    const double cdd = warp_sum_d(l_cdd);
+    double fj[3], w[6];
+    for (int q = 0; q < 3; ++q) fj[q] = warp_sum_d(l_fj[q]);
+    for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(l_w[q]);
+    cdsbo *= aq.dsbo2[j];                                // dE/dSBO
+    const double prod = aq.prodexp[j];
+    if (lane == 0) {
+      acc.e[T_VAL * s.n + j] = eval;
+      acc.e[T_PEN * s.n + j] = epen;
+      acc.e[T_COA * s.n + j] = ecoa;
+      force_add<double>(s, j, fj[0], fj[1], fj[2]);
+      const double dsbo_dsum = -(1.0 - prod) * (1.0 + (double)P->p_val8 * aq.dnlp[j]);
+      fix_add(aq.cddelta + j, cdd + cdsbo * dsbo_dsum, s.err);
+      for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
+    }
+    // SBO depends on every bond of j: distribute dE/dSBO over j's row
+    if (cdsbo != 0.0) {
+      const double fac = aq.sbo_fac[j];
+      for (int k = lane; k < nb; k += 32) {
+        const int e = j * bl.cap + k;
+        const double b = (double)bo[e];
+        const double b2 = b * b, b4 = b2 * b2;
+        fix_add(bl.cdbopi + e, cdsbo, s.err);
+        fix_add(bl.cdbopp + e, cdsbo, s.err);
+        fix_add(bl.cdbo + e, cdsbo * prod * 8.0 * b4 * b2 * b * fac, s.err);
+      }
     }
   }
 }
@@ -489,7 +539,9 @@ __global__ void k_torsions(Sys s, BondList bl, AtomQ aq, Accum acc, const DParam
     const R V1 = P->V1[pt], V2 = P->V2[pt], V3 = P->V3[pt], pt1 = P->p_tor1[pt], pc1 = P->p_cot1[pt];
     const R pt2 = P->p_tor2, pc2 = P->p_cot2;
     const R BOpi2 = bo_pi[ejk];
-    const R Dsum = (R)(aq.dang[j] + aq.dang[k]);
+    R Dsum;
+    if constexpr (sizeof(R) == 4) Dsum = aq.dang_f[j] + aq.dang_f[k];
+    else Dsum = (R)(aq.dang[j] + aq.dang[k]);
     R f11, df11;
     f9fun<R>(P->p_tor3, P->p_tor4, Dsum, f11, df11);
     const R xb = R(2) - BOpi2 - f11;
@@ -596,28 +648,67 @@ __global__ void k_torsions(Sys s, BondList bl, AtomQ aq, Accum acc, const DParam
       vir_sub(l_w, gg2, u2);
       vir_sub(l_w, gg3, u3);
     }
-    double fk[3];
-    for (int q = 0; q < 3; ++q) fk[q] = warp_sum_d(l_fk[q]);
-    const double cddk = warp_sum_d(l_cddk);
-    const double cdbo2 = warp_sum_d(l_cdbo2);
-    const double cdbopi2 = warp_sum_d(l_cdbopi2);
-    if (lane == 0) {
-      force_add<double>(s, k, fk[0], fk[1], fk[2]);
-      fix_add(aq.cddelta + k, cddk, s.err);
-      fix_add(bl.cdbo + ejk, cdbo2, s.err);
-      fix_add(bl.cdbopi + ejk, cdbopi2, s.err);
+    if constexpr (sizeof(R) == 4) {
+      // per central bond: float-float totals, lane q adds value q (FP32 only)
+      constexpr int NVK = 6;   // 0-2 F_k, 3 dE/dDelta_k, 4 dE/dBO_jk, 5 dE/dBOpi_jk
+      float hi[NVK] = {l_fk[0], l_fk[1], l_fk[2], l_cddk, l_cdbo2, l_cdbopi2};
+      float lo[NVK];
+#pragma unroll
+      for (int q = 0; q < NVK; ++q) {
+        lo[q] = 0.0f;
+        warp_sum_ff2(hi[q], lo[q]);
+      }
+      float h, l;
+      lane_pick<NVK>(hi, lo, lane, h, l);
+      if (lane < NVK) {
+        unsigned long long* dst = lane == 0 ? s.fx + k : lane == 1 ? s.fy + k : lane == 2 ? s.fz + k
+                                : lane == 3 ? aq.cddelta + k : lane == 4 ? bl.cdbo + ejk : bl.cdbopi + ejk;
+        fix_add_ff(dst, h, l, s.err);
+      }
+    } else {
+      double fk[3];
+      for (int q = 0; q < 3; ++q) fk[q] = warp_sum_d(l_fk[q]);
+      const double cddk = warp_sum_d(l_cddk);
+      const double cdbo2 = warp_sum_d(l_cdbo2);
+      const double cdbopi2 = warp_sum_d(l_cdbopi2);
+      if (lane == 0) {
+        force_add<double>(s, k, fk[0], fk[1], fk[2]);
+        fix_add(aq.cddelta + k, cddk, s.err);
+        fix_add(bl.cdbo + ejk, cdbo2, s.err);
+        fix_add(bl.cdbopi + ejk, cdbopi2, s.err);
+      }
     }
   }
-  const double etor = warp_sum_d(l_etor), econ = warp_sum_d(l_econ), cddj = warp_sum_d(l_cddj);
-  double fj[3], w[6];
-  for (int q = 0; q < 3; ++q) fj[q] = warp_sum_d(l_fj[q]);
-  for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(l_w[q]);
-  if (lane == 0) {
-    acc.e[T_TORS * s.n + j] = etor;
-    acc.e[T_CONJ * s.n + j] = econ;
-    force_add<double>(s, j, fj[0], fj[1], fj[2]);
-    fix_add(aq.cddelta + j, cddj, s.err);
-    for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
+  if constexpr (sizeof(R) == 4) {
+    constexpr int NVJ = 12;   // 0-1 E_tors, E_conj; 2-4 F_j; 5 dE/dDelta_j; 6-11 virial
+    float hi[NVJ] = {l_etor, l_econ, l_fj[0], l_fj[1], l_fj[2], l_cddj, l_w[0], l_w[1], l_w[2], l_w[3], l_w[4], l_w[5]};
+    float lo[NVJ];
+#pragma unroll
+    for (int q = 0; q < NVJ; ++q) {
+      lo[q] = 0.0f;
+      warp_sum_ff2(hi[q], lo[q]);
+    }
+    float h, l;
+    lane_pick<NVJ>(hi, lo, lane, h, l);
+    if (lane < 2) {
+      acc.e[(T_TORS + lane) * s.n + j] = (double)h + (double)l;
+    } else if (lane < 6) {
+      fix_add_ff((lane == 2 ? s.fx + j : lane == 3 ? s.fy + j : lane == 4 ? s.fz + j : aq.cddelta + j), h, l, s.err);
+    } else if (lane < NVJ) {
+      acc.vir[(lane - 6) * s.n + j] += (double)h + (double)l;
+    }
+  } else {
+    const double etor = warp_sum_d(l_etor), econ = warp_sum_d(l_econ), cddj = warp_sum_d(l_cddj);
+    double fj[3], w[6];
+    for (int q = 0; q < 3; ++q) fj[q] = warp_sum_d(l_fj[q]);
+    for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(l_w[q]);
+    if (lane == 0) {
+      acc.e[T_TORS * s.n + j] = etor;
+      acc.e[T_CONJ * s.n + j] = econ;
+      force_add<double>(s, j, fj[0], fj[1], fj[2]);
+      fix_add(aq.cddelta + j, cddj, s.err);
+      for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
+    }
   }
 }
 
@@ -681,22 +772,57 @@ __global__ void k_hbonds(Sys s, BondList bl, HbList hl, Accum acc, const DParams
       vir_sub(l_w, gu, u);
       vir_sub(l_w, gv, v);
     }
-    const double cdb = warp_sum_d(l_cdb);
-    double fx[3];
-    for (int q = 0; q < 3; ++q) fx[q] = warp_sum_d(l_fx[q]);
-    if (lane == 0) {
-      fix_add(bl.cdbo + ea, cdb, s.err);
-      force_add<double>(s, x, fx[0], fx[1], fx[2]);
+    if constexpr (sizeof(R) == 4) {
+      constexpr int NVX = 4;   // 0 dE/dBO_jx, 1-3 F_x
+      float hi[NVX] = {l_cdb, l_fx[0], l_fx[1], l_fx[2]};
+      float lo[NVX];
+#pragma unroll
+      for (int q = 0; q < NVX; ++q) {
+        lo[q] = 0.0f;
+        warp_sum_ff2(hi[q], lo[q]);
+      }
+      float h, l;
+      lane_pick<NVX>(hi, lo, lane, h, l);
+      if (lane < NVX)
+        fix_add_ff(lane == 0 ? bl.cdbo + ea : lane == 1 ? s.fx + x : lane == 2 ? s.fy + x : s.fz + x, h, l, s.err);
+    } else {
+      const double cdb = warp_sum_d(l_cdb);
+      double fx[3];
+      for (int q = 0; q < 3; ++q) fx[q] = warp_sum_d(l_fx[q]);
+      if (lane == 0) {
+        fix_add(bl.cdbo + ea, cdb, s.err);
+        force_add<double>(s, x, fx[0], fx[1], fx[2]);
+      }
     }
   }
-  const double ehb = warp_sum_d(l_ehb);
-  double fj[3], w[6];
-  for (int q = 0; q < 3; ++q) fj[q] = warp_sum_d(l_fj[q]);
-  for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(l_w[q]);
-  if (lane == 0) {
-    acc.e[T_HB * s.n + j] = ehb;
-    force_add<double>(s, j, fj[0], fj[1], fj[2]);
-    for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
+  if constexpr (sizeof(R) == 4) {
+    constexpr int NVJ = 10;   // 0 E_hb; 1-3 F_j; 4-9 virial
+    float hi[NVJ] = {l_ehb, l_fj[0], l_fj[1], l_fj[2], l_w[0], l_w[1], l_w[2], l_w[3], l_w[4], l_w[5]};
+    float lo[NVJ];
+#pragma unroll
+    for (int q = 0; q < NVJ; ++q) {
+      lo[q] = 0.0f;
+      warp_sum_ff2(hi[q], lo[q]);
+    }
+    float h, l;
+    lane_pick<NVJ>(hi, lo, lane, h, l);
+    if (lane == 0) {
+      acc.e[T_HB * s.n + j] = (double)h + (double)l;
+    } else if (lane < 4) {
+      fix_add_ff(lane == 1 ? s.fx + j : lane == 2 ? s.fy + j : s.fz + j, h, l, s.err);
+    } else if (lane < NVJ) {
+      acc.vir[(lane - 4) * s.n + j] += (double)h + (double)l;
+    }
+  } else {
+    const double ehb = warp_sum_d(l_ehb);
+    double fj[3], w[6];
+    for (int q = 0; q < 3; ++q) fj[q] = warp_sum_d(l_fj[q]);
+    for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(l_w[q]);
+    if (lane == 0) {
+      acc.e[T_HB * s.n + j] = ehb;
+      force_add<double>(s, j, fj[0], fj[1], fj[2]);
+      for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
+    }
   }
 }
 

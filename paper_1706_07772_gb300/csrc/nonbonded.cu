@@ -89,20 +89,46 @@ __global__ void k_nonbonded(Sys s, FarList f, Accum acc, const DParams<R>* __res
   const int nfa = f.cnt[i], rowf = i * f.cap;
   for (int k = lane; k < nfa; k += 32)
     nb_pair<R, true, R>(s, P, i, f.j[rowf + k], f.s[rowf + k], r, ti, qi, wv, wc, lev, lec, lfx, lfy, lfz, lw);
-  const double ev = warp_sum_d(nev) + warp_sum_d(lev), ec = warp_sum_d(nec) + warp_sum_d(lec);
-  const double fx = warp_sum_d(nfx) + warp_sum_d(lfx), fy = warp_sum_d(nfy) + warp_sum_d(lfy);
-  const double fz = warp_sum_d(nfz) + warp_sum_d(lfz);
-  double w[6];
-  for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(nw[q]) + warp_sum_d(lw[q]);
-  if (lane == 0) {
-    acc.e[T_VDW * s.n + i] = 0.5 * ev;
-    acc.e[T_COUL * s.n + i] = 0.5 * ec;
-    const double q = s.q[i];
-    acc.e[T_POL * s.n + i] = (double)P->chi[ti] * q + 0.5 * (double)P->eta[ti] * q * q;
-    fix_add(s.fx + i, fx, s.err);
-    fix_add(s.fy + i, fy, s.err);
-    fix_add(s.fz + i, fz, s.err);
-    for (int q6 = 0; q6 < 6; ++q6) acc.vir[q6 * s.n + i] += w[q6];
+  if constexpr (sizeof(R) == 4) {
+    // near + far partials joined error-free per lane, float-float warp totals (FP32 only),
+    // then lane q handles value q: the FP64 conversions are one warp instruction each
+    constexpr int NVN = 11;   // 0-2 F_i; 3 E_vdW; 4 E_Coulomb; 5-10 virial
+    const float nv[NVN] = {nfx, nfy, nfz, nev, nec, nw[0], nw[1], nw[2], nw[3], nw[4], nw[5]};
+    const float fv[NVN] = {lfx, lfy, lfz, lev, lec, lw[0], lw[1], lw[2], lw[3], lw[4], lw[5]};
+    float hi[NVN], lo[NVN];
+#pragma unroll
+    for (int q = 0; q < NVN; ++q) {
+      two_sum(nv[q], fv[q], hi[q], lo[q]);
+      warp_sum_ff2(hi[q], lo[q]);
+    }
+    float h, l;
+    lane_pick<NVN>(hi, lo, lane, h, l);
+    if (lane < 3) {
+      fix_add_ff((lane == 0 ? s.fx : lane == 1 ? s.fy : s.fz) + i, h, l, s.err);
+    } else if (lane < 5) {
+      acc.e[(T_VDW + lane - 3) * s.n + i] = 0.5 * ((double)h + (double)l);
+    } else if (lane < NVN) {
+      acc.vir[(lane - 5) * s.n + i] += (double)h + (double)l;
+    } else if (lane == NVN) {
+      const double q = s.q[i];
+      acc.e[T_POL * s.n + i] = (double)P->chi[ti] * q + 0.5 * (double)P->eta[ti] * q * q;
+    }
+  } else {
+    const double ev = warp_sum_d(nev) + warp_sum_d(lev), ec = warp_sum_d(nec) + warp_sum_d(lec);
+    const double fx = warp_sum_d(nfx) + warp_sum_d(lfx), fy = warp_sum_d(nfy) + warp_sum_d(lfy);
+    const double fz = warp_sum_d(nfz) + warp_sum_d(lfz);
+    double w[6];
+    for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(nw[q]) + warp_sum_d(lw[q]);
+    if (lane == 0) {
+      acc.e[T_VDW * s.n + i] = 0.5 * ev;
+      acc.e[T_COUL * s.n + i] = 0.5 * ec;
+      const double q = s.q[i];
+      acc.e[T_POL * s.n + i] = (double)P->chi[ti] * q + 0.5 * (double)P->eta[ti] * q * q;
+      fix_add(s.fx + i, fx, s.err);
+      fix_add(s.fy + i, fy, s.err);
+      fix_add(s.fz + i, fz, s.err);
+      for (int q6 = 0; q6 < 6; ++q6) acc.vir[q6 * s.n + i] += w[q6];
+    }
   }
 }
 

@@ -157,6 +157,7 @@ struct AtomQ {                 // per-atom bond-order quantities (double)
   double *prodexp, *sbo2, *dsbo2, *sbo_fac;               // sbo_fac = -Delta_ang - p_val8 nlp
   double *cds, *A;             // dE/dS, chain-rule dE/dDelta'
   unsigned long long* cddelta; // dE/d(sum BO) accumulator (fixed point)
+  float *sumbo_f, *dang_f;     // FP32 copies for the mixed-path angle and torsion kernels
 };
 
 struct Accum {                 // per-atom energies and virial (owner-written, double)
@@ -176,13 +177,34 @@ __device__ __forceinline__ void fix_add(unsigned long long* p, double v, int* er
   long long f = fix_of(v, err);
   if (f != 0) atomicAdd(p, (unsigned long long)f);
 }
-// FP32 value -> fixed point without FP64 instructions: v * 2^32 is exact in FP32
+// FP32 value -> 2^32 fixed point with 32-bit conversions only (GB300 issues 64-bit
+// conversions at the FP64 rate, ~16x slower than 32-bit ones). t = v 2^32 is exact; for
+// |t| < 2^31 a 32-bit round-to-nearest conversion gives round(t); a larger |t| is already
+// an integer (its ulp is >= 2^8) and is rebuilt exactly from its bits. The result equals
+// what a 64-bit round-to-nearest conversion of t gives.
+__device__ __forceinline__ long long fix_of_f(float v) {
+  const float t = v * 4294967296.0f;
+  if (fabsf(t) < 2147483648.0f) return (long long)__float2int_rn(t);
+  const int b = __float_as_int(t);
+  const int e = ((b >> 23) & 0xff) - 150;           // t = m 2^e, 8 <= e <= 38 below FIX_LIMIT
+  const long long mag = (long long)((b & 0x7fffff) | 0x800000) << e;
+  return b < 0 ? -mag : mag;
+}
 __device__ __forceinline__ void fix_add(unsigned long long* p, float v, int* err) {
   if (!(fabsf(v) < (float)FIX_LIMIT)) {
     atomicOr(err, ERR_NAN);
     return;
   }
-  const long long f = __float2ll_rn(v * 4294967296.0f);
+  const long long f = fix_of_f(v);
+  if (f != 0) atomicAdd(p, (unsigned long long)f);
+}
+// a float-float value hi + lo (|lo| <= ulp(hi)/2): both parts converted, then summed
+__device__ __forceinline__ void fix_add_ff(unsigned long long* p, float hi, float lo, int* err) {
+  if (!(fabsf(hi) < (float)FIX_LIMIT)) {
+    atomicOr(err, ERR_NAN);
+    return;
+  }
+  const long long f = fix_of_f(hi) + fix_of_f(lo);
   if (f != 0) atomicAdd(p, (unsigned long long)f);
 }
 __device__ __forceinline__ double fix_get(const unsigned long long* p) {
@@ -198,21 +220,43 @@ __device__ __forceinline__ double warp_sum(double v) {
 // FP32 instructions (GB300 runs FP64 at 1/64 of the FP32 rate, and an FP64 butterfly
 // costs 5 FP64 adds in every lane); exact to ~2^-48 of the partials. The same value
 // in every lane (the error term of a TwoSum is unique, so the butterfly is symmetric).
-__device__ __forceinline__ double warp_sum_ff(float v) {
-  float hi = v, lo = 0.0f;
+// error-free sum: s + e == a + b exactly (Knuth TwoSum, FP32)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// float-float butterfly: on return every lane holds the warp total of the (hi, lo) pairs
+__device__ __forceinline__ void warp_sum_ff2(float& hi, float& lo) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
     const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
-    const float s = __fadd_rn(hi, ohi);
-    const float bb = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(ohi, bb));
+    float s, e;
+    two_sum(hi, ohi, s, e);
     lo = __fadd_rn(__fadd_rn(lo, olo), e);
     hi = s;
   }
+}
+__device__ __forceinline__ double warp_sum_ff(float v) {
+  float hi = v, lo = 0.0f;
+  warp_sum_ff2(hi, lo);
   return (double)hi + (double)lo;
 }
-// warp sum of a per-lane partial in the path precision, combined to FP64
+// lane q takes value q of N float-float totals held by every lane (q >= N: zeros). Used
+// to spread the few FP64 conversions of a warp's results over its lanes, so that one
+// warp instruction converts them all.
+template <int N>
+__device__ __forceinline__ void lane_pick(const float* hi, const float* lo, int q, float& h, float& l) {
+  h = 0.0f;
+  l = 0.0f;
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (k == q) {
+      h = hi[k];
+      l = lo[k];
+    }
+}
 __device__ __forceinline__ double warp_sum_d(float v) { return warp_sum_ff(v); }
 __device__ __forceinline__ double warp_sum_d(double v) { return warp_sum(v); }
 __device__ __forceinline__ float warp_sumf(float v) {
@@ -293,11 +337,6 @@ template <typename R> __device__ __forceinline__ void taper(R r, R Rc, R& t, R& 
 // Image vector d = (x_j - x_i) + s*L of a list entry (shift code 0..26).
 // FP64: the defining arithmetic. FP32: hi/lo float positions with an error-free
 // difference of the hi parts, so d is within ~1 ulp of its own magnitude (not of L).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
 template <typename R> struct PairVec;
 template <> struct PairVec<double> {
   static __device__ __forceinline__ void get(const Sys& s, int i, int j, int code, int r, double& dx,

@@ -224,10 +224,18 @@ class ReaxFF:
         v = None if v is None else np.ascontiguousarray(v, np.float64).reshape(self.n, 3)
         self._check(self.lib.reaxff_set_state(self.h, _dp(x), _dp(v)))
 
-    def get_state(self):
-        x = np.empty((self.n, 3))
-        v = np.empty((self.n, 3))
-        q = np.empty(self.n)
+    def get_state(self, out=None):
+        """Positions, velocities and charges; `out` = (x, v, q) C-contiguous float64 arrays
+        of shapes (n, 3), (n, 3), (n,) to fill instead of new ones (e.g. pinned buffers)."""
+        if out is None:
+            x = np.empty((self.n, 3))
+            v = np.empty((self.n, 3))
+            q = np.empty(self.n)
+        else:
+            x, v, q = out
+            for a, shape in ((x, (self.n, 3)), (v, (self.n, 3)), (q, (self.n,))):
+                if a.shape != shape or a.dtype != np.float64 or not a.flags.c_contiguous:
+                    raise ValueError("get_state out arrays must be C-contiguous float64 of shape %s" % (shape,))
         self._check(self.lib.reaxff_get_state(self.h, _dp(x), _dp(v), _dp(q)))
         return x, v, q
 
