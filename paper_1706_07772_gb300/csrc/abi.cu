@@ -528,6 +528,8 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   s.fx = facc; s.fy = facc ? facc + n : nullptr; s.fz = facc ? facc + 2 * (size_t)n : nullptr;
   s.q = B.alloc<double>(n);
   s.qf = B.alloc<float>(n);
+  s.ph = B.alloc<float4>(n);
+  s.pl = B.alloc<float4>(n);
   s.err = B.alloc<int>(1);
   s.img = B.alloc<int>(3 * (size_t)n);
   s.xb = B.alloc<double>(3 * (size_t)n);
@@ -669,6 +671,8 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   if (e == cudaSuccess) e = cudaMemset(s.vz, 0, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(s.q, 0, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(s.qf, 0, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(s.ph, 0, n * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMemset(s.pl, 0, n * sizeof(float4));
   if (e == cudaSuccess) e = cudaMemset(s.img, 0, 3 * (size_t)n * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(s.rebuild, 1, sizeof(int));
   if (e != cudaSuccess) {

@@ -29,11 +29,7 @@ __global__ void k_cell_assign(Sys s, Cells c) {
   int cell = c.cell_off[r] + (cc[2] * nc[1] + cc[1]) * nc[0] + cc[0];
   c.atom_cell[i] = cell;
   atomicAdd(&c.count[cell], 1);
-  // float hi/lo copies of the positions
-  float h;
-  h = (float)s.x[i]; s.xh[i] = h; s.xl[i] = (float)(s.x[i] - (double)h);
-  h = (float)s.y[i]; s.yh[i] = h; s.yl[i] = (float)(s.y[i] - (double)h);
-  h = (float)s.z[i]; s.zh[i] = h; s.zl[i] = (float)(s.z[i] - (double)h);
+  write_pos_f32(s, i);   // float hi/lo copies of the positions
 }
 
 // single-block exclusive scan over cell counts
@@ -337,9 +333,10 @@ __global__ void k_bond_list(Sys s, FarList f, BondList bl, HbList hl, AtomQ aq,
         const float* Lh = s.boxh + 3 * r;
         const float* Ll = s.boxl + 3 * r;
         float dh[3], dl[3], rh, rl;
-        pv_comp_ff(s.xh[j], s.xh[i], s.xl[j], s.xl[i], sx, Lh[0], Ll[0], dh[0], dl[0]);
-        pv_comp_ff(s.yh[j], s.yh[i], s.yl[j], s.yl[i], sy, Lh[1], Ll[1], dh[1], dl[1]);
-        pv_comp_ff(s.zh[j], s.zh[i], s.zl[j], s.zl[i], sz, Lh[2], Ll[2], dh[2], dl[2]);
+        const float4 hj = s.ph[j], hi = s.ph[i], lj = s.pl[j], li = s.pl[i];
+        pv_comp_ff(hj.x, hi.x, lj.x, li.x, sx, Lh[0], Ll[0], dh[0], dl[0]);
+        pv_comp_ff(hj.y, hi.y, lj.y, li.y, sy, Lh[1], Ll[1], dh[1], dl[1]);
+        pv_comp_ff(hj.z, hi.z, lj.z, li.z, sz, Lh[2], Ll[2], dh[2], dl[2]);
         norm_ff(dh, dl, rh, rl);
         dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
         rr = (R)rh;
@@ -437,10 +434,7 @@ __global__ void k_bond_mirror(Sys s, BondList bl) {
 __global__ void k_pos_f32(Sys s) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
-  float h;
-  h = (float)s.x[i]; s.xh[i] = h; s.xl[i] = (float)(s.x[i] - (double)h);
-  h = (float)s.y[i]; s.yh[i] = h; s.yl[i] = (float)(s.y[i] - (double)h);
-  h = (float)s.z[i]; s.zh[i] = h; s.zl[i] = (float)(s.z[i] - (double)h);
+  write_pos_f32(s, i);
 }
 
 // displacement since the last build, |(x + img L) - xb|, against skin/2
@@ -546,8 +540,9 @@ __global__ void k_cand_filter(Sys s, CandList cl, FarList f, const DParams<R>* _
       sz += s.img[3 * j + 2] - ii2;
       if (sx >= -1 && sx <= 1 && sy >= -1 && sy <= 1 && sz >= -1 && sz <= 1) {
         code = (sx + 1) * 9 + (sy + 1) * 3 + (sz + 1);
-        const float dx = (s.xh[j] - xi) + sx * Lh[0], dy = (s.yh[j] - yi) + sy * Lh[1];
-        const float dz = (s.zh[j] - zi) + sz * Lh[2];
+        const float4 hj = s.ph[j];
+        const float dx = (hj.x - xi) + sx * Lh[0], dy = (hj.y - yi) + sy * Lh[1];
+        const float dz = (hj.z - zi) + sz * Lh[2];
         const float r2f = dx * dx + dy * dy + dz * dz;
         ok = !(j == i && code == 13) && in_range(s, i, j, code, r, r2f, R2f, margin, R2);
         if (ok) near = in_range(s, i, j, code, r, r2f, Rb2f, margin_near, Rb2);
@@ -558,11 +553,19 @@ __global__ void k_cand_filter(Sys s, CandList cl, FarList f, const DParams<R>* _
     const unsigned below = (1u << lane) - 1u;
     if (ok) {
       R dx, dy, dz;
-      PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
+      int tj;
+      if constexpr (sizeof(R) == 4) {
+        float4 hj, lj;
+        PairVec<float>::getv(s, i, j, code, r, dx, dy, dz, hj, lj);
+        tj = __float_as_int(lj.w);
+      } else {
+        PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
+        tj = s.type[j];
+      }
       const R rr = m_sqrt(dx * dx + dy * dy + dz * dz);
       R tap, dtap;
       taper<R>(rr, P->r_nb, tap, dtap);
-      const R sh3 = rr * rr * rr + P->gamma_m3[ti * MAXT + s.type[j]];
+      const R sh3 = rr * rr * rr + P->gamma_m3[ti * MAXT + tj];
       if (near) {
         const int pos = cntn + __popc(mn & below);
         if (pos < f.capn) {
@@ -694,7 +697,7 @@ void bond_list(const Launch& L, Sys s, FarList f, BondList b, HbList h, AtomQ a,
 namespace {
 __global__ void k_q_to_f32(Sys s) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < s.n) s.qf[i] = (float)s.q[i];
+  if (i < s.n) write_q_f32(s, i, s.q[i]);
 }
 }  // namespace
 void charges_to_f32(const Launch& L, Sys s) {

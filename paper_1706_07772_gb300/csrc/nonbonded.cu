@@ -30,13 +30,23 @@ template <> struct QLoad<float> {
 template <typename R, bool FAST, typename A>
 __device__ __forceinline__ void nb_pair(const Sys& s, const DParams<R>* __restrict__ P, int i, int j, int code, int r,
                                         int ti, R qi, R wv, R wc, A& ev, A& ec, A& fx, A& fy, A& fz, A* w) {
-  R dx, dy, dz;
-  PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
+  R dx, dy, dz, qj;
+  int tj;
+  if constexpr (sizeof(R) == 4) {
+    float4 hj, lj;
+    PairVec<float>::getv(s, i, j, code, r, dx, dy, dz, hj, lj);   // charge and type ride along
+    qj = hj.w;
+    tj = __float_as_int(lj.w);
+  } else {
+    PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
+    qj = QLoad<R>::get(s, j);
+    tj = s.type[j];
+  }
   const R r2 = dx * dx + dy * dy + dz * dz;
   const R rr = m_sqrt(r2);
   R tap, dtap;
   taper<R>(rr, P->r_nb, tap, dtap);
-  const int pt = ti * MAXT + s.type[j];
+  const int pt = ti * MAXT + tj;
   const R pv = P->p_vdW1, ipv = R(1) / P->p_vdW1;
   // van der Waals
   const R rp = FAST ? f_pow(rr, pv) : m_pow(rr, pv);
@@ -52,7 +62,7 @@ __device__ __forceinline__ void nb_pair(const Sys& s, const DParams<R>* __restri
   // Coulomb
   const R sh3 = r2 * rr + P->gamma_m3[pt];
   const R ish = FAST ? f_pow(sh3, R(-1) / R(3)) : R(1) / m_cbrt(sh3);
-  const R kq = P->k_e * qi * QLoad<R>::get(s, j);
+  const R kq = P->k_e * qi * qj;
   const R ecp = kq * ish;
   const R decp = -kq * r2 * ish * ish * ish * ish;
   ev += (A)(tap * evp);

@@ -61,6 +61,7 @@ struct CG {
   void* zg;                                // interleaved (s, t) SpMV operand: float2 or double2
   double* q;
   float* qf;
+  float4* ph;                              // packed records: charge field (may be null)
   double* part;                            // [2][NQ][nchunk] chunk partials, two buffers
   double* scal;                            // [grid][nrep*(NS+NQ)+4] scalars, unless in shared memory
   double* state;                           // [grid][NV_STATE][rows_blk] row state, unless in shared memory
@@ -552,6 +553,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
       const double qi = B.v(V_XS, li) - mu * B.v(V_XT, li);
       a.q[i] = qi;
       a.qf[i] = (float)qi;
+      if (a.ph) ((float*)(a.ph + i))[3] = (float)qi;
     });
   });
 }
@@ -579,7 +581,7 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   a.nh = warm == REAXFF_WARM_EXTRAP ? Q.nhist : 0;
   a.outs = hs(-1); a.outt = ht(-1);                    // the oldest slots
   a.zg = Q.zg;
-  a.q = s.q; a.qf = s.qf; a.part = Q.part; a.scal = Q.scal; a.state = Q.state;
+  a.q = s.q; a.qf = s.qf; a.ph = s.ph; a.part = Q.part; a.scal = Q.scal; a.state = Q.state;
   a.rows_blk = Q.rows_blk; a.scal_smem = Q.scal_smem; a.state_smem = Q.state_smem;
   a.ieta = Q.ieta;
   a.chunk_lo = Q.chunk_lo; a.chunk_rep = Q.chunk_rep; a.rep_chunk = Q.rep_chunk;

@@ -80,6 +80,8 @@ struct Sys {                   // per-atom and per-replica state
   unsigned long long *fx, *fy, *fz;   // fixed-point force accumulators
   double* q;
   float* qf;                   // FP32 copy of q (mixed-path nonbonded)
+  float4* ph;                  // packed FP32 pair records (mixed path; may be null):
+  float4* pl;                  //   ph = (x_hi, y_hi, z_hi, q), pl = (x_lo, y_lo, z_lo, type bits)
   int* err;
   int* img;                    // [3n] box crossings since the last candidate-list build
   double* xb;                  // [3n] wrapped positions at the last candidate-list build
@@ -388,17 +390,45 @@ __device__ __forceinline__ void norm_ff(const float* dh, const float* dl, float&
 }
 
 template <> struct PairVec<float> {
-  static __device__ __forceinline__ void get(const Sys& s, int i, int j, int code, int r, float& dx,
-                                             float& dy, float& dz) {
+  // image vector from the packed records (two 16-byte gathers per atom); hj, lj return
+  // atom j's records for the caller's use of the charge and type fields
+  static __device__ __forceinline__ void getv(const Sys& s, int i, int j, int code, int r, float& dx, float& dy,
+                                              float& dz, float4& hj, float4& lj) {
     int sx, sy, sz;
     shift_decode(code, sx, sy, sz);
     const float* Lh = s.boxh + 3 * r;
     const float* Ll = s.boxl + 3 * r;
-    dx = pv_comp(s.xh[j], s.xh[i], s.xl[j], s.xl[i], sx, Lh[0], Ll[0]);
-    dy = pv_comp(s.yh[j], s.yh[i], s.yl[j], s.yl[i], sy, Lh[1], Ll[1]);
-    dz = pv_comp(s.zh[j], s.zh[i], s.zl[j], s.zl[i], sz, Lh[2], Ll[2]);
+    hj = s.ph[j];
+    lj = s.pl[j];
+    const float4 hi = s.ph[i], li = s.pl[i];
+    dx = pv_comp(hj.x, hi.x, lj.x, li.x, sx, Lh[0], Ll[0]);
+    dy = pv_comp(hj.y, hi.y, lj.y, li.y, sy, Lh[1], Ll[1]);
+    dz = pv_comp(hj.z, hi.z, lj.z, li.z, sz, Lh[2], Ll[2]);
+  }
+  static __device__ __forceinline__ void get(const Sys& s, int i, int j, int code, int r, float& dx,
+                                             float& dy, float& dz) {
+    float4 hj, lj;
+    getv(s, i, j, code, r, dx, dy, dz, hj, lj);
   }
 };
+// FP32 hi/lo position copies of atom i: the split arrays and, when present, the packed
+// records (the charge field is left to the charge writers)
+__device__ __forceinline__ void write_pos_f32(const Sys& s, int i) {
+  const float xh = (float)s.x[i], yh = (float)s.y[i], zh = (float)s.z[i];
+  const float xl = (float)(s.x[i] - (double)xh), yl = (float)(s.y[i] - (double)yh), zl = (float)(s.z[i] - (double)zh);
+  s.xh[i] = xh; s.yh[i] = yh; s.zh[i] = zh;
+  s.xl[i] = xl; s.yl[i] = yl; s.zl[i] = zl;
+  if (s.ph) {
+    float* h = (float*)(s.ph + i);
+    h[0] = xh; h[1] = yh; h[2] = zh;
+    s.pl[i] = make_float4(xl, yl, zl, __int_as_float(s.type[i]));
+  }
+}
+__device__ __forceinline__ void write_q_f32(const Sys& s, int i, double q) {
+  const float qf = (float)q;
+  s.qf[i] = qf;
+  if (s.ph) ((float*)(s.ph + i))[3] = qf;
+}
 // r^2 exactly as the list definition fixes it (FP64, no contraction)
 __device__ __forceinline__ double r2_exact(const Sys& s, int i, int j, int code, int r) {
   double dx, dy, dz;
