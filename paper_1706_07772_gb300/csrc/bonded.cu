@@ -510,204 +510,221 @@ __global__ void k_angles(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<
 }
 
 // ------------------------------------------------------------------ torsion + conjugation
+// One group of TG lanes per canonical bond j-k (the central bond; j < k, or the same atom
+// through a periodic image with shift code > 13). The group's lanes take the
+// (nb_j - 1)(nb_k - 1) choices of an outer bond i-j and l-k; per-quadruple terms go to i, l
+// and the outer bonds by fixed-point atomics, the group totals for j, k and the central
+// bond are combined inside the group (float-float on the mixed path) and added by fixed-
+// point atomics, energies and virial into per-atom fixed-point accumulators. Integer
+// atomics make the result independent of scheduling.
+constexpr int TG = 4;
+
+template <typename R> struct GroupSum;
+template <> struct GroupSum<float> {
+  // every lane of the TG-lane group gets the group total (hi, lo)
+  static __device__ __forceinline__ void run(float& hi, float& lo) {
+#pragma unroll
+    for (int o = TG / 2; o > 0; o >>= 1) {
+      const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+      const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+      float s, e;
+      two_sum(hi, ohi, s, e);
+      lo = __fadd_rn(__fadd_rn(lo, olo), e);
+      hi = s;
+    }
+  }
+  static __device__ __forceinline__ void add(unsigned long long* p, float hi, float lo, int* err) {
+    fix_add_ff(p, hi, lo, err);
+  }
+};
+template <> struct GroupSum<double> {
+  static __device__ __forceinline__ void run(double& hi, double& lo) {
+#pragma unroll
+    for (int o = TG / 2; o > 0; o >>= 1) hi += __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = 0.0;
+  }
+  static __device__ __forceinline__ void add(unsigned long long* p, double hi, double lo, int* err) {
+    fix_add(p, hi + lo, err);
+  }
+};
+
 template <typename R>
-__global__ void k_torsions(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<R>* __restrict__ P,
-                           unsigned mask) {
-  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void __launch_bounds__(128) k_torsions(Sys s, BondList bl, AtomQ aq, Accum acc,
+                                                   const DParams<R>* __restrict__ P, unsigned mask) {
   const int lane = threadIdx.x & 31;
-  if (j >= s.n) return;
-  const int nbj = bl.cnt[j];
-  if (nbj < 2) return;
+  const int sub = lane & (TG - 1);
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int ncanon = *bl.ncanon;
   const R* bo = (const R*)bl.bo;
   const R* bo_pi = (const R*)bl.bo_pi;
   const R wt = wbit<R>(mask, T_TORS), wcj = wbit<R>(mask, T_CONJ);
-  const int tj = s.type[j];
-  R l_etor = 0, l_econ = 0, l_fj[3] = {0, 0, 0}, l_w[6] = {0, 0, 0, 0, 0, 0}, l_cddj = 0;
-  for (int cb = 0; cb < nbj; ++cb) {
-    const int ejk = j * bl.cap + cb;
-    const int k = bl.j[ejk];
-    const int codejk = bl.s[ejk];
-    if (!((j < k) || (j == k && codejk > 13))) continue;
-    const R BO2 = bo[ejk];
-    if (!(BO2 > P->thb_cut)) continue;
-    const int nbk = bl.cnt[k];
-    if (nbk < 2) continue;
-    const int ekj = bl.mirror[ejk];
-    if (ekj / bl.cap != k) continue;                 // mirror missing (flagged by the list pass)
-    const int tk = s.type[k];
-    const int pt = tj * MAXT + tk;
-    const R V1 = P->V1[pt], V2 = P->V2[pt], V3 = P->V3[pt], pt1 = P->p_tor1[pt], pc1 = P->p_cot1[pt];
-    const R pt2 = P->p_tor2, pc2 = P->p_cot2;
-    const R BOpi2 = bo_pi[ejk];
-    R Dsum;
-    if constexpr (sizeof(R) == 4) Dsum = aq.dang_f[j] + aq.dang_f[k];
-    else Dsum = (R)(aq.dang[j] + aq.dang[k]);
-    R f11, df11;
-    f9fun<R>(P->p_tor3, P->p_tor4, Dsum, f11, df11);
-    const R xb = R(2) - BOpi2 - f11;
-    const R ex = m_exp(pt1 * xb * xb);
-    const R g2 = -m_expm1(-pt2 * BO2), dg2 = pt2 * m_exp(-pt2 * BO2);
-    const R h2 = m_exp(-pc2 * (BO2 - R(1.5)) * (BO2 - R(1.5)));
-    const Vec3<R> u2 = load_vec<R>(bl, ejk);
-    const R L2 = dot3(u2, u2), l2 = m_sqrt(L2);
-    int sjk[3];
-    shift_decode(codejk, sjk[0], sjk[1], sjk[2]);
-    R l_fk[3] = {0, 0, 0}, l_cddk = 0, l_cdbo2 = 0, l_cdbopi2 = 0;
-    const int ntot = (nbj - 1) * (nbk - 1);
-    for (int p = lane; p < ntot; p += 32) {
-      int ia = p / (nbk - 1), ic = p % (nbk - 1);
-      const int ea = j * bl.cap + ia + (j * bl.cap + ia >= ejk ? 1 : 0);
-      int ec = k * bl.cap + ic;
-      if (ec >= ekj) ++ec;
-      const int i = bl.j[ea], l = bl.j[ec];
-      if (i == l) {
-        int si[3], sl[3];
-        shift_decode(bl.s[ea], si[0], si[1], si[2]);
-        shift_decode(bl.s[ec], sl[0], sl[1], sl[2]);
-        if (si[0] == sjk[0] + sl[0] && si[1] == sjk[1] + sl[1] && si[2] == sjk[2] + sl[2]) continue;
-      }
-      const R BO1 = bo[ea], BO3 = bo[ec];
-      if (!(BO1 * BO2 * BO3 > P->thb_cut)) continue;
-      const Vec3<R> u1 = load_vec<R>(bl, ea), u3 = load_vec<R>(bl, ec);
-      // Well-conditioned torsion geometry: n1 = u1 x u2, n2 = u3 x u2, A = |n1|, B = |n2|,
-      // P = n1.n2, V = u3.n1 (L2 V^2 = A^2 B^2 - P^2), D0 = l1 l2^2 l3. Then
-      //   s1 s2 = A B / D0 = S,  s1 s2 cos w = P / D0 = C,  s1 s2 cos^3 w = P^3/(A^2 B^2 D0) = M,
-      //   s1 s2 (1 - cos^2 w) = V^2 / (A B l1 l3) = Y,
-      //   E_tors = f10 [V1 (S + C)/2 + V2 e Y + V3 (S + 4M - 3C)/2],  E_conj = K (1 - Y).
-      const Vec3<R> n1 = cross_acc(u1, u2), n2 = cross_acc(u3, u2);
-      const R A2 = dot3(n1, n1), B2 = dot3(n2, n2);
-      const R L1 = dot3(u1, u1), L3 = dot3(u3, u3);
-      const R l1 = m_sqrt(L1), l3 = m_sqrt(L3);
-      const R Am = m_sqrt(A2), Bm = m_sqrt(B2);
-      if (!(Am > R(1e-10) * l1 * l2 && Bm > R(1e-10) * l2 * l3)) continue;   // collinear: sin th ~ 0
-      const R Pn = dot3(n1, n2);
-      const R Vt = dot3(u3, n1);
-      const R D0 = l1 * L2 * l3;
-      const R cw = rclamp(Pn / (Am * Bm), R(-1), R(1));
-      const R S = Am * Bm / D0, Cc = Pn / D0, M = cw * cw * Cc, Y = Vt * Vt / (Am * Bm * l1 * l3);
-      // energy
-      const R g1 = -m_expm1(-pt2 * BO1), g3 = -m_expm1(-pt2 * BO3);
-      const R dg1 = pt2 * m_exp(-pt2 * BO1), dg3 = pt2 * m_exp(-pt2 * BO3);
-      const R f10 = g1 * g2 * g3;
-      const R Tsum = R(0.5) * V1 * (S + Cc) + V2 * ex * Y + R(0.5) * V3 * (S + R(4) * M - R(3) * Cc);
-      const R h1 = m_exp(-pc2 * (BO1 - R(1.5)) * (BO1 - R(1.5)));
-      const R h3 = m_exp(-pc2 * (BO3 - R(1.5)) * (BO3 - R(1.5)));
-      const R K = pc1 * h1 * h2 * h3;
-      const R et = f10 * Tsum;
-      const R ecj = K * (R(1) - Y);
-      l_etor += et;
-      l_econ += ecj;
-      // non-geometric derivatives
-      const R dBO1 = wt * dg1 * g2 * g3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO1 - R(1.5)));
-      const R dBO3 = wt * g1 * g2 * dg3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO3 - R(1.5)));
-      const R dBO2 = wt * g1 * dg2 * g3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO2 - R(1.5)));
-      const R dTdx = V2 * Y * ex * pt1 * R(2) * xb;   // d Tsum / d xb
-      const R dpi = wt * f10 * dTdx * R(-1);
-      const R dD = wt * f10 * dTdx * (-df11);
-      fix_add(bl.cdbo + ea, dBO1, s.err);
-      fix_add(bl.cdbo + ec, dBO3, s.err);
-      l_cdbo2 += dBO2;
-      l_cdbopi2 += dpi;
-      l_cddj += dD;
-      l_cddk += dD;
-      // geometric derivatives through (A, B, P, V, l1, l2, l3)
-      const R dES = wt * f10 * R(0.5) * (V1 + V3);
-      const R dEC = wt * f10 * (R(0.5) * V1 - R(1.5) * V3);
-      const R dEM = wt * f10 * R(2) * V3;
-      const R dEY = wt * f10 * V2 * ex - wcj * K;
-      const R gA = (dES * S - R(2) * dEM * M - dEY * Y) / Am;
-      const R gB = (dES * S - R(2) * dEM * M - dEY * Y) / Bm;
-      const R gP = (dEC + dEM * R(3) * cw * cw) / D0;
-      const R gV = dEY * R(2) * Vt / (Am * Bm * l1 * l3);
-      const R T0 = dES * S + dEC * Cc + dEM * M;
-      const R gl1 = -(T0 + dEY * Y) / L1;             // per unit of u1 (d l1 / d u1 = u1 / l1)
-      const R gl2 = R(-2) * T0 / L2;
-      const R gl3 = -(T0 + dEY * Y) / L3;
-      const R iA = gA / Am, iB = gB / Bm;
-      // dA/du1 = (u2 x n1)/A, dA/du2 = (n1 x u1)/A, dB/du3 = (u2 x n2)/B, dB/du2 = (n2 x u3)/B
-      // dP/du1 = u2 x n2, dP/du2 = n2 x u1 + n1 x u3, dP/du3 = u2 x n1
-      // dV/du1 = u2 x u3, dV/du2 = u3 x u1, dV/du3 = n1
-      const Vec3<R> u2n1 = cross3(u2, n1), u2n2 = cross3(u2, n2), u2u3 = cross3(u2, u3);
-      const Vec3<R> n1u1 = cross3(n1, u1), n2u3 = cross3(n2, u3), n2u1 = cross3(n2, u1), n1u3 = cross3(n1, u3);
-      const Vec3<R> u3u1 = cross3(u3, u1);
-      Vec3<R> gg1, gg2, gg3;
-      gg1.x = iA * u2n1.x + gP * u2n2.x + gV * u2u3.x + gl1 * u1.x;
-      gg1.y = iA * u2n1.y + gP * u2n2.y + gV * u2u3.y + gl1 * u1.y;
-      gg1.z = iA * u2n1.z + gP * u2n2.z + gV * u2u3.z + gl1 * u1.z;
-      gg2.x = iA * n1u1.x + iB * n2u3.x + gP * (n2u1.x + n1u3.x) + gV * u3u1.x + gl2 * u2.x;
-      gg2.y = iA * n1u1.y + iB * n2u3.y + gP * (n2u1.y + n1u3.y) + gV * u3u1.y + gl2 * u2.y;
-      gg2.z = iA * n1u1.z + iB * n2u3.z + gP * (n2u1.z + n1u3.z) + gV * u3u1.z + gl2 * u2.z;
-      gg3.x = iB * u2n2.x + gP * u2n1.x + gV * n1.x + gl3 * u3.x;
-      gg3.y = iB * u2n2.y + gP * u2n1.y + gV * n1.y + gl3 * u3.y;
-      gg3.z = iB * u2n2.z + gP * u2n1.z + gV * n1.z + gl3 * u3.z;
-      force_add<R>(s, i, -gg1.x, -gg1.y, -gg1.z);
-      force_add<R>(s, l, -gg3.x, -gg3.y, -gg3.z);
-      l_fj[0] += gg1.x + gg2.x; l_fj[1] += gg1.y + gg2.y; l_fj[2] += gg1.z + gg2.z;
-      l_fk[0] += gg3.x - gg2.x; l_fk[1] += gg3.y - gg2.y; l_fk[2] += gg3.z - gg2.z;
-      vir_sub(l_w, gg1, u1);
-      vir_sub(l_w, gg2, u2);
-      vir_sub(l_w, gg3, u3);
+  // warp-uniform loop: 32/TG central bonds per warp and pass
+  for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / TG); base < ncanon;
+       base += nwarps * (32 / TG)) {
+    const int t = base + lane / TG;
+    int j = 0, k = 0, ejk = 0, ekj = 0, nbj = 0, nbk = 0, ntot = 0, codejk = 13;
+    if (t < ncanon) {
+      ejk = bl.canon[t];
+      j = ejk / bl.cap;
+      k = bl.j[ejk];
+      codejk = bl.s[ejk];
+      nbj = bl.cnt[j];
+      nbk = bl.cnt[k];
+      ekj = bl.mirror[ejk];
+      if (nbj >= 2 && nbk >= 2 && ekj / bl.cap == k && bo[ejk] > P->thb_cut) ntot = (nbj - 1) * (nbk - 1);
     }
-    if constexpr (sizeof(R) == 4) {
-      // per central bond: float-float totals, lane q adds value q (FP32 only)
-      constexpr int NVK = 6;   // 0-2 F_k, 3 dE/dDelta_k, 4 dE/dBO_jk, 5 dE/dBOpi_jk
-      float hi[NVK] = {l_fk[0], l_fk[1], l_fk[2], l_cddk, l_cdbo2, l_cdbopi2};
-      float lo[NVK];
+    // per-lane partials: 0-2 F_j, 3 dE/dDelta_j, 4 E_tors, 5 E_conj, 6-11 virial (at j),
+    // 12-14 F_k, 15 dE/dDelta_k, 16 dE/dBO_jk, 17 dE/dBOpi_jk
+    constexpr int NV = 18;
+    R v[NV];
 #pragma unroll
-      for (int q = 0; q < NVK; ++q) {
-        lo[q] = 0.0f;
-        warp_sum_ff2(hi[q], lo[q]);
-      }
-      float h, l;
-      lane_pick<NVK>(hi, lo, lane, h, l);
-      if (lane < NVK) {
-        unsigned long long* dst = lane == 0 ? s.fx + k : lane == 1 ? s.fy + k : lane == 2 ? s.fz + k
-                                : lane == 3 ? aq.cddelta + k : lane == 4 ? bl.cdbo + ejk : bl.cdbopi + ejk;
-        fix_add_ff(dst, h, l, s.err);
-      }
-    } else {
-      double fk[3];
-      for (int q = 0; q < 3; ++q) fk[q] = warp_sum_d(l_fk[q]);
-      const double cddk = warp_sum_d(l_cddk);
-      const double cdbo2 = warp_sum_d(l_cdbo2);
-      const double cdbopi2 = warp_sum_d(l_cdbopi2);
-      if (lane == 0) {
-        force_add<double>(s, k, fk[0], fk[1], fk[2]);
-        fix_add(aq.cddelta + k, cddk, s.err);
-        fix_add(bl.cdbo + ejk, cdbo2, s.err);
-        fix_add(bl.cdbopi + ejk, cdbopi2, s.err);
+    for (int q = 0; q < NV; ++q) v[q] = R(0);
+    if (ntot > 0) {
+      const int tj = s.type[j], tk = s.type[k];
+      const int pt = tj * MAXT + tk;
+      const R V1 = P->V1[pt], V2 = P->V2[pt], V3 = P->V3[pt], pt1 = P->p_tor1[pt], pc1 = P->p_cot1[pt];
+      const R pt2 = P->p_tor2, pc2 = P->p_cot2;
+      const R BO2 = bo[ejk];
+      const R BOpi2 = bo_pi[ejk];
+      R Dsum;
+      if constexpr (sizeof(R) == 4) Dsum = aq.dang_f[j] + aq.dang_f[k];
+      else Dsum = (R)(aq.dang[j] + aq.dang[k]);
+      R f11, df11;
+      f9fun<R>(P->p_tor3, P->p_tor4, Dsum, f11, df11);
+      const R xb = R(2) - BOpi2 - f11;
+      const R ex = m_exp(pt1 * xb * xb);
+      const R g2 = -m_expm1(-pt2 * BO2), dg2 = pt2 * m_exp(-pt2 * BO2);
+      const R h2 = m_exp(-pc2 * (BO2 - R(1.5)) * (BO2 - R(1.5)));
+      const Vec3<R> u2 = load_vec<R>(bl, ejk);
+      const R L2 = dot3(u2, u2), l2 = m_sqrt(L2);
+      int sjk[3];
+      shift_decode(codejk, sjk[0], sjk[1], sjk[2]);
+      for (int p = sub; p < ntot; p += TG) {
+        const int ia = p / (nbk - 1), ic = p % (nbk - 1);
+        const int ea = j * bl.cap + ia + (j * bl.cap + ia >= ejk ? 1 : 0);
+        int ec = k * bl.cap + ic;
+        if (ec >= ekj) ++ec;
+        const int i = bl.j[ea], l = bl.j[ec];
+        if (i == l) {
+          int si[3], sl[3];
+          shift_decode(bl.s[ea], si[0], si[1], si[2]);
+          shift_decode(bl.s[ec], sl[0], sl[1], sl[2]);
+          if (si[0] == sjk[0] + sl[0] && si[1] == sjk[1] + sl[1] && si[2] == sjk[2] + sl[2]) continue;
+        }
+        const R BO1 = bo[ea], BO3 = bo[ec];
+        if (!(BO1 * BO2 * BO3 > P->thb_cut)) continue;
+        const Vec3<R> u1 = load_vec<R>(bl, ea), u3 = load_vec<R>(bl, ec);
+        // Well-conditioned torsion geometry: n1 = u1 x u2, n2 = u3 x u2, A = |n1|, B = |n2|,
+        // P = n1.n2, V = u3.n1 (L2 V^2 = A^2 B^2 - P^2), D0 = l1 l2^2 l3. Then
+        //   s1 s2 = A B / D0 = S,  s1 s2 cos w = P / D0 = C,  s1 s2 cos^3 w = P^3/(A^2 B^2 D0) = M,
+        //   s1 s2 (1 - cos^2 w) = V^2 / (A B l1 l3) = Y,
+        //   E_tors = f10 [V1 (S + C)/2 + V2 e Y + V3 (S + 4M - 3C)/2],  E_conj = K (1 - Y).
+        const Vec3<R> n1 = cross_acc(u1, u2), n2 = cross_acc(u3, u2);
+        const R A2 = dot3(n1, n1), B2 = dot3(n2, n2);
+        const R L1 = dot3(u1, u1), L3 = dot3(u3, u3);
+        const R l1 = m_sqrt(L1), l3 = m_sqrt(L3);
+        const R Am = m_sqrt(A2), Bm = m_sqrt(B2);
+        if (!(Am > R(1e-10) * l1 * l2 && Bm > R(1e-10) * l2 * l3)) continue;   // collinear: sin th ~ 0
+        const R Pn = dot3(n1, n2);
+        const R Vt = dot3(u3, n1);
+        const R D0 = l1 * L2 * l3;
+        const R cw = rclamp(Pn / (Am * Bm), R(-1), R(1));
+        const R S = Am * Bm / D0, Cc = Pn / D0, M = cw * cw * Cc, Y = Vt * Vt / (Am * Bm * l1 * l3);
+        // energy
+        const R g1 = -m_expm1(-pt2 * BO1), g3 = -m_expm1(-pt2 * BO3);
+        const R dg1 = pt2 * m_exp(-pt2 * BO1), dg3 = pt2 * m_exp(-pt2 * BO3);
+        const R f10 = g1 * g2 * g3;
+        const R Tsum = R(0.5) * V1 * (S + Cc) + V2 * ex * Y + R(0.5) * V3 * (S + R(4) * M - R(3) * Cc);
+        const R h1 = m_exp(-pc2 * (BO1 - R(1.5)) * (BO1 - R(1.5)));
+        const R h3 = m_exp(-pc2 * (BO3 - R(1.5)) * (BO3 - R(1.5)));
+        const R K = pc1 * h1 * h2 * h3;
+        const R et = f10 * Tsum;
+        const R ecj = K * (R(1) - Y);
+        v[4] += et;
+        v[5] += ecj;
+        // non-geometric derivatives
+        const R dBO1 = wt * dg1 * g2 * g3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO1 - R(1.5)));
+        const R dBO3 = wt * g1 * g2 * dg3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO3 - R(1.5)));
+        const R dBO2 = wt * g1 * dg2 * g3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO2 - R(1.5)));
+        const R dTdx = V2 * Y * ex * pt1 * R(2) * xb;   // d Tsum / d xb
+        const R dpi = wt * f10 * dTdx * R(-1);
+        const R dD = wt * f10 * dTdx * (-df11);
+        fix_add(bl.cdbo + ea, dBO1, s.err);
+        fix_add(bl.cdbo + ec, dBO3, s.err);
+        v[16] += dBO2;
+        v[17] += dpi;
+        v[3] += dD;
+        v[15] += dD;
+        // geometric derivatives through (A, B, P, V, l1, l2, l3)
+        const R dES = wt * f10 * R(0.5) * (V1 + V3);
+        const R dEC = wt * f10 * (R(0.5) * V1 - R(1.5) * V3);
+        const R dEM = wt * f10 * R(2) * V3;
+        const R dEY = wt * f10 * V2 * ex - wcj * K;
+        const R gA = (dES * S - R(2) * dEM * M - dEY * Y) / Am;
+        const R gB = (dES * S - R(2) * dEM * M - dEY * Y) / Bm;
+        const R gP = (dEC + dEM * R(3) * cw * cw) / D0;
+        const R gV = dEY * R(2) * Vt / (Am * Bm * l1 * l3);
+        const R T0 = dES * S + dEC * Cc + dEM * M;
+        const R gl1 = -(T0 + dEY * Y) / L1;             // per unit of u1 (d l1 / d u1 = u1 / l1)
+        const R gl2 = R(-2) * T0 / L2;
+        const R gl3 = -(T0 + dEY * Y) / L3;
+        const R iA = gA / Am, iB = gB / Bm;
+        // dA/du1 = (u2 x n1)/A, dA/du2 = (n1 x u1)/A, dB/du3 = (u2 x n2)/B, dB/du2 = (n2 x u3)/B
+        // dP/du1 = u2 x n2, dP/du2 = n2 x u1 + n1 x u3, dP/du3 = u2 x n1
+        // dV/du1 = u2 x u3, dV/du2 = u3 x u1, dV/du3 = n1
+        const Vec3<R> u2n1 = cross3(u2, n1), u2n2 = cross3(u2, n2), u2u3 = cross3(u2, u3);
+        const Vec3<R> n1u1 = cross3(n1, u1), n2u3 = cross3(n2, u3), n2u1 = cross3(n2, u1), n1u3 = cross3(n1, u3);
+        const Vec3<R> u3u1 = cross3(u3, u1);
+        Vec3<R> gg1, gg2, gg3;
+        gg1.x = iA * u2n1.x + gP * u2n2.x + gV * u2u3.x + gl1 * u1.x;
+        gg1.y = iA * u2n1.y + gP * u2n2.y + gV * u2u3.y + gl1 * u1.y;
+        gg1.z = iA * u2n1.z + gP * u2n2.z + gV * u2u3.z + gl1 * u1.z;
+        gg2.x = iA * n1u1.x + iB * n2u3.x + gP * (n2u1.x + n1u3.x) + gV * u3u1.x + gl2 * u2.x;
+        gg2.y = iA * n1u1.y + iB * n2u3.y + gP * (n2u1.y + n1u3.y) + gV * u3u1.y + gl2 * u2.y;
+        gg2.z = iA * n1u1.z + iB * n2u3.z + gP * (n2u1.z + n1u3.z) + gV * u3u1.z + gl2 * u2.z;
+        gg3.x = iB * u2n2.x + gP * u2n1.x + gV * n1.x + gl3 * u3.x;
+        gg3.y = iB * u2n2.y + gP * u2n1.y + gV * n1.y + gl3 * u3.y;
+        gg3.z = iB * u2n2.z + gP * u2n1.z + gV * n1.z + gl3 * u3.z;
+        force_add<R>(s, i, -gg1.x, -gg1.y, -gg1.z);
+        force_add<R>(s, l, -gg3.x, -gg3.y, -gg3.z);
+        v[0] += gg1.x + gg2.x; v[1] += gg1.y + gg2.y; v[2] += gg1.z + gg2.z;
+        v[12] += gg3.x - gg2.x; v[13] += gg3.y - gg2.y; v[14] += gg3.z - gg2.z;
+        vir_sub(v + 6, gg1, u1);
+        vir_sub(v + 6, gg2, u2);
+        vir_sub(v + 6, gg3, u3);
       }
     }
-  }
-  if constexpr (sizeof(R) == 4) {
-    constexpr int NVJ = 12;   // 0-1 E_tors, E_conj; 2-4 F_j; 5 dE/dDelta_j; 6-11 virial
-    float hi[NVJ] = {l_etor, l_econ, l_fj[0], l_fj[1], l_fj[2], l_cddj, l_w[0], l_w[1], l_w[2], l_w[3], l_w[4], l_w[5]};
-    float lo[NVJ];
+    // group totals (all lanes take part: the shuffles span the whole warp), then lane q of
+    // the group adds values q, q + TG, q + 2 TG
+    R hi[NV], lo[NV];
 #pragma unroll
-    for (int q = 0; q < NVJ; ++q) {
-      lo[q] = 0.0f;
-      warp_sum_ff2(hi[q], lo[q]);
+    for (int q = 0; q < NV; ++q) {
+      hi[q] = v[q];
+      lo[q] = R(0);
+      GroupSum<R>::run(hi[q], lo[q]);
     }
-    float h, l;
-    lane_pick<NVJ>(hi, lo, lane, h, l);
-    if (lane < 2) {
-      acc.e[(T_TORS + lane) * s.n + j] = (double)h + (double)l;
-    } else if (lane < 6) {
-      fix_add_ff((lane == 2 ? s.fx + j : lane == 3 ? s.fy + j : lane == 4 ? s.fz + j : aq.cddelta + j), h, l, s.err);
-    } else if (lane < NVJ) {
-      acc.vir[(lane - 6) * s.n + j] += (double)h + (double)l;
-    }
-  } else {
-    const double etor = warp_sum_d(l_etor), econ = warp_sum_d(l_econ), cddj = warp_sum_d(l_cddj);
-    double fj[3], w[6];
-    for (int q = 0; q < 3; ++q) fj[q] = warp_sum_d(l_fj[q]);
-    for (int q = 0; q < 6; ++q) w[q] = warp_sum_d(l_w[q]);
-    if (lane == 0) {
-      acc.e[T_TORS * s.n + j] = etor;
-      acc.e[T_CONJ * s.n + j] = econ;
-      force_add<double>(s, j, fj[0], fj[1], fj[2]);
-      fix_add(aq.cddelta + j, cddj, s.err);
-      for (int q = 0; q < 6; ++q) acc.vir[q * s.n + j] += w[q];
+    if (ntot > 0) {
+#pragma unroll
+      for (int rnd = 0; rnd < (NV + TG - 1) / TG; ++rnd) {
+        const int q = sub + rnd * TG;
+        R h = R(0), l = R(0);
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+          if (c == q) {
+            h = hi[c];
+            l = lo[c];
+          }
+        unsigned long long* dst = nullptr;
+        if (q < 3) dst = (q == 0 ? s.fx : q == 1 ? s.fy : s.fz) + j;
+        else if (q == 3) dst = aq.cddelta + j;
+        else if (q < 6) dst = acc.efx + (size_t)(q - 4) * s.n + j;
+        else if (q < 12) dst = acc.vfx + (size_t)(q - 6) * s.n + j;
+        else if (q < 15) dst = (q == 12 ? s.fx : q == 13 ? s.fy : s.fz) + k;
+        else if (q == 15) dst = aq.cddelta + k;
+        else if (q == 16) dst = bl.cdbo + ejk;
+        else if (q == 17) dst = bl.cdbopi + ejk;
+        if (dst) GroupSum<R>::add(dst, h, l, s.err);
+      }
     }
   }
 }
@@ -855,7 +872,10 @@ void angles(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParam
 }
 template <typename R>
 void torsions(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P, unsigned mask) {
-  k_torsions<R><<<grid_for((long long)s.n * 32, 128), 128, 0, L.st>>>(s, b, a, acc, P, mask);
+  // central bonds: at most one per directed entry pair; about one per atom in molecular
+  // systems. The grid covers n central bonds in one pass and loops beyond that.
+  const long long threads = (long long)s.n * TG;
+  k_torsions<R><<<grid_for(threads, 128), 128, 0, L.st>>>(s, b, a, acc, P, mask);
   *L.count += 1;
 }
 template <typename R>

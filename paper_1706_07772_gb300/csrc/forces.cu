@@ -108,8 +108,10 @@ __global__ void k_finalize(Sys s, double* F) {
 // Both passes have a fixed reduction order, so the sums are bitwise reproducible.
 constexpr int NQ_RED = NTERMS + 7;
 __device__ __forceinline__ double red_value(const Sys& s, const Accum& acc, const double* mass_t, int q, int64_t i) {
+  if (q == T_TORS || q == T_CONJ) return acc.e[(size_t)q * s.n + i] + fix_get(acc.efx + (size_t)(q - T_TORS) * s.n + i);
   if (q < NTERMS) return acc.e[(size_t)q * s.n + i];
-  if (q < NTERMS + 6) return acc.vir[(size_t)(q - NTERMS) * s.n + i];
+  if (q < NTERMS + 6)
+    return acc.vir[(size_t)(q - NTERMS) * s.n + i] + fix_get(acc.vfx + (size_t)(q - NTERMS) * s.n + i);
   const double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
   return 0.5 * mass_t[s.type[i]] * (vx * vx + vy * vy + vz * vz) / 4.184e-4;
 }

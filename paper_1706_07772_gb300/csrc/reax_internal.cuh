@@ -162,9 +162,11 @@ struct AtomQ {                 // per-atom bond-order quantities (double)
   float *sumbo_f, *dang_f;     // FP32 copies for the mixed-path angle and torsion kernels
 };
 
-struct Accum {                 // per-atom energies and virial (owner-written, double)
-  double* e;                   // [NTERMS*n]
-  double* vir;                 // [6*n]
+struct Accum {                 // per-atom energies and virial
+  double* e;                   // [NTERMS*n] owner-written
+  double* vir;                 // [6*n] owner-accumulated
+  unsigned long long* efx;     // [2*n] torsion, conjugation energies (fixed point, atomics)
+  unsigned long long* vfx;     // [6*n] virial contributions added by atomics (fixed point)
 };
 
 // ------------------------------------------------------------------ device helpers
