@@ -78,6 +78,75 @@ __device__ __forceinline__ void nb_pair(const Sys& s, const DParams<R>* __restri
   w[3] += (A)(hc * dx * dy); w[4] += (A)(hc * dx * dz); w[5] += (A)(hc * dy * dz);
 }
 
+// MUFU approximations (PTX ex2/lg2/rcp/rsqrt .approx): the far pairs' transcendentals run
+// at these accuracies already (pow and exp as ex2(y lg2 x)), and they replace the
+// correctly rounded square root and divisions there as well
+__device__ __forceinline__ float ex2a(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2a(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcpa(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqa(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// one far directed pair (r_bond <= r < r_nb) on the mixed path: the terms of nb_pair with
+// r^-1 from rsqrt, x^y = 2^(y log2 x), e^x = 2^(x log2 e) and reciprocals by rcp
+template <typename A>
+__device__ __forceinline__ void nb_pair_far(const Sys& s, const DParams<float>* __restrict__ P, int i, int j, int code,
+                                            int r, int ti, float qi, float wv, float wc, float iRc, float pv, float ipv,
+                                            A& ev, A& ec, A& fx, A& fy, A& fz, A* w) {
+  float dx, dy, dz;
+  float4 hj, lj;
+  PairVec<float>::getv(s, i, j, code, r, dx, dy, dz, hj, lj);
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  const float ir = rsqa(r2);
+  const float rr = r2 * ir;
+  const float x = rr * iRc, x2 = x * x, x3 = x2 * x;
+  const float tap = ((((20.0f * x - 70.0f) * x + 84.0f) * x - 35.0f) * x2 * x2) + 1.0f;
+  const float dtap = ((((140.0f * x - 420.0f) * x + 420.0f) * x - 140.0f) * x3) * iRc;
+  const int pt = ti * MAXT + __float_as_int(lj.w);
+  // van der Waals
+  const float rp = ex2a(pv * lg2a(rr));
+  const float base = rp + P->vdw_gw_pow[pt];
+  const float f13 = ex2a(ipv * lg2a(base));
+  const float df13 = f13 * rp * ir * rcpa(base);
+  const float al = P->vdw_alpha[pt], irv = rcpa(P->vdw_rv[pt]), D = P->vdw_D[pt];
+  const float t = al * (1.0f - f13 * irv) * 1.44269504088896341f;   // al (1 - f13/rv) log2(e)
+  const float E1 = ex2a(t), E2 = ex2a(0.5f * t);
+  const float evp = D * (E1 - 2.0f * E2);
+  const float devp = -(D * al * irv) * (E1 - E2);
+  // Coulomb
+  const float sh3 = r2 * rr + P->gamma_m3[pt];
+  const float ish = ex2a(-0.333333343f * lg2a(sh3));
+  const float kq = P->k_e * qi * hj.w;
+  const float ecp = kq * ish;
+  const float ish2 = ish * ish;
+  const float decp = -kq * r2 * ish2 * ish2;
+  ev += (A)(tap * evp);
+  ec += (A)(tap * ecp);
+  const float de = wv * (dtap * evp + tap * devp * df13) + wc * (dtap * ecp + tap * decp);
+  const float c = de * ir;
+  fx += (A)(c * dx);
+  fy += (A)(c * dy);
+  fz += (A)(c * dz);
+  const float hc = -0.5f * c;
+  w[0] += (A)(hc * dx * dx); w[1] += (A)(hc * dy * dy); w[2] += (A)(hc * dz * dz);
+  w[3] += (A)(hc * dx * dy); w[4] += (A)(hc * dx * dz); w[5] += (A)(hc * dy * dz);
+}
+
 template <typename R>
 __global__ void k_nonbonded(Sys s, FarList f, Accum acc, const DParams<R>* __restrict__ P, unsigned mask) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -97,8 +166,14 @@ __global__ void k_nonbonded(Sys s, FarList f, Accum acc, const DParams<R>* __res
   // far part (r_bond <= r < r_nb): MUFU pow/exp in FP32
   R lev = 0, lec = 0, lfx = 0, lfy = 0, lfz = 0, lw[6] = {0, 0, 0, 0, 0, 0};
   const int nfa = f.cnt[i], rowf = i * f.cap;
-  for (int k = lane; k < nfa; k += 32)
-    nb_pair<R, true, R>(s, P, i, f.j[rowf + k], f.s[rowf + k], r, ti, qi, wv, wc, lev, lec, lfx, lfy, lfz, lw);
+  if constexpr (sizeof(R) == 4) {
+    const float iRc = 1.0f / P->r_nb, pv = P->p_vdW1, ipv = 1.0f / P->p_vdW1;
+    for (int k = lane; k < nfa; k += 32)
+      nb_pair_far<R>(s, P, i, f.j[rowf + k], f.s[rowf + k], r, ti, qi, wv, wc, iRc, pv, ipv, lev, lec, lfx, lfy, lfz, lw);
+  } else {
+    for (int k = lane; k < nfa; k += 32)
+      nb_pair<R, true, R>(s, P, i, f.j[rowf + k], f.s[rowf + k], r, ti, qi, wv, wc, lev, lec, lfx, lfy, lfz, lw);
+  }
   if constexpr (sizeof(R) == 4) {
     // near + far partials joined error-free per lane, float-float warp totals (FP32 only),
     // then lane q handles value q: the FP64 conversions are one warp instruction each
