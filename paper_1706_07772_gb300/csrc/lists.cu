@@ -504,6 +504,7 @@ __global__ void k_cand_build(Sys s, Cells c, CandList cl) {
   if (lane < 3) {
     s.xb[3 * i + lane] = lane == 0 ? s.x[i] : (lane == 1 ? s.y[i] : s.z[i]);
     s.img[3 * i + lane] = 0;
+    if (lane == 0 && s.pl) ((float*)(s.pl + i))[3] = pack_type_img(s.type[i], 0, 0, 0);
   }
 }
 
@@ -520,7 +521,8 @@ __global__ void k_cand_filter(Sys s, CandList cl, FarList f, const DParams<R>* _
   const float* Lh = s.boxh + 3 * r;
   const float R2f = (float)R2, Rb2f = (float)Rb2;
   const float xi = s.xh[i], yi = s.yh[i], zi = s.zh[i];
-  const int ii0 = s.img[3 * i], ii1 = s.img[3 * i + 1], ii2 = s.img[3 * i + 2];
+  int ii0, ii1, ii2;
+  rec_img(s.pl[i].w, ii0, ii1, ii2);
   const int ti = s.type[i];
   const int nc = cl.cnt[i], crow = i * cl.cap;
   int cntn = 0, cntf = 0;
@@ -533,14 +535,15 @@ __global__ void k_cand_filter(Sys s, CandList cl, FarList f, const DParams<R>* _
     int j = -1, code = 13;
     if (k < nc) {
       j = cl.j[crow + k];
-      int sx, sy, sz;
+      int sx, sy, sz, jx, jy, jz;
       shift_decode(cl.s[crow + k], sx, sy, sz);
-      sx += s.img[3 * j] - ii0;
-      sy += s.img[3 * j + 1] - ii1;
-      sz += s.img[3 * j + 2] - ii2;
+      const float4 hj = s.ph[j];
+      rec_img(s.pl[j].w, jx, jy, jz);                   // crossing counters ride in the record
+      sx += jx - ii0;
+      sy += jy - ii1;
+      sz += jz - ii2;
       if (sx >= -1 && sx <= 1 && sy >= -1 && sy <= 1 && sz >= -1 && sz <= 1) {
         code = (sx + 1) * 9 + (sy + 1) * 3 + (sz + 1);
-        const float4 hj = s.ph[j];
         const float dx = (hj.x - xi) + sx * Lh[0], dy = (hj.y - yi) + sy * Lh[1];
         const float dz = (hj.z - zi) + sz * Lh[2];
         const float r2f = dx * dx + dy * dy + dz * dz;
@@ -557,7 +560,7 @@ __global__ void k_cand_filter(Sys s, CandList cl, FarList f, const DParams<R>* _
       if constexpr (sizeof(R) == 4) {
         float4 hj, lj;
         PairVec<float>::getv(s, i, j, code, r, dx, dy, dz, hj, lj);
-        tj = __float_as_int(lj.w);
+        tj = rec_type(lj.w);
       } else {
         PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
         tj = s.type[j];

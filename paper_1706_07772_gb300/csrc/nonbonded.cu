@@ -36,7 +36,7 @@ __device__ __forceinline__ void nb_pair(const Sys& s, const DParams<R>* __restri
     float4 hj, lj;
     PairVec<float>::getv(s, i, j, code, r, dx, dy, dz, hj, lj);   // charge and type ride along
     qj = hj.w;
-    tj = __float_as_int(lj.w);
+    tj = rec_type(lj.w);
   } else {
     PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
     qj = QLoad<R>::get(s, j);
@@ -117,7 +117,7 @@ __device__ __forceinline__ void nb_pair_far(const Sys& s, const DParams<float>* 
   const float x = rr * iRc, x2 = x * x, x3 = x2 * x;
   const float tap = ((((20.0f * x - 70.0f) * x + 84.0f) * x - 35.0f) * x2 * x2) + 1.0f;
   const float dtap = ((((140.0f * x - 420.0f) * x + 420.0f) * x - 140.0f) * x3) * iRc;
-  const int pt = ti * MAXT + __float_as_int(lj.w);
+  const int pt = ti * MAXT + rec_type(lj.w);
   // van der Waals
   const float rp = ex2a(pv * lg2a(rr));
   const float base = rp + P->vdw_gw_pow[pt];

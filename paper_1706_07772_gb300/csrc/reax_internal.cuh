@@ -413,6 +413,19 @@ template <> struct PairVec<float> {
     getv(s, i, j, code, r, dx, dy, dz, hj, lj);
   }
 };
+// Fourth word of a pl record: type (8 bits) and the three box-crossing counters since the
+// last candidate-list build (8-bit two's complement each; an atom moves less than half the
+// skin between builds, so each counter is -1, 0 or 1 there)
+__device__ __forceinline__ float pack_type_img(int type, int ix, int iy, int iz) {
+  return __int_as_float((type & 0xff) | ((ix & 0xff) << 8) | ((iy & 0xff) << 16) | ((iz & 0xff) << 24));
+}
+__device__ __forceinline__ int rec_type(float w) { return __float_as_int(w) & 0xff; }
+__device__ __forceinline__ void rec_img(float w, int& ix, int& iy, int& iz) {
+  const int b = __float_as_int(w);
+  ix = (b << 16) >> 24;
+  iy = (b << 8) >> 24;
+  iz = b >> 24;
+}
 // FP32 hi/lo position copies of atom i: the split arrays and, when present, the packed
 // records (the charge field is left to the charge writers)
 __device__ __forceinline__ void write_pos_f32(const Sys& s, int i) {
@@ -423,7 +436,7 @@ __device__ __forceinline__ void write_pos_f32(const Sys& s, int i) {
   if (s.ph) {
     float* h = (float*)(s.ph + i);
     h[0] = xh; h[1] = yh; h[2] = zh;
-    s.pl[i] = make_float4(xl, yl, zl, __int_as_float(s.type[i]));
+    s.pl[i] = make_float4(xl, yl, zl, pack_type_img(s.type[i], s.img[3 * i], s.img[3 * i + 1], s.img[3 * i + 2]));
   }
 }
 __device__ __forceinline__ void write_q_f32(const Sys& s, int i, double q) {
