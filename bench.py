@@ -135,7 +135,23 @@ def peaks():
 # ---------------------------------------------------------------------------------------
 # algorithmic cost model of the timed stages (per launch), from the list sizes
 # ---------------------------------------------------------------------------------------
-def stage_costs(ctx, n, prec_bytes, qeq_iters):
+def cg_traffic_per_spmv():
+    """DRAM bytes per SpMV of k_cg from the committed ncu summary, or None when qeq.cu has
+    changed since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_cg_petn32k_mixed.md")
+    src = os.path.join(ROOT, "paper_1706_07772_gb300", "csrc", "qeq.cu")
+    try:
+        txt = open(path).read()
+        per = int(txt.split("traffic_bytes_per_spmv:")[1].split()[0])
+        sha = txt.split("source_sha256 qeq.cu:")[1].split()[0]
+    except (OSError, IndexError, ValueError):
+        return None
+    with open(src, "rb") as f:
+        return per if hashlib.sha256(f.read()).hexdigest() == sha else None
+
+
+def stage_costs(ctx, n, prec_bytes, spmv_per_launch):
     """Algorithmic bytes per launch of the memory-bound stages:
       far_list  : write j (4 B) + image code (1 B) + H entry (R) per full-list entry
       qeq       : one read of H (index 4 B + value R) for both systems per SpMV: the
@@ -145,10 +161,9 @@ def stage_costs(ctx, n, prec_bytes, qeq_iters):
     """
     import paper_1706_07772_gb300.reaxff as rx
     nfar = ctx.get_lists(rx.LIST_FAR)[0].size
-    it = max(1, int(qeq_iters))
     return {
         "far_list": {"bytes": nfar * (5 + prec_bytes), "entries": nfar},
-        "qeq": {"bytes": (it + 1) * nfar * (4 + prec_bytes), "iters": it},
+        "qeq": {"bytes": spmv_per_launch * nfar * (4 + prec_bytes), "spmv": spmv_per_launch},
         "nonbonded": {"bytes": nfar * 5, "entries": nfar},
     }
 
@@ -182,6 +197,7 @@ def run_ours(a, rank, world):
     ctx.profile_enable(True)
     launches = 0
     ms_total = 0.0
+    spmv_sum = 0
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
@@ -196,6 +212,8 @@ def run_ours(a, rank, world):
         e1.synchronize()
         ms_total += e0.elapsed_time(e1)
         launches += ctx.last_launch_count()
+        its_k, itt_k = ctx.last_qeq_iters()                 # after the step (outside the events)
+        spmv_sum += 1 + max(int(its_k.max()), int(itt_k.max()))
     torch.cuda.synchronize()
     barrier(world)
     clocks.stop()
@@ -224,9 +242,16 @@ def run_ours(a, rank, world):
     out["stages"] = {k: round(v["ms_per_step"], 4) for k, v in sorted(stages.items(), key=lambda t: -t[1]["ms_per_step"])}
     # roofline of the dominant stage
     pk = peaks()
-    costs = stage_costs(ctx, n, 4 if prec == rx.MIXED else 8, int(its[0]) + 0)
+    spmv = spmv_sum / max(a.steps, 1)                        # SpMVs per QEq launch, averaged
+    costs = stage_costs(ctx, n, 4 if prec == rx.MIXED else 8, spmv)
     dom = max(stages, key=lambda k: stages[k]["ms_per_step"])
     out["roofline"] = roofline(dom, stages, costs, pk, prec)
+    if dom == "qeq" and prec == rx.MIXED and a.workload == "petn32k":
+        per = cg_traffic_per_spmv()
+        out["roofline"]["traffic"] = None if per is None else per * spmv
+        out["roofline"]["traffic_source"] = ("profiles/k_cg_petn32k_mixed.md (DRAM bytes per SpMV x SpMVs per launch)"
+                                            if per is not None else "kernel changed since the ncu capture")
+    out["qeq_spmv_per_launch"] = spmv
     out["_ctx"] = ctx
     out["_w"] = w
     out["_P"] = P
