@@ -186,9 +186,17 @@ int reaxff_forces(reaxff_ctx* ctx, double* F, double* E, double* virial);
 int reaxff_forces_fixed_q(reaxff_ctx* ctx, const double* q, double* F, double* E,
                           double* virial);
 
-/* nsteps velocity-Verlet steps of dt_fs. Each step rebuilds lists, solves QEq and
- * recomputes forces. E_tot (double[nsteps*nrep] or NULL) receives the total
- * (potential + kinetic) energy per step and replica. */
+/* nsteps velocity-Verlet steps of dt_fs (Sec. 4.1: dt = 0.1 fs). Each step updates the
+ * lists, solves QEq and recomputes forces. E_tot (double[nsteps*nrep] or NULL) receives
+ * the total (potential + kinetic) energy per step and replica.
+ * The steps of one call run without host synchronisation (one CUDA graph per step where
+ * stream capture is available); the device error flags are read once at the end. If a
+ * list capacity overflowed anywhere in the call, the call is rolled back to its starting
+ * positions, velocities and QEq history, the lists are regrown, and the steps are redone
+ * with a check after every list build; the results are then the same as if the capacity
+ * had been large enough from the start (up to the QEq history, which only moves the CG
+ * starting point). Other errors (E_NAN, E_TIMEOUT, E_NOT_CONVERGED) are reported for
+ * the call as a whole. */
 int reaxff_step(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot);
 
 /* Kernel launches issued by the last reaxff_step call (for launch accounting). */
@@ -199,6 +207,11 @@ int reaxff_last_qeq_iters(reaxff_ctx* ctx, int32_t* iters_s, int32_t* iters_t);
 
 /* Forget the QEq solution history (the next solve starts from zero). */
 void reaxff_reset_qeq_history(reaxff_ctx* ctx);
+
+/* Sparse matrix-vector products (one read of H for both systems) performed by all QEq
+ * solves of this context since its creation: the initial residual of every solve plus
+ * one per CG iteration. Synchronises the context's stream; -1 on a CUDA error. */
+int64_t reaxff_qeq_spmv_total(reaxff_ctx* ctx);
 
 /* Per-stage timing with CUDA events recorded on the context's stream around every
  * kernel group (cells, far_list, bond_list, bo_prime64, qeq, bo_correct, atom_terms,

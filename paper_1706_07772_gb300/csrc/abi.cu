@@ -10,6 +10,8 @@
 
 #include "reax_internal.cuh"
 
+constexpr int ETOT_CHUNK = 256;   // steps per batch of device-side total energies
+
 std::string cuda_err_str(cudaError_t e) { return std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e); }
 
 namespace {
@@ -72,6 +74,20 @@ struct reaxff_ctx {
   bool use_skin = true;
   double skin = 1.0;
   CandList cand{};
+  // MD steps without host synchronisation: one CUDA graph per step (captured on first use,
+  // dropped when the list buffers, dt or the profiling switch change), flags checked once
+  // per call; a call that overflowed a list capacity is rolled back from a snapshot
+  cudaGraphExec_t gexec = nullptr;
+  bool capturing = false;      // inside a step capture: stage events become graph nodes
+  bool graph_ok = true;        // capture works here (else the steps are launched directly)
+  double g_dt = 0.0;
+  bool g_prof = false;
+  int64_t g_launches = 0;
+  std::vector<std::pair<int, int>> g_events;
+  double* etot_buf = nullptr;  // [ETOT_CHUNK * nrep] per-step total energies
+  int* etot_idx = nullptr;     // device step index into etot_buf
+  double* snap = nullptr;      // x, v (6n) and the QEq rings (7n)
+  int* snap_i = nullptr;       // the rings' state (4)
   // per-stage CUDA-event timing (reaxff_profile_*)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -148,7 +164,13 @@ void rx_fill_params_double(DParams<double>& d, const reaxff_params& p, const rea
 namespace {
 
 // allocate the three lists at the current capacities
+void drop_graph(reaxff_ctx* ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
+}
+
 int alloc_lists(reaxff_ctx* ctx) {
+  drop_graph(ctx);
   ctx->lists.free_all();
   DevBuf& B = ctx->lists;
   const size_t n = ctx->n;
@@ -222,12 +244,17 @@ struct Stage {
       ctx->ev_pool.push_back(e);
     }
     idx = (int)(2 * ctx->ev_pending.size());
-    cudaEventRecord(ctx->ev_pool[idx], ctx->st);
+    record(ctx->ev_pool[idx]);
   }
   ~Stage() {
     if (idx < 0) return;
-    cudaEventRecord(ctx->ev_pool[idx + 1], ctx->st);
+    record(ctx->ev_pool[idx + 1]);
     ctx->ev_pending.push_back({id, idx});
+  }
+  // under stream capture an event must be recorded as an external node to be timed later
+  void record(cudaEvent_t e) {
+    if (ctx->capturing) cudaEventRecordWithFlags(e, ctx->st, cudaEventRecordExternal);
+    else cudaEventRecord(e, ctx->st);
   }
 };
 
@@ -251,10 +278,22 @@ int read_err(reaxff_ctx* ctx, int* flags) {
   return REAXFF_OK;
 }
 
-int build_lists_impl(reaxff_ctx* ctx) {
+// capacities after an overflow (flags from the device)
+void grow_caps(reaxff_ctx* ctx, int flags) {
+  if (flags & ERR_CAP_FAR) ctx->cap_far = round_up(ctx->cap_far * 1.5, 32);
+  if (flags & ERR_CAP_NEAR) ctx->cap_near = round_up(ctx->cap_near * 1.5, 32);
+  if (flags & ERR_CAP_CAND) ctx->cap_cand = round_up(ctx->cap_cand * 1.5, 32);
+  if (flags & ERR_CAP_BOND) ctx->cap_bond = round_up(ctx->cap_bond * 1.5, 8);
+  if (flags & ERR_CAP_HB) ctx->cap_hb = round_up(ctx->cap_hb * 1.5, 32);
+}
+
+// checked: clear the flags, read them back after the build and regrow and retry on a
+// capacity overflow (host synchronisation). Unchecked: launches only; the caller reads the
+// flags later (the error word is not cleared, so earlier flags of a batch survive).
+int build_lists_impl(reaxff_ctx* ctx, bool checked = true) {
   for (int attempt = 0; attempt < 3; ++attempt) {
     rx::Launch L = launch_of(ctx);
-    CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
+    if (checked) CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
     CK(cudaMemsetAsync(ctx->bond.ncanon, 0, sizeof(int), ctx->st));
     if (ctx->use_skin) {
       // Verlet-skin candidates (rebuilt on the device only when an atom moved > skin/2),
@@ -283,6 +322,10 @@ int build_lists_impl(reaxff_ctx* ctx) {
     { Stage st(ctx, 2); rx::bond_mirror(L, ctx->sys, ctx->bond); }
     { Stage st(ctx, 3); rx::bo_prime64(L, ctx->sys, ctx->bond, ctx->aq, ctx->Pd, ctx->n * ctx->bond.cap); }
     CK(cudaGetLastError());
+    if (!checked) {
+      ctx->lists_valid = true;
+      return REAXFF_OK;
+    }
     int flags = 0;
     int rc = read_err(ctx, &flags);
     if (rc) return rc;
@@ -292,11 +335,7 @@ int build_lists_impl(reaxff_ctx* ctx) {
       return REAXFF_OK;
     }
     if (attempt == 2) break;
-    if (flags & ERR_CAP_FAR) ctx->cap_far = round_up(ctx->cap_far * 1.5, 32);
-    if (flags & ERR_CAP_NEAR) ctx->cap_near = round_up(ctx->cap_near * 1.5, 32);
-    if (flags & ERR_CAP_CAND) ctx->cap_cand = round_up(ctx->cap_cand * 1.5, 32);
-    if (flags & ERR_CAP_BOND) ctx->cap_bond = round_up(ctx->cap_bond * 1.5, 8);
-    if (flags & ERR_CAP_HB) ctx->cap_hb = round_up(ctx->cap_hb * 1.5, 32);
+    grow_caps(ctx, flags);
     int r2 = alloc_lists(ctx);
     if (r2) return r2;
     CK(cudaMemsetAsync(ctx->sys.rebuild, 1, sizeof(int), ctx->st));   // candidates were reallocated
@@ -319,7 +358,6 @@ int qeq_impl(reaxff_ctx* ctx) {
     cudaError_t e = cudaGetLastError();
     return fail(ctx, REAXFF_E_CUDA, "cooperative QEq launch failed: " + cuda_err_str(e));
   }
-  rx::qeq_push_history(L, ctx->n, ctx->Q);
   return REAXFF_OK;
 }
 
@@ -351,9 +389,9 @@ int zero_accumulators(reaxff_ctx* ctx) {
 }
 
 // lists -> (QEq) -> all terms -> chain rule; energies reduced into E_rep / vir_rep
-int forces_impl(reaxff_ctx* ctx, bool solve_q, bool reduce = true) {
+int forces_impl(reaxff_ctx* ctx, bool solve_q, bool reduce = true, bool checked = true) {
   if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
-  int rc = build_lists_impl(ctx);
+  int rc = build_lists_impl(ctx, checked);
   if (rc) return rc;
   rc = zero_accumulators(ctx);
   if (rc) return rc;
@@ -565,11 +603,8 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   rx::QeqState& Q = ctx->Q;
   Q.grid = rx::qeq_grid_size(ctx->nsm);
   Q.zg = B.alloc<double>(2 * (size_t)n);
-  Q.hist_s = B.alloc<double>(4 * (size_t)n);
-  Q.hist_t = B.alloc<double>(3 * (size_t)n);
-  Q.nhist = 0;
-  Q.hpos_s = 0;
-  Q.hpos_t = 0;
+  Q.hist_s = B.alloc<double>(7 * (size_t)n);      // s ring (4 slots) then t ring (3 slots)
+  Q.hist_t = Q.hist_s + 4 * (size_t)n;
   const int rows = std::max(8, (int)((n + Q.grid - 1) / Q.grid));
   std::vector<int> clo, crep, rchunk(nrep + 1, 0);
   for (int r = 0; r < nrep; ++r) {
@@ -616,6 +651,12 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   ctx->red.part = B.alloc<double>((size_t)ctx->red.nchunk * 20);
   Q.iters = B.alloc<int>(2 * nrep);
   Q.bar = B.alloc<GridBar>(1);
+  Q.hst = B.alloc<int>(4);
+  Q.spmv_total = B.alloc<unsigned long long>(1);
+  ctx->etot_buf = B.alloc<double>((size_t)ETOT_CHUNK * nrep);
+  ctx->etot_idx = B.alloc<int>(1);
+  ctx->snap = B.alloc<double>(13 * (size_t)n);
+  ctx->snap_i = B.alloc<int>(4);
   if (B.err != cudaSuccess) {
     std::string m = "allocation: " + cuda_err_str(B.err);
     B.free_all();
@@ -678,6 +719,9 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   if (e == cudaSuccess) e = cudaMemset(s.pl, 0, n * sizeof(float4));
   if (e == cudaSuccess) e = cudaMemset(s.img, 0, 3 * (size_t)n * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(s.rebuild, 1, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->Q.hst, 0, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->Q.spmv_total, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(ctx->Q.bar, 0, sizeof(GridBar));
   if (e != cudaSuccess) {
     B.free_all();
     delete ctx;
@@ -703,6 +747,7 @@ int reaxff_create(const reaxff_params* params, const int32_t* types, int64_t n, 
 void reaxff_destroy(reaxff_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
+  drop_graph(ctx);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->Etot_dev) cudaFree(ctx->Etot_dev);
   ctx->lists.free_all();
@@ -957,6 +1002,99 @@ int reaxff_forces_fixed_q(reaxff_ctx* ctx, const double* q, double* F, double* E
   return copy_outputs(ctx, F, E, virial);
 }
 
+// one velocity-Verlet step's launches (forces of the current positions are valid on entry);
+// the total energy per replica goes to Etot_out (at *etot_idx when given)
+static int step_once(reaxff_ctx* ctx, double dt, bool checked, double* Etot_out, int* etot_idx) {
+  rx::Launch L = launch_of(ctx);
+  { Stage sg(ctx, 14); rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 1); }
+  int rc = forces_impl(ctx, true, false, checked);
+  if (rc) return rc;
+  { Stage sg(ctx, 14); rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 0); }
+  Stage sg(ctx, 15);
+  rx::reduce_energies(L, ctx->sys, ctx->acc, ctx->mass_t, ctx->red, ctx->E_rep, ctx->vir_rep, ctx->ke_rep);
+  rx::etot_combine(L, ctx->nrep, ctx->E_rep, ctx->ke_rep, Etot_out, etot_idx);
+  return REAXFF_OK;
+}
+
+// capture one unchecked step into a CUDA graph; false when capture is not available
+static bool capture_step(reaxff_ctx* ctx, double dt) {
+  drop_graph(ctx);
+  collect_profile(ctx);
+  if (ctx->prof)
+    while (ctx->ev_pool.size() < 64) {                 // no event creation during capture
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return false;
+      ctx->ev_pool.push_back(e);
+    }
+  const int64_t l0 = ctx->launches;
+  if (cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  ctx->capturing = true;
+  const int rc = step_once(ctx, dt, false, ctx->etot_buf, ctx->etot_idx);
+  ctx->capturing = false;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
+  if (rc == REAXFF_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  const bool ok = rc == REAXFF_OK && e == cudaSuccess && ctx->gexec;
+  if (!ok) {
+    cudaGetLastError();
+    ctx->gexec = nullptr;
+    ctx->ev_pending.clear();
+    ctx->launches = l0;
+    return false;
+  }
+  ctx->g_launches = ctx->launches - l0;
+  ctx->launches = l0;
+  ctx->g_events.swap(ctx->ev_pending);
+  ctx->ev_pending.clear();
+  ctx->g_dt = dt;
+  ctx->g_prof = ctx->prof;
+  return true;
+}
+
+// stage times of the last graph replay (its event-record nodes)
+static void collect_graph_profile(reaxff_ctx* ctx) {
+  cudaStreamSynchronize(ctx->st);
+  for (auto& p : ctx->g_events) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev_pool[p.second], ctx->ev_pool[p.second + 1]) == cudaSuccess) {
+      ctx->stage_ms[p.first] += ms;
+      ctx->stage_calls[p.first] += 1;
+    }
+  }
+}
+
+// the steps of one call without host synchronisation; returns the device flags
+static int run_unchecked(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev, int* flags) {
+  rx::Launch L = launch_of(ctx);
+  rx::snapshot(L, ctx->sys, ctx->Q.hist_s, 7 * ctx->n, ctx->Q.hst, ctx->snap, ctx->snap_i, 0);
+  CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
+  for (int c0 = 0; c0 < nsteps; c0 += ETOT_CHUNK) {
+    const int len = std::min(ETOT_CHUNK, nsteps - c0);
+    CK(cudaMemsetAsync(ctx->etot_idx, 0, sizeof(int), ctx->st));
+    for (int k = 0; k < len; ++k) {
+      if (ctx->graph_ok && (!ctx->gexec || ctx->g_dt != dt || ctx->g_prof != ctx->prof))
+        ctx->graph_ok = capture_step(ctx, dt);
+      if (ctx->graph_ok) {
+        CK(cudaGraphLaunch(ctx->gexec, ctx->st));
+        ctx->launches += ctx->g_launches;
+        if (ctx->prof) collect_graph_profile(ctx);
+      } else {
+        int rc = step_once(ctx, dt, false, ctx->etot_buf, ctx->etot_idx);
+        if (rc) return rc;
+      }
+    }
+    if (Etot_dev)
+      CK(cudaMemcpyAsync(Etot_dev + (size_t)c0 * ctx->nrep, ctx->etot_buf, (size_t)len * ctx->nrep * sizeof(double),
+                         cudaMemcpyDeviceToDevice, ctx->st));
+  }
+  CK(cudaGetLastError());
+  return read_err(ctx, flags);
+}
+
 static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev) {
   if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
   ctx->launches = 0;
@@ -964,16 +1102,29 @@ static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev) {
   if (!ctx->forces_valid) {
     if ((rc = forces_impl(ctx, true))) return rc;
   }
-  rx::Launch L = launch_of(ctx);
-  for (int st = 0; st < nsteps; ++st) {
-    { Stage sg(ctx, 14); rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 1); }
-    if ((rc = forces_impl(ctx, true, false))) return rc;
-    { Stage sg(ctx, 14); rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 0); }
-    Stage sg(ctx, 15);
-    rx::reduce_energies(L, ctx->sys, ctx->acc, ctx->mass_t, ctx->red, ctx->E_rep, ctx->vir_rep, ctx->ke_rep);
-    if (Etot_dev) {
-      rx::etot_combine(L, ctx->nrep, ctx->E_rep, ctx->ke_rep, Etot_dev + (size_t)st * ctx->nrep);
+  if (nsteps > 0) {
+    int flags = 0;
+    if ((rc = run_unchecked(ctx, nsteps, dt, Etot_dev, &flags))) return rc;
+    const int cap = ERR_CAP_FAR | ERR_CAP_BOND | ERR_CAP_HB | ERR_CAP_NEAR | ERR_CAP_CAND;
+    if (!(flags & cap) || (flags & (ERR_NAN | ERR_TIMEOUT))) {
+      rc = check_flags(ctx, false);
+      collect_profile(ctx);
+      return rc;
     }
+    // a list overflowed during the call: restore its starting state, regrow, redo it checked
+    rx::Launch L = launch_of(ctx);
+    rx::snapshot(L, ctx->sys, ctx->Q.hist_s, 7 * ctx->n, ctx->Q.hst, ctx->snap, ctx->snap_i, 1);
+    CK(cudaMemsetAsync(ctx->sys.img, 0, 3 * (size_t)ctx->n * sizeof(int), ctx->st));
+    CK(cudaMemsetAsync(ctx->sys.rebuild, 1, sizeof(int), ctx->st));
+    grow_caps(ctx, flags);
+    if ((rc = alloc_lists(ctx))) return rc;
+    CK(cudaMemsetAsync(ctx->sys.rebuild, 1, sizeof(int), ctx->st));
+    ctx->forces_valid = false;
+    if ((rc = forces_impl(ctx, true))) return rc;
+  }
+  for (int st = 0; st < nsteps; ++st) {
+    if ((rc = step_once(ctx, dt, true, Etot_dev ? Etot_dev + (size_t)st * ctx->nrep : ctx->etot_buf, nullptr)))
+      return rc;
   }
   CK(cudaGetLastError());
   rc = check_flags(ctx, false);
@@ -1014,8 +1165,16 @@ int reaxff_last_qeq_iters(reaxff_ctx* ctx, int32_t* iters_s, int32_t* iters_t) {
   return REAXFF_OK;
 }
 
+int64_t reaxff_qeq_spmv_total(reaxff_ctx* ctx) {
+  if (!ctx) return -1;
+  unsigned long long v = 0;
+  if (cudaMemcpyAsync(&v, ctx->Q.spmv_total, sizeof(v), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess) return -1;
+  if (cudaStreamSynchronize(ctx->st) != cudaSuccess) return -1;
+  return (int64_t)v;
+}
+
 void reaxff_reset_qeq_history(reaxff_ctx* ctx) {
-  if (ctx) ctx->Q.nhist = 0;
+  if (ctx) cudaMemsetAsync(ctx->Q.hst + 2, 0, sizeof(int), ctx->st);   // no usable history
 }
 
 void reaxff_profile_enable(reaxff_ctx* ctx, int32_t on) {

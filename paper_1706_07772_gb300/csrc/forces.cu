@@ -166,19 +166,44 @@ __global__ void k_kick_drift(Sys s, const double* mass_t, double dt, int drift) 
   }
 }
 
-__global__ void k_etot(int nrep, const double* E_rep, const double* ke, double* out) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrep) return;
-  double t = 0.0;
-  for (int q = 0; q < NTERMS; ++q) t += E_rep[r * NTERMS + q];
-  out[r] = t + ke[r];
+// total energy per replica into out[k*nrep + r]; k = *idx (then advanced) or 0 without idx
+__global__ void k_etot(int nrep, const double* E_rep, const double* ke, double* out, int* idx) {
+  const int k = idx ? *idx : 0;
+  for (int r = threadIdx.x; r < nrep; r += blockDim.x) {
+    double t = 0.0;
+    for (int q = 0; q < NTERMS; ++q) t += E_rep[r * NTERMS + q];
+    out[(size_t)k * nrep + r] = t + ke[r];
+  }
+  __syncthreads();
+  if (idx && threadIdx.x == 0) *idx = k + 1;
+}
+
+// copy (save) or restore the primary MD state of a batch: positions, velocities and the
+// QEq solution rings with their state
+__global__ void k_snapshot(Sys s, double* hist, int nhist_doubles, int* hst, double* buf, int* ibuf, int restore) {
+  const size_t n = (size_t)s.n;
+  double* src[6] = {s.x, s.y, s.z, s.vx, s.vy, s.vz};
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < 6 * n + (size_t)nhist_doubles;
+       t += (size_t)gridDim.x * blockDim.x) {
+    double* p = t < 6 * n ? src[t / n] + t % n : hist + (t - 6 * n);
+    if (restore) *p = buf[t];
+    else buf[t] = *p;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 4) {
+    if (restore) hst[threadIdx.x] = ibuf[threadIdx.x];
+    else ibuf[threadIdx.x] = hst[threadIdx.x];
+  }
 }
 
 }  // namespace
 
 namespace rx {
-void etot_combine(const Launch& L, int nrep, const double* E_rep, const double* ke, double* out) {
-  k_etot<<<(nrep + 127) / 128, 128, 0, L.st>>>(nrep, E_rep, ke, out);
+void etot_combine(const Launch& L, int nrep, const double* E_rep, const double* ke, double* out, int* idx) {
+  k_etot<<<1, 256, 0, L.st>>>(nrep, E_rep, ke, out, idx);
+  *L.count += 1;
+}
+void snapshot(const Launch& L, Sys s, double* hist, int nhist_doubles, int* hst, double* buf, int* ibuf, int restore) {
+  k_snapshot<<<4 * 152, 256, 0, L.st>>>(s, hist, nhist_doubles, hst, buf, ibuf, restore);
   *L.count += 1;
 }
 template <typename R> void chain_rule(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc) {

@@ -53,11 +53,12 @@ struct CG {
   const R* Hn;
   int capn;
   const double *eta, *chi, *ieta;          // per type (double); ieta = 1/eta
-  // solution history, newest first (s: 4 slots, t: 3); nh usable entries; the new
-  // solutions go to outs/outt (the ring slot of the oldest entry, read only at init)
-  const double *h0s, *h1s, *h2s, *h3s, *h0t, *h1t, *h2t;
-  int nh;
-  double *outs, *outt;
+  // solution history rings (s: 4 slots, t: 3) and their device state hst = {slot of the
+  // newest s, slot of the newest t, usable entries}; read by every block at the start,
+  // advanced by block 0 at the end (the new solutions go to the oldest slots)
+  double *hist_s, *hist_t;
+  int* hst;
+  int warm;                                // 1: extrapolate from the history, 0: start at 0
   void* zg;                                // interleaved (s, t) SpMV operand: float2 or double2
   double* q;
   float* qf;
@@ -71,6 +72,7 @@ struct CG {
   const int* chunk_rep;                    // [nchunk]
   const int* rep_chunk;                    // [nrep+1] chunk ranges per replica
   int* iters;                              // [2*nrep]
+  unsigned long long* spmv_total;          // SpMVs performed by all solves (diagnostic)
   GridBar* bar;
   int* err;
 };
@@ -372,6 +374,18 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
   int pb = 0;
   double* S = B.S;
   double* red = B.red;
+  const int hpos_s = a.hst[0], hpos_t = a.hst[1], nhist = a.hst[2];
+  const int nh = a.warm ? nhist : 0;
+  const size_t n = (size_t)a.n;
+  const double* h0s = a.hist_s + (size_t)((hpos_s + 4) % 4) * n;   // newest first
+  const double* h1s = a.hist_s + (size_t)((hpos_s + 3) % 4) * n;
+  const double* h2s = a.hist_s + (size_t)((hpos_s + 2) % 4) * n;
+  const double* h3s = a.hist_s + (size_t)((hpos_s + 1) % 4) * n;
+  const double* h0t = a.hist_t + (size_t)((hpos_t + 3) % 3) * n;
+  const double* h1t = a.hist_t + (size_t)((hpos_t + 2) % 3) * n;
+  const double* h2t = a.hist_t + (size_t)((hpos_t + 1) % 3) * n;
+  double* outs = a.hist_s + (size_t)((hpos_s + 1) % 4) * n;        // the oldest slots
+  double* outt = a.hist_t + (size_t)((hpos_t + 1) % 3) * n;
   // ---------------- init: eta, 1/eta and the initial guess into the row state; guess into
   // zg. Guess: Lagrange extrapolation of the solution history (cubic for s from 4 points,
   // quadratic for t from 3; lower order while the history is short; 0 without one)
@@ -381,13 +395,13 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
       const int li = off + i - lo;
       const int t = a.type[i];
       double xs = 0.0, xt = 0.0;
-      if (a.nh >= 4) xs = 4 * a.h0s[i] - 6 * a.h1s[i] + 4 * a.h2s[i] - a.h3s[i];
-      else if (a.nh == 3) xs = 3 * a.h0s[i] - 3 * a.h1s[i] + a.h2s[i];
-      else if (a.nh == 2) xs = 2 * a.h0s[i] - a.h1s[i];
-      else if (a.nh == 1) xs = a.h0s[i];
-      if (a.nh >= 3) xt = 3 * a.h0t[i] - 3 * a.h1t[i] + a.h2t[i];
-      else if (a.nh == 2) xt = 2 * a.h0t[i] - a.h1t[i];
-      else if (a.nh == 1) xt = a.h0t[i];
+      if (nh >= 4) xs = 4 * h0s[i] - 6 * h1s[i] + 4 * h2s[i] - h3s[i];
+      else if (nh == 3) xs = 3 * h0s[i] - 3 * h1s[i] + h2s[i];
+      else if (nh == 2) xs = 2 * h0s[i] - h1s[i];
+      else if (nh == 1) xs = h0s[i];
+      if (nh >= 3) xt = 3 * h0t[i] - 3 * h1t[i] + h2t[i];
+      else if (nh == 2) xt = 2 * h0t[i] - h1t[i];
+      else if (nh == 1) xt = h0t[i];
       const double e = a.eta[t], ie = a.ieta[t];
       B.v(V_ETA, li) = e; B.v(V_IETA, li) = ie;
       B.v(V_XS, li) = xs; B.v(V_XT, li) = xt;
@@ -431,6 +445,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
     sr[S_ACT_T] = rd[3] > a.tol2 * rd[5] ? 1.0 : 0.0;
     if (lead) { a.iters[2 * r] = 0; a.iters[2 * r + 1] = 0; }
   }
+  if (lead && threadIdx.x == 0) *a.spmv_total += 1;   // the initial residual
   count_active(S, a.nrep);
   // z into zg for the first iteration's SpMV: every block has finished the initial SpMV
   // (which gathered x from the same buffer) -- the barrier above -- and the next barrier
@@ -526,6 +541,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
         if (!(red[r * NQ + 3] > a.tol2 * sr[S_BB_T])) sr[S_ACT_T] = 0.0;
       }
     }
+    if (lead && threadIdx.x == 0) *a.spmv_total += 1;
     count_active(S, a.nrep);
   }
   if (S[a.nrep * NS] > 0.0 && lead && threadIdx.x == 0) atomicOr(a.err, ERR_CG);
@@ -535,8 +551,8 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
     for_rows(lo, hi, [&](int i) {
       const int li = off + i - lo;
       const double xs = B.v(V_XS, li), xt = B.v(V_XT, li);
-      a.outs[i] = xs;
-      a.outt[i] = xt;
+      outs[i] = xs;
+      outt[i] = xt;
       v[0] += xs;
       v[1] += xt;
     });
@@ -556,6 +572,12 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
       if (a.ph) ((float*)(a.ph + i))[3] = (float)qi;
     });
   });
+  // advance the history (every block read hst before its first barrier)
+  if (lead && threadIdx.x == 0) {
+    a.hst[0] = (hpos_s + 1) % 4;
+    a.hst[1] = (hpos_t + 1) % 3;
+    a.hst[2] = nhist < 4 ? nhist + 1 : 4;
+  }
 }
 
 }  // namespace
@@ -566,9 +588,6 @@ template <typename R>
 int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* P, const double* chi,
               const double* eta, double tol, int max_iter, int warm) {
   (void)P;
-  const size_t n = (size_t)s.n;
-  auto hs = [&](int k) { return Q.hist_s + (size_t)((Q.hpos_s - k + 8) % 4) * n; };   // k = 0: newest
-  auto ht = [&](int k) { return Q.hist_t + (size_t)((Q.hpos_t - k + 6) % 3) * n; };
   CG<R> a;
   a.n = s.n; a.nrep = s.nrep; a.nchunk = Q.nchunk; a.max_iter = max_iter;
   a.tol2 = tol * tol;
@@ -576,30 +595,19 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   a.cnt = f.cnt; a.col = f.j; a.H = (const R*)f.H; a.cap = f.cap;
   a.cntn = f.cntn; a.coln = f.jn; a.Hn = (const R*)f.Hn; a.capn = f.capn;
   a.eta = eta; a.chi = chi;
-  a.h0s = hs(0); a.h1s = hs(1); a.h2s = hs(2); a.h3s = hs(3);
-  a.h0t = ht(0); a.h1t = ht(1); a.h2t = ht(2);
-  a.nh = warm == REAXFF_WARM_EXTRAP ? Q.nhist : 0;
-  a.outs = hs(-1); a.outt = ht(-1);                    // the oldest slots
+  a.hist_s = Q.hist_s; a.hist_t = Q.hist_t; a.hst = Q.hst;
+  a.warm = warm == REAXFF_WARM_EXTRAP ? 1 : 0;
   a.zg = Q.zg;
   a.q = s.q; a.qf = s.qf; a.ph = s.ph; a.part = Q.part; a.scal = Q.scal; a.state = Q.state;
   a.rows_blk = Q.rows_blk; a.scal_smem = Q.scal_smem; a.state_smem = Q.state_smem;
   a.ieta = Q.ieta;
   a.chunk_lo = Q.chunk_lo; a.chunk_rep = Q.chunk_rep; a.rep_chunk = Q.rep_chunk;
-  a.iters = Q.iters; a.bar = Q.bar; a.err = s.err;
+  a.iters = Q.iters; a.spmv_total = Q.spmv_total; a.bar = Q.bar; a.err = s.err;
   cudaMemsetAsync(Q.bar, 0, sizeof(GridBar), L.st);
   void* args[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel((void*)k_cg<R>, dim3(Q.grid), dim3(1024), args, Q.smem_bytes, L.st);
   *L.count += 2;
   return e == cudaSuccess ? 0 : -1;
-}
-
-// the solve wrote its solutions into the oldest ring slots: advance the newest-slot index
-void qeq_push_history(const Launch& L, int n, QeqState& Q) {
-  (void)L;
-  (void)n;
-  Q.hpos_s = (Q.hpos_s + 1) % 4;
-  Q.hpos_t = (Q.hpos_t + 1) % 3;
-  Q.nhist = Q.nhist < 4 ? Q.nhist + 1 : 4;
 }
 
 int qeq_grid_size(int nsm) {

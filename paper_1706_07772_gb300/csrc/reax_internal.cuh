@@ -525,7 +525,10 @@ struct RedPlan {                // chunks (<= 4096 atoms, never straddling repli
 void reduce_energies(const Launch& L, Sys s, Accum acc, const double* mass_t, const RedPlan& rp, double* E_rep,
                      double* vir_rep, double* ke_rep);
 void verlet_kick_drift(const Launch& L, Sys s, const double* mass_t, double dt, int drift);
-void etot_combine(const Launch& L, int nrep, const double* E_rep, const double* ke, double* out);
+void etot_combine(const Launch& L, int nrep, const double* E_rep, const double* ke, double* out, int* idx);
+// save (restore = 0) or restore the primary MD state: x, v, the QEq rings (contiguous,
+// nhist_doubles) and their device state hst[4]; buf holds 6n + nhist_doubles doubles
+void snapshot(const Launch& L, Sys s, double* hist, int nhist_doubles, int* hst, double* buf, int* ibuf, int restore);
 // qeq.cu
 // QEq solver state. The cooperative kernel keeps each block's per-replica scalars and the
 // CG vectors of its rows in dynamic shared memory when they fit in QEQ_SMEM_MAX bytes,
@@ -536,8 +539,7 @@ constexpr int QEQ_SCAL_PER_REP = 24;         // doubles per replica of scalars +
 struct QeqState {
   double *hist_s, *hist_t;     // [4*n], [3*n] solution rings (s, t); the solver writes each
                                // new solution into the oldest slot
-  int nhist;                   // usable history entries (0..4)
-  int hpos_s, hpos_t;          // ring slot of the newest s and t
+  int* hst;                    // device {slot of the newest s, of the newest t, usable entries}
   void* zg;                    // interleaved (s, t) copy of the SpMV operand: float2 or double2
   const double* ieta;          // 1/eta per type
   double* part;                // chunk partials [2][8][nchunk]
@@ -551,12 +553,12 @@ struct QeqState {
   int* rep_chunk;              // first chunk of each replica [nrep+1]
   int nchunk;
   int* iters;                  // [2*nrep]
+  unsigned long long* spmv_total;   // SpMVs of all solves since creation
   GridBar* bar;
   int grid;                    // cooperative grid size
 };
 template <typename R>
 int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* P, const double* chi,
               const double* eta, double tol, int max_iter, int warm);
-void qeq_push_history(const Launch& L, int n, QeqState& Q);
 int qeq_grid_size(int nsm);
 }  // namespace rx

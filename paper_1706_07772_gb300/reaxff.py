@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
         "reaxff_get_state_dev": (C.c_int, [vp, vp, vp, vp, vp]),
         "reaxff_step_dev": (C.c_int, [vp, i32, C.c_double, vp, vp]),
         "reaxff_reset_qeq_history": (None, [vp]),
+        "reaxff_qeq_spmv_total": (i64, [vp]),
         "reaxff_last_qeq_iters": (C.c_int, [vp, ip32, ip32]),
         "reaxff_profile_enable": (None, [vp, i32]),
         "reaxff_profile_read": (i32, [vp, i32, dp, ip64]),
@@ -296,6 +297,13 @@ class ReaxFF:
 
     def reset_qeq_history(self):
         self.lib.reaxff_reset_qeq_history(self.h)
+
+    def qeq_spmv_total(self):
+        """SpMVs (one read of H for both systems) of all QEq solves so far."""
+        v = self.lib.reaxff_qeq_spmv_total(self.h)
+        if v < 0:
+            raise ReaxFFError(E_CUDA, "reaxff_qeq_spmv_total failed")
+        return int(v)
 
     def last_qeq_iters(self):
         its = np.empty(self.nrep, np.int32)
