@@ -260,6 +260,56 @@ int reaxff_far_list_noalloc(const reaxff_params* params, const reaxff_options* o
                             int32_t* cnt_dev, int32_t* j_dev, uint8_t* shift_dev, double* H_dev,
                             void* stream, const char** err_msg);
 
+/* ---- (e5) Learned QEq warm start -------------------------------------------------------
+ * Sec. 3.3 starts the QEq CG from an extrapolated guess; a per-atom network trained on
+ * charges the method itself produced gives another guess (options.warm_start =
+ * REAXFF_WARM_MLP). CG still runs to the same tolerance, so the guess moves only its
+ * starting point. Descriptors: REAXFF_MLP_NF = 192 per atom, for each neighbour element
+ * e = 0..3 (element types must be 0..3): 32 radial Gaussians sum exp(-eta (r - mu_k)^2)
+ * fc(r) (mu_k = 0.8 + 5.2 k/31 A, eta = 1/(2 (5.2/31)^2), cosine cutoff 6 A) and 16
+ * angular terms 2^(1-zeta) sum over ordered neighbour pairs (j of e, k any, both within
+ * 3.5 A) of (1 + lambda cos theta)^zeta exp(-eta_a (r_ij^2 + r_ik^2)) fc fc, zeta in
+ * {1,2,4,8}, eta_a in {0.05, 0.3}, lambda in {+1,-1}, index 4 zeta_idx + 2 eta_idx +
+ * lambda_idx; per element [32 radial, 16 angular]. Network per centre element:
+ * x~ = (x - mean) inv_std, z1 = x~ W1 + b1, z2 = silu(z1) W2 + b2, y = silu(z2) . w3 + b3
+ * (192 -> 64 -> 64 -> 1). Parameters per element (float, REAXFF_MLP_NPAR = 16577):
+ * W1[192][64] row-major, b1[64], W2[64][64], b2[64], w3[64], b3; four elements in a row.
+ * Inference runs BF16 operands on the tensor cores with FP32 accumulation; training runs
+ * FP32 kernels (MSE loss over the atoms of one snapshot per Adam step). All buffers are
+ * host pointers; every call synchronises the context's stream. */
+#define REAXFF_MLP_NF 192
+#define REAXFF_MLP_NPAR 16577
+/* Seeded initial parameters (normal, variance 1/fan-in; biases 0; the output biases are
+ * set to the mean training charge of each element by the first reaxff_mlp_train). */
+int reaxff_mlp_init(reaxff_ctx* ctx, uint64_t seed);
+/* Parameters theta float[4*16577], normalisation mean float[192] and inv_std float[192]
+ * (0 for a constant feature); set marks the network ready for prediction. */
+int reaxff_mlp_set_params(reaxff_ctx* ctx, const float* theta, const float* mean, const float* inv_std);
+int reaxff_mlp_get_params(reaxff_ctx* ctx, float* theta, float* mean, float* inv_std);
+/* Descriptors float[n*192] of the current positions (lists built if needed).
+ * E_CAPACITY if an atom has more than 192 neighbours within 6 A or 64 within 3.5 A. */
+int reaxff_mlp_descriptors(reaxff_ctx* ctx, float* D);
+/* Tensor-core forward of the context's network on m caller descriptor rows
+ * (float[m*192], raw, normalised inside) of elements types int32[m]; y float[m]. */
+int reaxff_mlp_infer(reaxff_ctx* ctx, const float* D, const int32_t* types, int64_t m, float* y);
+/* FP32 loss L = mean_i (y_i - q_i)^2 over m caller rows and dL/dtheta float[4*16577]. */
+int reaxff_mlp_loss_grad(reaxff_ctx* ctx, const float* D, const int32_t* types, const float* q, int64_t m,
+                         float* grad, double* loss);
+/* One Adam update (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, step counter kept
+ * by the context) of the parameters with the caller's gradient float[4*16577]. */
+int reaxff_mlp_adam_step(reaxff_ctx* ctx, const float* grad, double lr);
+/* Training set of nsnap snapshots (descriptors and charges of all atoms); clears it. */
+int reaxff_mlp_reserve(reaxff_ctx* ctx, int32_t nsnap);
+/* Append the current state (its descriptors and QEq charges; forces are computed first
+ * if the current positions have none) to the training set. E_CAPACITY when full. */
+int reaxff_mlp_collect(reaxff_ctx* ctx);
+/* epochs passes over the collected snapshots in order, one Adam step (learning rate lr)
+ * per snapshot; normalisation statistics from the whole set; loss_out (or NULL) gets
+ * the mean loss of the last pass. The network is then ready. */
+int reaxff_mlp_train(reaxff_ctx* ctx, int32_t epochs, double lr, double* loss_out);
+/* Predicted charges double[n] at the current positions (tensor-core inference). */
+int reaxff_mlp_predict(reaxff_ctx* ctx, double* q);
+
 #ifdef __cplusplus
 }
 #endif

@@ -115,12 +115,17 @@ def unpack(theta):
     return W1, b1, W2, b2, w3, b3
 
 
+def _sigmoid(z):
+    """Logistic function written without overflow: 1/(1 + e^-z) = (1 + tanh(z/2)) / 2."""
+    return 0.5 * (1.0 + np.tanh(0.5 * z))
+
+
 def silu(z):
-    return z / (1.0 + np.exp(-z))
+    return z * _sigmoid(z)
 
 
 def silu_grad(z):
-    s = 1.0 / (1.0 + np.exp(-z))
+    s = _sigmoid(z)
     return s * (1.0 + z * (1.0 - s))
 
 

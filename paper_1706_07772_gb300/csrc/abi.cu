@@ -88,6 +88,22 @@ struct reaxff_ctx {
   int* etot_idx = nullptr;     // device step index into etot_buf
   double* snap = nullptr;      // x, v (6n) and the QEq rings (7n)
   int* snap_i = nullptr;       // the rings' state (4)
+  // learned QEq warm start (allocated on first use)
+  struct Mlp {
+    bool alloc = false, ready = false, fresh = false;
+    DevBuf buf, data;
+    float *theta = nullptr, *mean = nullptr, *inv = nullptr, *madam = nullptr, *vadam = nullptr, *grad = nullptr;
+    double* loss = nullptr;
+    float *D = nullptr, *y = nullptr;      // descriptors and predictions at the current positions
+    int* types = nullptr;                  // [n] element of each atom
+    int* off = nullptr;                    // [5] element offsets into tiles.perm
+    rx::MlpTiles tiles{};
+    rx::MlpInfer inf{};
+    rx::MlpScratch scr{};
+    int adam_step = 0;
+    int cap = 0, count = 0;                // training snapshots
+    float *TD = nullptr, *TQ = nullptr;
+  } mlp;
   // per-stage CUDA-event timing (reaxff_profile_*)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -748,6 +764,8 @@ void reaxff_destroy(reaxff_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   drop_graph(ctx);
+  ctx->mlp.buf.free_all();
+  ctx->mlp.data.free_all();
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->Etot_dev) cudaFree(ctx->Etot_dev);
   ctx->lists.free_all();
@@ -1208,6 +1226,368 @@ int reaxff_step_dev(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot
   CK(cudaStreamWaitEvent((cudaStream_t)stream, ev, 0));
   cudaEventDestroy(ev);
   return rc;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ learned warm start
+namespace {
+// element tiles over m samples with the given elements (host side: counting sort, stable)
+void mlp_tiles_host(const std::vector<int>& types, std::vector<int>& perm, std::vector<int>& tile_type,
+                    std::vector<int>& rows_off, int off[5]) {
+  const int m = (int)types.size();
+  perm.clear(); tile_type.clear(); rows_off.clear();
+  for (int t = 0; t < rx::MLP_NT; ++t) {
+    off[t] = (int)perm.size();
+    for (int i = 0; i < m; ++i)
+      if (types[i] == t) perm.push_back(i);
+    for (int r = off[t]; r < (int)perm.size(); r += 128) {
+      tile_type.push_back(t);
+      rows_off.push_back(r);
+    }
+  }
+  off[rx::MLP_NT] = (int)perm.size();
+  rows_off.push_back((int)perm.size());
+}
+
+// splitmix64 -> uniform (0, 1)
+double u01(uint64_t& st) {
+  uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return ((double)(z >> 11) + 0.5) / 9007199254740992.0;
+}
+
+int mlp_alloc(reaxff_ctx* ctx) {
+  auto& M = ctx->mlp;
+  if (M.alloc) return REAXFF_OK;
+  const int n = ctx->n;
+  for (int t : ctx->h_types)
+    if (t < 0 || t >= rx::MLP_NT) return fail(ctx, REAXFF_E_INVALID, "the learned warm start needs element types 0..3");
+  DevBuf& B = M.buf;
+  const size_t NPT = (size_t)rx::MLP_NT * rx::MLP_NPAR;
+  M.theta = B.alloc<float>(NPT); M.madam = B.alloc<float>(NPT); M.vadam = B.alloc<float>(NPT); M.grad = B.alloc<float>(NPT);
+  M.mean = B.alloc<float>(rx::MLP_NF); M.inv = B.alloc<float>(rx::MLP_NF);
+  M.loss = B.alloc<double>(1);
+  M.D = B.alloc<float>((size_t)n * rx::MLP_NF);
+  M.y = B.alloc<float>(n);
+  M.types = B.alloc<int>(n);
+  M.off = B.alloc<int>(rx::MLP_NT + 1);
+  std::vector<int> perm, tt, ro;
+  int off[5];
+  mlp_tiles_host(ctx->h_types, perm, tt, ro, off);
+  M.tiles.rows = (int)perm.size();
+  M.tiles.ntile = (int)tt.size();
+  M.tiles.perm = B.alloc<int>(perm.size());
+  M.tiles.tile_type = B.alloc<int>(tt.size());
+  M.tiles.rows_off = B.alloc<int>(ro.size());
+  M.inf.Xp = B.alloc_bytes((size_t)n * rx::MLP_NF * 2);
+  M.inf.W1t = B.alloc_bytes((size_t)rx::MLP_NT * rx::MLP_HID * rx::MLP_NF * 2);
+  M.inf.W2t = B.alloc_bytes((size_t)rx::MLP_NT * rx::MLP_HID * rx::MLP_HID * 2);
+  M.inf.fp = B.alloc<float>((size_t)rx::MLP_NT * (3 * rx::MLP_HID + 1));
+  float** sc[] = {&M.scr.z1, &M.scr.z2, &M.scr.dz1, &M.scr.dz2};
+  for (float** p : sc) *p = B.alloc<float>((size_t)n * rx::MLP_HID);
+  M.scr.y = B.alloc<float>(n);
+  M.scr.l = B.alloc<float>(n);
+  if (B.err != cudaSuccess) {
+    B.free_all();
+    return fail(ctx, REAXFF_E_CUDA, "learned warm start allocation: " + cuda_err_str(B.err));
+  }
+  CK(cudaMemcpyAsync(M.tiles.perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(M.tiles.tile_type, tt.data(), tt.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(M.tiles.rows_off, ro.data(), ro.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(M.types, ctx->h_types.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(M.off, off, sizeof(off), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(M.theta, 0, NPT * sizeof(float), ctx->st));
+  CK(cudaMemsetAsync(M.madam, 0, NPT * sizeof(float), ctx->st));
+  CK(cudaMemsetAsync(M.vadam, 0, NPT * sizeof(float), ctx->st));
+  CK(cudaMemsetAsync(M.mean, 0, rx::MLP_NF * sizeof(float), ctx->st));
+  CK(cudaMemsetAsync(M.inv, 0, rx::MLP_NF * sizeof(float), ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (rx::mlp_tc_setup() != 0) return fail(ctx, REAXFF_E_CUDA, "tensor-core kernel shared-memory attribute");
+  M.alloc = true;
+  return REAXFF_OK;
+}
+
+// descriptors of the current positions (lists built or reused as the forces left them)
+int mlp_current_descriptors(reaxff_ctx* ctx) {
+  if (!ctx->lists_valid) {
+    int rc = build_lists_impl(ctx);
+    if (rc) return rc;
+  }
+  rx::mlp_descriptors(launch_of(ctx), ctx->sys, ctx->far, ctx->mlp.D);
+  return REAXFF_OK;
+}
+
+// temporary device copies of caller data for the test entry points
+struct Tmp {
+  std::vector<void*> p;
+  ~Tmp() { for (void* q : p) cudaFree(q); }
+  template <typename T> T* up(reaxff_ctx* ctx, const T* host, size_t count) {
+    void* d = nullptr;
+    if (cudaMalloc(&d, (count ? count : 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    p.push_back(d);
+    if (host && cudaMemcpyAsync(d, host, count * sizeof(T), cudaMemcpyHostToDevice, ctx->st) != cudaSuccess) return nullptr;
+    return (T*)d;
+  }
+};
+
+__global__ void k_q_to_float(const double* q, float* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)q[i];
+}
+}  // namespace
+
+extern "C" {
+
+int reaxff_mlp_init(reaxff_ctx* ctx, uint64_t seed) {
+  if (!ctx) return REAXFF_E_INVALID;
+  int rc = mlp_alloc(ctx);
+  if (rc) return rc;
+  auto& M = ctx->mlp;
+  std::vector<float> th((size_t)rx::MLP_NT * rx::MLP_NPAR, 0.0f);
+  uint64_t st = seed;
+  const int NF = rx::MLP_NF, H = rx::MLP_HID;
+  for (int t = 0; t < rx::MLP_NT; ++t) {
+    float* w = th.data() + (size_t)t * rx::MLP_NPAR;
+    auto normal = [&]() {                                 // Box-Muller, draws in a fixed order
+      const double u1 = u01(st), u2 = u01(st);
+      return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+    };
+    for (int k = 0; k < NF * H; ++k) w[k] = (float)(normal() * std::sqrt(1.0 / NF));
+    for (int k = 0; k < H * H; ++k) w[NF * H + H + k] = (float)(normal() * std::sqrt(1.0 / H));
+    for (int k = 0; k < H; ++k) w[NF * H + H + H * H + H + k] = (float)(normal() * std::sqrt(1.0 / H));
+  }
+  CK(cudaMemcpyAsync(M.theta, th.data(), th.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(M.madam, 0, th.size() * sizeof(float), ctx->st));
+  CK(cudaMemsetAsync(M.vadam, 0, th.size() * sizeof(float), ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  M.adam_step = 0;
+  M.fresh = true;
+  M.ready = false;
+  return REAXFF_OK;
+}
+
+int reaxff_mlp_set_params(reaxff_ctx* ctx, const float* theta, const float* mean, const float* inv_std) {
+  if (!ctx || !theta || !mean || !inv_std) return REAXFF_E_INVALID;
+  int rc = mlp_alloc(ctx);
+  if (rc) return rc;
+  auto& M = ctx->mlp;
+  CK(cudaMemcpyAsync(M.theta, theta, (size_t)rx::MLP_NT * rx::MLP_NPAR * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(M.mean, mean, rx::MLP_NF * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(M.inv, inv_std, rx::MLP_NF * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  M.ready = true;
+  M.fresh = false;
+  return REAXFF_OK;
+}
+
+int reaxff_mlp_get_params(reaxff_ctx* ctx, float* theta, float* mean, float* inv_std) {
+  if (!ctx) return REAXFF_E_INVALID;
+  int rc = mlp_alloc(ctx);
+  if (rc) return rc;
+  auto& M = ctx->mlp;
+  if (theta) CK(cudaMemcpyAsync(theta, M.theta, (size_t)rx::MLP_NT * rx::MLP_NPAR * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+  if (mean) CK(cudaMemcpyAsync(mean, M.mean, rx::MLP_NF * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+  if (inv_std) CK(cudaMemcpyAsync(inv_std, M.inv, rx::MLP_NF * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return REAXFF_OK;
+}
+
+int reaxff_mlp_descriptors(reaxff_ctx* ctx, float* D) {
+  if (!ctx) return REAXFF_E_INVALID;
+  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  int rc = mlp_alloc(ctx);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
+  if ((rc = mlp_current_descriptors(ctx))) return rc;
+  int flags = 0;
+  if ((rc = read_err(ctx, &flags))) return rc;
+  if (flags & ERR_CAP_DESC) return fail(ctx, REAXFF_E_CAPACITY, "more neighbours than the descriptor kernel keeps");
+  if (D) {
+    CK(cudaMemcpyAsync(D, ctx->mlp.D, (size_t)ctx->n * rx::MLP_NF * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  return REAXFF_OK;
+}
+
+int reaxff_mlp_infer(reaxff_ctx* ctx, const float* D, const int32_t* types, int64_t m, float* y) {
+  if (!ctx || !D || !types || !y || m <= 0 || m > (1 << 30)) return REAXFF_E_INVALID;
+  int rc = mlp_alloc(ctx);
+  if (rc) return rc;
+  std::vector<int> ty(types, types + m), perm, tt, ro;
+  for (int t : ty)
+    if (t < 0 || t >= rx::MLP_NT) return fail(ctx, REAXFF_E_INVALID, "element types must be 0..3");
+  int off[5];
+  mlp_tiles_host(ty, perm, tt, ro, off);
+  Tmp T;
+  float* Dd = T.up(ctx, D, (size_t)m * rx::MLP_NF);
+  float* yd = T.up<float>(ctx, nullptr, m);
+  rx::MlpTiles tl{(int)perm.size(), (int)tt.size(), T.up(ctx, perm.data(), perm.size()), T.up(ctx, tt.data(), tt.size()),
+                  T.up(ctx, ro.data(), ro.size())};
+  rx::MlpInfer inf = ctx->mlp.inf;
+  inf.Xp = T.up<char>(ctx, nullptr, (size_t)m * rx::MLP_NF * 2);
+  if (!Dd || !yd || !tl.perm || !tl.tile_type || !tl.rows_off || !inf.Xp) return fail(ctx, REAXFF_E_CUDA, "allocation");
+  CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
+  rx::mlp_infer(launch_of(ctx), Dd, tl, ctx->mlp.mean, ctx->mlp.inv, ctx->mlp.theta, inf, yd, ctx->sys.err, ctx->nsm);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(y, yd, m * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+  int flags = 0;
+  if ((rc = read_err(ctx, &flags))) return rc;
+  if (flags & ERR_TIMEOUT) return fail(ctx, REAXFF_E_TIMEOUT, "tensor-core wait hit its spin limit");
+  return REAXFF_OK;
+}
+
+int reaxff_mlp_loss_grad(reaxff_ctx* ctx, const float* D, const int32_t* types, const float* q, int64_t m, float* grad,
+                         double* loss) {
+  if (!ctx || !D || !types || !q || m <= 0 || m > (1 << 30)) return REAXFF_E_INVALID;
+  int rc = mlp_alloc(ctx);
+  if (rc) return rc;
+  std::vector<int> ty(types, types + m), perm, tt, ro;
+  for (int t : ty)
+    if (t < 0 || t >= rx::MLP_NT) return fail(ctx, REAXFF_E_INVALID, "element types must be 0..3");
+  int off[5];
+  mlp_tiles_host(ty, perm, tt, ro, off);
+  Tmp T;
+  float* Dd = T.up(ctx, D, (size_t)m * rx::MLP_NF);
+  float* qd = T.up(ctx, q, m);
+  int* td = T.up(ctx, ty.data(), m);
+  int* pd = T.up(ctx, perm.data(), perm.size());
+  int* od = T.up(ctx, off, 5);
+  rx::MlpScratch w{};
+  float** sc[] = {&w.z1, &w.z2, &w.dz1, &w.dz2};
+  for (float** p : sc) *p = T.up<float>(ctx, nullptr, (size_t)m * rx::MLP_HID);
+  w.y = T.up<float>(ctx, nullptr, m);
+  w.l = T.up<float>(ctx, nullptr, m);
+  if (!Dd || !qd || !td || !pd || !od || !w.z1 || !w.z2 || !w.dz1 || !w.dz2 || !w.y || !w.l)
+    return fail(ctx, REAXFF_E_CUDA, "allocation");
+  auto& M = ctx->mlp;
+  rx::mlp_loss_grad(launch_of(ctx), Dd, td, pd, od, qd, (int)m, M.theta, M.mean, M.inv, w, M.grad, M.loss);
+  CK(cudaGetLastError());
+  if (grad) CK(cudaMemcpyAsync(grad, M.grad, (size_t)rx::MLP_NT * rx::MLP_NPAR * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+  double l = 0.0;
+  CK(cudaMemcpyAsync(&l, M.loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (loss) *loss = l;
+  return REAXFF_OK;
+}
+
+int reaxff_mlp_adam_step(reaxff_ctx* ctx, const float* grad, double lr) {
+  if (!ctx || !grad || !(lr > 0)) return REAXFF_E_INVALID;
+  int rc = mlp_alloc(ctx);
+  if (rc) return rc;
+  auto& M = ctx->mlp;
+  CK(cudaMemcpyAsync(M.grad, grad, (size_t)rx::MLP_NT * rx::MLP_NPAR * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
+  rx::mlp_adam(launch_of(ctx), M.theta, M.grad, M.madam, M.vadam, ++M.adam_step, (float)lr);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->st));
+  return REAXFF_OK;
+}
+
+int reaxff_mlp_reserve(reaxff_ctx* ctx, int32_t nsnap) {
+  if (!ctx || nsnap < 1) return REAXFF_E_INVALID;
+  int rc = mlp_alloc(ctx);
+  if (rc) return rc;
+  auto& M = ctx->mlp;
+  M.data.free_all();
+  M.TD = M.data.alloc<float>((size_t)nsnap * ctx->n * rx::MLP_NF);
+  M.TQ = M.data.alloc<float>((size_t)nsnap * ctx->n);
+  if (M.data.err != cudaSuccess) {
+    M.data.free_all();
+    M.cap = M.count = 0;
+    return fail(ctx, REAXFF_E_CUDA, "training-set allocation: " + cuda_err_str(M.data.err));
+  }
+  M.cap = nsnap;
+  M.count = 0;
+  return REAXFF_OK;
+}
+
+int reaxff_mlp_collect(reaxff_ctx* ctx) {
+  if (!ctx) return REAXFF_E_INVALID;
+  auto& M = ctx->mlp;
+  if (!M.alloc || M.count >= M.cap) return fail(ctx, REAXFF_E_CAPACITY, "training set full (reaxff_mlp_reserve)");
+  int rc;
+  if (!ctx->forces_valid) {
+    if ((rc = forces_impl(ctx, true))) return rc;
+  }
+  CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
+  if ((rc = mlp_current_descriptors(ctx))) return rc;
+  const size_t n = ctx->n;
+  CK(cudaMemcpyAsync(M.TD + (size_t)M.count * n * rx::MLP_NF, M.D, n * rx::MLP_NF * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
+  k_q_to_float<<<(ctx->n + 255) / 256, 256, 0, ctx->st>>>(ctx->sys.q, M.TQ + (size_t)M.count * n, ctx->n);
+  CK(cudaGetLastError());
+  int flags = 0;
+  if ((rc = read_err(ctx, &flags))) return rc;
+  if (flags & ERR_CAP_DESC) return fail(ctx, REAXFF_E_CAPACITY, "more neighbours than the descriptor kernel keeps");
+  ++M.count;
+  return REAXFF_OK;
+}
+
+int reaxff_mlp_train(reaxff_ctx* ctx, int32_t epochs, double lr, double* loss_out) {
+  if (!ctx || epochs < 1 || !(lr > 0)) return REAXFF_E_INVALID;
+  auto& M = ctx->mlp;
+  if (!M.alloc || M.count < 1) return fail(ctx, REAXFF_E_STATE, "no training snapshots (reaxff_mlp_collect)");
+  rx::Launch L = launch_of(ctx);
+  const size_t n = ctx->n;
+  rx::mlp_stats(L, M.TD, (int64_t)M.count * n, M.mean, M.inv);
+  if (M.fresh) {
+    // output bias of each element's network = its mean training charge
+    std::vector<float> q((size_t)M.count * n);
+    CK(cudaMemcpyAsync(q.data(), M.TQ, q.size() * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int t = 0; t < rx::MLP_NT; ++t) {
+      double sum = 0.0;
+      size_t c = 0;
+      for (size_t k = 0; k < q.size(); ++k)
+        if (ctx->h_types[k % n] == t) { sum += q[k]; ++c; }
+      const float b3 = c ? (float)(sum / c) : 0.0f;
+      CK(cudaMemcpyAsync(M.theta + (size_t)t * rx::MLP_NPAR + rx::MLP_NPAR - 1, &b3, sizeof(float), cudaMemcpyHostToDevice, ctx->st));
+      CK(cudaStreamSynchronize(ctx->st));
+    }
+    M.fresh = false;
+  }
+  double last = 0.0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    double sum = 0.0;
+    for (int sidx = 0; sidx < M.count; ++sidx) {
+      rx::mlp_loss_grad(L, M.TD + (size_t)sidx * n * rx::MLP_NF, M.types, M.tiles.perm, M.off, M.TQ + (size_t)sidx * n,
+                        ctx->n, M.theta, M.mean, M.inv, M.scr, M.grad, M.loss);
+      rx::mlp_adam(L, M.theta, M.grad, M.madam, M.vadam, ++M.adam_step, (float)lr);
+      if (ep == epochs - 1) {
+        double l = 0.0;
+        CK(cudaMemcpyAsync(&l, M.loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        sum += l;
+      }
+    }
+    last = sum / M.count;
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->st));
+  M.ready = true;
+  if (loss_out) *loss_out = last;
+  return REAXFF_OK;
+}
+
+int reaxff_mlp_predict(reaxff_ctx* ctx, double* q) {
+  if (!ctx || !q) return REAXFF_E_INVALID;
+  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  auto& M = ctx->mlp;
+  if (!M.alloc || !M.ready) return fail(ctx, REAXFF_E_STATE, "the network has no parameters (train or set them)");
+  int rc;
+  CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
+  if ((rc = mlp_current_descriptors(ctx))) return rc;
+  rx::mlp_infer(launch_of(ctx), M.D, M.tiles, M.mean, M.inv, M.theta, M.inf, M.y, ctx->sys.err, ctx->nsm);
+  CK(cudaGetLastError());
+  std::vector<float> y(ctx->n);
+  CK(cudaMemcpyAsync(y.data(), M.y, ctx->n * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+  int flags = 0;
+  if ((rc = read_err(ctx, &flags))) return rc;
+  if (flags & ERR_TIMEOUT) return fail(ctx, REAXFF_E_TIMEOUT, "tensor-core wait hit its spin limit");
+  if (flags & ERR_CAP_DESC) return fail(ctx, REAXFF_E_CAPACITY, "more neighbours than the descriptor kernel keeps");
+  for (int i = 0; i < ctx->n; ++i) q[i] = y[i];
+  return REAXFF_OK;
 }
 
 }  // extern "C"

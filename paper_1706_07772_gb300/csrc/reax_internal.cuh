@@ -31,7 +31,7 @@ enum { T_BOND = 0, T_LP, T_OVER, T_UNDER, T_VAL, T_PEN, T_COA, T_TORS, T_CONJ, T
 
 // error flag bits (device-side, read by the host after a stage)
 enum { ERR_CAP_FAR = 1, ERR_CAP_BOND = 2, ERR_CAP_HB = 4, ERR_TIMEOUT = 8, ERR_NAN = 16,
-       ERR_CG = 32, ERR_CAP_NEAR = 64, ERR_CAP_CAND = 128 };
+       ERR_CG = 32, ERR_CAP_NEAR = 64, ERR_CAP_CAND = 128, ERR_CAP_DESC = 256 };
 
 constexpr double FIX_SCALE = 4294967296.0;         // 2^32
 constexpr double FIX_INV = 1.0 / 4294967296.0;
@@ -561,4 +561,35 @@ template <typename R>
 int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* P, const double* chi,
               const double* eta, double tol, int max_iter, int warm);
 int qeq_grid_size(int nsm);
+
+// mlp.cu: learned QEq warm start (descriptors, BF16 tensor-core inference, FP32 training)
+constexpr int MLP_NF = 192, MLP_HID = 64, MLP_NT = 4;
+constexpr int MLP_NPAR = MLP_NF * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID + 1;   // per element
+struct MlpScratch {            // per-sample training activations and gradients
+  float *z1, *z2, *dz1, *dz2;  // [m][64]
+  float *y, *l;                // [m]
+};
+struct MlpTiles {              // tiles of <= 128 rows of one element, rows in element order
+  int rows, ntile;
+  int* perm;                   // [rows] packed row -> sample
+  int* tile_type;              // [ntile]
+  int* rows_off;               // [ntile + 1]
+};
+struct MlpInfer {              // BF16 operands of the tensor-core forward
+  void* Xp;                    // [rows][192] BF16 normalised inputs
+  void* W1t;                   // [4][64][192] BF16
+  void* W2t;                   // [4][64][64] BF16
+  float* fp;                   // [4][193] b1, b2, w3, b3
+};
+void mlp_descriptors(const Launch& L, Sys s, FarList f, float* D);
+void mlp_stats(const Launch& L, const float* X, int64_t rows, float* mean, float* inv);
+void mlp_loss_grad(const Launch& L, const float* X, const int* type, const int* idx, const int* off, const float* Q,
+                   int m, const float* theta, const float* mean, const float* inv, MlpScratch& w, float* G,
+                   double* loss);
+void mlp_forward32(const Launch& L, const float* X, const int* type, int m, const float* theta, const float* mean,
+                   const float* inv, MlpScratch& w);
+void mlp_adam(const Launch& L, float* theta, const float* g, float* mo, float* vo, int step, float lr);
+void mlp_infer(const Launch& L, const float* D, const MlpTiles& T, const float* mean, const float* inv,
+               const float* theta, MlpInfer& w, float* y_out, int* err, int nsm);
+int mlp_tc_setup();
 }  // namespace rx

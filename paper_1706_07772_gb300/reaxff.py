@@ -68,6 +68,7 @@ def load(path: str = LIB_PATH):
         raise ImportError("libreaxff.so not built: run `python -m paper_1706_07772_gb300.build` (%s)" % path)
     lib = C.CDLL(path)
     vp, i32, i64, dp, ip32, ip64 = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+    fp = C.POINTER(C.c_float)
     sig = {
         "reaxff_sizeof_params": (i64, []), "reaxff_sizeof_options": (i64, []),
         "reaxff_params_offset": (i64, [C.c_char_p]),
@@ -89,6 +90,17 @@ def load(path: str = LIB_PATH):
         "reaxff_step_dev": (C.c_int, [vp, i32, C.c_double, vp, vp]),
         "reaxff_reset_qeq_history": (None, [vp]),
         "reaxff_qeq_spmv_total": (i64, [vp]),
+        "reaxff_mlp_init": (C.c_int, [vp, C.c_uint64]),
+        "reaxff_mlp_set_params": (C.c_int, [vp, fp, fp, fp]),
+        "reaxff_mlp_get_params": (C.c_int, [vp, fp, fp, fp]),
+        "reaxff_mlp_descriptors": (C.c_int, [vp, fp]),
+        "reaxff_mlp_infer": (C.c_int, [vp, fp, ip32, i64, fp]),
+        "reaxff_mlp_loss_grad": (C.c_int, [vp, fp, ip32, fp, i64, fp, dp]),
+        "reaxff_mlp_adam_step": (C.c_int, [vp, fp, C.c_double]),
+        "reaxff_mlp_reserve": (C.c_int, [vp, i32]),
+        "reaxff_mlp_collect": (C.c_int, [vp]),
+        "reaxff_mlp_train": (C.c_int, [vp, i32, C.c_double, dp]),
+        "reaxff_mlp_predict": (C.c_int, [vp, dp]),
         "reaxff_last_qeq_iters": (C.c_int, [vp, ip32, ip32]),
         "reaxff_profile_enable": (None, [vp, i32]),
         "reaxff_profile_read": (i32, [vp, i32, dp, ip64]),
@@ -106,6 +118,10 @@ def load(path: str = LIB_PATH):
             raise ImportError("reaxff_params field offset mismatch: " + name)
     _lib = lib
     return lib
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
 
 
 def _dp(a):
@@ -297,6 +313,69 @@ class ReaxFF:
 
     def reset_qeq_history(self):
         self.lib.reaxff_reset_qeq_history(self.h)
+
+    # ---- learned QEq warm start (marshalling only)
+    MLP_NF, MLP_NPAR = 192, 16577
+
+    def mlp_init(self, seed):
+        self._check(self.lib.reaxff_mlp_init(self.h, int(seed)))
+
+    def mlp_set_params(self, theta, mean, inv_std):
+        th = np.ascontiguousarray(theta, np.float32).reshape(-1)
+        mu = np.ascontiguousarray(mean, np.float32).reshape(-1)
+        iv = np.ascontiguousarray(inv_std, np.float32).reshape(-1)
+        if th.size != 4 * self.MLP_NPAR or mu.size != self.MLP_NF or iv.size != self.MLP_NF:
+            raise ValueError("mlp_set_params: theta (4, 16577), mean (192,), inv_std (192,)")
+        self._check(self.lib.reaxff_mlp_set_params(self.h, _fp(th), _fp(mu), _fp(iv)))
+
+    def mlp_get_params(self):
+        th = np.empty((4, self.MLP_NPAR), np.float32)
+        mu = np.empty(self.MLP_NF, np.float32)
+        iv = np.empty(self.MLP_NF, np.float32)
+        self._check(self.lib.reaxff_mlp_get_params(self.h, _fp(th), _fp(mu), _fp(iv)))
+        return th, mu, iv
+
+    def mlp_descriptors(self):
+        D = np.empty((self.n, self.MLP_NF), np.float32)
+        self._check(self.lib.reaxff_mlp_descriptors(self.h, _fp(D)))
+        return D
+
+    def mlp_infer(self, D, types):
+        D = np.ascontiguousarray(D, np.float32)
+        t = np.ascontiguousarray(types, np.int32)
+        y = np.empty(len(t), np.float32)
+        self._check(self.lib.reaxff_mlp_infer(self.h, _fp(D), t.ctypes.data_as(C.POINTER(C.c_int32)), len(t), _fp(y)))
+        return y
+
+    def mlp_loss_grad(self, D, types, q):
+        D = np.ascontiguousarray(D, np.float32)
+        t = np.ascontiguousarray(types, np.int32)
+        qq = np.ascontiguousarray(q, np.float32)
+        g = np.empty((4, self.MLP_NPAR), np.float32)
+        loss = C.c_double()
+        self._check(self.lib.reaxff_mlp_loss_grad(self.h, _fp(D), t.ctypes.data_as(C.POINTER(C.c_int32)), _fp(qq),
+                                                  len(t), _fp(g), C.byref(loss)))
+        return loss.value, g
+
+    def mlp_adam_step(self, grad, lr):
+        g = np.ascontiguousarray(grad, np.float32).reshape(-1)
+        self._check(self.lib.reaxff_mlp_adam_step(self.h, _fp(g), float(lr)))
+
+    def mlp_reserve(self, nsnap):
+        self._check(self.lib.reaxff_mlp_reserve(self.h, int(nsnap)))
+
+    def mlp_collect(self):
+        self._check(self.lib.reaxff_mlp_collect(self.h))
+
+    def mlp_train(self, epochs, lr):
+        loss = C.c_double()
+        self._check(self.lib.reaxff_mlp_train(self.h, int(epochs), float(lr), C.byref(loss)))
+        return loss.value
+
+    def mlp_predict(self):
+        q = np.empty(self.n)
+        self._check(self.lib.reaxff_mlp_predict(self.h, _dp(q)))
+        return q
 
     def qeq_spmv_total(self):
         """SpMVs (one read of H for both systems) of all QEq solves so far."""
