@@ -208,6 +208,11 @@ int reaxff_last_qeq_iters(reaxff_ctx* ctx, int32_t* iters_s, int32_t* iters_t);
 /* Forget the QEq solution history (the next solve starts from zero). */
 void reaxff_reset_qeq_history(reaxff_ctx* ctx);
 
+/* Per replica (int32[nrep]): 1 where the last QEq solve started s from the learned guess
+ * (options.warm_start = REAXFF_WARM_MLP with a trained network), 0 where the extrapolated
+ * guess had the smaller initial residual. */
+int reaxff_qeq_warm_choice(reaxff_ctx* ctx, int32_t* mlp_used);
+
 /* Sparse matrix-vector products (one read of H for both systems) performed by all QEq
  * solves of this context since its creation: the initial residual of every solve plus
  * one per CG iteration. Synchronises the context's stream; -1 on a CUDA error. */
@@ -216,7 +221,7 @@ int64_t reaxff_qeq_spmv_total(reaxff_ctx* ctx);
 /* Per-stage timing with CUDA events recorded on the context's stream around every
  * kernel group (cells, far_list, bond_list, bo_prime64, qeq, bo_correct, atom_terms,
  * over_under_bond, s_gather, angles, torsions, hbonds, nonbonded, chain_rule, verlet,
- * reduce). enable(1) also zeroes the totals. read() fills ms[] (accumulated
+ * reduce, mlp_guess). enable(1) also zeroes the totals. read() fills ms[] (accumulated
  * milliseconds) and calls[] (timed launches) for up to nstage stages and returns the
  * number of stages; stage_name() gives each stage's name. */
 void reaxff_profile_enable(reaxff_ctx* ctx, int32_t on);

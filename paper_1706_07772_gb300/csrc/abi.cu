@@ -244,8 +244,8 @@ rx::Launch launch_of(reaxff_ctx* ctx) { return rx::Launch{ctx->st, &ctx->launche
 
 const char* const STAGE_NAMES[] = {"cells", "far_list", "bond_list", "bo_prime64", "qeq", "bo_correct",
                                    "atom_terms", "over_under_bond", "s_gather", "angles", "torsions",
-                                   "hbonds", "nonbonded", "chain_rule", "verlet", "reduce"};
-constexpr int NSTAGES = 16;
+                                   "hbonds", "nonbonded", "chain_rule", "verlet", "reduce", "mlp_guess"};
+constexpr int NSTAGES = 17;
 
 // scoped event pair around one stage (only when profiling is on)
 struct Stage {
@@ -365,11 +365,20 @@ template <> const DParams<float>* params_of<float>(reaxff_ctx* ctx) { return ctx
 
 int qeq_impl(reaxff_ctx* ctx) {
   rx::Launch L = launch_of(ctx);
+  const float* qhat = nullptr;
+  if (ctx->ho.warm_start == REAXFF_WARM_MLP && ctx->mlp.alloc && ctx->mlp.ready) {
+    // learned guess: descriptors of the current lists, tensor-core forward
+    Stage stg(ctx, 16);
+    auto& M = ctx->mlp;
+    rx::mlp_descriptors(L, ctx->sys, ctx->far, M.D);
+    rx::mlp_infer(L, M.D, M.tiles, M.mean, M.inv, M.inf, M.y, ctx->sys.err, ctx->nsm);
+    qhat = M.y;
+  }
   Stage stg(ctx, 4);
   int rc = ctx->fp64 ? rx::qeq_solve<double>(L, ctx->sys, ctx->far, ctx->Q, ctx->Pd, ctx->chi_t, ctx->eta_t,
-                                             ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start)
+                                             ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start, qhat)
                      : rx::qeq_solve<float>(L, ctx->sys, ctx->far, ctx->Q, ctx->Pf, ctx->chi_t, ctx->eta_t,
-                                            ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start);
+                                            ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start, qhat);
   if (rc) {
     cudaError_t e = cudaGetLastError();
     return fail(ctx, REAXFF_E_CUDA, "cooperative QEq launch failed: " + cuda_err_str(e));
@@ -669,6 +678,7 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   Q.bar = B.alloc<GridBar>(1);
   Q.hst = B.alloc<int>(4);
   Q.spmv_total = B.alloc<unsigned long long>(1);
+  Q.mlp_used = B.alloc<int>(nrep);
   ctx->etot_buf = B.alloc<double>((size_t)ETOT_CHUNK * nrep);
   ctx->etot_idx = B.alloc<int>(1);
   ctx->snap = B.alloc<double>(13 * (size_t)n);
@@ -737,6 +747,7 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   if (e == cudaSuccess) e = cudaMemset(s.rebuild, 1, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->Q.hst, 0, 4 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->Q.spmv_total, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(ctx->Q.mlp_used, 0, nrep * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->Q.bar, 0, sizeof(GridBar));
   if (e != cudaSuccess) {
     B.free_all();
@@ -1183,6 +1194,13 @@ int reaxff_last_qeq_iters(reaxff_ctx* ctx, int32_t* iters_s, int32_t* iters_t) {
   return REAXFF_OK;
 }
 
+int reaxff_qeq_warm_choice(reaxff_ctx* ctx, int32_t* mlp_used) {
+  if (!ctx || !mlp_used) return REAXFF_E_INVALID;
+  CK(cudaMemcpyAsync(mlp_used, ctx->Q.mlp_used, ctx->nrep * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return REAXFF_OK;
+}
+
 int64_t reaxff_qeq_spmv_total(reaxff_ctx* ctx) {
   if (!ctx) return -1;
   unsigned long long v = 0;
@@ -1377,9 +1395,11 @@ int reaxff_mlp_set_params(reaxff_ctx* ctx, const float* theta, const float* mean
   CK(cudaMemcpyAsync(M.theta, theta, (size_t)rx::MLP_NT * rx::MLP_NPAR * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(M.mean, mean, rx::MLP_NF * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(M.inv, inv_std, rx::MLP_NF * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
+  rx::mlp_weights(launch_of(ctx), M.theta, M.inf);
   CK(cudaStreamSynchronize(ctx->st));
   M.ready = true;
   M.fresh = false;
+  drop_graph(ctx);
   return REAXFF_OK;
 }
 
@@ -1430,7 +1450,8 @@ int reaxff_mlp_infer(reaxff_ctx* ctx, const float* D, const int32_t* types, int6
   inf.Xp = T.up<char>(ctx, nullptr, (size_t)m * rx::MLP_NF * 2);
   if (!Dd || !yd || !tl.perm || !tl.tile_type || !tl.rows_off || !inf.Xp) return fail(ctx, REAXFF_E_CUDA, "allocation");
   CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
-  rx::mlp_infer(launch_of(ctx), Dd, tl, ctx->mlp.mean, ctx->mlp.inv, ctx->mlp.theta, inf, yd, ctx->sys.err, ctx->nsm);
+  rx::mlp_weights(launch_of(ctx), ctx->mlp.theta, inf);
+  rx::mlp_infer(launch_of(ctx), Dd, tl, ctx->mlp.mean, ctx->mlp.inv, inf, yd, ctx->sys.err, ctx->nsm);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(y, yd, m * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
   int flags = 0;
@@ -1480,6 +1501,7 @@ int reaxff_mlp_adam_step(reaxff_ctx* ctx, const float* grad, double lr) {
   auto& M = ctx->mlp;
   CK(cudaMemcpyAsync(M.grad, grad, (size_t)rx::MLP_NT * rx::MLP_NPAR * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
   rx::mlp_adam(launch_of(ctx), M.theta, M.grad, M.madam, M.vadam, ++M.adam_step, (float)lr);
+  rx::mlp_weights(launch_of(ctx), M.theta, M.inf);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->st));
   return REAXFF_OK;
@@ -1563,9 +1585,11 @@ int reaxff_mlp_train(reaxff_ctx* ctx, int32_t epochs, double lr, double* loss_ou
     }
     last = sum / M.count;
   }
+  rx::mlp_weights(L, M.theta, M.inf);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->st));
   M.ready = true;
+  drop_graph(ctx);                        // the step graph now runs the network
   if (loss_out) *loss_out = last;
   return REAXFF_OK;
 }
@@ -1578,7 +1602,7 @@ int reaxff_mlp_predict(reaxff_ctx* ctx, double* q) {
   int rc;
   CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
   if ((rc = mlp_current_descriptors(ctx))) return rc;
-  rx::mlp_infer(launch_of(ctx), M.D, M.tiles, M.mean, M.inv, M.theta, M.inf, M.y, ctx->sys.err, ctx->nsm);
+  rx::mlp_infer(launch_of(ctx), M.D, M.tiles, M.mean, M.inv, M.inf, M.y, ctx->sys.err, ctx->nsm);
   CK(cudaGetLastError());
   std::vector<float> y(ctx->n);
   CK(cudaMemcpyAsync(y.data(), M.y, ctx->n * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));

@@ -522,15 +522,19 @@ __global__ void k_mlp_weights(const float* theta, __nv_bfloat16* W1t, __nv_bfloa
 
 namespace rx {
 
-void mlp_infer(const Launch& L, const float* D, const MlpTiles& T, const float* mean, const float* inv,
-               const float* theta, MlpInfer& w, float* y_out, int* err, int nsm) {
+void mlp_weights(const Launch& L, const float* theta, MlpInfer& w) {
   k_mlp_weights<<<(NT * (HID * NF + HID * HID + 3 * HID + 1) + 255) / 256, 256, 0, L.st>>>(theta, (__nv_bfloat16*)w.W1t, (__nv_bfloat16*)w.W2t, w.fp);
+  *L.count += 1;
+}
+
+void mlp_infer(const Launch& L, const float* D, const MlpTiles& T, const float* mean, const float* inv,
+               MlpInfer& w, float* y_out, int* err, int nsm) {
   const int64_t tot = (int64_t)T.rows * NF;
   k_mlp_pack<<<(unsigned)((tot + 255) / 256), 256, 0, L.st>>>(D, T.perm, T.rows, mean, inv, (__nv_bfloat16*)w.Xp);
   const int grid = T.ntile < nsm ? T.ntile : nsm;
   if (grid > 0)
     k_mlp_tc<<<grid, 128, TC_SMEM, L.st>>>((const __nv_bfloat16*)w.Xp, T.tile_type, T.rows_off, T.perm, T.ntile, (const __nv_bfloat16*)w.W1t, (const __nv_bfloat16*)w.W2t, w.fp, y_out, err);
-  *L.count += 3;
+  *L.count += 2;
 }
 
 int mlp_tc_setup() {

@@ -31,7 +31,7 @@ namespace {
 constexpr int NQ = 8;          // partial-sum slots per chunk
 constexpr int NS = 16;         // scalars per replica
 // scalar slots per replica
-enum { S_RHO_S = 0, S_RHO_T, S_AL_S, S_AL_T, S_BE_S, S_BE_T, S_BB_S, S_BB_T, S_ACT_S, S_ACT_T, S_MU };
+enum { S_RHO_S = 0, S_RHO_T, S_AL_S, S_AL_T, S_BE_S, S_BE_T, S_BB_S, S_BB_T, S_ACT_S, S_ACT_T, S_MU, S_USE };
 // row state of a block (doubles per row; U holds the SpMV row sums as two values of the
 // path type)
 enum { V_XS = 0, V_XT, V_RS, V_RT, V_PS, V_PT, V_WS, V_WT, V_ZS, V_ZT, V_ETA, V_IETA, V_U, V_U2, NV_STATE };
@@ -59,6 +59,8 @@ struct CG {
   double *hist_s, *hist_t;
   int* hst;
   int warm;                                // 1: extrapolate from the history, 0: start at 0
+  const float* qhat;                       // learned charges (or null): a second guess for s
+  int* mlp_used;                           // [nrep] 1 where the learned guess was kept
   void* zg;                                // interleaved (s, t) SpMV operand: float2 or double2
   double* q;
   float* qf;
@@ -408,6 +410,68 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
       put_zg(a, i, xs, xt);
     });
   });
+  if (a.qhat) {
+    // learned guess for s: s_mlp = q^ + mu t_ext with mu = sum s_ext / sum t_ext of the
+    // replica (then s_mlp - mu t_ext = q^); kept for a replica when its initial residual
+    // ||b_s - H s|| is below the extrapolated guess's (one extra SpMV for both candidates)
+    for_chunks(a, C, [&](int c, int lo, int hi, int, int off) {
+      double v[2] = {0, 0};
+      for_rows(lo, hi, [&](int i) {
+        v[0] += B.v(V_XS, off + i - lo);
+        v[1] += B.v(V_XT, off + i - lo);
+      });
+      block_sum<2>(a, v, hi - lo, pb, c);
+    });
+    if (!grid_barrier(a.bar, a.err)) return;
+    reduce_parts<2>(a, pb, red);
+    pb ^= 1;
+    for (int r = threadIdx.x; r < a.nrep; r += blockDim.x)
+      S[r * NS + S_MU] = red[r * NQ + 1] != 0.0 ? red[r * NQ + 0] / red[r * NQ + 1] : 0.0;
+    __syncthreads();
+    for_chunks(a, C, [&](int, int lo, int hi, int rep, int off) {
+      const double mu = S[rep * NS + S_MU];
+      for_rows(lo, hi, [&](int i) {
+        const int li = off + i - lo;
+        put_zg(a, i, (double)a.qhat[i] + mu * B.v(V_XT, li), B.v(V_XS, li));
+      });
+    });
+    if (!grid_barrier(a.bar, a.err)) return;
+    for_chunks(a, C, [&](int c, int lo, int hi, int rep, int off) {
+      spmv_chunk(a, B, lo, hi, off);
+      __syncthreads();
+      const double mu = S[rep * NS + S_MU];
+      const R* us = B.u<R>(0);
+      const R* ut = B.u<R>(1);
+      double v[2] = {0, 0};
+      for_rows(lo, hi, [&](int i) {
+        const int li = off + i - lo;
+        const double e = B.v(V_ETA, li), bs = -a.chi[a.type[i]];
+        const double sm = (double)a.qhat[i] + mu * B.v(V_XT, li);
+        const double r1 = bs - ((double)us[li] + e * sm), r2 = bs - ((double)ut[li] + e * B.v(V_XS, li));
+        v[0] += r1 * r1;
+        v[1] += r2 * r2;
+      });
+      block_sum<2>(a, v, hi - lo, pb, c);
+    });
+    if (!grid_barrier(a.bar, a.err)) return;
+    reduce_parts<2>(a, pb, red);
+    pb ^= 1;
+    for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
+      const bool use = red[r * NQ + 0] < red[r * NQ + 1];
+      S[r * NS + S_USE] = use ? 1.0 : 0.0;
+      if (lead) a.mlp_used[r] = use ? 1 : 0;
+    }
+    __syncthreads();
+    for_chunks(a, C, [&](int, int lo, int hi, int rep, int off) {
+      const bool use = S[rep * NS + S_USE] > 0.0;
+      const double mu = S[rep * NS + S_MU];
+      for_rows(lo, hi, [&](int i) {
+        const int li = off + i - lo;
+        if (use) B.v(V_XS, li) = (double)a.qhat[i] + mu * B.v(V_XT, li);
+        put_zg(a, i, B.v(V_XS, li), B.v(V_XT, li));
+      });
+    });
+  }
   if (!grid_barrier(a.bar, a.err)) return;
   // r = b - H x, z = r/eta, p = w = 0
   for_chunks(a, C, [&](int c, int lo, int hi, int, int off) {
@@ -586,7 +650,7 @@ namespace rx {
 
 template <typename R>
 int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* P, const double* chi,
-              const double* eta, double tol, int max_iter, int warm) {
+              const double* eta, double tol, int max_iter, int warm, const float* qhat) {
   (void)P;
   CG<R> a;
   a.n = s.n; a.nrep = s.nrep; a.nchunk = Q.nchunk; a.max_iter = max_iter;
@@ -596,7 +660,9 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   a.cntn = f.cntn; a.coln = f.jn; a.Hn = (const R*)f.Hn; a.capn = f.capn;
   a.eta = eta; a.chi = chi;
   a.hist_s = Q.hist_s; a.hist_t = Q.hist_t; a.hst = Q.hst;
-  a.warm = warm == REAXFF_WARM_EXTRAP ? 1 : 0;
+  a.warm = (warm == REAXFF_WARM_EXTRAP || warm == REAXFF_WARM_MLP) ? 1 : 0;
+  a.qhat = qhat;
+  a.mlp_used = Q.mlp_used;
   a.zg = Q.zg;
   a.q = s.q; a.qf = s.qf; a.ph = s.ph; a.part = Q.part; a.scal = Q.scal; a.state = Q.state;
   a.rows_blk = Q.rows_blk; a.scal_smem = Q.scal_smem; a.state_smem = Q.state_smem;
@@ -623,7 +689,7 @@ int qeq_grid_size(int nsm) {
 }
 
 template int qeq_solve<double>(const Launch&, Sys, FarList, QeqState&, const DParams<double>*, const double*,
-                               const double*, double, int, int);
+                               const double*, double, int, int, const float*);
 template int qeq_solve<float>(const Launch&, Sys, FarList, QeqState&, const DParams<float>*, const double*,
-                              const double*, double, int, int);
+                              const double*, double, int, int, const float*);
 }  // namespace rx

@@ -554,12 +554,14 @@ struct QeqState {
   int nchunk;
   int* iters;                  // [2*nrep]
   unsigned long long* spmv_total;   // SpMVs of all solves since creation
+  int* mlp_used;               // [nrep] learned guess kept in the last solve
   GridBar* bar;
   int grid;                    // cooperative grid size
 };
+// qhat (device, or null): learned charges offered as a second starting guess for s
 template <typename R>
 int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* P, const double* chi,
-              const double* eta, double tol, int max_iter, int warm);
+              const double* eta, double tol, int max_iter, int warm, const float* qhat);
 int qeq_grid_size(int nsm);
 
 // mlp.cu: learned QEq warm start (descriptors, BF16 tensor-core inference, FP32 training)
@@ -589,7 +591,10 @@ void mlp_loss_grad(const Launch& L, const float* X, const int* type, const int* 
 void mlp_forward32(const Launch& L, const float* X, const int* type, int m, const float* theta, const float* mean,
                    const float* inv, MlpScratch& w);
 void mlp_adam(const Launch& L, float* theta, const float* g, float* mo, float* vo, int step, float lr);
+// BF16 tensor-core operands from the FP32 parameters (after every parameter change)
+void mlp_weights(const Launch& L, const float* theta, MlpInfer& w);
+// y[perm-order samples] = network(D) on the tensor cores (uses the converted weights)
 void mlp_infer(const Launch& L, const float* D, const MlpTiles& T, const float* mean, const float* inv,
-               const float* theta, MlpInfer& w, float* y_out, int* err, int nsm);
+               MlpInfer& w, float* y_out, int* err, int nsm);
 int mlp_tc_setup();
 }  // namespace rx

@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "reaxff_step_dev": (C.c_int, [vp, i32, C.c_double, vp, vp]),
         "reaxff_reset_qeq_history": (None, [vp]),
         "reaxff_qeq_spmv_total": (i64, [vp]),
+        "reaxff_qeq_warm_choice": (C.c_int, [vp, ip32]),
         "reaxff_mlp_init": (C.c_int, [vp, C.c_uint64]),
         "reaxff_mlp_set_params": (C.c_int, [vp, fp, fp, fp]),
         "reaxff_mlp_get_params": (C.c_int, [vp, fp, fp, fp]),
@@ -376,6 +377,12 @@ class ReaxFF:
         q = np.empty(self.n)
         self._check(self.lib.reaxff_mlp_predict(self.h, _dp(q)))
         return q
+
+    def qeq_warm_choice(self):
+        """Per replica: 1 where the last QEq solve kept the learned guess for s."""
+        u = np.empty(self.nrep, np.int32)
+        self._check(self.lib.reaxff_qeq_warm_choice(self.h, u.ctypes.data_as(C.POINTER(C.c_int32))))
+        return u
 
     def qeq_spmv_total(self):
         """SpMVs (one read of H for both systems) of all QEq solves so far."""

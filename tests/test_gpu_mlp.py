@@ -157,3 +157,38 @@ def test_training_learns_charges(rx, params):
     assert loss < 0.5 * loss0
     assert np.sqrt(((qp - q) ** 2).mean()) < 0.5 * np.sqrt(((base - q) ** 2).mean())
     c.close()
+
+
+def test_learned_guess_saves_iterations_and_keeps_charges(rx, params):
+    """Cold start (no solution history) on a held-out state: the learned guess for s cuts
+    the CG iterations against the zero start, and the charges stay those of the solve."""
+    w = synth.workload("petn464")
+    c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=rx.MIXED, warm_start=rx.WARM_MLP)
+    c.set_state(w["x"], w["v"])
+    c.mlp_reserve(16)
+    c.mlp_init(99)
+    for _ in range(16):
+        c.step(2, 0.1)
+        c.mlp_collect()
+    c.mlp_train(80, 2e-3)
+    theta, mean, inv = c.mlp_get_params()
+    c.close()
+    w2 = synth.workload("petn464", seed=7)                 # other jitter and velocities
+    cz = rx.ReaxFF(params, w2["types"], w2["box"], w2["options"], precision=rx.MIXED, warm_start=rx.WARM_ZERO)
+    cz.set_state(w2["x"], w2["v"])
+    cz.step(10, 0.1)
+    x2, v2, _ = cz.get_state()
+    cz.set_state(x2, v2)
+    cz.reset_qeq_history()
+    qz, itz, ttz, _ = cz.qeq()
+    cm = rx.ReaxFF(params, w2["types"], w2["box"], w2["options"], precision=rx.MIXED, warm_start=rx.WARM_MLP)
+    cm.mlp_set_params(theta, mean, inv)
+    cm.set_state(x2, v2)
+    qm, itm, ttm, _ = cm.qeq()
+    assert cm.qeq_warm_choice()[0] == 1
+    assert itm[0] < itz[0], (itm, itz)
+    assert ttm[0] == ttz[0]                                 # t starts at zero in both
+    assert np.abs(qm - qz).max() < 1e-5
+    assert abs(qm.sum()) < 1e-9 * len(qm)
+    cz.close()
+    cm.close()
