@@ -299,6 +299,67 @@ def e2e(ctx, w, steps, dt):
             "d2h_bytes_per_step": 56 * n + 8, "steps": steps}
 
 
+def learned_warm_start(P, a):
+    """The learned QEq warm start on the benchmark crystal: the network is trained on
+    snapshots of 2000 MD steps of the method itself (every 20th step), then compared with
+    the extrapolated and zero starts on a held-out state (other jitter and velocity seed):
+    CG iterations of a cold start (no solution history), SpMVs per step over held-out MD,
+    and the charge difference between the learned-start and extrapolated-start solves."""
+    import torch
+
+    import paper_1706_07772_gb300.reaxff as rx
+    import synth
+    w = synth.workload(a.workload)
+    c = rx.ReaxFF(P, w["types"], w["box"], w["options"], precision=rx.MIXED, warm_start=rx.WARM_MLP)
+    c.set_state(w["x"], w["v"])
+    train_steps, every, epochs, lr = 2000, 20, 30, 2e-3
+    c.mlp_reserve(train_steps // every)
+    c.mlp_init(2017)
+    t0 = time.perf_counter()
+    for _ in range(train_steps // every):
+        c.step(every, a.dt)
+        c.mlp_collect()
+    t_md = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = c.mlp_train(epochs, lr)
+    t_train = time.perf_counter() - t0
+    theta, mean, inv = c.mlp_get_params()
+    c.close()
+    w2 = synth.workload(a.workload, seed=11)
+    held, out = 50, {}
+    st = torch.cuda.current_stream()
+    et = torch.zeros(held, dtype=torch.float64, device="cuda")
+    qs = {}
+    for name, mode in (("learned", rx.WARM_MLP), ("extrapolated", rx.WARM_EXTRAP), ("zero", rx.WARM_ZERO)):
+        cc = rx.ReaxFF(P, w2["types"], w2["box"], w2["options"], precision=rx.MIXED, warm_start=mode)
+        if mode == rx.WARM_MLP:
+            cc.mlp_set_params(theta, mean, inv)
+        cc.set_state(w2["x"], w2["v"])
+        q0, its, itt, _ = cc.qeq()
+        qs[name] = q0
+        rec = {"cold_start_iters": [int(its[0]), int(itt[0])]}
+        if mode == rx.WARM_MLP:
+            rec["cold_start_learned_kept"] = bool(cc.qeq_warm_choice()[0])
+        cc.step_dev(3, a.dt, et.data_ptr(), st.cuda_stream)
+        sp0 = cc.qeq_spmv_total()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        cc.step_dev(held, a.dt, et.data_ptr(), st.cuda_stream)
+        e1.record(st)
+        e1.synchronize()
+        rec["spmv_per_step"] = (cc.qeq_spmv_total() - sp0) / held
+        rec["ms_per_step"] = e0.elapsed_time(e1) / held
+        if mode == rx.WARM_MLP:
+            rec["learned_kept_last_step"] = bool(cc.qeq_warm_choice()[0])
+        out[name] = rec
+        cc.close()
+    out["dq_max_learned_vs_extrapolated"] = float(np.abs(qs["learned"] - qs["extrapolated"]).max())
+    out["training"] = {"md_steps": train_steps, "snapshots": train_steps // every, "epochs": epochs, "lr": lr,
+                       "final_mse_e2": loss, "md_s": round(t_md, 2), "train_s": round(t_train, 2)}
+    out["held_out"] = {"workload": a.workload, "seed": 11, "steps": held}
+    return out
+
+
 def cpu_oracle_step(P, w):
     """One oracle MD step (lists, QEq to the workload tolerance, energy + forces, Verlet
     update) on the host cores. Returns (seconds, threads, model, lists)."""
@@ -383,6 +444,8 @@ def main():
                               "mixed_over_fp64": (ms64 / out["ms_per_step"])}
         # end to end through the host API
         out["e2e"] = e2e(ctx, w, max(5, min(20, a.steps // 5)), a.dt)
+        # learned QEq warm start (trained here on the method's own charges)
+        out["learned_warm_start"] = learned_warm_start(P, a)
         # CPU baseline (oracle) and force error of both GPU paths at the same state
         t, cores, m, L = cpu_oracle_step(P, w)
         nat = len(w["x"])
