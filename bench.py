@@ -360,6 +360,62 @@ def learned_warm_start(P, a):
     return out
 
 
+def batched(P, a, steps=20):
+    """64 independent replicas of uneven size (2x2x2 to 8x4x4 cells of the crystal, seeded
+    jitter and temperatures 250-350 K) in one context: every stage is one launch for all
+    replicas, one CUDA graph per step. Compared with the same replicas stepped one context
+    after another. atom-steps/s over all replicas; L2 flushed before each timed call."""
+    import torch
+
+    import paper_1706_07772_gb300.reaxff as rx
+    import synth
+    from synth.workloads import batch_shapes
+    shapes, temps = batch_shapes(64, seed=0)
+    reps = []
+    for r, (sh, temp) in enumerate(zip(shapes, temps)):
+        t, x, box = synth.crystal(sh, seed=100 + r)
+        reps.append((t, x, np.asarray(box, float), synth.velocities(t, float(temp), seed=200 + r)))
+    opts = dict(synth.OPTIONS_DEFAULT)
+    types = np.concatenate([r[0] for r in reps])
+    x = np.concatenate([r[1] for r in reps])
+    v = np.concatenate([r[3] for r in reps])
+    off = np.cumsum([0] + [len(r[0]) for r in reps])
+    boxes = np.stack([r[2] for r in reps])
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    et = torch.zeros(max(steps, 64) * 64, dtype=torch.float64, device="cuda")
+
+    def timed(c, k):
+        c.step_dev(3, a.dt, et.data_ptr(), st.cuda_stream)        # warm-up, graph capture
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        c.step_dev(k, a.dt, et.data_ptr(), st.cuda_stream)
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    cb = rx.ReaxFF(P, types, boxes, opts, precision=rx.MIXED, rep_offsets=off)
+    cb.set_state(x, v)
+    ms_b = timed(cb, steps)
+    launches = cb.last_launch_count()
+    cb.close()
+    ms_seq = 0.0
+    for t, xr, box, vr in reps:
+        c = rx.ReaxFF(P, t, box, opts, precision=rx.MIXED)
+        c.set_state(xr, vr)
+        ms_seq += timed(c, steps)
+        c.close()
+    natoms = int(off[-1])
+    return {"replicas": len(reps), "atoms": natoms, "min_atoms": int(np.diff(off).min()),
+            "max_atoms": int(np.diff(off).max()), "steps": steps,
+            "value": natoms * steps / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b / steps,
+            "gpu_launches_per_step": launches / steps,
+            "one_at_a_time": {"value": natoms * steps / (ms_seq * 1e-3), "ms_per_step": ms_seq / steps},
+            "speedup_batched": ms_seq / ms_b}
+
+
 def cpu_oracle_step(P, w):
     """One oracle MD step (lists, QEq to the workload tolerance, energy + forces, Verlet
     update) on the host cores. Returns (seconds, threads, model, lists)."""
@@ -444,6 +500,8 @@ def main():
                               "mixed_over_fp64": (ms64 / out["ms_per_step"])}
         # end to end through the host API
         out["e2e"] = e2e(ctx, w, max(5, min(20, a.steps // 5)), a.dt)
+        # 64 uneven replicas in one context vs one at a time
+        out["batched"] = batched(P, a)
         # learned QEq warm start (trained here on the method's own charges)
         out["learned_warm_start"] = learned_warm_start(P, a)
         # CPU baseline (oracle) and force error of both GPU paths at the same state

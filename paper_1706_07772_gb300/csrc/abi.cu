@@ -1308,6 +1308,7 @@ int mlp_alloc(reaxff_ctx* ctx) {
   for (float** p : sc) *p = B.alloc<float>((size_t)n * rx::MLP_HID);
   M.scr.y = B.alloc<float>(n);
   M.scr.l = B.alloc<float>(n);
+  M.scr.part = B.alloc<float>((size_t)((n + rx::MLP_WG_CHUNK - 1) / rx::MLP_WG_CHUNK) * rx::MLP_NT * rx::MLP_NPAR);
   if (B.err != cudaSuccess) {
     B.free_all();
     return fail(ctx, REAXFF_E_CUDA, "learned warm start allocation: " + cuda_err_str(B.err));
@@ -1481,7 +1482,8 @@ int reaxff_mlp_loss_grad(reaxff_ctx* ctx, const float* D, const int32_t* types, 
   for (float** p : sc) *p = T.up<float>(ctx, nullptr, (size_t)m * rx::MLP_HID);
   w.y = T.up<float>(ctx, nullptr, m);
   w.l = T.up<float>(ctx, nullptr, m);
-  if (!Dd || !qd || !td || !pd || !od || !w.z1 || !w.z2 || !w.dz1 || !w.dz2 || !w.y || !w.l)
+  w.part = T.up<float>(ctx, nullptr, (size_t)((m + rx::MLP_WG_CHUNK - 1) / rx::MLP_WG_CHUNK) * rx::MLP_NT * rx::MLP_NPAR);
+  if (!Dd || !qd || !td || !pd || !od || !w.z1 || !w.z2 || !w.dz1 || !w.dz2 || !w.y || !w.l || !w.part)
     return fail(ctx, REAXFF_E_CUDA, "allocation");
   auto& M = ctx->mlp;
   rx::mlp_loss_grad(launch_of(ctx), Dd, td, pd, od, qd, (int)m, M.theta, M.mean, M.inv, w, M.grad, M.loss);

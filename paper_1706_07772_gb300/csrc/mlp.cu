@@ -221,16 +221,19 @@ __global__ void k_bwd32(const int* type, int m, const float* theta, const float*
   }
 }
 
-// weight gradients, one thread per parameter of one element: sums over that element's
-// samples in index order (deterministic). Samples of element t are idx[off[t] .. off[t+1]).
+// weight gradients, one thread per parameter of one element and chunk of WG_CHUNK of that
+// element's samples (idx[off[t] .. off[t+1]), in index order): partial sums part[c][gid],
+// then summed over the chunks in order by k_wgrad_sum (deterministic)
+constexpr int WG_CHUNK = rx::MLP_WG_CHUNK;
 __global__ void k_wgrad(const float* X, const int* idx, const int* off, const float* theta, const float* mean,
                         const float* inv, const float* Z1, const float* Z2, const float* DZ1, const float* DZ2,
-                        const float* Y, const float* Q, int m, float* G) {
+                        const float* Y, const float* Q, int m, float* part) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= NT * NPAR) return;
   const int t = gid / NPAR, p = gid % NPAR;
   float acc = 0.0f;
-  const int a = off[t], bnd = off[t + 1];
+  const int a = min(off[t] + (int)blockIdx.y * WG_CHUNK, off[t + 1]);
+  const int bnd = min(a + WG_CHUNK, off[t + 1]);
   if (p < O_B1) {                                      // W1[k][j] = sum x~_k dz1_j
     const int k = p / HID, j = p % HID;
     for (int s = a; s < bnd; ++s) {
@@ -258,7 +261,14 @@ __global__ void k_wgrad(const float* X, const int* idx, const int* off, const fl
   } else {                                             // b3
     for (int s = a; s < bnd; ++s) acc += 2.0f * (Y[idx[s]] - Q[idx[s]]) / (float)m;
   }
-  G[gid] = acc;
+  part[(size_t)blockIdx.y * (NT * NPAR) + gid] = acc;
+}
+__global__ void k_wgrad_sum(const float* part, int nchunk, float* G) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= NT * NPAR) return;
+  float s = 0.0f;
+  for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * (NT * NPAR) + gid];
+  G[gid] = s;
 }
 
 __global__ void k_adam(float* theta, const float* g, float* mo, float* vo, int np, float lr, float b1, float b2,
@@ -556,10 +566,12 @@ void mlp_loss_grad(const Launch& L, const float* X, const int* type, const int* 
                    double* loss) {
   k_fwd32<<<(m + 127) / 128, 128, 0, L.st>>>(X, type, m, theta, mean, inv, w.z1, w.z2, w.y);
   k_bwd32<<<(m + 127) / 128, 128, 0, L.st>>>(type, m, theta, Q, w.z1, w.z2, w.y, w.dz1, w.dz2, w.l);
-  k_wgrad<<<(NT * NPAR + 127) / 128, 128, 0, L.st>>>(X, idx, off, theta, mean, inv, w.z1, w.z2, w.dz1, w.dz2, w.y,
-                                                     Q, m, G);
+  const int nchunk = (m + WG_CHUNK - 1) / WG_CHUNK;     // enough for any one element
+  k_wgrad<<<dim3((NT * NPAR + 127) / 128, nchunk), 128, 0, L.st>>>(X, idx, off, theta, mean, inv, w.z1, w.z2, w.dz1,
+                                                                  w.dz2, w.y, Q, m, w.part);
+  k_wgrad_sum<<<(NT * NPAR + 255) / 256, 256, 0, L.st>>>(w.part, nchunk, G);
   k_sumsq<<<1, 256, 0, L.st>>>(w.l, m, loss);
-  *L.count += 4;
+  *L.count += 5;
 }
 
 void mlp_forward32(const Launch& L, const float* X, const int* type, int m, const float* theta, const float* mean,

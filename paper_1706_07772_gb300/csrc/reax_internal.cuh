@@ -570,7 +570,9 @@ constexpr int MLP_NPAR = MLP_NF * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HI
 struct MlpScratch {            // per-sample training activations and gradients
   float *z1, *z2, *dz1, *dz2;  // [m][64]
   float *y, *l;                // [m]
+  float* part;                 // [ceil(m / 256)][4 * 16577] weight-gradient chunk partials
 };
+constexpr int MLP_WG_CHUNK = 256;
 struct MlpTiles {              // tiles of <= 128 rows of one element, rows in element order
   int rows, ntile;
   int* perm;                   // [rows] packed row -> sample
