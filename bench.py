@@ -500,6 +500,17 @@ def main():
                               "mixed_over_fp64": (ms64 / out["ms_per_step"])}
         # end to end through the host API
         out["e2e"] = e2e(ctx, w, max(5, min(20, a.steps // 5)), a.dt)
+        # in-situ species analysis of the current state (Sec. 3.4)
+        t0 = time.perf_counter()
+        mol, sp = ctx.species()
+        t_sp = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        mol, sp = ctx.species()
+        t_sp = min(t_sp, time.perf_counter() - t0)
+        top = sorted(sp.items(), key=lambda kv: -kv[1])[:3]
+        out["species"] = {"ms_per_analysis": 1e3 * t_sp, "molecules": int(mol.max()) + 1, "distinct": len(sp),
+                          "top": [{"counts_CHNO": list(k[1:5]), "molecules": v} for k, v in top],
+                          "overhead_at_one_analysis_per_1000_steps": 1e3 * t_sp / (1000 * out["ms_per_step"])}
         # 64 uneven replicas in one context vs one at a time
         out["batched"] = batched(P, a)
         # learned QEq warm start (trained here on the method's own charges)

@@ -315,6 +315,20 @@ int reaxff_mlp_train(reaxff_ctx* ctx, int32_t epochs, double lr, double* loss_ou
 /* Predicted charges double[n] at the current positions (tensor-core inference). */
 int reaxff_mlp_predict(reaxff_ctx* ctx, double* q);
 
+/* ---- In-situ molecular species analysis (Sec. 3.4) ----------------------------------------
+ * At the current positions (forces are computed first if the current positions have none):
+ * atoms i, j are bonded when their corrected bond order exceeds bo_threshold[t_i*8 + t_j]
+ * (double[REAXFF_MAXT*REAXFF_MAXT], or NULL for 0.3 everywhere); a molecule is a connected
+ * component of that graph, numbered 0..M-1 in the order of its smallest atom index; a
+ * species is the vector of atom counts per type of a molecule (isomers not told apart).
+ * mol_id (int32[n] or NULL) receives each atom's molecule, *nmol (or NULL) M. species
+ * (int32[cap][REAXFF_MAXT + 2], rows: replica, count of type 0..7, molecules) receives the
+ * summary sorted by (replica, counts) and *nspecies its length; E_CAPACITY (with
+ * *nspecies set) when it has more than cap rows. Connectivity, numbering and counting run
+ * on the GPU; the host tallies the M count vectors into the summary. */
+int reaxff_species(reaxff_ctx* ctx, const double* bo_threshold, int32_t* mol_id, int64_t* nmol, int32_t cap,
+                   int32_t* species, int32_t* nspecies);
+
 #ifdef __cplusplus
 }
 #endif

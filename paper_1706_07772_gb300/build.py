@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libreaxff.so")
-UNITS = ["lists", "bonded", "nonbonded", "qeq", "forces", "abi", "peaks", "noalloc", "mlp"]
+UNITS = ["lists", "bonded", "nonbonded", "qeq", "forces", "abi", "peaks", "noalloc", "mlp", "species"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <string>
 #include <algorithm>
+#include <array>
 #include <vector>
 
 #include "reax_internal.cuh"
@@ -104,6 +105,10 @@ struct reaxff_ctx {
     int cap = 0, count = 0;                // training snapshots
     float *TD = nullptr, *TQ = nullptr;
   } mlp;
+  // species analysis buffers (allocated on first use)
+  DevBuf spbuf;
+  rx::SpeciesBuf sp{};
+  double* sp_thr = nullptr;
   // per-stage CUDA-event timing (reaxff_profile_*)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -777,6 +782,8 @@ void reaxff_destroy(reaxff_ctx* ctx) {
   drop_graph(ctx);
   ctx->mlp.buf.free_all();
   ctx->mlp.data.free_all();
+  ctx->spbuf.free_all();
+  if (ctx->sp.h_changed) cudaFreeHost(ctx->sp.h_changed);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->Etot_dev) cudaFree(ctx->Etot_dev);
   ctx->lists.free_all();
@@ -1613,6 +1620,76 @@ int reaxff_mlp_predict(reaxff_ctx* ctx, double* q) {
   if (flags & ERR_TIMEOUT) return fail(ctx, REAXFF_E_TIMEOUT, "tensor-core wait hit its spin limit");
   if (flags & ERR_CAP_DESC) return fail(ctx, REAXFF_E_CAPACITY, "more neighbours than the descriptor kernel keeps");
   for (int i = 0; i < ctx->n; ++i) q[i] = y[i];
+  return REAXFF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ species analysis
+extern "C" {
+
+int reaxff_species(reaxff_ctx* ctx, const double* bo_threshold, int32_t* mol_id, int64_t* nmol, int32_t cap,
+                   int32_t* species, int32_t* nspecies) {
+  if (!ctx || cap < 0 || (cap > 0 && !species)) return REAXFF_E_INVALID;
+  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  int rc;
+  if (!ctx->forces_valid) {
+    if ((rc = forces_impl(ctx, true))) return rc;
+  }
+  const int n = ctx->n;
+  rx::SpeciesBuf& b = ctx->sp;
+  if (!b.lab) {
+    DevBuf& B = ctx->spbuf;
+    b.lab = B.alloc<int>(n); b.rank = B.alloc<int>(n); b.mol = B.alloc<int>(n);
+    b.cnt = B.alloc<int>((size_t)n * MAXT); b.mrep = B.alloc<int>(n);
+    b.boff = B.alloc<int>(n / 1024 + 2); b.nmol = B.alloc<int>(1); b.changed = B.alloc<int>(1);
+    ctx->sp_thr = B.alloc<double>(MAXT * MAXT);
+    if (B.err != cudaSuccess || cudaMallocHost(&b.h_changed, sizeof(int)) != cudaSuccess) {
+      B.free_all();
+      b = rx::SpeciesBuf{};
+      return fail(ctx, REAXFF_E_CUDA, "species buffers");
+    }
+  }
+  double thr[MAXT * MAXT];
+  for (int k = 0; k < MAXT * MAXT; ++k) thr[k] = bo_threshold ? bo_threshold[k] : 0.3;
+  CK(cudaMemcpyAsync(ctx->sp_thr, thr, sizeof(thr), cudaMemcpyHostToDevice, ctx->st));
+  rx::Launch L = launch_of(ctx);
+  const int passes = ctx->fp64 ? rx::species_components<double>(L, ctx->sys, ctx->bond, ctx->sp_thr, b, 256)
+                               : rx::species_components<float>(L, ctx->sys, ctx->bond, ctx->sp_thr, b, 256);
+  CK(cudaGetLastError());
+  if (passes < 0) return fail(ctx, REAXFF_E_NOT_CONVERGED, "species components did not settle in 256 passes");
+  rx::species_molecules(L, ctx->sys, b);
+  CK(cudaGetLastError());
+  int M = 0;
+  CK(cudaMemcpyAsync(&M, b.nmol, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  std::vector<int> cnt((size_t)M * MAXT), mrep(M);
+  CK(cudaMemcpyAsync(cnt.data(), b.cnt, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(mrep.data(), b.mrep, mrep.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (mol_id) CK(cudaMemcpyAsync(mol_id, b.mol, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  // the summary: molecules per (replica, element counts), in that order
+  constexpr int W = MAXT + 2;
+  std::vector<std::array<int, MAXT + 1>> keys(M);
+  for (int m = 0; m < M; ++m) {
+    keys[m][0] = mrep[m];
+    for (int t = 0; t < MAXT; ++t) keys[m][1 + t] = cnt[(size_t)m * MAXT + t];
+  }
+  std::sort(keys.begin(), keys.end());
+  int ns = 0;
+  for (int m = 0; m < M;) {
+    int e = m;
+    while (e < M && keys[e] == keys[m]) ++e;
+    if (ns < cap) {
+      for (int q = 0; q <= MAXT; ++q) species[ns * W + q] = keys[m][q];
+      species[ns * W + MAXT + 1] = e - m;
+    }
+    ++ns;
+    m = e;
+  }
+  if (nmol) *nmol = M;
+  if (nspecies) *nspecies = ns;
+  if (ns > cap) return fail(ctx, REAXFF_E_CAPACITY, "more species than cap (count in *nspecies)");
   return REAXFF_OK;
 }
 

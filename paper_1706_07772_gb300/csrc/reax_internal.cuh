@@ -599,4 +599,15 @@ void mlp_weights(const Launch& L, const float* theta, MlpInfer& w);
 void mlp_infer(const Launch& L, const float* D, const MlpTiles& T, const float* mean, const float* inv,
                MlpInfer& w, float* y_out, int* err, int nsm);
 int mlp_tc_setup();
+
+// species.cu: molecular species analysis
+struct SpeciesBuf {
+  int *lab, *rank, *mol;       // [n] root labels, root ranks, molecule of each atom
+  int *cnt, *mrep;             // [n*MAXT] element counts per molecule, [n] replica per molecule
+  int *boff, *nmol, *changed;  // block offsets, molecule count, hook flag
+  int* h_changed;              // pinned host copy of the flag
+};
+template <typename R>
+int species_components(const Launch& L, Sys s, BondList bl, const double* thr, SpeciesBuf& b, int max_pass);
+void species_molecules(const Launch& L, Sys s, SpeciesBuf& b);
 }  // namespace rx

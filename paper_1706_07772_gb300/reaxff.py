@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
         "reaxff_reset_qeq_history": (None, [vp]),
         "reaxff_qeq_spmv_total": (i64, [vp]),
         "reaxff_qeq_warm_choice": (C.c_int, [vp, ip32]),
+        "reaxff_species": (C.c_int, [vp, dp, ip32, ip64, i32, ip32, ip32]),
         "reaxff_mlp_init": (C.c_int, [vp, C.c_uint64]),
         "reaxff_mlp_set_params": (C.c_int, [vp, fp, fp, fp]),
         "reaxff_mlp_get_params": (C.c_int, [vp, fp, fp, fp]),
@@ -377,6 +378,21 @@ class ReaxFF:
         q = np.empty(self.n)
         self._check(self.lib.reaxff_mlp_predict(self.h, _dp(q)))
         return q
+
+    def species(self, bo_threshold=None, cap=4096):
+        """Molecular species at the current positions: (mol_id int32[n], {(replica,
+        counts of types 0..7): molecules})."""
+        thr = None
+        if bo_threshold is not None:
+            thr = np.ascontiguousarray(bo_threshold, np.float64).reshape(MAXT * MAXT)
+        mol = np.empty(self.n, np.int32)
+        nmol = C.c_int64()
+        rows = np.empty((cap, MAXT + 2), np.int32)
+        ns = C.c_int32()
+        self._check(self.lib.reaxff_species(self.h, None if thr is None else _dp(thr),
+                                            mol.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(nmol), cap,
+                                            rows.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(ns)))
+        return mol, {tuple(int(v) for v in r[:-1]): int(r[-1]) for r in rows[:ns.value]}
 
     def qeq_warm_choice(self):
         """Per replica: 1 where the last QEq solve kept the learned guess for s."""
