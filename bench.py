@@ -188,6 +188,7 @@ def run_ours(a, rank, world):
     prec = rx.MIXED if a.precision == "mixed" else rx.FP64
     ctx = rx.ReaxFF(P, w["types"], w["box"], w["options"], precision=prec, warm_start=rx.WARM_EXTRAP)
     ctx.set_state(w["x"], w["v"])
+    schedule = ctx.autotune()                               # launch schedules (untimed setup)
     stream = torch.cuda.current_stream(dev)
     etot = torch.zeros(max(a.steps, 1), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -238,7 +239,9 @@ def run_ours(a, rank, world):
                    "warm_start": "extrapolated", "qeq_tol": w["options"]["qeq_tol"], "dt_fs": a.dt,
                    "lists": "Verlet-skin candidates (1 A skin, rebuilt on displacement > skin/2), exact cutoff filter every step",
                    "l2": "flushed (256 MB write) before each library call of %d steps; each step streams > 200 MB of lists" % CALL_STEPS,
-                   "parallelism": "independent system per GPU" if world > 1 else "single GPU"},
+                   "parallelism": "independent system per GPU" if world > 1 else "single GPU",
+                   "schedule": dict(zip(("torsion_lanes", "nonbonded_block", "filter_block", "bond_list_block",
+                                         "angle_block", "hbond_block"), schedule))},
         "clocks": clocks.summary(),
         "gpu_launches": launches,
         "qeq_iters_last": [int(its[0]), int(itt[0])],

@@ -105,6 +105,7 @@ struct reaxff_ctx {
     int cap = 0, count = 0;                // training snapshots
     float *TD = nullptr, *TQ = nullptr;
   } mlp;
+  rx::Tune tune{};              // launch schedules (reaxff_autotune)
   // species analysis buffers (allocated on first use)
   DevBuf spbuf;
   rx::SpeciesBuf sp{};
@@ -245,7 +246,7 @@ int alloc_lists(reaxff_ctx* ctx) {
   return REAXFF_OK;
 }
 
-rx::Launch launch_of(reaxff_ctx* ctx) { return rx::Launch{ctx->st, &ctx->launches}; }
+rx::Launch launch_of(reaxff_ctx* ctx) { return rx::Launch{ctx->st, &ctx->launches, &ctx->tune}; }
 
 const char* const STAGE_NAMES[] = {"cells", "far_list", "bond_list", "bo_prime64", "qeq", "bo_correct",
                                    "atom_terms", "over_under_bond", "s_gather", "angles", "torsions",
@@ -1690,6 +1691,121 @@ int reaxff_species(reaxff_ctx* ctx, const double* bo_threshold, int32_t* mol_id,
   if (nmol) *nmol = M;
   if (nspecies) *nspecies = ns;
   if (ns > cap) return fail(ctx, REAXFF_E_CAPACITY, "more species than cap (count in *nspecies)");
+  return REAXFF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ autotuner
+namespace {
+template <typename R> const DParams<R>* params_ptr(reaxff_ctx* ctx);
+template <> const DParams<double>* params_ptr<double>(reaxff_ctx* ctx) { return ctx->Pd; }
+template <> const DParams<float>* params_ptr<float>(reaxff_ctx* ctx) { return ctx->Pf; }
+
+// mean device time (ms) of `launch` over 8 runs after 2 warm-up runs; +inf if it fails
+template <typename F> float time_launch(reaxff_ctx* ctx, F&& launch) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return 1e30f;
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return 1e30f; }
+  for (int k = 0; k < 2; ++k) launch();
+  cudaEventRecord(a, ctx->st);
+  for (int k = 0; k < 8; ++k) launch();
+  cudaEventRecord(b, ctx->st);
+  float ms = 1e30f;
+  if (cudaEventSynchronize(b) == cudaSuccess && cudaGetLastError() == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+  else ms = 1e30f;
+  cudaGetLastError();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / 8.0f;
+}
+
+template <typename R> void tune_all(reaxff_ctx* ctx) {
+  rx::Launch L = launch_of(ctx);
+  const DParams<R>* P = params_ptr<R>(ctx);
+  rx::Tune& T = ctx->tune;
+  auto pick = [&](int& knob, std::initializer_list<int> cands, auto&& run) {
+    float best = 1e30f;
+    int arg = knob;
+    for (int c : cands) {
+      knob = c;
+      const float ms = time_launch(ctx, run);
+      if (ms < best) { best = ms; arg = c; }
+    }
+    knob = arg;
+  };
+  pick(T.tors_lanes, {2, 4, 8}, [&] { rx::torsions<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); });
+  pick(T.nb_block, {128, 256, 512}, [&] { rx::nonbonded<R>(L, ctx->sys, ctx->far, ctx->acc, P, ctx->mask); });
+  pick(T.ang_block, {64, 128, 256}, [&] { rx::angles<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); });
+  pick(T.hb_block, {64, 128, 256}, [&] { rx::hbonds<R>(L, ctx->sys, ctx->bond, ctx->hb, ctx->acc, P, ctx->mask); });
+  if (ctx->use_skin)
+    pick(T.cf_block, {128, 256, 512}, [&] {
+      rx::cand_filter<R>(L, ctx->sys, ctx->cand, ctx->far, P, ctx->far_margin, ctx->near_margin);
+    });
+  pick(T.bl_block, {128, 256, 512}, [&] {
+    cudaMemsetAsync(ctx->bond.ncanon, 0, sizeof(int), ctx->st);
+    rx::bond_list<R>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, P, ctx->Pd);
+  });
+}
+
+std::string tune_key(reaxff_ctx* ctx) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp pr{};
+  cudaGetDeviceProperties(&pr, dev);
+  char buf[256];
+  snprintf(buf, sizeof(buf), "n=%d nrep=%d prec=%d skin=%d sm=%d.%d sms=%d", ctx->n, ctx->nrep, ctx->fp64 ? 0 : 1,
+           ctx->use_skin ? 1 : 0, pr.major, pr.minor, pr.multiProcessorCount);
+  return buf;
+}
+}  // namespace
+
+extern "C" {
+
+int reaxff_autotune(reaxff_ctx* ctx, const char* cache_path, int32_t* schedule) {
+  if (!ctx) return REAXFF_E_INVALID;
+  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  const std::string key = tune_key(ctx);
+  bool found = false;
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char line[512];
+      while (fgets(line, sizeof(line), f)) {
+        rx::Tune t{};
+        char k[256];
+        if (sscanf(line, "reaxff-tune %255[^|]| tors=%d nb=%d cf=%d bl=%d ang=%d hb=%d", k, &t.tors_lanes, &t.nb_block,
+                   &t.cf_block, &t.bl_block, &t.ang_block, &t.hb_block) == 7 &&
+            key == std::string(k).substr(0, std::string(k).find_last_not_of(' ') + 1)) {
+          ctx->tune = t;
+          found = true;
+        }
+      }
+      fclose(f);
+    }
+  }
+  int rc;
+  if (!found) {
+    if ((rc = forces_impl(ctx, true))) return rc;                // lists and bond data to time on
+    if (ctx->fp64) tune_all<double>(ctx);
+    else tune_all<float>(ctx);
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->forces_valid = false;                                  // the timing runs accumulated
+    if ((rc = forces_impl(ctx, true))) return rc;
+    if (cache_path) {
+      if (FILE* f = fopen(cache_path, "a")) {
+        const rx::Tune& t = ctx->tune;
+        fprintf(f, "reaxff-tune %s | tors=%d nb=%d cf=%d bl=%d ang=%d hb=%d\n", key.c_str(), t.tors_lanes, t.nb_block,
+                t.cf_block, t.bl_block, t.ang_block, t.hb_block);
+        fclose(f);
+      }
+    }
+  }
+  drop_graph(ctx);                                              // schedules are baked into the graph
+  if (schedule) {
+    const rx::Tune& t = ctx->tune;
+    const int v[6] = {t.tors_lanes, t.nb_block, t.cf_block, t.bl_block, t.ang_block, t.hb_block};
+    for (int q = 0; q < 6; ++q) schedule[q] = v[q];
+  }
   return REAXFF_OK;
 }
 

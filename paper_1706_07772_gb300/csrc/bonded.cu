@@ -517,10 +517,9 @@ __global__ void k_angles(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<
 // bond are combined inside the group (float-float on the mixed path) and added by fixed-
 // point atomics, energies and virial into per-atom fixed-point accumulators. Integer
 // atomics make the result independent of scheduling.
-constexpr int TG = 4;
 
-template <typename R> struct GroupSum;
-template <> struct GroupSum<float> {
+template <typename R, int TG> struct GroupSum;
+template <int TG> struct GroupSum<float, TG> {
   // every lane of the TG-lane group gets the group total (hi, lo)
   static __device__ __forceinline__ void run(float& hi, float& lo) {
 #pragma unroll
@@ -537,7 +536,7 @@ template <> struct GroupSum<float> {
     fix_add_ff(p, hi, lo, err);
   }
 };
-template <> struct GroupSum<double> {
+template <int TG> struct GroupSum<double, TG> {
   static __device__ __forceinline__ void run(double& hi, double& lo) {
 #pragma unroll
     for (int o = TG / 2; o > 0; o >>= 1) hi += __shfl_xor_sync(0xffffffffu, hi, o);
@@ -548,7 +547,7 @@ template <> struct GroupSum<double> {
   }
 };
 
-template <typename R>
+template <typename R, int TG>
 __global__ void __launch_bounds__(128) k_torsions(Sys s, BondList bl, AtomQ aq, Accum acc,
                                                    const DParams<R>* __restrict__ P, unsigned mask) {
   const int lane = threadIdx.x & 31;
@@ -701,7 +700,7 @@ __global__ void __launch_bounds__(128) k_torsions(Sys s, BondList bl, AtomQ aq, 
     for (int q = 0; q < NV; ++q) {
       hi[q] = v[q];
       lo[q] = R(0);
-      GroupSum<R>::run(hi[q], lo[q]);
+      GroupSum<R, TG>::run(hi[q], lo[q]);
     }
     if (ntot > 0) {
 #pragma unroll
@@ -723,7 +722,7 @@ __global__ void __launch_bounds__(128) k_torsions(Sys s, BondList bl, AtomQ aq, 
         else if (q == 15) dst = aq.cddelta + k;
         else if (q == 16) dst = bl.cdbo + ejk;
         else if (q == 17) dst = bl.cdbopi + ejk;
-        if (dst) GroupSum<R>::add(dst, h, l, s.err);
+        if (dst) GroupSum<R, TG>::add(dst, h, l, s.err);
       }
     }
   }
@@ -867,20 +866,25 @@ template <typename R> void s_gather(const Launch& L, Sys s, BondList b, AtomQ a)
 }
 template <typename R>
 void angles(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P, unsigned mask) {
-  k_angles<R><<<grid_for((long long)s.n * 32, 128), 128, 0, L.st>>>(s, b, a, acc, P, mask);
+  const int bs = L.t().ang_block;
+  k_angles<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, b, a, acc, P, mask);
   *L.count += 1;
 }
 template <typename R>
 void torsions(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P, unsigned mask) {
-  // central bonds: at most one per directed entry pair; about one per atom in molecular
-  // systems. The grid covers n central bonds in one pass and loops beyond that.
-  const long long threads = (long long)s.n * TG;
-  k_torsions<R><<<grid_for(threads, 128), 128, 0, L.st>>>(s, b, a, acc, P, mask);
+  // one group of lanes per central bond; about one central bond per atom in molecular
+  // systems: the grid covers n central bonds in one pass and loops beyond that
+  const int tg = L.t().tors_lanes;
+  const unsigned grid = grid_for((long long)s.n * tg, 128);
+  if (tg == 2) k_torsions<R, 2><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
+  else if (tg == 8) k_torsions<R, 8><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
+  else k_torsions<R, 4><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
   *L.count += 1;
 }
 template <typename R>
 void hbonds(const Launch& L, Sys s, BondList b, HbList h, Accum acc, const DParams<R>* P, unsigned mask) {
-  k_hbonds<R><<<grid_for((long long)s.n * 32, 128), 128, 0, L.st>>>(s, b, h, acc, P, mask);
+  const int bs = L.t().hb_block;
+  k_hbonds<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, b, h, acc, P, mask);
   *L.count += 1;
 }
 

@@ -668,7 +668,8 @@ void cand_build(const Launch& L, Sys s, Cells c, CandList cl) {
 
 template <typename R>
 void cand_filter(const Launch& L, Sys s, CandList cl, FarList f, const DParams<R>* P, float margin, float margin_near) {
-  k_cand_filter<R><<<grid_for((long long)s.n * 32, 256), 256, 0, L.st>>>(s, cl, f, P, margin, margin_near, f.r2_nb,
+  const int bs = L.t().cf_block;
+  k_cand_filter<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, cl, f, P, margin, margin_near, f.r2_nb,
                                                                          f.r2_bond);
   k_rebuild_done<<<1, 32, 0, L.st>>>(s);
   *L.count += 2;
@@ -693,7 +694,8 @@ void far_list_split(const Launch& L, Sys s, Cells c, FarList f, const DParams<R>
 template <typename R>
 void bond_list(const Launch& L, Sys s, FarList f, BondList b, HbList h, AtomQ a, const DParams<R>* P,
                const DParams<double>* Pd) {
-  k_bond_list<R><<<grid_for((long long)s.n * 32, 256), 256, 0, L.st>>>(s, f, b, h, a, P, Pd);
+  const int bs = L.t().bl_block;
+  k_bond_list<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, f, b, h, a, P, Pd);
   *L.count += 1;
 }
 

@@ -222,7 +222,8 @@ __global__ void k_nonbonded(Sys s, FarList f, Accum acc, const DParams<R>* __res
 namespace rx {
 template <typename R>
 void nonbonded(const Launch& L, Sys s, FarList f, Accum acc, const DParams<R>* P, unsigned mask) {
-  k_nonbonded<R><<<grid_for((long long)s.n * 32, 256), 256, 0, L.st>>>(s, f, acc, P, mask);
+  const int bs = L.t().nb_block;
+  k_nonbonded<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, f, acc, P, mask);
   *L.count += 1;
 }
 template void nonbonded<double>(const Launch&, Sys, FarList, Accum, const DParams<double>*, unsigned);

@@ -466,9 +466,23 @@ std::string cuda_err_str(cudaError_t e);
 
 // kernel entry points (host launch wrappers), defined in the .cu files
 namespace rx {
+// launch schedules picked by the autotuner (reaxff_autotune); defaults otherwise
+struct Tune {
+  int tors_lanes = 4;          // lanes per central bond in the torsion kernel (2, 4, 8)
+  int nb_block = 256;          // threads per block: nonbonded (warp per atom)
+  int cf_block = 256;          //   candidate filter (warp per atom)
+  int bl_block = 256;          //   bond list (warp per atom)
+  int ang_block = 128;         //   angles (warp per centre)
+  int hb_block = 128;          //   H-bonds (warp per hydrogen)
+};
 struct Launch {
   cudaStream_t st;
   int64_t* count;              // launch counter
+  const Tune* tune = nullptr;  // schedules (null: defaults)
+  const Tune& t() const {
+    static const Tune def{};
+    return tune ? *tune : def;
+  }
 };
 // lists.cu
 void cells_build(const Launch& L, Sys s, Cells c);

@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
         "reaxff_qeq_spmv_total": (i64, [vp]),
         "reaxff_qeq_warm_choice": (C.c_int, [vp, ip32]),
         "reaxff_species": (C.c_int, [vp, dp, ip32, ip64, i32, ip32, ip32]),
+        "reaxff_autotune": (C.c_int, [vp, C.c_char_p, ip32]),
         "reaxff_mlp_init": (C.c_int, [vp, C.c_uint64]),
         "reaxff_mlp_set_params": (C.c_int, [vp, fp, fp, fp]),
         "reaxff_mlp_get_params": (C.c_int, [vp, fp, fp, fp]),
@@ -393,6 +394,14 @@ class ReaxFF:
                                             mol.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(nmol), cap,
                                             rows.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(ns)))
         return mol, {tuple(int(v) for v in r[:-1]): int(r[-1]) for r in rows[:ns.value]}
+
+    def autotune(self, cache_path=None):
+        """Pick launch schedules by timing; returns (torsion lanes, nonbonded, filter,
+        bond list, angles, H-bonds)."""
+        sch = np.empty(6, np.int32)
+        self._check(self.lib.reaxff_autotune(self.h, None if cache_path is None else str(cache_path).encode(),
+                                             sch.ctypes.data_as(C.POINTER(C.c_int32))))
+        return tuple(int(v) for v in sch)
 
     def qeq_warm_choice(self):
         """Per replica: 1 where the last QEq solve kept the learned guess for s."""

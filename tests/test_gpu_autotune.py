@@ -1,0 +1,39 @@
+"""Launch-schedule autotuner: picks among the stated alternatives, keeps results within
+rounding of the default schedule, and reuses its cache file."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotune_schedule_and_cache(params, tmp_path, prec):
+    import paper_1706_07772_gb300.reaxff as rx
+    w = synth.workload("petn464")
+    c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=prec)
+    c.set_state(w["x"], w["v"])
+    c.forces()
+    _, _, q = c.get_state()
+    F0, E0, _ = c.forces(q=q)                       # fixed charges: only the schedule changes
+    cache = tmp_path / "tune.txt"
+    sch = c.autotune(cache)
+    assert sch[0] in (2, 4, 8) and sch[1] in (128, 256, 512) and sch[2] in (128, 256, 512)
+    assert sch[3] in (128, 256, 512) and sch[4] in (64, 128, 256) and sch[5] in (64, 128, 256)
+    F1, E1, _ = c.forces(q=q)
+    rms = np.sqrt((F0 ** 2).mean())
+    assert np.abs(F1 - F0).max() < (1e-12 if prec == 0 else 1e-6) * rms
+    assert np.allclose(E1, E0, rtol=1e-12 if prec == 0 else 1e-7)
+    # a second context of the same system takes the schedule from the cache
+    c2 = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=prec)
+    c2.set_state(w["x"], w["v"])
+    assert c2.autotune(cache) == sch
+    assert len(cache.read_text().splitlines()) == 1
+    c2.step(3, 0.1)
+    c.step(3, 0.1)
+    x1, _, _ = c.get_state()
+    x2, _, _ = c2.get_state()
+    assert np.abs(x1 - x2).max() < 1e-9
+    c.close()
+    c2.close()
