@@ -172,6 +172,44 @@ template <typename R> void fill_params(DParams<R>& d, const reaxff_params& p, co
 #undef PG
   d.r_nb = (R)o.r_nb; d.r_bond = (R)o.r_bond; d.r_hb = (R)o.r_hb; d.bo_cut = (R)o.bo_cut;
   d.thb_cut = (R)o.thb_cut; d.thb_cutsq = (R)o.thb_cutsq; d.hb_bo_min = (R)o.hb_bo_min;
+  // the distance at which BO'(r) = bo_cut, per type pair (bisection in FP64 after checking
+  // that BO' decreases over (0, r_bond]); the kernels decide membership by comparing r with
+  // it and evaluate BO' in FP64 only within a tiny band around it
+  for (int a = 0; a < MAXT; ++a)
+    for (int b = 0; b < MAXT; ++b) {
+      const int k = a * MAXT + b;
+      auto bop = [&](double r) {
+        double t = 0.0;
+        if (p.r0s[a][b] > 0) t += (1.0 + o.bo_cut) * std::exp(p.p_bo1[a][b] * std::pow(r / p.r0s[a][b], p.p_bo2[a][b]));
+        if (p.r0p[a][b] > 0) t += std::exp(p.p_bo3[a][b] * std::pow(r / p.r0p[a][b], p.p_bo4[a][b]));
+        if (p.r0pp[a][b] > 0) t += std::exp(p.p_bo5[a][b] * std::pow(r / p.r0pp[a][b], p.p_bo6[a][b]));
+        return t;
+      };
+      bool mono = a < p.ntypes && b < p.ntypes;
+      double prev = bop(1e-3);
+      for (int q = 1; q <= 2000 && mono; ++q) {
+        const double v = bop(1e-3 + (o.r_bond - 1e-3) * q / 2000.0);
+        if (v > prev) mono = false;
+        prev = v;
+      }
+      double cut = 0.0;
+      if (mono) {
+        if (bop(o.r_bond) >= o.bo_cut) cut = o.r_bond * 2.0;          // every near pair bonds
+        else if (bop(1e-3) < o.bo_cut) cut = 0.0;                      // none does
+        else {
+          double lo = 1e-3, hi = o.r_bond;
+          for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (bop(mid) >= o.bo_cut) lo = mid; else hi = mid;
+          }
+          cut = 0.5 * (lo + hi);
+        }
+      }
+      d.bcut[k] = cut;
+      d.bcut_h[k] = (float)cut;
+      d.bcut_l[k] = (float)(cut - (double)(float)cut);
+      d.bcut_ok[k] = mono ? 1 : 0;
+    }
 }
 
 int round_up(double v, int m) { return (int)((std::ceil(v) + m - 1) / m) * m; }

@@ -322,11 +322,16 @@ __global__ void k_bond_list(Sys s, FarList f, BondList bl, HbList hl, AtomQ aq,
       j = f.jn[frow + k];
       code = f.sn[frow + k];
       const int pt = ti * MAXT + s.type[j];
-      R bs, bp, bpp, dbs, dbp, dbpp;
+      // membership: BO'(r) >= bo_cut  <=>  r <= bcut (exact FP64 evaluation within 1e-7 A of
+      // bcut, where the float-float or double distance cannot decide)
+      constexpr double BAND = 1e-7;
       if (sizeof(R) == 8) {
         PairVec<R>::get(s, i, j, code, r, dx, dy, dz);
         rr = m_sqrt(dx * dx + dy * dy + dz * dz);
-        isb = bond_member_exact(s, Pd, i, j, code, r, pt);
+        const double dr = (double)rr - Pd->bcut[pt];
+        isb = (Pd->bcut_ok[pt] && dr < -BAND) ? true
+              : (Pd->bcut_ok[pt] && dr > BAND) ? false
+              : bond_member_exact(s, Pd, i, j, code, r, pt);
       } else {
         int sx, sy, sz;
         shift_decode(code, sx, sy, sz);
@@ -340,10 +345,10 @@ __global__ void k_bond_list(Sys s, FarList f, BondList bl, HbList hl, AtomQ aq,
         norm_ff(dh, dl, rh, rl);
         dx = (R)dh[0]; dy = (R)dh[1]; dz = (R)dh[2];
         rr = (R)rh;
-        bo_prime<R>(P, pt, rr, (R)rl, bs, bp, bpp, dbs, dbp, dbpp);
-        const R tot = bs + bp + bpp;
-        const bool clear = fabsf((float)(tot - P->bo_cut)) > 1e-3f * (float)P->bo_cut;
-        isb = clear ? tot >= P->bo_cut : bond_member_exact(s, Pd, i, j, code, r, pt);
+        const float dr = (rh - P->bcut_h[pt]) + (rl - P->bcut_l[pt]);   // exact leading difference
+        isb = (P->bcut_ok[pt] && dr < -(float)BAND) ? true
+              : (P->bcut_ok[pt] && dr > (float)BAND) ? false
+              : bond_member_exact(s, Pd, i, j, code, r, pt);
       }
       ish = is_h && P->hb[s.type[j]] == 2;               // r < r_bond <= r_hb
     }

@@ -55,6 +55,12 @@ struct DParams {
       p_val4[MAXT * MAXT * MAXT], p_val7[MAXT * MAXT * MAXT], p_pen1[MAXT * MAXT * MAXT],
       p_coa1[MAXT * MAXT * MAXT];
   R r0s_lo[MAXT * MAXT], r0p_lo[MAXT * MAXT], r0pp_lo[MAXT * MAXT];   // r0 - R(r0) (float-float)
+  // bond membership as a distance: BO'(r) >= bo_cut exactly when r <= bcut (each BO' term
+  // decreases with r); bcut as double and float-float; bcut_ok = 0 where that does not hold
+  // for the parameters (then membership is decided in FP64 every time)
+  double bcut[MAXT * MAXT];
+  float bcut_h[MAXT * MAXT], bcut_l[MAXT * MAXT];
+  int bcut_ok[MAXT * MAXT];
   R V1[MAXT * MAXT], V2[MAXT * MAXT], V3[MAXT * MAXT], p_tor1[MAXT * MAXT], p_cot1[MAXT * MAXT];
   R r0hb[MAXT * MAXT], p_hb1[MAXT * MAXT], p_hb2[MAXT * MAXT], p_hb3[MAXT * MAXT];
   R p_boc1, p_boc2, p_lp1, p_ovun3, p_ovun4, p_ovun6, p_ovun7, p_ovun8, p_val6, p_val8, p_val9,
