@@ -71,7 +71,7 @@ struct reaxff_ctx {
   double *chi_t = nullptr, *eta_t = nullptr, *mass_t = nullptr;
   int* h_err_pinned = nullptr;
   int cap_far = 0, cap_bond = 0, cap_hb = 0, cap_near = 0, cap_cand = 0;
-  float near_margin = 0.f;
+  float near_margin = 0.f, hb_margin = 0.f;
   bool use_skin = true;
   double skin = 1.0;
   CandList cand{};
@@ -248,6 +248,7 @@ int alloc_lists(reaxff_ctx* ctx) {
   f.Hn = B.alloc_bytes(n * f.capn * rs);
   f.r2_nb = ctx->ho.r_nb * ctx->ho.r_nb;
   f.r2_bond = ctx->ho.r_bond * ctx->ho.r_bond;
+  f.r2_hb = ctx->ho.r_hb * ctx->ho.r_hb;
   BondList& b = ctx->bond;
   b.cap = ctx->cap_bond;
   const size_t nb = n * b.cap;
@@ -363,11 +364,11 @@ int build_lists_impl(reaxff_ctx* ctx, bool checked = true) {
         rx::skin_check(L, ctx->sys, ctx->cand);
         rx::cand_build(L, ctx->sys, ctx->cells, ctx->cand); }
       if (ctx->fp64) {
-        { Stage st(ctx, 1); rx::cand_filter<double>(L, ctx->sys, ctx->cand, ctx->far, ctx->Pd, ctx->far_margin, ctx->near_margin); }
-        { Stage st(ctx, 2); rx::bond_list<double>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pd, ctx->Pd); }
+        { Stage st(ctx, 1); rx::cand_filter<double>(L, ctx->sys, ctx->cand, ctx->far, ctx->hb, ctx->Pd, ctx->far_margin, ctx->near_margin, ctx->hb_margin); }
+        { Stage st(ctx, 2); rx::bond_list<double>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pd, ctx->Pd, true); }
       } else {
-        { Stage st(ctx, 1); rx::cand_filter<float>(L, ctx->sys, ctx->cand, ctx->far, ctx->Pf, ctx->far_margin, ctx->near_margin); }
-        { Stage st(ctx, 2); rx::bond_list<float>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pf, ctx->Pd); }
+        { Stage st(ctx, 1); rx::cand_filter<float>(L, ctx->sys, ctx->cand, ctx->far, ctx->hb, ctx->Pf, ctx->far_margin, ctx->near_margin, ctx->hb_margin); }
+        { Stage st(ctx, 2); rx::bond_list<float>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pf, ctx->Pd, true); }
       }
     } else {
     { Stage st(ctx, 0); rx::cells_build(L, ctx->sys, ctx->cells); }
@@ -598,6 +599,7 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   const double u = std::ldexp(1.0, -24);
   ctx->far_margin = (float)(32.0 * u * (lmax * options->r_nb + options->r_nb * options->r_nb));
   ctx->near_margin = (float)(32.0 * u * (lmax * options->r_bond + options->r_bond * options->r_bond));
+  ctx->hb_margin = (float)(32.0 * u * (lmax * options->r_hb + options->r_hb * options->r_hb));
   {
     const double rc = options->r_nb + ctx->skin;
     ctx->cand.rc2 = (float)(rc * rc + 64.0 * u * (lmax * rc + rc * rc));
@@ -1778,11 +1780,11 @@ template <typename R> void tune_all(reaxff_ctx* ctx) {
   pick(T.hb_block, {64, 128, 256}, [&] { rx::hbonds<R>(L, ctx->sys, ctx->bond, ctx->hb, ctx->acc, P, ctx->mask); });
   if (ctx->use_skin)
     pick(T.cf_block, {128, 256, 512}, [&] {
-      rx::cand_filter<R>(L, ctx->sys, ctx->cand, ctx->far, P, ctx->far_margin, ctx->near_margin);
+      rx::cand_filter<R>(L, ctx->sys, ctx->cand, ctx->far, ctx->hb, P, ctx->far_margin, ctx->near_margin, ctx->hb_margin);
     });
   pick(T.bl_block, {128, 256, 512}, [&] {
     cudaMemsetAsync(ctx->bond.ncanon, 0, sizeof(int), ctx->st);
-    rx::bond_list<R>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, P, ctx->Pd);
+    rx::bond_list<R>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, P, ctx->Pd, ctx->use_skin);
   });
 }
 

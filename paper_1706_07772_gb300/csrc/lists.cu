@@ -298,14 +298,14 @@ __device__ __forceinline__ bool bond_member_exact(const Sys& s, const DParams<do
 
 template <typename R>
 __global__ void k_bond_list(Sys s, FarList f, BondList bl, HbList hl, AtomQ aq,
-                            const DParams<R>* __restrict__ P, const DParams<double>* __restrict__ Pd) {
+                            const DParams<R>* __restrict__ P, const DParams<double>* __restrict__ Pd, int hb_built) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= s.n) return;
   const int i = warp;
   const int r = s.rep[i];
   const int ti = s.type[i];
-  const bool is_h = P->hb[ti] == 1;
+  const bool is_h = !hb_built && P->hb[ti] == 1;       // hb_built: the candidate filter made that list
   const int brow = i * bl.cap, hrow = i * hl.cap;
   R* bdx = (R*)bl.dx; R* bdy = (R*)bl.dy; R* bdz = (R*)bl.dz; R* br = (R*)bl.r;
   const double rh2 = Pd->r_hb * Pd->r_hb;
@@ -404,9 +404,11 @@ __global__ void k_bond_list(Sys s, FarList f, BondList bl, HbList hl, AtomQ aq,
   }
   if (lane == 0) {
     bl.cnt[i] = nb < bl.cap ? nb : bl.cap;
-    hl.cnt[i] = nh < hl.cap ? nh : hl.cap;
     if (nb > bl.cap) atomicOr(s.err, ERR_CAP_BOND);
-    if (nh > hl.cap) atomicOr(s.err, ERR_CAP_HB);
+    if (!hb_built) {
+      hl.cnt[i] = nh < hl.cap ? nh : hl.cap;
+      if (nh > hl.cap) atomicOr(s.err, ERR_CAP_HB);
+    }
   }
 }
 
@@ -516,34 +518,37 @@ __global__ void k_cand_build(Sys s, Cells c, CandList cl) {
 // every step: exact membership (same rule as the stencil far list) over the candidates;
 // image shift corrected by the box crossings since the build
 template <typename R>
-__global__ void k_cand_filter(Sys s, CandList cl, FarList f, const DParams<R>* __restrict__ P, float margin,
-                              float margin_near, double R2, double Rb2) {
+__global__ void k_cand_filter(Sys s, CandList cl, FarList f, HbList hl, const DParams<R>* __restrict__ P, float margin,
+                              float margin_near, float margin_hb, double R2, double Rb2, double Rh2) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= s.n) return;
   const int i = warp;
   const int r = s.rep[i];
   const float* Lh = s.boxh + 3 * r;
-  const float R2f = (float)R2, Rb2f = (float)Rb2;
+  const float R2f = (float)R2, Rb2f = (float)Rb2, Rh2f = (float)Rh2;
   const float xi = s.xh[i], yi = s.yh[i], zi = s.zh[i];
   int ii0, ii1, ii2;
   rec_img(s.pl[i].w, ii0, ii1, ii2);
   const int ti = s.type[i];
+  const bool is_h = P->hb[ti] == 1;                     // H atoms also collect their H-bond partners
   const int nc = cl.cnt[i], crow = i * cl.cap;
-  int cntn = 0, cntf = 0;
+  const int hrow = i * hl.cap;
+  int cntn = 0, cntf = 0, cnth = 0;
   const int rown = i * f.capn, rowf = i * f.cap;
   R* Hn = (R*)f.Hn;
   R* Hf = (R*)f.H;
   for (int base = 0; base < nc; base += 32) {
     const int k = base + lane;
-    bool ok = false, near = false;
+    bool ok = false, near = false, ish = false;
     int j = -1, code = 13;
     if (k < nc) {
       j = cl.j[crow + k];
       int sx, sy, sz, jx, jy, jz;
       shift_decode(cl.s[crow + k], sx, sy, sz);
       const float4 hj = s.ph[j];
-      rec_img(s.pl[j].w, jx, jy, jz);                   // crossing counters ride in the record
+      const float wj = s.pl[j].w;
+      rec_img(wj, jx, jy, jz);                          // crossing counters ride in the record
       sx += jx - ii0;
       sy += jy - ii1;
       sz += jz - ii2;
@@ -554,11 +559,23 @@ __global__ void k_cand_filter(Sys s, CandList cl, FarList f, const DParams<R>* _
         const float r2f = dx * dx + dy * dy + dz * dz;
         ok = !(j == i && code == 13) && in_range(s, i, j, code, r, r2f, R2f, margin, R2);
         if (ok) near = in_range(s, i, j, code, r, r2f, Rb2f, margin_near, Rb2);
+        // H-bond partner: an acceptor with r < r_hb (every near pair of one is, r_bond <= r_hb)
+        if (ok && is_h && P->hb[rec_type(wj)] == 2)
+          ish = near || in_range(s, i, j, code, r, r2f, Rh2f, margin_hb, Rh2);
       }
     }
     const unsigned mn = __ballot_sync(0xffffffffu, ok && near);
     const unsigned mf = __ballot_sync(0xffffffffu, ok && !near);
+    const unsigned mh = __ballot_sync(0xffffffffu, ish);
     const unsigned below = (1u << lane) - 1u;
+    if (ish) {
+      const int hp = cnth + __popc(mh & below);
+      if (hp < hl.cap) {
+        hl.j[hrow + hp] = j;
+        hl.s[hrow + hp] = (uint8_t)code;
+      }
+    }
+    cnth += __popc(mh);
     if (ok) {
       R dx, dy, dz;
       int tj;
@@ -596,8 +613,10 @@ __global__ void k_cand_filter(Sys s, CandList cl, FarList f, const DParams<R>* _
   if (lane == 0) {
     f.cntn[i] = cntn < f.capn ? cntn : f.capn;
     f.cnt[i] = cntf < f.cap ? cntf : f.cap;
+    hl.cnt[i] = cnth < hl.cap ? cnth : hl.cap;
     if (cntn > f.capn) atomicOr(s.err, ERR_CAP_NEAR);
     if (cntf > f.cap) atomicOr(s.err, ERR_CAP_FAR);
+    if (cnth > hl.cap) atomicOr(s.err, ERR_CAP_HB);
   }
 }
 
@@ -672,15 +691,18 @@ void cand_build(const Launch& L, Sys s, Cells c, CandList cl) {
 }
 
 template <typename R>
-void cand_filter(const Launch& L, Sys s, CandList cl, FarList f, const DParams<R>* P, float margin, float margin_near) {
+void cand_filter(const Launch& L, Sys s, CandList cl, FarList f, HbList h, const DParams<R>* P, float margin,
+                 float margin_near, float margin_hb) {
   const int bs = L.t().cf_block;
-  k_cand_filter<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, cl, f, P, margin, margin_near, f.r2_nb,
-                                                                         f.r2_bond);
+  k_cand_filter<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, cl, f, h, P, margin, margin_near, margin_hb,
+                                                                         f.r2_nb, f.r2_bond, f.r2_hb);
   k_rebuild_done<<<1, 32, 0, L.st>>>(s);
   *L.count += 2;
 }
-template void cand_filter<double>(const Launch&, Sys, CandList, FarList, const DParams<double>*, float, float);
-template void cand_filter<float>(const Launch&, Sys, CandList, FarList, const DParams<float>*, float, float);
+template void cand_filter<double>(const Launch&, Sys, CandList, FarList, HbList, const DParams<double>*, float, float,
+                                  float);
+template void cand_filter<float>(const Launch&, Sys, CandList, FarList, HbList, const DParams<float>*, float, float,
+                                 float);
 
 template <typename R>
 void far_list(const Launch& L, Sys s, Cells c, FarList f, const DParams<R>* P, float margin) {
@@ -698,9 +720,9 @@ void far_list_split(const Launch& L, Sys s, Cells c, FarList f, const DParams<R>
 
 template <typename R>
 void bond_list(const Launch& L, Sys s, FarList f, BondList b, HbList h, AtomQ a, const DParams<R>* P,
-               const DParams<double>* Pd) {
+               const DParams<double>* Pd, bool hb_built) {
   const int bs = L.t().bl_block;
-  k_bond_list<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, f, b, h, a, P, Pd);
+  k_bond_list<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, f, b, h, a, P, Pd, hb_built ? 1 : 0);
   *L.count += 1;
 }
 
@@ -731,7 +753,7 @@ template void far_list<float>(const Launch&, Sys, Cells, FarList, const DParams<
 template void far_list_split<double>(const Launch&, Sys, Cells, FarList, const DParams<double>*, float, float);
 template void far_list_split<float>(const Launch&, Sys, Cells, FarList, const DParams<float>*, float, float);
 template void bond_list<double>(const Launch&, Sys, FarList, BondList, HbList, AtomQ, const DParams<double>*,
-                                const DParams<double>*);
+                                const DParams<double>*, bool);
 template void bond_list<float>(const Launch&, Sys, FarList, BondList, HbList, AtomQ, const DParams<float>*,
-                               const DParams<double>*);
+                               const DParams<double>*, bool);
 }  // namespace rx

@@ -130,7 +130,7 @@ struct FarList {
   int* jn;
   uint8_t* sn;
   void* Hn;
-  double r2_nb, r2_bond;       // squared cutoffs (precomputed on the host)
+  double r2_nb, r2_bond, r2_hb; // squared cutoffs (precomputed on the host)
 };
 
 struct BondList {
@@ -504,10 +504,11 @@ void positions_f32(const Launch& L, Sys s);
 void skin_check(const Launch& L, Sys s, CandList cl);
 void cand_build(const Launch& L, Sys s, Cells c, CandList cl);
 template <typename R>
-void cand_filter(const Launch& L, Sys s, CandList cl, FarList f, const DParams<R>* P, float margin, float margin_near);
+void cand_filter(const Launch& L, Sys s, CandList cl, FarList f, HbList h, const DParams<R>* P, float margin,
+                 float margin_near, float margin_hb);
 template <typename R>
 void bond_list(const Launch& L, Sys s, FarList f, BondList b, HbList h, AtomQ a, const DParams<R>* P,
-               const DParams<double>* Pd);
+               const DParams<double>* Pd, bool hb_built = false);   // hb_built: cand_filter made the H-bond list
 void bond_mirror(const Launch& L, Sys s, BondList b);
 void bo_prime64(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<double>* Pd, int n_canon_max);
 // bonded.cu
