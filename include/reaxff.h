@@ -114,7 +114,8 @@ typedef struct {
   double skin;        /* Verlet skin (A) of the neighbour candidate list, rebuilt on the device
                          only when an atom has moved more than skin/2; the far list is still
                          filtered exactly (r < r_nb) every step. 0 = default 1.0 A,
-                         negative = no candidate list (cell stencil every step). */
+                         negative = no candidate list (cell stencil every step). A system
+                         with a box edge <= r_nb + skin runs the cell stencil instead. */
 } reaxff_options;
 
 typedef struct reaxff_ctx reaxff_ctx;

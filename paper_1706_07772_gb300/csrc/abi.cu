@@ -591,8 +591,13 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   const double sph = 4.0 / 3.0 * M_PI;
   ctx->cap_far = std::max(64, round_up(margin * sph * (std::pow(options->r_nb, 3) - std::pow(options->r_bond, 3)) * rho + 16, 32));
   ctx->cap_near = std::max(32, round_up(margin * sph * std::pow(options->r_bond, 3) * rho + 16, 32));
-  ctx->use_skin = !(options->skin < 0.0);
   ctx->skin = options->skin > 0.0 ? options->skin : 1.0;
+  // candidates need every box edge above r_nb + skin (images beyond the nearest shifts stay
+  // out of reach between rebuilds); smaller boxes run the cell stencil every step
+  ctx->use_skin = !(options->skin < 0.0);
+  for (int r = 0; r < nrep; ++r)
+    for (int d = 0; d < 3; ++d)
+      if (!(boxes[3 * r + d] > options->r_nb + ctx->skin)) ctx->use_skin = false;
   ctx->cap_cand = std::max(64, round_up(margin * sph * std::pow(options->r_nb + ctx->skin, 3) * rho + 16, 32));
   ctx->cap_bond = 24;
   ctx->cap_hb = std::max(32, round_up(margin * sph * std::pow(options->r_hb, 3) * rho + 16, 32));
@@ -605,12 +610,14 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
     ctx->cand.rc2 = (float)(rc * rc + 64.0 * u * (lmax * rc + rc * rc));
     ctx->cand.half_skin2 = 0.25 * ctx->skin * ctx->skin;
   }
-  // ---- cells per replica
+  // ---- cells per replica: at least as wide as the largest distance the 27-cell stencil
+  // must cover (r_nb, or r_nb + skin for the Verlet candidates)
   std::vector<int> nc(3 * nrep), cell_off(nrep + 1, 0);
+  const double r_cell = ctx->use_skin ? options->r_nb + ctx->skin : options->r_nb;
   for (int r = 0; r < nrep; ++r) {
     int tot = 1;
     for (int d = 0; d < 3; ++d) {
-      nc[3 * r + d] = std::max(1, (int)std::floor(boxes[3 * r + d] / options->r_nb));
+      nc[3 * r + d] = std::max(1, (int)std::floor(boxes[3 * r + d] / r_cell));
       tot *= nc[3 * r + d];
     }
     cell_off[r + 1] = cell_off[r] + tot;
@@ -700,9 +707,11 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
     Q.rows_blk = *std::max_element(rowsb.begin(), rowsb.end());
     const size_t sc = (size_t)(nrep * rx::QEQ_SCAL_PER_REP + 4) * sizeof(double);
     const size_t st = (size_t)rx::QEQ_NV_STATE * Q.rows_blk * sizeof(double);
-    Q.scal_smem = sc <= (size_t)rx::QEQ_SMEM_MAX / 2;
-    Q.state_smem = (Q.scal_smem ? sc : 0) + st <= (size_t)rx::QEQ_SMEM_MAX;
-    Q.smem_bytes = (int)((Q.scal_smem ? sc : 0) + (Q.state_smem ? st : 0));
+    Q.ring_bytes = rx::qeq_ring_bytes(ctx->fp64);
+    const size_t avail = (size_t)rx::QEQ_SMEM_MAX - Q.ring_bytes;
+    Q.scal_smem = sc <= avail / 2;
+    Q.state_smem = (Q.scal_smem ? sc : 0) + st <= avail;
+    Q.smem_bytes = (int)(Q.ring_bytes + (Q.scal_smem ? sc : 0) + (Q.state_smem ? st : 0));
     Q.scal = Q.scal_smem ? nullptr : B.alloc<double>((size_t)Q.grid * (nrep * rx::QEQ_SCAL_PER_REP + 4));
     Q.state = Q.state_smem ? nullptr : B.alloc<double>((size_t)Q.grid * rx::QEQ_NV_STATE * Q.rows_blk);
   }

@@ -70,6 +70,7 @@ struct CG {
   double* state;                           // [grid][NV_STATE][rows_blk] row state, unless in shared memory
   int rows_blk;                            // most rows any block owns
   int scal_smem, state_smem;               // 1: kept in dynamic shared memory
+  int ring_bytes;                          // SpMV ring at the start of dynamic shared memory
   const int* chunk_lo;                     // [nchunk+1] rows
   const int* chunk_rep;                    // [nchunk]
   const int* rep_chunk;                    // [nrep+1] chunk ranges per replica
@@ -79,28 +80,28 @@ struct CG {
   int* err;
 };
 
-// bounded grid barrier (all blocks co-resident: cooperative launch)
-__device__ bool grid_barrier(GridBar* bar, int* err) {
+// Bounded grid barrier (all blocks co-resident: cooperative launch). The arrival counter
+// is zeroed before the launch and only grows: the k-th barrier completes when it reaches
+// k * gridDim.x (`target` counts this block's barriers). Thread 0 adds with acquire-release
+// semantics (publishes the block's writes, ordered before it by __syncthreads, and takes
+// those of the blocks that arrived earlier) and polls with acquire loads; no reset, so a
+// barrier costs one atomic round trip plus the wait for the last block. The wait gives up
+// after BAR_CYCLE_LIMIT SM cycles and raises ERR_TIMEOUT.
+__device__ bool grid_barrier(GridBar* bar, int* err, unsigned& target) {
   __syncthreads();
+  target += gridDim.x;
   if (threadIdx.x == 0) {
-    const unsigned g = *((volatile unsigned*)&bar->gen);
-    __threadfence();
-    const unsigned arrived = atomicAdd(&bar->arrive, 1u);
-    if (arrived == gridDim.x - 1) {
-      bar->arrive = 0;
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*((volatile unsigned*)&bar->gen) == g) {
-        if (++spins > BAR_SPIN_LIMIT) {
-          atomicOr(err, ERR_TIMEOUT);
-          break;
-        }
-        __nanosleep(32);
+    unsigned cur;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(cur) : "l"(&bar->arrive) : "memory");
+    cur += 1u;
+    const long long t0 = clock64();
+    while ((int)(cur - target) < 0) {
+      if (clock64() - t0 > BAR_CYCLE_LIMIT) {
+        atomicOr(err, ERR_TIMEOUT);
+        break;
       }
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->arrive) : "memory");
     }
-    __threadfence();
   }
   __syncthreads();
   return !(*((volatile int*)err) & ERR_TIMEOUT);
@@ -142,11 +143,25 @@ __device__ __forceinline__ void reduce_parts(const CG<R>& a, int pb, double* red
   constexpr int NVP = Pow2<NV>::v;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double* P = a.part + (size_t)pb * NQ * a.nchunk;
+  constexpr int U = NV <= 2 ? 4 : (NV <= 4 ? 2 : 1);      // chunks per lane in flight
   for (int r = wid; r < a.nrep; r += nw) {
     double v[NVP];
 #pragma unroll
     for (int q = 0; q < NVP; ++q) v[q] = 0.0;
-    for (int c = a.rep_chunk[r] + lane; c < a.rep_chunk[r + 1]; c += 32)
+    const int c1 = a.rep_chunk[r + 1];
+    int c = a.rep_chunk[r] + lane;
+    for (; c + 32 * (U - 1) < c1; c += 32 * U) {
+      double t[U][NV];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) t[u][q] = __ldcg(P + (size_t)q * a.nchunk + c + 32 * u);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] += t[u][q];
+    }
+    for (; c < c1; c += 32)
 #pragma unroll
       for (int q = 0; q < NV; ++q) v[q] += __ldcg(P + (size_t)q * a.nchunk + c);
     int slot;
@@ -268,11 +283,123 @@ __device__ __forceinline__ void spmv_part(const int* cnt, const int* col, const 
   }
 }
 
+// Mixed path SpMV of a warp's run of rows, with the matrix streamed through shared memory.
+// The work is a sequence of items: up to 128 consecutive entries of one part (near, then
+// far) of one row. Each warp owns SP_SLOTS ring slots of one item (128 columns, 128 H
+// values); lane l fills bytes 16l..16l+15 of both halves with cp.async (16-byte copies
+// that bypass L1 and hold no registers while in flight), zero-filling past the part's
+// count. The warp keeps SP_SLOTS - 1 items in flight ahead of the one it multiplies, across
+// row boundaries, so the stream does not wait on the gathers. Consuming an item, lane l
+// reads entries l, l+32, l+64, l+96 (the gathers of one load instruction fall on 32
+// consecutive list entries, a few cache lines) and refills the slot with the next item.
+// A row always yields its near item (possibly empty), so it ends on exactly one item,
+// where the lanes' sums are combined and stored. Zero-filled entries gather zg[0] with
+// h = 0 and add an exact zero. Rows start on 16-byte boundaries (capacities are multiples
+// of 32 entries).
+constexpr int SP_SLOTS = 3;
+constexpr int SP_SLOT_BYTES = 1024;
+constexpr int SP_RING_BYTES = 32 * SP_SLOTS * SP_SLOT_BYTES + 32 * SP_SLOTS * 4;   // slots, then tags
+
+struct SpCursor {
+  int i, part, k0;             // next item: row, part (0 near, 1 far), first entry
+  int bb, bn, bf;              // rows bb..bb+31: this lane holds the counts of row bb + lane
+};
+
+__device__ __forceinline__ void sp_counts(const CG<float>& a, SpCursor& c, int whi) {
+  const int i = c.bb + (threadIdx.x & 31);
+  c.bn = i < whi ? __ldg(a.cntn + i) : 0;
+  c.bf = i < whi ? __ldg(a.cnt + i) : 0;
+}
+
+__device__ __forceinline__ void cp_async16(unsigned saddr, const void* g, int nbytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// copies the cursor's item into the slot at shared address sa and moves the cursor to the
+// next item; returns the item's tag: 2 row + 1 when the item ends its row, else 2 row
+__device__ __forceinline__ int sp_issue(const CG<float>& a, SpCursor& c, int whi, unsigned sa) {
+  const int lane = threadIdx.x & 31;
+  const int n = __shfl_sync(0xffffffffu, c.part == 0 ? c.bn : c.bf, c.i - c.bb);
+  const size_t base = c.part == 0 ? (size_t)c.i * a.capn : (size_t)c.i * a.cap;
+  const int* cr = (c.part == 0 ? a.coln : a.col) + base;
+  const float* hr = (c.part == 0 ? a.Hn : a.H) + base;
+  const int k = c.k0 + 4 * lane;
+  const int nb = k < n ? min(4 * (n - k), 16) : 0;
+  const int ko = nb > 0 ? k : 0;
+  cp_async16(sa + 16 * lane, cr + ko, nb);
+  cp_async16(sa + 512 + 16 * lane, hr + ko, nb);
+  const int tag = 2 * c.i;
+  c.k0 += 128;
+  if (c.part == 0) {
+    if (c.k0 < n) return tag;
+    c.part = 1;
+    c.k0 = 0;
+  }
+  if (c.k0 < __shfl_sync(0xffffffffu, c.bf, c.i - c.bb)) return tag;
+  ++c.i;
+  c.part = 0;
+  c.k0 = 0;
+  if (c.i - c.bb == 32) {
+    c.bb = c.i;
+    sp_counts(a, c, whi);
+  }
+  return tag + 1;
+}
+
+__device__ __forceinline__ void spmv_ring_f(const CG<float>& a, unsigned char* ring, int wlo, int whi, float* us,
+                                            float* ut) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const float2* zg = (const float2*)a.zg;
+  unsigned char* mine = ring + wid * SP_SLOTS * SP_SLOT_BYTES;
+  int* tags = (int*)(ring + 32 * SP_SLOTS * SP_SLOT_BYTES) + wid * SP_SLOTS;
+  const unsigned sbase = (unsigned)__cvta_generic_to_shared(mine);
+  SpCursor c;
+  c.i = wlo; c.part = 0; c.k0 = 0; c.bb = wlo;
+  sp_counts(a, c, whi);
+#pragma unroll
+  for (int sl = 0; sl < SP_SLOTS; ++sl) {
+    const int tag = c.i < whi ? sp_issue(a, c, whi, sbase + sl * SP_SLOT_BYTES) : -1;
+    if (lane == 0) tags[sl] = tag;
+    cp_commit();
+  }
+  float sf = 0.f, tf = 0.f;
+  for (int sl = 0;; sl = sl + 1 == SP_SLOTS ? 0 : sl + 1) {
+    asm volatile("cp.async.wait_group %0;" ::"n"(SP_SLOTS - 1) : "memory");
+    __syncwarp();
+    const int tag = tags[sl];
+    if (tag < 0) break;
+    const int* sj = (const int*)(mine + sl * SP_SLOT_BYTES);
+    const float* sh = (const float*)(mine + sl * SP_SLOT_BYTES + 512);
+    const int j0 = sj[lane], j1 = sj[lane + 32], j2 = sj[lane + 64], j3 = sj[lane + 96];
+    const float h0 = sh[lane], h1 = sh[lane + 32], h2 = sh[lane + 64], h3 = sh[lane + 96];
+    const float2 z0 = zg[j0], z1 = zg[j1], z2 = zg[j2], z3 = zg[j3];
+    __syncwarp();                                        // every lane has read the slot
+    const int nt = c.i < whi ? sp_issue(a, c, whi, sbase + sl * SP_SLOT_BYTES) : -1;
+    if (lane == 0) tags[sl] = nt;
+    cp_commit();
+    sf = fmaf(h0, z0.x, sf); tf = fmaf(h0, z0.y, tf);
+    sf = fmaf(h1, z1.x, sf); tf = fmaf(h1, z1.y, tf);
+    sf = fmaf(h2, z2.x, sf); tf = fmaf(h2, z2.y, tf);
+    sf = fmaf(h3, z3.x, sf); tf = fmaf(h3, z3.y, tf);
+    if (tag & 1) {
+      sf = warp_sumf(sf);
+      tf = warp_sumf(tf);
+      if (lane == 0) { us[tag >> 1] = sf; ut[tag >> 1] = tf; }
+      sf = 0.f;
+      tf = 0.f;
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+}
+
 // where a block keeps its per-replica scalars and the CG vectors of its rows: shared
 // memory when they fit (the host decides), else a block-private global region. Either way
 // only this block reads or writes them, so no value crosses blocks except through zg and
 // the chunk partials.
 struct Blk {
+  unsigned char* ring;         // SpMV streaming ring (mixed path)
   double* S;                   // [nrep*NS + 4] scalars, then [nrep*NQ] reduced totals
   double* red;
   double* st;                  // [NV_STATE][rows] row state (structure of arrays)
@@ -292,6 +419,10 @@ __device__ __forceinline__ void spmv_chunk(const CG<R>& a, const Blk& B, int lo,
   const typename G2<R>::T* zg = (const typename G2<R>::T*)a.zg;
   R* us = B.u<R>(0);
   R* ut = B.u<R>(1);
+  if constexpr (sizeof(R) == 4) {
+    if (wlo < whi) spmv_ring_f(a, B.ring, wlo, whi, us + off - lo, ut + off - lo);
+    return;
+  }
   for (int i = wlo; i < whi; ++i) {
     R sf = 0, tf = 0;
     spmv_part<R>(a.cntn, a.coln, a.Hn, a.capn, i, zg, sf, tf);
@@ -358,9 +489,11 @@ __device__ __forceinline__ void count_active(double* S, int nrep) {
 
 template <typename R>
 __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
-  extern __shared__ double dsm[];
+  extern __shared__ double dsm_all[];
   __shared__ Chunks<R> C;
   Blk B;
+  B.ring = (unsigned char*)dsm_all;
+  double* dsm = dsm_all + a.ring_bytes / sizeof(double);
   const int sc = a.nrep * (NS + NQ) + 4;
   B.S = a.scal_smem ? dsm : a.scal + (size_t)blockIdx.x * sc;
   B.red = B.S + a.nrep * NS + 4;
@@ -373,6 +506,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
     }
   }
   const bool lead = blockIdx.x == 0;
+  unsigned bt = 0;                         // barriers passed x grid size
   int pb = 0;
   double* S = B.S;
   double* red = B.red;
@@ -422,7 +556,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
       });
       block_sum<2>(a, v, hi - lo, pb, c);
     });
-    if (!grid_barrier(a.bar, a.err)) return;
+    if (!grid_barrier(a.bar, a.err, bt)) return;
     reduce_parts<2>(a, pb, red);
     pb ^= 1;
     for (int r = threadIdx.x; r < a.nrep; r += blockDim.x)
@@ -435,7 +569,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
         put_zg(a, i, (double)a.qhat[i] + mu * B.v(V_XT, li), B.v(V_XS, li));
       });
     });
-    if (!grid_barrier(a.bar, a.err)) return;
+    if (!grid_barrier(a.bar, a.err, bt)) return;
     for_chunks(a, C, [&](int c, int lo, int hi, int rep, int off) {
       spmv_chunk(a, B, lo, hi, off);
       __syncthreads();
@@ -453,7 +587,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
       });
       block_sum<2>(a, v, hi - lo, pb, c);
     });
-    if (!grid_barrier(a.bar, a.err)) return;
+    if (!grid_barrier(a.bar, a.err, bt)) return;
     reduce_parts<2>(a, pb, red);
     pb ^= 1;
     for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
@@ -472,7 +606,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
       });
     });
   }
-  if (!grid_barrier(a.bar, a.err)) return;
+  if (!grid_barrier(a.bar, a.err, bt)) return;
   // r = b - H x, z = r/eta, p = w = 0
   for_chunks(a, C, [&](int c, int lo, int hi, int, int off) {
     spmv_chunk(a, B, lo, hi, off);
@@ -496,7 +630,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
     });
     block_sum<6>(a, v, hi - lo, pb, c);
   });
-  if (!grid_barrier(a.bar, a.err)) return;
+  if (!grid_barrier(a.bar, a.err, bt)) return;
   reduce_parts<6>(a, pb, red);
   pb ^= 1;
   for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
@@ -520,7 +654,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
       put_zg(a, i, B.v(V_ZS, li), B.v(V_ZT, li));
     });
   });
-  if (!grid_barrier(a.bar, a.err)) return;
+  if (!grid_barrier(a.bar, a.err, bt)) return;
   int it = 0;
   while (S[a.nrep * NS] > 0.0 && it < a.max_iter) {
     ++it;
@@ -550,7 +684,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
       });
       block_sum<2>(a, v, hi - lo, pb, c);
     });
-    if (!grid_barrier(a.bar, a.err)) return;
+    if (!grid_barrier(a.bar, a.err, bt)) return;
     reduce_parts<2>(a, pb, red);
     pb ^= 1;
     for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
@@ -587,7 +721,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
       });
       block_sum<4>(a, v, hi - lo, pb, c);
     });
-    if (!grid_barrier(a.bar, a.err)) return;
+    if (!grid_barrier(a.bar, a.err, bt)) return;
     reduce_parts<4>(a, pb, red);
     pb ^= 1;
     for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
@@ -622,7 +756,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
     });
     block_sum<2>(a, v, hi - lo, pb, c);
   });
-  if (!grid_barrier(a.bar, a.err)) return;
+  if (!grid_barrier(a.bar, a.err, bt)) return;
   reduce_parts<2>(a, pb, red);
   for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) S[r * NS + S_MU] = red[r * NQ + 0] / red[r * NQ + 1];
   __syncthreads();
@@ -666,6 +800,7 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   a.zg = Q.zg;
   a.q = s.q; a.qf = s.qf; a.ph = s.ph; a.part = Q.part; a.scal = Q.scal; a.state = Q.state;
   a.rows_blk = Q.rows_blk; a.scal_smem = Q.scal_smem; a.state_smem = Q.state_smem;
+  a.ring_bytes = Q.ring_bytes;
   a.ieta = Q.ieta;
   a.chunk_lo = Q.chunk_lo; a.chunk_rep = Q.chunk_rep; a.rep_chunk = Q.rep_chunk;
   a.iters = Q.iters; a.spmv_total = Q.spmv_total; a.bar = Q.bar; a.err = s.err;
@@ -675,6 +810,8 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   *L.count += 2;
   return e == cudaSuccess ? 0 : -1;
 }
+
+int qeq_ring_bytes(bool fp64) { return fp64 ? 0 : SP_RING_BYTES; }
 
 int qeq_grid_size(int nsm) {
   cudaFuncSetAttribute((const void*)k_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, QEQ_SMEM_MAX);

@@ -465,6 +465,7 @@ struct GridBar {
   unsigned int gen;
 };
 constexpr long long BAR_SPIN_LIMIT = 20000000LL;    // ~1-2 s of polling (64 ns sleeps)
+constexpr long long BAR_CYCLE_LIMIT = 3000000000LL; // ~1.5 s of SM clock at 2 GHz
 
 // ------------------------------------------------------------------ host side
 struct reaxff_ctx_impl;
@@ -569,6 +570,7 @@ struct QeqState {
   int rows_blk;                // most rows one block owns
   int scal_smem, state_smem;   // 1: held in dynamic shared memory
   int smem_bytes;              // dynamic shared memory of the launch
+  int ring_bytes;              // of which the SpMV streaming ring (mixed path; first in the layout)
   int* chunk_rep;              // replica of each chunk
   int* chunk_lo;               // first atom of each chunk [nchunk+1]
   int* rep_chunk;              // first chunk of each replica [nrep+1]
@@ -584,6 +586,7 @@ template <typename R>
 int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* P, const double* chi,
               const double* eta, double tol, int max_iter, int warm, const float* qhat);
 int qeq_grid_size(int nsm);
+int qeq_ring_bytes(bool fp64);   // shared memory of the SpMV streaming ring of a 1024-thread block
 
 // mlp.cu: learned QEq warm start (descriptors, BF16 tensor-core inference, FP32 training)
 constexpr int MLP_NF = 192, MLP_HID = 64, MLP_NT = 4;

@@ -293,3 +293,26 @@ def test_lists_stay_exact_along_md(rx, params, skin):
         got = keyset(*c.get_lists(which), n)
         assert np.array_equal(got, k), which
     c.close()
+
+
+def test_candidates_cover_pairs_two_cells_apart(rx, params):
+    """Two atoms 10.6 A apart across two cell boundaries of a 10.5 A grid (box 31.5 A)
+    drift towards each other by 0.35 A each (below the skin/2 rebuild trigger): the
+    pair, now 9.9 A apart, must be in the far list. The candidate cells have to be at
+    least r_nb + skin wide for the 27-cell stencil to have seen it at the build."""
+    box = np.array([31.5, 31.5, 31.5])
+    x = np.array([[10.45, 5.0, 5.0], [21.05, 5.0, 5.0]])
+    v = np.array([[0.035, 0.0, 0.0], [-0.035, 0.0, 0.0]])
+    types = np.array([0, 0], np.int32)
+    o = dict(synth.OPTIONS_DEFAULT)
+    c = rx.ReaxFF(params, types, box, o, precision=1, skin=1.0)
+    c.set_state(x, v)
+    c.step(20, 0.5)
+    xf, _, _ = c.get_state()
+    assert abs(np.linalg.norm(xf[1] - xf[0]) - 9.9) < 0.01
+    L = oracle.build_lists(xf, types, box, params, o)
+    want = keyset(L["far"]["i"], L["far"]["j"], L["far"]["s"], 2)
+    assert len(want) == 2                                  # (0, 1) and (1, 0), image shift 0
+    got = keyset(*c.get_lists(rx.LIST_FAR), 2)
+    assert np.array_equal(got, want)
+    c.close()
