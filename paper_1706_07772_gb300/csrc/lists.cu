@@ -657,6 +657,109 @@ __global__ void k_delta_prime(Sys s, BondList bl, AtomQ aq, const DParams<double
 
 inline unsigned grid_for(long long threads, int block) { return (unsigned)((threads + block - 1) / block); }
 
+// 1/cbrt(x) for x > 0: the MUFU estimate 2^(-log2(x)/3) (relative error ~1e-6) and one
+// Newton step on y^-3 = x, y <- y + y (1 - x y^3) / 3, which squares the relative error
+__device__ __forceinline__ float rcbrt_f(float x) {
+  const float y = __powf(x, -1.0f / 3.0f);
+  const float y3 = y * y * y;
+  const float e = __fmaf_rn(-x, y3, 1.0f);
+  return __fmaf_rn(y * (1.0f / 3.0f), e, y);
+}
+
+// Mixed path form of k_cand_filter: atom i's records, box and image counters live in
+// registers; the shift code is decoded once; atom j's two 16-byte records are read once and
+// give the exact-order float-float image vector used both for the range decisions (its error
+// is far inside the margins) and for H; H = Tap(r) k_e (r^3 + gamma^-3)^(-1/3) with one
+// branch-free rcbrt_f for near and far entries; the near/far destination is a per-lane
+// select, so the stores do not diverge.
+__global__ void k_cand_filter_f(Sys s, CandList cl, FarList f, HbList hl, const DParams<float>* __restrict__ P,
+                                float margin, float margin_near, float margin_hb, double R2, double Rb2, double Rh2) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= s.n) return;
+  const int i = warp;
+  const int r = s.rep[i];
+  const float Lh0 = s.boxh[3 * r], Lh1 = s.boxh[3 * r + 1], Lh2 = s.boxh[3 * r + 2];
+  const float Ll0 = s.boxl[3 * r], Ll1 = s.boxl[3 * r + 1], Ll2 = s.boxl[3 * r + 2];
+  const float R2f = (float)R2, Rb2f = (float)Rb2, Rh2f = (float)Rh2;
+  const float4 hi = s.ph[i], li = s.pl[i];
+  int ii0, ii1, ii2;
+  rec_img(li.w, ii0, ii1, ii2);
+  const int ti = s.type[i];
+  unsigned acc = 0;                                     // acceptor types, when i is an H-bond H
+  if (P->hb[ti] == 1)
+    for (int t = 0; t < MAXT; ++t) acc |= (P->hb[t] == 2 ? 1u : 0u) << t;
+  const float rnb = P->r_nb, ke = P->k_e;
+  const float* gam = P->gamma_m3 + ti * MAXT;
+  const int nc = cl.cnt[i], crow = i * cl.cap;
+  const int hrow = i * hl.cap;
+  int cntn = 0, cntf = 0, cnth = 0;
+  const int rown = i * f.capn, rowf = i * f.cap;
+  float* Hn = (float*)f.Hn;
+  float* Hf = (float*)f.H;
+  for (int base = 0; base < nc; base += 32) {
+    const int k = base + lane;
+    bool ok = false, near = false, ish = false;
+    int j = -1, code = 13, tj = 0;
+    float r2f = 0.f;
+    if (k < nc) {
+      j = cl.j[crow + k];
+      const int c0 = cl.s[crow + k];
+      const float4 hj = s.ph[j], lj = s.pl[j];
+      int jx, jy, jz;
+      rec_img(lj.w, jx, jy, jz);                        // crossing counters ride in the record
+      const int sx = c0 / 9 - 1 + jx - ii0, sy = (c0 / 3) % 3 - 1 + jy - ii1, sz = c0 % 3 - 1 + jz - ii2;
+      if (sx >= -1 && sx <= 1 && sy >= -1 && sy <= 1 && sz >= -1 && sz <= 1) {
+        code = (sx + 1) * 9 + (sy + 1) * 3 + (sz + 1);
+        tj = rec_type(lj.w);
+        const float dx = pv_comp(hj.x, hi.x, lj.x, li.x, sx, Lh0, Ll0);
+        const float dy = pv_comp(hj.y, hi.y, lj.y, li.y, sy, Lh1, Ll1);
+        const float dz = pv_comp(hj.z, hi.z, lj.z, li.z, sz, Lh2, Ll2);
+        r2f = dx * dx + dy * dy + dz * dz;
+        ok = !(j == i && code == 13) && in_range(s, i, j, code, r, r2f, R2f, margin, R2);
+        if (ok) near = in_range(s, i, j, code, r, r2f, Rb2f, margin_near, Rb2);
+        // H-bond partner: an acceptor with r < r_hb (every near pair of one is, r_bond <= r_hb)
+        if (ok && ((acc >> tj) & 1u)) ish = near || in_range(s, i, j, code, r, r2f, Rh2f, margin_hb, Rh2);
+      }
+    }
+    const unsigned mn = __ballot_sync(0xffffffffu, ok && near);
+    const unsigned mf = __ballot_sync(0xffffffffu, ok && !near);
+    const unsigned mh = __ballot_sync(0xffffffffu, ish);
+    const unsigned below = (1u << lane) - 1u;
+    if (ish) {
+      const int hp = cnth + __popc(mh & below);
+      if (hp < hl.cap) {
+        hl.j[hrow + hp] = j;
+        hl.s[hrow + hp] = (uint8_t)code;
+      }
+    }
+    cnth += __popc(mh);
+    if (ok) {
+      const float rr = sqrtf(r2f);
+      float tap, dtap;
+      taper<float>(rr, rnb, tap, dtap);
+      const float h = tap * ke * rcbrt_f(rr * rr * rr + gam[tj]);
+      const int pos = near ? cntn + __popc(mn & below) : cntf + __popc(mf & below);
+      if (pos < (near ? f.capn : f.cap)) {
+        const int e = (near ? rown : rowf) + pos;
+        (near ? f.jn : f.j)[e] = j;
+        (near ? f.sn : f.s)[e] = (uint8_t)code;
+        (near ? Hn : Hf)[e] = h;
+      }
+    }
+    cntn += __popc(mn);
+    cntf += __popc(mf);
+  }
+  if (lane == 0) {
+    f.cntn[i] = cntn < f.capn ? cntn : f.capn;
+    f.cnt[i] = cntf < f.cap ? cntf : f.cap;
+    hl.cnt[i] = cnth < hl.cap ? cnth : hl.cap;
+    if (cntn > f.capn) atomicOr(s.err, ERR_CAP_NEAR);
+    if (cntf > f.cap) atomicOr(s.err, ERR_CAP_FAR);
+    if (cnth > hl.cap) atomicOr(s.err, ERR_CAP_HB);
+  }
+}
+
 }  // namespace
 
 namespace rx {
@@ -694,8 +797,12 @@ template <typename R>
 void cand_filter(const Launch& L, Sys s, CandList cl, FarList f, HbList h, const DParams<R>* P, float margin,
                  float margin_near, float margin_hb) {
   const int bs = L.t().cf_block;
-  k_cand_filter<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, cl, f, h, P, margin, margin_near, margin_hb,
-                                                                         f.r2_nb, f.r2_bond, f.r2_hb);
+  if constexpr (sizeof(R) == 4)
+    k_cand_filter_f<<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, cl, f, h, P, margin, margin_near,
+                                                                        margin_hb, f.r2_nb, f.r2_bond, f.r2_hb);
+  else
+    k_cand_filter<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, cl, f, h, P, margin, margin_near,
+                                                                           margin_hb, f.r2_nb, f.r2_bond, f.r2_hb);
   k_rebuild_done<<<1, 32, 0, L.st>>>(s);
   *L.count += 2;
 }
