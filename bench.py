@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--dt", type=float, default=0.1)
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 compare, e2e and cpu baseline")
+    ap.add_argument("--tune-cache", default=None, help="launch-schedule cache file (read, else tuned and appended)")
+    ap.add_argument("--qeq-precond", default="jacobi", choices=["jacobi", "block32"],
+                    help="QEq preconditioner of the timed run (jacobi: the paper's)")
     return ap.parse_args()
 
 
@@ -186,9 +189,11 @@ def run_ours(a, rank, world):
     w = synth.workload(a.workload, seed=rank)
     n = len(w["x"])
     prec = rx.MIXED if a.precision == "mixed" else rx.FP64
-    ctx = rx.ReaxFF(P, w["types"], w["box"], w["options"], precision=prec, warm_start=rx.WARM_EXTRAP)
+    pc = rx.PRECOND_BLOCK32 if a.qeq_precond == "block32" else rx.PRECOND_JACOBI
+    ctx = rx.ReaxFF(P, w["types"], w["box"], w["options"], precision=prec, warm_start=rx.WARM_EXTRAP,
+                    qeq_precond=pc)
     ctx.set_state(w["x"], w["v"])
-    schedule = ctx.autotune()                               # launch schedules (untimed setup)
+    schedule = ctx.autotune(a.tune_cache)                   # launch schedules (untimed setup)
     stream = torch.cuda.current_stream(dev)
     etot = torch.zeros(max(a.steps, 1), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -236,7 +241,8 @@ def run_ours(a, rank, world):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if prec == rx.MIXED else "f64", "data": "synthetic",
         "config": {"workload": a.workload, "atoms": n, "atoms_per_gpu": n, "precision": a.precision,
-                   "warm_start": "extrapolated", "qeq_tol": w["options"]["qeq_tol"], "dt_fs": a.dt,
+                   "warm_start": "extrapolated", "qeq_tol": w["options"]["qeq_tol"], "qeq_precond": a.qeq_precond,
+                   "dt_fs": a.dt,
                    "lists": "Verlet-skin candidates (1 A skin, rebuilt on displacement > skin/2), exact cutoff filter every step",
                    "l2": "flushed (256 MB write) before each library call of %d steps; each step streams > 200 MB of lists" % CALL_STEPS,
                    "parallelism": "independent system per GPU" if world > 1 else "single GPU",
@@ -360,6 +366,54 @@ def learned_warm_start(P, a):
     out["training"] = {"md_steps": train_steps, "snapshots": train_steps // every, "epochs": epochs, "lr": lr,
                        "final_mse_e2": loss, "md_s": round(t_md, 2), "train_s": round(t_train, 2)}
     out["held_out"] = {"workload": a.workload, "seed": 11, "steps": held}
+    return out
+
+
+def solver_variants(P, a, steps=50):
+    """QEq preconditioners on the benchmark crystal at the same tolerance: Jacobi (the
+    paper's M = diag(H)) and block Jacobi over 32 consecutive atoms. Per variant: cold-start
+    iterations (no solution history), then over `steps` MD steps with the extrapolated
+    start: SpMVs per step (each one read of H for both systems), the bytes the solve moves
+    per step (H entries 8 B per SpMV; for block Jacobi also 128 B per atom per
+    preconditioner application and for the per-solve inverse), the QEq stage time
+    (setup included) and the whole step (CUDA events)."""
+    import torch
+
+    import paper_1706_07772_gb300.reaxff as rx
+    import synth
+    w = synth.workload(a.workload)
+    st = torch.cuda.current_stream()
+    et = torch.zeros(steps, dtype=torch.float64, device="cuda")
+    out, qs = {}, {}
+    for name, pc in (("jacobi", rx.PRECOND_JACOBI), ("block32", rx.PRECOND_BLOCK32)):
+        c = rx.ReaxFF(P, w["types"], w["box"], w["options"], precision=rx.MIXED, qeq_precond=pc)
+        c.set_state(w["x"], w["v"])
+        q0, its, itt, _ = c.qeq()
+        qs[name] = q0
+        rec = {"cold_start_iters": [int(its[0]), int(itt[0])]}
+        c.step_dev(5, a.dt, et.data_ptr(), st.cuda_stream)
+        nfar = c.get_lists(rx.LIST_FAR)[0].size
+        sp0 = c.qeq_spmv_total()
+        c.profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        c.step_dev(steps, a.dt, et.data_ptr(), st.cuda_stream)
+        e1.record(st)
+        e1.synchronize()
+        prof = c.profile_read()
+        c.profile_enable(False)
+        spmv = (c.qeq_spmv_total() - sp0) / steps
+        byts = spmv * nfar * 8 + (spmv * c.n * 128 + c.n * 128 if pc == rx.PRECOND_BLOCK32 else 0)
+        its, itt = c.last_qeq_iters()
+        rec.update({"spmv_per_step": spmv, "cg_bytes_per_step": byts, "iters_last": [int(its[0]), int(itt[0])],
+                    "qeq_ms_per_step": (prof["qeq"][0] + prof.get("qeq_precond", (0.0, 0))[0]) / steps,
+                    "precond_setup_ms_per_step": prof.get("qeq_precond", (0.0, 0))[0] / steps,
+                    "ms_per_step": e0.elapsed_time(e1) / steps,
+                    "atom_steps_per_s": c.n / (e0.elapsed_time(e1) / steps * 1e-3)})
+        out[name] = rec
+        c.close()
+    out["dq_max_cold_start"] = float(np.abs(qs["block32"] - qs["jacobi"]).max())
+    out["steps"] = steps
     return out
 
 
@@ -516,6 +570,8 @@ def main():
                           "overhead_at_one_analysis_per_1000_steps": 1e3 * t_sp / (1000 * out["ms_per_step"])}
         # 64 uneven replicas in one context vs one at a time
         out["batched"] = batched(P, a)
+        # QEq solver variants: Jacobi vs block-Jacobi preconditioning
+        out["solver_variants"] = solver_variants(P, a)
         # learned QEq warm start (trained here on the method's own charges)
         out["learned_warm_start"] = learned_warm_start(P, a)
         # CPU baseline (oracle) and force error of both GPU paths at the same state

@@ -57,6 +57,13 @@ enum {
 
 enum { REAXFF_FP64 = 0, REAXFF_MIXED = 1 };                  /* options.precision */
 enum { REAXFF_WARM_EXTRAP = 0, REAXFF_WARM_ZERO = 1, REAXFF_WARM_MLP = 2 };
+/* options.qeq_precond: the CG preconditioner M of both QEq systems. JACOBI is the paper's
+ * M = diag(H) (Sec. 3.3). BLOCK32 is block Jacobi over blocks of 32 consecutive atoms of a
+ * replica (the last block of a replica may be shorter): M = blockdiag(H_BB), with each
+ * block H_BB the exact restriction of H to the block (all images), inverted in FP32 once
+ * per solve. Both run CG to the same tolerance; BLOCK32 needs fewer iterations when
+ * strongly coupled atoms (molecules) are numbered consecutively. */
+enum { REAXFF_PRECOND_JACOBI = 0, REAXFF_PRECOND_BLOCK32 = 1 };
 enum { REAXFF_LIST_FAR = 0, REAXFF_LIST_BOND = 1, REAXFF_LIST_HBOND = 2 };
 
 /* Force-field parameters (tables indexed by atom type). Per-pair tables are
@@ -100,7 +107,7 @@ typedef struct {
 typedef struct {
   double r_nb;        /* nonbonded / QEq cutoff (A), 10 in the paper's setup (Sec. 4.2) */
   double r_bond;      /* bond-candidate cutoff (A) */
-  double r_hb;        /* hydrogen-bond partner cutoff (A) */
+  double r_hb;        /* hydrogen-bond partner cutoff (A); r_bond <= r_hb <= r_nb */
   double bo_cut;      /* bond kept when BO'sig+BO'pi+BO'pp >= bo_cut */
   double thb_cut;     /* valence-angle / torsion bond-order threshold */
   double thb_cutsq;   /* valence-angle product threshold */
@@ -116,6 +123,7 @@ typedef struct {
                          filtered exactly (r < r_nb) every step. 0 = default 1.0 A,
                          negative = no candidate list (cell stencil every step). A system
                          with a box edge <= r_nb + skin runs the cell stencil instead. */
+  int32_t qeq_precond; /* REAXFF_PRECOND_* (0 = Jacobi) */
 } reaxff_options;
 
 typedef struct reaxff_ctx reaxff_ctx;
@@ -222,7 +230,7 @@ int64_t reaxff_qeq_spmv_total(reaxff_ctx* ctx);
 /* Per-stage timing with CUDA events recorded on the context's stream around every
  * kernel group (cells, far_list, bond_list, bo_prime64, qeq, bo_correct, atom_terms,
  * over_under_bond, s_gather, angles, torsions, hbonds, nonbonded, chain_rule, verlet,
- * reduce, mlp_guess). enable(1) also zeroes the totals. read() fills ms[] (accumulated
+ * reduce, mlp_guess, qeq_precond). enable(1) also zeroes the totals. read() fills ms[] (accumulated
  * milliseconds) and calls[] (timed launches) for up to nstage stages and returns the
  * number of stages; stage_name() gives each stage's name. */
 void reaxff_profile_enable(reaxff_ctx* ctx, int32_t on);

@@ -9,7 +9,8 @@ terms, 3-body/4-body enumeration and QEq of Sec. 3.3):
   * uncorrected and corrected bond orders, atom over/under-coordination quantities
   * the 13 energy terms: bond, lp, over, under, val, pen, coa, tors, conj, hbond,
     vdW, coul, pol
-  * QEq: two Jacobi-preconditioned CG solves on the tapered H matrix, q = s - mu t
+  * QEq: two Jacobi-preconditioned CG solves on the tapered H matrix, q = s - mu t; a
+    block-Jacobi preconditioned variant (blocks of 32 consecutive atoms) with the same result
   * forces F = -dE/dx at fixed charges and the virial -dE/d(strain), both by reverse-mode
     differentiation of the energy as written (plain definition of a force)
   * velocity Verlet
@@ -291,8 +292,10 @@ class Model:
         Hm = Hm + sp.diags(P["eta"][self.types])
         return Hm.tocsr()
 
-    def qeq(self, x, L, tol=None, max_iter=1000, guess=None):
-        """QEq charges via two Jacobi-PCG solves: H s = -chi, H t = -1; q = s - (sum s / sum t) t.
+    def qeq(self, x, L, tol=None, max_iter=1000, guess=None, precond="jacobi"):
+        """QEq charges via two PCG solves: H s = -chi, H t = -1; q = s - (sum s / sum t) t.
+        precond "jacobi": M = diag(H), the paper's choice (Sec. 3.3); "block32": block
+        Jacobi over 32 consecutive atoms (pcg_block), a solver variant with the same result.
 
         Convergence per system: ||b - H x||_2 / ||b||_2 <= tol (residual updated recursively
         inside CG). Returns dict(q, s, t, iters_s, iters_t)."""
@@ -301,8 +304,13 @@ class Model:
         chi = self.P["chi"][self.types]
         eta = self.P["eta"][self.types]
         s0, t0 = (None, None) if guess is None else guess
-        s, its = pcg(Hm, -chi, eta, tol, max_iter, s0)
-        t, itt = pcg(Hm, -np.ones(self.n), eta, tol, max_iter, t0)
+        if precond == "block32":
+            blocks = blocks_of([0, self.n])
+            s, its = pcg_block(Hm, -chi, blocks, tol, max_iter, s0)
+            t, itt = pcg_block(Hm, -np.ones(self.n), blocks, tol, max_iter, t0)
+        else:
+            s, its = pcg(Hm, -chi, eta, tol, max_iter, s0)
+            t, itt = pcg(Hm, -np.ones(self.n), eta, tol, max_iter, t0)
         mu = s.sum() / t.sum()
         return dict(q=s - mu * t, s=s, t=t, iters_s=its, iters_t=itt, mu=mu)
 
@@ -630,6 +638,52 @@ def pcg(Hm, b, diag, tol, max_iter, x0=None):
         if np.linalg.norm(r) <= tol * bn:
             return x, it
         z = r / diag
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, max_iter
+
+
+def blocks_of(rep_offsets, size=32):
+    """Blocks of `size` consecutive atoms of each replica (the last block of a replica may be
+    shorter): list of (start, stop)."""
+    out = []
+    for r in range(len(rep_offsets) - 1):
+        for a in range(rep_offsets[r], rep_offsets[r + 1], size):
+            out.append((a, min(a + size, rep_offsets[r + 1])))
+    return out
+
+
+def pcg_block(Hm, b, blocks, tol, max_iter, x0=None):
+    """Block-Jacobi preconditioned CG for H x = b: M = blockdiag(H_BB) over the given
+    blocks (each H_BB the restriction of H to the block, every entry of H kept), applied as
+    z = H_BB^-1 r per block (dense FP64 inverse). Same stopping rule as pcg(): the
+    iteration ends when ||r||_2 / ||b||_2 <= tol. Returns (x, iterations)."""
+    Hd = Hm.tocsr()
+    inv = [(a, e, np.linalg.inv(Hd[a:e, a:e].toarray())) for a, e in blocks]
+
+    def apply(r):
+        z = np.empty_like(r)
+        for a, e, Bi in inv:
+            z[a:e] = Bi @ r[a:e]
+        return z
+
+    x = np.zeros_like(b) if x0 is None else np.array(x0, float)
+    r = b - Hm @ x
+    bn = np.linalg.norm(b)
+    if np.linalg.norm(r) <= tol * bn:
+        return x, 0
+    z = apply(r)
+    p = z.copy()
+    rz = r @ z
+    for it in range(1, max_iter + 1):
+        w = Hm @ p
+        alpha = rz / (p @ w)
+        x = x + alpha * p
+        r = r - alpha * w
+        if np.linalg.norm(r) <= tol * bn:
+            return x, it
+        z = apply(r)
         rz_new = r @ z
         p = z + (rz_new / rz) * p
         rz = rz_new

@@ -289,8 +289,9 @@ rx::Launch launch_of(reaxff_ctx* ctx) { return rx::Launch{ctx->st, &ctx->launche
 
 const char* const STAGE_NAMES[] = {"cells", "far_list", "bond_list", "bo_prime64", "qeq", "bo_correct",
                                    "atom_terms", "over_under_bond", "s_gather", "angles", "torsions",
-                                   "hbonds", "nonbonded", "chain_rule", "verlet", "reduce", "mlp_guess"};
-constexpr int NSTAGES = 17;
+                                   "hbonds", "nonbonded", "chain_rule", "verlet", "reduce", "mlp_guess",
+                                   "qeq_precond"};
+constexpr int NSTAGES = 18;
 
 // scoped event pair around one stage (only when profiling is on)
 struct Stage {
@@ -419,6 +420,10 @@ int qeq_impl(reaxff_ctx* ctx) {
     rx::mlp_infer(L, M.D, M.tiles, M.mean, M.inv, M.inf, M.y, ctx->sys.err, ctx->nsm);
     qhat = M.y;
   }
+  if (ctx->Q.precond != REAXFF_PRECOND_JACOBI) {
+    Stage stp(ctx, 17);
+    rx::qeq_precond_build(L, ctx->sys, ctx->Q);
+  }
   Stage stg(ctx, 4);
   int rc = ctx->fp64 ? rx::qeq_solve<double>(L, ctx->sys, ctx->far, ctx->Q, ctx->Pd, ctx->chi_t, ctx->eta_t,
                                              ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start, qhat)
@@ -499,13 +504,16 @@ int check_flags(reaxff_ctx* ctx, bool allow_nc) {
 int validate(const reaxff_params* p, const reaxff_options* o, std::string& msg) {
   if (!p || !o) { msg = "null params/options"; return REAXFF_E_INVALID; }
   if (p->ntypes < 1 || p->ntypes > MAXT) { msg = "ntypes out of range"; return REAXFF_E_INVALID; }
-  if (!(o->r_nb > 0 && o->r_bond > 0 && o->r_hb > 0 && o->r_bond <= o->r_nb && o->r_hb <= o->r_nb)) {
-    msg = "cutoffs must satisfy 0 < r_bond, r_hb <= r_nb"; return REAXFF_E_INVALID;
+  if (!(o->r_nb > 0 && o->r_bond > 0 && o->r_bond <= o->r_hb && o->r_hb <= o->r_nb)) {
+    msg = "cutoffs must satisfy 0 < r_bond <= r_hb <= r_nb"; return REAXFF_E_INVALID;
   }
   if (!(o->bo_cut > 0 && o->qeq_tol > 0 && o->qeq_max_iter > 0)) { msg = "bo_cut, qeq_tol, qeq_max_iter must be > 0"; return REAXFF_E_INVALID; }
   if (o->precision != REAXFF_FP64 && o->precision != REAXFF_MIXED) { msg = "unknown precision"; return REAXFF_E_INVALID; }
   if (o->warm_start < 0 || o->warm_start > REAXFF_WARM_MLP) { msg = "unknown warm_start"; return REAXFF_E_INVALID; }
   if (!std::isfinite(o->skin) || o->skin > 5.0) { msg = "skin must be finite and <= 5 A"; return REAXFF_E_INVALID; }
+  if (o->qeq_precond != REAXFF_PRECOND_JACOBI && o->qeq_precond != REAXFF_PRECOND_BLOCK32) {
+    msg = "unknown qeq_precond"; return REAXFF_E_INVALID;
+  }
   for (int a = 0; a < p->ntypes; ++a)
     if (!(p->mass[a] > 0 && p->eta[a] > 0)) { msg = "mass and eta must be > 0"; return REAXFF_E_INVALID; }
   return REAXFF_OK;
@@ -683,7 +691,10 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   Q.zg = B.alloc<double>(2 * (size_t)n);
   Q.hist_s = B.alloc<double>(7 * (size_t)n);      // s ring (4 slots) then t ring (3 slots)
   Q.hist_t = Q.hist_s + 4 * (size_t)n;
-  const int rows = std::max(8, (int)((n + Q.grid - 1) / Q.grid));
+  Q.precond = options->qeq_precond;
+  Q.Pf = ctx->Pf;
+  int rows = std::max(8, (int)((n + Q.grid - 1) / Q.grid));
+  if (Q.precond == REAXFF_PRECOND_BLOCK32) rows = round_up(rows, 32);   // chunks start on block boundaries
   std::vector<int> clo, crep, rchunk(nrep + 1, 0);
   for (int r = 0; r < nrep; ++r) {
     rchunk[r] = (int)crep.size();
@@ -698,6 +709,18 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   int* clo_d = B.alloc<int>(clo.size());
   int* crep_d = B.alloc<int>(crep.size());
   int* rchunk_d = B.alloc<int>(nrep + 1);
+  // block-Jacobi blocks: 32 consecutive atoms of a replica (fewer at its end)
+  std::vector<int> bjs, bjn;
+  if (Q.precond == REAXFF_PRECOND_BLOCK32)
+    for (int r = 0; r < nrep; ++r)
+      for (int64_t i = rep_offsets[r]; i < rep_offsets[r + 1]; i += 32) {
+        bjs.push_back((int)i);
+        bjn.push_back((int)std::min<int64_t>(32, rep_offsets[r + 1] - i));
+      }
+  Q.bj_nblk = (int)bjs.size();
+  Q.bj_start = Q.bj_nblk ? B.alloc<int>(Q.bj_nblk) : nullptr;
+  Q.bj_size = Q.bj_nblk ? B.alloc<int>(Q.bj_nblk) : nullptr;
+  Q.binv = Q.bj_nblk ? B.alloc<float>(32 * ((size_t)n + 32)) : nullptr;
   Q.chunk_lo = clo_d; Q.chunk_rep = crep_d; Q.rep_chunk = rchunk_d;
   Q.part = B.alloc<double>((size_t)Q.nchunk * 2 * 8);
   {
@@ -711,7 +734,10 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
     const size_t avail = (size_t)rx::QEQ_SMEM_MAX - Q.ring_bytes;
     Q.scal_smem = sc <= avail / 2;
     Q.state_smem = (Q.scal_smem ? sc : 0) + st <= avail;
-    Q.smem_bytes = (int)(Q.ring_bytes + (Q.scal_smem ? sc : 0) + (Q.state_smem ? st : 0));
+    const size_t bjb = Q.precond == REAXFF_PRECOND_BLOCK32 ? (size_t)Q.rows_blk * 32 * sizeof(float) : 0;
+    const size_t used = (Q.scal_smem ? sc : 0) + (Q.state_smem ? st : 0);
+    Q.bj_smem = bjb > 0 && used + bjb <= avail;
+    Q.smem_bytes = (int)(Q.ring_bytes + used + (Q.bj_smem ? bjb : 0));
     Q.scal = Q.scal_smem ? nullptr : B.alloc<double>((size_t)Q.grid * (nrep * rx::QEQ_SCAL_PER_REP + 4));
     Q.state = Q.state_smem ? nullptr : B.alloc<double>((size_t)Q.grid * rx::QEQ_NV_STATE * Q.rows_blk);
   }
@@ -784,6 +810,10 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   UP(clo_d, clo.data(), clo.size() * sizeof(int));
   UP(crep_d, crep.data(), crep.size() * sizeof(int));
   UP(rchunk_d, rchunk.data(), (nrep + 1) * sizeof(int));
+  if (Q.bj_nblk) {
+    UP(Q.bj_start, bjs.data(), bjs.size() * sizeof(int));
+    UP(Q.bj_size, bjn.data(), bjn.size() * sizeof(int));
+  }
   UP(rlo_d, rlo.data(), rlo.size() * sizeof(int));
   UP(rrep_d, rrep.data(), (nrep + 1) * sizeof(int));
   UP(ctx->chi_t, chi, sizeof(chi));

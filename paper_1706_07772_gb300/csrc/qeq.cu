@@ -53,6 +53,7 @@ struct CG {
   const R* Hn;
   int capn;
   const double *eta, *chi, *ieta;          // per type (double); ieta = 1/eta
+  const float* binv;                       // block-Jacobi inverses (null: Jacobi, z = r / eta)
   // solution history rings (s: 4 slots, t: 3) and their device state hst = {slot of the
   // newest s, slot of the newest t, usable entries}; read by every block at the start,
   // advanced by block 0 at the end (the new solutions go to the oldest slots)
@@ -71,6 +72,7 @@ struct CG {
   int rows_blk;                            // most rows any block owns
   int scal_smem, state_smem;               // 1: kept in dynamic shared memory
   int ring_bytes;                          // SpMV ring at the start of dynamic shared memory
+  int bj_smem;                             // 1: block inverses staged in shared memory after the state
   const int* chunk_lo;                     // [nchunk+1] rows
   const int* chunk_rep;                    // [nchunk]
   const int* rep_chunk;                    // [nrep+1] chunk ranges per replica
@@ -400,6 +402,7 @@ __device__ __forceinline__ void spmv_ring_f(const CG<float>& a, unsigned char* r
 // the chunk partials.
 struct Blk {
   unsigned char* ring;         // SpMV streaming ring (mixed path)
+  float* bjs;                  // this block's block-Jacobi inverses in shared memory (or null)
   double* S;                   // [nrep*NS + 4] scalars, then [nrep*NQ] reduced totals
   double* red;
   double* st;                  // [NV_STATE][rows] row state (structure of arrays)
@@ -407,6 +410,13 @@ struct Blk {
   __device__ __forceinline__ double& v(int k, int li) const { return st[k * rows + li]; }
   template <typename R>
   __device__ __forceinline__ R* u(int sys) const { return (R*)(st + V_U * rows) + sys * rows; }
+  // element (0, 0) of the inverse of the block holding row i (local row li), from shared
+  // memory when staged there, else from global memory
+  template <typename A>
+  __device__ __forceinline__ const float* bj_of(const A& a, int i, int li) const {
+    const int t = threadIdx.x & 31;
+    return bjs ? bjs + 32 * (li - t) : a.binv + 32 * (size_t)(i - t);
+  }
 };
 
 // off-diagonal SpMV of the chunk's rows into this block's U arrays (path precision). Warp w
@@ -466,6 +476,33 @@ __device__ __forceinline__ void for_rows(int lo, int hi, F&& f) {
   for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) f(i);
 }
 
+// warp-uniform row map (same rows per thread as for_rows): f(i, valid) on all 32 lanes of a
+// warp, valid = i < hi, so warp shuffles inside f see every lane
+template <typename F>
+__device__ __forceinline__ void for_warp_rows(int lo, int hi, F&& f) {
+  const int lane = threadIdx.x & 31;
+  for (int base = lo + (int)threadIdx.x - lane; base < hi; base += blockDim.x) f(base + lane, base + lane < hi);
+}
+
+// block-Jacobi preconditioner: (zs, zt) = B^-1 (rs, rt) over the warp's block (chunks
+// start on block boundaries, so a warp's rows are one block: its valid lanes, a prefix of
+// nv). FP32: lane t sums B^-1[t][m] r_m over m < nv with r_m from lane m; Bc points at
+// element (0, 0) of the block's column-major inverse (element (t, m) at Bc[32 m + t])
+__device__ __forceinline__ void bj_apply(const float* Bc, int nv, double rs, double rt, double& zs, double& zt) {
+  const int lane = threadIdx.x & 31;
+  Bc += lane;
+  const float fs = (float)rs, ft = (float)rt;
+  float as = 0.f, at = 0.f;
+#pragma unroll 8
+  for (int m = 0; m < nv; ++m) {
+    const float b = Bc[32 * m];
+    as = fmaf(b, __shfl_sync(0xffffffffu, fs, m), as);
+    at = fmaf(b, __shfl_sync(0xffffffffu, ft, m), at);
+  }
+  zs = (double)as;
+  zt = (double)at;
+}
+
 template <typename R>
 __device__ __forceinline__ void put_zg(const CG<R>& a, int i, double s, double t) {
   using T = typename G2<R>::T;
@@ -499,6 +536,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
   B.red = B.S + a.nrep * NS + 4;
   B.rows = a.rows_blk;
   B.st = a.state_smem ? dsm + (a.scal_smem ? sc : 0) : a.state + (size_t)blockIdx.x * NV_STATE * a.rows_blk;
+  B.bjs = a.bj_smem ? (float*)(dsm + (a.scal_smem ? sc : 0) + (a.state_smem ? NV_STATE * a.rows_blk : 0)) : nullptr;
   for (int k = threadIdx.x; k < MAXC; k += blockDim.x) {
     const int c = blockIdx.x + k * gridDim.x;
     if (c < a.nchunk) {
@@ -507,6 +545,19 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
   }
   const bool lead = blockIdx.x == 0;
   unsigned bt = 0;                         // barriers passed x grid size
+  __syncthreads();
+  if (B.bjs) {
+    // stage this block's inverses: row i's entries (t, m), m < its block's size
+    for_chunks(a, C, [&](int, int lo, int hi, int, int off) {
+      for_rows(lo, hi, [&](int i) {
+        const int t = (i - lo) & 31, li = off + i - lo;
+        const int nv = min(32, hi - (i - t));
+        const float* g = a.binv + 32 * (size_t)(i - t) + t;
+        float* d = B.bjs + 32 * (li - t) + t;
+        for (int m = 0; m < nv; ++m) d[32 * m] = __ldg(g + 32 * m);
+      });
+    });
+  }
   int pb = 0;
   double* S = B.S;
   double* red = B.red;
@@ -607,27 +658,45 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
     });
   }
   if (!grid_barrier(a.bar, a.err, bt)) return;
-  // r = b - H x, z = r/eta, p = w = 0
+  // r = b - H x, z = M^-1 r, p = w = 0
   for_chunks(a, C, [&](int c, int lo, int hi, int, int off) {
     spmv_chunk(a, B, lo, hi, off);
     __syncthreads();
     double v[6] = {0, 0, 0, 0, 0, 0};
     const R* us = B.u<R>(0);
     const R* ut = B.u<R>(1);
-    for_rows(lo, hi, [&](int i) {
-      const int li = off + i - lo;
-      const double e = B.v(V_ETA, li), ie = B.v(V_IETA, li);
+    auto resid = [&](int i, int li, double& rs, double& rt) {
+      const double e = B.v(V_ETA, li);
       const double hs = (double)us[li] + e * B.v(V_XS, li);
       const double ht = (double)ut[li] + e * B.v(V_XT, li);
       const double bs = -a.chi[a.type[i]], bt = -1.0;
-      const double rs = bs - hs, rt = bt - ht;
+      rs = bs - hs; rt = bt - ht;
       B.v(V_RS, li) = rs; B.v(V_RT, li) = rt;
-      B.v(V_ZS, li) = rs * ie; B.v(V_ZT, li) = rt * ie;
       B.v(V_PS, li) = 0; B.v(V_PT, li) = 0; B.v(V_WS, li) = 0; B.v(V_WT, li) = 0;
-      v[0] += rs * rs * ie; v[1] += rt * rt * ie;   // r.z
       v[2] += rs * rs; v[3] += rt * rt;             // r.r
       v[4] += bs * bs; v[5] += bt * bt;             // b.b
-    });
+    };
+    if (a.binv) {
+      for_warp_rows(lo, hi, [&](int i, bool valid) {
+        const int li = off + i - lo;
+        double rs = 0.0, rt = 0.0, zs, zt;
+        if (valid) resid(i, li, rs, rt);
+        bj_apply(B.bj_of(a, i, li), __popc(__ballot_sync(0xffffffffu, valid)), rs, rt, zs, zt);
+        if (valid) {
+          B.v(V_ZS, li) = zs; B.v(V_ZT, li) = zt;
+          v[0] += rs * zs; v[1] += rt * zt;         // r.z
+        }
+      });
+    } else {
+      for_rows(lo, hi, [&](int i) {
+        const int li = off + i - lo;
+        const double ie = B.v(V_IETA, li);
+        double rs, rt;
+        resid(i, li, rs, rt);
+        B.v(V_ZS, li) = rs * ie; B.v(V_ZT, li) = rt * ie;
+        v[0] += rs * rs * ie; v[1] += rt * rt * ie; // r.z
+      });
+    }
     block_sum<6>(a, v, hi - lo, pb, c);
   });
   if (!grid_barrier(a.bar, a.err, bt)) return;
@@ -699,26 +768,54 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
       const bool as = sr[S_ACT_S] > 0, at = sr[S_ACT_T] > 0;
       const double als = sr[S_AL_S], alt = sr[S_AL_T];
       double v[4] = {0, 0, 0, 0};
-      for_rows(lo, hi, [&](int i) {
-        const int li = off + i - lo;
-        const double ie = B.v(V_IETA, li);
-        double zs = B.v(V_ZS, li), zt = B.v(V_ZT, li);
-        if (as) {
-          B.v(V_XS, li) += als * B.v(V_PS, li);
-          const double r = B.v(V_RS, li) - als * B.v(V_WS, li);
-          zs = r * ie;
-          B.v(V_RS, li) = r; B.v(V_ZS, li) = zs;
-          v[0] += r * zs; v[2] += r * r;
-        }
-        if (at) {
-          B.v(V_XT, li) += alt * B.v(V_PT, li);
-          const double r = B.v(V_RT, li) - alt * B.v(V_WT, li);
-          zt = r * ie;
-          B.v(V_RT, li) = r; B.v(V_ZT, li) = zt;
-          v[1] += r * zt; v[3] += r * r;
-        }
-        put_zg(a, i, zs, zt);
-      });
+      if (a.binv) {
+        for_warp_rows(lo, hi, [&](int i, bool valid) {
+          const int li = off + i - lo;
+          double rs = 0.0, rt = 0.0;
+          if (valid) {
+            if (as) {
+              B.v(V_XS, li) += als * B.v(V_PS, li);
+              rs = B.v(V_RS, li) - als * B.v(V_WS, li);
+              B.v(V_RS, li) = rs;
+              v[2] += rs * rs;
+            }
+            if (at) {
+              B.v(V_XT, li) += alt * B.v(V_PT, li);
+              rt = B.v(V_RT, li) - alt * B.v(V_WT, li);
+              B.v(V_RT, li) = rt;
+              v[3] += rt * rt;
+            }
+          }
+          double zs, zt;
+          bj_apply(B.bj_of(a, i, li), __popc(__ballot_sync(0xffffffffu, valid)), rs, rt, zs, zt);
+          if (valid) {
+            if (as) { B.v(V_ZS, li) = zs; v[0] += rs * zs; } else zs = B.v(V_ZS, li);
+            if (at) { B.v(V_ZT, li) = zt; v[1] += rt * zt; } else zt = B.v(V_ZT, li);
+            put_zg(a, i, zs, zt);
+          }
+        });
+      } else {
+        for_rows(lo, hi, [&](int i) {
+          const int li = off + i - lo;
+          const double ie = B.v(V_IETA, li);
+          double zs = B.v(V_ZS, li), zt = B.v(V_ZT, li);
+          if (as) {
+            B.v(V_XS, li) += als * B.v(V_PS, li);
+            const double r = B.v(V_RS, li) - als * B.v(V_WS, li);
+            zs = r * ie;
+            B.v(V_RS, li) = r; B.v(V_ZS, li) = zs;
+            v[0] += r * zs; v[2] += r * r;
+          }
+          if (at) {
+            B.v(V_XT, li) += alt * B.v(V_PT, li);
+            const double r = B.v(V_RT, li) - alt * B.v(V_WT, li);
+            zt = r * ie;
+            B.v(V_RT, li) = r; B.v(V_ZT, li) = zt;
+            v[1] += r * zt; v[3] += r * r;
+          }
+          put_zg(a, i, zs, zt);
+        });
+      }
       block_sum<4>(a, v, hi - lo, pb, c);
     });
     if (!grid_barrier(a.bar, a.err, bt)) return;
@@ -778,6 +875,115 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
   }
 }
 
+
+// Block-Jacobi setup: one warp per block of sz <= 32 consecutive atoms (b0..b0+sz-1) of one
+// replica. The block's H in shared memory: eta on the diagonal and, for a != b, the sum over
+// every image of atom b within r_nb of Tap(r) k_e (r^3 + gamma^-3)^(-1/3) (the image vector
+// from the float hi/lo positions, exact to ~1 ulp; an image decided the other way at r_nb
+// carries a vanishing taper), each unordered pair evaluated once; rows and columns past sz
+// the identity's. The block is a principal submatrix of H, so symmetric positive definite:
+// Gauss-Jordan without pivoting inverts it in registers (row a in lane a, the pivot row by
+// shuffles), and the inverse, symmetrised, is stored column by column.
+constexpr int BJ_WARPS = 4;
+
+__global__ void __launch_bounds__(BJ_WARPS * 32) k_bj_build(Sys s, const DParams<float>* __restrict__ P,
+                                                            const int* __restrict__ bstart,
+                                                            const int* __restrict__ bsize, int nblk,
+                                                            float* __restrict__ binv) {
+  __shared__ float T[BJ_WARPS][32][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int blk = blockIdx.x * BJ_WARPS + w;
+  if (blk >= nblk) return;                              // whole warps
+  const int b0 = bstart[blk], sz = bsize[blk];
+  float* Trow = T[w][lane];
+  for (int b = 0; b < 32; ++b) Trow[b] = b == lane ? 1.0f : 0.0f;
+  if (lane < sz) Trow[lane] = P->eta[s.type[b0 + lane]];
+  __syncwarp();
+  // each unordered pair {a, b} once: lane a takes b = a + d (mod 32), d = 1..15, and lanes
+  // below 16 also d = 16 (15 or 16 pairs a lane); the value goes to both (a, b) and (b, a)
+  {
+    const int a = lane;
+    const float rnb = P->r_nb, rnb2 = rnb * rnb, ke = P->k_e;
+    const int ia = b0 + a;
+    const int rp = s.rep[b0];
+    const float Lh[3] = {s.boxh[3 * rp], s.boxh[3 * rp + 1], s.boxh[3 * rp + 2]};
+    const float Ll[3] = {s.boxl[3 * rp], s.boxl[3 * rp + 1], s.boxl[3 * rp + 2]};
+    float ah[3] = {0.f, 0.f, 0.f}, al[3] = {0.f, 0.f, 0.f};
+    int ta = 0;
+    if (a < sz) {
+      ah[0] = s.xh[ia]; ah[1] = s.yh[ia]; ah[2] = s.zh[ia];
+      al[0] = s.xl[ia]; al[1] = s.yl[ia]; al[2] = s.zl[ia];
+      ta = s.type[ia];
+    }
+    const int dmax = a < 16 ? 16 : 15;
+#pragma unroll 1
+    for (int d = 1; d <= dmax; ++d) {
+      const int b = (a + d) & 31;
+      if (a >= sz || b >= sz) continue;
+      const int ib = b0 + b;
+      const float bh[3] = {s.xh[ib], s.yh[ib], s.zh[ib]}, bl[3] = {s.xl[ib], s.yl[ib], s.zl[ib]};
+      const float g = P->gamma_m3[ta * MAXT + s.type[ib]];
+      // per dimension the image shifts within r_nb: at most two, the box exceeding r_nb
+      float d0[3], d1[3];
+      int nv[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        nv[c] = 0;
+        d0[c] = d1[c] = 0.f;
+#pragma unroll
+        for (int sh = -1; sh <= 1; ++sh) {
+          const float v = pv_comp(bh[c], ah[c], bl[c], al[c], sh, Lh[c], Ll[c]);
+          if (fabsf(v) < rnb) {
+            if (nv[c] == 0) d0[c] = v; else d1[c] = v;
+            ++nv[c];
+          }
+        }
+      }
+      float h = 0.f;
+#pragma unroll 1
+      for (int x = 0; x < nv[0]; ++x)
+#pragma unroll 1
+        for (int y = 0; y < nv[1]; ++y)
+#pragma unroll 1
+          for (int z = 0; z < nv[2]; ++z) {
+            const float dx = x ? d1[0] : d0[0], dy = y ? d1[1] : d0[1], dz = z ? d1[2] : d0[2];
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < rnb2) {
+              const float rr = sqrtf(r2);
+              float tap, dtap;
+              taper<float>(rr, rnb, tap, dtap);
+              h += tap * ke * rcbrtf(rr * rr * rr + g);
+            }
+          }
+      T[w][a][b] = h;
+      T[w][b][a] = h;
+    }
+  }
+  __syncwarp();
+  float R[32];
+#pragma unroll
+  for (int b = 0; b < 32; ++b) R[b] = Trow[b];
+  __syncwarp();
+  // Gauss-Jordan: after step k, column k holds the inverse's column k
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const float ip = 1.0f / __shfl_sync(0xffffffffu, R[k], k);
+    const float f = R[k] * ip;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float rkj = __shfl_sync(0xffffffffu, R[j], k);
+      if (lane == k) R[j] = j == k ? ip : rkj * ip;
+      else R[j] = j == k ? -f : fmaf(-f, rkj, R[j]);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 32; ++m) T[w][lane][m] = R[m];
+  __syncwarp();
+  // columns m < sz only: a shorter block ends where the next replica's first block begins
+  float* out = binv + 32 * (size_t)b0 + lane;
+  for (int m = 0; m < sz; ++m) out[32 * m] = 0.5f * (T[w][lane][m] + T[w][m][lane]);
+}
+
 }  // namespace
 
 namespace rx {
@@ -793,6 +999,8 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   a.cnt = f.cnt; a.col = f.j; a.H = (const R*)f.H; a.cap = f.cap;
   a.cntn = f.cntn; a.coln = f.jn; a.Hn = (const R*)f.Hn; a.capn = f.capn;
   a.eta = eta; a.chi = chi;
+  a.binv = Q.precond == REAXFF_PRECOND_BLOCK32 ? Q.binv : nullptr;
+  a.bj_smem = a.binv ? Q.bj_smem : 0;
   a.hist_s = Q.hist_s; a.hist_t = Q.hist_t; a.hst = Q.hst;
   a.warm = (warm == REAXFF_WARM_EXTRAP || warm == REAXFF_WARM_MLP) ? 1 : 0;
   a.qhat = qhat;
@@ -812,6 +1020,13 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
 }
 
 int qeq_ring_bytes(bool fp64) { return fp64 ? 0 : SP_RING_BYTES; }
+
+void qeq_precond_build(const Launch& L, Sys s, QeqState& Q) {
+  if (Q.precond != REAXFF_PRECOND_BLOCK32 || Q.bj_nblk == 0) return;
+  k_bj_build<<<(Q.bj_nblk + BJ_WARPS - 1) / BJ_WARPS, BJ_WARPS * 32, 0, L.st>>>(s, Q.Pf, Q.bj_start, Q.bj_size,
+                                                                               Q.bj_nblk, Q.binv);
+  *L.count += 1;
+}
 
 int qeq_grid_size(int nsm) {
   cudaFuncSetAttribute((const void*)k_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, QEQ_SMEM_MAX);

@@ -580,6 +580,16 @@ struct QeqState {
   int* mlp_used;               // [nrep] learned guess kept in the last solve
   GridBar* bar;
   int grid;                    // cooperative grid size
+  // block-Jacobi preconditioner (REAXFF_PRECOND_BLOCK32): blocks of 32 consecutive atoms of a
+  // replica; element (t, m) of the symmetrised FP32 inverse of the block starting at atom b0
+  // at binv[32 (b0 + m) + t] (32 (n + 32) floats); null for Jacobi
+  int precond;
+  float* binv;
+  int* bj_start;               // [bj_nblk] first atom of each block
+  int* bj_size;                // [bj_nblk] atoms in the block (32, fewer at a replica's end)
+  int bj_nblk;
+  int bj_smem;                 // 1: each block's inverses staged in its shared memory
+  const DParams<float>* Pf;    // FP32 parameters for the block build
 };
 // qhat (device, or null): learned charges offered as a second starting guess for s
 template <typename R>
@@ -587,6 +597,7 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
               const double* eta, double tol, int max_iter, int warm, const float* qhat);
 int qeq_grid_size(int nsm);
 int qeq_ring_bytes(bool fp64);   // shared memory of the SpMV streaming ring of a 1024-thread block
+void qeq_precond_build(const Launch& L, Sys s, QeqState& Q);   // block-Jacobi inverses (no-op for Jacobi)
 
 // mlp.cu: learned QEq warm start (descriptors, BF16 tensor-core inference, FP32 training)
 constexpr int MLP_NF = 192, MLP_HID = 64, MLP_NT = 4;

@@ -17,6 +17,7 @@ TERMS = ("bond", "lp", "over", "under", "val", "pen", "coa", "tors", "conj", "hb
 OK, E_INVALID, E_CUDA, E_CAPACITY, E_NOT_CONVERGED, E_TIMEOUT, E_NAN, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, MIXED = 0, 1
 WARM_EXTRAP, WARM_ZERO, WARM_MLP = 0, 1, 2
+PRECOND_JACOBI, PRECOND_BLOCK32 = 0, 1
 LIST_FAR, LIST_BOND, LIST_HBOND = 0, 1, 2
 
 _PER_TYPE = ("mass", "val", "vale", "valboc", "valang", "p_lp2", "p_ovun2", "p_ovun5", "p_val3", "p_val5",
@@ -46,7 +47,7 @@ class Options(C.Structure):
                 ("thb_cut", C.c_double), ("thb_cutsq", C.c_double), ("hb_bo_min", C.c_double),
                 ("qeq_tol", C.c_double), ("qeq_max_iter", C.c_int32), ("precision", C.c_int32),
                 ("warm_start", C.c_int32), ("term_mask", C.c_int32), ("capacity_margin", C.c_double),
-                ("skin", C.c_double)]
+                ("skin", C.c_double), ("qeq_precond", C.c_int32)]
 
 
 class ReaxFFError(RuntimeError):
@@ -161,7 +162,7 @@ def make_params(p: dict) -> Params:
 
 
 def make_options(o: dict, precision=FP64, warm_start=WARM_EXTRAP, term_mask=0, capacity_margin=0.0,
-                 skin=0.0) -> Options:
+                 skin=0.0, qeq_precond=0) -> Options:
     O = Options()
     for k in ("r_nb", "r_bond", "r_hb", "bo_cut", "thb_cut", "thb_cutsq", "hb_bo_min", "qeq_tol"):
         setattr(O, k, float(o[k]))
@@ -171,6 +172,7 @@ def make_options(o: dict, precision=FP64, warm_start=WARM_EXTRAP, term_mask=0, c
     O.term_mask = int(term_mask)
     O.capacity_margin = float(capacity_margin)
     O.skin = float(o.get("skin", skin))
+    O.qeq_precond = int(o.get("qeq_precond", qeq_precond))
     return O
 
 
@@ -211,10 +213,10 @@ class ReaxFF:
     """One library context (single system or a batch of replicas)."""
 
     def __init__(self, params: dict, types, box, options: dict, precision=FP64, warm_start=WARM_EXTRAP,
-                 term_mask=0, rep_offsets=None, capacity_margin=0.0, skin=0.0):
+                 term_mask=0, rep_offsets=None, capacity_margin=0.0, skin=0.0, qeq_precond=0):
         self.lib = load()
         P = make_params(params)
-        O = make_options(options, precision, warm_start, term_mask, capacity_margin, skin)
+        O = make_options(options, precision, warm_start, term_mask, capacity_margin, skin, qeq_precond)
         self.types = np.ascontiguousarray(types, np.int32)
         if rep_offsets is None:
             self.h = reaxff_create(P, self.types, np.asarray(box, float).reshape(3), O)

@@ -265,6 +265,35 @@ def test_qeq_cg_equals_dense_cholesky_and_neutral(params, name):
     assert abs(a["q"].sum()) < 1e-12 * len(w["x"])
 
 
+def test_block_jacobi_pcg_special_cases_and_solution(params):
+    """Block-Jacobi PCG (the solver variant): blocks of one atom are Jacobi (the iterates of
+    pcg up to rounding), one block covering every atom is the exact inverse (one iteration), and the
+    32-atom blocks reach the dense solution; the blocks tile each replica."""
+    w = synth.workload("petn464")
+    m = _model(params, w)
+    L = m.lists(w["x"])
+    Hm = m.qeq_matrix(w["x"], L)
+    n = len(w["x"])
+    chi = params["chi"][m.types]
+    eta = params["eta"][m.types]
+    b = -chi
+    xj, itj = ro.pcg(Hm, b, eta, 1e-10, 500)
+    x1, it1 = ro.pcg_block(Hm, b, ro.blocks_of([0, n], 1), 1e-10, 500)
+    assert abs(it1 - itj) <= 1                          # 1/eta vs a 1x1 inverse: rounding only
+    assert np.abs(x1 - xj).max() < 1e-9 * np.abs(xj).max()
+    xa, ita = ro.pcg_block(Hm, b, [(0, n)], 1e-10, 500)
+    assert ita == 1
+    xd = np.linalg.solve(Hm.toarray(), b)
+    assert np.abs(xa - xd).max() < 1e-9 * np.abs(xd).max()
+    x32, it32 = ro.pcg_block(Hm, b, ro.blocks_of([0, n]), 1e-10, 500)
+    assert np.abs(x32 - xd).max() < 1e-8 * np.abs(xd).max()
+    assert it32 < itj
+    assert ro.blocks_of([0, 70, 75]) == [(0, 32), (32, 64), (64, 70), (70, 75)]
+    q_j = m.qeq(w["x"], L, tol=1e-10)["q"]
+    q_b = m.qeq(w["x"], L, tol=1e-10, precond="block32")["q"]
+    assert np.abs(q_j - q_b).max() < 1e-8
+
+
 def test_qeq_two_atom_closed_form(params):
     """Two atoms: q1 = -q2 = (chi2 - chi1) / (eta1 + eta2 - 2 H12)."""
     P = params
