@@ -586,6 +586,23 @@ def main():
         out["species"] = {"ms_per_analysis": 1e3 * t_sp, "molecules": int(mol.max()) + 1, "distinct": len(sp),
                           "top": [{"counts_CHNO": list(k[1:5]), "molecules": v} for k, v in top],
                           "overhead_at_one_analysis_per_1000_steps": 1e3 * t_sp / (1000 * out["ms_per_step"])}
+        # time-averaged bonds: 10 samples, one every 2 steps, then the species on the averages
+        ctx.bo_average_reset()
+        t_sample = 0.0
+        for _ in range(10):
+            ctx.step(2, a.dt)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.bo_average_sample()
+            torch.cuda.synchronize()
+            t_sample += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        mol_a, sp_a = ctx.species_average()
+        t_avg = time.perf_counter() - t0
+        mol_i, _ = ctx.species()
+        out["species"]["time_averaged"] = {"samples": 10, "every_steps": 2, "ms_per_sample": 1e3 * t_sample / 10,
+                                           "ms_analysis": 1e3 * t_avg, "molecules": int(mol_a.max()) + 1,
+                                           "distinct": len(sp_a), "molecules_instantaneous": int(mol_i.max()) + 1}
         # 64 uneven replicas in one context vs one at a time
         out["batched"] = batched(P, a)
         # QEq solver variants: Jacobi vs block-Jacobi preconditioning

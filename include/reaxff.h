@@ -338,6 +338,26 @@ int reaxff_mlp_predict(reaxff_ctx* ctx, double* q);
 int reaxff_species(reaxff_ctx* ctx, const double* bo_threshold, int32_t* mol_id, int64_t* nmol, int32_t cap,
                    int32_t* species, int32_t* nspecies);
 
+/* Time-averaged bonds (Sec. 3.4: persistent bonds told from transient encounters by
+ * averaging bond orders over samples). reaxff_bo_average_sample adds the corrected bond
+ * order of every directed bond-list entry at the current positions (forces computed first
+ * when stale) to a running sum kept per (atom, neighbour, image); a pair missing from a
+ * sample adds 0, so the average is sum / samples over all samples taken since the last
+ * reset. Device work only, no synchronisation. reaxff_bo_average_reset clears the sums
+ * (also before the first sample). reaxff_get_bo_average exports every pair seen, directed,
+ * with its average (arrays as reaxff_get_lists plus avg double[count]; same capacity
+ * rules). reaxff_species_average runs reaxff_species's analysis with the averages in place
+ * of the instantaneous bond orders (same arguments and outputs). E_STATE without samples;
+ * E_CAPACITY when an atom met more distinct bonded pairs than its row holds (2 x the bond
+ * capacity, at least 48). */
+int reaxff_bo_average_reset(reaxff_ctx* ctx);
+int reaxff_bo_average_sample(reaxff_ctx* ctx);
+int64_t reaxff_bo_average_samples(reaxff_ctx* ctx);
+int reaxff_get_bo_average(reaxff_ctx* ctx, int64_t capacity, int64_t* count, int32_t* i, int32_t* j,
+                          int8_t* shift, double* avg);
+int reaxff_species_average(reaxff_ctx* ctx, const double* bo_threshold, int32_t* mol_id, int64_t* nmol,
+                           int32_t cap, int32_t* species, int32_t* nspecies);
+
 /* ---- Launch-schedule autotuner ----------------------------------------------------------
  * Times the alternatives of each tunable launch schedule on this context's current data
  * with CUDA events and keeps the fastest: lanes per central bond in the torsion kernel

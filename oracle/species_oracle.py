@@ -8,7 +8,8 @@ their pair of elements (default 0.3); the molecule ID of an atom is the smallest
 of its connected component in that bond graph; molecule IDs are renumbered 0..M-1 in the
 order of those smallest IDs; a species is the vector of atom counts per element of a
 molecule (isomers are not distinguished); the summary is the count of molecules of each
-species (per replica of a batch).
+species (per replica of a batch). The bond orders may be time averages over samples
+(average_bond_orders), so that transient encounters do not count as bonds.
 """
 from __future__ import annotations
 
@@ -65,6 +66,19 @@ def molecules_bfs(n, bi, bj, bo, types, thr=None):
                     todo.append(b)
         m += 1
     return mol, m
+
+
+def average_bond_orders(samples):
+    """Time-averaged bond orders (Sec. 3.4: bonds judged on bond orders averaged over
+    samples). samples: one (i, j, shift (m, 3), bo) tuple of directed bond entries per
+    sample. Returns {(i, j, sx, sy, sz): (sum of bo over the samples) / (number of
+    samples)} over every pair seen; a pair missing from a sample contributes 0."""
+    acc = {}
+    for i, j, sh, bo in samples:
+        for a, b, s3, v in zip(np.asarray(i), np.asarray(j), np.asarray(sh), np.asarray(bo)):
+            key = (int(a), int(b), int(s3[0]), int(s3[1]), int(s3[2]))
+            acc[key] = acc.get(key, 0.0) + float(v)
+    return {k: v / len(samples) for k, v in acc.items()}
 
 
 def species(types, mol, m, rep=None):

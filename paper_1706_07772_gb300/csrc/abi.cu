@@ -110,6 +110,9 @@ struct reaxff_ctx {
   DevBuf spbuf;
   rx::SpeciesBuf sp{};
   double* sp_thr = nullptr;
+  DevBuf avgbuf;               // time-averaged bond orders
+  rx::BoAvg avg{};
+  int64_t avg_samples = 0;
   // per-stage CUDA-event timing (reaxff_profile_*)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -863,6 +866,7 @@ void reaxff_destroy(reaxff_ctx* ctx) {
   ctx->mlp.buf.free_all();
   ctx->mlp.data.free_all();
   ctx->spbuf.free_all();
+  ctx->avgbuf.free_all();
   if (ctx->sp.h_changed) cudaFreeHost(ctx->sp.h_changed);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->Etot_dev) cudaFree(ctx->Etot_dev);
@@ -1706,16 +1710,11 @@ int reaxff_mlp_predict(reaxff_ctx* ctx, double* q) {
 }  // extern "C"
 
 // ------------------------------------------------------------------ species analysis
-extern "C" {
-
-int reaxff_species(reaxff_ctx* ctx, const double* bo_threshold, int32_t* mol_id, int64_t* nmol, int32_t cap,
-                   int32_t* species, int32_t* nspecies) {
-  if (!ctx || cap < 0 || (cap > 0 && !species)) return REAXFF_E_INVALID;
-  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
-  int rc;
-  if (!ctx->forces_valid) {
-    if ((rc = forces_impl(ctx, true))) return rc;
-  }
+namespace {
+// species analysis over a bond view (bonds with bo > threshold); bo_double: the view's bo
+// array is double, else the path type
+int species_impl(reaxff_ctx* ctx, const BondList& bl, bool bo_double, const double* bo_threshold,
+                 int32_t* mol_id, int64_t* nmol, int32_t cap, int32_t* species, int32_t* nspecies) {
   const int n = ctx->n;
   rx::SpeciesBuf& b = ctx->sp;
   if (!b.lab) {
@@ -1734,8 +1733,8 @@ int reaxff_species(reaxff_ctx* ctx, const double* bo_threshold, int32_t* mol_id,
   for (int k = 0; k < MAXT * MAXT; ++k) thr[k] = bo_threshold ? bo_threshold[k] : 0.3;
   CK(cudaMemcpyAsync(ctx->sp_thr, thr, sizeof(thr), cudaMemcpyHostToDevice, ctx->st));
   rx::Launch L = launch_of(ctx);
-  const int passes = ctx->fp64 ? rx::species_components<double>(L, ctx->sys, ctx->bond, ctx->sp_thr, b, 256)
-                               : rx::species_components<float>(L, ctx->sys, ctx->bond, ctx->sp_thr, b, 256);
+  const int passes = bo_double ? rx::species_components<double>(L, ctx->sys, bl, ctx->sp_thr, b, 256)
+                               : rx::species_components<float>(L, ctx->sys, bl, ctx->sp_thr, b, 256);
   CK(cudaGetLastError());
   if (passes < 0) return fail(ctx, REAXFF_E_NOT_CONVERGED, "species components did not settle in 256 passes");
   rx::species_molecules(L, ctx->sys, b);
@@ -1771,6 +1770,132 @@ int reaxff_species(reaxff_ctx* ctx, const double* bo_threshold, int32_t* mol_id,
   if (nspecies) *nspecies = ns;
   if (ns > cap) return fail(ctx, REAXFF_E_CAPACITY, "more species than cap (count in *nspecies)");
   return REAXFF_OK;
+}
+
+// the averages of the samples so far into avg.avg (needs at least one sample)
+int bo_average_ready(reaxff_ctx* ctx) {
+  if (ctx->avg_samples == 0) return fail(ctx, REAXFF_E_STATE, "no bond-order samples");
+  int over = 0;
+  CK(cudaMemcpyAsync(&over, ctx->avg.over, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (over) return fail(ctx, REAXFF_E_CAPACITY, "an atom met more distinct bonded pairs than the average table holds");
+  rx::Launch L = launch_of(ctx);
+  rx::bo_average_finish(L, ctx->n, ctx->avg, 1.0 / (double)ctx->avg_samples);
+  CK(cudaGetLastError());
+  return REAXFF_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int reaxff_species(reaxff_ctx* ctx, const double* bo_threshold, int32_t* mol_id, int64_t* nmol, int32_t cap,
+                   int32_t* species, int32_t* nspecies) {
+  if (!ctx || cap < 0 || (cap > 0 && !species)) return REAXFF_E_INVALID;
+  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  int rc;
+  if (!ctx->forces_valid) {
+    if ((rc = forces_impl(ctx, true))) return rc;
+  }
+  return species_impl(ctx, ctx->bond, ctx->fp64, bo_threshold, mol_id, nmol, cap, species, nspecies);
+}
+
+int reaxff_bo_average_reset(reaxff_ctx* ctx) {
+  if (!ctx) return REAXFF_E_INVALID;
+  ctx->avg_samples = 0;
+  if (ctx->avg.cnt) {
+    CK(cudaMemsetAsync(ctx->avg.cnt, 0, ctx->n * sizeof(int), ctx->st));
+    CK(cudaMemsetAsync(ctx->avg.over, 0, sizeof(int), ctx->st));
+  }
+  return REAXFF_OK;
+}
+
+int reaxff_bo_average_sample(reaxff_ctx* ctx) {
+  if (!ctx) return REAXFF_E_INVALID;
+  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  int rc;
+  if (!ctx->forces_valid) {
+    if ((rc = forces_impl(ctx, true))) return rc;
+  }
+  rx::BoAvg& A = ctx->avg;
+  if (!A.cnt) {
+    DevBuf& B = ctx->avgbuf;
+    const int n = ctx->n;
+    A.cap = std::max(48, 2 * ctx->cap_bond);
+    A.cnt = B.alloc<int>(n);
+    A.j = B.alloc<int>((size_t)n * A.cap);
+    A.s = B.alloc<uint8_t>((size_t)n * A.cap);
+    A.sum = B.alloc<double>((size_t)n * A.cap);
+    A.avg = B.alloc<double>((size_t)n * A.cap);
+    A.over = B.alloc<int>(1);
+    if (B.err != cudaSuccess) {
+      B.free_all();
+      A = rx::BoAvg{};
+      return fail(ctx, REAXFF_E_CUDA, "bond-order average buffers");
+    }
+    ctx->avg_samples = 0;
+    CK(cudaMemsetAsync(A.cnt, 0, n * sizeof(int), ctx->st));
+    CK(cudaMemsetAsync(A.over, 0, sizeof(int), ctx->st));
+  }
+  rx::Launch L = launch_of(ctx);
+  if (ctx->fp64) rx::bo_average_sample<double>(L, ctx->sys, ctx->bond, A);
+  else rx::bo_average_sample<float>(L, ctx->sys, ctx->bond, A);
+  CK(cudaGetLastError());
+  ++ctx->avg_samples;
+  return REAXFF_OK;
+}
+
+int64_t reaxff_bo_average_samples(reaxff_ctx* ctx) { return ctx ? ctx->avg_samples : -1; }
+
+int reaxff_get_bo_average(reaxff_ctx* ctx, int64_t capacity, int64_t* count, int32_t* i_out, int32_t* j_out,
+                          int8_t* shift, double* avg_out) {
+  if (!ctx || !count) return REAXFF_E_INVALID;
+  int rc = bo_average_ready(ctx);
+  if (rc) return rc;
+  const int n = ctx->n;
+  const rx::BoAvg& A = ctx->avg;
+  std::vector<int> cnt(n);
+  CK(cudaMemcpyAsync(cnt.data(), A.cnt, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  int64_t tot = 0;
+  for (int i = 0; i < n; ++i) tot += cnt[i];
+  *count = tot;
+  if (capacity == 0 && !i_out) return REAXFF_OK;
+  if (capacity < tot || !i_out || !j_out || !shift || !avg_out)
+    return fail(ctx, REAXFF_E_INVALID, "output capacity too small");
+  std::vector<int> jj((size_t)n * A.cap);
+  std::vector<uint8_t> ss((size_t)n * A.cap);
+  std::vector<double> av((size_t)n * A.cap);
+  CK(cudaMemcpyAsync(jj.data(), A.j, jj.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(ss.data(), A.s, ss.size(), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(av.data(), A.avg, av.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  int64_t k = 0;
+  for (int i = 0; i < n; ++i)
+    for (int m = 0; m < cnt[i]; ++m, ++k) {
+      const size_t e = (size_t)i * A.cap + m;
+      i_out[k] = i;
+      j_out[k] = jj[e];
+      const int c = ss[e];
+      shift[3 * k + 0] = (int8_t)(c / 9 - 1);
+      shift[3 * k + 1] = (int8_t)((c / 3) % 3 - 1);
+      shift[3 * k + 2] = (int8_t)(c % 3 - 1);
+      avg_out[k] = av[e];
+    }
+  return REAXFF_OK;
+}
+
+int reaxff_species_average(reaxff_ctx* ctx, const double* bo_threshold, int32_t* mol_id, int64_t* nmol,
+                           int32_t cap, int32_t* species, int32_t* nspecies) {
+  if (!ctx || cap < 0 || (cap > 0 && !species)) return REAXFF_E_INVALID;
+  int rc = bo_average_ready(ctx);
+  if (rc) return rc;
+  BondList v{};
+  v.cap = ctx->avg.cap;
+  v.cnt = ctx->avg.cnt;
+  v.j = ctx->avg.j;
+  v.s = ctx->avg.s;
+  v.bo = ctx->avg.avg;
+  return species_impl(ctx, v, true, bo_threshold, mol_id, nmol, cap, species, nspecies);
 }
 
 }  // extern "C"

@@ -645,4 +645,17 @@ struct SpeciesBuf {
 template <typename R>
 int species_components(const Launch& L, Sys s, BondList bl, const double* thr, SpeciesBuf& b, int max_pass);
 void species_molecules(const Launch& L, Sys s, SpeciesBuf& b);
+// time-averaged bond orders: per atom a row of cap (j, image code, running sum) entries keyed
+// by the neighbour and its image; avg = sum / samples is written by bo_average_finish
+struct BoAvg {
+  int cap;
+  int* cnt;                    // [n] entries in use
+  int* j;                      // [n*cap]
+  uint8_t* s;                  // [n*cap] image code
+  double *sum, *avg;           // [n*cap]
+  int* over;                   // set when a row had no room for a new pair
+};
+template <typename R>
+void bo_average_sample(const Launch& L, Sys s, BondList bl, BoAvg A);
+void bo_average_finish(const Launch& L, int n, BoAvg A, double inv_samples);
 }  // namespace rx

@@ -101,9 +101,66 @@ __global__ void k_sp_count(Sys s, const int* lab, const int* rank, int* mol, int
   mrep[m] = s.rep[i];                                   // every atom of a molecule: same replica
 }
 
+// Time-averaged bond orders (Sec. 3.4: bonds decided from bond orders averaged over samples
+// rather than one instant). One thread per atom adds each bond entry's corrected BO to the
+// running sum of the same (neighbour, image) in the atom's row, appending the pair when it
+// is new; a pair absent from a sample adds nothing, so sum / samples is the average with
+// zeros for the samples without it. Each row is owned by one thread and samples are added
+// in order: deterministic. The two directions of a bond carry the same BO in every sample,
+// so their sums are equal.
+template <typename R>
+__global__ void k_boavg_sample(Sys s, BondList bl, rx::BoAvg A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const R* bo = (const R*)bl.bo;
+  const size_t row = (size_t)i * A.cap;
+  int m = A.cnt[i];
+  const int nb = bl.cnt[i];
+  for (int k = 0; k < nb; ++k) {
+    const size_t e = (size_t)i * bl.cap + k;
+    const int j = bl.j[e];
+    const uint8_t c = bl.s[e];
+    const double v = (double)bo[e];
+    int q = 0;
+    while (q < m && !(A.j[row + q] == j && A.s[row + q] == c)) ++q;
+    if (q < m) {
+      A.sum[row + q] += v;
+    } else if (m < A.cap) {
+      A.j[row + m] = j;
+      A.s[row + m] = c;
+      A.sum[row + m] = v;
+      ++m;
+    } else {
+      *A.over = 1;
+    }
+  }
+  A.cnt[i] = m;
+}
+
+__global__ void k_boavg_finish(int n, rx::BoAvg A, double inv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const size_t row = (size_t)i * A.cap;
+  for (int q = 0; q < A.cnt[i]; ++q) A.avg[row + q] = A.sum[row + q] * inv;
+}
+
 }  // namespace
 
 namespace rx {
+
+template <typename R>
+void bo_average_sample(const Launch& L, Sys s, BondList bl, BoAvg A) {
+  k_boavg_sample<R><<<(s.n + 127) / 128, 128, 0, L.st>>>(s, bl, A);
+  *L.count += 1;
+}
+
+void bo_average_finish(const Launch& L, int n, BoAvg A, double inv_samples) {
+  k_boavg_finish<<<(n + 255) / 256, 256, 0, L.st>>>(n, A, inv_samples);
+  *L.count += 1;
+}
+
+template void bo_average_sample<double>(const Launch&, Sys, BondList, BoAvg);
+template void bo_average_sample<float>(const Launch&, Sys, BondList, BoAvg);
 
 // labels to the component minima; returns the number of hooking passes, or -1 when the
 // pass limit was reached (flags read on the host: synchronises the stream)

@@ -93,6 +93,10 @@ def load(path: str = LIB_PATH):
         "reaxff_qeq_spmv_total": (i64, [vp]),
         "reaxff_qeq_warm_choice": (C.c_int, [vp, ip32]),
         "reaxff_species": (C.c_int, [vp, dp, ip32, ip64, i32, ip32, ip32]),
+        "reaxff_species_average": (C.c_int, [vp, dp, ip32, ip64, i32, ip32, ip32]),
+        "reaxff_bo_average_reset": (C.c_int, [vp]), "reaxff_bo_average_sample": (C.c_int, [vp]),
+        "reaxff_bo_average_samples": (i64, [vp]),
+        "reaxff_get_bo_average": (C.c_int, [vp, i64, ip64, ip32, ip32, C.POINTER(C.c_int8), dp]),
         "reaxff_autotune": (C.c_int, [vp, C.c_char_p, ip32]),
         "reaxff_mlp_init": (C.c_int, [vp, C.c_uint64]),
         "reaxff_mlp_set_params": (C.c_int, [vp, fp, fp, fp]),
@@ -395,6 +399,44 @@ class ReaxFF:
         self._check(self.lib.reaxff_species(self.h, None if thr is None else _dp(thr),
                                             mol.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(nmol), cap,
                                             rows.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(ns)))
+        return mol, {tuple(int(v) for v in r[:-1]): int(r[-1]) for r in rows[:ns.value]}
+
+    def bo_average_reset(self):
+        self._check(self.lib.reaxff_bo_average_reset(self.h))
+
+    def bo_average_sample(self):
+        self._check(self.lib.reaxff_bo_average_sample(self.h))
+
+    def bo_average_samples(self):
+        return int(self.lib.reaxff_bo_average_samples(self.h))
+
+    def get_bo_average(self):
+        """Directed pairs seen since the last reset and their averaged bond orders:
+        (i int32[m], j int32[m], shift int8[m, 3], avg float64[m])."""
+        cnt = C.c_int64()
+        self._check(self.lib.reaxff_get_bo_average(self.h, 0, C.byref(cnt), None, None, None, None))
+        m = cnt.value
+        i = np.empty(m, np.int32)
+        j = np.empty(m, np.int32)
+        s = np.empty((m, 3), np.int8)
+        a = np.empty(m)
+        self._check(self.lib.reaxff_get_bo_average(self.h, m, C.byref(cnt), i.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                   j.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                   s.ctypes.data_as(C.POINTER(C.c_int8)), _dp(a)))
+        return i, j, s, a
+
+    def species_average(self, bo_threshold=None, cap=4096):
+        """species() on the time-averaged bond orders."""
+        thr = None
+        if bo_threshold is not None:
+            thr = np.ascontiguousarray(bo_threshold, np.float64).reshape(MAXT * MAXT)
+        mol = np.empty(self.n, np.int32)
+        nmol = C.c_int64()
+        rows = np.empty((cap, MAXT + 2), np.int32)
+        ns = C.c_int32()
+        self._check(self.lib.reaxff_species_average(self.h, None if thr is None else _dp(thr),
+                                                    mol.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(nmol), cap,
+                                                    rows.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(ns)))
         return mol, {tuple(int(v) for v in r[:-1]): int(r[-1]) for r in rows[:ns.value]}
 
     def autotune(self, cache_path=None):

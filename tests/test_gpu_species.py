@@ -85,3 +85,51 @@ def test_species_per_replica(rx, params):
         assert np.array_equal(mb - mb.min(), mol - mol.min())
         c.close()
     cb.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_time_averaged_bond_orders_and_species(rx, params, prec):
+    """Four samples at host-made positions (the crystal with seeded 0.03 A displacements):
+    the averaged bond order of every directed pair seen equals the oracle's average of its
+    own bond orders, and the species analysis on the averages matches the oracle's."""
+    w = synth.workload("petn464")
+    types = np.asarray(w["types"])
+    box = np.asarray(w["box"], float)
+    o = dict(w["options"], qeq_tol=1e-10)
+    rng = np.random.default_rng(5)
+    xs = [np.mod(w["x"] + rng.normal(scale=0.03, size=w["x"].shape), box) for _ in range(4)]
+    m = oracle.Model(params, types, box, o)
+    samples = []
+    for x in xs:
+        r = m.forces(x, tol=1e-10)
+        B, bo = r["lists"]["bond"], r["parts"]["bo"]
+        samples.append((np.concatenate([B["i"], B["j"]]), np.concatenate([B["j"], B["i"]]),
+                        np.concatenate([B["s"], -B["s"]]), np.concatenate([bo, bo])))
+    ref = so.average_bond_orders(samples)
+    c = rx.ReaxFF(params, w["types"], w["box"], o, precision=prec)
+    c.bo_average_reset()
+    for x in xs:
+        c.set_state(x, w["v"])
+        c.bo_average_sample()
+    assert c.bo_average_samples() == 4
+    i, j, s, a = c.get_bo_average()
+    got = {(int(p), int(q), int(t[0]), int(t[1]), int(t[2])): float(v) for p, q, t, v in zip(i, j, s, a)}
+    assert set(got) == set(ref)
+    tol = 1e-9 if prec == 0 else 2e-6
+    assert max(abs(got[k] - ref[k]) for k in ref) < tol
+    keys = sorted(ref)
+    avg = np.array([ref[k] for k in keys])
+    ki = np.array([k[0] for k in keys])
+    kj = np.array([k[1] for k in keys])
+    margin = 1e-9 if prec == 0 else 1e-4
+    assert np.all(np.abs(avg - 0.3) > margin)
+    mol_ref, m_ref = so.molecules(len(types), ki, kj, avg, types)
+    mol, sp = c.species_average()
+    assert np.array_equal(mol, mol_ref)
+    got_sp = {(k[0],) + k[1:5]: v for k, v in sp.items()}
+    assert got_sp == dict(so.species(types, mol_ref, m_ref))
+    c.bo_average_reset()
+    assert c.bo_average_samples() == 0
+    with pytest.raises(rx.ReaxFFError):
+        c.species_average()
+    c.close()

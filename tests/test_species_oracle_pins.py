@@ -48,3 +48,40 @@ def test_counts_sum_to_atoms():
     sp = so.species(types, mol, m)
     assert sum(sum(k[1:]) * v for k, v in sp.items()) == n
     assert sum(sp.values()) == m
+
+
+def test_time_average_hand_built():
+    """Averages by hand: a persistent pair (0.2, 0.4, 0.6 -> 0.4), a transient one seen in
+    one of three samples (0.9 -> 0.3), image shifts kept apart; one sample is itself."""
+    z = np.zeros((1, 3), int)
+    e = np.array([[1, 0, 0]])
+    samples = [
+        (np.array([0, 2]), np.array([1, 3]), np.array([[0, 0, 0], [0, 0, 0]]), np.array([0.2, 0.9])),
+        (np.array([0]), np.array([1]), z, np.array([0.4])),
+        (np.array([0, 0]), np.array([1, 1]), np.concatenate([z, e]), np.array([0.6, 0.75])),
+    ]
+    avg = so.average_bond_orders(samples)
+    assert set(avg) == {(0, 1, 0, 0, 0), (2, 3, 0, 0, 0), (0, 1, 1, 0, 0)}
+    assert abs(avg[(0, 1, 0, 0, 0)] - 0.4) < 1e-15
+    assert abs(avg[(2, 3, 0, 0, 0)] - 0.3) < 1e-15
+    assert abs(avg[(0, 1, 1, 0, 0)] - 0.25) < 1e-15
+    one = so.average_bond_orders(samples[:1])
+    assert one == {(0, 1, 0, 0, 0): 0.2, (2, 3, 0, 0, 0): 0.9}
+
+
+def test_transient_encounter_is_not_a_bond_after_averaging():
+    """An encounter at BO 0.9 in one of four samples averages to 0.225 < 0.3: the two atoms
+    stay separate molecules, while a bond at 0.35 in every sample joins its atoms."""
+    types = np.array([0, 1, 0, 1])
+    samples = []
+    for k in range(4):
+        bi, bj, bo = [0, 1], [1, 0], [0.35, 0.35]
+        if k == 2:
+            bi, bj, bo = bi + [2, 3], bj + [3, 2], bo + [0.9, 0.9]
+        samples.append((np.array(bi), np.array(bj), np.zeros((len(bi), 3), int), np.array(bo)))
+    avg = so.average_bond_orders(samples)
+    keys = sorted(avg)
+    mol, m = so.molecules(4, [k[0] for k in keys], [k[1] for k in keys], [avg[k] for k in keys], types)
+    assert m == 3 and list(mol) == [0, 0, 1, 2]
+    inst, mi = so.molecules(4, samples[2][0], samples[2][1], samples[2][3], types)
+    assert mi == 2 and list(inst) == [0, 0, 1, 1]          # the instant alone joins 2 and 3
