@@ -355,7 +355,9 @@ void grow_caps(reaxff_ctx* ctx, int flags) {
 // checked: clear the flags, read them back after the build and regrow and retry on a
 // capacity overflow (host synchronisation). Unchecked: launches only; the caller reads the
 // flags later (the error word is not cleared, so earlier flags of a batch survive).
-int build_lists_impl(reaxff_ctx* ctx, bool checked = true) {
+// drifted: the positions came from the fused drift kernel, which already wrote the float
+// records and ran the skin test
+int build_lists_impl(reaxff_ctx* ctx, bool checked = true, bool drifted = false) {
   for (int attempt = 0; attempt < 3; ++attempt) {
     rx::Launch L = launch_of(ctx);
     if (checked) CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
@@ -364,8 +366,10 @@ int build_lists_impl(reaxff_ctx* ctx, bool checked = true) {
       // Verlet-skin candidates (rebuilt on the device only when an atom moved > skin/2),
       // filtered exactly every step into the near/far rows
       { Stage st(ctx, 0);
-        rx::positions_f32(L, ctx->sys);
-        rx::skin_check(L, ctx->sys, ctx->cand);
+        if (!drifted || attempt > 0) {
+          rx::positions_f32(L, ctx->sys);
+          rx::skin_check(L, ctx->sys, ctx->cand);
+        }
         rx::cand_build(L, ctx->sys, ctx->cells, ctx->cand); }
       if (ctx->fp64) {
         { Stage st(ctx, 1); rx::cand_filter<double>(L, ctx->sys, ctx->cand, ctx->far, ctx->hb, ctx->Pd, ctx->far_margin, ctx->near_margin, ctx->hb_margin); }
@@ -467,9 +471,9 @@ int zero_accumulators(reaxff_ctx* ctx) {
 }
 
 // lists -> (QEq) -> all terms -> chain rule; energies reduced into E_rep / vir_rep
-int forces_impl(reaxff_ctx* ctx, bool solve_q, bool reduce = true, bool checked = true) {
+int forces_impl(reaxff_ctx* ctx, bool solve_q, bool reduce = true, bool checked = true, bool drifted = false) {
   if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
-  int rc = build_lists_impl(ctx, checked);
+  int rc = build_lists_impl(ctx, checked, drifted);
   if (rc) return rc;
   rc = zero_accumulators(ctx);
   if (rc) return rc;
@@ -685,7 +689,7 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   ctx->ke_rep = B.alloc<double>(nrep);
   ctx->chi_t = B.alloc<double>(MAXT);
   ctx->eta_t = B.alloc<double>(MAXT);
-  ctx->mass_t = B.alloc<double>(MAXT);
+  ctx->mass_t = B.alloc<double>(2 * MAXT);          // masses, then their reciprocals
   double* ieta_d = B.alloc<double>(MAXT);
   ctx->Q.ieta = ieta_d;
   // ---- QEq state and chunking (chunks never straddle replicas)
@@ -744,11 +748,11 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
     Q.scal = Q.scal_smem ? nullptr : B.alloc<double>((size_t)Q.grid * (nrep * rx::QEQ_SCAL_PER_REP + 4));
     Q.state = Q.state_smem ? nullptr : B.alloc<double>((size_t)Q.grid * rx::QEQ_NV_STATE * Q.rows_blk);
   }
-  // reduction chunks (<= 4096 atoms each, per replica)
+  // reduction chunks (<= RED_CHUNK atoms each, per replica)
   std::vector<int> rlo, rrep(nrep + 1, 0);
   for (int r = 0; r < nrep; ++r) {
     rrep[r] = (int)rlo.size();
-    for (int64_t i = rep_offsets[r]; i < rep_offsets[r + 1]; i += 4096) rlo.push_back((int)i);
+    for (int64_t i = rep_offsets[r]; i < rep_offsets[r + 1]; i += rx::RED_CHUNK) rlo.push_back((int)i);
   }
   rrep[nrep] = (int)rlo.size();
   ctx->red.nchunk = (int)rlo.size();
@@ -758,6 +762,7 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   ctx->red.chunk_lo = rlo_d;
   ctx->red.rep_chunk = rrep_d;
   ctx->red.part = B.alloc<double>((size_t)ctx->red.nchunk * 20);
+  ctx->red.done = B.alloc<unsigned>(1);
   Q.iters = B.alloc<int>(2 * nrep);
   Q.bar = B.alloc<GridBar>(1);
   Q.hst = B.alloc<int>(4);
@@ -821,7 +826,12 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   UP(rrep_d, rrep.data(), (nrep + 1) * sizeof(int));
   UP(ctx->chi_t, chi, sizeof(chi));
   UP(ctx->eta_t, eta, sizeof(eta));
-  UP(ctx->mass_t, mass, sizeof(mass));
+  double mass2[2 * MAXT];
+  for (int t = 0; t < MAXT; ++t) {
+    mass2[t] = mass[t];
+    mass2[MAXT + t] = mass[t] > 0 ? 1.0 / mass[t] : 0.0;
+  }
+  UP(ctx->mass_t, mass2, sizeof(mass2));
   UP(ieta_d, ieta, sizeof(ieta));
 #undef UP
   if (e == cudaSuccess) e = cudaMemset(s.vx, 0, n * sizeof(double));
@@ -837,6 +847,7 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   if (e == cudaSuccess) e = cudaMemset(ctx->Q.spmv_total, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(ctx->Q.mlp_used, 0, nrep * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->Q.bar, 0, sizeof(GridBar));
+  if (e == cudaSuccess) e = cudaMemset(ctx->red.done, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
     B.free_all();
     delete ctx;
@@ -1126,13 +1137,13 @@ int reaxff_forces_fixed_q(reaxff_ctx* ctx, const double* q, double* F, double* E
 // the total energy per replica goes to Etot_out (at *etot_idx when given)
 static int step_once(reaxff_ctx* ctx, double dt, bool checked, double* Etot_out, int* etot_idx) {
   rx::Launch L = launch_of(ctx);
-  { Stage sg(ctx, 14); rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 1); }
-  int rc = forces_impl(ctx, true, false, checked);
+  { Stage sg(ctx, 14); rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 1, ctx->use_skin ? &ctx->cand : nullptr); }
+  int rc = forces_impl(ctx, true, false, checked, ctx->use_skin);
   if (rc) return rc;
   { Stage sg(ctx, 14); rx::verlet_kick_drift(L, ctx->sys, ctx->mass_t, dt, 0); }
   Stage sg(ctx, 15);
-  rx::reduce_energies(L, ctx->sys, ctx->acc, ctx->mass_t, ctx->red, ctx->E_rep, ctx->vir_rep, ctx->ke_rep);
-  rx::etot_combine(L, ctx->nrep, ctx->E_rep, ctx->ke_rep, Etot_out, etot_idx);
+  rx::reduce_energies(L, ctx->sys, ctx->acc, ctx->mass_t, ctx->red, ctx->E_rep, ctx->vir_rep, ctx->ke_rep, Etot_out,
+                      etot_idx);
   return REAXFF_OK;
 }
 

@@ -107,49 +107,82 @@ __global__ void k_finalize(Sys s, double* F) {
 // replica; pass 2, one warp per (replica, q) sums that replica's chunk partials in order.
 // Both passes have a fixed reduction order, so the sums are bitwise reproducible.
 constexpr int NQ_RED = NTERMS + 7;
+constexpr int RED_PER_THREAD = 4, RED_BLOCK = 128;
+static_assert(RED_PER_THREAD * RED_BLOCK == rx::RED_CHUNK, "reduction chunk");
 __device__ __forceinline__ double red_value(const Sys& s, const Accum& acc, const double* mass_t, int q, int64_t i) {
   if (q == T_TORS || q == T_CONJ) return acc.e[(size_t)q * s.n + i] + fix_get(acc.efx + (size_t)(q - T_TORS) * s.n + i);
   if (q < NTERMS) return acc.e[(size_t)q * s.n + i];
   if (q < NTERMS + 6)
     return acc.vir[(size_t)(q - NTERMS) * s.n + i] + fix_get(acc.vfx + (size_t)(q - NTERMS) * s.n + i);
   const double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
-  return 0.5 * mass_t[s.type[i]] * (vx * vx + vy * vy + vz * vz) / 4.184e-4;
+  return (vx * vx + vy * vy + vz * vz) * mass_t[s.type[i]] * (0.5 / 4.184e-4);   // (amu A^2/fs^2 -> kcal/mol)
 }
-__global__ void k_reduce1(Sys s, Accum acc, const double* mass_t, const int* chunk_lo, double* part) {
+// Pass 1 per block (chunk, q); the block that finishes last (arrival counter, zeroed again
+// by it) runs pass 2 for every (replica, q) -- lane l of a warp sums chunks l, l+32, ... of
+// the replica in order -- and, when asked, the total energy per replica. The order of every
+// sum is fixed whichever block comes last.
+__global__ void k_reduce(Sys s, Accum acc, const double* mass_t, rx::RedPlan rp, double* E_rep, double* vir_rep,
+                         double* ke_rep, double* etot, int* etot_idx) {
   const int c = blockIdx.x, q = blockIdx.y;
+  // a chunk holds at most RED_PER_THREAD * blockDim.x atoms: each thread's values load
+  // together and are summed in a fixed order
+  const int lo = rp.chunk_lo[c], hi = rp.chunk_lo[c + 1];
   double v = 0.0;
-  for (int64_t i = chunk_lo[c] + threadIdx.x; i < chunk_lo[c + 1]; i += blockDim.x) v += red_value(s, acc, mass_t, q, i);
+#pragma unroll
+  for (int k = 0; k < RED_PER_THREAD; ++k) {
+    const int i = lo + threadIdx.x + k * blockDim.x;
+    if (i < hi) v += red_value(s, acc, mass_t, q, i);
+  }
   __shared__ double sh[32];
+  __shared__ bool last;
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    part[(size_t)c * NQ_RED + q] = t;
+    rp.part[(size_t)c * NQ_RED + q] = t;
+    __threadfence();
+    last = atomicAdd(rp.done, 1u) == gridDim.x * gridDim.y - 1;
   }
-}
-__global__ void k_reduce2(Sys s, const int* rep_chunk, const double* part, double* E_rep, double* vir_rep, double* ke_rep,
-                          double* etot) {
-  const int pq = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (pq >= s.nrep * NQ_RED) return;
-  const int r = pq / NQ_RED, q = pq % NQ_RED;
-  double v = 0.0;
-  for (int c = rep_chunk[r] + lane; c < rep_chunk[r + 1]; c += 32) v += part[(size_t)c * NQ_RED + q];
-  v = warp_sum(v);
-  if (lane == 0) {
-    if (!isfinite(v)) atomicOr(s.err, ERR_NAN);
-    if (q < NTERMS) E_rep[r * NTERMS + q] = v;
-    else if (q < NTERMS + 6) vir_rep[r * 6 + (q - NTERMS)] = v;
-    else ke_rep[r] = v;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int pq = threadIdx.x >> 5; pq < s.nrep * NQ_RED; pq += nw) {
+    const int r = pq / NQ_RED, qq = pq % NQ_RED;
+    double u = 0.0;
+    for (int k = rp.rep_chunk[r] + lane; k < rp.rep_chunk[r + 1]; k += 32) u += __ldcg(rp.part + (size_t)k * NQ_RED + qq);
+    u = warp_sum(u);
+    if (lane == 0) {
+      if (!isfinite(u)) atomicOr(s.err, ERR_NAN);
+      if (qq < NTERMS) E_rep[r * NTERMS + qq] = u;
+      else if (qq < NTERMS + 6) vir_rep[r * 6 + (qq - NTERMS)] = u;
+      else ke_rep[r] = u;
+    }
   }
+  __syncthreads();
+  if (etot) {
+    // total energy per replica into etot[k*nrep + r]; k = *etot_idx (then advanced) or 0
+    const int k = etot_idx ? *etot_idx : 0;
+    for (int r = threadIdx.x; r < s.nrep; r += blockDim.x) {
+      double t = 0.0;
+      for (int qq = 0; qq < NTERMS; ++qq) t += E_rep[r * NTERMS + qq];
+      etot[(size_t)k * s.nrep + r] = t + ke_rep[r];
+    }
+    __syncthreads();
+    if (etot_idx && threadIdx.x == 0) *etot_idx = k + 1;
+  }
+  if (threadIdx.x == 0) *rp.done = 0u;
 }
 
-__global__ void k_kick_drift(Sys s, const double* mass_t, double dt, int drift) {
+// half kick (and drift). With skin: after the drift, also the float position records and
+// the Verlet-skin test of the candidate list (displacement since the last build against
+// skin/2), which the list build would otherwise do in two more passes
+__global__ void k_kick_drift(Sys s, const double* mass_t, double dt, int drift, int skin, double half_skin2) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
-  const double c = 0.5 * dt * 4.184e-4 / mass_t[s.type[i]];
+  const double c = (0.5 * dt * 4.184e-4) * mass_t[MAXT + s.type[i]];    // mass_t[MAXT + t] = 1 / m_t
   double vx = s.vx[i] + c * fix_get(s.fx + i);
   double vy = s.vy[i] + c * fix_get(s.fy + i);
   double vz = s.vz[i] + c * fix_get(s.fz + i);
@@ -163,19 +196,16 @@ __global__ void k_kick_drift(Sys s, const double* mass_t, double dt, int drift) 
     }
     if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) atomicOr(s.err, ERR_NAN);
     s.x[i] = p[0]; s.y[i] = p[1]; s.z[i] = p[2];
+    if (skin) {
+      write_pos_f32(s, i);
+      double d2 = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double dd = (p[d] + s.img[3 * i + d] * L[d]) - s.xb[3 * i + d];
+        d2 += dd * dd;
+      }
+      if (!(d2 <= half_skin2)) atomicOr(s.rebuild, 1);
+    }
   }
-}
-
-// total energy per replica into out[k*nrep + r]; k = *idx (then advanced) or 0 without idx
-__global__ void k_etot(int nrep, const double* E_rep, const double* ke, double* out, int* idx) {
-  const int k = idx ? *idx : 0;
-  for (int r = threadIdx.x; r < nrep; r += blockDim.x) {
-    double t = 0.0;
-    for (int q = 0; q < NTERMS; ++q) t += E_rep[r * NTERMS + q];
-    out[(size_t)k * nrep + r] = t + ke[r];
-  }
-  __syncthreads();
-  if (idx && threadIdx.x == 0) *idx = k + 1;
 }
 
 // copy (save) or restore the primary MD state of a batch: positions, velocities and the
@@ -198,10 +228,6 @@ __global__ void k_snapshot(Sys s, double* hist, int nhist_doubles, int* hst, dou
 }  // namespace
 
 namespace rx {
-void etot_combine(const Launch& L, int nrep, const double* E_rep, const double* ke, double* out, int* idx) {
-  k_etot<<<1, 256, 0, L.st>>>(nrep, E_rep, ke, out, idx);
-  *L.count += 1;
-}
 void snapshot(const Launch& L, Sys s, double* hist, int nhist_doubles, int* hst, double* buf, int* ibuf, int restore) {
   k_snapshot<<<4 * 152, 256, 0, L.st>>>(s, hist, nhist_doubles, hst, buf, ibuf, restore);
   *L.count += 1;
@@ -219,14 +245,12 @@ void finalize_forces(const Launch& L, Sys s, double* F) {
   *L.count += 1;
 }
 void reduce_energies(const Launch& L, Sys s, Accum acc, const double* mass_t, const RedPlan& rp, double* E_rep,
-                     double* vir_rep, double* ke_rep) {
-  k_reduce1<<<dim3(rp.nchunk, NQ_RED), 256, 0, L.st>>>(s, acc, mass_t, rp.chunk_lo, rp.part);
-  const int warps = s.nrep * NQ_RED;
-  k_reduce2<<<(warps + 7) / 8, 256, 0, L.st>>>(s, rp.rep_chunk, rp.part, E_rep, vir_rep, ke_rep, nullptr);
-  *L.count += 2;
+                     double* vir_rep, double* ke_rep, double* etot, int* etot_idx) {
+  k_reduce<<<dim3(rp.nchunk, NQ_RED), RED_BLOCK, 0, L.st>>>(s, acc, mass_t, rp, E_rep, vir_rep, ke_rep, etot, etot_idx);
+  *L.count += 1;
 }
-void verlet_kick_drift(const Launch& L, Sys s, const double* mass_t, double dt, int drift) {
-  k_kick_drift<<<grid_for(s.n, 256), 256, 0, L.st>>>(s, mass_t, dt, drift);
+void verlet_kick_drift(const Launch& L, Sys s, const double* mass_t, double dt, int drift, const CandList* cl) {
+  k_kick_drift<<<grid_for(s.n, 256), 256, 0, L.st>>>(s, mass_t, dt, drift, cl ? 1 : 0, cl ? cl->half_skin2 : 0.0);
   *L.count += 1;
 }
 

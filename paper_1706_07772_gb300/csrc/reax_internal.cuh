@@ -538,16 +538,20 @@ void nonbonded(const Launch& L, Sys s, FarList f, Accum acc, const DParams<R>* P
 template <typename R>
 void chain_rule(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc);
 void finalize_forces(const Launch& L, Sys s, double* F);
-struct RedPlan {                // chunks (<= 4096 atoms, never straddling replicas) for reductions
+constexpr int RED_CHUNK = 512;   // atoms per reduction chunk
+struct RedPlan {                // chunks (<= RED_CHUNK atoms, never straddling replicas) for reductions
   int nchunk;
   int* chunk_lo;               // [nchunk+1]
   int* rep_chunk;              // [nrep+1]
   double* part;                // [nchunk*20]
+  unsigned* done;              // arrival counter of the reduction blocks (zero between launches)
 };
+// per-replica energies, virial and kinetic energy; with etot, also the total energy per
+// replica into etot[k*nrep + r], k = *etot_idx (then advanced) or 0 without etot_idx
 void reduce_energies(const Launch& L, Sys s, Accum acc, const double* mass_t, const RedPlan& rp, double* E_rep,
-                     double* vir_rep, double* ke_rep);
-void verlet_kick_drift(const Launch& L, Sys s, const double* mass_t, double dt, int drift);
-void etot_combine(const Launch& L, int nrep, const double* E_rep, const double* ke, double* out, int* idx);
+                     double* vir_rep, double* ke_rep, double* etot = nullptr, int* etot_idx = nullptr);
+void verlet_kick_drift(const Launch& L, Sys s, const double* mass_t, double dt, int drift,
+                       const CandList* cl = nullptr);   // cl: also float records + skin test
 // save (restore = 0) or restore the primary MD state: x, v, the QEq rings (contiguous,
 // nhist_doubles) and their device state hst[4]; buf holds 6n + nhist_doubles doubles
 void snapshot(const Launch& L, Sys s, double* hist, int nhist_doubles, int* hst, double* buf, int* ibuf, int restore);
