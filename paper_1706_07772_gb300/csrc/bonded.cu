@@ -547,6 +547,134 @@ template <int TG> struct GroupSum<double, TG> {
   }
 };
 
+// One torsion + conjugation term (i-j-k-l over the central bond j-k, Sec. 3.3 "4-body"):
+// energies and the derivatives with respect to BO_ij, BO_kl (fixed-point atomics on the bond
+// entries), forces on i and l (atomics), and the contributions to the central bond's totals in
+// v[18]: 0-2 F_j, 3 dE/dDelta_j, 4 E_tors, 5 E_conj, 6-11 virial, 12-14 F_k, 15 dE/dDelta_k,
+// 16 dE/dBO_jk, 17 dE/dBOpi_jk. False (and nothing added) for a collinear i-j-k or j-k-l.
+template <typename R>
+struct TorsBond {              // quantities of the central bond j-k shared by its torsions
+  R V1, V2, V3, pt1, pc1, pt2, pc2, BO2, xb, ex, g2, dg2, h2, df11, L2, l2;
+  Vec3<R> u2;
+  int j, k, ejk, code;
+};
+
+template <typename R>
+__device__ __forceinline__ void tors_bond(const Sys& s, const BondList& bl, const AtomQ& aq, const DParams<R>* P, int j,
+                                          int k, int ejk, TorsBond<R>& b) {
+  const R* bo = (const R*)bl.bo;
+  const R* bo_pi = (const R*)bl.bo_pi;
+  const int pt = s.type[j] * MAXT + s.type[k];
+  b.V1 = P->V1[pt]; b.V2 = P->V2[pt]; b.V3 = P->V3[pt]; b.pt1 = P->p_tor1[pt]; b.pc1 = P->p_cot1[pt];
+  b.pt2 = P->p_tor2; b.pc2 = P->p_cot2;
+  b.BO2 = bo[ejk];
+  const R BOpi2 = bo_pi[ejk];
+  R Dsum;
+  if constexpr (sizeof(R) == 4) Dsum = aq.dang_f[j] + aq.dang_f[k];
+  else Dsum = (R)(aq.dang[j] + aq.dang[k]);
+  R f11, df11;
+  f9fun<R>(P->p_tor3, P->p_tor4, Dsum, f11, df11);
+  b.df11 = df11;
+  b.xb = R(2) - BOpi2 - f11;
+  b.ex = m_exp(b.pt1 * b.xb * b.xb);
+  b.g2 = -m_expm1(-b.pt2 * b.BO2);
+  b.dg2 = b.pt2 * m_exp(-b.pt2 * b.BO2);
+  b.h2 = m_exp(-b.pc2 * (b.BO2 - R(1.5)) * (b.BO2 - R(1.5)));
+  b.u2 = load_vec<R>(bl, ejk);
+  b.L2 = dot3(b.u2, b.u2);
+  b.l2 = m_sqrt(b.L2);
+  b.j = j; b.k = k; b.ejk = ejk; b.code = bl.s[ejk];
+}
+
+template <typename R>
+__device__ __forceinline__ bool torsion_term(const Sys& s, const BondList& bl, const TorsBond<R>& b, R wt, R wcj,
+                                            int ea, int ec, int i, int l, R BO1, R BO3, R* v) {
+  const R V1 = b.V1, V2 = b.V2, V3 = b.V3, pt1 = b.pt1, pc1 = b.pc1, pt2 = b.pt2, pc2 = b.pc2;
+  const R BO2 = b.BO2, xb = b.xb, ex = b.ex, g2 = b.g2, dg2 = b.dg2, h2 = b.h2, df11 = b.df11;
+  const R L2 = b.L2, l2 = b.l2;
+  const Vec3<R> u2 = b.u2;
+  const Vec3<R> u1 = load_vec<R>(bl, ea), u3 = load_vec<R>(bl, ec);
+  // Well-conditioned torsion geometry: n1 = u1 x u2, n2 = u3 x u2, A = |n1|, B = |n2|,
+  // P = n1.n2, V = u3.n1 (L2 V^2 = A^2 B^2 - P^2), D0 = l1 l2^2 l3. Then
+  //   s1 s2 = A B / D0 = S,  s1 s2 cos w = P / D0 = C,  s1 s2 cos^3 w = P^3/(A^2 B^2 D0) = M,
+  //   s1 s2 (1 - cos^2 w) = V^2 / (A B l1 l3) = Y,
+  //   E_tors = f10 [V1 (S + C)/2 + V2 e Y + V3 (S + 4M - 3C)/2],  E_conj = K (1 - Y).
+  const Vec3<R> n1 = cross_acc(u1, u2), n2 = cross_acc(u3, u2);
+  const R A2 = dot3(n1, n1), B2 = dot3(n2, n2);
+  const R L1 = dot3(u1, u1), L3 = dot3(u3, u3);
+  const R l1 = m_sqrt(L1), l3 = m_sqrt(L3);
+  const R Am = m_sqrt(A2), Bm = m_sqrt(B2);
+  if (!(Am > R(1e-10) * l1 * l2 && Bm > R(1e-10) * l2 * l3)) return false;   // collinear: sin th ~ 0
+  const R Pn = dot3(n1, n2);
+  const R Vt = dot3(u3, n1);
+  const R D0 = l1 * L2 * l3;
+  const R cw = rclamp(Pn / (Am * Bm), R(-1), R(1));
+  const R S = Am * Bm / D0, Cc = Pn / D0, M = cw * cw * Cc, Y = Vt * Vt / (Am * Bm * l1 * l3);
+  // energy
+  const R g1 = -m_expm1(-pt2 * BO1), g3 = -m_expm1(-pt2 * BO3);
+  const R dg1 = pt2 * m_exp(-pt2 * BO1), dg3 = pt2 * m_exp(-pt2 * BO3);
+  const R f10 = g1 * g2 * g3;
+  const R Tsum = R(0.5) * V1 * (S + Cc) + V2 * ex * Y + R(0.5) * V3 * (S + R(4) * M - R(3) * Cc);
+  const R h1 = m_exp(-pc2 * (BO1 - R(1.5)) * (BO1 - R(1.5)));
+  const R h3 = m_exp(-pc2 * (BO3 - R(1.5)) * (BO3 - R(1.5)));
+  const R K = pc1 * h1 * h2 * h3;
+  const R et = f10 * Tsum;
+  const R ecj = K * (R(1) - Y);
+  v[4] += et;
+  v[5] += ecj;
+  // non-geometric derivatives
+  const R dBO1 = wt * dg1 * g2 * g3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO1 - R(1.5)));
+  const R dBO3 = wt * g1 * g2 * dg3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO3 - R(1.5)));
+  const R dBO2 = wt * g1 * dg2 * g3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO2 - R(1.5)));
+  const R dTdx = V2 * Y * ex * pt1 * R(2) * xb;   // d Tsum / d xb
+  const R dpi = wt * f10 * dTdx * R(-1);
+  const R dD = wt * f10 * dTdx * (-df11);
+  fix_add(bl.cdbo + ea, dBO1, s.err);
+  fix_add(bl.cdbo + ec, dBO3, s.err);
+  v[16] += dBO2;
+  v[17] += dpi;
+  v[3] += dD;
+  v[15] += dD;
+  // geometric derivatives through (A, B, P, V, l1, l2, l3)
+  const R dES = wt * f10 * R(0.5) * (V1 + V3);
+  const R dEC = wt * f10 * (R(0.5) * V1 - R(1.5) * V3);
+  const R dEM = wt * f10 * R(2) * V3;
+  const R dEY = wt * f10 * V2 * ex - wcj * K;
+  const R gA = (dES * S - R(2) * dEM * M - dEY * Y) / Am;
+  const R gB = (dES * S - R(2) * dEM * M - dEY * Y) / Bm;
+  const R gP = (dEC + dEM * R(3) * cw * cw) / D0;
+  const R gV = dEY * R(2) * Vt / (Am * Bm * l1 * l3);
+  const R T0 = dES * S + dEC * Cc + dEM * M;
+  const R gl1 = -(T0 + dEY * Y) / L1;             // per unit of u1 (d l1 / d u1 = u1 / l1)
+  const R gl2 = R(-2) * T0 / L2;
+  const R gl3 = -(T0 + dEY * Y) / L3;
+  const R iA = gA / Am, iB = gB / Bm;
+  // dA/du1 = (u2 x n1)/A, dA/du2 = (n1 x u1)/A, dB/du3 = (u2 x n2)/B, dB/du2 = (n2 x u3)/B
+  // dP/du1 = u2 x n2, dP/du2 = n2 x u1 + n1 x u3, dP/du3 = u2 x n1
+  // dV/du1 = u2 x u3, dV/du2 = u3 x u1, dV/du3 = n1
+  const Vec3<R> u2n1 = cross3(u2, n1), u2n2 = cross3(u2, n2), u2u3 = cross3(u2, u3);
+  const Vec3<R> n1u1 = cross3(n1, u1), n2u3 = cross3(n2, u3), n2u1 = cross3(n2, u1), n1u3 = cross3(n1, u3);
+  const Vec3<R> u3u1 = cross3(u3, u1);
+  Vec3<R> gg1, gg2, gg3;
+  gg1.x = iA * u2n1.x + gP * u2n2.x + gV * u2u3.x + gl1 * u1.x;
+  gg1.y = iA * u2n1.y + gP * u2n2.y + gV * u2u3.y + gl1 * u1.y;
+  gg1.z = iA * u2n1.z + gP * u2n2.z + gV * u2u3.z + gl1 * u1.z;
+  gg2.x = iA * n1u1.x + iB * n2u3.x + gP * (n2u1.x + n1u3.x) + gV * u3u1.x + gl2 * u2.x;
+  gg2.y = iA * n1u1.y + iB * n2u3.y + gP * (n2u1.y + n1u3.y) + gV * u3u1.y + gl2 * u2.y;
+  gg2.z = iA * n1u1.z + iB * n2u3.z + gP * (n2u1.z + n1u3.z) + gV * u3u1.z + gl2 * u2.z;
+  gg3.x = iB * u2n2.x + gP * u2n1.x + gV * n1.x + gl3 * u3.x;
+  gg3.y = iB * u2n2.y + gP * u2n1.y + gV * n1.y + gl3 * u3.y;
+  gg3.z = iB * u2n2.z + gP * u2n1.z + gV * n1.z + gl3 * u3.z;
+  force_add<R>(s, i, -gg1.x, -gg1.y, -gg1.z);
+  force_add<R>(s, l, -gg3.x, -gg3.y, -gg3.z);
+  v[0] += gg1.x + gg2.x; v[1] += gg1.y + gg2.y; v[2] += gg1.z + gg2.z;
+  v[12] += gg3.x - gg2.x; v[13] += gg3.y - gg2.y; v[14] += gg3.z - gg2.z;
+  vir_sub(v + 6, gg1, u1);
+  vir_sub(v + 6, gg2, u2);
+  vir_sub(v + 6, gg3, u3);
+  return true;
+}
+
 template <typename R, int TG>
 __global__ void __launch_bounds__(128) k_torsions(Sys s, BondList bl, AtomQ aq, Accum acc,
                                                    const DParams<R>* __restrict__ P, unsigned mask) {
@@ -579,23 +707,9 @@ __global__ void __launch_bounds__(128) k_torsions(Sys s, BondList bl, AtomQ aq, 
 #pragma unroll
     for (int q = 0; q < NV; ++q) v[q] = R(0);
     if (ntot > 0) {
-      const int tj = s.type[j], tk = s.type[k];
-      const int pt = tj * MAXT + tk;
-      const R V1 = P->V1[pt], V2 = P->V2[pt], V3 = P->V3[pt], pt1 = P->p_tor1[pt], pc1 = P->p_cot1[pt];
-      const R pt2 = P->p_tor2, pc2 = P->p_cot2;
-      const R BO2 = bo[ejk];
-      const R BOpi2 = bo_pi[ejk];
-      R Dsum;
-      if constexpr (sizeof(R) == 4) Dsum = aq.dang_f[j] + aq.dang_f[k];
-      else Dsum = (R)(aq.dang[j] + aq.dang[k]);
-      R f11, df11;
-      f9fun<R>(P->p_tor3, P->p_tor4, Dsum, f11, df11);
-      const R xb = R(2) - BOpi2 - f11;
-      const R ex = m_exp(pt1 * xb * xb);
-      const R g2 = -m_expm1(-pt2 * BO2), dg2 = pt2 * m_exp(-pt2 * BO2);
-      const R h2 = m_exp(-pc2 * (BO2 - R(1.5)) * (BO2 - R(1.5)));
-      const Vec3<R> u2 = load_vec<R>(bl, ejk);
-      const R L2 = dot3(u2, u2), l2 = m_sqrt(L2);
+      TorsBond<R> tb;
+      tors_bond<R>(s, bl, aq, P, j, k, ejk, tb);
+      const R BO2 = tb.BO2;
       int sjk[3];
       shift_decode(codejk, sjk[0], sjk[1], sjk[2]);
       for (int p = sub; p < ntot; p += TG) {
@@ -612,85 +726,7 @@ __global__ void __launch_bounds__(128) k_torsions(Sys s, BondList bl, AtomQ aq, 
         }
         const R BO1 = bo[ea], BO3 = bo[ec];
         if (!(BO1 * BO2 * BO3 > P->thb_cut)) continue;
-        const Vec3<R> u1 = load_vec<R>(bl, ea), u3 = load_vec<R>(bl, ec);
-        // Well-conditioned torsion geometry: n1 = u1 x u2, n2 = u3 x u2, A = |n1|, B = |n2|,
-        // P = n1.n2, V = u3.n1 (L2 V^2 = A^2 B^2 - P^2), D0 = l1 l2^2 l3. Then
-        //   s1 s2 = A B / D0 = S,  s1 s2 cos w = P / D0 = C,  s1 s2 cos^3 w = P^3/(A^2 B^2 D0) = M,
-        //   s1 s2 (1 - cos^2 w) = V^2 / (A B l1 l3) = Y,
-        //   E_tors = f10 [V1 (S + C)/2 + V2 e Y + V3 (S + 4M - 3C)/2],  E_conj = K (1 - Y).
-        const Vec3<R> n1 = cross_acc(u1, u2), n2 = cross_acc(u3, u2);
-        const R A2 = dot3(n1, n1), B2 = dot3(n2, n2);
-        const R L1 = dot3(u1, u1), L3 = dot3(u3, u3);
-        const R l1 = m_sqrt(L1), l3 = m_sqrt(L3);
-        const R Am = m_sqrt(A2), Bm = m_sqrt(B2);
-        if (!(Am > R(1e-10) * l1 * l2 && Bm > R(1e-10) * l2 * l3)) continue;   // collinear: sin th ~ 0
-        const R Pn = dot3(n1, n2);
-        const R Vt = dot3(u3, n1);
-        const R D0 = l1 * L2 * l3;
-        const R cw = rclamp(Pn / (Am * Bm), R(-1), R(1));
-        const R S = Am * Bm / D0, Cc = Pn / D0, M = cw * cw * Cc, Y = Vt * Vt / (Am * Bm * l1 * l3);
-        // energy
-        const R g1 = -m_expm1(-pt2 * BO1), g3 = -m_expm1(-pt2 * BO3);
-        const R dg1 = pt2 * m_exp(-pt2 * BO1), dg3 = pt2 * m_exp(-pt2 * BO3);
-        const R f10 = g1 * g2 * g3;
-        const R Tsum = R(0.5) * V1 * (S + Cc) + V2 * ex * Y + R(0.5) * V3 * (S + R(4) * M - R(3) * Cc);
-        const R h1 = m_exp(-pc2 * (BO1 - R(1.5)) * (BO1 - R(1.5)));
-        const R h3 = m_exp(-pc2 * (BO3 - R(1.5)) * (BO3 - R(1.5)));
-        const R K = pc1 * h1 * h2 * h3;
-        const R et = f10 * Tsum;
-        const R ecj = K * (R(1) - Y);
-        v[4] += et;
-        v[5] += ecj;
-        // non-geometric derivatives
-        const R dBO1 = wt * dg1 * g2 * g3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO1 - R(1.5)));
-        const R dBO3 = wt * g1 * g2 * dg3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO3 - R(1.5)));
-        const R dBO2 = wt * g1 * dg2 * g3 * Tsum + wcj * ecj * (R(-2) * pc2 * (BO2 - R(1.5)));
-        const R dTdx = V2 * Y * ex * pt1 * R(2) * xb;   // d Tsum / d xb
-        const R dpi = wt * f10 * dTdx * R(-1);
-        const R dD = wt * f10 * dTdx * (-df11);
-        fix_add(bl.cdbo + ea, dBO1, s.err);
-        fix_add(bl.cdbo + ec, dBO3, s.err);
-        v[16] += dBO2;
-        v[17] += dpi;
-        v[3] += dD;
-        v[15] += dD;
-        // geometric derivatives through (A, B, P, V, l1, l2, l3)
-        const R dES = wt * f10 * R(0.5) * (V1 + V3);
-        const R dEC = wt * f10 * (R(0.5) * V1 - R(1.5) * V3);
-        const R dEM = wt * f10 * R(2) * V3;
-        const R dEY = wt * f10 * V2 * ex - wcj * K;
-        const R gA = (dES * S - R(2) * dEM * M - dEY * Y) / Am;
-        const R gB = (dES * S - R(2) * dEM * M - dEY * Y) / Bm;
-        const R gP = (dEC + dEM * R(3) * cw * cw) / D0;
-        const R gV = dEY * R(2) * Vt / (Am * Bm * l1 * l3);
-        const R T0 = dES * S + dEC * Cc + dEM * M;
-        const R gl1 = -(T0 + dEY * Y) / L1;             // per unit of u1 (d l1 / d u1 = u1 / l1)
-        const R gl2 = R(-2) * T0 / L2;
-        const R gl3 = -(T0 + dEY * Y) / L3;
-        const R iA = gA / Am, iB = gB / Bm;
-        // dA/du1 = (u2 x n1)/A, dA/du2 = (n1 x u1)/A, dB/du3 = (u2 x n2)/B, dB/du2 = (n2 x u3)/B
-        // dP/du1 = u2 x n2, dP/du2 = n2 x u1 + n1 x u3, dP/du3 = u2 x n1
-        // dV/du1 = u2 x u3, dV/du2 = u3 x u1, dV/du3 = n1
-        const Vec3<R> u2n1 = cross3(u2, n1), u2n2 = cross3(u2, n2), u2u3 = cross3(u2, u3);
-        const Vec3<R> n1u1 = cross3(n1, u1), n2u3 = cross3(n2, u3), n2u1 = cross3(n2, u1), n1u3 = cross3(n1, u3);
-        const Vec3<R> u3u1 = cross3(u3, u1);
-        Vec3<R> gg1, gg2, gg3;
-        gg1.x = iA * u2n1.x + gP * u2n2.x + gV * u2u3.x + gl1 * u1.x;
-        gg1.y = iA * u2n1.y + gP * u2n2.y + gV * u2u3.y + gl1 * u1.y;
-        gg1.z = iA * u2n1.z + gP * u2n2.z + gV * u2u3.z + gl1 * u1.z;
-        gg2.x = iA * n1u1.x + iB * n2u3.x + gP * (n2u1.x + n1u3.x) + gV * u3u1.x + gl2 * u2.x;
-        gg2.y = iA * n1u1.y + iB * n2u3.y + gP * (n2u1.y + n1u3.y) + gV * u3u1.y + gl2 * u2.y;
-        gg2.z = iA * n1u1.z + iB * n2u3.z + gP * (n2u1.z + n1u3.z) + gV * u3u1.z + gl2 * u2.z;
-        gg3.x = iB * u2n2.x + gP * u2n1.x + gV * n1.x + gl3 * u3.x;
-        gg3.y = iB * u2n2.y + gP * u2n1.y + gV * n1.y + gl3 * u3.y;
-        gg3.z = iB * u2n2.z + gP * u2n1.z + gV * n1.z + gl3 * u3.z;
-        force_add<R>(s, i, -gg1.x, -gg1.y, -gg1.z);
-        force_add<R>(s, l, -gg3.x, -gg3.y, -gg3.z);
-        v[0] += gg1.x + gg2.x; v[1] += gg1.y + gg2.y; v[2] += gg1.z + gg2.z;
-        v[12] += gg3.x - gg2.x; v[13] += gg3.y - gg2.y; v[14] += gg3.z - gg2.z;
-        vir_sub(v + 6, gg1, u1);
-        vir_sub(v + 6, gg2, u2);
-        vir_sub(v + 6, gg3, u3);
+        if (!torsion_term<R>(s, bl, tb, wt, wcj, ea, ec, i, l, BO1, BO3, v)) continue;
       }
     }
     // group totals (all lanes take part: the shuffles span the whole warp), then lane q of
@@ -725,6 +761,121 @@ __global__ void __launch_bounds__(128) k_torsions(Sys s, BondList bl, AtomQ aq, 
         if (dst) GroupSum<R, TG>::add(dst, h, l, s.err);
       }
     }
+  }
+}
+
+// Mixed path, candidate compaction: a warp takes NB = 32 / TG central bonds per pass; the TG
+// lanes of each group test their bond's (i, l) candidates with the cheap threshold and the
+// passing ones are appended (ballot order) to a per-warp queue in shared memory; whenever 32
+// are queued all lanes evaluate one each (torsion_term), so the heavy arithmetic runs on full
+// warps instead of on the ~40 % of lanes whose candidate passed. A lane adds its term's
+// contributions to the central bond's atoms and entries directly to the global 2^-32 fixed-
+// point accumulators (integer atomics without a return value: exact, so their order does not
+// matter and the sums are deterministic; no per-bond pre-sum is needed).
+template <int TG>
+__global__ void __launch_bounds__(128) k_torsions_q(Sys s, BondList bl, AtomQ aq, Accum acc,
+                                                     const DParams<float>* __restrict__ P, unsigned mask) {
+  constexpr int NB = 32 / TG, NV = 18, QCAP = 64, WPB = 4;
+  __shared__ TorsBond<float> sb[WPB][NB];
+  __shared__ int4 sq[WPB][QCAP];
+  __shared__ int sslot[WPB][QCAP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int sub = lane & (TG - 1), g = lane / TG;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int ncanon = *bl.ncanon;
+  const float* bo = (const float*)bl.bo;
+  const float wt = wbit<float>(mask, T_TORS), wcj = wbit<float>(mask, T_CONJ);
+  const float thb = P->thb_cut;
+  const unsigned below = (1u << lane) - 1u;
+
+  auto batch = [&](int nact) {
+    if (lane < nact) {
+      const int4 e = sq[w][lane];
+      const int gg = sslot[w][lane];
+      float v[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) v[q] = 0.f;
+      if (torsion_term<float>(s, bl, sb[w][gg], wt, wcj, e.x, e.y, e.z, e.w, bo[e.x], bo[e.y], v)) {
+        const int bj = sb[w][gg].j, bk = sb[w][gg].k, be = sb[w][gg].ejk;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          unsigned long long* dst;
+          if (c < 3) dst = (c == 0 ? s.fx : c == 1 ? s.fy : s.fz) + bj;
+          else if (c == 3) dst = aq.cddelta + bj;
+          else if (c < 6) dst = acc.efx + (size_t)(c - 4) * s.n + bj;
+          else if (c < 12) dst = acc.vfx + (size_t)(c - 6) * s.n + bj;
+          else if (c < 15) dst = (c == 12 ? s.fx : c == 13 ? s.fy : s.fz) + bk;
+          else if (c == 15) dst = aq.cddelta + bk;
+          else if (c == 16) dst = bl.cdbo + be;
+          else dst = bl.cdbopi + be;
+          fix_add(dst, v[c], s.err);
+        }
+      }
+    }
+    __syncwarp();
+  };
+
+  for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * NB; base < ncanon; base += nwarps * NB) {
+    const int t = base + g;
+    int j = 0, k = 0, ejk = 0, ekj = 0, nbk = 0, ntot = 0;
+    if (t < ncanon) {
+      ejk = bl.canon[t];
+      j = ejk / bl.cap;
+      k = bl.j[ejk];
+      const int nbj = bl.cnt[j];
+      nbk = bl.cnt[k];
+      ekj = bl.mirror[ejk];
+      if (nbj >= 2 && nbk >= 2 && ekj / bl.cap == k && bo[ejk] > thb) ntot = (nbj - 1) * (nbk - 1);
+    }
+    if (ntot > 0 && sub == 0) tors_bond<float>(s, bl, aq, P, j, k, ejk, sb[w][g]);
+    __syncwarp();
+    const float BO2 = ntot > 0 ? bo[ejk] : 0.f;
+    int sjk[3] = {0, 0, 0};
+    if (ntot > 0) shift_decode(bl.s[ejk], sjk[0], sjk[1], sjk[2]);
+    const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)((ntot + TG - 1) / TG));
+    int qn = 0;
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int p = rd * TG + sub;
+      bool pass = false;
+      int ea = 0, ec = 0, i = 0, l = 0;
+      if (p < ntot) {
+        const int ia = p / (nbk - 1), ic = p % (nbk - 1);
+        ea = j * bl.cap + ia + (j * bl.cap + ia >= ejk ? 1 : 0);
+        ec = k * bl.cap + ic;
+        if (ec >= ekj) ++ec;
+        i = bl.j[ea];
+        l = bl.j[ec];
+        pass = true;
+        if (i == l) {
+          int si[3], sl[3];
+          shift_decode(bl.s[ea], si[0], si[1], si[2]);
+          shift_decode(bl.s[ec], sl[0], sl[1], sl[2]);
+          if (si[0] == sjk[0] + sl[0] && si[1] == sjk[1] + sl[1] && si[2] == sjk[2] + sl[2]) pass = false;
+        }
+        if (pass) pass = bo[ea] * BO2 * bo[ec] > thb;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (pass) {
+        const int pos = qn + __popc(m & below);
+        sq[w][pos] = make_int4(ea, ec, i, l);
+        sslot[w][pos] = g;
+      }
+      qn += __popc(m);
+      __syncwarp();
+      if (qn >= 32) {
+        batch(32);
+        const int left = qn - 32;
+        int4 e = make_int4(0, 0, 0, 0);
+        int gs = 0;
+        if (lane < left) { e = sq[w][32 + lane]; gs = sslot[w][32 + lane]; }
+        __syncwarp();
+        if (lane < left) { sq[w][lane] = e; sslot[w][lane] = gs; }
+        __syncwarp();
+        qn = left;
+      }
+    }
+    if (qn > 0) batch(qn);
+    __syncwarp();
   }
 }
 
@@ -876,9 +1027,15 @@ void torsions(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DPar
   // systems: the grid covers n central bonds in one pass and loops beyond that
   const int tg = L.t().tors_lanes;
   const unsigned grid = grid_for((long long)s.n * tg, 128);
-  if (tg == 2) k_torsions<R, 2><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
-  else if (tg == 8) k_torsions<R, 8><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
-  else k_torsions<R, 4><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
+  if constexpr (sizeof(R) == 4) {
+    if (tg == 2) k_torsions_q<2><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
+    else if (tg == 8) k_torsions_q<8><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
+    else k_torsions_q<4><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
+  } else {
+    if (tg == 2) k_torsions<R, 2><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
+    else if (tg == 8) k_torsions<R, 8><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
+    else k_torsions<R, 4><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
+  }
   *L.count += 1;
 }
 template <typename R>
