@@ -1951,6 +1951,8 @@ template <typename R> void tune_all(reaxff_ctx* ctx) {
   };
   pick(T.tors_lanes, {2, 4, 8}, [&] { rx::torsions<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); });
   pick(T.nb_block, {128, 256, 512}, [&] { rx::nonbonded<R>(L, ctx->sys, ctx->far, ctx->acc, P, ctx->mask); });
+  if (!ctx->fp64)
+    pick(T.ang_lanes, {8, 16, 32}, [&] { rx::angles<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); });
   pick(T.ang_block, {64, 128, 256}, [&] { rx::angles<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); });
   pick(T.hb_block, {64, 128, 256}, [&] { rx::hbonds<R>(L, ctx->sys, ctx->bond, ctx->hb, ctx->acc, P, ctx->mask); });
   if (ctx->use_skin)
@@ -1988,8 +1990,8 @@ int reaxff_autotune(reaxff_ctx* ctx, const char* cache_path, int32_t* schedule) 
       while (fgets(line, sizeof(line), f)) {
         rx::Tune t{};
         char k[256];
-        if (sscanf(line, "reaxff-tune %255[^|]| tors=%d nb=%d cf=%d bl=%d ang=%d hb=%d", k, &t.tors_lanes, &t.nb_block,
-                   &t.cf_block, &t.bl_block, &t.ang_block, &t.hb_block) == 7 &&
+        if (sscanf(line, "reaxff-tune %255[^|]| tors=%d nb=%d cf=%d bl=%d ang=%d hb=%d angl=%d", k, &t.tors_lanes,
+                   &t.nb_block, &t.cf_block, &t.bl_block, &t.ang_block, &t.hb_block, &t.ang_lanes) == 8 &&
             key == std::string(k).substr(0, std::string(k).find_last_not_of(' ') + 1)) {
           ctx->tune = t;
           found = true;
@@ -2009,8 +2011,8 @@ int reaxff_autotune(reaxff_ctx* ctx, const char* cache_path, int32_t* schedule) 
     if (cache_path) {
       if (FILE* f = fopen(cache_path, "a")) {
         const rx::Tune& t = ctx->tune;
-        fprintf(f, "reaxff-tune %s | tors=%d nb=%d cf=%d bl=%d ang=%d hb=%d\n", key.c_str(), t.tors_lanes, t.nb_block,
-                t.cf_block, t.bl_block, t.ang_block, t.hb_block);
+        fprintf(f, "reaxff-tune %s | tors=%d nb=%d cf=%d bl=%d ang=%d hb=%d angl=%d\n", key.c_str(), t.tors_lanes,
+                t.nb_block, t.cf_block, t.bl_block, t.ang_block, t.hb_block, t.ang_lanes);
         fclose(f);
       }
     }
@@ -2018,8 +2020,8 @@ int reaxff_autotune(reaxff_ctx* ctx, const char* cache_path, int32_t* schedule) 
   drop_graph(ctx);                                              // schedules are baked into the graph
   if (schedule) {
     const rx::Tune& t = ctx->tune;
-    const int v[6] = {t.tors_lanes, t.nb_block, t.cf_block, t.bl_block, t.ang_block, t.hb_block};
-    for (int q = 0; q < 6; ++q) schedule[q] = v[q];
+    const int v[7] = {t.tors_lanes, t.nb_block, t.cf_block, t.bl_block, t.ang_block, t.hb_block, t.ang_lanes};
+    for (int q = 0; q < 7; ++q) schedule[q] = v[q];
   }
   return REAXFF_OK;
 }

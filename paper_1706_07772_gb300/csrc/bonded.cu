@@ -547,6 +547,160 @@ template <int TG> struct GroupSum<double, TG> {
   }
 };
 
+// Mixed path with G lanes per centre atom (32 / G centres per warp): molecular centres have
+// few bond pairs (about 9 at this density, half passing the thresholds), so a whole warp per
+// centre would leave most lanes idle. The group's float-float totals come from group
+// butterflies; lane q of the group then converts and stores totals q, q + G, ...
+template <int G>
+__global__ void k_angles_g(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<float>* __restrict__ P,
+                           unsigned mask) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = gt / G;
+  const int lane = threadIdx.x & 31, sub = lane & (G - 1);
+  // no early exit: the group butterflies below span the whole warp
+  const int nb = j < s.n ? bl.cnt[j] : 0;
+  const bool act = nb >= 2;
+  const int jj = act ? j : 0;
+  const int tj = s.type[jj];
+  const float* bo = (const float*)bl.bo;
+  const float dang = (float)aq.dang[jj], delta = (float)aq.delta[jj];
+  const float sbo2 = (float)aq.sbo2[jj];
+  const float wv = wbit<float>(mask, T_VAL), wp = wbit<float>(mask, T_PEN), wc = wbit<float>(mask, T_COA);
+  const float pv5 = P->p_val5[tj];
+  const float e6 = m_expc(P->p_val6 * dang);
+  const float ex2 = m_exp(-P->p_val10 * (2.0f - sbo2));
+  const float dth0_dsbo2 = ex2 * P->p_val10;
+  float f9, df9;
+  f9fun<float>(P->p_pen3, P->p_pen4, delta, f9, df9);
+  float scoa, scoad;
+  sig_pair<float>(P->p_coa2 * dang, scoa, scoad);
+  float l_eval = 0, l_epen = 0, l_ecoa = 0, l_cdsbo = 0, l_cdd = 0;
+  float l_fj[3] = {0, 0, 0}, l_w[6] = {0, 0, 0, 0, 0, 0};
+  const int npair = act ? nb * (nb - 1) / 2 : 0;
+  for (int p = sub; p < npair; p += G) {
+    int a = 0, rem = p;
+    while (rem >= nb - 1 - a) { rem -= nb - 1 - a; ++a; }
+    const int b = a + 1 + rem;
+    const int ea = j * bl.cap + a, eb = j * bl.cap + b;
+    const float BOa = bo[ea], BOb = bo[eb];
+    if (!(BOa > P->thb_cut && BOb > P->thb_cut && BOa * BOb > P->thb_cutsq)) continue;
+    const int i = bl.j[ea], k = bl.j[eb];
+    const int ti = s.type[i], tk = s.type[k];
+    const int t3 = (ti * MAXT + tj) * MAXT + tk;
+    const Vec3<float> u = load_vec<float>(bl, ea), v = load_vec<float>(bl, eb);
+    const float L1 = dot3(u, u), L2 = dot3(v, v);
+    // theta = atan2(|u x v|, u.v): accurate at every angle; d theta/du = (u x n^)/|u|^2,
+    // d theta/dv = (n^ x v)/|v|^2 with n^ = (u x v)/|u x v|
+    const Vec3<float> nrm = cross_acc(u, v);
+    const float nn = m_sqrt(dot3(nrm, nrm));
+    const float th = m_atan2(nn, dot3(u, v));
+    const bool cok = nn > float(0);
+    // valence
+    const float th00 = P->th00[t3];
+    const float th0 = float(3.14159265358979323846) - th00 * (float(1) - ex2);
+    const float pv3 = P->p_val3[tj], pv4 = P->p_val4[t3];
+    const float pa = m_pow(BOa, pv4), pb = m_pow(BOb, pv4);
+    const float ea7 = m_exp(-pv3 * pa), eb7 = m_exp(-pv3 * pb);
+    const float f7a = -m_expm1(-pv3 * pa), f7b = -m_expm1(-pv3 * pb);
+    const float df7a = ea7 * pv3 * pv4 * pa / BOa, df7b = eb7 * pv3 * pv4 * pb / BOb;
+    // f8 = pv5 - (pv5 - 1)(2 + e6)/(1 + e6 + e7); with u = e6/den, v = e7/den:
+    // d[(2 + e6)/den]/dDang = (2 p7 v - p6 u)/den + (p6 + p7) u v
+    const float p7 = P->p_val7[t3];
+    const float e7 = m_expc(-p7 * dang);
+    const float den8 = float(1) + e6 + e7;
+    const float u8 = e6 / den8, v8 = e7 / den8;
+    const float f8 = pv5 - (pv5 - float(1)) * (float(2) / den8 + u8);
+    const float df8 = -(pv5 - float(1)) * ((float(2) * p7 * v8 - P->p_val6 * u8) / den8 + (P->p_val6 + p7) * u8 * v8);
+    const float pv1 = P->p_val1[t3], pv2 = P->p_val2[t3];
+    const float D = th0 - th;
+    const float exv = m_exp(-pv2 * D * D);
+    const float gth = -m_expm1(-pv2 * D * D);
+    const float Cv = f7a * f7b * f8 * pv1;
+    const float ev = Cv * gth;
+    const float dEdD = Cv * exv * float(2) * pv2 * D;          // d/dD of Cv (1 - e^{-pv2 D^2})
+    const float dEv_dth = -dEdD;
+    const float dEv_dsbo2 = dEdD * th00 * dth0_dsbo2;
+    // penalty
+    const float pp2 = P->p_pen2;
+    const float ga = m_exp(-pp2 * (BOa - float(2)) * (BOa - float(2))), gb = m_exp(-pp2 * (BOb - float(2)) * (BOb - float(2)));
+    const float ep = P->p_pen1[t3] * f9 * ga * gb;
+    // coalition
+    const float sbi = aq.sumbo_f[i] - BOa;
+    const float sbk = aq.sumbo_f[k] - BOb;
+    const float pc3 = P->p_coa3, pc4 = P->p_coa4;
+    const float ec = P->p_coa1[t3] * scoa * m_exp(-pc3 * sbi * sbi) * m_exp(-pc3 * sbk * sbk) *
+                 m_exp(-pc4 * (BOa - float(1.5)) * (BOa - float(1.5))) * m_exp(-pc4 * (BOb - float(1.5)) * (BOb - float(1.5)));
+    l_eval += ev;
+    l_epen += ep;
+    l_ecoa += ec;
+    // bond-order and Delta derivatives
+    const float dBOa = wv * df7a * f7b * f8 * pv1 * gth + wp * ep * (float(-2) * pp2 * (BOa - float(2))) +
+                   wc * ec * (float(2) * pc3 * sbi - float(2) * pc4 * (BOa - float(1.5)));
+    const float dBOb = wv * f7a * df7b * f8 * pv1 * gth + wp * ep * (float(-2) * pp2 * (BOb - float(2))) +
+                   wc * ec * (float(2) * pc3 * sbk - float(2) * pc4 * (BOb - float(1.5)));
+    fix_add(bl.cdbo + ea, dBOa, s.err);
+    fix_add(bl.cdbo + eb, dBOb, s.err);
+    fix_add(aq.cddelta + i, wc * ec * (float(-2) * pc3 * sbi), s.err);
+    fix_add(aq.cddelta + k, wc * ec * (float(-2) * pc3 * sbk), s.err);
+    l_cdd += wv * f7a * f7b * df8 * pv1 * gth + wp * P->p_pen1[t3] * df9 * ga * gb +
+             wc * (scoa > float(0) ? -ec * P->p_coa2 * scoad / scoa : float(0));
+    l_cdsbo += wv * dEv_dsbo2;
+    // geometry: E depends on cos(theta) only through the valence term
+    if (cok) {
+      const float gt = wv * dEv_dth / nn;
+      const Vec3<float> cu = cross3(u, nrm), cv = cross3(nrm, v);
+      const Vec3<float> gu = Vec3<float>{gt * cu.x / L1, gt * cu.y / L1, gt * cu.z / L1};
+      const Vec3<float> gv = Vec3<float>{gt * cv.x / L2, gt * cv.y / L2, gt * cv.z / L2};
+      force_add<float>(s, i, -gu.x, -gu.y, -gu.z);
+      force_add<float>(s, k, -gv.x, -gv.y, -gv.z);
+      l_fj[0] += gu.x + gv.x; l_fj[1] += gu.y + gv.y; l_fj[2] += gu.z + gv.z;
+      vir_sub(l_w, gu, u);
+      vir_sub(l_w, gv, v);
+    }
+  }
+  constexpr int NVA = 14;   // 0-2 E_val, E_pen, E_coa; 3-5 F_j; 6-11 virial; 12 dE/dSBO2; 13 dE/dDelta
+  float hi[NVA] = {l_eval, l_epen, l_ecoa, l_fj[0], l_fj[1], l_fj[2], l_w[0], l_w[1], l_w[2], l_w[3], l_w[4],
+                   l_w[5], l_cdsbo, l_cdd};
+  float lo[NVA];
+#pragma unroll
+  for (int q = 0; q < NVA; ++q) {
+    lo[q] = 0.0f;
+    GroupSum<float, G>::run(hi[q], lo[q]);
+  }
+  if (!act) return;
+  const double cdsbo = ((double)hi[12] + (double)lo[12]) * aq.dsbo2[j];   // dE/dSBO
+  const double prod = aq.prodexp[j];
+#pragma unroll
+  for (int rnd = 0; rnd < (NVA + G - 1) / G; ++rnd) {
+    const int q = sub + rnd * G;
+    float h, l;
+    lane_pick<NVA>(hi, lo, q, h, l);
+    const double d = (double)h + (double)l;
+    if (q < 3) {
+      acc.e[(T_VAL + q) * s.n + j] = d;
+    } else if (q < 6) {
+      fix_add_ff((q == 3 ? s.fx : q == 4 ? s.fy : s.fz) + j, h, l, s.err);
+    } else if (q < 12) {
+      acc.vir[(q - 6) * s.n + j] += d;
+    } else if (q == 13) {
+      const double dsbo_dsum = -(1.0 - prod) * (1.0 + (double)P->p_val8 * aq.dnlp[j]);
+      fix_add(aq.cddelta + j, d + cdsbo * dsbo_dsum, s.err);
+    }
+  }
+  // SBO depends on every bond of j: distribute dE/dSBO over j's row (FP32 terms)
+  if (cdsbo != 0.0) {
+    const float cf = (float)cdsbo, pf = (float)prod, ff = (float)aq.sbo_fac[j];
+    for (int k = sub; k < nb; k += G) {
+      const int e = j * bl.cap + k;
+      const float b = bo[e];
+      const float b2 = b * b, b4 = b2 * b2;
+      fix_add(bl.cdbopi + e, cf, s.err);
+      fix_add(bl.cdbopp + e, cf, s.err);
+      fix_add(bl.cdbo + e, cf * pf * 8.0f * b4 * b2 * b * ff, s.err);
+    }
+  }
+}
+
 // One torsion + conjugation term (i-j-k-l over the central bond j-k, Sec. 3.3 "4-body"):
 // energies and the derivatives with respect to BO_ij, BO_kl (fixed-point atomics on the bond
 // entries), forces on i and l (atomics), and the contributions to the central bond's totals in
@@ -1018,7 +1172,15 @@ template <typename R> void s_gather(const Launch& L, Sys s, BondList b, AtomQ a)
 template <typename R>
 void angles(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P, unsigned mask) {
   const int bs = L.t().ang_block;
-  k_angles<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, b, a, acc, P, mask);
+  const int g = L.t().ang_lanes;
+  if constexpr (sizeof(R) == 4) {
+    const unsigned grid = grid_for((long long)s.n * g, bs);
+    if (g == 8) k_angles_g<8><<<grid, bs, 0, L.st>>>(s, b, a, acc, P, mask);
+    else if (g == 16) k_angles_g<16><<<grid, bs, 0, L.st>>>(s, b, a, acc, P, mask);
+    else k_angles_g<32><<<grid, bs, 0, L.st>>>(s, b, a, acc, P, mask);
+  } else {
+    k_angles<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, b, a, acc, P, mask);
+  }
   *L.count += 1;
 }
 template <typename R>

@@ -479,7 +479,8 @@ struct Tune {
   int nb_block = 256;          // threads per block: nonbonded (warp per atom)
   int cf_block = 256;          //   candidate filter (warp per atom)
   int bl_block = 256;          //   bond list (warp per atom)
-  int ang_block = 128;         //   angles (warp per centre)
+  int ang_block = 128;         //   angles
+  int ang_lanes = 8;           // lanes per centre atom in the angle kernel (8, 16, 32; mixed path)
   int hb_block = 128;          //   H-bonds (warp per hydrogen)
 };
 struct Launch {

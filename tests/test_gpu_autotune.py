@@ -21,6 +21,7 @@ def test_autotune_schedule_and_cache(params, tmp_path, prec):
     sch = c.autotune(cache)
     assert sch[0] in (2, 4, 8) and sch[1] in (128, 256, 512) and sch[2] in (128, 256, 512)
     assert sch[3] in (128, 256, 512) and sch[4] in (64, 128, 256) and sch[5] in (64, 128, 256)
+    assert sch[6] in (8, 16, 32)
     F1, E1, _ = c.forces(q=q)
     rms = np.sqrt((F0 ** 2).mean())
     assert np.abs(F1 - F0).max() < (1e-12 if prec == 0 else 1e-6) * rms
