@@ -397,8 +397,9 @@ def learned_warm_start(P, a):
 
 
 def solver_variants(P, a, steps=50):
-    """QEq preconditioners on the benchmark crystal at the same tolerance: Jacobi (the
-    paper's M = diag(H)) and block Jacobi over 32 consecutive atoms. Per variant: cold-start
+    """QEq solver variants on the benchmark crystal at the same tolerance: Jacobi (the
+    paper's M = diag(H)) and block Jacobi over 32 consecutive atoms, both with the
+    least-squares initial guess, and Jacobi with Lagrange extrapolation. Per variant: cold-start
     iterations (no solution history), then over `steps` MD steps with the extrapolated
     start: SpMVs per step (each one read of H for both systems), the bytes the solve moves
     per step (H entries 8 B per SpMV; for block Jacobi also 128 B per atom per
@@ -412,8 +413,9 @@ def solver_variants(P, a, steps=50):
     st = torch.cuda.current_stream()
     et = torch.zeros(steps, dtype=torch.float64, device="cuda")
     out, qs = {}, {}
-    for name, pc in (("jacobi", rx.PRECOND_JACOBI), ("block32", rx.PRECOND_BLOCK32)):
-        c = rx.ReaxFF(P, w["types"], w["box"], w["options"], precision=rx.MIXED, qeq_precond=pc)
+    for name, pc, ws in (("jacobi", rx.PRECOND_JACOBI, rx.WARM_EXTRAP), ("block32", rx.PRECOND_BLOCK32, rx.WARM_EXTRAP),
+                         ("jacobi_lagrange_guess", rx.PRECOND_JACOBI, rx.WARM_LAGRANGE)):
+        c = rx.ReaxFF(P, w["types"], w["box"], w["options"], precision=rx.MIXED, qeq_precond=pc, warm_start=ws)
         c.set_state(w["x"], w["v"])
         q0, its, itt, _ = c.qeq()
         qs[name] = q0

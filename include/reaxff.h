@@ -56,7 +56,22 @@ enum {
 };
 
 enum { REAXFF_FP64 = 0, REAXFF_MIXED = 1 };                  /* options.precision */
-enum { REAXFF_WARM_EXTRAP = 0, REAXFF_WARM_ZERO = 1, REAXFF_WARM_MLP = 2 };
+/* options.warm_start: the QEq initial guess from the solutions of the previous steps (Sec. 3.3
+ * names an extrapolation scheme without its form). The last 8 solutions of each system are
+ * kept; a guess is sum_k w[m][k] x_k over the m kept (newest first), from one of three
+ * predictors: 0, Lagrange (cubic through 4 points for s, quadratic through 3 for t); 1 and
+ * 2, the value of the cubic fitted by least squares to the last 6 or 8 solutions (lower
+ * degree while fewer are kept). The fits smooth the solve-tolerance noise of the stored
+ * solutions, which dominates at loose tolerances; Lagrange has the smaller truncation error,
+ * which dominates at tight ones. EXTRAP: adaptive, every solve scores the three predictors
+ * against the solution it found and the best is used next, per replica and system;
+ * LAGRANGE: predictor 0 always; ZERO: no history; MLP: EXTRAP plus the learned guess for s
+ * (reaxff_mlp_*). */
+enum { REAXFF_WARM_EXTRAP = 0, REAXFF_WARM_ZERO = 1, REAXFF_WARM_MLP = 2, REAXFF_WARM_LAGRANGE = 3 };
+/* The weights of initial-guess predictor 0..2 (host only, no GPU): w (double[2*9*8])
+ * receives w[sys][m][k], the weight of the k-th newest kept solution (k = 0 the newest)
+ * when m are kept, for sys 0 (s) and 1 (t). E_INVALID for another predictor or a NULL w. */
+int reaxff_extrap_weights(int32_t predictor, double* w);
 /* options.qeq_precond: the CG preconditioner M of both QEq systems. JACOBI is the paper's
  * M = diag(H) (Sec. 3.3). BLOCK32 is block Jacobi over blocks of 32 consecutive atoms of a
  * replica (the last block of a replica may be shorter): M = blockdiag(H_BB), with each

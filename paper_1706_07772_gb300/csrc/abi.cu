@@ -508,6 +508,49 @@ int check_flags(reaxff_ctx* ctx, bool allow_nc) {
   return REAXFF_OK;
 }
 
+// Initial-guess weights w[sys][m][k] of predictor `pred` (sys 0: s, 1: t; m newest solutions
+// available, k = 0 the newest). Predictor 0, Lagrange: cubic through 4 points for s,
+// quadratic through 3 for t. Predictors 1 and 2, least squares: the value at the next step
+// of the polynomial of degree min(m' - 1, 3) fitted by least squares to the last m' =
+// min(m, 6) or min(m, 8) solutions at equal steps (Lagrange up to 4 points, smoothing the
+// solve-tolerance noise of the stored solutions beyond).
+void extrap_weights(int pred, std::vector<double>& w) {
+  const int H = rx::QEQ_HIST;
+  w.assign(2 * (H + 1) * H, 0.0);
+  for (int sys = 0; sys < 2; ++sys)
+    for (int m = 1; m <= H; ++m) {
+      double* o = w.data() + ((size_t)sys * (H + 1) + m) * H;
+      int npt = std::min(m, pred == 1 ? 6 : H);
+      int deg = std::min(npt - 1, 3);
+      if (pred == 0) {
+        deg = std::min(m - 1, sys == 0 ? 3 : 2);
+        npt = deg + 1;
+      }
+      // normal equations (V^T V) c = e_0 for the fit to t_k = -(k + 1); w = V c
+      double A[4][4] = {}, c[4] = {1.0, 0.0, 0.0, 0.0};
+      const int D = deg + 1;
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b)
+          for (int k = 0; k < npt; ++k) A[a][b] += std::pow(-(k + 1.0), a + b);
+      for (int col = 0; col < D; ++col) {            // Gauss-Jordan (SPD, tiny)
+        const double piv = A[col][col];
+        for (int b = 0; b < D; ++b) A[col][b] /= piv;
+        c[col] /= piv;
+        for (int r = 0; r < D; ++r) {
+          if (r == col) continue;
+          const double f = A[r][col];
+          for (int b = 0; b < D; ++b) A[r][b] -= f * A[col][b];
+          c[r] -= f * c[col];
+        }
+      }
+      for (int k = 0; k < npt; ++k) {
+        double v = 0.0;
+        for (int a = 0; a < D; ++a) v += std::pow(-(k + 1.0), a) * c[a];
+        o[k] = v;
+      }
+    }
+}
+
 int validate(const reaxff_params* p, const reaxff_options* o, std::string& msg) {
   if (!p || !o) { msg = "null params/options"; return REAXFF_E_INVALID; }
   if (p->ntypes < 1 || p->ntypes > MAXT) { msg = "ntypes out of range"; return REAXFF_E_INVALID; }
@@ -516,7 +559,7 @@ int validate(const reaxff_params* p, const reaxff_options* o, std::string& msg) 
   }
   if (!(o->bo_cut > 0 && o->qeq_tol > 0 && o->qeq_max_iter > 0)) { msg = "bo_cut, qeq_tol, qeq_max_iter must be > 0"; return REAXFF_E_INVALID; }
   if (o->precision != REAXFF_FP64 && o->precision != REAXFF_MIXED) { msg = "unknown precision"; return REAXFF_E_INVALID; }
-  if (o->warm_start < 0 || o->warm_start > REAXFF_WARM_MLP) { msg = "unknown warm_start"; return REAXFF_E_INVALID; }
+  if (o->warm_start < 0 || o->warm_start > REAXFF_WARM_LAGRANGE) { msg = "unknown warm_start"; return REAXFF_E_INVALID; }
   if (!std::isfinite(o->skin) || o->skin > 5.0) { msg = "skin must be finite and <= 5 A"; return REAXFF_E_INVALID; }
   if (o->qeq_precond != REAXFF_PRECOND_JACOBI && o->qeq_precond != REAXFF_PRECOND_BLOCK32) {
     msg = "unknown qeq_precond"; return REAXFF_E_INVALID;
@@ -696,8 +739,10 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   rx::QeqState& Q = ctx->Q;
   Q.grid = rx::qeq_grid_size(ctx->nsm);
   Q.zg = B.alloc<double>(2 * (size_t)n);
-  Q.hist_s = B.alloc<double>(7 * (size_t)n);      // s ring (4 slots) then t ring (3 slots)
-  Q.hist_t = Q.hist_s + 4 * (size_t)n;
+  Q.hist_s = B.alloc<double>(2 * rx::QEQ_HIST * (size_t)n);   // s ring, then t ring
+  Q.hist_t = Q.hist_s + rx::QEQ_HIST * (size_t)n;
+  Q.wext = B.alloc<double>(rx::QEQ_NPRED * 2 * (rx::QEQ_HIST + 1) * rx::QEQ_HIST);
+  Q.pred = B.alloc<int>(2 * nrep);
   Q.precond = options->qeq_precond;
   Q.Pf = ctx->Pf;
   int rows = std::max(8, (int)((n + Q.grid - 1) / Q.grid));
@@ -770,7 +815,7 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   Q.mlp_used = B.alloc<int>(nrep);
   ctx->etot_buf = B.alloc<double>((size_t)ETOT_CHUNK * nrep);
   ctx->etot_idx = B.alloc<int>(1);
-  ctx->snap = B.alloc<double>(13 * (size_t)n);
+  ctx->snap = B.alloc<double>((6 + 2 * rx::QEQ_HIST) * (size_t)n);
   ctx->snap_i = B.alloc<int>(4);
   if (B.err != cudaSuccess) {
     std::string m = "allocation: " + cuda_err_str(B.err);
@@ -818,6 +863,16 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   UP(clo_d, clo.data(), clo.size() * sizeof(int));
   UP(crep_d, crep.data(), crep.size() * sizeof(int));
   UP(rchunk_d, rchunk.data(), (nrep + 1) * sizeof(int));
+  {
+    std::vector<double> wx;
+    for (int p = 0; p < rx::QEQ_NPRED; ++p) {
+      std::vector<double> w1;
+      extrap_weights(p, w1);
+      wx.insert(wx.end(), w1.begin(), w1.end());
+    }
+    UP(Q.wext, wx.data(), wx.size() * sizeof(double));
+  }
+  if (e == cudaSuccess) e = cudaMemset(Q.pred, 0, 2 * nrep * sizeof(int));
   if (Q.bj_nblk) {
     UP(Q.bj_start, bjs.data(), bjs.size() * sizeof(int));
     UP(Q.bj_size, bjn.data(), bjn.size() * sizeof(int));
@@ -1201,7 +1256,7 @@ static void collect_graph_profile(reaxff_ctx* ctx) {
 // the steps of one call without host synchronisation; returns the device flags
 static int run_unchecked(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev, int* flags) {
   rx::Launch L = launch_of(ctx);
-  rx::snapshot(L, ctx->sys, ctx->Q.hist_s, 7 * ctx->n, ctx->Q.hst, ctx->snap, ctx->snap_i, 0);
+  rx::snapshot(L, ctx->sys, ctx->Q.hist_s, 2 * rx::QEQ_HIST * ctx->n, ctx->Q.hst, ctx->snap, ctx->snap_i, 0);
   CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
   for (int c0 = 0; c0 < nsteps; c0 += ETOT_CHUNK) {
     const int len = std::min(ETOT_CHUNK, nsteps - c0);
@@ -1244,7 +1299,7 @@ static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev) {
     }
     // a list overflowed during the call: restore its starting state, regrow, redo it checked
     rx::Launch L = launch_of(ctx);
-    rx::snapshot(L, ctx->sys, ctx->Q.hist_s, 7 * ctx->n, ctx->Q.hst, ctx->snap, ctx->snap_i, 1);
+    rx::snapshot(L, ctx->sys, ctx->Q.hist_s, 2 * rx::QEQ_HIST * ctx->n, ctx->Q.hst, ctx->snap, ctx->snap_i, 1);
     CK(cudaMemsetAsync(ctx->sys.img, 0, 3 * (size_t)ctx->n * sizeof(int), ctx->st));
     CK(cudaMemsetAsync(ctx->sys.rebuild, 1, sizeof(int), ctx->st));
     grow_caps(ctx, flags);
@@ -1978,6 +2033,14 @@ std::string tune_key(reaxff_ctx* ctx) {
 }  // namespace
 
 extern "C" {
+
+int reaxff_extrap_weights(int32_t predictor, double* w) {
+  if (!w || predictor < 0 || predictor >= rx::QEQ_NPRED) return REAXFF_E_INVALID;
+  std::vector<double> v;
+  extrap_weights(predictor, v);
+  std::copy(v.begin(), v.end(), w);
+  return REAXFF_OK;
+}
 
 int reaxff_autotune(reaxff_ctx* ctx, const char* cache_path, int32_t* schedule) {
   if (!ctx) return REAXFF_E_INVALID;

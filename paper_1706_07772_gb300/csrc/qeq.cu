@@ -54,12 +54,15 @@ struct CG {
   int capn;
   const double *eta, *chi, *ieta;          // per type (double); ieta = 1/eta
   const float* binv;                       // block-Jacobi inverses (null: Jacobi, z = r / eta)
-  // solution history rings (s: 4 slots, t: 3) and their device state hst = {slot of the
+  // solution history rings (rx::QEQ_HIST slots each) and their device state hst = {slot of the
   // newest s, slot of the newest t, usable entries}; read by every block at the start,
   // advanced by block 0 at the end (the new solutions go to the oldest slots)
   double *hist_s, *hist_t;
   int* hst;
   int warm;                                // 1: extrapolate from the history, 0: start at 0
+  const double* wext;                      // [QEQ_NPRED][2][H+1][H] guess weights (H = QEQ_HIST)
+  int* pred;                               // [2*nrep] predictor in use per replica and system
+  int adapt;                               // 1: re-pick the predictor after every solve
   const float* qhat;                       // learned charges (or null): a second guess for s
   int* mlp_used;                           // [nrep] 1 where the learned guess was kept
   void* zg;                                // interleaved (s, t) SpMV operand: float2 or double2
@@ -561,34 +564,29 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
   int pb = 0;
   double* S = B.S;
   double* red = B.red;
-  const int hpos_s = a.hst[0], hpos_t = a.hst[1], nhist = a.hst[2];
-  const int nh = a.warm ? nhist : 0;
+  const int hpos = a.hst[0], nhist = a.hst[2];
+  const int nh = a.warm ? min(nhist, rx::QEQ_HIST) : 0;
   const size_t n = (size_t)a.n;
-  const double* h0s = a.hist_s + (size_t)((hpos_s + 4) % 4) * n;   // newest first
-  const double* h1s = a.hist_s + (size_t)((hpos_s + 3) % 4) * n;
-  const double* h2s = a.hist_s + (size_t)((hpos_s + 2) % 4) * n;
-  const double* h3s = a.hist_s + (size_t)((hpos_s + 1) % 4) * n;
-  const double* h0t = a.hist_t + (size_t)((hpos_t + 3) % 3) * n;
-  const double* h1t = a.hist_t + (size_t)((hpos_t + 2) % 3) * n;
-  const double* h2t = a.hist_t + (size_t)((hpos_t + 1) % 3) * n;
-  double* outs = a.hist_s + (size_t)((hpos_s + 1) % 4) * n;        // the oldest slots
-  double* outt = a.hist_t + (size_t)((hpos_t + 1) % 3) * n;
+  double* outs = a.hist_s + (size_t)((hpos + 1) % rx::QEQ_HIST) * n;   // the oldest slots
+  double* outt = a.hist_t + (size_t)((hpos + 1) % rx::QEQ_HIST) * n;
   // ---------------- init: eta, 1/eta and the initial guess into the row state; guess into
-  // zg. Guess: Lagrange extrapolation of the solution history (cubic for s from 4 points,
-  // quadratic for t from 3; lower order while the history is short; 0 without one)
+  // zg. Guess: x = sum_k w[p][sys][nh][k] x_k over the nh newest solutions (newest first),
+  // with the host's weights of the replica's current predictor p (0 without a history)
+  constexpr int H = rx::QEQ_HIST;
+  auto wrow = [&](int p, int sys) { return a.wext + ((size_t)(p * 2 + sys) * (H + 1) + nh) * H; };
   __syncthreads();
-  for_chunks(a, C, [&](int, int lo, int hi, int, int off) {
+  for_chunks(a, C, [&](int, int lo, int hi, int rep, int off) {
+    const double* wsv = wrow(a.pred[2 * rep], 0);
+    const double* wtv = wrow(a.pred[2 * rep + 1], 1);
     for_rows(lo, hi, [&](int i) {
       const int li = off + i - lo;
       const int t = a.type[i];
       double xs = 0.0, xt = 0.0;
-      if (nh >= 4) xs = 4 * h0s[i] - 6 * h1s[i] + 4 * h2s[i] - h3s[i];
-      else if (nh == 3) xs = 3 * h0s[i] - 3 * h1s[i] + h2s[i];
-      else if (nh == 2) xs = 2 * h0s[i] - h1s[i];
-      else if (nh == 1) xs = h0s[i];
-      if (nh >= 3) xt = 3 * h0t[i] - 3 * h1t[i] + h2t[i];
-      else if (nh == 2) xt = 2 * h0t[i] - h1t[i];
-      else if (nh == 1) xt = h0t[i];
+      for (int k = 0; k < nh; ++k) {
+        const size_t slot = (size_t)((hpos - k + rx::QEQ_HIST) % rx::QEQ_HIST) * n;
+        xs += __ldg(wsv + k) * a.hist_s[slot + i];
+        xt += __ldg(wtv + k) * a.hist_t[slot + i];
+      }
       const double e = a.eta[t], ie = a.ieta[t];
       B.v(V_ETA, li) = e; B.v(V_IETA, li) = ie;
       B.v(V_XS, li) = xs; B.v(V_XT, li) = xt;
@@ -840,22 +838,52 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
     count_active(S, a.nrep);
   }
   if (S[a.nrep * NS] > 0.0 && lead && threadIdx.x == 0) atomicOr(a.err, ERR_CG);
-  // ---------------- solutions out; mu = sum s / sum t per replica, q = s - mu t
+  // ---------------- solutions out; mu = sum s / sum t per replica, q = s - mu t. With an
+  // adaptive guess, also the squared error every predictor's guess would have had for this
+  // solve (same history), so that each replica and system uses the best one next time
+  const bool score = a.adapt && nh > 0;
   for_chunks(a, C, [&](int c, int lo, int hi, int, int off) {
-    double v[2] = {0, 0};
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // sum s, sum t, error of s by predictor 0..2, of t
     for_rows(lo, hi, [&](int i) {
       const int li = off + i - lo;
       const double xs = B.v(V_XS, li), xt = B.v(V_XT, li);
-      outs[i] = xs;
+      if (score) {
+#pragma unroll
+        for (int p = 0; p < rx::QEQ_NPRED; ++p) {
+          const double* ws = wrow(p, 0);
+          const double* wt = wrow(p, 1);
+          double gs = 0.0, gt = 0.0;
+          for (int k = 0; k < nh; ++k) {
+            const size_t slot = (size_t)((hpos - k + H) % H) * n;
+            gs += __ldg(ws + k) * a.hist_s[slot + i];
+            gt += __ldg(wt + k) * a.hist_t[slot + i];
+          }
+          v[2 + p] += (gs - xs) * (gs - xs);
+          v[5 + p] += (gt - xt) * (gt - xt);
+        }
+      }
+      outs[i] = xs;                          // after the history was read: this is its oldest slot
       outt[i] = xt;
       v[0] += xs;
       v[1] += xt;
     });
-    block_sum<2>(a, v, hi - lo, pb, c);
+    block_sum<8>(a, v, hi - lo, pb, c);
   });
   if (!grid_barrier(a.bar, a.err, bt)) return;
-  reduce_parts<2>(a, pb, red);
-  for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) S[r * NS + S_MU] = red[r * NQ + 0] / red[r * NQ + 1];
+  reduce_parts<8>(a, pb, red);
+  for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
+    const double* rd = red + r * NQ;
+    S[r * NS + S_MU] = rd[0] / rd[1];
+    if (score && lead) {
+      int bs = 0, bt2 = 0;
+      for (int p = 1; p < rx::QEQ_NPRED; ++p) {
+        if (rd[2 + p] < rd[2 + bs]) bs = p;
+        if (rd[5 + p] < rd[5 + bt2]) bt2 = p;
+      }
+      a.pred[2 * r] = bs;
+      a.pred[2 * r + 1] = bt2;
+    }
+  }
   __syncthreads();
   for_chunks(a, C, [&](int, int lo, int hi, int rep, int off) {
     const double mu = S[rep * NS + S_MU];
@@ -869,9 +897,9 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
   });
   // advance the history (every block read hst before its first barrier)
   if (lead && threadIdx.x == 0) {
-    a.hst[0] = (hpos_s + 1) % 4;
-    a.hst[1] = (hpos_t + 1) % 3;
-    a.hst[2] = nhist < 4 ? nhist + 1 : 4;
+    a.hst[0] = (hpos + 1) % rx::QEQ_HIST;
+    a.hst[1] = a.hst[0];
+    a.hst[2] = nhist < rx::QEQ_HIST ? nhist + 1 : rx::QEQ_HIST;
   }
 }
 
@@ -1001,8 +1029,9 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   a.eta = eta; a.chi = chi;
   a.binv = Q.precond == REAXFF_PRECOND_BLOCK32 ? Q.binv : nullptr;
   a.bj_smem = a.binv ? Q.bj_smem : 0;
-  a.hist_s = Q.hist_s; a.hist_t = Q.hist_t; a.hst = Q.hst;
-  a.warm = (warm == REAXFF_WARM_EXTRAP || warm == REAXFF_WARM_MLP) ? 1 : 0;
+  a.hist_s = Q.hist_s; a.hist_t = Q.hist_t; a.hst = Q.hst; a.wext = Q.wext; a.pred = Q.pred;
+  a.adapt = warm != REAXFF_WARM_LAGRANGE;
+  a.warm = (warm == REAXFF_WARM_EXTRAP || warm == REAXFF_WARM_MLP || warm == REAXFF_WARM_LAGRANGE) ? 1 : 0;
   a.qhat = qhat;
   a.mlp_used = Q.mlp_used;
   a.zg = Q.zg;

@@ -562,10 +562,14 @@ void snapshot(const Launch& L, Sys s, double* hist, int nhist_doubles, int* hst,
 // else in block-private global regions (scal, state).
 constexpr int QEQ_SMEM_MAX = 200 * 1024;
 constexpr int QEQ_NV_STATE = 14;             // doubles per row of CG state
+constexpr int QEQ_HIST = 8;                  // solutions kept per system for the initial guess
+constexpr int QEQ_NPRED = 3;                 // initial-guess predictors: Lagrange, least squares over 6, over 8
 constexpr int QEQ_SCAL_PER_REP = 24;         // doubles per replica of scalars + reductions
 struct QeqState {
-  double *hist_s, *hist_t;     // [4*n], [3*n] solution rings (s, t); the solver writes each
-                               // new solution into the oldest slot
+  double *hist_s, *hist_t;     // [QEQ_HIST*n] each: solution rings (s, t); the solver writes
+                               // each new solution into the oldest slot
+  double* wext;                // [QEQ_NPRED][2][QEQ_HIST+1][QEQ_HIST] guess weights by history length
+  int* pred;                   // [2*nrep] predictor in use per replica and system (s, t)
   int* hst;                    // device {slot of the newest s, of the newest t, usable entries}
   void* zg;                    // interleaved (s, t) copy of the SpMV operand: float2 or double2
   const double* ieta;          // 1/eta per type

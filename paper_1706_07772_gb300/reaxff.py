@@ -16,7 +16,7 @@ NTERMS = 13
 TERMS = ("bond", "lp", "over", "under", "val", "pen", "coa", "tors", "conj", "hbond", "vdw", "coul", "pol")
 OK, E_INVALID, E_CUDA, E_CAPACITY, E_NOT_CONVERGED, E_TIMEOUT, E_NAN, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, MIXED = 0, 1
-WARM_EXTRAP, WARM_ZERO, WARM_MLP = 0, 1, 2
+WARM_EXTRAP, WARM_ZERO, WARM_MLP, WARM_LAGRANGE = 0, 1, 2, 3
 PRECOND_JACOBI, PRECOND_BLOCK32 = 0, 1
 LIST_FAR, LIST_BOND, LIST_HBOND = 0, 1, 2
 
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
         "reaxff_bo_average_samples": (i64, [vp]),
         "reaxff_get_bo_average": (C.c_int, [vp, i64, ip64, ip32, ip32, C.POINTER(C.c_int8), dp]),
         "reaxff_autotune": (C.c_int, [vp, C.c_char_p, ip32]),
+        "reaxff_extrap_weights": (C.c_int, [i32, dp]),
         "reaxff_mlp_init": (C.c_int, [vp, C.c_uint64]),
         "reaxff_mlp_set_params": (C.c_int, [vp, fp, fp, fp]),
         "reaxff_mlp_get_params": (C.c_int, [vp, fp, fp, fp]),
@@ -178,6 +179,16 @@ def make_options(o: dict, precision=FP64, warm_start=WARM_EXTRAP, term_mask=0, c
     O.skin = float(o.get("skin", skin))
     O.qeq_precond = int(o.get("qeq_precond", qeq_precond))
     return O
+
+
+def extrap_weights(predictor=0):
+    """Weights w[sys, m, k] of initial-guess predictor 0 (Lagrange), 1 or 2 (least squares
+    over 6 or 8 solutions); host only."""
+    w = np.empty(2 * 9 * 8)
+    rc = load().reaxff_extrap_weights(int(predictor), _dp(w))
+    if rc != OK:
+        raise ReaxFFError(rc, "reaxff_extrap_weights failed")
+    return w.reshape(2, 9, 8)
 
 
 def term_mask(*names) -> int:

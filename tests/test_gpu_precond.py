@@ -102,3 +102,27 @@ def test_block32_md_matches_jacobi(rx, params, prec):
     assert np.abs(x1 - x0).max() < 1e-8
     assert np.abs(q1 - q0).max() < (1e-7 if prec == 0 else 2e-5)
     assert np.abs(e1 - e0).max() < 1e-6 * np.abs(e0).max()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-8), (1, 1e-6)])
+def test_adaptive_guess_saves_spmvs(rx, params, prec, tol):
+    """Thirty MD steps after a warm-up that fills the solution history: the adaptive
+    initial guess (the best of Lagrange and two least-squares predictors, scored on each
+    solve) needs no more SpMVs than Lagrange extrapolation at a tight and at a loose
+    tolerance, and the trajectories agree to within the solve tolerance."""
+    w = synth.workload("petn464")
+    o = dict(w["options"], qeq_tol=tol)
+    res = {}
+    for mode in (rx.WARM_EXTRAP, rx.WARM_LAGRANGE):
+        c = rx.ReaxFF(params, w["types"], w["box"], o, precision=prec, warm_start=mode)
+        c.set_state(w["x"], w["v"])
+        c.step(12, 0.1)
+        sp0 = c.qeq_spmv_total()
+        c.step(30, 0.1)
+        x, _, q = c.get_state()
+        res[mode] = (c.qeq_spmv_total() - sp0, x, q)
+        c.close()
+    (n_ad, x_ad, q_ad), (n_lg, x_lg, q_lg) = res[rx.WARM_EXTRAP], res[rx.WARM_LAGRANGE]
+    assert n_ad <= n_lg, (n_ad, n_lg)
+    assert np.abs(x_ad - x_lg).max() < max(1e-8, 0.1 * tol)   # forces differ at the tolerance level
+    assert np.abs(q_ad - q_lg).max() < 100 * tol
