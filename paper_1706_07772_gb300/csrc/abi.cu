@@ -466,7 +466,7 @@ int zero_accumulators(reaxff_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->aq.cddelta, 0, n * sizeof(unsigned long long), ctx->st));
   CK(cudaMemsetAsync(ctx->acc.e, 0, NTERMS * n * sizeof(double), ctx->st));
   CK(cudaMemsetAsync(ctx->acc.vir, 0, 6 * n * sizeof(double), ctx->st));
-  CK(cudaMemsetAsync(ctx->acc.efx, 0, 8 * n * sizeof(unsigned long long), ctx->st));   // efx and vfx
+  CK(cudaMemsetAsync(ctx->acc.efx, 0, (NTERMS + 6) * n * sizeof(unsigned long long), ctx->st));   // efx and vfx
   return REAXFF_OK;
 }
 
@@ -722,10 +722,11 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   a.cddelta = B.alloc<unsigned long long>(n);
   a.sumbo_f = B.alloc<float>(n);
   a.dang_f = B.alloc<float>(n);
+  for (float** p : {&a.delta_f, &a.sbo2_f, &a.dsbo2_f, &a.prodexp_f, &a.sbo_fac_f, &a.dnlp_f}) *p = B.alloc<float>(n);
   ctx->acc.e = B.alloc<double>((size_t)NTERMS * n);
   ctx->acc.vir = B.alloc<double>(6 * (size_t)n);
-  ctx->acc.efx = B.alloc<unsigned long long>(8 * (size_t)n);   // efx [2n] then vfx [6n], one block
-  ctx->acc.vfx = ctx->acc.efx + 2 * (size_t)n;
+  ctx->acc.efx = B.alloc<unsigned long long>((NTERMS + 6) * (size_t)n);   // efx [NTERMS n], vfx [6n]
+  ctx->acc.vfx = ctx->acc.efx + NTERMS * (size_t)n;
   ctx->F_out = B.alloc<double>(3 * (size_t)n);
   ctx->E_rep = B.alloc<double>(NTERMS * nrep);
   ctx->vir_rep = B.alloc<double>(6 * nrep);

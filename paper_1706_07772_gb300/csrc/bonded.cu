@@ -174,6 +174,12 @@ __global__ void k_atom_terms(Sys s, BondList bl, AtomQ aq, Accum acc, const DPar
   aq.sbo2[i] = sbo2;
   aq.dsbo2[i] = dsbo2;
   aq.sbo_fac[i] = sbo_fac;
+  aq.delta_f[i] = (float)delta;
+  aq.sbo2_f[i] = (float)sbo2;
+  aq.dsbo2_f[i] = (float)dsbo2;
+  aq.prodexp_f[i] = (float)prodexp;
+  aq.sbo_fac_f[i] = (float)sbo_fac;
+  aq.dnlp_f[i] = (float)dnlp;
   acc.e[T_LP * s.n + i] = elp;
 }
 
@@ -563,8 +569,8 @@ __global__ void k_angles_g(Sys s, BondList bl, AtomQ aq, Accum acc, const DParam
   const int jj = act ? j : 0;
   const int tj = s.type[jj];
   const float* bo = (const float*)bl.bo;
-  const float dang = (float)aq.dang[jj], delta = (float)aq.delta[jj];
-  const float sbo2 = (float)aq.sbo2[jj];
+  const float dang = aq.dang_f[jj], delta = aq.delta_f[jj];
+  const float sbo2 = aq.sbo2_f[jj];
   const float wv = wbit<float>(mask, T_VAL), wp = wbit<float>(mask, T_PEN), wc = wbit<float>(mask, T_COA);
   const float pv5 = P->p_val5[tj];
   const float e6 = m_expc(P->p_val6 * dang);
@@ -668,28 +674,30 @@ __global__ void k_angles_g(Sys s, BondList bl, AtomQ aq, Accum acc, const DParam
     GroupSum<float, G>::run(hi[q], lo[q]);
   }
   if (!act) return;
-  const double cdsbo = ((double)hi[12] + (double)lo[12]) * aq.dsbo2[j];   // dE/dSBO
-  const double prod = aq.prodexp[j];
+  // every total goes to a 2^-32 fixed-point accumulator through 32-bit conversions: no FP64
+  // instruction (each would hold the SM's FP64 pipe for ~16 cycles)
+  const float cdsbo = (hi[12] + lo[12]) * aq.dsbo2_f[j];   // dE/dSBO
+  const float prod = aq.prodexp_f[j];
 #pragma unroll
   for (int rnd = 0; rnd < (NVA + G - 1) / G; ++rnd) {
     const int q = sub + rnd * G;
     float h, l;
     lane_pick<NVA>(hi, lo, q, h, l);
-    const double d = (double)h + (double)l;
     if (q < 3) {
-      acc.e[(T_VAL + q) * s.n + j] = d;
+      fix_add_ff(acc.efx + (size_t)(T_VAL + q) * s.n + j, h, l, s.err);
     } else if (q < 6) {
       fix_add_ff((q == 3 ? s.fx : q == 4 ? s.fy : s.fz) + j, h, l, s.err);
     } else if (q < 12) {
-      acc.vir[(q - 6) * s.n + j] += d;
+      fix_add_ff(acc.vfx + (size_t)(q - 6) * s.n + j, h, l, s.err);
     } else if (q == 13) {
-      const double dsbo_dsum = -(1.0 - prod) * (1.0 + (double)P->p_val8 * aq.dnlp[j]);
-      fix_add(aq.cddelta + j, d + cdsbo * dsbo_dsum, s.err);
+      const float dsbo_dsum = -(1.0f - prod) * (1.0f + P->p_val8 * aq.dnlp_f[j]);
+      fix_add_ff(aq.cddelta + j, h, l, s.err);
+      fix_add(aq.cddelta + j, cdsbo * dsbo_dsum, s.err);
     }
   }
   // SBO depends on every bond of j: distribute dE/dSBO over j's row (FP32 terms)
-  if (cdsbo != 0.0) {
-    const float cf = (float)cdsbo, pf = (float)prod, ff = (float)aq.sbo_fac[j];
+  if (cdsbo != 0.0f) {
+    const float cf = cdsbo, pf = prod, ff = aq.sbo_fac_f[j];
     for (int k = sub; k < nb; k += G) {
       const int e = j * bl.cap + k;
       const float b = bo[e];
@@ -906,7 +914,7 @@ __global__ void __launch_bounds__(128) k_torsions(Sys s, BondList bl, AtomQ aq, 
         unsigned long long* dst = nullptr;
         if (q < 3) dst = (q == 0 ? s.fx : q == 1 ? s.fy : s.fz) + j;
         else if (q == 3) dst = aq.cddelta + j;
-        else if (q < 6) dst = acc.efx + (size_t)(q - 4) * s.n + j;
+        else if (q < 6) dst = acc.efx + (size_t)(T_TORS + q - 4) * s.n + j;
         else if (q < 12) dst = acc.vfx + (size_t)(q - 6) * s.n + j;
         else if (q < 15) dst = (q == 12 ? s.fx : q == 13 ? s.fy : s.fz) + k;
         else if (q == 15) dst = aq.cddelta + k;
@@ -956,7 +964,7 @@ __global__ void __launch_bounds__(128) k_torsions_q(Sys s, BondList bl, AtomQ aq
           unsigned long long* dst;
           if (c < 3) dst = (c == 0 ? s.fx : c == 1 ? s.fy : s.fz) + bj;
           else if (c == 3) dst = aq.cddelta + bj;
-          else if (c < 6) dst = acc.efx + (size_t)(c - 4) * s.n + bj;
+          else if (c < 6) dst = acc.efx + (size_t)(T_TORS + c - 4) * s.n + bj;
           else if (c < 12) dst = acc.vfx + (size_t)(c - 6) * s.n + bj;
           else if (c < 15) dst = (c == 12 ? s.fx : c == 13 ? s.fy : s.fz) + bk;
           else if (c == 15) dst = aq.cddelta + bk;
@@ -1128,11 +1136,11 @@ __global__ void k_hbonds(Sys s, BondList bl, HbList hl, Accum acc, const DParams
     float h, l;
     lane_pick<NVJ>(hi, lo, lane, h, l);
     if (lane == 0) {
-      acc.e[T_HB * s.n + j] = (double)h + (double)l;
+      fix_add_ff(acc.efx + (size_t)T_HB * s.n + j, h, l, s.err);
     } else if (lane < 4) {
       fix_add_ff(lane == 1 ? s.fx + j : lane == 2 ? s.fy + j : s.fz + j, h, l, s.err);
     } else if (lane < NVJ) {
-      acc.vir[(lane - 4) * s.n + j] += (double)h + (double)l;
+      fix_add_ff(acc.vfx + (size_t)(lane - 4) * s.n + j, h, l, s.err);
     }
   } else {
     const double ehb = warp_sum_d(l_ehb);

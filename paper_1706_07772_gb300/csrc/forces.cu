@@ -110,8 +110,7 @@ constexpr int NQ_RED = NTERMS + 7;
 constexpr int RED_PER_THREAD = 4, RED_BLOCK = 128;
 static_assert(RED_PER_THREAD * RED_BLOCK == rx::RED_CHUNK, "reduction chunk");
 __device__ __forceinline__ double red_value(const Sys& s, const Accum& acc, const double* mass_t, int q, int64_t i) {
-  if (q == T_TORS || q == T_CONJ) return acc.e[(size_t)q * s.n + i] + fix_get(acc.efx + (size_t)(q - T_TORS) * s.n + i);
-  if (q < NTERMS) return acc.e[(size_t)q * s.n + i];
+  if (q < NTERMS) return acc.e[(size_t)q * s.n + i] + fix_get(acc.efx + (size_t)q * s.n + i);
   if (q < NTERMS + 6)
     return acc.vir[(size_t)(q - NTERMS) * s.n + i] + fix_get(acc.vfx + (size_t)(q - NTERMS) * s.n + i);
   const double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];

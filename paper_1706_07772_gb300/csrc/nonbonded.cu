@@ -188,12 +188,13 @@ __global__ void k_nonbonded(Sys s, FarList f, Accum acc, const DParams<R>* __res
     }
     float h, l;
     lane_pick<NVN>(hi, lo, lane, h, l);
+    // fixed-point accumulators through 32-bit conversions (no FP64 instruction per value)
     if (lane < 3) {
       fix_add_ff((lane == 0 ? s.fx : lane == 1 ? s.fy : s.fz) + i, h, l, s.err);
     } else if (lane < 5) {
-      acc.e[(T_VDW + lane - 3) * s.n + i] = 0.5 * ((double)h + (double)l);
+      fix_add_ff(acc.efx + (size_t)(T_VDW + lane - 3) * s.n + i, 0.5f * h, 0.5f * l, s.err);   // exact halving
     } else if (lane < NVN) {
-      acc.vir[(lane - 5) * s.n + i] += (double)h + (double)l;
+      fix_add_ff(acc.vfx + (size_t)(lane - 5) * s.n + i, h, l, s.err);
     } else if (lane == NVN) {
       const double q = s.q[i];
       acc.e[T_POL * s.n + i] = (double)P->chi[ti] * q + 0.5 * (double)P->eta[ti] * q * q;

@@ -166,12 +166,14 @@ struct AtomQ {                 // per-atom bond-order quantities (double)
   double *cds, *A;             // dE/dS, chain-rule dE/dDelta'
   unsigned long long* cddelta; // dE/d(sum BO) accumulator (fixed point)
   float *sumbo_f, *dang_f;     // FP32 copies for the mixed-path angle and torsion kernels
+  float *delta_f, *sbo2_f, *dsbo2_f, *prodexp_f, *sbo_fac_f, *dnlp_f;
 };
 
 struct Accum {                 // per-atom energies and virial
   double* e;                   // [NTERMS*n] owner-written
   double* vir;                 // [6*n] owner-accumulated
-  unsigned long long* efx;     // [2*n] torsion, conjugation energies (fixed point, atomics)
+  unsigned long long* efx;     // [NTERMS*n] energies added as 2^-32 fixed point (atomics, or FP32
+                               // warp totals without FP64 conversions), per term like e
   unsigned long long* vfx;     // [6*n] virial contributions added by atomics (fixed point)
 };
 
