@@ -10,7 +10,8 @@ terms, 3-body/4-body enumeration and QEq of Sec. 3.3):
   * the 13 energy terms: bond, lp, over, under, val, pen, coa, tors, conj, hbond,
     vdW, coul, pol
   * QEq: two Jacobi-preconditioned CG solves on the tapered H matrix, q = s - mu t; a
-    block-Jacobi preconditioned variant (blocks of 32 consecutive atoms) with the same result
+    block-Jacobi preconditioned variant (blocks of 32 consecutive atoms) with the same result;
+    restarted GMRES as a comparison solver
   * forces F = -dE/dx at fixed charges and the virial -dE/d(strain), both by reverse-mode
     differentiation of the energy as written (plain definition of a force)
   * velocity Verlet
@@ -688,6 +689,58 @@ def pcg_block(Hm, b, blocks, tol, max_iter, x0=None):
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, max_iter
+
+
+def gmres(Hm, b, diag, tol, max_iter, restart=50, x0=None):
+    """Restarted GMRES(m) for H x = b (Saad and Schultz), right Jacobi preconditioning
+    (H M^-1 y = b, x = M^-1 y, M = diag), Arnoldi by modified Gram-Schmidt, the small least-
+    squares problem by Givens rotations. Same stopping rule as pcg(): ||r||_2 / ||b||_2 <=
+    tol. Returns (x, iterations, residual-norm history). Sec. 3.3 names GMRES beside CG for
+    the QEq systems; this is the solver-variant comparison, not the path's solver."""
+    n = len(b)
+    x = np.zeros(n) if x0 is None else np.array(x0, float)
+    bn = np.linalg.norm(b)
+    r = b - Hm @ x
+    beta = np.linalg.norm(r)
+    hist = [beta / bn]
+    it = 0
+    while beta > tol * bn and it < max_iter:
+        m = min(restart, max_iter - it)
+        V = np.zeros((m + 1, n))
+        Hh = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k_used = 0
+        for k in range(m):
+            w = Hm @ (V[k] / diag)
+            for jj in range(k + 1):
+                Hh[jj, k] = w @ V[jj]
+                w = w - Hh[jj, k] * V[jj]
+            Hh[k + 1, k] = np.linalg.norm(w)
+            if Hh[k + 1, k] > 0:
+                V[k + 1] = w / Hh[k + 1, k]
+            for jj in range(k):                        # earlier rotations on the new column
+                t = cs[jj] * Hh[jj, k] + sn[jj] * Hh[jj + 1, k]
+                Hh[jj + 1, k] = -sn[jj] * Hh[jj, k] + cs[jj] * Hh[jj + 1, k]
+                Hh[jj, k] = t
+            den = np.hypot(Hh[k, k], Hh[k + 1, k])
+            cs[k], sn[k] = Hh[k, k] / den, Hh[k + 1, k] / den
+            Hh[k, k] = den
+            Hh[k + 1, k] = 0.0
+            g[k + 1] = -sn[k] * g[k]
+            g[k] = cs[k] * g[k]
+            it += 1
+            k_used = k + 1
+            hist.append(abs(g[k + 1]) / bn)
+            if abs(g[k + 1]) <= tol * bn:
+                break
+        y = np.linalg.solve(np.triu(Hh[:k_used, :k_used]), g[:k_used])
+        x = x + (V[:k_used].T @ y) / diag
+        r = b - Hm @ x
+        beta = np.linalg.norm(r)
+    return x, it, np.array(hist)
 
 
 def kinetic(v, masses):

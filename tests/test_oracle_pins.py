@@ -294,6 +294,37 @@ def test_block_jacobi_pcg_special_cases_and_solution(params):
     assert np.abs(q_j - q_b).max() < 1e-8
 
 
+def test_gmres_solution_and_minimal_residual(params):
+    """GMRES (comparison solver): reaches the dense solution with non-increasing residuals;
+    unpreconditioned and unrestarted, its residual after k steps is the minimum over the
+    Krylov space CG also searches, so never above CG's; a diagonal system converges in one
+    Jacobi-preconditioned step."""
+    w = synth.workload("petn464")
+    m = _model(params, w)
+    L = m.lists(w["x"])
+    Hm = m.qeq_matrix(w["x"], L)
+    chi = params["chi"][m.types]
+    eta = params["eta"][m.types]
+    b = -chi
+    xg, itg, hist = ro.gmres(Hm, b, eta, 1e-10, 500, restart=500)
+    xd = np.linalg.solve(Hm.toarray(), b)
+    assert np.abs(xg - xd).max() < 1e-8 * np.abs(xd).max()
+    assert np.all(np.diff(hist) <= 1e-12)                  # non-increasing residuals
+    # CG residual history with the same (identity) preconditioner: GMRES is never above it
+    res_cg = []
+    x = np.zeros_like(b); r = b.copy(); p = r.copy(); rr = r @ r
+    for _ in range(25):
+        wv = Hm @ p; al = rr / (p @ wv); x = x + al * p; r = r - al * wv
+        res_cg.append(np.linalg.norm(r) / np.linalg.norm(b))
+        rr2 = r @ r; p = r + rr2 / rr * p; rr = rr2
+    _, _, hist_id = ro.gmres(Hm, b, np.ones_like(eta), 1e-14, 25, restart=25)
+    assert np.all(hist_id[1:26] <= np.array(res_cg) * (1 + 1e-9) + 1e-15)
+    import scipy.sparse as sp
+    D = sp.diags(eta)
+    xd1, it1, _ = ro.gmres(D.tocsr(), b, eta, 1e-12, 10)
+    assert it1 == 1 and np.abs(xd1 - b / eta).max() < 1e-12
+
+
 def test_qeq_two_atom_closed_form(params):
     """Two atoms: q1 = -q2 = (chi2 - chi1) / (eta1 + eta2 - 2 H12)."""
     P = params
