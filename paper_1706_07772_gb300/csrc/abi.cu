@@ -158,6 +158,9 @@ template <typename R> void fill_params(DParams<R>& d, const reaxff_params& p, co
       d.r0s_lo[k] = (R)(p.r0s[a][b] - (double)(R)p.r0s[a][b]);
       d.r0p_lo[k] = (R)(p.r0p[a][b] - (double)(R)p.r0p[a][b]);
       d.r0pp_lo[k] = (R)(p.r0pp[a][b] - (double)(R)p.r0pp[a][b]);
+      d.lr0s[k] = p.r0s[a][b] > 0 ? (R)std::log(p.r0s[a][b]) : R(0);
+      d.lr0p[k] = p.r0p[a][b] > 0 ? (R)std::log(p.r0p[a][b]) : R(0);
+      d.lr0pp[k] = p.r0pp[a][b] > 0 ? (R)std::log(p.r0pp[a][b]) : R(0);
       d.gamma_m3[k] = (R)std::pow(p.gamma[a][b], -3.0);
       for (int c = 0; c < MAXT; ++c) {
         const int t3 = (a * MAXT + b) * MAXT + c;

@@ -20,11 +20,22 @@ namespace {
 
 inline unsigned grid_for(long long threads, int block) { return (unsigned)((threads + block - 1) / block); }
 
+// CHAIN_G lanes per atom (a lane per bond of the row, about four bonds per atom): four times
+// the threads of one per atom, so the dependent loads of the FP64 chain overlap; the lanes'
+// partial sums are combined by fixed-order group butterflies (deterministic)
+constexpr int CHAIN_G = 4;
+__device__ __forceinline__ double group_sum_d(double v) {
+#pragma unroll
+  for (int o = CHAIN_G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 template <typename R>
 __global__ void k_chain1(Sys s, BondList bl, AtomQ aq) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s.n) return;
-  const int nb = bl.cnt[i];
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / CHAIN_G, sub = gt & (CHAIN_G - 1);
+  // no early exit: the group sum spans the warp
+  const int nb = i < s.n ? bl.cnt[i] : 0;
   const double* BOp = bl.bop;
   const double* BOpi = bl.bopi;
   const double* BOpp = bl.bopp;
@@ -32,9 +43,9 @@ __global__ void k_chain1(Sys s, BondList bl, AtomQ aq) {
   const double* FT = (const double*)bl.ft; const double* DF1 = (const double*)bl.df1;
   const double* DFOB = (const double*)bl.dfo_bo; const double* DFTB = (const double*)bl.dft_bo;
   const double* DFOD = (const double*)bl.dfo_d;
-  const long long cdi = (long long)aq.cddelta[i];
+  const long long cdi = nb > 0 ? (long long)aq.cddelta[i] : 0;
   double A = 0.0;
-  for (int k = 0; k < nb; ++k) {
+  for (int k = sub; k < nb; k += CHAIN_G) {
     const int e = i * bl.cap + k;
     const int m = bl.mirror[e];
     const int j = bl.j[e];
@@ -61,20 +72,21 @@ __global__ void k_chain1(Sys s, BondList bl, AtomQ aq) {
     const double dGdD = 2.0 * f1 * df1 * fo * ft + f1 * f1 * dfo_d * ft;
     A += C * bp * dFdD + piw * dGdD;
   }
-  aq.A[i] = A;
+  A = group_sum_d(A);
+  if (i < s.n && sub == 0) aq.A[i] = A;
 }
 
 template <typename R>
 __global__ void k_chain2(Sys s, BondList bl, AtomQ aq, Accum acc) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s.n) return;
-  const int nb = bl.cnt[i];
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / CHAIN_G, sub = gt & (CHAIN_G - 1);
+  const int nb = i < s.n ? bl.cnt[i] : 0;
   const R* DX = (const R*)bl.dx; const R* DY = (const R*)bl.dy; const R* DZ = (const R*)bl.dz;
   const R* RR = (const R*)bl.r;
   const double* DB = bl.dbop; const double* DBPI = bl.dbopi; const double* DBPP = bl.dbopp;
-  const double Ai = aq.A[i];
+  const double Ai = nb > 0 ? aq.A[i] : 0.0;
   double fx = 0, fy = 0, fz = 0, w[6] = {0, 0, 0, 0, 0, 0};
-  for (int k = 0; k < nb; ++k) {
+  for (int k = sub; k < nb; k += CHAIN_G) {
     const int e = i * bl.cap + k;
     const int j = bl.j[e];
     const bool own_lo = (i < j) || (i == j && bl.s[e] > 13);
@@ -82,16 +94,25 @@ __global__ void k_chain2(Sys s, BondList bl, AtomQ aq, Accum acc) {
     const double Asum = own_lo ? Ai + Aj : Aj + Ai;
     const double c = (bl.dEdBOp[e] + Asum) * DB[e] + bl.dEdBOpi[e] * DBPI[e] + bl.dEdBOpp[e] * DBPP[e];
     const double dx = (double)DX[e], dy = (double)DY[e], dz = (double)DZ[e];
-    const double cr = c / (double)RR[e];
+    double cr;
+    if constexpr (sizeof(R) == 4) cr = c * (double)(1.0f / RR[e]);   // FP32 reciprocal: no FP64 division
+    else cr = c / (double)RR[e];
     fx += cr * dx; fy += cr * dy; fz += cr * dz;
     const double hc = -0.5 * cr;
     w[0] += hc * dx * dx; w[1] += hc * dy * dy; w[2] += hc * dz * dz;
     w[3] += hc * dx * dy; w[4] += hc * dx * dz; w[5] += hc * dy * dz;
   }
-  fix_add(s.fx + i, fx, s.err);
-  fix_add(s.fy + i, fy, s.err);
-  fix_add(s.fz + i, fz, s.err);
-  for (int q = 0; q < 6; ++q) acc.vir[q * s.n + i] += w[q];
+  fx = group_sum_d(fx);
+  fy = group_sum_d(fy);
+  fz = group_sum_d(fz);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) w[q] = group_sum_d(w[q]);
+  if (i < s.n && sub == 0) {
+    fix_add(s.fx + i, fx, s.err);
+    fix_add(s.fy + i, fy, s.err);
+    fix_add(s.fz + i, fz, s.err);
+    for (int q = 0; q < 6; ++q) acc.vir[q * s.n + i] += w[q];
+  }
 }
 
 __global__ void k_finalize(Sys s, double* F) {
@@ -232,8 +253,8 @@ void snapshot(const Launch& L, Sys s, double* hist, int nhist_doubles, int* hst,
   *L.count += 1;
 }
 template <typename R> void chain_rule(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc) {
-  k_chain1<R><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a);
-  k_chain2<R><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a, acc);
+  k_chain1<R><<<grid_for((long long)s.n * CHAIN_G, 128), 128, 0, L.st>>>(s, b, a);
+  k_chain2<R><<<grid_for((long long)s.n * CHAIN_G, 128), 128, 0, L.st>>>(s, b, a, acc);
   *L.count += 2;
 }
 template void chain_rule<double>(const Launch&, Sys, BondList, AtomQ, Accum);

@@ -55,6 +55,7 @@ struct DParams {
       p_val4[MAXT * MAXT * MAXT], p_val7[MAXT * MAXT * MAXT], p_pen1[MAXT * MAXT * MAXT],
       p_coa1[MAXT * MAXT * MAXT];
   R r0s_lo[MAXT * MAXT], r0p_lo[MAXT * MAXT], r0pp_lo[MAXT * MAXT];   // r0 - R(r0) (float-float)
+  R lr0s[MAXT * MAXT], lr0p[MAXT * MAXT], lr0pp[MAXT * MAXT];         // log r0 (0 where r0 <= 0)
   // bond membership as a distance: BO'(r) >= bo_cut exactly when r <= bcut (each BO' term
   // decreases with r); bcut as double and float-float; bcut_ok = 0 where that does not hold
   // for the parameters (then membership is decided in FP64 every time)
