@@ -47,6 +47,8 @@ struct reaxff_ctx {
   unsigned mask = 0x1fff;
   int nsm = 0;
   cudaStream_t st = nullptr;
+  cudaStream_t st2 = nullptr;  // second stream: bonded terms beside the nonbonded kernel
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int64_t launches = 0;
   bool have_pos = false, forces_valid = false, lists_valid = false;
   float far_margin = 0.f;
@@ -453,10 +455,27 @@ template <typename R> void terms_impl(reaxff_ctx* ctx) {
   { Stage st(ctx, 6); rx::atom_terms<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
   { Stage st(ctx, 7); rx::over_under_bond<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
   { Stage st(ctx, 8); rx::s_gather<R>(L, ctx->sys, ctx->bond, ctx->aq); }
-  { Stage st(ctx, 9); rx::angles<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
-  { Stage st(ctx, 10); rx::torsions<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
-  { Stage st(ctx, 11); rx::hbonds<R>(L, ctx->sys, ctx->bond, ctx->hb, ctx->acc, P, ctx->mask); }
-  { Stage st(ctx, 12); rx::nonbonded<R>(L, ctx->sys, ctx->far, ctx->acc, P, ctx->mask); }
+  if (sizeof(R) == 4 && !ctx->prof) {
+    // the angle, torsion and H-bond terms (charge-independent) on the second stream beside the
+    // nonbonded kernel: on the mixed path all four add their results through fixed-point
+    // atomics only (exact, order-free) and read nothing another writes, so they commute;
+    // fork and join by events (graph edges under stream capture). The stage timers keep the
+    // serial order.
+    cudaEventRecord(ctx->ev_fork, ctx->st);                 // errors surface at the caller's check
+    cudaStreamWaitEvent(ctx->st2, ctx->ev_fork, 0);
+    rx::Launch L2{ctx->st2, &ctx->launches, &ctx->tune};
+    rx::angles<R>(L2, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+    rx::torsions<R>(L2, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+    rx::hbonds<R>(L2, ctx->sys, ctx->bond, ctx->hb, ctx->acc, P, ctx->mask);
+    rx::nonbonded<R>(L, ctx->sys, ctx->far, ctx->acc, P, ctx->mask);
+    cudaEventRecord(ctx->ev_join, ctx->st2);
+    cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0);
+  } else {
+    { Stage st(ctx, 9); rx::angles<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
+    { Stage st(ctx, 10); rx::torsions<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
+    { Stage st(ctx, 11); rx::hbonds<R>(L, ctx->sys, ctx->bond, ctx->hb, ctx->acc, P, ctx->mask); }
+    { Stage st(ctx, 12); rx::nonbonded<R>(L, ctx->sys, ctx->far, ctx->acc, P, ctx->mask); }
+  }
   { Stage st(ctx, 13); rx::chain_rule<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc); }
 }
 
@@ -636,6 +655,9 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   int coop = 0;
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
   if (ce != cudaSuccess || !coop) {
     delete ctx;
     return REAXFF_E_CUDA;
@@ -943,6 +965,9 @@ void reaxff_destroy(reaxff_ctx* ctx) {
   ctx->lists.free_all();
   ctx->fixed.free_all();
   if (ctx->h_err_pinned) cudaFreeHost(ctx->h_err_pinned);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->st2) cudaStreamDestroy(ctx->st2);
   if (ctx->st) cudaStreamDestroy(ctx->st);
   delete ctx;
 }
