@@ -711,7 +711,7 @@ __global__ void k_cand_filter_f(Sys s, CandList cl, FarList f, HbList hl, const 
   unsigned acc = 0;                                     // acceptor types, when i is an H-bond H
   if (P->hb[ti] == 1)
     for (int t = 0; t < MAXT; ++t) acc |= (P->hb[t] == 2 ? 1u : 0u) << t;
-  const float rnb = P->r_nb, ke = P->k_e;
+  const float irnb = 1.0f / P->r_nb, ke = P->k_e;
   const float* gam = P->gamma_m3 + ti * MAXT;
   const int nc = cl.cnt[i], crow = i * cl.cap;
   const int hrow = i * hl.cap;
@@ -757,10 +757,12 @@ __global__ void k_cand_filter_f(Sys s, CandList cl, FarList f, HbList hl, const 
     }
     cnth += __popc(mh);
     if (ok) {
-      const float rr = sqrtf(r2f);
-      float tap, dtap;
-      taper<float>(rr, rnb, tap, dtap);
-      const float h = tap * ke * rcbrt_f(rr * rr * rr + gam[tj]);
+      // r from the MUFU reciprocal square root (relative error ~1e-7, far inside what the
+      // solve tolerance allows for H) and x = r / r_nb by the reciprocal cutoff
+      const float rr = r2f * rsqrtf(r2f);
+      const float x = rr * irnb, x2 = x * x;
+      const float tap = ((((20.0f * x - 70.0f) * x + 84.0f) * x - 35.0f) * x2 * x2) + 1.0f;
+      const float h = tap * ke * rcbrt_f(rr * r2f + gam[tj]);
       const int pos = near ? cntn + __popc(mn & below) : cntf + __popc(mf & below);
       if (pos < (near ? f.capn : f.cap)) {
         const int e = (near ? rown : rowf) + pos;
