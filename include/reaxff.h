@@ -131,7 +131,9 @@ typedef struct {
   int32_t qeq_max_iter;
   int32_t precision;  /* REAXFF_FP64 or REAXFF_MIXED (FP32 interaction math, FP64 sums) */
   int32_t warm_start; /* REAXFF_WARM_* */
-  int32_t term_mask;  /* bit t set = energy term t contributes to forces (0 = all) */
+  int32_t term_mask;  /* bit t set = energy term t contributes to forces (0 = all); bits
+                         above the 13 terms select nothing, so 1 << 13 alone switches every
+                         term off (free flight: zero forces, constant velocities) */
   double capacity_margin; /* list capacity headroom factor (>= 1; 0 = default 1.35) */
   double skin;        /* Verlet skin (A) of the neighbour candidate list, rebuilt on the device
                          only when an atom has moved more than skin/2; the far list is still

@@ -748,6 +748,19 @@ def kinetic(v, masses):
     return 0.5 * float((masses[:, None] * v * v).sum()) / ACC_CONV
 
 
+def free_flight(x, v, box, dt, nsteps):
+    """Velocity Verlet with every force zero: the velocities stay, and each step moves
+    x to x + dt v (product and sum rounded separately) and wraps it into the box."""
+    x = np.array(x, float)
+    v = np.asarray(v, float)
+    box = np.asarray(box, float)
+    for _ in range(nsteps):
+        x = x + dt * v
+        x = np.where(x < 0, x + box, x)
+        x = np.where(x >= box, x - box, x)
+    return x
+
+
 def verlet(model, x, v, dt, nsteps, F=None, q_hist=None):
     """Velocity Verlet (dt in fs): v += dt/2 a; x += dt v (wrapped into the box);
     recompute forces; v += dt/2 a. Returns x, v, F and per-step total energy."""

@@ -209,7 +209,10 @@ __global__ void k_kick_drift(Sys s, const double* mass_t, double dt, int drift, 
   s.vx[i] = vx; s.vy[i] = vy; s.vz[i] = vz;
   if (drift) {
     const double* L = s.box + 3 * s.rep[i];
-    double p[3] = {s.x[i] + dt * vx, s.y[i] + dt * vy, s.z[i] + dt * vz};
+    // x + dt v with the product and the sum rounded separately (no fused multiply-add),
+    // so that a host reproduces the drift bit for bit
+    double p[3] = {__dadd_rn(s.x[i], __dmul_rn(dt, vx)), __dadd_rn(s.y[i], __dmul_rn(dt, vy)),
+                   __dadd_rn(s.z[i], __dmul_rn(dt, vz))};
     for (int d = 0; d < 3; ++d) {
       if (p[d] < 0.0) { p[d] += L[d]; s.img[3 * i + d] -= 1; }
       if (p[d] >= L[d]) { p[d] -= L[d]; s.img[3 * i + d] += 1; }

@@ -14,6 +14,7 @@ import numpy as np
 MAXT = 8
 NTERMS = 13
 TERMS = ("bond", "lp", "over", "under", "val", "pen", "coa", "tors", "conj", "hbond", "vdw", "coul", "pol")
+NO_TERMS = 1 << NTERMS     # term mask that selects no term: zero forces (free flight)
 OK, E_INVALID, E_CUDA, E_CAPACITY, E_NOT_CONVERGED, E_TIMEOUT, E_NAN, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, MIXED = 0, 1
 WARM_EXTRAP, WARM_ZERO, WARM_MLP, WARM_LAGRANGE = 0, 1, 2, 3

@@ -35,6 +35,13 @@ def workload(name: str, seed: int = 0, temperature: float = 300.0):
     return dict(types=types, x=x, v=v, box=np.asarray(box, float), options=opts)
 
 
+def fixed_charges(n: int, seed: int = 0, scale: float = 0.3):
+    """Seeded neutral charges (e) for evaluating forces at fixed charges: normal with standard
+    deviation `scale`, shifted to zero sum."""
+    q = np.random.default_rng(seed).normal(0.0, scale, n)
+    return q - q.mean()
+
+
 def batch_shapes(nrep: int = 64, seed: int = 0):
     """Seeded uneven replica shapes from 2x2x2 to 8x4x4 cells and temperatures 250-350 K."""
     rng = np.random.default_rng(seed)

@@ -272,15 +272,19 @@ def test_batched_replicas_match_single_runs(rx, params):
 
 @pytest.mark.parametrize("skin", [0.02, 1.0, -1.0])
 def test_lists_stay_exact_along_md(rx, params, skin):
-    """After MD steps that move atoms across box faces (hot start) the far, bond and
-    H-bond lists of the running context equal the oracle's lists at the final positions,
-    with the skin candidate list rebuilt often (0.02 A), rarely (1 A) or not used (< 0)."""
+    """After steps that move atoms across box faces (3000 K velocities, every term off so
+    that the positions are the host's own free flight, bit for bit) the far, bond and H-bond
+    lists of the running context equal the oracle's lists at those positions, with the skin
+    candidate list rebuilt often (0.02 A), rarely (1 A) or not used (< 0)."""
     w = synth.workload("cluster300", temperature=3000.0)
     n = len(w["x"])
-    c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=1, skin=skin)
+    assert np.all((w["x"] >= 0) & (w["x"] < w["box"]))
+    c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=1, skin=skin, term_mask=rx.NO_TERMS)
     c.set_state(w["x"], w["v"])
     c.step(30, 0.5)
-    x, _, _ = c.get_state()
+    xg, vg, _ = c.get_state()
+    x = oracle.free_flight(w["x"], w["v"], w["box"], 0.5, 30)
+    assert np.array_equal(xg, x) and np.array_equal(vg, w["v"])
     L = oracle.build_lists(x, w["types"], w["box"], params, w["options"])
     B = L["bond"]
     want = {
@@ -297,7 +301,7 @@ def test_lists_stay_exact_along_md(rx, params, skin):
 
 def test_candidates_cover_pairs_two_cells_apart(rx, params):
     """Two atoms 10.6 A apart across two cell boundaries of a 10.5 A grid (box 31.5 A)
-    drift towards each other by 0.35 A each (below the skin/2 rebuild trigger): the
+    fly towards each other by 0.35 A each (below the skin/2 rebuild trigger): the
     pair, now 9.9 A apart, must be in the far list. The candidate cells have to be at
     least r_nb + skin wide for the 27-cell stencil to have seen it at the build."""
     box = np.array([31.5, 31.5, 31.5])
@@ -305,10 +309,12 @@ def test_candidates_cover_pairs_two_cells_apart(rx, params):
     v = np.array([[0.035, 0.0, 0.0], [-0.035, 0.0, 0.0]])
     types = np.array([0, 0], np.int32)
     o = dict(synth.OPTIONS_DEFAULT)
-    c = rx.ReaxFF(params, types, box, o, precision=1, skin=1.0)
+    c = rx.ReaxFF(params, types, box, o, precision=1, skin=1.0, term_mask=rx.NO_TERMS)
     c.set_state(x, v)
     c.step(20, 0.5)
-    xf, _, _ = c.get_state()
+    xg, _, _ = c.get_state()
+    xf = oracle.free_flight(x, v, box, 0.5, 20)            # every term off: straight lines
+    assert np.array_equal(xg, xf)
     assert abs(np.linalg.norm(xf[1] - xf[0]) - 9.9) < 0.01
     L = oracle.build_lists(xf, types, box, params, o)
     want = keyset(L["far"]["i"], L["far"]["j"], L["far"]["s"], 2)

@@ -511,3 +511,21 @@ def test_verlet_free_particles_move_ballistically(params):
     assert np.abs(F).max() == 0.0
     assert np.array_equal(x1, x + 0.1 * v)
     assert np.array_equal(v1, v)
+
+
+def test_free_flight_is_verlet_with_every_term_off():
+    """Free flight equals the oracle's velocity Verlet on a model whose terms are all off
+    (zero forces), bit for bit, and the straight line x + k dt v folded into the box."""
+    P = synth.make_params()
+    w = synth.workload("cluster150", temperature=3000.0)
+    m = oracle.Model(P, w["types"], w["box"], w["options"], term_mask=())
+    xv, vv, F, _ = oracle.verlet(m, w["x"], w["v"], 0.5, 6)
+    assert np.all(F == 0.0) and np.array_equal(vv, w["v"])
+    xf = oracle.free_flight(w["x"], w["v"], w["box"], 0.5, 6)
+    assert np.array_equal(xf, xv)
+    assert np.all((xf >= 0) & (xf < w["box"]))
+    line = np.mod(w["x"] + 6 * 0.5 * w["v"], w["box"])
+    d = xf - line
+    d -= w["box"] * np.round(d / w["box"])
+    assert np.abs(d).max() < 1e-12
+    assert np.abs(xf - w["x"]).max() > 0.1                   # the atoms did move
