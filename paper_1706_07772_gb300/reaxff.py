@@ -280,6 +280,12 @@ class ReaxFF:
     def build_lists(self):
         self._check(self.lib.reaxff_build_lists(self.h))
 
+    def list_count(self, which):
+        """Entries of a list (both directions for the far and bond lists)."""
+        cnt = C.c_int64()
+        self._check(self.lib.reaxff_get_lists(self.h, which, 0, C.byref(cnt), None, None, None))
+        return cnt.value
+
     def get_lists(self, which):
         cnt = C.c_int64()
         self._check(self.lib.reaxff_get_lists(self.h, which, 0, C.byref(cnt), None, None, None))
