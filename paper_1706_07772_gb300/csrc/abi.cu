@@ -164,6 +164,16 @@ template <typename R> void fill_params(DParams<R>& d, const reaxff_params& p, co
       d.lr0p[k] = p.r0p[a][b] > 0 ? (R)std::log(p.r0p[a][b]) : R(0);
       d.lr0pp[k] = p.r0pp[a][b] > 0 ? (R)std::log(p.r0pp[a][b]) : R(0);
       d.gamma_m3[k] = (R)std::pow(p.gamma[a][b], -3.0);
+      {
+        R* t = d.nbf + 8 * k;
+        const double al = p.vdw_alpha[a][b], rv = p.vdw_rv[a][b], D = p.vdw_D[a][b];
+        t[0] = (R)std::pow(p.vdw_gw[a][b], -p.p_vdW1);
+        t[1] = (R)(al * 1.4426950408889634);
+        t[2] = (R)(1.0 / rv);
+        t[3] = (R)D;
+        t[4] = (R)std::pow(p.gamma[a][b], -3.0);
+        t[5] = (R)(-D * al / rv);
+      }
       for (int c = 0; c < MAXT; ++c) {
         const int t3 = (a * MAXT + b) * MAXT + c;
         d.th00[t3] = (R)p.th00[a][b][c]; d.p_val1[t3] = (R)p.p_val1[a][b][c];

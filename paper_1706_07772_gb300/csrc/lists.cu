@@ -690,8 +690,8 @@ __device__ __forceinline__ float rcbrt_f(float x) {
 
 // Mixed path form of k_cand_filter: atom i's records, box and image counters live in
 // registers; the shift code is decoded once; atom j's two 16-byte records are read once and
-// give the exact-order float-float image vector used both for the range decisions (its error
-// is far inside the margins) and for H; H = Tap(r) k_e (r^3 + gamma^-3)^(-1/3) with one
+// give the FP32 image vector used both for the range decisions (its error is far inside the
+// margins) and for H; H = Tap(r) k_e (r^3 + gamma^-3)^(-1/3) with one
 // branch-free rcbrt_f for near and far entries; the near/far destination is a per-lane
 // select, so the stores do not diverge.
 __global__ void k_cand_filter_f(Sys s, CandList cl, FarList f, HbList hl, const DParams<float>* __restrict__ P,
@@ -734,9 +734,13 @@ __global__ void k_cand_filter_f(Sys s, CandList cl, FarList f, HbList hl, const 
       if (sx >= -1 && sx <= 1 && sy >= -1 && sy <= 1 && sz >= -1 && sz <= 1) {
         code = (sx + 1) * 9 + (sy + 1) * 3 + (sz + 1);
         tj = rec_type(lj.w);
-        const float dx = pv_comp(hj.x, hi.x, lj.x, li.x, sx, Lh0, Ll0);
-        const float dy = pv_comp(hj.y, hi.y, lj.y, li.y, sy, Lh1, Ll1);
-        const float dz = pv_comp(hj.z, hi.z, lj.z, li.z, sz, Lh2, Ll2);
+        // plain FP32 image vector (hi difference + lo difference, image shift by exact
+        // products): |error of r^2| <= u (3.5 r L_max + 8 r^2), inside the decision margins
+        // 32 u (L_max R + R^2) by a factor of ~8; pairs inside a margin are decided in FP64
+        const float fx = (float)sx, fy = (float)sy, fz = (float)sz;
+        const float dx = fmaf(fx, Lh0, hj.x - hi.x) + fmaf(fx, Ll0, lj.x - li.x);
+        const float dy = fmaf(fy, Lh1, hj.y - hi.y) + fmaf(fy, Ll1, lj.y - li.y);
+        const float dz = fmaf(fz, Lh2, hj.z - hi.z) + fmaf(fz, Ll2, lj.z - li.z);
         r2f = dx * dx + dy * dy + dz * dz;
         ok = !(j == i && code == 13) && in_range(s, i, j, code, r, r2f, R2f, margin, R2);
         if (ok) near = in_range(s, i, j, code, r, r2f, Rb2f, margin_near, Rb2);

@@ -103,54 +103,80 @@ __device__ __forceinline__ float rsqa(float x) {
 }
 
 // one far directed pair (r_bond <= r < r_nb) on the mixed path: the terms of nb_pair with
-// r^-1 from rsqrt, x^y = 2^(y log2 x), e^x = 2^(x log2 e) and reciprocals by rcp
+// r^-1 from rsqrt, x^y = 2^(y log2 x), e^x = 2^(x log2 e) and reciprocals by rcp. The image
+// vector is the plain FP32 difference of the hi parts plus that of the lo parts: its error
+// (half an ulp of the hi difference, < 4e-6 A for a 100 A box) is < 1e-6 of r at r >= r_bond,
+// far below the accuracy of these approximations. Atom i's records, the box halves, the
+// constants of the pair type (`pt`: 2 x float4, see DParams::nbf) and the image signs
+// (`sg`, one float4 per code) come from the caller. Accumulates the force and the UNSCALED
+// pair virial d F^T (the caller multiplies by -1/2).
+struct FarAtom {
+  float4 hi, li;
+  float Lhx, Lhy, Lhz, Llx, Lly, Llz;
+  float kqi, wv, wc, iRc, pv, ipv;
+};
 template <typename A>
-__device__ __forceinline__ void nb_pair_far(const Sys& s, const DParams<float>* __restrict__ P, int i, int j, int code,
-                                            int r, int ti, float qi, float wv, float wc, float iRc, float pv, float ipv,
-                                            A& ev, A& ec, A& fx, A& fy, A& fz, A* w) {
-  float dx, dy, dz;
-  float4 hj, lj;
-  PairVec<float>::getv(s, i, j, code, r, dx, dy, dz, hj, lj);
+__device__ __forceinline__ void nb_pair_far(const Sys& s, const FarAtom& a, const float4* __restrict__ sg_tab,
+                                            const float4* __restrict__ pt_tab, int j, int code, A& ev, A& ec,
+                                            A& fx, A& fy, A& fz, A* w) {
+  const float4 hj = s.ph[j], lj = s.pl[j];
+  const float4 sg = sg_tab[code];
+  const float dx = fmaf(sg.x, a.Lhx, hj.x - a.hi.x) + fmaf(sg.x, a.Llx, lj.x - a.li.x);
+  const float dy = fmaf(sg.y, a.Lhy, hj.y - a.hi.y) + fmaf(sg.y, a.Lly, lj.y - a.li.y);
+  const float dz = fmaf(sg.z, a.Lhz, hj.z - a.hi.z) + fmaf(sg.z, a.Llz, lj.z - a.li.z);
   const float r2 = dx * dx + dy * dy + dz * dz;
   const float ir = rsqa(r2);
   const float rr = r2 * ir;
-  const float x = rr * iRc, x2 = x * x, x3 = x2 * x;
+  const float x = rr * a.iRc, x2 = x * x, x3 = x2 * x;
   const float tap = ((((20.0f * x - 70.0f) * x + 84.0f) * x - 35.0f) * x2 * x2) + 1.0f;
-  const float dtap = ((((140.0f * x - 420.0f) * x + 420.0f) * x - 140.0f) * x3) * iRc;
-  const int pt = ti * MAXT + rec_type(lj.w);
+  const float dtap = ((((140.0f * x - 420.0f) * x + 420.0f) * x - 140.0f) * x3) * a.iRc;
+  const float4 c0 = pt_tab[2 * rec_type(lj.w)], c1 = pt_tab[2 * rec_type(lj.w) + 1];
   // van der Waals
-  const float rp = ex2a(pv * lg2a(rr));
-  const float base = rp + P->vdw_gw_pow[pt];
-  const float f13 = ex2a(ipv * lg2a(base));
+  const float rp = ex2a(a.pv * lg2a(rr));
+  const float base = rp + c0.x;
+  const float f13 = ex2a(a.ipv * lg2a(base));
   const float df13 = f13 * rp * ir * rcpa(base);
-  const float al = P->vdw_alpha[pt], irv = rcpa(P->vdw_rv[pt]), D = P->vdw_D[pt];
-  const float t = al * (1.0f - f13 * irv) * 1.44269504088896341f;   // al (1 - f13/rv) log2(e)
+  const float t = c0.y * fmaf(-f13, c0.z, 1.0f);          // alpha (1 - f13/rv) log2(e)
   const float E1 = ex2a(t), E2 = ex2a(0.5f * t);
-  const float evp = D * (E1 - 2.0f * E2);
-  const float devp = -(D * al * irv) * (E1 - E2);
+  const float evp = c0.w * fmaf(-2.0f, E2, E1);
+  const float devp = c1.y * (E1 - E2);
   // Coulomb
-  const float sh3 = r2 * rr + P->gamma_m3[pt];
+  const float sh3 = fmaf(r2, rr, c1.x);
   const float ish = ex2a(-0.333333343f * lg2a(sh3));
-  const float kq = P->k_e * qi * hj.w;
+  const float kq = a.kqi * hj.w;
   const float ecp = kq * ish;
   const float ish2 = ish * ish;
   const float decp = -kq * r2 * ish2 * ish2;
   ev += (A)(tap * evp);
   ec += (A)(tap * ecp);
-  const float de = wv * (dtap * evp + tap * devp * df13) + wc * (dtap * ecp + tap * decp);
+  const float de = a.wv * (dtap * evp + tap * devp * df13) + a.wc * (dtap * ecp + tap * decp);
   const float c = de * ir;
-  fx += (A)(c * dx);
-  fy += (A)(c * dy);
-  fz += (A)(c * dz);
-  const float hc = -0.5f * c;
-  w[0] += (A)(hc * dx * dx); w[1] += (A)(hc * dy * dy); w[2] += (A)(hc * dz * dz);
-  w[3] += (A)(hc * dx * dy); w[4] += (A)(hc * dx * dz); w[5] += (A)(hc * dy * dz);
+  const float px = c * dx, py = c * dy, pz = c * dz;
+  fx += (A)px;
+  fy += (A)py;
+  fz += (A)pz;
+  w[0] += (A)(px * dx); w[1] += (A)(py * dy); w[2] += (A)(pz * dz);
+  w[3] += (A)(px * dy); w[4] += (A)(px * dz); w[5] += (A)(py * dz);
 }
 
 template <typename R>
 __global__ void k_nonbonded(Sys s, FarList f, Accum acc, const DParams<R>* __restrict__ P, unsigned mask) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  // mixed path: image signs per shift code and the far-pair constants, staged once per block
+  __shared__ float4 sg_tab[27];
+  __shared__ float4 pt_tab[MAXT * MAXT * 2];
+  if constexpr (sizeof(R) == 4) {
+    for (int t = threadIdx.x; t < 27 + MAXT * MAXT * 2; t += blockDim.x) {
+      if (t < 27) {
+        sg_tab[t] = make_float4((float)(t / 9 - 1), (float)((t / 3) % 3 - 1), (float)(t % 3 - 1), 0.0f);
+      } else {
+        const float* c = reinterpret_cast<const float*>(P->nbf) + 4 * (t - 27);
+        pt_tab[t - 27] = make_float4(c[0], c[1], c[2], c[3]);
+      }
+    }
+    __syncthreads();
+  }
   if (i >= s.n) return;
   const int ti = s.type[i];
   const int r = s.rep[i];
@@ -167,9 +193,19 @@ __global__ void k_nonbonded(Sys s, FarList f, Accum acc, const DParams<R>* __res
   R lev = 0, lec = 0, lfx = 0, lfy = 0, lfz = 0, lw[6] = {0, 0, 0, 0, 0, 0};
   const int nfa = f.cnt[i], rowf = i * f.cap;
   if constexpr (sizeof(R) == 4) {
-    const float iRc = 1.0f / P->r_nb, pv = P->p_vdW1, ipv = 1.0f / P->p_vdW1;
+    FarAtom a;
+    a.hi = s.ph[i];
+    a.li = s.pl[i];
+    a.Lhx = s.boxh[3 * r]; a.Lhy = s.boxh[3 * r + 1]; a.Lhz = s.boxh[3 * r + 2];
+    a.Llx = s.boxl[3 * r]; a.Lly = s.boxl[3 * r + 1]; a.Llz = s.boxl[3 * r + 2];
+    a.kqi = P->k_e * qi;
+    a.wv = wv; a.wc = wc;
+    a.iRc = 1.0f / P->r_nb; a.pv = P->p_vdW1; a.ipv = 1.0f / P->p_vdW1;
+    const float4* pt = pt_tab + 2 * MAXT * ti;
     for (int k = lane; k < nfa; k += 32)
-      nb_pair_far<R>(s, P, i, f.j[rowf + k], f.s[rowf + k], r, ti, qi, wv, wc, iRc, pv, ipv, lev, lec, lfx, lfy, lfz, lw);
+      nb_pair_far<R>(s, a, sg_tab, pt, f.j[rowf + k], f.s[rowf + k], lev, lec, lfx, lfy, lfz, lw);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) lw[q] *= -0.5f;        // half of W_ab = -dE/dr d_a d_b / r (exact)
   } else {
     for (int k = lane; k < nfa; k += 32)
       nb_pair<R, true, R>(s, P, i, f.j[rowf + k], f.s[rowf + k], r, ti, qi, wv, wc, lev, lec, lfx, lfy, lfz, lw);

@@ -64,6 +64,9 @@ struct DParams {
   int bcut_ok[MAXT * MAXT];
   R V1[MAXT * MAXT], V2[MAXT * MAXT], V3[MAXT * MAXT], p_tor1[MAXT * MAXT], p_cot1[MAXT * MAXT];
   R r0hb[MAXT * MAXT], p_hb1[MAXT * MAXT], p_hb2[MAXT * MAXT], p_hb3[MAXT * MAXT];
+  // far-pair constants per type pair, rounded once from FP64 (mixed-path nonbonded):
+  // [gw^-p_vdW1, alpha log2(e), 1/r_vdW, D, gamma^-3, -D alpha / r_vdW, 0, 0]
+  alignas(16) R nbf[MAXT * MAXT * 8];
   R p_boc1, p_boc2, p_lp1, p_ovun3, p_ovun4, p_ovun6, p_ovun7, p_ovun8, p_val6, p_val8, p_val9,
       p_val10, p_pen2, p_pen3, p_pen4, p_coa2, p_coa3, p_coa4, p_tor2, p_tor3, p_tor4, p_cot2,
       p_vdW1, k_e;
