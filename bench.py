@@ -274,7 +274,7 @@ def run_ours(a, rank, world):
                    "l2": "flushed (256 MB write) before each library call of %d steps; each step streams > 200 MB of lists" % CALL_STEPS,
                    "parallelism": "independent system per GPU" if world > 1 else "single GPU",
                    "schedule": dict(zip(("torsion_lanes", "nonbonded_block", "filter_block", "bond_list_block",
-                                         "angle_block", "hbond_block", "angle_lanes"), schedule))},
+                                         "angle_block", "hbond_block", "angle_lanes", "qeq_beside_terms"), schedule))},
         "clocks": clocks.summary(),
         "gpu_launches": launches,
         "qeq_iters_last": [int(its[0]), int(itt[0])],

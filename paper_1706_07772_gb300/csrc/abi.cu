@@ -431,8 +431,14 @@ template <typename R> const DParams<R>* params_of(reaxff_ctx* ctx);
 template <> const DParams<double>* params_of<double>(reaxff_ctx* ctx) { return ctx->Pd; }
 template <> const DParams<float>* params_of<float>(reaxff_ctx* ctx) { return ctx->Pf; }
 
-int qeq_impl(reaxff_ctx* ctx) {
+// side: on the second stream with the CG on 512 or 256 threads per SM (schedule), beside the
+// charge-free terms (mixed path). The serial order with the stage timers on launches the CG
+// in the shape the schedule gives it, so that its stage time is that launch's own.
+int qeq_impl(reaxff_ctx* ctx, bool side = false) {
   rx::Launch L = launch_of(ctx);
+  if (side) L.st = ctx->st2;
+  const int ovl = (side || (ctx->prof && !ctx->fp64)) ? ctx->tune.qeq_overlap : 0;
+  const int threads = ovl == 2 ? 256 : ovl == 1 ? 512 : 1024;
   const float* qhat = nullptr;
   if (ctx->ho.warm_start == REAXFF_WARM_MLP && ctx->mlp.alloc && ctx->mlp.ready) {
     // learned guess: descriptors of the current lists, tensor-core forward
@@ -450,11 +456,45 @@ int qeq_impl(reaxff_ctx* ctx) {
   int rc = ctx->fp64 ? rx::qeq_solve<double>(L, ctx->sys, ctx->far, ctx->Q, ctx->Pd, ctx->chi_t, ctx->eta_t,
                                              ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start, qhat)
                      : rx::qeq_solve<float>(L, ctx->sys, ctx->far, ctx->Q, ctx->Pf, ctx->chi_t, ctx->eta_t,
-                                            ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start, qhat);
+                                            ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start, qhat,
+                                            threads);
   if (rc) {
     cudaError_t e = cudaGetLastError();
     return fail(ctx, REAXFF_E_CUDA, "cooperative QEq launch failed: " + cuda_err_str(e));
   }
+  return REAXFF_OK;
+}
+
+// Mixed path with the solve beside the charge-free terms. QEq (k_cg on 512 or 256 threads per
+// SM, with the largest shared-memory carveout,
+// then the nonbonded kernel, the only charge-dependent term) runs on the second stream; the
+// bond-order corrections, atom terms, angles, torsions, H-bonds and the chain rule run on the
+// main stream meanwhile. Neither side reads what the other writes (the solve writes charges,
+// solutions and its own state; the terms read positions, bond data and write per-atom
+// quantities, bond accumulators and, like the nonbonded kernel, forces, energies and the
+// virial only through exact fixed-point atomics), so nothing races. The results agree with
+// the serial order to within rounding: with fewer threads each CG thread takes several rows,
+// which changes the order of the FP64 dot-product partials. Fork and join by events (graph
+// edges under stream capture).
+int forces_overlap(reaxff_ctx* ctx) {
+  rx::Launch L = launch_of(ctx);
+  const DParams<float>* P = ctx->Pf;
+  cudaEventRecord(ctx->ev_fork, ctx->st);
+  cudaStreamWaitEvent(ctx->st2, ctx->ev_fork, 0);
+  int rc = qeq_impl(ctx, true);
+  if (rc) return rc;
+  rx::Launch L2{ctx->st2, &ctx->launches, &ctx->tune};
+  rx::nonbonded<float>(L2, ctx->sys, ctx->far, ctx->acc, P, ctx->mask);
+  cudaEventRecord(ctx->ev_join, ctx->st2);
+  rx::bo_correct<float>(L, ctx->sys, ctx->bond, ctx->aq, P);
+  rx::atom_terms<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  rx::over_under_bond<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  rx::s_gather<float>(L, ctx->sys, ctx->bond, ctx->aq);
+  rx::angles<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  rx::torsions<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  rx::hbonds<float>(L, ctx->sys, ctx->bond, ctx->hb, ctx->acc, P, ctx->mask);
+  rx::chain_rule<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc);
+  CK(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
   return REAXFF_OK;
 }
 
@@ -509,12 +549,17 @@ int forces_impl(reaxff_ctx* ctx, bool solve_q, bool reduce = true, bool checked 
   if (rc) return rc;
   rc = zero_accumulators(ctx);
   if (rc) return rc;
-  if (solve_q) {
-    rc = qeq_impl(ctx);
+  if (solve_q && !ctx->fp64 && !ctx->prof && ctx->tune.qeq_overlap) {
+    rc = forces_overlap(ctx);
     if (rc) return rc;
+  } else {
+    if (solve_q) {
+      rc = qeq_impl(ctx);
+      if (rc) return rc;
+    }
+    if (ctx->fp64) terms_impl<double>(ctx);
+    else terms_impl<float>(ctx);
   }
-  if (ctx->fp64) terms_impl<double>(ctx);
-  else terms_impl<float>(ctx);
   if (reduce) {
     Stage st(ctx, 15);
     rx::reduce_energies(launch_of(ctx), ctx->sys, ctx->acc, ctx->mass_t, ctx->red, ctx->E_rep, ctx->vir_rep, ctx->ke_rep);
@@ -665,7 +710,13 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   int coop = 0;
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking);
-  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) {
+    // the second stream at the highest priority: the solve's blocks are placed before those of
+    // the kernels beside it
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    ce = cudaStreamCreateWithPriority(&ctx->st2, cudaStreamNonBlocking, hi);
+  }
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
   if (ce != cudaSuccess || !coop) {
@@ -2057,6 +2108,20 @@ template <typename R> void tune_all(reaxff_ctx* ctx) {
     cudaMemsetAsync(ctx->bond.ncanon, 0, sizeof(int), ctx->st);
     rx::bond_list<R>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, P, ctx->Pd, ctx->use_skin);
   });
+  // the solve beside the charge-free terms or before them: whole force evaluations timed.
+  // Repeated at the same positions, a warm-started solve would converge at once; each timed
+  // solve instead starts without history and is capped at 8 SpMVs, about those of an MD step
+  // (the capped solves' flags are cleared by the checked evaluation that follows tuning)
+  if (!ctx->fp64) {
+    const int mi = ctx->ho.qeq_max_iter;
+    ctx->ho.qeq_max_iter = 7;
+    pick(T.qeq_overlap, {0, 1, 2}, [&] {
+      cudaMemsetAsync(ctx->Q.hst + 2, 0, sizeof(int), ctx->st);
+      forces_impl(ctx, true, true, false);
+    });
+    ctx->ho.qeq_max_iter = mi;
+    cudaMemsetAsync(ctx->Q.hst + 2, 0, sizeof(int), ctx->st);
+  }
 }
 
 std::string tune_key(reaxff_ctx* ctx) {
@@ -2092,8 +2157,9 @@ int reaxff_autotune(reaxff_ctx* ctx, const char* cache_path, int32_t* schedule) 
       while (fgets(line, sizeof(line), f)) {
         rx::Tune t{};
         char k[256];
-        if (sscanf(line, "reaxff-tune %255[^|]| tors=%d nb=%d cf=%d bl=%d ang=%d hb=%d angl=%d", k, &t.tors_lanes,
-                   &t.nb_block, &t.cf_block, &t.bl_block, &t.ang_block, &t.hb_block, &t.ang_lanes) == 8 &&
+        if (sscanf(line, "reaxff-tune %255[^|]| tors=%d nb=%d cf=%d bl=%d ang=%d hb=%d angl=%d qov=%d", k,
+                   &t.tors_lanes, &t.nb_block, &t.cf_block, &t.bl_block, &t.ang_block, &t.hb_block, &t.ang_lanes,
+                   &t.qeq_overlap) == 9 &&
             key == std::string(k).substr(0, std::string(k).find_last_not_of(' ') + 1)) {
           ctx->tune = t;
           found = true;
@@ -2113,8 +2179,9 @@ int reaxff_autotune(reaxff_ctx* ctx, const char* cache_path, int32_t* schedule) 
     if (cache_path) {
       if (FILE* f = fopen(cache_path, "a")) {
         const rx::Tune& t = ctx->tune;
-        fprintf(f, "reaxff-tune %s | tors=%d nb=%d cf=%d bl=%d ang=%d hb=%d angl=%d\n", key.c_str(), t.tors_lanes,
-                t.nb_block, t.cf_block, t.bl_block, t.ang_block, t.hb_block, t.ang_lanes);
+        fprintf(f, "reaxff-tune %s | tors=%d nb=%d cf=%d bl=%d ang=%d hb=%d angl=%d qov=%d\n", key.c_str(),
+                t.tors_lanes, t.nb_block, t.cf_block, t.bl_block, t.ang_block, t.hb_block, t.ang_lanes,
+                t.qeq_overlap);
         fclose(f);
       }
     }
@@ -2122,8 +2189,9 @@ int reaxff_autotune(reaxff_ctx* ctx, const char* cache_path, int32_t* schedule) 
   drop_graph(ctx);                                              // schedules are baked into the graph
   if (schedule) {
     const rx::Tune& t = ctx->tune;
-    const int v[7] = {t.tors_lanes, t.nb_block, t.cf_block, t.bl_block, t.ang_block, t.hb_block, t.ang_lanes};
-    for (int q = 0; q < 7; ++q) schedule[q] = v[q];
+    const int v[8] = {t.tors_lanes, t.nb_block, t.cf_block, t.bl_block, t.ang_block, t.hb_block, t.ang_lanes,
+                      t.qeq_overlap};
+    for (int q = 0; q < 8; ++q) schedule[q] = v[q];
   }
   return REAXFF_OK;
 }

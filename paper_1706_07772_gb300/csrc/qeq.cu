@@ -301,9 +301,12 @@ __device__ __forceinline__ void spmv_part(const int* cnt, const int* col, const 
 // where the lanes' sums are combined and stored. Zero-filled entries gather zg[0] with
 // h = 0 and add an exact zero. Rows start on 16-byte boundaries (capacities are multiples
 // of 32 entries).
+// The ring holds SP_RING_SLOTS slots per block: SP_SLOTS per warp at 32 warps, twice as many
+// per warp at 16 warps (the same bytes in flight per SM with half the threads).
 constexpr int SP_SLOTS = 3;
+constexpr int SP_RING_SLOTS = 32 * SP_SLOTS;
 constexpr int SP_SLOT_BYTES = 1024;
-constexpr int SP_RING_BYTES = 32 * SP_SLOTS * SP_SLOT_BYTES + 32 * SP_SLOTS * 4;   // slots, then tags
+constexpr int SP_RING_BYTES = SP_RING_SLOTS * SP_SLOT_BYTES + SP_RING_SLOTS * 4;   // slots, then tags
 
 struct SpCursor {
   int i, part, k0;             // next item: row, part (0 near, 1 far), first entry
@@ -352,25 +355,27 @@ __device__ __forceinline__ int sp_issue(const CG<float>& a, SpCursor& c, int whi
   return tag + 1;
 }
 
+template <int SLOTS>
 __device__ __forceinline__ void spmv_ring_f(const CG<float>& a, unsigned char* ring, int wlo, int whi, float* us,
                                             float* ut) {
+  static_assert(SLOTS * 32 <= SP_RING_SLOTS * 32 && SP_RING_SLOTS % SLOTS == 0, "ring slots");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const float2* zg = (const float2*)a.zg;
-  unsigned char* mine = ring + wid * SP_SLOTS * SP_SLOT_BYTES;
-  int* tags = (int*)(ring + 32 * SP_SLOTS * SP_SLOT_BYTES) + wid * SP_SLOTS;
+  unsigned char* mine = ring + wid * SLOTS * SP_SLOT_BYTES;
+  int* tags = (int*)(ring + SP_RING_SLOTS * SP_SLOT_BYTES) + wid * SLOTS;
   const unsigned sbase = (unsigned)__cvta_generic_to_shared(mine);
   SpCursor c;
   c.i = wlo; c.part = 0; c.k0 = 0; c.bb = wlo;
   sp_counts(a, c, whi);
 #pragma unroll
-  for (int sl = 0; sl < SP_SLOTS; ++sl) {
+  for (int sl = 0; sl < SLOTS; ++sl) {
     const int tag = c.i < whi ? sp_issue(a, c, whi, sbase + sl * SP_SLOT_BYTES) : -1;
     if (lane == 0) tags[sl] = tag;
     cp_commit();
   }
   float sf = 0.f, tf = 0.f;
-  for (int sl = 0;; sl = sl + 1 == SP_SLOTS ? 0 : sl + 1) {
-    asm volatile("cp.async.wait_group %0;" ::"n"(SP_SLOTS - 1) : "memory");
+  for (int sl = 0;; sl = sl + 1 == SLOTS ? 0 : sl + 1) {
+    asm volatile("cp.async.wait_group %0;" ::"n"(SLOTS - 1) : "memory");
     __syncwarp();
     const int tag = tags[sl];
     if (tag < 0) break;
@@ -433,7 +438,11 @@ __device__ __forceinline__ void spmv_chunk(const CG<R>& a, const Blk& B, int lo,
   R* us = B.u<R>(0);
   R* ut = B.u<R>(1);
   if constexpr (sizeof(R) == 4) {
-    if (wlo < whi) spmv_ring_f(a, B.ring, wlo, whi, us + off - lo, ut + off - lo);
+    if (wlo < whi) {
+      if (nw == 8) spmv_ring_f<4 * SP_SLOTS>(a, B.ring, wlo, whi, us + off - lo, ut + off - lo);
+      else if (nw == 16) spmv_ring_f<2 * SP_SLOTS>(a, B.ring, wlo, whi, us + off - lo, ut + off - lo);
+      else spmv_ring_f<SP_SLOTS>(a, B.ring, wlo, whi, us + off - lo, ut + off - lo);
+    }
     return;
   }
   for (int i = wlo; i < whi; ++i) {
@@ -527,8 +536,11 @@ __device__ __forceinline__ void count_active(double* S, int nrep) {
   __syncthreads();
 }
 
-template <typename R>
-__global__ void __launch_bounds__(1024, 1) k_cg(CG<R> a) {
+// NT threads per block, one block per SM; every loop is strided by blockDim.x. NT < 1024
+// is the shape for running beside other kernels (fewer registers held per SM); the register
+// budget stays 64 per thread for every NT.
+template <typename R, int NT = 1024>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_cg(CG<R> a) {
   extern __shared__ double dsm_all[];
   __shared__ Chunks<R> C;
   Blk B;
@@ -1018,7 +1030,7 @@ namespace rx {
 
 template <typename R>
 int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* P, const double* chi,
-              const double* eta, double tol, int max_iter, int warm, const float* qhat) {
+              const double* eta, double tol, int max_iter, int warm, const float* qhat, int threads) {
   (void)P;
   CG<R> a;
   a.n = s.n; a.nrep = s.nrep; a.nchunk = Q.nchunk; a.max_iter = max_iter;
@@ -1043,7 +1055,15 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   a.iters = Q.iters; a.spmv_total = Q.spmv_total; a.bar = Q.bar; a.err = s.err;
   cudaMemsetAsync(Q.bar, 0, sizeof(GridBar), L.st);
   void* args[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_cg<R>, dim3(Q.grid), dim3(1024), args, Q.smem_bytes, L.st);
+  // 1024 threads per SM, or 512 / 256 (mixed path) to leave registers and shared memory of
+  // each SM to kernels running beside the solve
+  void* fn = (void*)k_cg<R, 1024>;
+  int nt = 1024;
+  if constexpr (sizeof(R) == 4) {
+    if (threads == 512) { fn = (void*)k_cg<R, 512>; nt = 512; }
+    else if (threads == 256) { fn = (void*)k_cg<R, 256>; nt = 256; }
+  }
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(Q.grid), dim3(nt), args, Q.smem_bytes, L.st);
   *L.count += 2;
   return e == cudaSuccess ? 0 : -1;
 }
@@ -1060,6 +1080,13 @@ void qeq_precond_build(const Launch& L, Sys s, QeqState& Q) {
 int qeq_grid_size(int nsm) {
   cudaFuncSetAttribute((const void*)k_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, QEQ_SMEM_MAX);
   cudaFuncSetAttribute((const void*)k_cg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, QEQ_SMEM_MAX);
+  // the shapes that run beside other kernels prefer a 164 KB shared-memory carveout (72 % of
+  // the maximum): an SM holding a solve block (~130 KB) keeps room for the other kernels'
+  // shared memory and still 92 KB of L1 for the solve's gathers
+  for (const void* f : {(const void*)k_cg<float, 512>, (const void*)k_cg<float, 256>}) {
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, QEQ_SMEM_MAX);
+    cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 72);
+  }
   int per = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_cg<double>, 1024, QEQ_SMEM_MAX);
   int per_f = 0;
@@ -1070,7 +1097,7 @@ int qeq_grid_size(int nsm) {
 }
 
 template int qeq_solve<double>(const Launch&, Sys, FarList, QeqState&, const DParams<double>*, const double*,
-                               const double*, double, int, int, const float*);
+                               const double*, double, int, int, const float*, int);
 template int qeq_solve<float>(const Launch&, Sys, FarList, QeqState&, const DParams<float>*, const double*,
-                              const double*, double, int, int, const float*);
+                              const double*, double, int, int, const float*, int);
 }  // namespace rx

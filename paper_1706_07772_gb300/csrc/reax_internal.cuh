@@ -488,6 +488,8 @@ struct Tune {
   int ang_block = 128;         //   angles
   int ang_lanes = 8;           // lanes per centre atom in the angle kernel (8, 16, 32; mixed path)
   int hb_block = 128;          //   H-bonds (warp per hydrogen)
+  int qeq_overlap = 0;         // 1 / 2: QEq (CG on 512 / 256 threads per SM) runs beside the
+                               //    charge-free bond-order and bonded kernels (mixed path)
 };
 struct Launch {
   cudaStream_t st;
@@ -609,7 +611,7 @@ struct QeqState {
 // qhat (device, or null): learned charges offered as a second starting guess for s
 template <typename R>
 int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* P, const double* chi,
-              const double* eta, double tol, int max_iter, int warm, const float* qhat);
+              const double* eta, double tol, int max_iter, int warm, const float* qhat, int threads = 1024);
 int qeq_grid_size(int nsm);
 int qeq_ring_bytes(bool fp64);   // shared memory of the SpMV streaming ring of a 1024-thread block
 void qeq_precond_build(const Launch& L, Sys s, QeqState& Q);   // block-Jacobi inverses (no-op for Jacobi)

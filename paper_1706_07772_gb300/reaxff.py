@@ -459,8 +459,8 @@ class ReaxFF:
 
     def autotune(self, cache_path=None):
         """Pick launch schedules by timing; returns (torsion lanes, nonbonded, filter,
-        bond list, angles, H-bonds, angle lanes)."""
-        sch = np.empty(7, np.int32)
+        bond list, angles, H-bonds, angle lanes, QEq beside the charge-free terms)."""
+        sch = np.empty(8, np.int32)
         self._check(self.lib.reaxff_autotune(self.h, None if cache_path is None else str(cache_path).encode(),
                                              sch.ctypes.data_as(C.POINTER(C.c_int32))))
         return tuple(int(v) for v in sch)

@@ -21,7 +21,7 @@ def test_autotune_schedule_and_cache(params, tmp_path, prec):
     sch = c.autotune(cache)
     assert sch[0] in (2, 4, 8) and sch[1] in (128, 256, 512) and sch[2] in (128, 256, 512)
     assert sch[3] in (128, 256, 512) and sch[4] in (64, 128, 256) and sch[5] in (64, 128, 256)
-    assert sch[6] in (8, 16, 32)
+    assert sch[6] in (8, 16, 32) and sch[7] in (0, 1, 2)
     F1, E1, _ = c.forces(q=q)
     rms = np.sqrt((F0 ** 2).mean())
     assert np.abs(F1 - F0).max() < (1e-12 if prec == 0 else 1e-6) * rms
@@ -38,3 +38,40 @@ def test_autotune_schedule_and_cache(params, tmp_path, prec):
     assert np.abs(x1 - x2).max() < 1e-9
     c.close()
     c2.close()
+
+
+@pytest.mark.parametrize("name", ["petn464", "cluster300"])
+def test_qeq_beside_terms_matches_serial_order(params, tmp_path, name):
+    """The QEq solve on the second stream beside the charge-free terms (schedule entry 7 = 1
+    or 2: 512 or 256 threads per SM) and before them (0) give the same MD trajectory,
+    charges, forces and energies, to within the rounding of the CG dot products (their
+    partial sums follow the thread count)."""
+    import re
+
+    import paper_1706_07772_gb300.reaxff as rx
+    w = synth.workload(name)
+    c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=rx.MIXED)
+    c.set_state(w["x"], w["v"])
+    c.autotune(tmp_path / "tune.txt")
+    c.close()
+    line = (tmp_path / "tune.txt").read_text().strip()
+    assert re.search(r"qov=[012]$", line)
+    res = []
+    for qov in (0, 1, 2):
+        f = tmp_path / ("tune%d.txt" % qov)
+        f.write_text(re.sub(r"qov=[012]$", "qov=%d" % qov, line) + "\n")
+        c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=rx.MIXED)
+        c.set_state(w["x"], w["v"])
+        assert c.autotune(f)[7] == qov
+        e = c.step(20, 0.1)
+        x, v, q = c.get_state()
+        F, E, _ = c.forces()
+        res.append((e[:, 0], x, v, q, F, E[0]))
+        c.close()
+    e0, x0, v0, q0, F0, E0 = res[0]
+    for e1, x1, v1, q1, F1, E1 in res[1:]:
+        assert np.abs(x1 - x0).max() < 1e-9 and np.abs(v1 - v0).max() < 1e-9
+        assert np.abs(q1 - q0).max() < 1e-7
+        assert np.abs(F1 - F0).max() < 1e-6 * np.sqrt((F0 ** 2).mean())
+        assert np.abs(e1 - e0).max() < 1e-9 * np.abs(e0).max()
+        assert np.abs(E1.sum() - E0.sum()) < 1e-9 * abs(E0.sum())
