@@ -372,7 +372,16 @@ void grow_caps(reaxff_ctx* ctx, int flags) {
 // flags later (the error word is not cleared, so earlier flags of a batch survive).
 // drifted: the positions came from the fused drift kernel, which already wrote the float
 // records and ran the skin test
-int build_lists_impl(reaxff_ctx* ctx, bool checked = true, bool drifted = false) {
+// far_only (unchecked builds only): stop after the far and H-bond lists; the caller builds
+// the bond list (bond_lists_impl) later, beside the QEq solve
+void bond_lists_impl(reaxff_ctx* ctx, const rx::Launch& L) {
+  if (ctx->fp64) rx::bond_list<double>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pd, ctx->Pd, ctx->use_skin);
+  else rx::bond_list<float>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pf, ctx->Pd, ctx->use_skin);
+  rx::bond_mirror(L, ctx->sys, ctx->bond);
+  rx::bo_prime64(L, ctx->sys, ctx->bond, ctx->aq, ctx->Pd, ctx->n * ctx->bond.cap);
+}
+
+int build_lists_impl(reaxff_ctx* ctx, bool checked = true, bool drifted = false, bool far_only = false) {
   for (int attempt = 0; attempt < 3; ++attempt) {
     rx::Launch L = launch_of(ctx);
     if (checked) CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
@@ -388,23 +397,25 @@ int build_lists_impl(reaxff_ctx* ctx, bool checked = true, bool drifted = false)
         rx::cand_build(L, ctx->sys, ctx->cells, ctx->cand); }
       if (ctx->fp64) {
         { Stage st(ctx, 1); rx::cand_filter<double>(L, ctx->sys, ctx->cand, ctx->far, ctx->hb, ctx->Pd, ctx->far_margin, ctx->near_margin, ctx->hb_margin); }
-        { Stage st(ctx, 2); rx::bond_list<double>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pd, ctx->Pd, true); }
+        if (!far_only) { Stage st(ctx, 2); rx::bond_list<double>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pd, ctx->Pd, true); }
       } else {
         { Stage st(ctx, 1); rx::cand_filter<float>(L, ctx->sys, ctx->cand, ctx->far, ctx->hb, ctx->Pf, ctx->far_margin, ctx->near_margin, ctx->hb_margin); }
-        { Stage st(ctx, 2); rx::bond_list<float>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pf, ctx->Pd, true); }
+        if (!far_only) { Stage st(ctx, 2); rx::bond_list<float>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pf, ctx->Pd, true); }
       }
     } else {
     { Stage st(ctx, 0); rx::cells_build(L, ctx->sys, ctx->cells); }
     if (ctx->fp64) {
       { Stage st(ctx, 1); rx::far_list_split<double>(L, ctx->sys, ctx->cells, ctx->far, ctx->Pd, ctx->far_margin, ctx->near_margin); }
-      { Stage st(ctx, 2); rx::bond_list<double>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pd, ctx->Pd); }
+      if (!far_only) { Stage st(ctx, 2); rx::bond_list<double>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pd, ctx->Pd); }
     } else {
       { Stage st(ctx, 1); rx::far_list_split<float>(L, ctx->sys, ctx->cells, ctx->far, ctx->Pf, ctx->far_margin, ctx->near_margin); }
-      { Stage st(ctx, 2); rx::bond_list<float>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pf, ctx->Pd); }
+      if (!far_only) { Stage st(ctx, 2); rx::bond_list<float>(L, ctx->sys, ctx->far, ctx->bond, ctx->hb, ctx->aq, ctx->Pf, ctx->Pd); }
     }
     }
-    { Stage st(ctx, 2); rx::bond_mirror(L, ctx->sys, ctx->bond); }
-    { Stage st(ctx, 3); rx::bo_prime64(L, ctx->sys, ctx->bond, ctx->aq, ctx->Pd, ctx->n * ctx->bond.cap); }
+    if (!far_only) {
+      { Stage st(ctx, 2); rx::bond_mirror(L, ctx->sys, ctx->bond); }
+      { Stage st(ctx, 3); rx::bo_prime64(L, ctx->sys, ctx->bond, ctx->aq, ctx->Pd, ctx->n * ctx->bond.cap); }
+    }
     CK(cudaGetLastError());
     if (!checked) {
       ctx->lists_valid = true;
@@ -476,7 +487,7 @@ int qeq_impl(reaxff_ctx* ctx, bool side = false) {
 // the serial order to within rounding: with fewer threads each CG thread takes several rows,
 // which changes the order of the FP64 dot-product partials. Fork and join by events (graph
 // edges under stream capture).
-int forces_overlap(reaxff_ctx* ctx) {
+int forces_overlap(reaxff_ctx* ctx, bool bonds_pending) {
   rx::Launch L = launch_of(ctx);
   const DParams<float>* P = ctx->Pf;
   cudaEventRecord(ctx->ev_fork, ctx->st);
@@ -486,6 +497,7 @@ int forces_overlap(reaxff_ctx* ctx) {
   rx::Launch L2{ctx->st2, &ctx->launches, &ctx->tune};
   rx::nonbonded<float>(L2, ctx->sys, ctx->far, ctx->acc, P, ctx->mask);
   cudaEventRecord(ctx->ev_join, ctx->st2);
+  if (bonds_pending) bond_lists_impl(ctx, L);      // the solve reads only the far list
   rx::bo_correct<float>(L, ctx->sys, ctx->bond, ctx->aq, P);
   rx::atom_terms<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
   rx::over_under_bond<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
@@ -545,12 +557,16 @@ int zero_accumulators(reaxff_ctx* ctx) {
 // lists -> (QEq) -> all terms -> chain rule; energies reduced into E_rep / vir_rep
 int forces_impl(reaxff_ctx* ctx, bool solve_q, bool reduce = true, bool checked = true, bool drifted = false) {
   if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
-  int rc = build_lists_impl(ctx, checked, drifted);
+  const bool ovl = solve_q && !ctx->fp64 && !ctx->prof && ctx->tune.qeq_overlap;
+  // unchecked (MD steps): the bond list is built beside the solve; checked builds read the
+  // capacity flags of every list before anything else runs
+  const bool bonds_later = ovl && !checked;
+  int rc = build_lists_impl(ctx, checked, drifted, bonds_later);
   if (rc) return rc;
   rc = zero_accumulators(ctx);
   if (rc) return rc;
-  if (solve_q && !ctx->fp64 && !ctx->prof && ctx->tune.qeq_overlap) {
-    rc = forces_overlap(ctx);
+  if (ovl) {
+    rc = forces_overlap(ctx, bonds_later);
     if (rc) return rc;
   } else {
     if (solve_q) {
