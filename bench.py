@@ -259,6 +259,19 @@ def run_ours(a, rank, world):
     ms_prof, _, spmv_prof = run_steps(a.steps)
     prof = ctx.profile_read()
     ctx.profile_enable(False)
+    # with the solve beside the charge-free terms: the two paths from the fork, timed in that
+    # order (up to 100 steps; energies into the profiled pass's half of the buffer)
+    paths = None
+    if len(schedule) > 7 and schedule[7] and prec == rx.MIXED:
+        k_saved = a.steps
+        a.steps = k_paths = min(10 * CALL_STEPS, k_saved)
+        ctx.profile_enable(2)
+        ms_paths, _, _ = run_steps(k_saved)
+        pp = ctx.profile_read()
+        ctx.profile_enable(False)
+        a.steps = k_saved
+        paths = {k: round(pp[k][0] / max(pp[k][1], 1), 4) for k in ("solve_path", "terms_path") if pp[k][1] > 0}
+        paths["ms_per_step"] = round(ms_paths / k_paths, 4)
     ms_step = max_over_ranks(ms_total / max(a.steps, 1), world)
     value = job_value(n, ms_step, world)
     et = etot.cpu().numpy()[: a.steps]
@@ -294,6 +307,8 @@ def run_ours(a, rank, world):
         out["roofline"]["traffic"] = None if per is None else per * spmv
         out["roofline"]["traffic_source"] = ("profiles/k_cg_petn32k_mixed.md (DRAM bytes per SpMV x SpMVs per launch)"
                                             if per is not None else "kernel changed since the ncu capture")
+    if paths:
+        out["overlap_paths_ms_per_step"] = paths
     out["qeq_spmv_per_launch"] = spmv
     out["qeq_spmv_per_step_timed"] = spmv_sum / max(a.steps, 1)
     out["_ctx"] = ctx

@@ -247,9 +247,13 @@ int64_t reaxff_qeq_spmv_total(reaxff_ctx* ctx);
 /* Per-stage timing with CUDA events recorded on the context's stream around every
  * kernel group (cells, far_list, bond_list, bo_prime64, qeq, bo_correct, atom_terms,
  * over_under_bond, s_gather, angles, torsions, hbonds, nonbonded, chain_rule, verlet,
- * reduce, mlp_guess, qeq_precond). enable(1) also zeroes the totals. read() fills ms[] (accumulated
- * milliseconds) and calls[] (timed launches) for up to nstage stages and returns the
- * number of stages; stage_name() gives each stage's name. */
+ * reduce, mlp_guess, qeq_precond), the groups run one after another. enable(2) instead
+ * keeps the QEq solve beside the charge-free terms (where the schedule has it there) and
+ * times that part as two spans from the fork: solve_path (solve and nonbonded kernel) and
+ * terms_path (bond list, bond orders, bonded terms, chain rule); the groups outside it are
+ * timed as with enable(1). enable(0) turns timing off; enable(1 or 2) also zeroes the
+ * totals. read() fills ms[] (accumulated milliseconds) and calls[] (timed launches) for up
+ * to nstage stages and returns the number of stages; stage_name() gives each stage's name. */
 void reaxff_profile_enable(reaxff_ctx* ctx, int32_t on);
 int32_t reaxff_profile_read(reaxff_ctx* ctx, int32_t nstage, double* ms, int64_t* calls);
 const char* reaxff_stage_name(int32_t stage);

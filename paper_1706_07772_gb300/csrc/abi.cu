@@ -47,7 +47,8 @@ struct reaxff_ctx {
   unsigned mask = 0x1fff;
   int nsm = 0;
   cudaStream_t st = nullptr;
-  cudaStream_t st2 = nullptr;  // second stream: bonded terms beside the nonbonded kernel
+  cudaStream_t st2 = nullptr;  // second stream (highest priority): bonded terms beside the
+                               // nonbonded kernel, or the QEq solve beside the charge-free terms
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int64_t launches = 0;
   bool have_pos = false, forces_valid = false, lists_valid = false;
@@ -84,7 +85,7 @@ struct reaxff_ctx {
   bool capturing = false;      // inside a step capture: stage events become graph nodes
   bool graph_ok = true;        // capture works here (else the steps are launched directly)
   double g_dt = 0.0;
-  bool g_prof = false;
+  int g_prof = 0;
   int64_t g_launches = 0;
   std::vector<std::pair<int, int>> g_events;
   double* etot_buf = nullptr;  // [ETOT_CHUNK * nrep] per-step total energies
@@ -116,7 +117,7 @@ struct reaxff_ctx {
   rx::BoAvg avg{};
   int64_t avg_samples = 0;
   // per-stage CUDA-event timing (reaxff_profile_*)
-  bool prof = false;
+  int prof = 0;                // 0 off; 1 stage timers (serial order); 2 overlap path spans
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_pending;   // (stage, index of start event; end = +1)
   double stage_ms[32] = {0};
@@ -308,8 +309,9 @@ rx::Launch launch_of(reaxff_ctx* ctx) { return rx::Launch{ctx->st, &ctx->launche
 const char* const STAGE_NAMES[] = {"cells", "far_list", "bond_list", "bo_prime64", "qeq", "bo_correct",
                                    "atom_terms", "over_under_bond", "s_gather", "angles", "torsions",
                                    "hbonds", "nonbonded", "chain_rule", "verlet", "reduce", "mlp_guess",
-                                   "qeq_precond"};
-constexpr int NSTAGES = 18;
+                                   "qeq_precond", "solve_path", "terms_path"};
+constexpr int NSTAGES = 20;
+constexpr int STAGE_SOLVE_PATH = 18, STAGE_TERMS_PATH = 19;
 
 // scoped event pair around one stage (only when profiling is on)
 struct Stage {
@@ -337,6 +339,29 @@ struct Stage {
     else cudaEventRecord(e, ctx->st);
   }
 };
+
+// profiling mode 2: two spans that start together on the main stream (at the fork of the
+// overlapped evaluation) and end on the stream given to span_end; returns the first span's
+// event index or -1
+void record_on(reaxff_ctx* ctx, cudaEvent_t e, cudaStream_t st) {
+  if (ctx->capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else cudaEventRecord(e, st);
+}
+int spans_begin(reaxff_ctx* ctx, int id0, int id1) {
+  if (ctx->prof != 2) return -1;
+  const size_t need = 2 * (ctx->ev_pending.size() + 2);
+  while (ctx->ev_pool.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    ctx->ev_pool.push_back(e);
+  }
+  const int idx = (int)(2 * ctx->ev_pending.size());
+  record_on(ctx, ctx->ev_pool[idx], ctx->st);
+  record_on(ctx, ctx->ev_pool[idx + 2], ctx->st);
+  ctx->ev_pending.push_back({id0, idx});
+  ctx->ev_pending.push_back({id1, idx + 2});
+  return idx;
+}
 
 void collect_profile(reaxff_ctx* ctx) {
   if (ctx->ev_pending.empty()) return;
@@ -448,7 +473,7 @@ template <> const DParams<float>* params_of<float>(reaxff_ctx* ctx) { return ctx
 int qeq_impl(reaxff_ctx* ctx, bool side = false) {
   rx::Launch L = launch_of(ctx);
   if (side) L.st = ctx->st2;
-  const int ovl = (side || (ctx->prof && !ctx->fp64)) ? ctx->tune.qeq_overlap : 0;
+  const int ovl = (side || (ctx->prof == 1 && !ctx->fp64)) ? ctx->tune.qeq_overlap : 0;
   const int threads = ovl == 2 ? 256 : ovl == 1 ? 512 : 1024;
   const float* qhat = nullptr;
   if (ctx->ho.warm_start == REAXFF_WARM_MLP && ctx->mlp.alloc && ctx->mlp.ready) {
@@ -477,10 +502,10 @@ int qeq_impl(reaxff_ctx* ctx, bool side = false) {
 }
 
 // Mixed path with the solve beside the charge-free terms. QEq (k_cg on 512 or 256 threads per
-// SM, with the largest shared-memory carveout,
-// then the nonbonded kernel, the only charge-dependent term) runs on the second stream; the
-// bond-order corrections, atom terms, angles, torsions, H-bonds and the chain rule run on the
-// main stream meanwhile. Neither side reads what the other writes (the solve writes charges,
+// SM, with a 164 KB shared-memory carveout) and then the nonbonded kernel, the only
+// charge-dependent term, run on the second stream; the bond list and bond orders (when
+// bonds_pending), their corrections, atom terms, angles, torsions, H-bonds and the chain rule
+// run on the main stream meanwhile. Neither side reads what the other writes (the solve writes charges,
 // solutions and its own state; the terms read positions, bond data and write per-atom
 // quantities, bond accumulators and, like the nonbonded kernel, forces, energies and the
 // virial only through exact fixed-point atomics), so nothing races. The results agree with
@@ -490,12 +515,14 @@ int qeq_impl(reaxff_ctx* ctx, bool side = false) {
 int forces_overlap(reaxff_ctx* ctx, bool bonds_pending) {
   rx::Launch L = launch_of(ctx);
   const DParams<float>* P = ctx->Pf;
+  const int sp = spans_begin(ctx, STAGE_SOLVE_PATH, STAGE_TERMS_PATH);
   cudaEventRecord(ctx->ev_fork, ctx->st);
   cudaStreamWaitEvent(ctx->st2, ctx->ev_fork, 0);
   int rc = qeq_impl(ctx, true);
   if (rc) return rc;
   rx::Launch L2{ctx->st2, &ctx->launches, &ctx->tune};
   rx::nonbonded<float>(L2, ctx->sys, ctx->far, ctx->acc, P, ctx->mask);
+  if (sp >= 0) record_on(ctx, ctx->ev_pool[sp + 1], ctx->st2);
   cudaEventRecord(ctx->ev_join, ctx->st2);
   if (bonds_pending) bond_lists_impl(ctx, L);      // the solve reads only the far list
   rx::bo_correct<float>(L, ctx->sys, ctx->bond, ctx->aq, P);
@@ -506,6 +533,7 @@ int forces_overlap(reaxff_ctx* ctx, bool bonds_pending) {
   rx::torsions<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
   rx::hbonds<float>(L, ctx->sys, ctx->bond, ctx->hb, ctx->acc, P, ctx->mask);
   rx::chain_rule<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc);
+  if (sp >= 0) record_on(ctx, ctx->ev_pool[sp + 3], ctx->st);
   CK(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
   return REAXFF_OK;
 }
@@ -517,7 +545,7 @@ template <typename R> void terms_impl(reaxff_ctx* ctx) {
   { Stage st(ctx, 6); rx::atom_terms<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
   { Stage st(ctx, 7); rx::over_under_bond<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
   { Stage st(ctx, 8); rx::s_gather<R>(L, ctx->sys, ctx->bond, ctx->aq); }
-  if (sizeof(R) == 4 && !ctx->prof) {
+  if (sizeof(R) == 4 && ctx->prof != 1) {
     // the angle, torsion and H-bond terms (charge-independent) on the second stream beside the
     // nonbonded kernel: on the mixed path all four add their results through fixed-point
     // atomics only (exact, order-free) and read nothing another writes, so they commute;
@@ -557,7 +585,7 @@ int zero_accumulators(reaxff_ctx* ctx) {
 // lists -> (QEq) -> all terms -> chain rule; energies reduced into E_rep / vir_rep
 int forces_impl(reaxff_ctx* ctx, bool solve_q, bool reduce = true, bool checked = true, bool drifted = false) {
   if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
-  const bool ovl = solve_q && !ctx->fp64 && !ctx->prof && ctx->tune.qeq_overlap;
+  const bool ovl = solve_q && !ctx->fp64 && ctx->prof != 1 && ctx->tune.qeq_overlap;
   // unchecked (MD steps): the bond list is built beside the solve; checked builds read the
   // capacity flags of every list before anything else runs
   const bool bonds_later = ovl && !checked;
@@ -727,11 +755,11 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking);
   if (ce == cudaSuccess) {
-    // the second stream at the highest priority: the solve's blocks are placed before those of
-    // the kernels beside it
-    int lo = 0, hi = 0;
-    cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    ce = cudaStreamCreateWithPriority(&ctx->st2, cudaStreamNonBlocking, hi);
+    // the second stream at the highest priority: the persistent solve's blocks are placed
+    // before those of the kernels beside it
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    ce = cudaStreamCreateWithPriority(&ctx->st2, cudaStreamNonBlocking, greatest);
   }
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
@@ -1478,7 +1506,7 @@ void reaxff_reset_qeq_history(reaxff_ctx* ctx) {
 
 void reaxff_profile_enable(reaxff_ctx* ctx, int32_t on) {
   if (!ctx) return;
-  ctx->prof = on != 0;
+  ctx->prof = on == 2 ? 2 : on != 0 ? 1 : 0;
   for (int s = 0; s < 32; ++s) { ctx->stage_ms[s] = 0; ctx->stage_calls[s] = 0; }
 }
 

@@ -319,8 +319,18 @@ __device__ __forceinline__ void sp_counts(const CG<float>& a, SpCursor& c, int w
   c.bf = i < whi ? __ldg(a.cnt + i) : 0;
 }
 
-__device__ __forceinline__ void cp_async16(unsigned saddr, const void* g, int nbytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(nbytes) : "memory");
+// 16-byte copy with an L2 evict-first policy: the matrix is read once per SpMV and does not
+// stay in L2 between SpMVs (126 MB L2, > 100 MB per SpMV), so it should not push out the
+// gathered vector or the data of kernels running beside the solve
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void cp_async16(unsigned saddr, const void* g, int nbytes, unsigned long long pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(saddr), "l"(g), "r"(nbytes),
+               "l"(pol)
+               : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
@@ -335,8 +345,9 @@ __device__ __forceinline__ int sp_issue(const CG<float>& a, SpCursor& c, int whi
   const int k = c.k0 + 4 * lane;
   const int nb = k < n ? min(4 * (n - k), 16) : 0;
   const int ko = nb > 0 ? k : 0;
-  cp_async16(sa + 16 * lane, cr + ko, nb);
-  cp_async16(sa + 512 + 16 * lane, hr + ko, nb);
+  const unsigned long long pol = l2_evict_first();
+  cp_async16(sa + 16 * lane, cr + ko, nb, pol);
+  cp_async16(sa + 512 + 16 * lane, hr + ko, nb, pol);
   const int tag = 2 * c.i;
   c.k0 += 128;
   if (c.part == 0) {

@@ -486,7 +486,9 @@ class ReaxFF:
         return its, itt
 
     def profile_enable(self, on=True):
-        self.lib.reaxff_profile_enable(self.h, 1 if on else 0)
+        """True / 1: stage timers with the stages in order; 2: the overlapped order with its
+        two path spans; False / 0: off."""
+        self.lib.reaxff_profile_enable(self.h, int(on))
 
     def profile_read(self):
         """{stage name: (accumulated ms, timed launches)} from the CUDA-event stage timers."""
