@@ -174,7 +174,10 @@ int32_t reaxff_num_replicas(const reaxff_ctx* ctx);
 /* Positions x (double[n*3], row-major xyz, A) and velocities v (double[n*3], A/fs,
  * NULL = zero). Positions are wrapped into [0, L). The QEq solution history used for
  * the extrapolated initial guess is kept (it only changes the starting point of CG,
- * never the converged charges); reaxff_reset_qeq_history() clears it. */
+ * never the converged charges); reaxff_reset_qeq_history() clears it. Positions equal
+ * bit for bit to those the context holds (as last set or read back by get_state, with no
+ * step since) keep the current forces, lists and candidate list, so a round trip of the
+ * state through the host costs no extra force evaluation. */
 int reaxff_set_state(reaxff_ctx* ctx, const double* x, const double* v);
 /* Copy out positions, velocities (double[n*3]) and charges (double[n]); any may be NULL. */
 int reaxff_get_state(reaxff_ctx* ctx, double* x, double* v, double* q);

@@ -73,6 +73,13 @@ struct reaxff_ctx {
   int Etot_cap = 0;
   double *chi_t = nullptr, *eta_t = nullptr, *mass_t = nullptr;
   int* h_err_pinned = nullptr;
+  // host I/O: pinned staging for the state copies (6n doubles: x, y, z, vx, vy, vz as SoA,
+  // allocated on first use) and the device positions as last uploaded or downloaded, valid
+  // until a step moves the atoms (a round trip of unchanged positions then keeps forces,
+  // lists and image counters)
+  double* h_stage = nullptr;
+  std::vector<double> h_pos;
+  bool h_pos_valid = false;
   int cap_far = 0, cap_bond = 0, cap_hb = 0, cap_near = 0, cap_cand = 0;
   float near_margin = 0.f, hb_margin = 0.f;
   bool use_skin = true;
@@ -1070,6 +1077,7 @@ void reaxff_destroy(reaxff_ctx* ctx) {
   ctx->lists.free_all();
   ctx->fixed.free_all();
   if (ctx->h_err_pinned) cudaFreeHost(ctx->h_err_pinned);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->st2) cudaStreamDestroy(ctx->st2);
@@ -1077,51 +1085,72 @@ void reaxff_destroy(reaxff_ctx* ctx) {
   delete ctx;
 }
 
+static int stage_buffer(reaxff_ctx* ctx) {
+  if (!ctx->h_stage) CK(cudaMallocHost(&ctx->h_stage, 6 * (size_t)ctx->n * sizeof(double)));
+  return REAXFF_OK;
+}
+
 static int set_state_common(reaxff_ctx* ctx, const double* x, const double* v, cudaMemcpyKind kind,
                             cudaStream_t user) {
   const int n = ctx->n;
-  // positions arrive interleaved xyz; de-interleave into SoA with wrap
+  const size_t n3 = 3 * (size_t)n;
+  int rc;
+  if ((rc = stage_buffer(ctx))) return rc;
+  // positions arrive interleaved xyz; de-interleave into SoA with wrap (pinned staging)
   std::vector<double> hx, hv;
   const double* xs = x;
   const double* vs = v;
   if (kind == cudaMemcpyDeviceToHost || kind == cudaMemcpyDeviceToDevice) {
-    hx.resize(3 * (size_t)n);
-    CK(cudaMemcpyAsync(hx.data(), x, 3 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, user));
+    hx.resize(n3);
+    CK(cudaMemcpyAsync(hx.data(), x, n3 * sizeof(double), cudaMemcpyDeviceToHost, user));
     if (v) {
-      hv.resize(3 * (size_t)n);
-      CK(cudaMemcpyAsync(hv.data(), v, 3 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, user));
+      hv.resize(n3);
+      CK(cudaMemcpyAsync(hv.data(), v, n3 * sizeof(double), cudaMemcpyDeviceToHost, user));
     }
     CK(cudaStreamSynchronize(user));
     xs = hx.data();
     vs = v ? hv.data() : nullptr;
   }
-  std::vector<double> soa(3 * (size_t)n), vsoa(3 * (size_t)n, 0.0);
+  double* soa = ctx->h_stage;
+  double* vsoa = ctx->h_stage + n3;
   for (int r = 0; r < ctx->nrep; ++r) {
+    const double* L = ctx->h_box.data() + 3 * r;
     for (int64_t i = ctx->h_rep_off[r]; i < ctx->h_rep_off[r + 1]; ++i) {
       for (int d = 0; d < 3; ++d) {
         double p = xs[3 * i + d];
-        if (!std::isfinite(p)) return fail(ctx, REAXFF_E_NAN, "non-finite position");
-        const double L = ctx->h_box[3 * r + d];
-        p = std::fmod(p, L);
-        if (p < 0) p += L;
-        if (p >= L) p -= L;
+        if (!(p >= 0.0 && p < L[d])) {                   // outside the box (or not finite): wrap
+          if (!std::isfinite(p)) return fail(ctx, REAXFF_E_NAN, "non-finite position");
+          p = std::fmod(p, L[d]);
+          if (p < 0) p += L[d];
+          if (p >= L[d]) p -= L[d];
+        }
         soa[d * (size_t)n + i] = p;
-        if (vs) vsoa[d * (size_t)n + i] = vs[3 * i + d];
+        vsoa[d * (size_t)n + i] = vs ? vs[3 * i + d] : 0.0;
       }
     }
   }
-  CK(cudaMemcpyAsync(ctx->sys.x, soa.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->sys.y, soa.data() + n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->sys.z, soa.data() + 2 * (size_t)n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->sys.vx, vsoa.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->sys.vy, vsoa.data() + n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->sys.vz, vsoa.data() + 2 * (size_t)n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemsetAsync(ctx->sys.img, 0, 3 * (size_t)n * sizeof(int), ctx->st));
-  CK(cudaMemsetAsync(ctx->sys.rebuild, 1, sizeof(int), ctx->st));     // new positions: rebuild candidates
-  CK(cudaStreamSynchronize(ctx->st));
-  ctx->have_pos = true;
-  ctx->forces_valid = false;
-  ctx->lists_valid = false;
+  // the same positions as the device holds (bit for bit): forces, lists, candidates and
+  // image counters stay valid (the copy below rewrites the same values)
+  const bool same = ctx->have_pos && ctx->h_pos_valid &&
+                    std::memcmp(soa, ctx->h_pos.data(), n3 * sizeof(double)) == 0;
+  CK(cudaMemcpyAsync(ctx->sys.x, soa, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->sys.y, soa + n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->sys.z, soa + 2 * (size_t)n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->sys.vx, vsoa, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->sys.vy, vsoa + n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->sys.vz, vsoa + 2 * (size_t)n, n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  if (!same) {
+    CK(cudaMemsetAsync(ctx->sys.img, 0, n3 * sizeof(int), ctx->st));
+    CK(cudaMemsetAsync(ctx->sys.rebuild, 1, sizeof(int), ctx->st));   // new positions: rebuild candidates
+    ctx->h_pos.assign(soa, soa + n3);
+    ctx->h_pos_valid = true;
+  }
+  CK(cudaStreamSynchronize(ctx->st));                   // the staging buffer is reused next call
+  if (!same) {
+    ctx->have_pos = true;
+    ctx->forces_valid = false;
+    ctx->lists_valid = false;
+  }
   return REAXFF_OK;
 }
 
@@ -1135,15 +1164,23 @@ int reaxff_set_state_dev(reaxff_ctx* ctx, const double* x_dev, const double* v_d
   return set_state_common(ctx, x_dev, v_dev, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
 }
 
+// three device arrays (SoA) into interleaved host out[3n], through the pinned staging buffer;
+// positions (a == sys.x) are also kept as the host copy of the device positions
 static int get_soa3(reaxff_ctx* ctx, const double* a, const double* b, const double* c, double* out) {
   const int n = ctx->n;
-  std::vector<double> t(3 * (size_t)n);
-  CK(cudaMemcpyAsync(t.data(), a, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaMemcpyAsync(t.data() + n, b, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaMemcpyAsync(t.data() + 2 * (size_t)n, c, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  int rc;
+  if ((rc = stage_buffer(ctx))) return rc;
+  double* t = ctx->h_stage;
+  CK(cudaMemcpyAsync(t, a, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(t + n, b, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(t + 2 * (size_t)n, c, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   for (int i = 0; i < n; ++i)
     for (int d = 0; d < 3; ++d) out[3 * (size_t)i + d] = t[d * (size_t)n + i];
+  if (a == ctx->sys.x) {
+    ctx->h_pos.assign(t, t + 3 * (size_t)n);
+    ctx->h_pos_valid = true;
+  }
   return REAXFF_OK;
 }
 
@@ -1418,6 +1455,7 @@ static int run_unchecked(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_de
 static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev) {
   if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
   ctx->launches = 0;
+  if (nsteps > 0) ctx->h_pos_valid = false;               // the atoms move
   int rc;
   if (!ctx->forces_valid) {
     if ((rc = forces_impl(ctx, true))) return rc;

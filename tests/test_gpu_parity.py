@@ -322,3 +322,34 @@ def test_candidates_cover_pairs_two_cells_apart(rx, params):
     got = keyset(*c.get_lists(rx.LIST_FAR), 2)
     assert np.array_equal(got, want)
     c.close()
+
+
+def test_state_round_trip_keeps_the_trajectory(rx, params):
+    """Downloading the state and uploading it unchanged between two calls of 5 steps gives
+    the 10-step trajectory bit for bit (the unchanged positions keep forces, lists and the
+    solution history); a moved atom is seen (forces equal a fresh context's at that state)."""
+    w = synth.workload("petn464")
+    a = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=1)
+    a.set_state(w["x"], w["v"])
+    ea = a.step(10, 0.1)
+    xa, va, qa = a.get_state()
+    b = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=1)
+    b.set_state(w["x"], w["v"])
+    eb1 = b.step(5, 0.1)
+    x5, v5, _ = b.get_state()
+    b.set_state(x5, v5)
+    eb2 = b.step(5, 0.1)
+    xb, vb, qb = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(qa, qb)
+    assert np.array_equal(ea, np.concatenate([eb1, eb2]))
+    xm = xb.copy()
+    xm[0, 0] += 0.01
+    b.set_state(xm, vb)
+    q = synth.fixed_charges(len(xm), seed=3)
+    Fb, Eb, _ = b.forces(q=q)
+    c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=1)
+    c.set_state(xm, vb)
+    Fc, Ec, _ = c.forces(q=q)
+    assert np.array_equal(Fb, Fc) and np.array_equal(Eb, Ec)
+    for ctx in (a, b, c):
+        ctx.close()
