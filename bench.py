@@ -414,6 +414,43 @@ def learned_warm_start(P, a):
     return out
 
 
+def spatial_order(P, a, steps=100):
+    """The 32,480-atom crystal with its atoms in a seeded random order, stepped as given and
+    with spatial_sort (cell order inside the context), beside the generator's order (already
+    spatially coherent): atom-steps/s of the mixed path, autotuned, 100 steps after 5."""
+    import torch
+
+    import paper_1706_07772_gb300.reaxff as rx
+    import synth
+    w = synth.workload("petn32k")
+    p = np.random.default_rng(2024).permutation(len(w["x"]))
+    ws = dict(w, types=w["types"][p], x=w["x"][p], v=w["v"][p])
+    st = torch.cuda.current_stream()
+    et = torch.zeros(2 * steps, dtype=torch.float64, device="cuda")
+    out = {}
+    for label, src, srt in (("generator_order", w, 0), ("shuffled", ws, 0), ("shuffled_spatial_sort", ws, 1)):
+        c = rx.ReaxFF(P, src["types"], src["box"], src["options"], precision=rx.MIXED, warm_start=rx.WARM_EXTRAP,
+                      spatial_sort=srt)
+        c.set_state(src["x"], src["v"])
+        c.autotune(a.tune_cache)
+        c.step_dev(5, a.dt, et.data_ptr(), st.cuda_stream)
+        torch.cuda.synchronize()
+        ms, done = 0.0, 0
+        while done < steps:
+            k = min(CALL_STEPS, steps - done)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            c.step_dev(k, a.dt, et.data_ptr(), st.cuda_stream)
+            e1.record(st)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            done += k
+        out[label] = {"value": len(src["x"]) * steps / (ms * 1e-3), "ms_per_step": ms / steps}
+        c.close()
+    out["steps"] = steps
+    return out
+
+
 def large_system(P, a, mlp, steps=20, steps64=3):
     """The 1,039,360-atom crystal (32x28x20 cells) on one GPU, 300 K, dt as the main run:
     atom-steps/s of the mixed path with the extrapolated and with the learned warm start
@@ -723,6 +760,8 @@ def main():
         # learned QEq warm start (trained here on the method's own charges)
         out["learned_warm_start"] = learned_warm_start(P, a)
         mlp = out["learned_warm_start"].pop("_mlp")
+        # atom order: a shuffled input stepped as given and with the spatial sort
+        out["spatial_sort"] = spatial_order(P, a)
         # the 1,039,360-atom crystal: mixed (extrapolated / learned start) against FP64
         if a.workload == "petn32k" and not a.no_large:
             out["large"] = large_system(P, a, mlp)

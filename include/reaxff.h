@@ -141,6 +141,11 @@ typedef struct {
                          negative = no candidate list (cell stencil every step). A system
                          with a box edge <= r_nb + skin runs the cell stencil instead. */
   int32_t qeq_precond; /* REAXFF_PRECOND_* (0 = Jacobi) */
+  int32_t spatial_sort; /* 1: the context stores the atoms of each replica in cell order
+                           (5 A cells, z-major), taken from the positions of the first
+                           reaxff_set_state and again at each reaxff_resort, for locality of
+                           the neighbour gathers (Sec. 3.2's spatial ordering); every input and
+                           output stays in the caller's order. 0: the caller's order. */
 } reaxff_options;
 
 typedef struct reaxff_ctx reaxff_ctx;
@@ -179,6 +184,12 @@ int32_t reaxff_num_replicas(const reaxff_ctx* ctx);
  * step since) keep the current forces, lists and candidate list, so a round trip of the
  * state through the host costs no extra force evaluation. */
 int reaxff_set_state(reaxff_ctx* ctx, const double* x, const double* v);
+/* With options.spatial_sort: store the atoms again in cell order of their current
+ * positions (for long runs in which atoms wander away from their neighbours in memory). The
+ * state is unchanged; the QEq solution history, bond-order averages and collected training
+ * snapshots are dropped, and lists and forces are rebuilt at the next call. No-op without
+ * spatial_sort. */
+int reaxff_resort(reaxff_ctx* ctx);
 /* Copy out positions, velocities (double[n*3]) and charges (double[n]); any may be NULL. */
 int reaxff_get_state(reaxff_ctx* ctx, double* x, double* v, double* q);
 

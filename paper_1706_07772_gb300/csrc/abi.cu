@@ -55,7 +55,12 @@ struct reaxff_ctx {
   float far_margin = 0.f;
   std::vector<int64_t> h_rep_off;
   std::vector<double> h_box;
-  std::vector<int> h_types;
+  std::vector<int> h_types;      // per atom, in storage order
+  // storage order (options.spatial_sort): perm[k] = the caller's index of the atom stored at
+  // k; empty = the caller's order
+  bool sort_on = false;
+  std::vector<int> perm, h_types_ext;
+  int* type_d = nullptr;
   // device memory: fixed part and list part (re-allocated on regrow)
   DevBuf fixed, lists;
   DParams<double>* Pd = nullptr;
@@ -697,6 +702,65 @@ int validate(const reaxff_params* p, const reaxff_options* o, std::string& msg) 
   return REAXFF_OK;
 }
 
+// ---- storage order ------------------------------------------------------------------------
+// the caller's index of the atom stored at k
+static inline int ext_of(const reaxff_ctx* ctx, int k) { return ctx->perm.empty() ? k : ctx->perm[(size_t)k]; }
+// rows of w values: storage order -> the caller's order, and back
+template <typename T> static void rows_to_caller(const reaxff_ctx* ctx, const T* src, T* dst, int w) {
+  for (int k = 0; k < ctx->n; ++k)
+    for (int c = 0; c < w; ++c) dst[(size_t)w * ext_of(ctx, k) + c] = src[(size_t)w * k + c];
+}
+template <typename T> static void rows_from_caller(const reaxff_ctx* ctx, const T* src, T* dst, int w) {
+  for (int k = 0; k < ctx->n; ++k)
+    for (int c = 0; c < w; ++c) dst[(size_t)w * k + c] = src[(size_t)w * ext_of(ctx, k) + c];
+}
+int mlp_tiles_upload(reaxff_ctx* ctx);
+
+// Cell order of each replica's atoms from positions given in the caller's order (xyz rows):
+// 5 A cells (at least one per axis), z-major, the caller's order within a cell. Switching to
+// it rebuilds what depends on the order (types; the learned start's element tiles) and drops
+// what cannot be carried over (solution history, bond-order averages, training snapshots).
+static int apply_spatial_order(reaxff_ctx* ctx, const double* xs) {
+  const int n = ctx->n;
+  std::vector<int> perm(n);
+  std::vector<std::pair<long long, int>> key;
+  for (int r = 0; r < ctx->nrep; ++r) {
+    const double* L = ctx->h_box.data() + 3 * r;
+    int nc[3];
+    for (int d = 0; d < 3; ++d) nc[d] = std::max(1, (int)std::floor(L[d] / 5.0));
+    const int64_t a = ctx->h_rep_off[r], b = ctx->h_rep_off[r + 1];
+    key.clear();
+    for (int64_t i = a; i < b; ++i) {
+      int c[3];
+      for (int d = 0; d < 3; ++d) {
+        double p = std::fmod(xs[3 * i + d], L[d]);
+        if (p < 0) p += L[d];
+        c[d] = std::min(nc[d] - 1, std::max(0, (int)std::floor(p / L[d] * nc[d])));
+      }
+      key.push_back({((long long)c[2] * nc[1] + c[1]) * nc[0] + c[0], (int)i});
+    }
+    std::stable_sort(key.begin(), key.end(),
+                     [](const std::pair<long long, int>& u, const std::pair<long long, int>& v) { return u.first < v.first; });
+    for (int64_t i = a; i < b; ++i) perm[i] = key[i - a].second;
+  }
+  ctx->perm.swap(perm);
+  for (int k = 0; k < n; ++k) ctx->h_types[k] = ctx->h_types_ext[ctx->perm[k]];
+  CK(cudaMemcpyAsync(ctx->type_d, ctx->h_types.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(ctx->Q.hst + 2, 0, sizeof(int), ctx->st));          // no usable solution history
+  int rc = reaxff_bo_average_reset(ctx);
+  if (rc) return rc;
+  if (ctx->mlp.alloc) {
+    ctx->mlp.count = 0;
+    if ((rc = mlp_tiles_upload(ctx))) return rc;
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->h_pos_valid = false;
+  ctx->forces_valid = false;
+  ctx->lists_valid = false;
+  drop_graph(ctx);
+  return REAXFF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -755,6 +819,8 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   ctx->h_rep_off.assign(rep_offsets, rep_offsets + nrep + 1);
   ctx->h_box.assign(boxes, boxes + 3 * nrep);
   ctx->h_types.assign(types, types + n64);
+  ctx->h_types_ext.assign(types, types + n64);
+  ctx->sort_on = options->spatial_sort != 0;
   int dev = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -991,6 +1057,7 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   UP(ctx->Pd, &hd, sizeof(hd));
   UP(ctx->Pf, &hf, sizeof(hf));
   UP(type_d, types, n * sizeof(int));
+  ctx->type_d = type_d;
   UP(rep_d, rep_h.data(), n * sizeof(int));
   UP(box_d, boxes, 3 * nrep * sizeof(double));
   UP(off_d, rep_offsets, (nrep + 1) * sizeof(int64_t));
@@ -1111,13 +1178,19 @@ static int set_state_common(reaxff_ctx* ctx, const double* x, const double* v, c
     xs = hx.data();
     vs = v ? hv.data() : nullptr;
   }
+  if (ctx->sort_on && ctx->perm.empty()) {
+    for (size_t e = 0; e < n3; ++e)
+      if (!std::isfinite(xs[e])) return fail(ctx, REAXFF_E_NAN, "non-finite position");
+    if ((rc = apply_spatial_order(ctx, xs))) return rc;
+  }
   double* soa = ctx->h_stage;
   double* vsoa = ctx->h_stage + n3;
   for (int r = 0; r < ctx->nrep; ++r) {
     const double* L = ctx->h_box.data() + 3 * r;
     for (int64_t i = ctx->h_rep_off[r]; i < ctx->h_rep_off[r + 1]; ++i) {
+      const int64_t e = ext_of(ctx, (int)i);             // the caller's row of stored atom i
       for (int d = 0; d < 3; ++d) {
-        double p = xs[3 * i + d];
+        double p = xs[3 * e + d];
         if (!(p >= 0.0 && p < L[d])) {                   // outside the box (or not finite): wrap
           if (!std::isfinite(p)) return fail(ctx, REAXFF_E_NAN, "non-finite position");
           p = std::fmod(p, L[d]);
@@ -1125,7 +1198,7 @@ static int set_state_common(reaxff_ctx* ctx, const double* x, const double* v, c
           if (p >= L[d]) p -= L[d];
         }
         soa[d * (size_t)n + i] = p;
-        vsoa[d * (size_t)n + i] = vs ? vs[3 * i + d] : 0.0;
+        vsoa[d * (size_t)n + i] = vs ? vs[3 * e + d] : 0.0;
       }
     }
   }
@@ -1159,6 +1232,18 @@ int reaxff_set_state(reaxff_ctx* ctx, const double* x, const double* v) {
   return set_state_common(ctx, x, v, cudaMemcpyHostToHost, ctx->st);
 }
 
+int reaxff_resort(reaxff_ctx* ctx) {
+  if (!ctx) return REAXFF_E_INVALID;
+  if (!ctx->sort_on) return REAXFF_OK;
+  if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  const size_t n3 = 3 * (size_t)ctx->n;
+  std::vector<double> x(n3), v(n3);
+  int rc;
+  if ((rc = reaxff_get_state(ctx, x.data(), v.data(), nullptr))) return rc;
+  if ((rc = apply_spatial_order(ctx, x.data()))) return rc;
+  return set_state_common(ctx, x.data(), v.data(), cudaMemcpyHostToHost, ctx->st);
+}
+
 int reaxff_set_state_dev(reaxff_ctx* ctx, const double* x_dev, const double* v_dev, void* stream) {
   if (!ctx || !x_dev) return REAXFF_E_INVALID;
   return set_state_common(ctx, x_dev, v_dev, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
@@ -1176,7 +1261,7 @@ static int get_soa3(reaxff_ctx* ctx, const double* a, const double* b, const dou
   CK(cudaMemcpyAsync(t + 2 * (size_t)n, c, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   for (int i = 0; i < n; ++i)
-    for (int d = 0; d < 3; ++d) out[3 * (size_t)i + d] = t[d * (size_t)n + i];
+    for (int d = 0; d < 3; ++d) out[3 * (size_t)ext_of(ctx, i) + d] = t[d * (size_t)n + i];
   if (a == ctx->sys.x) {
     ctx->h_pos.assign(t, t + 3 * (size_t)n);
     ctx->h_pos_valid = true;
@@ -1191,8 +1276,10 @@ int reaxff_get_state(reaxff_ctx* ctx, double* x, double* v, double* q) {
   if (x && (rc = get_soa3(ctx, ctx->sys.x, ctx->sys.y, ctx->sys.z, x))) return rc;
   if (v && (rc = get_soa3(ctx, ctx->sys.vx, ctx->sys.vy, ctx->sys.vz, v))) return rc;
   if (q) {
-    CK(cudaMemcpyAsync(q, ctx->sys.q, ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    std::vector<double> t(ctx->n);
+    CK(cudaMemcpyAsync(t.data(), ctx->sys.q, ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    rows_to_caller(ctx, t.data(), q, 1);
   }
   return REAXFF_OK;
 }
@@ -1212,8 +1299,12 @@ int reaxff_get_state_dev(reaxff_ctx* ctx, double* x_dev, double* v_dev, double* 
     CK(cudaStreamSynchronize((cudaStream_t)stream));
   }
   if (q_dev) {
+    std::vector<double> t(ctx->n), u(ctx->n);
+    CK(cudaMemcpyAsync(t.data(), ctx->sys.q, ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    CK(cudaMemcpyAsync(q_dev, ctx->sys.q, ctx->n * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    rows_to_caller(ctx, t.data(), u.data(), 1);
+    CK(cudaMemcpyAsync(q_dev, u.data(), ctx->n * sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
   }
   return REAXFF_OK;
 }
@@ -1265,8 +1356,8 @@ int reaxff_get_lists(reaxff_ctx* ctx, int32_t which, int64_t capacity, int64_t* 
     for (size_t p = 0; p < parts.size(); ++p)
       for (int m = 0; m < cnts[p][i]; ++m) {
         const size_t e = (size_t)i * parts[p].cap + m;
-        i_out[k] = i;
-        j_out[k] = jj[p][e];
+        i_out[k] = ext_of(ctx, i);
+        j_out[k] = ext_of(ctx, jj[p][e]);
         const int c = ss[p][e];
         shift[3 * k + 0] = (int8_t)(c / 9 - 1);
         shift[3 * k + 1] = (int8_t)((c / 3) % 3 - 1);
@@ -1317,9 +1408,11 @@ int reaxff_qeq(reaxff_ctx* ctx, double* q_out, int32_t* iters_s, int32_t* iters_
   int frc = check_flags(ctx, true);
   if (frc && frc != REAXFF_E_NOT_CONVERGED) return frc;
   std::vector<int> it(2 * ctx->nrep);
+  std::vector<double> qs(q_out ? ctx->n : 0);
   CK(cudaMemcpyAsync(it.data(), ctx->Q.iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-  if (q_out) CK(cudaMemcpyAsync(q_out, ctx->sys.q, ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  if (q_out) CK(cudaMemcpyAsync(qs.data(), ctx->sys.q, ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  if (q_out) rows_to_caller(ctx, qs.data(), q_out, 1);
   for (int r = 0; r < ctx->nrep; ++r) {
     if (iters_s) iters_s[r] = it[2 * r];
     if (iters_t) iters_t[r] = it[2 * r + 1];
@@ -1328,13 +1421,16 @@ int reaxff_qeq(reaxff_ctx* ctx, double* q_out, int32_t* iters_s, int32_t* iters_
 }
 
 static int copy_outputs(reaxff_ctx* ctx, double* F, double* E, double* virial) {
+  std::vector<double> Fs(F && !ctx->perm.empty() ? 3 * (size_t)ctx->n : 0);
   if (F) {
     rx::finalize_forces(launch_of(ctx), ctx->sys, ctx->F_out);
-    CK(cudaMemcpyAsync(F, ctx->F_out, 3 * (size_t)ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(Fs.empty() ? F : Fs.data(), ctx->F_out, 3 * (size_t)ctx->n * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->st));
   }
   if (E) CK(cudaMemcpyAsync(E, ctx->E_rep, NTERMS * ctx->nrep * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
   if (virial) CK(cudaMemcpyAsync(virial, ctx->vir_rep, 6 * ctx->nrep * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  if (!Fs.empty()) rows_to_caller(ctx, Fs.data(), F, 3);
   return REAXFF_OK;
 }
 
@@ -1350,7 +1446,10 @@ int reaxff_forces(reaxff_ctx* ctx, double* F, double* E, double* virial) {
 
 int reaxff_forces_fixed_q(reaxff_ctx* ctx, const double* q, double* F, double* E, double* virial) {
   if (!ctx || !q) return REAXFF_E_INVALID;
-  CK(cudaMemcpyAsync(ctx->sys.q, q, ctx->n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  std::vector<double> qs(ctx->n);
+  rows_from_caller(ctx, q, qs.data(), 1);
+  CK(cudaMemcpyAsync(ctx->sys.q, qs.data(), ctx->n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
   rx::charges_to_f32(launch_of(ctx), ctx->sys);
   int rc = forces_impl(ctx, false);
   if (rc) return rc;
@@ -1606,6 +1705,23 @@ double u01(uint64_t& st) {
   return ((double)(z >> 11) + 0.5) / 9007199254740992.0;
 }
 
+// element tiles and per-atom elements of the current storage order
+int mlp_tiles_upload(reaxff_ctx* ctx) {
+  auto& M = ctx->mlp;
+  std::vector<int> perm, tt, ro;
+  int off[5];
+  mlp_tiles_host(ctx->h_types, perm, tt, ro, off);
+  M.tiles.rows = (int)perm.size();
+  M.tiles.ntile = (int)tt.size();
+  CK(cudaMemcpyAsync(M.tiles.perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(M.tiles.tile_type, tt.data(), tt.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(M.tiles.rows_off, ro.data(), ro.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(M.types, ctx->h_types.data(), ctx->n * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(M.off, off, sizeof(off), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return REAXFF_OK;
+}
+
 int mlp_alloc(reaxff_ctx* ctx) {
   auto& M = ctx->mlp;
   if (M.alloc) return REAXFF_OK;
@@ -1627,8 +1743,8 @@ int mlp_alloc(reaxff_ctx* ctx) {
   M.tiles.rows = (int)perm.size();
   M.tiles.ntile = (int)tt.size();
   M.tiles.perm = B.alloc<int>(perm.size());
-  M.tiles.tile_type = B.alloc<int>(tt.size());
-  M.tiles.rows_off = B.alloc<int>(ro.size());
+  M.tiles.tile_type = B.alloc<int>(ctx->n / 128 + rx::MLP_NT + 1);   // tiles: at most n/128 + one per element
+  M.tiles.rows_off = B.alloc<int>(ctx->n / 128 + rx::MLP_NT + 2);
   M.inf.Xp = B.alloc_bytes((size_t)n * rx::MLP_NF * 2);
   M.inf.W1t = B.alloc_bytes((size_t)rx::MLP_NT * rx::MLP_HID * rx::MLP_NF * 2);
   M.inf.W2t = B.alloc_bytes((size_t)rx::MLP_NT * rx::MLP_HID * rx::MLP_HID * 2);
@@ -1642,11 +1758,8 @@ int mlp_alloc(reaxff_ctx* ctx) {
     B.free_all();
     return fail(ctx, REAXFF_E_CUDA, "learned warm start allocation: " + cuda_err_str(B.err));
   }
-  CK(cudaMemcpyAsync(M.tiles.perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(M.tiles.tile_type, tt.data(), tt.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(M.tiles.rows_off, ro.data(), ro.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(M.types, ctx->h_types.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(M.off, off, sizeof(off), cudaMemcpyHostToDevice, ctx->st));
+  int rc = mlp_tiles_upload(ctx);
+  if (rc) return rc;
   CK(cudaMemsetAsync(M.theta, 0, NPT * sizeof(float), ctx->st));
   CK(cudaMemsetAsync(M.madam, 0, NPT * sizeof(float), ctx->st));
   CK(cudaMemsetAsync(M.vadam, 0, NPT * sizeof(float), ctx->st));
@@ -1756,8 +1869,11 @@ int reaxff_mlp_descriptors(reaxff_ctx* ctx, float* D) {
   if ((rc = read_err(ctx, &flags))) return rc;
   if (flags & ERR_CAP_DESC) return fail(ctx, REAXFF_E_CAPACITY, "more neighbours than the descriptor kernel keeps");
   if (D) {
-    CK(cudaMemcpyAsync(D, ctx->mlp.D, (size_t)ctx->n * rx::MLP_NF * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+    std::vector<float> Ds(ctx->perm.empty() ? 0 : (size_t)ctx->n * rx::MLP_NF);
+    CK(cudaMemcpyAsync(Ds.empty() ? D : Ds.data(), ctx->mlp.D, (size_t)ctx->n * rx::MLP_NF * sizeof(float),
+                       cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    if (!Ds.empty()) rows_to_caller(ctx, Ds.data(), D, rx::MLP_NF);
   }
   return REAXFF_OK;
 }
@@ -1941,7 +2057,7 @@ int reaxff_mlp_predict(reaxff_ctx* ctx, double* q) {
   if ((rc = read_err(ctx, &flags))) return rc;
   if (flags & ERR_TIMEOUT) return fail(ctx, REAXFF_E_TIMEOUT, "tensor-core wait hit its spin limit");
   if (flags & ERR_CAP_DESC) return fail(ctx, REAXFF_E_CAPACITY, "more neighbours than the descriptor kernel keeps");
-  for (int i = 0; i < ctx->n; ++i) q[i] = y[i];
+  for (int i = 0; i < ctx->n; ++i) q[ext_of(ctx, i)] = y[i];
   return REAXFF_OK;
 }
 
@@ -1983,8 +2099,18 @@ int species_impl(reaxff_ctx* ctx, const BondList& bl, bool bo_double, const doub
   std::vector<int> cnt((size_t)M * MAXT), mrep(M);
   CK(cudaMemcpyAsync(cnt.data(), b.cnt, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaMemcpyAsync(mrep.data(), b.mrep, mrep.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-  if (mol_id) CK(cudaMemcpyAsync(mol_id, b.mol, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  std::vector<int> ms(mol_id && !ctx->perm.empty() ? n : 0);
+  if (mol_id) CK(cudaMemcpyAsync(ms.empty() ? mol_id : ms.data(), b.mol, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  if (!ms.empty()) {
+    // stored in cell order: number the molecules by their smallest index in the caller's order
+    std::vector<int> first(M, n), order(M), id(M);
+    for (int k = 0; k < n; ++k) first[ms[k]] = std::min(first[ms[k]], ext_of(ctx, k));
+    for (int m = 0; m < M; ++m) order[m] = m;
+    std::sort(order.begin(), order.end(), [&](int u, int v) { return first[u] < first[v]; });
+    for (int m = 0; m < M; ++m) id[order[m]] = m;
+    for (int k = 0; k < n; ++k) mol_id[ext_of(ctx, k)] = id[ms[k]];
+  }
   // the summary: molecules per (replica, element counts), in that order
   constexpr int W = MAXT + 2;
   std::vector<std::array<int, MAXT + 1>> keys(M);
@@ -2111,8 +2237,8 @@ int reaxff_get_bo_average(reaxff_ctx* ctx, int64_t capacity, int64_t* count, int
   for (int i = 0; i < n; ++i)
     for (int m = 0; m < cnt[i]; ++m, ++k) {
       const size_t e = (size_t)i * A.cap + m;
-      i_out[k] = i;
-      j_out[k] = jj[e];
+      i_out[k] = ext_of(ctx, i);
+      j_out[k] = ext_of(ctx, jj[e]);
       const int c = ss[e];
       shift[3 * k + 0] = (int8_t)(c / 9 - 1);
       shift[3 * k + 1] = (int8_t)((c / 3) % 3 - 1);

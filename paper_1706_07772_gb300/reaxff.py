@@ -48,7 +48,7 @@ class Options(C.Structure):
                 ("thb_cut", C.c_double), ("thb_cutsq", C.c_double), ("hb_bo_min", C.c_double),
                 ("qeq_tol", C.c_double), ("qeq_max_iter", C.c_int32), ("precision", C.c_int32),
                 ("warm_start", C.c_int32), ("term_mask", C.c_int32), ("capacity_margin", C.c_double),
-                ("skin", C.c_double), ("qeq_precond", C.c_int32)]
+                ("skin", C.c_double), ("qeq_precond", C.c_int32), ("spatial_sort", C.c_int32)]
 
 
 class ReaxFFError(RuntimeError):
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
         "reaxff_destroy": (None, [vp]), "reaxff_last_error": (C.c_char_p, [vp]),
         "reaxff_num_atoms": (i64, [vp]), "reaxff_num_replicas": (i32, [vp]),
         "reaxff_set_state": (C.c_int, [vp, dp, dp]), "reaxff_get_state": (C.c_int, [vp, dp, dp, dp]),
+        "reaxff_resort": (C.c_int, [vp]),
         "reaxff_build_lists": (C.c_int, [vp]),
         "reaxff_get_lists": (C.c_int, [vp, i32, i64, ip64, ip32, ip32, C.POINTER(C.c_int8)]),
         "reaxff_get_bond_orders": (C.c_int, [vp, i64, ip64, dp, dp, dp, dp]),
@@ -168,7 +169,7 @@ def make_params(p: dict) -> Params:
 
 
 def make_options(o: dict, precision=FP64, warm_start=WARM_EXTRAP, term_mask=0, capacity_margin=0.0,
-                 skin=0.0, qeq_precond=0) -> Options:
+                 skin=0.0, qeq_precond=0, spatial_sort=0) -> Options:
     O = Options()
     for k in ("r_nb", "r_bond", "r_hb", "bo_cut", "thb_cut", "thb_cutsq", "hb_bo_min", "qeq_tol"):
         setattr(O, k, float(o[k]))
@@ -179,6 +180,7 @@ def make_options(o: dict, precision=FP64, warm_start=WARM_EXTRAP, term_mask=0, c
     O.capacity_margin = float(capacity_margin)
     O.skin = float(o.get("skin", skin))
     O.qeq_precond = int(o.get("qeq_precond", qeq_precond))
+    O.spatial_sort = int(o.get("spatial_sort", spatial_sort))
     return O
 
 
@@ -229,10 +231,11 @@ class ReaxFF:
     """One library context (single system or a batch of replicas)."""
 
     def __init__(self, params: dict, types, box, options: dict, precision=FP64, warm_start=WARM_EXTRAP,
-                 term_mask=0, rep_offsets=None, capacity_margin=0.0, skin=0.0, qeq_precond=0):
+                 term_mask=0, rep_offsets=None, capacity_margin=0.0, skin=0.0, qeq_precond=0, spatial_sort=0):
         self.lib = load()
         P = make_params(params)
-        O = make_options(options, precision, warm_start, term_mask, capacity_margin, skin, qeq_precond)
+        O = make_options(options, precision, warm_start, term_mask, capacity_margin, skin, qeq_precond,
+                         spatial_sort)
         self.types = np.ascontiguousarray(types, np.int32)
         if rep_offsets is None:
             self.h = reaxff_create(P, self.types, np.asarray(box, float).reshape(3), O)
@@ -261,6 +264,10 @@ class ReaxFF:
         x = np.ascontiguousarray(x, np.float64).reshape(self.n, 3)
         v = None if v is None else np.ascontiguousarray(v, np.float64).reshape(self.n, 3)
         self._check(self.lib.reaxff_set_state(self.h, _dp(x), _dp(v)))
+
+    def resort(self):
+        """Store the atoms again in cell order of their current positions (spatial_sort)."""
+        self._check(self.lib.reaxff_resort(self.h))
 
     def get_state(self, out=None):
         """Positions, velocities and charges; `out` = (x, v, q) C-contiguous float64 arrays
