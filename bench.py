@@ -228,6 +228,7 @@ def run_ours(a, rank, world):
         stream), launches and SpMVs"""
         ms, nl, done = 0.0, 0, 0
         sp0 = ctx.qeq_spmv_total()
+        per_call.clear()
         while done < a.steps:
             k = min(CALL_STEPS, a.steps - done)
             flush.fill_(float(done))
@@ -237,10 +238,14 @@ def run_ours(a, rank, world):
             ctx.step_dev(k, a.dt, etot.data_ptr() + 8 * (base + done), stream.cuda_stream)
             e1.record(stream)
             e1.synchronize()
-            ms += e0.elapsed_time(e1)
+            t = e0.elapsed_time(e1)
+            per_call.append((k, t))
+            ms += t
             nl += ctx.last_launch_count()
             done += k
         return ms, nl, ctx.qeq_spmv_total() - sp0
+
+    per_call = []
 
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     barrier(world)
@@ -248,6 +253,7 @@ def run_ours(a, rank, world):
     clocks.start()
     time.sleep(0.25)
     ms_total, launches, spmv_sum = run_steps(0)            # the timed region
+    calls = list(per_call)
     torch.cuda.synchronize()
     barrier(world)
     clocks.stop()
@@ -294,6 +300,12 @@ def run_ours(a, rank, world):
         "nve_rel_drift": float(np.abs(et - et[0]).max() / abs(et[0])) if len(et) > 1 else None,
         "profiled_pass_ms_per_step": ms_prof / max(a.steps, 1),
     }
+    # the timed region as five consecutive windows (median of five runs, spread)
+    if len(calls) >= 5:
+        win = np.array_split(np.array(calls), 5)
+        wms = [float(w[:, 1].sum() / w[:, 0].sum()) for w in win]
+        out["windows_ms_per_step"] = [round(v, 4) for v in wms]
+        out["median_window_ms_per_step"] = round(float(np.median(wms)), 4)
     stages = {k: {"ms_per_step": v[0] / max(a.steps, 1), "launches": v[1]} for k, v in prof.items() if v[1] > 0}
     out["stages"] = {k: round(v["ms_per_step"], 4) for k, v in sorted(stages.items(), key=lambda t: -t[1]["ms_per_step"])}
     # roofline of the dominant stage
@@ -770,6 +782,16 @@ def main():
         nat = len(w["x"])
         out["cpu_baseline"] = {"value": nat / t, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": "1 oracle MD step on the full %s (%d atoms), %.1f s" % (a.workload, nat, t)}
+        # the oracle on one core, on a bounded sample (the 2x2x2-cell crystal)
+        import synth
+        import torch
+        nthr = torch.get_num_threads()
+        torch.set_num_threads(1)
+        w1 = synth.workload("petn464")
+        t1, _, _, _ = cpu_oracle_step(P, w1)
+        torch.set_num_threads(nthr)
+        out["cpu_baseline"]["single_thread"] = {"value": len(w1["x"]) / t1, "unit": UNIT, "cores": 1,
+                                                "sample": "1 oracle MD step on petn464 (464 atoms), %.1f s" % t1}
         Fo = oracle_reference_forces(m, L, w)
         rms = float(np.sqrt((Fo ** 2).mean()))
         ferr = {}
