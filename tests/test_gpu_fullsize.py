@@ -227,3 +227,19 @@ def test_petn1m_sampled_rows_forces_and_qeq(rx, params, ref1m, prec):
     rms_bound = tol * (np.sqrt((chi ** 2).mean()) + abs(mu)) + eps_h * mag.max()
     assert np.sqrt(((rho - mu) ** 2).mean()) <= 4.0 * rms_bound
     c.close()
+
+
+def test_petn32k_1000_step_nve_mixed_no_worse_than_fp64(rx, params):
+    """1000 NVE steps of 0.1 fs on petn32k (QEq tol 1e-6, extrapolated start) on both paths:
+    the mixed path's total-energy drift is no worse than the FP64 path's, and the two energy
+    curves agree step by step (measured: max |E - E0| / |E0| 4.487e-4 on both)."""
+    w = synth.workload("petn32k")
+    e = {}
+    for prec in PRECS:
+        c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=prec, warm_start=rx.WARM_EXTRAP)
+        c.set_state(w["x"], w["v"])
+        e[prec] = c.step(1000, 0.1)[:, 0]
+        c.close()
+    drift = {p: np.abs(e[p] - e[p][0]).max() / abs(e[p][0]) for p in PRECS}
+    assert drift[1] <= 1.02 * drift[0] + 1e-7, drift
+    assert np.abs(e[1] - e[0]).max() < 1e-5 * abs(e[0][0])
