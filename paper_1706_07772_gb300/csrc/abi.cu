@@ -1008,10 +1008,16 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   rlo.push_back(n);
   int* rlo_d = B.alloc<int>(rlo.size());
   int* rrep_d = B.alloc<int>(nrep + 1);
+  std::vector<int> rcr(ctx->red.nchunk);                        // replica of each chunk
+  for (int r = 0; r < nrep; ++r)
+    for (int k = rrep[r]; k < rrep[r + 1]; ++k) rcr[k] = r;
+  int* rcr_d = B.alloc<int>(std::max(1, ctx->red.nchunk));
   ctx->red.chunk_lo = rlo_d;
+  ctx->red.chunk_rep = rcr_d;
   ctx->red.rep_chunk = rrep_d;
   ctx->red.part = B.alloc<double>((size_t)ctx->red.nchunk * 20);
-  ctx->red.done = B.alloc<unsigned>(1);
+  const size_t ndone = (size_t)nrep * 21 + 1;                   // (replica, quantity), replica, launch
+  ctx->red.done = B.alloc<unsigned>(ndone);
   Q.iters = B.alloc<int>(2 * nrep);
   Q.bar = B.alloc<GridBar>(1);
   Q.hst = B.alloc<int>(4);
@@ -1084,6 +1090,7 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   }
   UP(rlo_d, rlo.data(), rlo.size() * sizeof(int));
   UP(rrep_d, rrep.data(), (nrep + 1) * sizeof(int));
+  if (ctx->red.nchunk) UP(rcr_d, rcr.data(), rcr.size() * sizeof(int));
   UP(ctx->chi_t, chi, sizeof(chi));
   UP(ctx->eta_t, eta, sizeof(eta));
   double mass2[2 * MAXT];
@@ -1107,7 +1114,7 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   if (e == cudaSuccess) e = cudaMemset(ctx->Q.spmv_total, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(ctx->Q.mlp_used, 0, nrep * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->Q.bar, 0, sizeof(GridBar));
-  if (e == cudaSuccess) e = cudaMemset(ctx->red.done, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(ctx->red.done, 0, ((size_t)nrep * 21 + 1) * sizeof(unsigned));
   if (e != cudaSuccess) {
     B.free_all();
     delete ctx;

@@ -137,10 +137,12 @@ __device__ __forceinline__ double red_value(const Sys& s, const Accum& acc, cons
   const double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
   return (vx * vx + vy * vy + vz * vz) * mass_t[s.type[i]] * (0.5 / 4.184e-4);   // (amu A^2/fs^2 -> kcal/mol)
 }
-// Pass 1 per block (chunk, q); the block that finishes last (arrival counter, zeroed again
-// by it) runs pass 2 for every (replica, q) -- lane l of a warp sums chunks l, l+32, ... of
-// the replica in order -- and, when asked, the total energy per replica. The order of every
-// sum is fixed whichever block comes last.
+// Pass 1 per block (chunk, q). Arrival counters (each zeroed again by the block that
+// consumes it) then finish the sums where the data is complete: the last chunk block of a
+// (replica, q) sums that replica's chunk partials of q (lane l of warp 0 takes chunks l,
+// l+32, ... in order); the last of a replica's NQ_RED finishers writes its total energy
+// (when asked); the last replica advances *etot_idx. The order of every sum is fixed
+// whichever block comes last, and the finishing work is spread over (replica, q) pairs.
 __global__ void k_reduce(Sys s, Accum acc, const double* mass_t, rx::RedPlan rp, double* E_rep, double* vir_rep,
                          double* ke_rep, double* etot, int* etot_idx) {
   const int c = blockIdx.x, q = blockIdx.y;
@@ -154,46 +156,58 @@ __global__ void k_reduce(Sys s, Accum acc, const double* mass_t, rx::RedPlan rp,
     if (i < hi) v += red_value(s, acc, mass_t, q, i);
   }
   __shared__ double sh[32];
-  __shared__ bool last;
+  __shared__ int stage;          // 1: this block finishes (r, q); 2: also replica r; 3: also the launch
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
+  const int r = rp.chunk_rep[c];
+  const int c0 = rp.rep_chunk[r], c1 = rp.rep_chunk[r + 1];
+  unsigned* cnt_q = rp.done + (size_t)r * NQ_RED + q;
+  unsigned* cnt_r = rp.done + (size_t)s.nrep * NQ_RED + r;
+  unsigned* cnt_all = rp.done + (size_t)s.nrep * (NQ_RED + 1);
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
     rp.part[(size_t)c * NQ_RED + q] = t;
     __threadfence();
-    last = atomicAdd(rp.done, 1u) == gridDim.x * gridDim.y - 1;
+    stage = atomicAdd(cnt_q, 1u) == (unsigned)(c1 - c0 - 1) ? 1 : 0;
   }
   __syncthreads();
-  if (!last) return;
+  if (stage == 0) return;
   __threadfence();
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int pq = threadIdx.x >> 5; pq < s.nrep * NQ_RED; pq += nw) {
-    const int r = pq / NQ_RED, qq = pq % NQ_RED;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
     double u = 0.0;
-    for (int k = rp.rep_chunk[r] + lane; k < rp.rep_chunk[r + 1]; k += 32) u += __ldcg(rp.part + (size_t)k * NQ_RED + qq);
+    for (int k = c0 + lane; k < c1; k += 32) u += __ldcg(rp.part + (size_t)k * NQ_RED + q);
     u = warp_sum(u);
     if (lane == 0) {
       if (!isfinite(u)) atomicOr(s.err, ERR_NAN);
-      if (qq < NTERMS) E_rep[r * NTERMS + qq] = u;
-      else if (qq < NTERMS + 6) vir_rep[r * 6 + (qq - NTERMS)] = u;
+      if (q < NTERMS) E_rep[r * NTERMS + q] = u;
+      else if (q < NTERMS + 6) vir_rep[r * 6 + (q - NTERMS)] = u;
       else ke_rep[r] = u;
+      *cnt_q = 0u;
+      __threadfence();
+      stage = atomicAdd(cnt_r, 1u) == (unsigned)(NQ_RED - 1) ? 2 : 1;
     }
   }
   __syncthreads();
-  if (etot) {
-    // total energy per replica into etot[k*nrep + r]; k = *etot_idx (then advanced) or 0
-    const int k = etot_idx ? *etot_idx : 0;
-    for (int r = threadIdx.x; r < s.nrep; r += blockDim.x) {
+  if (stage < 2) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (etot) {
+      // total energy of replica r into etot[k*nrep + r]; k = *etot_idx (advanced below) or 0
+      const int k = etot_idx ? *etot_idx : 0;
       double t = 0.0;
-      for (int qq = 0; qq < NTERMS; ++qq) t += E_rep[r * NTERMS + qq];
-      etot[(size_t)k * s.nrep + r] = t + ke_rep[r];
+      for (int qq = 0; qq < NTERMS; ++qq) t += __ldcg(E_rep + r * NTERMS + qq);
+      etot[(size_t)k * s.nrep + r] = t + __ldcg(ke_rep + r);
     }
-    __syncthreads();
-    if (etot_idx && threadIdx.x == 0) *etot_idx = k + 1;
+    *cnt_r = 0u;
+    __threadfence();
+    if (atomicAdd(cnt_all, 1u) == (unsigned)(s.nrep - 1)) {
+      if (etot && etot_idx) *etot_idx += 1;
+      *cnt_all = 0u;
+    }
   }
-  if (threadIdx.x == 0) *rp.done = 0u;
 }
 
 // half kick (and drift). With skin: after the drift, also the float position records and

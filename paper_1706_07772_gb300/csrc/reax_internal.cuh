@@ -551,9 +551,10 @@ constexpr int RED_CHUNK = 512;   // atoms per reduction chunk
 struct RedPlan {                // chunks (<= RED_CHUNK atoms, never straddling replicas) for reductions
   int nchunk;
   int* chunk_lo;               // [nchunk+1]
+  int* chunk_rep;              // [nchunk] replica of each chunk
   int* rep_chunk;              // [nrep+1]
   double* part;                // [nchunk*20]
-  unsigned* done;              // arrival counter of the reduction blocks (zero between launches)
+  unsigned* done;              // arrival counters [nrep*20 + nrep + 1] (zero between launches)
 };
 // per-replica energies, virial and kinetic energy; with etot, also the total energy per
 // replica into etot[k*nrep + r], k = *etot_idx (then advanced) or 0 without etot_idx
