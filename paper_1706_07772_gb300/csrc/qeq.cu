@@ -750,12 +750,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cg(CG<R> a) {
     ++it;
     // ---------------- A: u = H z; p = z + beta p; w = u + beta w; p.w
     for_chunks(a, C, [&](int c, int lo, int hi, int rep, int off) {
+      spmv_chunk(a, B, lo, hi, off);
+      __syncthreads();
       const double* sr = S + rep * NS;
       const bool as = sr[S_ACT_S] > 0, at = sr[S_ACT_T] > 0;
-      // a replica whose two systems have converged needs no SpMV (the flags are the same in
-      // every block, and no replica's rows reach another's atoms)
-      if (as || at) spmv_chunk(a, B, lo, hi, off);
-      __syncthreads();
       const double bes = sr[S_BE_S], bet = sr[S_BE_T];
       const R* us = B.u<R>(0);
       const R* ut = B.u<R>(1);
