@@ -558,7 +558,7 @@ template <int TG> struct GroupSum<double, TG> {
 // centre would leave most lanes idle. The group's float-float totals come from group
 // butterflies; lane q of the group then converts and stores totals q, q + G, ...
 template <int G>
-__global__ void k_angles_g(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<float>* __restrict__ P,
+__global__ void __maxnreg__(72) k_angles_g(Sys s, BondList bl, AtomQ aq, Accum acc, const DParams<float>* __restrict__ P,
                            unsigned mask) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = gt / G;

@@ -77,7 +77,7 @@ __global__ void k_chain1(Sys s, BondList bl, AtomQ aq) {
 }
 
 template <typename R>
-__global__ void k_chain2(Sys s, BondList bl, AtomQ aq, Accum acc) {
+__global__ void __maxnreg__(72) k_chain2(Sys s, BondList bl, AtomQ aq, Accum acc) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt / CHAIN_G, sub = gt & (CHAIN_G - 1);
   const int nb = i < s.n ? bl.cnt[i] : 0;
