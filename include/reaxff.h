@@ -290,9 +290,11 @@ int reaxff_step_dev(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot
  * grid, FP32 position copies, sorted atoms, parameter block; about 2.9 MB) is one
  * file-scope __device__ array that every GPU loading the library keeps until exit.
  *
- * Limits: n <= 65536 atoms and at most 16384 cells (cell edge >= r_nb); larger inputs
- * are rejected with REAXFF_E_INVALID. Inputs (device pointers): types int32[n],
- * positions x, y, z double[n] each (already wrapped into [0, L)). Outputs (device
+ * Limits: n <= 65536 atoms, at most 16384 cells (cell edge >= r_nb) and n * cap below
+ * 2^31 entries; larger inputs are rejected with REAXFF_E_INVALID. Inputs (device
+ * pointers): types int32[n], each in [0, ntypes), and positions x, y, z double[n] each,
+ * already wrapped into [0, L); a device-side check runs first, and a type or position
+ * outside those ranges (or not finite) returns REAXFF_E_INVALID with no list built. Outputs (device
  * pointers, caller-allocated): cnt int32[n] (entries per row, at most cap),
  * j int32[n*cap] and shift uint8[n*cap] (image code (sx+1)*9 + (sy+1)*3 + (sz+1)) and
  * H double[n*cap], row i at [i*cap, i*cap + cnt[i]). Returns REAXFF_E_CAPACITY when a
@@ -301,6 +303,8 @@ int reaxff_step_dev(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot
  * *err_msg (if not NULL) receives a static description of any error.
  * The first call on each device looks up the scratch array's device address (once per
  * device, with that device current); make that first call before any stream capture.
+ * The address is kept for the life of the process, so the entry point must not be used
+ * on a device after cudaDeviceReset (a new context would not hold that address).
  * All calls share the one scratch array and each call clears what must start at zero;
  * calls that overlap on the GPU (several streams or host threads) race on it. */
 int reaxff_far_list_noalloc(const reaxff_params* params, const reaxff_options* options,

@@ -278,16 +278,23 @@ class Model:
         return build_lists(x, self.types, self.box, self.P, self.opts, brute=brute)
 
     # ---------------------------------------------------------------- QEq matrix
+    def qeq_entries(self, x, fi, fj, fs):
+        """Off-diagonal QEq matrix entry of each far-list entry (i, j, s):
+        Tap(r) k_e / (r^3 + gamma_ij^-3)^(1/3), r = |x_j + s L - x_i| (Sec. 3.3 "QEq")."""
+        P = self.P
+        x = np.asarray(x, float)
+        d = (x[fj] - x[fi]) + np.asarray(fs) * self.box
+        r = np.sqrt((d * d).sum(1))
+        g = P["gamma"][self.types[fi], self.types[fj]]
+        return taper(r, self.opts["r_nb"]) * P["k_e"] / np.cbrt(r ** 3 + g ** -3.0)
+
     def qeq_matrix(self, x, L):
         """Sparse H (scipy CSR): H_ii = eta_i; H_ij = sum over images in range of
         Tap(r) k_e / (r^3 + gamma_ij^-3)^(1/3) (Sec. 3.3 "QEq")."""
         import scipy.sparse as sp
         P = self.P
         fi, fj, fs = L["far"]["i"], L["far"]["j"], L["far"]["s"]
-        d = (x[fj] - x[fi]) + fs * self.box
-        r = np.sqrt((d * d).sum(1))
-        g = P["gamma"][self.types[fi], self.types[fj]]
-        v = taper(r, self.opts["r_nb"]) * P["k_e"] / np.cbrt(r ** 3 + g ** -3.0)
+        v = self.qeq_entries(x, fi, fj, fs)
         n = self.n
         Hm = sp.csr_matrix((v, (fi, fj)), shape=(n, n))
         Hm = Hm + sp.diags(P["eta"][self.types])

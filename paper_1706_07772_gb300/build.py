@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libreaxff.so")
-UNITS = ["lists", "bonded", "nonbonded", "qeq", "forces", "abi", "peaks", "noalloc", "mlp", "species"]
+UNITS = ["lists", "bonded", "nonbonded", "qeq", "forces", "abi", "noalloc", "mlp", "species"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
@@ -30,8 +30,7 @@ def _stale(target, deps):
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    headers = [os.path.join(SRC, "reax_internal.cuh"), os.path.join(ROOT, "include", "reaxff.h"),
-               os.path.join(ROOT, "include", "reaxff_probe.h")]
+    headers = [os.path.join(SRC, "reax_internal.cuh"), os.path.join(ROOT, "include", "reaxff.h")]
     objs, jobs = [], []
     for u in UNITS:
         src = os.path.join(SRC, u + ".cu")

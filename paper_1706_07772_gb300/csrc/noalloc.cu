@@ -40,6 +40,29 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
 unsigned char* g_scratch_dev[NOALLOC_MAX_DEVICES] = {nullptr};
 
+// input-check bits of this entry point (kept apart from the list kernels' bits)
+constexpr int NOALLOC_BAD_TYPE = 1 << 20;
+constexpr int NOALLOC_BAD_POS = 1 << 21;
+
+// Device-side input check, run before any kernel indexes a table by type or a cell by
+// position: a type outside [0, ntypes) would index the per-pair tables out of range, and a
+// position outside [0, L) (or not finite) would be clamped into an edge cell, where the
+// 27-cell stencil misses some of its neighbours.
+__global__ void k_noalloc_check(const int32_t* __restrict__ type, const double* __restrict__ x,
+                                const double* __restrict__ y, const double* __restrict__ z, int n,
+                                int ntypes, double Lx, double Ly, double Lz, int* err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int bad = 0;
+  int t = type[i];
+  if (t < 0 || t >= ntypes) bad |= NOALLOC_BAD_TYPE;
+  double p[3] = {x[i], y[i], z[i]};
+  double L[3] = {Lx, Ly, Lz};
+  for (int d = 0; d < 3; ++d)
+    if (!(p[d] >= 0.0 && p[d] < L[d])) bad |= NOALLOC_BAD_POS;   // also catches NaN
+  if (bad) atomicOr(err, bad);
+}
+
 }  // namespace
 
 void rx_fill_params_double(DParams<double>& d, const reaxff_params& p, const reaxff_options& o);
@@ -63,6 +86,10 @@ extern "C" int reaxff_far_list_noalloc(const reaxff_params* params, const reaxff
   }
   if (cap < 1 || params->ntypes < 1 || params->ntypes > MAXT || !(options->r_nb > 0)) {
     *em = "invalid cap, ntypes or r_nb";
+    return REAXFF_E_INVALID;
+  }
+  if ((int64_t)n * (int64_t)cap > (int64_t)INT32_MAX) {
+    *em = "n * cap exceeds 2^31 - 1 entries (row offsets are 32-bit)";
     return REAXFF_E_INVALID;
   }
   int nc[3], ncell = 1;
@@ -128,6 +155,25 @@ extern "C" int reaxff_far_list_noalloc(const reaxff_params* params, const reaxff
     *em = "copy of the header into the scratch array failed";
     return REAXFF_E_CUDA;
   }
+  // reject invalid device inputs before any kernel uses them as indexes
+  int flags = 0;
+  k_noalloc_check<<<(int)((n + 255) / 256), 256, 0, st>>>(types_dev, x_dev, y_dev, z_dev, (int)n,
+                                                          params->ntypes, box[0], box[1], box[2], &hd->err);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, &hd->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    *em = "input check launch or synchronisation failed";
+    return REAXFF_E_CUDA;
+  }
+  if (flags & NOALLOC_BAD_TYPE) {
+    *em = "a type is outside [0, ntypes)";
+    return REAXFF_E_INVALID;
+  }
+  if (flags & NOALLOC_BAD_POS) {
+    *em = "a position is outside [0, L) or not finite (wrap positions into the box first)";
+    return REAXFF_E_INVALID;
+  }
   Sys s{};
   s.n = (int)n;
   s.nrep = 1;
@@ -165,7 +211,7 @@ extern "C" int reaxff_far_list_noalloc(const reaxff_params* params, const reaxff
   rx::Launch L{st, &launches};
   rx::cells_build(L, s, c);
   rx::far_list<double>(L, s, c, f, &hd->P, margin);
-  int flags = 0;
+  flags = 0;
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, &hd->err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

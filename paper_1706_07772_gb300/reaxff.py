@@ -116,7 +116,6 @@ def load(path: str = LIB_PATH):
         "reaxff_profile_enable": (None, [vp, i32]),
         "reaxff_profile_read": (i32, [vp, i32, dp, ip64]),
         "reaxff_stage_name": (C.c_char_p, [i32]),
-        "reaxff_probe_fma_gflops": (C.c_double, [C.c_int, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -503,11 +502,6 @@ class ReaxFF:
         calls = np.zeros(32, np.int64)
         k = self.lib.reaxff_profile_read(self.h, 32, _dp(ms), calls.ctypes.data_as(C.POINTER(C.c_int64)))
         return {self.lib.reaxff_stage_name(i).decode(): (float(ms[i]), int(calls[i])) for i in range(k)}
-
-
-def probe_fma_gflops(fp64: bool, iters: int = 0) -> float:
-    """Measured FMA throughput of the current GPU (GFLOP/s) from reaxff_probe_fma_gflops."""
-    return float(load().reaxff_probe_fma_gflops(1 if fp64 else 0, int(iters)))
 
 
 def virial_matrix(w6):

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", h) for h in ("reaxff.h", "reaxff_probe.h")]
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("reaxff.h",)]
 
 
 @pytest.fixture(scope="module")
