@@ -465,17 +465,6 @@ def test_valence_angle_energy_vanishes_at_its_minimum(params):
     assert 0 < np.argmin(es) < len(es) - 1
 
 
-def test_lone_pair_counts_at_integer_valence(params):
-    """n_lp of an atom with sum BO = Val is (Vale - Val)/2 up to exp(-4 lambda) (O: 2, N: 1, C: 0)."""
-    P = params
-    lam = P["p_lp1"]
-    for t, expect in ((3, 2.0), (2, 1.0), (0, 0.0)):
-        dele = P["val"][t] - P["vale"][t]
-        T = np.trunc(dele / 2)
-        nlp = np.exp(-lam * (2 + dele - 2 * T) ** 2) - T
-        assert nlp == pytest.approx(expect, abs=2 * np.exp(-4 * lam))
-
-
 # ------------------------------------------------------------------ dynamics
 def test_nve_energy_error_is_second_order_in_dt(params):
     """Velocity Verlet on a smooth energy (the tapered nonbonded terms with QEq charges)
