@@ -187,16 +187,22 @@ def test_nve_trajectory_matches_oracle(rx, params):
 
 
 def test_mixed_nve_drift_no_worse_than_fp64(rx, params):
+    """40 NVE steps on petn464: the mixed path's drift max |E - E0| / |E0| is the FP64 path's
+    up to rounding. The slack is 2 % of the FP64 drift plus 4e-7 for two energy evaluations
+    at the mixed path's energy error (measured <= 2e-7 relative per evaluation). The energy
+    curves also agree step by step to 1e-6."""
     w = synth.workload("petn464")
-    drift = []
+    drift, curves = [], []
     for prec in PRECS:
         c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=prec)
         c.set_state(w["x"], w["v"])
         e = c.step(40, 0.1)[:, 0]
+        curves.append(e)
         drift.append(np.abs(e - e[0]).max() / abs(e[0]))
         c.close()
     assert drift[0] < 1e-4
-    assert drift[1] < max(2.0 * drift[0], 1e-6)
+    assert drift[1] <= 1.02 * drift[0] + 4e-7, drift
+    assert np.abs(curves[1] - curves[0]).max() < 1e-6 * abs(curves[0][0])
 
 
 def test_bitwise_reproducible(rx, params):
