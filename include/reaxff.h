@@ -248,6 +248,14 @@ int reaxff_last_qeq_iters(reaxff_ctx* ctx, int32_t* iters_s, int32_t* iters_t);
 /* Forget the QEq solution history (the next solve starts from zero). */
 void reaxff_reset_qeq_history(reaxff_ctx* ctx);
 
+/* Limit, in SM clock cycles, of every wait of the persistent QEq kernel at its grid
+ * barrier (Sec. 3.3's concurrent CG iterations synchronise there); cycles <= 0 restores
+ * the default (3e9 cycles, about 1.5 s at 2 GHz). A wait that runs out sets the device
+ * error flag and every block leaves the solve at its next barrier, so the call returns
+ * REAXFF_E_TIMEOUT instead of waiting on; the context stays usable. A small limit is a
+ * test hook for that path; the default is what production runs use. */
+int reaxff_set_wait_limit(reaxff_ctx* ctx, int64_t cycles);
+
 /* Per replica (int32[nrep]): 1 where the last QEq solve started s from the learned guess
  * (options.warm_start = REAXFF_WARM_MLP with a trained network), 0 where the extrapolated
  * guess had the smaller initial residual. */

@@ -489,11 +489,14 @@ int qeq_impl(reaxff_ctx* ctx, bool side = false) {
   const int threads = ovl == 2 ? 256 : ovl == 1 ? 512 : 1024;
   const float* qhat = nullptr;
   if (ctx->ho.warm_start == REAXFF_WARM_MLP && ctx->mlp.alloc && ctx->mlp.ready) {
-    // learned guess: descriptors of the current lists, tensor-core forward
+    // learned guess: descriptors of the current lists, tensor-core forward. Only a solve
+    // without a usable solution history (the first one, or after a history reset, a re-sort
+    // or a rolled-back call) takes it: with a history the extrapolated start is the better
+    // one, so the kernels check the device history state and return at once
     Stage stg(ctx, 16);
     auto& M = ctx->mlp;
-    rx::mlp_descriptors(L, ctx->sys, ctx->far, M.D);
-    rx::mlp_infer(L, M.D, M.tiles, M.mean, M.inv, M.inf, M.y, ctx->sys.err, ctx->nsm);
+    rx::mlp_descriptors(L, ctx->sys, ctx->far, M.D, ctx->Q.hst);
+    rx::mlp_infer(L, M.D, M.tiles, M.mean, M.inv, M.inf, M.y, ctx->sys.err, ctx->nsm, ctx->Q.hst);
     qhat = M.y;
   }
   if (ctx->Q.precond != REAXFF_PRECOND_JACOBI) {
@@ -1642,6 +1645,13 @@ int64_t reaxff_qeq_spmv_total(reaxff_ctx* ctx) {
   if (cudaMemcpyAsync(&v, ctx->Q.spmv_total, sizeof(v), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess) return -1;
   if (cudaStreamSynchronize(ctx->st) != cudaSuccess) return -1;
   return (int64_t)v;
+}
+
+int reaxff_set_wait_limit(reaxff_ctx* ctx, int64_t cycles) {
+  if (!ctx) return REAXFF_E_INVALID;
+  ctx->Q.bar_limit = cycles > 0 ? (long long)cycles : 0;
+  drop_graph(ctx);                                   // captured launches carry the old limit
+  return REAXFF_OK;
 }
 
 void reaxff_reset_qeq_history(reaxff_ctx* ctx) {

@@ -996,11 +996,15 @@ __global__ void __launch_bounds__(128) k_torsions_q(Sys s, BondList bl, AtomQ aq
     if (ntot > 0) shift_decode(bl.s[ejk], sjk[0], sjk[1], sjk[2]);
     const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)((ntot + TG - 1) / TG));
     int qn = 0;
-    for (int rd = 0; rd < rounds; ++rd) {
+    // rounds of candidate tests, then one more pass that only flushes the queue: every
+    // queued candidate is evaluated by the one batch() call below, whichever pass or queue
+    // position it lands in (the canonical-bond order, and so the queues, vary from run to
+    // run: canon is filled by an atomic append)
+    for (int rd = 0; rd <= rounds; ++rd) {
       const int p = rd * TG + sub;
       bool pass = false;
       int ea = 0, ec = 0, i = 0, l = 0;
-      if (p < ntot) {
+      if (rd < rounds && p < ntot) {
         const int ia = p / (nbk - 1), ic = p % (nbk - 1);
         ea = j * bl.cap + ia + (j * bl.cap + ia >= ejk ? 1 : 0);
         ec = k * bl.cap + ic;
@@ -1024,9 +1028,12 @@ __global__ void __launch_bounds__(128) k_torsions_q(Sys s, BondList bl, AtomQ aq
       }
       qn += __popc(m);
       __syncwarp();
-      if (qn >= 32) {
-        batch(32);
-        const int left = qn - 32;
+      // a full batch of 32 while testing, whatever is left on the flushing pass (qn < 32
+      // then); qn, rd and rounds are warp-uniform
+      const int nact = rd < rounds ? (qn >= 32 ? 32 : 0) : qn;
+      if (nact > 0) {
+        batch(nact);
+        const int left = qn - nact;
         int4 e = make_int4(0, 0, 0, 0);
         int gs = 0;
         if (lane < left) { e = sq[w][32 + lane]; gs = sslot[w][32 + lane]; }
@@ -1036,7 +1043,6 @@ __global__ void __launch_bounds__(128) k_torsions_q(Sys s, BondList bl, AtomQ aq
         qn = left;
       }
     }
-    if (qn > 0) batch(qn);
     __syncwarp();
   }
 }

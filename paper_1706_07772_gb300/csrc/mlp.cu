@@ -45,9 +45,14 @@ __device__ __forceinline__ float cutoff(float r, float rc) {
 // for the four elements, and the angular features are summed per element over the
 // ordered pairs of the 3.5 A neighbours (lanes over pairs, fixed-order warp reduction).
 constexpr int DW = 4;           // warps per block
-__global__ void __launch_bounds__(DW * 32) k_desc(Sys s, FarList f, float* D, int n) {
+// gate (or null): the QEq history state {newest s, newest t, usable solutions}; with a
+// usable history the extrapolated start is kept, so the learned guess is not computed
+__device__ __forceinline__ bool gated_off(const int* gate) { return gate && gate[2] > 0; }
+
+__global__ void __launch_bounds__(DW * 32) k_desc(Sys s, FarList f, float* D, int n, const int* gate) {
   __shared__ float sr[DW][DESC_NB], sx[DW][DESC_NB], sy[DW][DESC_NB], sz[DW][DESC_NB];
   __shared__ int st[DW][DESC_NB];
+  if (gated_off(gate)) return;                         // grid-uniform
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * DW + w;
   if (i >= n) return;                                  // warp-uniform
@@ -395,10 +400,11 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const __nv_bfloat16* __restri
                                                    const int* rows_off, const int* perm, int ntile,
                                                    const __nv_bfloat16* __restrict__ W1t,
                                                    const __nv_bfloat16* __restrict__ W2t, const float* fp,
-                                                   float* y_out, int* err) {
+                                                   float* y_out, int* err, const int* gate) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
+  if (gated_off(gate)) return;                         // grid-uniform, before any TMEM allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" :: "r"(smem_u32(&tmem_slot)) : "memory");
@@ -501,7 +507,8 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const __nv_bfloat16* __restri
 
 // x~ = (x - mean) inv_std in BF16, packed in tile order: row p <- atom perm[p]
 __global__ void k_mlp_pack(const float* D, const int* perm, int rows, const float* mean, const float* inv,
-                           __nv_bfloat16* Xp) {
+                           __nv_bfloat16* Xp, const int* gate) {
+  if (gated_off(gate)) return;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)rows * NF) return;
   const int p = (int)(e / NF), k = (int)(e % NF);
@@ -538,12 +545,13 @@ void mlp_weights(const Launch& L, const float* theta, MlpInfer& w) {
 }
 
 void mlp_infer(const Launch& L, const float* D, const MlpTiles& T, const float* mean, const float* inv,
-               MlpInfer& w, float* y_out, int* err, int nsm) {
+               MlpInfer& w, float* y_out, int* err, int nsm, const int* gate) {
   const int64_t tot = (int64_t)T.rows * NF;
-  k_mlp_pack<<<(unsigned)((tot + 255) / 256), 256, 0, L.st>>>(D, T.perm, T.rows, mean, inv, (__nv_bfloat16*)w.Xp);
+  k_mlp_pack<<<(unsigned)((tot + 255) / 256), 256, 0, L.st>>>(D, T.perm, T.rows, mean, inv, (__nv_bfloat16*)w.Xp,
+                                                               gate);
   const int grid = T.ntile < nsm ? T.ntile : nsm;
   if (grid > 0)
-    k_mlp_tc<<<grid, 128, TC_SMEM, L.st>>>((const __nv_bfloat16*)w.Xp, T.tile_type, T.rows_off, T.perm, T.ntile, (const __nv_bfloat16*)w.W1t, (const __nv_bfloat16*)w.W2t, w.fp, y_out, err);
+    k_mlp_tc<<<grid, 128, TC_SMEM, L.st>>>((const __nv_bfloat16*)w.Xp, T.tile_type, T.rows_off, T.perm, T.ntile, (const __nv_bfloat16*)w.W1t, (const __nv_bfloat16*)w.W2t, w.fp, y_out, err, gate);
   *L.count += 2;
 }
 
@@ -551,8 +559,8 @@ int mlp_tc_setup() {
   return (int)cudaFuncSetAttribute((const void*)k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
 }
 
-void mlp_descriptors(const Launch& L, Sys s, FarList f, float* D) {
-  k_desc<<<(s.n + DW - 1) / DW, DW * 32, 0, L.st>>>(s, f, D, s.n);
+void mlp_descriptors(const Launch& L, Sys s, FarList f, float* D, const int* gate) {
+  k_desc<<<(s.n + DW - 1) / DW, DW * 32, 0, L.st>>>(s, f, D, s.n, gate);
   *L.count += 1;
 }
 

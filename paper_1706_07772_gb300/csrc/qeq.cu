@@ -82,6 +82,7 @@ struct CG {
   int* iters;                              // [2*nrep]
   unsigned long long* spmv_total;          // SpMVs performed by all solves (diagnostic)
   GridBar* bar;
+  long long bar_limit;                     // SM cycles a grid-barrier wait may take
   int* err;
 };
 
@@ -91,8 +92,10 @@ struct CG {
 // semantics (publishes the block's writes, ordered before it by __syncthreads, and takes
 // those of the blocks that arrived earlier) and polls with acquire loads; no reset, so a
 // barrier costs one atomic round trip plus the wait for the last block. The wait gives up
-// after BAR_CYCLE_LIMIT SM cycles and raises ERR_TIMEOUT.
-__device__ bool grid_barrier(GridBar* bar, int* err, unsigned& target) {
+// after `limit` SM cycles (BAR_CYCLE_LIMIT unless the context set another) and raises
+// ERR_TIMEOUT; every block then leaves the kernel at its next barrier (no cp.async copy is
+// in flight at a barrier: the SpMV ring drains before it returns).
+__device__ bool grid_barrier(GridBar* bar, int* err, unsigned& target, long long limit) {
   __syncthreads();
   target += gridDim.x;
   if (threadIdx.x == 0) {
@@ -101,7 +104,7 @@ __device__ bool grid_barrier(GridBar* bar, int* err, unsigned& target) {
     cur += 1u;
     const long long t0 = clock64();
     while ((int)(cur - target) < 0) {
-      if (clock64() - t0 > BAR_CYCLE_LIMIT) {
+      if (clock64() - t0 > limit) {
         atomicOr(err, ERR_TIMEOUT);
         break;
       }
@@ -616,10 +619,14 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cg(CG<R> a) {
       put_zg(a, i, xs, xt);
     });
   });
-  if (a.qhat) {
-    // learned guess for s: s_mlp = q^ + mu t_ext with mu = sum s_ext / sum t_ext of the
-    // replica (then s_mlp - mu t_ext = q^); kept for a replica when its initial residual
-    // ||b_s - H s|| is below the extrapolated guess's (one extra SpMV for both candidates)
+  if (a.qhat && nhist > 0 && lead)
+    for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) a.mlp_used[r] = 0;
+  if (a.qhat && nhist == 0) {
+    // learned guess for s (only without a usable history: with one, the extrapolated guess
+    // is used and the learned one was not computed): s_mlp = q^ + mu t_ext with mu = sum
+    // s_ext / sum t_ext of the replica (then s_mlp - mu t_ext = q^); kept for a replica when
+    // its initial residual ||b_s - H s|| is below the extrapolated guess's (one extra SpMV
+    // for both candidates)
     for_chunks(a, C, [&](int c, int lo, int hi, int, int off) {
       double v[2] = {0, 0};
       for_rows(lo, hi, [&](int i) {
@@ -628,7 +635,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cg(CG<R> a) {
       });
       block_sum<2>(a, v, hi - lo, pb, c);
     });
-    if (!grid_barrier(a.bar, a.err, bt)) return;
+    if (!grid_barrier(a.bar, a.err, bt, a.bar_limit)) return;
     reduce_parts<2>(a, pb, red);
     pb ^= 1;
     for (int r = threadIdx.x; r < a.nrep; r += blockDim.x)
@@ -641,7 +648,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cg(CG<R> a) {
         put_zg(a, i, (double)a.qhat[i] + mu * B.v(V_XT, li), B.v(V_XS, li));
       });
     });
-    if (!grid_barrier(a.bar, a.err, bt)) return;
+    if (!grid_barrier(a.bar, a.err, bt, a.bar_limit)) return;
     for_chunks(a, C, [&](int c, int lo, int hi, int rep, int off) {
       spmv_chunk(a, B, lo, hi, off);
       __syncthreads();
@@ -659,7 +666,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cg(CG<R> a) {
       });
       block_sum<2>(a, v, hi - lo, pb, c);
     });
-    if (!grid_barrier(a.bar, a.err, bt)) return;
+    if (!grid_barrier(a.bar, a.err, bt, a.bar_limit)) return;
     reduce_parts<2>(a, pb, red);
     pb ^= 1;
     for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
@@ -678,7 +685,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cg(CG<R> a) {
       });
     });
   }
-  if (!grid_barrier(a.bar, a.err, bt)) return;
+  if (!grid_barrier(a.bar, a.err, bt, a.bar_limit)) return;
   // r = b - H x, z = M^-1 r, p = w = 0
   for_chunks(a, C, [&](int c, int lo, int hi, int, int off) {
     spmv_chunk(a, B, lo, hi, off);
@@ -720,7 +727,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cg(CG<R> a) {
     }
     block_sum<6>(a, v, hi - lo, pb, c);
   });
-  if (!grid_barrier(a.bar, a.err, bt)) return;
+  if (!grid_barrier(a.bar, a.err, bt, a.bar_limit)) return;
   reduce_parts<6>(a, pb, red);
   pb ^= 1;
   for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
@@ -744,7 +751,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cg(CG<R> a) {
       put_zg(a, i, B.v(V_ZS, li), B.v(V_ZT, li));
     });
   });
-  if (!grid_barrier(a.bar, a.err, bt)) return;
+  if (!grid_barrier(a.bar, a.err, bt, a.bar_limit)) return;
   int it = 0;
   while (S[a.nrep * NS] > 0.0 && it < a.max_iter) {
     ++it;
@@ -774,7 +781,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cg(CG<R> a) {
       });
       block_sum<2>(a, v, hi - lo, pb, c);
     });
-    if (!grid_barrier(a.bar, a.err, bt)) return;
+    if (!grid_barrier(a.bar, a.err, bt, a.bar_limit)) return;
     reduce_parts<2>(a, pb, red);
     pb ^= 1;
     for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
@@ -839,7 +846,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cg(CG<R> a) {
       }
       block_sum<4>(a, v, hi - lo, pb, c);
     });
-    if (!grid_barrier(a.bar, a.err, bt)) return;
+    if (!grid_barrier(a.bar, a.err, bt, a.bar_limit)) return;
     reduce_parts<4>(a, pb, red);
     pb ^= 1;
     for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
@@ -892,7 +899,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_cg(CG<R> a) {
     });
     block_sum<8>(a, v, hi - lo, pb, c);
   });
-  if (!grid_barrier(a.bar, a.err, bt)) return;
+  if (!grid_barrier(a.bar, a.err, bt, a.bar_limit)) return;
   reduce_parts<8>(a, pb, red);
   for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
     const double* rd = red + r * NQ;
@@ -1064,6 +1071,7 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   a.ieta = Q.ieta;
   a.chunk_lo = Q.chunk_lo; a.chunk_rep = Q.chunk_rep; a.rep_chunk = Q.rep_chunk;
   a.iters = Q.iters; a.spmv_total = Q.spmv_total; a.bar = Q.bar; a.err = s.err;
+  a.bar_limit = Q.bar_limit > 0 ? Q.bar_limit : BAR_CYCLE_LIMIT;
   cudaMemsetAsync(Q.bar, 0, sizeof(GridBar), L.st);
   void* args[] = {&a};
   // 1024 threads per SM, or 512 / 256 (mixed path) to leave registers and shared memory of

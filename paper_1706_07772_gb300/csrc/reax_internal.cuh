@@ -608,6 +608,7 @@ struct QeqState {
   int bj_nblk;
   int bj_smem;                 // 1: each block's inverses staged in its shared memory
   const DParams<float>* Pf;    // FP32 parameters for the block build
+  long long bar_limit;         // grid-barrier wait limit in SM cycles (0: BAR_CYCLE_LIMIT)
 };
 // qhat (device, or null): learned charges offered as a second starting guess for s
 template <typename R>
@@ -638,7 +639,8 @@ struct MlpInfer {              // BF16 operands of the tensor-core forward
   void* W2t;                   // [4][64][64] BF16
   float* fp;                   // [4][193] b1, b2, w3, b3
 };
-void mlp_descriptors(const Launch& L, Sys s, FarList f, float* D);
+// gate (device QEq history state, or null): skip the work when a solution history exists
+void mlp_descriptors(const Launch& L, Sys s, FarList f, float* D, const int* gate = nullptr);
 void mlp_stats(const Launch& L, const float* X, int64_t rows, float* mean, float* inv);
 void mlp_loss_grad(const Launch& L, const float* X, const int* type, const int* idx, const int* off, const float* Q,
                    int m, const float* theta, const float* mean, const float* inv, MlpScratch& w, float* G,
@@ -650,7 +652,7 @@ void mlp_adam(const Launch& L, float* theta, const float* g, float* mo, float* v
 void mlp_weights(const Launch& L, const float* theta, MlpInfer& w);
 // y[perm-order samples] = network(D) on the tensor cores (uses the converted weights)
 void mlp_infer(const Launch& L, const float* D, const MlpTiles& T, const float* mean, const float* inv,
-               MlpInfer& w, float* y_out, int* err, int nsm);
+               MlpInfer& w, float* y_out, int* err, int nsm, const int* gate = nullptr);
 int mlp_tc_setup();
 
 // species.cu: molecular species analysis

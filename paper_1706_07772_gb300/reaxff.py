@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
         "reaxff_get_state_dev": (C.c_int, [vp, vp, vp, vp, vp]),
         "reaxff_step_dev": (C.c_int, [vp, i32, C.c_double, vp, vp]),
         "reaxff_reset_qeq_history": (None, [vp]),
+        "reaxff_set_wait_limit": (C.c_int, [vp, i64]),
         "reaxff_qeq_spmv_total": (i64, [vp]),
         "reaxff_qeq_warm_choice": (C.c_int, [vp, ip32]),
         "reaxff_species": (C.c_int, [vp, dp, ip32, ip64, i32, ip32, ip32]),
@@ -346,6 +347,10 @@ class ReaxFF:
 
     def reset_qeq_history(self):
         self.lib.reaxff_reset_qeq_history(self.h)
+
+    def set_wait_limit(self, cycles):
+        """Grid-barrier wait limit of the QEq kernel in SM cycles (<= 0: the default)."""
+        self._check(self.lib.reaxff_set_wait_limit(self.h, int(cycles)))
 
     # ---- learned QEq warm start (marshalling only)
     MLP_NF, MLP_NPAR = 192, 16577

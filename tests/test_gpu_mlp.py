@@ -192,3 +192,42 @@ def test_learned_guess_saves_iterations_and_keeps_charges(rx, params):
     assert abs(qm.sum()) < 1e-9 * len(qm)
     cz.close()
     cm.close()
+
+
+def test_learned_guess_only_without_history(rx, params):
+    """The learned start runs only for a solve without a usable solution history: the cold
+    solve keeps it, while the steps that follow use the extrapolated start. Their solves then
+    run the same SpMVs as a context with the extrapolated start, so no probe SpMV of the learned
+    guess is added per step (that would be 10 extra over 10 steps). After a history reset the
+    next solve takes the learned guess again."""
+    w = synth.workload("petn464")
+    c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=rx.MIXED, warm_start=rx.WARM_MLP)
+    c.set_state(w["x"], w["v"])
+    c.mlp_reserve(8)
+    c.mlp_init(5)
+    for _ in range(8):
+        c.step(2, 0.1)
+        c.mlp_collect()
+    c.mlp_train(40, 2e-3)
+    theta, mean, inv = c.mlp_get_params()
+    c.close()
+    w2 = synth.workload("petn464", seed=7)
+    cm = rx.ReaxFF(params, w2["types"], w2["box"], w2["options"], precision=rx.MIXED, warm_start=rx.WARM_MLP)
+    cm.mlp_set_params(theta, mean, inv)
+    ce = rx.ReaxFF(params, w2["types"], w2["box"], w2["options"], precision=rx.MIXED, warm_start=rx.WARM_EXTRAP)
+    for cc in (cm, ce):
+        cc.set_state(w2["x"], w2["v"])
+        cc.qeq()
+    assert cm.qeq_warm_choice()[0] == 1
+    sp = []
+    for cc in (cm, ce):
+        s0 = cc.qeq_spmv_total()
+        cc.step(10, 0.1)
+        sp.append(cc.qeq_spmv_total() - s0)
+    assert cm.qeq_warm_choice()[0] == 0
+    assert sp[0] <= sp[1] + 2, sp
+    cm.reset_qeq_history()
+    cm.qeq()
+    assert cm.qeq_warm_choice()[0] == 1
+    cm.close()
+    ce.close()

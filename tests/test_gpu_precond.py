@@ -126,3 +126,4 @@ def test_adaptive_guess_saves_spmvs(rx, params, prec, tol):
     assert n_ad <= n_lg, (n_ad, n_lg)
     assert np.abs(x_ad - x_lg).max() < max(1e-8, 0.1 * tol)   # forces differ at the tolerance level
     assert np.abs(q_ad - q_lg).max() < 100 * tol
+
