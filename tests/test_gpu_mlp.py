@@ -203,12 +203,12 @@ def test_learned_guess_only_without_history(rx, params):
     w = synth.workload("petn464")
     c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=rx.MIXED, warm_start=rx.WARM_MLP)
     c.set_state(w["x"], w["v"])
-    c.mlp_reserve(8)
-    c.mlp_init(5)
-    for _ in range(8):
+    c.mlp_reserve(16)
+    c.mlp_init(99)
+    for _ in range(16):
         c.step(2, 0.1)
         c.mlp_collect()
-    c.mlp_train(40, 2e-3)
+    c.mlp_train(80, 2e-3)
     theta, mean, inv = c.mlp_get_params()
     c.close()
     w2 = synth.workload("petn464", seed=7)
