@@ -50,6 +50,9 @@ struct reaxff_ctx {
   cudaStream_t st2 = nullptr;  // second stream (highest priority): bonded terms beside the
                                // nonbonded kernel, or the QEq solve beside the charge-free terms
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t st3 = nullptr;  // third stream: the torsion kernel beside the angle and H-bond
+                               // kernels inside the charge-free path (mixed path)
+  cudaEvent_t ev_fork3 = nullptr, ev_join3 = nullptr;
   int64_t launches = 0;
   bool have_pos = false, forces_valid = false, lists_valid = false;
   float far_margin = 0.f;
@@ -544,9 +547,18 @@ int forces_overlap(reaxff_ctx* ctx, bool bonds_pending) {
   rx::atom_terms<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
   rx::over_under_bond<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
   rx::s_gather<float>(L, ctx->sys, ctx->bond, ctx->aq);
+  // torsions on a third stream beside the angle and H-bond kernels: the three read the same
+  // bond data and add forces, energies, the virial and the dE/dBO, dE/dDelta accumulators
+  // only through exact fixed-point atomics, so their order cannot matter; the chain rule,
+  // which reads those accumulators, waits for all three
+  cudaEventRecord(ctx->ev_fork3, ctx->st);
+  cudaStreamWaitEvent(ctx->st3, ctx->ev_fork3, 0);
+  rx::Launch L3{ctx->st3, &ctx->launches, &ctx->tune};
+  rx::torsions<float>(L3, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  cudaEventRecord(ctx->ev_join3, ctx->st3);
   rx::angles<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
-  rx::torsions<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
   rx::hbonds<float>(L, ctx->sys, ctx->bond, ctx->hb, ctx->acc, P, ctx->mask);
+  CK(cudaStreamWaitEvent(ctx->st, ctx->ev_join3, 0));
   rx::chain_rule<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc);
   if (sp >= 0) record_on(ctx, ctx->ev_pool[sp + 3], ctx->st);
   CK(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
@@ -839,6 +851,9 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   }
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&ctx->st3, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->ev_fork3, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->ev_join3, cudaEventDisableTiming);
   if (ce != cudaSuccess || !coop) {
     delete ctx;
     return REAXFF_E_CUDA;
@@ -1157,6 +1172,9 @@ void reaxff_destroy(reaxff_ctx* ctx) {
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ev_fork3) cudaEventDestroy(ctx->ev_fork3);
+  if (ctx->ev_join3) cudaEventDestroy(ctx->ev_join3);
+  if (ctx->st3) cudaStreamDestroy(ctx->st3);
   if (ctx->st2) cudaStreamDestroy(ctx->st2);
   if (ctx->st) cudaStreamDestroy(ctx->st);
   delete ctx;
