@@ -81,6 +81,11 @@ struct reaxff_ctx {
   int Etot_cap = 0;
   double *chi_t = nullptr, *eta_t = nullptr, *mass_t = nullptr;
   int* h_err_pinned = nullptr;
+  // device-side state I/O (contexts in the caller's order): interleaved input and output
+  // rows, the SoA staging of an upload, and a flag word (allocated on first use)
+  double* d_io = nullptr;      // [13n]: x in [3n], v in [3n], SoA stage [6n]; output x, v, q [7n]
+  int* d_io_flag = nullptr;
+  int* h_io_flag = nullptr;    // pinned
   // host I/O: pinned staging for the state copies (6n doubles: x, y, z, vx, vy, vz as SoA,
   // allocated on first use) and the device positions as last uploaded or downloaded, valid
   // until a step moves the atoms (a round trip of unchanged positions then keeps forces,
@@ -1169,6 +1174,9 @@ void reaxff_destroy(reaxff_ctx* ctx) {
   ctx->lists.free_all();
   ctx->fixed.free_all();
   if (ctx->h_err_pinned) cudaFreeHost(ctx->h_err_pinned);
+  if (ctx->d_io) cudaFree(ctx->d_io);
+  if (ctx->d_io_flag) cudaFree(ctx->d_io_flag);
+  if (ctx->h_io_flag) cudaFreeHost(ctx->h_io_flag);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -1178,6 +1186,108 @@ void reaxff_destroy(reaxff_ctx* ctx) {
   if (ctx->st2) cudaStreamDestroy(ctx->st2);
   if (ctx->st) cudaStreamDestroy(ctx->st);
   delete ctx;
+}
+
+// ---- state I/O on the device (contexts whose atoms are stored in the caller's order)
+namespace {
+// caller's interleaved rows x[3n] (and v[3n], or zeros) -> SoA stage[6n] (x, y, z, vx, vy,
+// vz) with each position wrapped into [0, L) of its replica exactly as the host path does it
+// (fmod is exact; the same additions); flag bit 0: a non-finite position, bit 1: a wrapped
+// position differs from the one the device holds (compared bit for bit; only when `cmp`)
+__global__ void k_state_in(const double* __restrict__ x, const double* __restrict__ v, int n,
+                           const int* __restrict__ rep, const double* __restrict__ box, const double* __restrict__ cx,
+                           const double* __restrict__ cy, const double* __restrict__ cz, int cmp,
+                           double* __restrict__ stage, int* flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* L = box + 3 * rep[i];
+  const double* cur[3] = {cx, cy, cz};
+  int f = 0;
+  for (int d = 0; d < 3; ++d) {
+    double p = x[3 * (size_t)i + d];
+    if (!(p >= 0.0 && p < L[d])) {
+      if (!isfinite(p)) f |= 1;
+      p = fmod(p, L[d]);
+      if (p < 0) p += L[d];
+      if (p >= L[d]) p -= L[d];
+    }
+    stage[d * (size_t)n + i] = p;
+    stage[(3 + d) * (size_t)n + i] = v ? v[3 * (size_t)i + d] : 0.0;
+    if (cmp && __double_as_longlong(p) != __double_as_longlong(cur[d][i])) f |= 2;
+  }
+  if (f) atomicOr(flag, f);
+}
+// SoA state -> interleaved rows: x[3n], v[3n], q[n] at out, out + 3n, out + 6n
+__global__ void k_state_out(Sys s, int want_x, int want_v, int want_q, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const size_t n3 = 3 * (size_t)s.n;
+  if (want_x) {
+    out[3 * (size_t)i] = s.x[i]; out[3 * (size_t)i + 1] = s.y[i]; out[3 * (size_t)i + 2] = s.z[i];
+  }
+  if (want_v) {
+    out[n3 + 3 * (size_t)i] = s.vx[i]; out[n3 + 3 * (size_t)i + 1] = s.vy[i]; out[n3 + 3 * (size_t)i + 2] = s.vz[i];
+  }
+  if (want_q) out[2 * n3 + i] = s.q[i];
+}
+}  // namespace
+
+static int io_buffers(reaxff_ctx* ctx) {
+  if (!ctx->d_io) CK(cudaMalloc(&ctx->d_io, 13 * (size_t)ctx->n * sizeof(double)));
+  if (!ctx->d_io_flag) CK(cudaMalloc(&ctx->d_io_flag, sizeof(int)));
+  if (!ctx->h_io_flag) CK(cudaMallocHost(&ctx->h_io_flag, sizeof(int)));
+  return REAXFF_OK;
+}
+
+// host rows -> device state with the unpacking, wrap, checks and comparison on the device:
+// the host only issues the copies (one synchronisation, for the flags)
+static int set_state_device_io(reaxff_ctx* ctx, const double* x, const double* v) {
+  int rc;
+  if ((rc = io_buffers(ctx))) return rc;
+  const int n = ctx->n;
+  const size_t n3 = 3 * (size_t)n;
+  double* xin = ctx->d_io;
+  double* vin = ctx->d_io + n3;
+  double* stage = ctx->d_io + 2 * n3;
+  CK(cudaMemcpyAsync(xin, x, n3 * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  if (v) CK(cudaMemcpyAsync(vin, v, n3 * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(ctx->d_io_flag, 0, sizeof(int), ctx->st));
+  k_state_in<<<(n + 255) / 256, 256, 0, ctx->st>>>(xin, v ? vin : nullptr, n, ctx->sys.rep, ctx->sys.box, ctx->sys.x,
+                                                   ctx->sys.y, ctx->sys.z, ctx->have_pos ? 1 : 0, stage,
+                                                   ctx->d_io_flag);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->h_io_flag, ctx->d_io_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));                   // the caller's rows are consumed here
+  const int flags = *ctx->h_io_flag;
+  if (flags & 1) return fail(ctx, REAXFF_E_NAN, "non-finite position");
+  // positions bit for bit those the device holds: forces, lists, candidates and image
+  // counters stay valid (the copies below rewrite the same values)
+  const bool same = ctx->have_pos && !(flags & 2);
+  double* dst[6] = {ctx->sys.x, ctx->sys.y, ctx->sys.z, ctx->sys.vx, ctx->sys.vy, ctx->sys.vz};
+  for (int k = 0; k < 6; ++k)
+    CK(cudaMemcpyAsync(dst[k], stage + k * (size_t)n, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  if (!same) {
+    CK(cudaMemsetAsync(ctx->sys.img, 0, n3 * sizeof(int), ctx->st));
+    CK(cudaMemsetAsync(ctx->sys.rebuild, 1, sizeof(int), ctx->st));   // new positions: rebuild candidates
+    ctx->have_pos = true;
+    ctx->forces_valid = false;
+    ctx->lists_valid = false;
+  }
+  ctx->h_pos_valid = false;                             // no host copy of the positions is kept
+  return REAXFF_OK;
+}
+
+static int get_state_device_io(reaxff_ctx* ctx, double* x, double* v, double* q) {
+  int rc;
+  if ((rc = io_buffers(ctx))) return rc;
+  const size_t n = ctx->n, n3 = 3 * n;
+  k_state_out<<<(unsigned)((n + 255) / 256), 256, 0, ctx->st>>>(ctx->sys, x ? 1 : 0, v ? 1 : 0, q ? 1 : 0, ctx->d_io);
+  CK(cudaGetLastError());
+  if (x) CK(cudaMemcpyAsync(x, ctx->d_io, n3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  if (v) CK(cudaMemcpyAsync(v, ctx->d_io + n3, n3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  if (q) CK(cudaMemcpyAsync(q, ctx->d_io + 2 * n3, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return REAXFF_OK;
 }
 
 static int stage_buffer(reaxff_ctx* ctx) {
@@ -1257,6 +1367,7 @@ static int set_state_common(reaxff_ctx* ctx, const double* x, const double* v, c
 
 int reaxff_set_state(reaxff_ctx* ctx, const double* x, const double* v) {
   if (!ctx || !x) return REAXFF_E_INVALID;
+  if (!ctx->sort_on) return set_state_device_io(ctx, x, v);
   return set_state_common(ctx, x, v, cudaMemcpyHostToHost, ctx->st);
 }
 
@@ -1300,6 +1411,7 @@ static int get_soa3(reaxff_ctx* ctx, const double* a, const double* b, const dou
 int reaxff_get_state(reaxff_ctx* ctx, double* x, double* v, double* q) {
   if (!ctx) return REAXFF_E_INVALID;
   if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
+  if (ctx->perm.empty()) return get_state_device_io(ctx, x, v, q);
   int rc;
   if (x && (rc = get_soa3(ctx, ctx->sys.x, ctx->sys.y, ctx->sys.z, x))) return rc;
   if (v && (rc = get_soa3(ctx, ctx->sys.vx, ctx->sys.vy, ctx->sys.vz, v))) return rc;
