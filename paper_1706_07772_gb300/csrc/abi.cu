@@ -2470,10 +2470,21 @@ template <typename R> void tune_all(reaxff_ctx* ctx) {
   if (!ctx->fp64) {
     const int mi = ctx->ho.qeq_max_iter;
     ctx->ho.qeq_max_iter = 7;
-    pick(T.qeq_overlap, {0, 1, 2}, [&] {
+    auto whole = [&] {
       cudaMemsetAsync(ctx->Q.hst + 2, 0, sizeof(int), ctx->st);
       forces_impl(ctx, true, true, false);
-    });
+    };
+    pick(T.qeq_overlap, {0, 1, 2}, whole);
+    if (T.qeq_overlap != 0) {
+      // beside the resident solve the charge-free kernels get fewer registers and warps per
+      // SM than when timed alone above: their launch shapes are picked again by whole
+      // overlapped force evaluations
+      pick(T.tors_lanes, {2, 4, 8}, whole);
+      pick(T.ang_lanes, {8, 16, 32}, whole);
+      pick(T.ang_block, {64, 128, 256}, whole);
+      pick(T.hb_block, {64, 128, 256}, whole);
+      pick(T.nb_block, {128, 256, 512}, whole);
+    }
     ctx->ho.qeq_max_iter = mi;
     cudaMemsetAsync(ctx->Q.hst + 2, 0, sizeof(int), ctx->st);
   }
