@@ -2479,8 +2479,8 @@ template <typename R> void tune_all(reaxff_ctx* ctx) {
       // beside the resident solve the charge-free kernels get fewer registers and warps per
       // SM than when timed alone above: their launch shapes are picked again by whole
       // overlapped force evaluations
-      pick(T.tors_lanes, {2, 4, 8}, whole);
-      pick(T.ang_lanes, {8, 16, 32}, whole);
+      pick(T.tors_lanes, {1, 2, 4, 8}, whole);
+      pick(T.ang_lanes, {4, 8, 16, 32}, whole);
       pick(T.ang_block, {64, 128, 256}, whole);
       pick(T.hb_block, {64, 128, 256}, whole);
       pick(T.nb_block, {128, 256, 512}, whole);

@@ -1189,7 +1189,8 @@ void angles(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParam
   const int g = L.t().ang_lanes;
   if constexpr (sizeof(R) == 4) {
     const unsigned grid = grid_for((long long)s.n * g, bs);
-    if (g == 8) k_angles_g<8><<<grid, bs, 0, L.st>>>(s, b, a, acc, P, mask);
+    if (g == 4) k_angles_g<4><<<grid, bs, 0, L.st>>>(s, b, a, acc, P, mask);
+    else if (g == 8) k_angles_g<8><<<grid, bs, 0, L.st>>>(s, b, a, acc, P, mask);
     else if (g == 16) k_angles_g<16><<<grid, bs, 0, L.st>>>(s, b, a, acc, P, mask);
     else k_angles_g<32><<<grid, bs, 0, L.st>>>(s, b, a, acc, P, mask);
   } else {
@@ -1204,7 +1205,8 @@ void torsions(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DPar
   const int tg = L.t().tors_lanes;
   const unsigned grid = grid_for((long long)s.n * tg, 128);
   if constexpr (sizeof(R) == 4) {
-    if (tg == 2) k_torsions_q<2><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
+    if (tg == 1) k_torsions_q<1><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
+    else if (tg == 2) k_torsions_q<2><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
     else if (tg == 8) k_torsions_q<8><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
     else k_torsions_q<4><<<grid, 128, 0, L.st>>>(s, b, a, acc, P, mask);
   } else {

@@ -481,12 +481,12 @@ std::string cuda_err_str(cudaError_t e);
 namespace rx {
 // launch schedules picked by the autotuner (reaxff_autotune); defaults otherwise
 struct Tune {
-  int tors_lanes = 4;          // lanes per central bond in the torsion kernel (2, 4, 8)
+  int tors_lanes = 4;          // lanes per central bond in the torsion kernel (1 mixed path only, 2, 4, 8)
   int nb_block = 256;          // threads per block: nonbonded (warp per atom)
   int cf_block = 256;          //   candidate filter (warp per atom)
   int bl_block = 256;          //   bond list (warp per atom)
   int ang_block = 128;         //   angles
-  int ang_lanes = 8;           // lanes per centre atom in the angle kernel (8, 16, 32; mixed path)
+  int ang_lanes = 8;           // lanes per centre atom in the angle kernel (4, 8, 16, 32; mixed path)
   int hb_block = 128;          //   H-bonds (warp per hydrogen)
   int qeq_overlap = 0;         // 1 / 2: QEq (CG on 512 / 256 threads per SM) runs beside the
                                //    charge-free bond-order and bonded kernels (mixed path)

@@ -19,9 +19,10 @@ def test_autotune_schedule_and_cache(params, tmp_path, prec):
     F0, E0, _ = c.forces(q=q)                       # fixed charges: only the schedule changes
     cache = tmp_path / "tune.txt"
     sch = c.autotune(cache)
-    assert sch[0] in (2, 4, 8) and sch[1] in (128, 256, 512) and sch[2] in (128, 256, 512)
+    # torsion lanes 1 and angle lanes 4 are candidates of the second, overlapped tuning pass
+    assert sch[0] in (1, 2, 4, 8) and sch[1] in (128, 256, 512) and sch[2] in (128, 256, 512)
     assert sch[3] in (128, 256, 512) and sch[4] in (64, 128, 256) and sch[5] in (64, 128, 256)
-    assert sch[6] in (8, 16, 32) and sch[7] in (0, 1, 2)
+    assert sch[6] in (4, 8, 16, 32) and sch[7] in (0, 1, 2)
     F1, E1, _ = c.forces(q=q)
     rms = np.sqrt((F0 ** 2).mean())
     assert np.abs(F1 - F0).max() < (1e-12 if prec == 0 else 1e-6) * rms
