@@ -414,8 +414,8 @@ int reaxff_species_average(reaxff_ctx* ctx, const double* bo_threshold, int32_t*
  * stream beside the charge-independent bond-order and bonded terms, with a half (1) or a
  * quarter (2) of each SM's threads, instead of before them (0) (the same results to within the rounding of the CG dot
  * products, whose partial sums follow the thread count). With the solve beside the terms,
- * the torsion lanes (1, 2, 4, 8), angle lanes (4, 8, 16, 32), angle, H-bond and nonbonded
- * blocks are timed again by whole force evaluations in that schedule. Needs positions; forces are
+ * the torsion lanes (1, 2, 4, 8), angle lanes (4, 8, 16, 32), angle, H-bond, nonbonded and
+ * bond-list blocks are timed again by whole force evaluations in that schedule. Needs positions; forces are
  * recomputed afterwards (the timing runs accumulate into them). cache_path (or NULL): a
  * text file of "reaxff-tune <key> | ..." lines, the key being (n, replicas, precision,
  * skin, compute capability, SM count); a matching line is used instead of timing, a new

@@ -2484,6 +2484,7 @@ template <typename R> void tune_all(reaxff_ctx* ctx) {
       pick(T.ang_block, {64, 128, 256}, whole);
       pick(T.hb_block, {64, 128, 256}, whole);
       pick(T.nb_block, {128, 256, 512}, whole);
+      pick(T.bl_block, {128, 256, 512}, whole);
     }
     ctx->ho.qeq_max_iter = mi;
     cudaMemsetAsync(ctx->Q.hst + 2, 0, sizeof(int), ctx->st);
