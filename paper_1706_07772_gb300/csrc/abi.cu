@@ -645,10 +645,8 @@ int forces_impl(reaxff_ctx* ctx, bool solve_q, bool reduce = true, bool checked 
   return REAXFF_OK;
 }
 
-int check_flags(reaxff_ctx* ctx, bool allow_nc) {
-  int flags = 0;
-  int rc = read_err(ctx, &flags);
-  if (rc) return rc;
+// the status a set of device error flags stands for
+int flags_status(reaxff_ctx* ctx, int flags, bool allow_nc) {
   if (flags & ERR_TIMEOUT) return fail(ctx, REAXFF_E_TIMEOUT, "a device-side wait hit its spin limit");
   if (flags & ERR_NAN) return fail(ctx, REAXFF_E_NAN, "non-finite or out-of-range value in forces/energies");
   if (flags & (ERR_CAP_FAR | ERR_CAP_BOND | ERR_CAP_HB | ERR_CAP_NEAR | ERR_CAP_CAND))
@@ -659,6 +657,13 @@ int check_flags(reaxff_ctx* ctx, bool allow_nc) {
     return REAXFF_E_NOT_CONVERGED;
   }
   return REAXFF_OK;
+}
+
+int check_flags(reaxff_ctx* ctx, bool allow_nc) {
+  int flags = 0;
+  int rc = read_err(ctx, &flags);
+  if (rc) return rc;
+  return flags_status(ctx, flags, allow_nc);
 }
 
 // Initial-guess weights w[sys][m][k] of predictor `pred` (sys 0: s, 1: t; m newest solutions
@@ -1704,7 +1709,7 @@ static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev) {
     if ((rc = run_unchecked(ctx, nsteps, dt, Etot_dev, &flags))) return rc;
     const int cap = ERR_CAP_FAR | ERR_CAP_BOND | ERR_CAP_HB | ERR_CAP_NEAR | ERR_CAP_CAND;
     if (!(flags & cap) || (flags & (ERR_NAN | ERR_TIMEOUT))) {
-      rc = check_flags(ctx, false);
+      rc = flags_status(ctx, flags, false);               // the flags were read after the last step
       collect_profile(ctx);
       return rc;
     }
