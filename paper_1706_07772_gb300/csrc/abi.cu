@@ -495,6 +495,7 @@ int qeq_impl(reaxff_ctx* ctx, bool side = false) {
   if (side) L.st = ctx->st2;
   const int ovl = (side || (ctx->prof == 1 && !ctx->fp64)) ? ctx->tune.qeq_overlap : 0;
   const int threads = ovl == 2 ? 256 : ovl == 1 ? 512 : 1024;
+  const int layout = ovl >= 3 ? ovl - 2 : 0;
   const float* qhat = nullptr;
   if (ctx->ho.warm_start == REAXFF_WARM_MLP && ctx->mlp.alloc && ctx->mlp.ready) {
     // learned guess: descriptors of the current lists, tensor-core forward. Only a solve
@@ -516,7 +517,7 @@ int qeq_impl(reaxff_ctx* ctx, bool side = false) {
                                              ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start, qhat)
                      : rx::qeq_solve<float>(L, ctx->sys, ctx->far, ctx->Q, ctx->Pf, ctx->chi_t, ctx->eta_t,
                                             ctx->ho.qeq_tol, ctx->ho.qeq_max_iter, ctx->ho.warm_start, qhat,
-                                            threads);
+                                            threads, layout);
   if (rc) {
     cudaError_t e = cudaGetLastError();
     return fail(ctx, REAXFF_E_CUDA, "cooperative QEq launch failed: " + cuda_err_str(e));
@@ -548,17 +549,19 @@ int forces_overlap(reaxff_ctx* ctx, bool bonds_pending) {
   if (sp >= 0) record_on(ctx, ctx->ev_pool[sp + 1], ctx->st2);
   cudaEventRecord(ctx->ev_join, ctx->st2);
   if (bonds_pending) bond_lists_impl(ctx, L);      // the solve reads only the far list
-  rx::bo_correct<float>(L, ctx->sys, ctx->bond, ctx->aq, P);
-  rx::atom_terms<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
-  rx::over_under_bond<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
-  rx::s_gather<float>(L, ctx->sys, ctx->bond, ctx->aq);
-  // torsions on a third stream beside the angle and H-bond kernels: the three read the same
-  // bond data and add forces, energies, the virial and the dE/dBO, dE/dDelta accumulators
-  // only through exact fixed-point atomics, so their order cannot matter; the chain rule,
-  // which reads those accumulators, waits for all three
+  rx::bo_correct_atom_terms<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  // over/under-coordination with the bond energy, the S gather and the torsions on a third
+  // stream beside the angle and H-bond kernels. The angle, torsion and H-bond kernels read
+  // only the corrected bond orders and the atom quantities of the kernel above; the
+  // over/under kernel's own outputs (dE/dS) are read by the S gather after it on the same
+  // stream. Everything else they write (forces, energies, the virial, the dE/dBO and dE/dDelta
+  // accumulators) is added through exact fixed-point atomics or owner-written per term, so
+  // their order cannot matter; the chain rule, which reads the accumulators, waits for all
   cudaEventRecord(ctx->ev_fork3, ctx->st);
   cudaStreamWaitEvent(ctx->st3, ctx->ev_fork3, 0);
   rx::Launch L3{ctx->st3, &ctx->launches, &ctx->tune};
+  rx::over_under_bond<float>(L3, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  rx::s_gather<float>(L3, ctx->sys, ctx->bond, ctx->aq);
   rx::torsions<float>(L3, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
   cudaEventRecord(ctx->ev_join3, ctx->st3);
   rx::angles<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
@@ -573,8 +576,12 @@ int forces_overlap(reaxff_ctx* ctx, bool bonds_pending) {
 template <typename R> void terms_impl(reaxff_ctx* ctx) {
   rx::Launch L = launch_of(ctx);
   const DParams<R>* P = params_of<R>(ctx);
-  { Stage st(ctx, 5); rx::bo_correct<R>(L, ctx->sys, ctx->bond, ctx->aq, P); }
-  { Stage st(ctx, 6); rx::atom_terms<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
+  if (ctx->prof == 1) {                                   // stage timers: one kernel per stage
+    { Stage st(ctx, 5); rx::bo_correct<R>(L, ctx->sys, ctx->bond, ctx->aq, P); }
+    { Stage st(ctx, 6); rx::atom_terms<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
+  } else {
+    rx::bo_correct_atom_terms<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  }
   { Stage st(ctx, 7); rx::over_under_bond<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
   { Stage st(ctx, 8); rx::s_gather<R>(L, ctx->sys, ctx->bond, ctx->aq); }
   if (sizeof(R) == 4 && ctx->prof != 1) {
@@ -969,7 +976,7 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   ctx->Q.ieta = ieta_d;
   // ---- QEq state and chunking (chunks never straddle replicas)
   rx::QeqState& Q = ctx->Q;
-  Q.grid = rx::qeq_grid_size(ctx->nsm);
+  const int grid_all = rx::qeq_grid_size(ctx->nsm);
   Q.zg = B.alloc<double>(2 * (size_t)n);
   Q.hist_s = B.alloc<double>(2 * rx::QEQ_HIST * (size_t)n);   // s ring, then t ring
   Q.hist_t = Q.hist_s + rx::QEQ_HIST * (size_t)n;
@@ -977,22 +984,6 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   Q.pred = B.alloc<int>(2 * nrep);
   Q.precond = options->qeq_precond;
   Q.Pf = ctx->Pf;
-  int rows = std::max(8, (int)((n + Q.grid - 1) / Q.grid));
-  if (Q.precond == REAXFF_PRECOND_BLOCK32) rows = round_up(rows, 32);   // chunks start on block boundaries
-  std::vector<int> clo, crep, rchunk(nrep + 1, 0);
-  for (int r = 0; r < nrep; ++r) {
-    rchunk[r] = (int)crep.size();
-    for (int64_t i = rep_offsets[r]; i < rep_offsets[r + 1]; i += rows) {
-      clo.push_back((int)i);
-      crep.push_back(r);
-    }
-  }
-  rchunk[nrep] = (int)crep.size();
-  Q.nchunk = (int)crep.size();
-  clo.push_back(n);
-  int* clo_d = B.alloc<int>(clo.size());
-  int* crep_d = B.alloc<int>(crep.size());
-  int* rchunk_d = B.alloc<int>(nrep + 1);
   // block-Jacobi blocks: 32 consecutive atoms of a replica (fewer at its end)
   std::vector<int> bjs, bjn;
   if (Q.precond == REAXFF_PRECOND_BLOCK32)
@@ -1005,26 +996,53 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   Q.bj_start = Q.bj_nblk ? B.alloc<int>(Q.bj_nblk) : nullptr;
   Q.bj_size = Q.bj_nblk ? B.alloc<int>(Q.bj_nblk) : nullptr;
   Q.binv = Q.bj_nblk ? B.alloc<float>(32 * ((size_t)n + 32)) : nullptr;
-  Q.chunk_lo = clo_d; Q.chunk_rep = crep_d; Q.rep_chunk = rchunk_d;
-  Q.part = B.alloc<double>((size_t)Q.nchunk * 2 * 8);
-  {
-    // rows per block (block b owns chunks b, b + grid, ...); shared memory when it fits
-    std::vector<int> rowsb(Q.grid, 0);
-    for (int c = 0; c < Q.nchunk; ++c) rowsb[c % Q.grid] += clo[c + 1] - clo[c];
-    Q.rows_blk = *std::max_element(rowsb.begin(), rowsb.end());
-    const size_t sc = (size_t)(nrep * rx::QEQ_SCAL_PER_REP + 4) * sizeof(double);
-    const size_t st = (size_t)rx::QEQ_NV_STATE * Q.rows_blk * sizeof(double);
-    Q.ring_bytes = rx::qeq_ring_bytes(ctx->fp64);
+  Q.ring_bytes = rx::qeq_ring_bytes(ctx->fp64);
+  // launch shapes: chunks of about n / grid rows that never straddle replicas, and per block
+  // its rows' state in shared memory when it fits
+  std::vector<std::vector<int>> h_clo(rx::QEQ_NLAYOUT), h_crep(rx::QEQ_NLAYOUT), h_rchunk(rx::QEQ_NLAYOUT);
+  size_t part_chunks = 0, scal_rows = 0, state_rows = 0;
+  const size_t sc = (size_t)(nrep * rx::QEQ_SCAL_PER_REP + 4) * sizeof(double);
+  for (int l = 0; l < rx::QEQ_NLAYOUT; ++l) {
+    rx::QeqLayout& Y = Q.lay[l];
+    Y.grid = std::max(1, grid_all * rx::QEQ_PART_NUM[l] / 8);
+    int rows = std::max(8, (int)((n + Y.grid - 1) / Y.grid));
+    if (Q.precond == REAXFF_PRECOND_BLOCK32) rows = round_up(rows, 32);   // chunks start on block boundaries
+    std::vector<int>& clo = h_clo[l];
+    std::vector<int>& crep = h_crep[l];
+    std::vector<int>& rchunk = h_rchunk[l];
+    rchunk.assign(nrep + 1, 0);
+    for (int r = 0; r < nrep; ++r) {
+      rchunk[r] = (int)crep.size();
+      for (int64_t i = rep_offsets[r]; i < rep_offsets[r + 1]; i += rows) {
+        clo.push_back((int)i);
+        crep.push_back(r);
+      }
+    }
+    rchunk[nrep] = (int)crep.size();
+    Y.nchunk = (int)crep.size();
+    clo.push_back(n);
+    Y.chunk_lo = B.alloc<int>(clo.size());
+    Y.chunk_rep = B.alloc<int>(crep.size());
+    Y.rep_chunk = B.alloc<int>(nrep + 1);
+    // rows per block (block b owns chunks b, b + grid, ...)
+    std::vector<int> rowsb(Y.grid, 0);
+    for (int c = 0; c < Y.nchunk; ++c) rowsb[c % Y.grid] += clo[c + 1] - clo[c];
+    Y.rows_blk = *std::max_element(rowsb.begin(), rowsb.end());
+    const size_t st = (size_t)rx::QEQ_NV_STATE * Y.rows_blk * sizeof(double);
     const size_t avail = (size_t)rx::QEQ_SMEM_MAX - Q.ring_bytes;
-    Q.scal_smem = sc <= avail / 2;
-    Q.state_smem = (Q.scal_smem ? sc : 0) + st <= avail;
-    const size_t bjb = Q.precond == REAXFF_PRECOND_BLOCK32 ? (size_t)Q.rows_blk * 32 * sizeof(float) : 0;
-    const size_t used = (Q.scal_smem ? sc : 0) + (Q.state_smem ? st : 0);
-    Q.bj_smem = bjb > 0 && used + bjb <= avail;
-    Q.smem_bytes = (int)(Q.ring_bytes + used + (Q.bj_smem ? bjb : 0));
-    Q.scal = Q.scal_smem ? nullptr : B.alloc<double>((size_t)Q.grid * (nrep * rx::QEQ_SCAL_PER_REP + 4));
-    Q.state = Q.state_smem ? nullptr : B.alloc<double>((size_t)Q.grid * rx::QEQ_NV_STATE * Q.rows_blk);
+    Y.scal_smem = sc <= avail / 2;
+    Y.state_smem = (Y.scal_smem ? sc : 0) + st <= avail;
+    const size_t bjb = Q.precond == REAXFF_PRECOND_BLOCK32 ? (size_t)Y.rows_blk * 32 * sizeof(float) : 0;
+    const size_t used = (Y.scal_smem ? sc : 0) + (Y.state_smem ? st : 0);
+    Y.bj_smem = bjb > 0 && used + bjb <= avail;
+    Y.smem_bytes = (int)(Q.ring_bytes + used + (Y.bj_smem ? bjb : 0));
+    part_chunks = std::max(part_chunks, (size_t)Y.nchunk);
+    if (!Y.scal_smem) scal_rows = std::max(scal_rows, (size_t)Y.grid);
+    if (!Y.state_smem) state_rows = std::max(state_rows, (size_t)Y.grid * Y.rows_blk);
   }
+  Q.part = B.alloc<double>(part_chunks * 2 * 8);
+  Q.scal = scal_rows ? B.alloc<double>(scal_rows * (nrep * rx::QEQ_SCAL_PER_REP + 4)) : nullptr;
+  Q.state = state_rows ? B.alloc<double>(state_rows * rx::QEQ_NV_STATE) : nullptr;
   // reduction chunks (<= RED_CHUNK atoms each, per replica)
   std::vector<int> rlo, rrep(nrep + 1, 0);
   for (int r = 0; r < nrep; ++r) {
@@ -1099,9 +1117,11 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   UP(boxl_d, bl.data(), 3 * nrep * sizeof(float));
   UP(nc_d, nc.data(), 3 * nrep * sizeof(int));
   UP(coff_d, cell_off.data(), (nrep + 1) * sizeof(int));
-  UP(clo_d, clo.data(), clo.size() * sizeof(int));
-  UP(crep_d, crep.data(), crep.size() * sizeof(int));
-  UP(rchunk_d, rchunk.data(), (nrep + 1) * sizeof(int));
+  for (int l = 0; l < rx::QEQ_NLAYOUT; ++l) {
+    UP(Q.lay[l].chunk_lo, h_clo[l].data(), h_clo[l].size() * sizeof(int));
+    UP(Q.lay[l].chunk_rep, h_crep[l].data(), h_crep[l].size() * sizeof(int));
+    UP(Q.lay[l].rep_chunk, h_rchunk[l].data(), (nrep + 1) * sizeof(int));
+  }
   {
     std::vector<double> wx;
     for (int p = 0; p < rx::QEQ_NPRED; ++p) {
@@ -1637,7 +1657,7 @@ static bool capture_step(reaxff_ctx* ctx, double dt) {
   ctx->capturing = false;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
-  if (rc == REAXFF_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+  if (rc == REAXFF_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&ctx->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
   if (g) cudaGraphDestroy(g);
   const bool ok = rc == REAXFF_OK && e == cudaSuccess && ctx->gexec;
   if (!ok) {
@@ -2479,7 +2499,7 @@ template <typename R> void tune_all(reaxff_ctx* ctx) {
       cudaMemsetAsync(ctx->Q.hst + 2, 0, sizeof(int), ctx->st);
       forces_impl(ctx, true, true, false);
     };
-    pick(T.qeq_overlap, {0, 1, 2}, whole);
+    pick(T.qeq_overlap, {0, 1, 2, 3, 4, 5}, whole);
     if (T.qeq_overlap != 0) {
       // beside the resident solve the charge-free kernels get fewer registers and warps per
       // SM than when timed alone above: their launch shapes are picked again by whole
@@ -2494,6 +2514,19 @@ template <typename R> void tune_all(reaxff_ctx* ctx) {
     ctx->ho.qeq_max_iter = mi;
     cudaMemsetAsync(ctx->Q.hst + 2, 0, sizeof(int), ctx->st);
   }
+}
+
+// a schedule read from a cache file: every entry one the tuner can pick (a line edited by hand
+// or from another version is ignored, and the context is tuned again)
+bool tune_valid(const rx::Tune& t) {
+  auto in = [](int v, std::initializer_list<int> set) {
+    for (int c : set)
+      if (v == c) return true;
+    return false;
+  };
+  return in(t.tors_lanes, {1, 2, 4, 8}) && in(t.ang_lanes, {4, 8, 16, 32}) && in(t.nb_block, {128, 256, 512}) &&
+         in(t.cf_block, {128, 256, 512}) && in(t.bl_block, {128, 256, 512}) && in(t.ang_block, {64, 128, 256}) &&
+         in(t.hb_block, {64, 128, 256}) && t.qeq_overlap >= 0 && t.qeq_overlap <= 1 + rx::QEQ_NLAYOUT;
 }
 
 std::string tune_key(reaxff_ctx* ctx) {
@@ -2531,7 +2564,7 @@ int reaxff_autotune(reaxff_ctx* ctx, const char* cache_path, int32_t* schedule) 
         char k[256];
         if (sscanf(line, "reaxff-tune %255[^|]| tors=%d nb=%d cf=%d bl=%d ang=%d hb=%d angl=%d qov=%d", k,
                    &t.tors_lanes, &t.nb_block, &t.cf_block, &t.bl_block, &t.ang_block, &t.hb_block, &t.ang_lanes,
-                   &t.qeq_overlap) == 9 &&
+                   &t.qeq_overlap) == 9 && tune_valid(t) &&
             key == std::string(k).substr(0, std::string(k).find_last_not_of(' ') + 1)) {
           ctx->tune = t;
           found = true;

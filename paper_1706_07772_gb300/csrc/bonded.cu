@@ -44,11 +44,20 @@ template <typename R> __device__ __forceinline__ R wbit(unsigned mask, int t) {
   return ((mask >> t) & 1u) ? R(1) : R(0);
 }
 
+template <typename R>
+__device__ __forceinline__ void atom_terms_of(int i, const Sys& s, const BondList& bl, const AtomQ& aq,
+                                              const Accum& acc, const DParams<R>* __restrict__ P, unsigned mask);
+
 // ------------------------------------------------------------------ BO correction
 // Evaluated in the path's precision R from FP64 Delta' and BO'; the factors and their
-// partials are stored in FP64 for the chain rule, BO, BO_pi and BO_pp in R.
-template <typename R>
-__global__ void k_bo_correct(Sys s, BondList bl, AtomQ aq, const DParams<R>* __restrict__ P) {
+// partials are stored in FP64 for the chain rule, BO, BO_pi and BO_pp in R. Every entry of
+// row i is corrected by thread i (a bond's two entries by the two atoms' threads, with the
+// same operands in the same order), so with ATOM the thread goes on to atom i's terms, which
+// read only row i's corrected orders: the same values, written and read back by the same
+// thread, as the separate kernel reads.
+template <typename R, bool ATOM = false>
+__global__ void k_bo_correct(Sys s, BondList bl, AtomQ aq, const DParams<R>* __restrict__ P, Accum acc,
+                             unsigned mask) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
   const int ti = s.type[i];
@@ -109,6 +118,7 @@ __global__ void k_bo_correct(Sys s, BondList bl, AtomQ aq, const DParams<R>* __r
     f1a[e] = f1; foa[e] = fo; fta[e] = ft; df1a[e] = df1;
     dfoba[e] = dfo_bo; dftba[e] = dft_bo; dfoda[e] = dfo_d;
   }
+  if constexpr (ATOM) atom_terms_of<R>(i, s, bl, aq, acc, P, mask);
 }
 
 // ------------------------------------------------------------------ atom terms + lone pair
@@ -117,6 +127,12 @@ __global__ void k_atom_terms(Sys s, BondList bl, AtomQ aq, Accum acc, const DPar
                              unsigned mask) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
+  atom_terms_of<R>(i, s, bl, aq, acc, P, mask);
+}
+
+template <typename R>
+__device__ __forceinline__ void atom_terms_of(int i, const Sys& s, const BondList& bl, const AtomQ& aq,
+                                              const Accum& acc, const DParams<R>* __restrict__ P, unsigned mask) {
   const int ti = s.type[i];
   const int nb = bl.cnt[i];
   const R* bo = (const R*)bl.bo;
@@ -1166,7 +1182,13 @@ __global__ void k_hbonds(Sys s, BondList bl, HbList hl, Accum acc, const DParams
 namespace rx {
 
 template <typename R> void bo_correct(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<R>* P) {
-  k_bo_correct<R><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a, P);
+  k_bo_correct<R, false><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a, P, Accum{}, 0u);
+  *L.count += 1;
+}
+template <typename R>
+void bo_correct_atom_terms(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P,
+                           unsigned mask) {
+  k_bo_correct<R, true><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a, P, acc, mask);
   *L.count += 1;
 }
 template <typename R>
@@ -1226,6 +1248,7 @@ void hbonds(const Launch& L, Sys s, BondList b, HbList h, Accum acc, const DPara
 #define INST(R)                                                                                           \
   template void bo_correct<R>(const Launch&, Sys, BondList, AtomQ, const DParams<R>*);                    \
   template void atom_terms<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned);   \
+  template void bo_correct_atom_terms<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned); \
   template void over_under_bond<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned); \
   template void s_gather<R>(const Launch&, Sys, BondList, AtomQ);                                         \
   template void angles<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned);       \

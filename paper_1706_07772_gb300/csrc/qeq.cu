@@ -1048,17 +1048,20 @@ namespace rx {
 
 template <typename R>
 int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* P, const double* chi,
-              const double* eta, double tol, int max_iter, int warm, const float* qhat, int threads) {
+              const double* eta, double tol, int max_iter, int warm, const float* qhat, int threads,
+              int layout) {
   (void)P;
+  if (layout < 0 || layout >= QEQ_NLAYOUT || (layout > 0 && threads != 1024)) return -1;
+  const QeqLayout& Y = Q.lay[layout];
   CG<R> a;
-  a.n = s.n; a.nrep = s.nrep; a.nchunk = Q.nchunk; a.max_iter = max_iter;
+  a.n = s.n; a.nrep = s.nrep; a.nchunk = Y.nchunk; a.max_iter = max_iter;
   a.tol2 = tol * tol;
   a.type = s.type;
   a.cnt = f.cnt; a.col = f.j; a.H = (const R*)f.H; a.cap = f.cap;
   a.cntn = f.cntn; a.coln = f.jn; a.Hn = (const R*)f.Hn; a.capn = f.capn;
   a.eta = eta; a.chi = chi;
   a.binv = Q.precond == REAXFF_PRECOND_BLOCK32 ? Q.binv : nullptr;
-  a.bj_smem = a.binv ? Q.bj_smem : 0;
+  a.bj_smem = a.binv ? Y.bj_smem : 0;
   a.hist_s = Q.hist_s; a.hist_t = Q.hist_t; a.hst = Q.hst; a.wext = Q.wext; a.pred = Q.pred;
   a.adapt = warm != REAXFF_WARM_LAGRANGE;
   a.warm = (warm == REAXFF_WARM_EXTRAP || warm == REAXFF_WARM_MLP || warm == REAXFF_WARM_LAGRANGE) ? 1 : 0;
@@ -1066,23 +1069,24 @@ int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* 
   a.mlp_used = Q.mlp_used;
   a.zg = Q.zg;
   a.q = s.q; a.qf = s.qf; a.ph = s.ph; a.part = Q.part; a.scal = Q.scal; a.state = Q.state;
-  a.rows_blk = Q.rows_blk; a.scal_smem = Q.scal_smem; a.state_smem = Q.state_smem;
+  a.rows_blk = Y.rows_blk; a.scal_smem = Y.scal_smem; a.state_smem = Y.state_smem;
   a.ring_bytes = Q.ring_bytes;
   a.ieta = Q.ieta;
-  a.chunk_lo = Q.chunk_lo; a.chunk_rep = Q.chunk_rep; a.rep_chunk = Q.rep_chunk;
+  a.chunk_lo = Y.chunk_lo; a.chunk_rep = Y.chunk_rep; a.rep_chunk = Y.rep_chunk;
   a.iters = Q.iters; a.spmv_total = Q.spmv_total; a.bar = Q.bar; a.err = s.err;
   a.bar_limit = Q.bar_limit > 0 ? Q.bar_limit : BAR_CYCLE_LIMIT;
   cudaMemsetAsync(Q.bar, 0, sizeof(GridBar), L.st);
   void* args[] = {&a};
   // 1024 threads per SM, or 512 / 256 (mixed path) to leave registers and shared memory of
-  // each SM to kernels running beside the solve
+  // each SM to kernels running beside the solve; the shapes past the first put 1024-thread
+  // blocks on a part of the SMs instead
   void* fn = (void*)k_cg<R, 1024>;
   int nt = 1024;
   if constexpr (sizeof(R) == 4) {
     if (threads == 512) { fn = (void*)k_cg<R, 512>; nt = 512; }
     else if (threads == 256) { fn = (void*)k_cg<R, 256>; nt = 256; }
   }
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(Q.grid), dim3(nt), args, Q.smem_bytes, L.st);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(Y.grid), dim3(nt), args, Y.smem_bytes, L.st);
   *L.count += 2;
   return e == cudaSuccess ? 0 : -1;
 }
@@ -1116,7 +1120,7 @@ int qeq_grid_size(int nsm) {
 }
 
 template int qeq_solve<double>(const Launch&, Sys, FarList, QeqState&, const DParams<double>*, const double*,
-                               const double*, double, int, int, const float*, int);
+                               const double*, double, int, int, const float*, int, int);
 template int qeq_solve<float>(const Launch&, Sys, FarList, QeqState&, const DParams<float>*, const double*,
-                              const double*, double, int, int, const float*, int);
+                              const double*, double, int, int, const float*, int, int);
 }  // namespace rx

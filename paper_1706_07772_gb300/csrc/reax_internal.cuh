@@ -489,7 +489,8 @@ struct Tune {
   int ang_lanes = 8;           // lanes per centre atom in the angle kernel (4, 8, 16, 32; mixed path)
   int hb_block = 128;          //   H-bonds (warp per hydrogen)
   int qeq_overlap = 0;         // 1 / 2: QEq (CG on 512 / 256 threads per SM) runs beside the
-                               //    charge-free bond-order and bonded kernels (mixed path)
+                               //    charge-free bond-order and bonded kernels (mixed path);
+                               //    3.. : beside them on 1024-thread blocks, shape qeq_overlap - 2
 };
 struct Launch {
   cudaStream_t st;
@@ -527,6 +528,10 @@ void bo_correct(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<R>* P
 template <typename R>
 void atom_terms(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P,
                 unsigned mask);
+// the two above in one kernel (thread i corrects row i, then takes atom i's terms)
+template <typename R>
+void bo_correct_atom_terms(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P,
+                           unsigned mask);
 template <typename R>
 void over_under_bond(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P,
                      unsigned mask);
@@ -574,6 +579,25 @@ constexpr int QEQ_NV_STATE = 14;             // doubles per row of CG state
 constexpr int QEQ_HIST = 8;                  // solutions kept per system for the initial guess
 constexpr int QEQ_NPRED = 3;                 // initial-guess predictors: Lagrange, least squares over 6, over 8
 constexpr int QEQ_SCAL_PER_REP = 24;         // doubles per replica of scalars + reductions
+// One cooperative launch shape of the solve: the grid, the chunks of rows (runs of atoms of
+// one replica; block b owns chunks b, b + grid, ...) and where each block keeps its row state,
+// scalars and block inverses. Shape 0 has one block on every SM (1024, 512 or 256 threads);
+// the others have 1024-thread blocks on a part of the SMs, which leaves the rest of the GPU
+// whole to the kernels running beside the solve.
+struct QeqLayout {
+  int grid;                    // blocks
+  int nchunk;
+  int* chunk_lo;               // first atom of each chunk [nchunk+1]
+  int* chunk_rep;              // replica of each chunk
+  int* rep_chunk;              // first chunk of each replica [nrep+1]
+  int rows_blk;                // most rows one block owns
+  int scal_smem, state_smem;   // 1: held in dynamic shared memory
+  int bj_smem;                 // 1: each block's inverses staged in its shared memory
+  int smem_bytes;              // dynamic shared memory of the launch
+};
+// shapes 1.. : grid = QEQ_PART_NUM[k] / 8 of the SMs
+constexpr int QEQ_NLAYOUT = 4;
+constexpr int QEQ_PART_NUM[QEQ_NLAYOUT] = {8, 4, 3, 5};
 struct QeqState {
   double *hist_s, *hist_t;     // [QEQ_HIST*n] each: solution rings (s, t); the solver writes
                                // each new solution into the oldest slot
@@ -582,22 +606,15 @@ struct QeqState {
   int* hst;                    // device {slot of the newest s, of the newest t, usable entries}
   void* zg;                    // interleaved (s, t) copy of the SpMV operand: float2 or double2
   const double* ieta;          // 1/eta per type
-  double* part;                // chunk partials [2][8][nchunk]
+  double* part;                // chunk partials [2][8][nchunk] (the most chunks of any shape)
   double* scal;                // [grid][nrep*24+4] per-block scalars (when not in shared memory)
   double* state;               // [grid][14][rows_blk] per-block row state (when not in shared memory)
-  int rows_blk;                // most rows one block owns
-  int scal_smem, state_smem;   // 1: held in dynamic shared memory
-  int smem_bytes;              // dynamic shared memory of the launch
-  int ring_bytes;              // of which the SpMV streaming ring (mixed path; first in the layout)
-  int* chunk_rep;              // replica of each chunk
-  int* chunk_lo;               // first atom of each chunk [nchunk+1]
-  int* rep_chunk;              // first chunk of each replica [nrep+1]
-  int nchunk;
+  int ring_bytes;              // SpMV streaming ring (mixed path; first in the shared memory layout)
+  QeqLayout lay[QEQ_NLAYOUT];  // launch shapes
   int* iters;                  // [2*nrep]
   unsigned long long* spmv_total;   // SpMVs of all solves since creation
   int* mlp_used;               // [nrep] learned guess kept in the last solve
   GridBar* bar;
-  int grid;                    // cooperative grid size
   // block-Jacobi preconditioner (REAXFF_PRECOND_BLOCK32): blocks of 32 consecutive atoms of a
   // replica; element (t, m) of the symmetrised FP32 inverse of the block starting at atom b0
   // at binv[32 (b0 + m) + t] (32 (n + 32) floats); null for Jacobi
@@ -606,14 +623,14 @@ struct QeqState {
   int* bj_start;               // [bj_nblk] first atom of each block
   int* bj_size;                // [bj_nblk] atoms in the block (32, fewer at a replica's end)
   int bj_nblk;
-  int bj_smem;                 // 1: each block's inverses staged in its shared memory
   const DParams<float>* Pf;    // FP32 parameters for the block build
   long long bar_limit;         // grid-barrier wait limit in SM cycles (0: BAR_CYCLE_LIMIT)
 };
 // qhat (device, or null): learned charges offered as a second starting guess for s
 template <typename R>
 int qeq_solve(const Launch& L, Sys s, FarList f, QeqState& Q, const DParams<R>* P, const double* chi,
-              const double* eta, double tol, int max_iter, int warm, const float* qhat, int threads = 1024);
+              const double* eta, double tol, int max_iter, int warm, const float* qhat, int threads = 1024,
+              int layout = 0);
 int qeq_grid_size(int nsm);
 int qeq_ring_bytes(bool fp64);   // shared memory of the SpMV streaming ring of a 1024-thread block
 void qeq_precond_build(const Launch& L, Sys s, QeqState& Q);   // block-Jacobi inverses (no-op for Jacobi)

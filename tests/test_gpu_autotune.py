@@ -22,7 +22,7 @@ def test_autotune_schedule_and_cache(params, tmp_path, prec):
     # torsion lanes 1 and angle lanes 4 are candidates of the second, overlapped tuning pass
     assert sch[0] in (1, 2, 4, 8) and sch[1] in (128, 256, 512) and sch[2] in (128, 256, 512)
     assert sch[3] in (128, 256, 512) and sch[4] in (64, 128, 256) and sch[5] in (64, 128, 256)
-    assert sch[6] in (4, 8, 16, 32) and sch[7] in (0, 1, 2)
+    assert sch[6] in (4, 8, 16, 32) and sch[7] in (0, 1, 2, 3, 4, 5)
     F1, E1, _ = c.forces(q=q)
     rms = np.sqrt((F0 ** 2).mean())
     assert np.abs(F1 - F0).max() < (1e-12 if prec == 0 else 1e-6) * rms
@@ -59,9 +59,11 @@ def _system(name):
 @pytest.mark.parametrize("name", ["petn464", "cluster300", "batch3"])
 def test_qeq_beside_terms_matches_serial_order(params, tmp_path, name):
     """The QEq solve on the second stream beside the charge-free terms (schedule entry 7 = 1
-    or 2: 512 or 256 threads per SM) and before them (0) give the same MD trajectory,
+    or 2: 512 or 256 threads on every SM; 3, 4, 5: 1024-thread blocks on 1/2, 3/8, 5/8 of the
+    SMs, with their own chunks of rows) and before them (0) give the same MD trajectory,
     charges, forces and energies to within the solve tolerance (1e-6): the CG dot products'
-    partial sums follow the thread count, so a solve may stop one iteration apart."""
+    partial sums follow the thread count and the chunks, so a solve may stop one iteration
+    apart."""
     import re
 
     import paper_1706_07772_gb300.reaxff as rx
@@ -71,11 +73,11 @@ def test_qeq_beside_terms_matches_serial_order(params, tmp_path, name):
     c.autotune(tmp_path / "tune.txt")
     c.close()
     line = (tmp_path / "tune.txt").read_text().strip()
-    assert re.search(r"qov=[012]$", line)
+    assert re.search(r"qov=[0-5]$", line)
     res = []
-    for qov in (0, 1, 2):
+    for qov in (0, 1, 2, 3, 4, 5):
         f = tmp_path / ("tune%d.txt" % qov)
-        f.write_text(re.sub(r"qov=[012]$", "qov=%d" % qov, line) + "\n")
+        f.write_text(re.sub(r"qov=[0-5]$", "qov=%d" % qov, line) + "\n")
         c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=rx.MIXED, **kw)
         c.set_state(w["x"], w["v"])
         assert c.autotune(f)[7] == qov
@@ -91,3 +93,28 @@ def test_qeq_beside_terms_matches_serial_order(params, tmp_path, name):
         assert np.abs(F1 - F0).max() < 1e-5 * np.sqrt((F0 ** 2).mean())
         assert np.abs(e1 - e0).max() < 1e-7 * np.abs(e0).max()
         assert np.abs(E1 - E0).max() < 1e-7 * np.abs(E0).max()
+
+
+def test_cache_line_out_of_range_is_retuned(params, tmp_path):
+    """A cache line whose entries the tuner could not have picked (a solve shape past the last,
+    a block size of 100) is ignored: the context is tuned again and the new line appended."""
+    import re
+
+    import paper_1706_07772_gb300.reaxff as rx
+    w = synth.workload("petn464")
+    c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=rx.MIXED)
+    c.set_state(w["x"], w["v"])
+    good = tmp_path / "tune.txt"
+    sch = c.autotune(good)
+    line = good.read_text().strip()
+    for bad_line in (re.sub(r"qov=[0-5]$", "qov=9", line), re.sub(r"nb=\d+", "nb=100", line)):
+        f = tmp_path / "bad.txt"
+        f.write_text(bad_line + "\n")
+        s2 = c.autotune(f)
+        assert s2[7] in (0, 1, 2, 3, 4, 5) and s2[1] in (128, 256, 512)
+        lines = f.read_text().strip().splitlines()
+        assert len(lines) == 2 and lines[0] == bad_line
+    F, E, _ = c.forces()
+    assert np.isfinite(F).all()
+    assert len(sch) == 8
+    c.close()

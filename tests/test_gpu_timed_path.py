@@ -3,9 +3,10 @@
 Two configurations are covered. The first is the MD step as the benchmark runs it: mixed
 precision, the adaptive extrapolated QEq start, Verlet-skin candidates, launch schedules
 from the autotuner, the QEq solve on a second stream beside the charge-free terms, and
-the per-step CUDA graph. Its positions, velocities, charges and per-step total energies
-after K steps are compared with the oracle's velocity Verlet (Sec. 4.1: dt = 0.1 fs,
-charges re-equilibrated every step, Sec. 3.3). The second is the batched context (uneven
+the per-step CUDA graph; the solve shares every SM with the terms (512 threads per SM) or
+has half of the SMs to itself (1024-thread blocks). Its positions, velocities, charges and
+per-step total energies after K steps are compared with the oracle's velocity Verlet
+(Sec. 4.1: dt = 0.1 fs, charges re-equilibrated every step, Sec. 3.3). The second is the batched context (uneven
 replicas in one launch per stage), compared per replica with the oracle, for a single
 force call and along the same graph-captured step.
 
@@ -43,9 +44,9 @@ def _overlapped(rx, c, tmp_path, qov=1):
     f = tmp_path / "tune.txt"
     c.autotune(f)
     line = f.read_text().strip().splitlines()[-1]
-    assert re.search(r"qov=[012]$", line)
+    assert re.search(r"qov=[0-5]$", line)
     g = tmp_path / "tune_forced.txt"
-    g.write_text(re.sub(r"qov=[012]$", "qov=%d" % qov, line) + "\n")
+    g.write_text(re.sub(r"qov=[0-5]$", "qov=%d" % qov, line) + "\n")
     sch = c.autotune(g)
     assert sch[7] == qov
     return sch
@@ -62,24 +63,28 @@ def test_timed_step_matches_oracle_trajectory(rx, params, tmp_path, name):
     m = oracle.Model(params, w["types"], w["box"], dict(w["options"], qeq_tol=1e-10))
     x_o, v_o, _, e_o = oracle.verlet(m, w["x"], w["v"], 0.1, K)
     q_o = m.qeq(x_o, m.lists(x_o), tol=1e-10)["q"]
-    c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=rx.MIXED, warm_start=rx.WARM_EXTRAP)
-    c.set_state(w["x"], w["v"])
-    _overlapped(rx, c, tmp_path)
-    e_g = c.step(K, 0.1)[:, 0]
-    x_g, v_g, q_g = c.get_state()
-    assert np.abs(_wrap_diff(x_g, x_o, w["box"])).max() < 1e-6
-    assert np.abs(v_g - v_o).max() < 1e-6
-    assert np.abs(q_g - q_o).max() < MIX_Q
-    assert abs(q_g.sum()) < 1e-9 * len(q_g)
-    assert np.abs(e_g - e_o).max() < MIX_E * abs(e_o[0])
-    # and the forces, energies and virial at the final state (the step's own last evaluation
-    # is what the next kick uses; reaxff_forces recomputes them in the checked order)
     ref = m.forces(x_o, tol=1e-12)
-    F, E, W = c.forces(q=ref["qeq"]["q"])
     rms = np.sqrt((ref["F"] ** 2).mean())
-    assert np.abs(F - ref["F"]).max() / rms < MIX_F
-    assert abs(E[0].sum() - ref["E_total"]) < MIX_E * abs(ref["E_total"])
-    c.close()
+    # the solve beside the terms on 512 threads of every SM (1), and on 1024-thread blocks
+    # on half of the SMs (3)
+    for qov in (1, 3):
+        c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=rx.MIXED, warm_start=rx.WARM_EXTRAP)
+        c.set_state(w["x"], w["v"])
+        _overlapped(rx, c, tmp_path, qov)
+        e_g = c.step(K, 0.1)[:, 0]
+        x_g, v_g, q_g = c.get_state()
+        assert np.abs(_wrap_diff(x_g, x_o, w["box"])).max() < 1e-6, qov
+        assert np.abs(v_g - v_o).max() < 1e-6, qov
+        assert np.abs(q_g - q_o).max() < MIX_Q, qov
+        assert abs(q_g.sum()) < 1e-9 * len(q_g), qov
+        assert np.abs(e_g - e_o).max() < MIX_E * abs(e_o[0]), qov
+        # and the forces, energies and virial at the final state (the step's own last
+        # evaluation is what the next kick uses; reaxff_forces recomputes them in the checked
+        # order)
+        F, E, W = c.forces(q=ref["qeq"]["q"])
+        assert np.abs(F - ref["F"]).max() / rms < MIX_F, qov
+        assert abs(E[0].sum() - ref["E_total"]) < MIX_E * abs(ref["E_total"]), qov
+        c.close()
 
 
 def _batch():
@@ -135,17 +140,20 @@ def test_batched_timed_step_matches_oracle_per_replica(rx, params, tmp_path, bat
     oracle trajectory."""
     reps, types, x, v, off, boxes, ref = batch_ref
     ksteps = 3
-    c = rx.ReaxFF(params, types, boxes, synth.OPTIONS_DEFAULT, precision=rx.MIXED, rep_offsets=off)
-    c.set_state(x, v)
-    _overlapped(rx, c, tmp_path)
-    e_g = c.step(ksteps, 0.1)
-    x_g, v_g, q_g = c.get_state()
+    traj = []
     for r, (m, _) in enumerate(ref):
-        sl = slice(off[r], off[r + 1])
         x_o, v_o, _, e_o = oracle.verlet(m, reps[r]["x"], reps[r]["v"], 0.1, ksteps)
-        assert np.abs(_wrap_diff(x_g[sl], x_o, reps[r]["box"])).max() < 1e-6, r
-        assert np.abs(v_g[sl] - v_o).max() < 1e-6, r
-        assert np.abs(e_g[:, r] - e_o).max() < MIX_E * abs(e_o[0]), r
-        q_o = m.qeq(x_o, m.lists(x_o), tol=1e-10)["q"]
-        assert np.abs(q_g[sl] - q_o).max() < MIX_Q, r
-    c.close()
+        traj.append((x_o, v_o, e_o, m.qeq(x_o, m.lists(x_o), tol=1e-10)["q"]))
+    for qov in (1, 3):
+        c = rx.ReaxFF(params, types, boxes, synth.OPTIONS_DEFAULT, precision=rx.MIXED, rep_offsets=off)
+        c.set_state(x, v)
+        _overlapped(rx, c, tmp_path, qov)
+        e_g = c.step(ksteps, 0.1)
+        x_g, v_g, q_g = c.get_state()
+        for r, (x_o, v_o, e_o, q_o) in enumerate(traj):
+            sl = slice(off[r], off[r + 1])
+            assert np.abs(_wrap_diff(x_g[sl], x_o, reps[r]["box"])).max() < 1e-6, (qov, r)
+            assert np.abs(v_g[sl] - v_o).max() < 1e-6, (qov, r)
+            assert np.abs(e_g[:, r] - e_o).max() < MIX_E * abs(e_o[0]), (qov, r)
+            assert np.abs(q_g[sl] - q_o).max() < MIX_Q, (qov, r)
+        c.close()
