@@ -407,20 +407,26 @@ int reaxff_species_average(reaxff_ctx* ctx, const double* bo_threshold, int32_t*
 
 /* ---- Launch-schedule autotuner ----------------------------------------------------------
  * Times the alternatives of each tunable launch schedule on this context's current data
- * with CUDA events and keeps the fastest: lanes per central bond in the torsion kernel
- * (2, 4, 8), lanes per centre atom in the angle kernel (8, 16, 32; mixed path), threads
- * per block of the nonbonded, candidate-filter, bond-list, angle and H-bond kernels, and
- * (mixed path; whole force evaluations timed) whether the QEq solve runs on a second
- * stream beside the charge-independent bond-order and bonded terms, with a half (1) or a
- * quarter (2) of each SM's threads, instead of before them (0) (the same results to within the rounding of the CG dot
- * products, whose partial sums follow the thread count). With the solve beside the terms,
- * the torsion lanes (1, 2, 4, 8), angle lanes (4, 8, 16, 32), angle, H-bond, nonbonded and
- * bond-list blocks are timed again by whole force evaluations in that schedule. Needs positions; forces are
- * recomputed afterwards (the timing runs accumulate into them). cache_path (or NULL): a
- * text file of "reaxff-tune <key> | ..." lines, the key being (n, replicas, precision,
- * skin, compute capability, SM count); a matching line is used instead of timing, a new
- * result is appended. schedule (int32[8] or NULL) receives (torsion lanes, nonbonded,
- * filter, bond list, angles, H-bonds, angle lanes, QEq beside the terms 0/1/2). */
+ * with CUDA events and keeps the fastest:
+ *  - lanes per central bond in the torsion kernel (2, 4, 8);
+ *  - lanes per centre atom in the angle kernel (8, 16, 32; mixed path);
+ *  - threads per block of the nonbonded, candidate-filter, bond-list, angle and H-bond
+ *    kernels;
+ *  - (mixed path; whole force evaluations timed) where the QEq solve runs. 0: before the
+ *    charge-independent bond-order and bonded terms. On a second stream beside them:
+ *    1 / 2 with a half / a quarter of every SM's threads; 3 / 4 / 5 with 1024-thread blocks
+ *    on 1/2, 3/8 or 5/8 of the SMs. The results agree to within the rounding of the CG dot
+ *    products, whose partial sums follow the thread count and the rows per block.
+ * With the solve beside the terms, the torsion lanes (1, 2, 4, 8), angle lanes (4, 8, 16,
+ * 32), angle, H-bond, nonbonded and bond-list blocks are timed again by whole force
+ * evaluations in that schedule. Needs positions; forces are recomputed afterwards (the
+ * timing runs accumulate into them).
+ * cache_path (or NULL): a text file of "reaxff-tune <key> | ..." lines, the key being (n,
+ * replicas, precision, skin, compute capability, SM count). A matching line whose every entry
+ * is one the tuner can pick is used instead of timing; otherwise the context is tuned and
+ * the result appended.
+ * schedule (int32[8] or NULL) receives (torsion lanes, nonbonded, filter, bond list, angles,
+ * H-bonds, angle lanes, QEq placement 0..5). */
 int reaxff_autotune(reaxff_ctx* ctx, const char* cache_path, int32_t* schedule);
 
 #ifdef __cplusplus
