@@ -615,6 +615,7 @@ int zero_accumulators(reaxff_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->bond.cdbopi, 0, nb * sizeof(unsigned long long), ctx->st));
   CK(cudaMemsetAsync(ctx->bond.cdbopp, 0, nb * sizeof(unsigned long long), ctx->st));
   CK(cudaMemsetAsync(ctx->aq.cddelta, 0, n * sizeof(unsigned long long), ctx->st));
+  CK(cudaMemsetAsync(ctx->aq.A, 0, n * sizeof(unsigned long long), ctx->st));
   CK(cudaMemsetAsync(ctx->acc.e, 0, NTERMS * n * sizeof(double), ctx->st));
   CK(cudaMemsetAsync(ctx->acc.vir, 0, 6 * n * sizeof(double), ctx->st));
   CK(cudaMemsetAsync(ctx->acc.efx, 0, (NTERMS + 6) * n * sizeof(unsigned long long), ctx->st));   // efx and vfx
@@ -955,8 +956,9 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   c.atoms = B.alloc<int>(n); c.atom_cell = B.alloc<int>(n); c.tmp = B.alloc<int>(n);
   AtomQ& a = ctx->aq;
   double** aqf[] = {&a.dp, &a.dpboc, &a.sumbo, &a.delta, &a.dang, &a.nlp, &a.dnlp, &a.dlp, &a.dd,
-                    &a.prodexp, &a.sbo2, &a.dsbo2, &a.sbo_fac, &a.cds, &a.A};
+                    &a.prodexp, &a.sbo2, &a.dsbo2, &a.sbo_fac, &a.cds};
   for (double** p : aqf) *p = B.alloc<double>(n);
+  a.A = B.alloc<unsigned long long>(n);
   a.cddelta = B.alloc<unsigned long long>(n);
   a.sumbo_f = B.alloc<float>(n);
   a.dang_f = B.alloc<float>(n);

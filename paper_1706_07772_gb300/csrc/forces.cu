@@ -12,30 +12,22 @@
 //   dE/dBO'pi    = C_pi G,   dE/dBO'pp = C_pp G        (F = f1 f4 f5, G = f1^2 f4 f5)
 //   A_i          = sum over i's bonds of dE/dDelta'_i
 //   dE/dr_ij     = (dE/dBO' + A_i + A_j) dBO'/dr + dE/dBO'pi dBO'pi/dr + dE/dBO'pp dBO'pp/dr
-// Pass 1 (atom i over its row) forms the per-entry coefficients and A_i; pass 2 (atom i
-// over its row) gathers F_i = sum_j dE/dr_ij (x_j - x_i)/r -- owner computes, no atomics.
+// One thread per unordered bond (the canonical entry e of atom i and its mirror m in atom j's
+// row) in both passes. Everything above except the A_i, A_j terms is symmetric in the two
+// entries (their stored factors are the same values in swapped roles), so it is evaluated
+// once per bond. Pass 1 forms the three coefficients and each entry's dE/dDelta' term, from
+// that entry's own stored factors, and adds the latter to A_i and A_j. Pass 2 turns the
+// coefficients into the pair force, +f on i and -f on j, and the bond's virial. Per-atom sums
+// (A, forces, virial) are 2^-32 fixed-point atomics: exact, so the result does not depend on
+// the order of the canonical list (filled by an atomic append) or of the additions.
 #include "reax_internal.cuh"
 
 namespace {
 
 inline unsigned grid_for(long long threads, int block) { return (unsigned)((threads + block - 1) / block); }
 
-// CHAIN_G lanes per atom (a lane per bond of the row, about four bonds per atom): four times
-// the threads of one per atom, so the dependent loads of the FP64 chain overlap; the lanes'
-// partial sums are combined by fixed-order group butterflies (deterministic)
-constexpr int CHAIN_G = 4;
-__device__ __forceinline__ double group_sum_d(double v) {
-#pragma unroll
-  for (int o = CHAIN_G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-template <typename R>
 __global__ void k_chain1(Sys s, BondList bl, AtomQ aq) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = gt / CHAIN_G, sub = gt & (CHAIN_G - 1);
-  // no early exit: the group sum spans the warp
-  const int nb = i < s.n ? bl.cnt[i] : 0;
+  const int nc = *bl.ncanon;
   const double* BOp = bl.bop;
   const double* BOpi = bl.bopi;
   const double* BOpp = bl.bopp;
@@ -43,75 +35,79 @@ __global__ void k_chain1(Sys s, BondList bl, AtomQ aq) {
   const double* FT = (const double*)bl.ft; const double* DF1 = (const double*)bl.df1;
   const double* DFOB = (const double*)bl.dfo_bo; const double* DFTB = (const double*)bl.dft_bo;
   const double* DFOD = (const double*)bl.dfo_d;
-  const long long cdi = nb > 0 ? (long long)aq.cddelta[i] : 0;
-  double A = 0.0;
-  for (int k = sub; k < nb; k += CHAIN_G) {
-    const int e = i * bl.cap + k;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += gridDim.x * blockDim.x) {
+    const int e = bl.canon[t];
+    const int i = e / bl.cap;
     const int m = bl.mirror[e];
     const int j = bl.j[e];
-    const bool own_lo = (i < j) || (i == j && bl.s[e] > 13);
-    // exact integer sums: identical in both directions
-    const double C = (double)((long long)bl.cdbo[e] + (long long)bl.cdbo[m] + cdi + (long long)aq.cddelta[j]) * FIX_INV;
+    // exact integer sums: the same from either entry
+    const double C = (double)((long long)bl.cdbo[e] + (long long)bl.cdbo[m] + (long long)aq.cddelta[i] +
+                              (long long)aq.cddelta[j]) * FIX_INV;
     const double Cpi = (double)((long long)bl.cdbopi[e] + (long long)bl.cdbopi[m]) * FIX_INV;
     const double Cpp = (double)((long long)bl.cdbopp[e] + (long long)bl.cdbopp[m]) * FIX_INV;
     const double bp = BOp[e], bpi = BOpi[e], bpp = BOpp[e];
-    const double f1 = (double)F1[e], fo = (double)FO[e], ft = (double)FT[e];
-    const double dfo_bo = (double)DFOB[e], dft_bo = (double)DFTB[e];
-    const double flo = own_lo ? fo : ft, fhi = own_lo ? ft : fo;
-    const double dflo = own_lo ? dfo_bo : dft_bo, dfhi = own_lo ? dft_bo : dfo_bo;
+    // e is the canonical (lower) entry: its own factor f4/f5 comes first
+    const double f1 = F1[e], flo = FO[e], fhi = FT[e];
+    const double dflo = DFOB[e], dfhi = DFTB[e];
     const double F = f1 * flo * fhi;
     const double G = f1 * f1 * flo * fhi;
     const double d45 = dflo * fhi + flo * dfhi;
     const double dFdB = f1 * d45, dGdB = f1 * f1 * d45;
     const double piw = Cpi * bpi + Cpp * bpp;
-    bl.dEdBOp[e] = C * (F + bp * dFdB) + piw * dGdB;
-    bl.dEdBOpi[e] = Cpi * G;
-    bl.dEdBOpp[e] = Cpp * G;
-    const double df1 = (double)DF1[e], dfo_d = (double)DFOD[e];
-    const double dFdD = df1 * fo * ft + f1 * dfo_d * ft;
-    const double dGdD = 2.0 * f1 * df1 * fo * ft + f1 * f1 * dfo_d * ft;
-    A += C * bp * dFdD + piw * dGdD;
+    bl.dEdBOp[t] = C * (F + bp * dFdB) + piw * dGdB;
+    bl.dEdBOpi[t] = Cpi * G;
+    bl.dEdBOpp[t] = Cpp * G;
+    // dE/dDelta' of each entry's own atom, from that entry's factors (own f4 first)
+    {
+      const double fo = FO[e], ft = FT[e], df1 = DF1[e], dfo_d = DFOD[e];
+      const double dFdD = df1 * fo * ft + f1 * dfo_d * ft;
+      const double dGdD = 2.0 * f1 * df1 * fo * ft + f1 * f1 * dfo_d * ft;
+      fix_add(aq.A + i, C * bp * dFdD + piw * dGdD, s.err);
+    }
+    {
+      const double f1m = F1[m], fo = FO[m], ft = FT[m], df1 = DF1[m], dfo_d = DFOD[m];
+      const double dFdD = df1 * fo * ft + f1m * dfo_d * ft;
+      const double dGdD = 2.0 * f1m * df1 * fo * ft + f1m * f1m * dfo_d * ft;
+      fix_add(aq.A + j, C * bp * dFdD + piw * dGdD, s.err);
+    }
   }
-  A = group_sum_d(A);
-  if (i < s.n && sub == 0) aq.A[i] = A;
 }
 
+// pass 2: dE/dr of the bond; the pair force f = c d / r (d the entry's image vector) is
+// added to i and subtracted from j, the virial -f d (both entries' halves) to atom i. Mixed
+// path: c in FP64, then the force and virial products in FP32 (the precision of every other
+// mixed-path force term) into the fixed-point sums
 template <typename R>
-__global__ void __maxnreg__(72) k_chain2(Sys s, BondList bl, AtomQ aq, Accum acc) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = gt / CHAIN_G, sub = gt & (CHAIN_G - 1);
-  const int nb = i < s.n ? bl.cnt[i] : 0;
+__global__ void k_chain2(Sys s, BondList bl, AtomQ aq, Accum acc) {
+  const int nc = *bl.ncanon;
   const R* DX = (const R*)bl.dx; const R* DY = (const R*)bl.dy; const R* DZ = (const R*)bl.dz;
   const R* RR = (const R*)bl.r;
   const double* DB = bl.dbop; const double* DBPI = bl.dbopi; const double* DBPP = bl.dbopp;
-  const double Ai = nb > 0 ? aq.A[i] : 0.0;
-  double fx = 0, fy = 0, fz = 0, w[6] = {0, 0, 0, 0, 0, 0};
-  for (int k = sub; k < nb; k += CHAIN_G) {
-    const int e = i * bl.cap + k;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += gridDim.x * blockDim.x) {
+    const int e = bl.canon[t];
+    const int i = e / bl.cap;
     const int j = bl.j[e];
-    const bool own_lo = (i < j) || (i == j && bl.s[e] > 13);
-    const double Aj = aq.A[j];
-    const double Asum = own_lo ? Ai + Aj : Aj + Ai;
-    const double c = (bl.dEdBOp[e] + Asum) * DB[e] + bl.dEdBOpi[e] * DBPI[e] + bl.dEdBOpp[e] * DBPP[e];
-    const double dx = (double)DX[e], dy = (double)DY[e], dz = (double)DZ[e];
-    double cr;
-    if constexpr (sizeof(R) == 4) cr = c * (double)(1.0f / RR[e]);   // FP32 reciprocal: no FP64 division
+    const double Asum = fix_get(aq.A + i) + fix_get(aq.A + j);
+    const double c = (bl.dEdBOp[t] + Asum) * DB[e] + bl.dEdBOpi[t] * DBPI[e] + bl.dEdBOpp[t] * DBPP[e];
+    R cr;
+    if constexpr (sizeof(R) == 4) cr = (float)(c * (double)(1.0f / RR[e]));   // FP32 reciprocal: no FP64 division
     else cr = c / (double)RR[e];
-    fx += cr * dx; fy += cr * dy; fz += cr * dz;
-    const double hc = -0.5 * cr;
-    w[0] += hc * dx * dx; w[1] += hc * dy * dy; w[2] += hc * dz * dz;
-    w[3] += hc * dx * dy; w[4] += hc * dx * dz; w[5] += hc * dy * dz;
-  }
-  fx = group_sum_d(fx);
-  fy = group_sum_d(fy);
-  fz = group_sum_d(fz);
-#pragma unroll
-  for (int q = 0; q < 6; ++q) w[q] = group_sum_d(w[q]);
-  if (i < s.n && sub == 0) {
+    const R dx = DX[e], dy = DY[e], dz = DZ[e];
+    const R fx = cr * dx, fy = cr * dy, fz = cr * dz;
     fix_add(s.fx + i, fx, s.err);
     fix_add(s.fy + i, fy, s.err);
     fix_add(s.fz + i, fz, s.err);
-    for (int q = 0; q < 6; ++q) acc.vir[q * s.n + i] += w[q];
+    fix_add(s.fx + j, -fx, s.err);
+    fix_add(s.fy + j, -fy, s.err);
+    fix_add(s.fz + j, -fz, s.err);
+    unsigned long long* w = acc.vfx + i;
+    const size_t n = s.n;
+    fix_add(w, -fx * dx, s.err);
+    fix_add(w + n, -fy * dy, s.err);
+    fix_add(w + 2 * n, -fz * dz, s.err);
+    fix_add(w + 3 * n, -fx * dy, s.err);
+    fix_add(w + 4 * n, -fx * dz, s.err);
+    fix_add(w + 5 * n, -fy * dz, s.err);
   }
 }
 
@@ -270,8 +266,11 @@ void snapshot(const Launch& L, Sys s, double* hist, int nhist_doubles, int* hst,
   *L.count += 1;
 }
 template <typename R> void chain_rule(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc) {
-  k_chain1<R><<<grid_for((long long)s.n * CHAIN_G, 128), 128, 0, L.st>>>(s, b, a);
-  k_chain2<R><<<grid_for((long long)s.n * CHAIN_G, 128), 128, 0, L.st>>>(s, b, a, acc);
+  // two threads per atom: about one pass over the canonical bonds of molecular systems (the
+  // loops stride over any more)
+  const unsigned grid = grid_for(2LL * s.n, 128);
+  k_chain1<<<grid, 128, 0, L.st>>>(s, b, a);
+  k_chain2<R><<<grid, 128, 0, L.st>>>(s, b, a, acc);
   *L.count += 2;
 }
 template void chain_rule<double>(const Launch&, Sys, BondList, AtomQ, Accum);

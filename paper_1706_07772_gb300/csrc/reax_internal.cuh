@@ -167,7 +167,8 @@ struct AtomQ {                 // per-atom bond-order quantities (double)
   double *dp, *dpboc;          // Delta', Delta'boc
   double *sumbo, *delta, *dang, *nlp, *dnlp, *dlp, *dd;   // dd = Delta - Delta_lp
   double *prodexp, *sbo2, *dsbo2, *sbo_fac;               // sbo_fac = -Delta_ang - p_val8 nlp
-  double *cds, *A;             // dE/dS, chain-rule dE/dDelta'
+  double* cds;                 // dE/dS
+  unsigned long long* A;       // chain-rule dE/dDelta' per atom (fixed point)
   unsigned long long* cddelta; // dE/d(sum BO) accumulator (fixed point)
   float *sumbo_f, *dang_f;     // FP32 copies for the mixed-path angle and torsion kernels
   float *delta_f, *sbo2_f, *dsbo2_f, *prodexp_f, *sbo_fac_f, *dnlp_f;
