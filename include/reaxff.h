@@ -412,10 +412,10 @@ int reaxff_species_average(reaxff_ctx* ctx, const double* bo_threshold, int32_t*
  *  - lanes per centre atom in the angle kernel (8, 16, 32; mixed path);
  *  - threads per block of the nonbonded, candidate-filter, bond-list, angle and H-bond
  *    kernels;
- *  - (mixed path; whole force evaluations timed) where the QEq solve runs. 0: before the
- *    charge-independent bond-order and bonded terms. On a second stream beside them:
- *    1 / 2 with a half / a quarter of every SM's threads; 3 / 4 / 5 with 1024-thread blocks
- *    on 1/2, 3/8 or 5/8 of the SMs. The results agree to within the rounding of the CG dot
+ *  - (mixed path) where the QEq solve runs. 0: before the charge-independent bond-order
+ *    and bonded terms. On a second stream beside them: 1 / 2 with a half / a quarter of every
+ *    SM's threads; 3 / 4 / 5 with 1024-thread blocks on 1/2, 3/8 or 5/8 of the SMs. This entry is timed on MD steps (0.1 fs, from the context's state,
+ *    which is restored afterwards). The results agree to within the rounding of the CG dot
  *    products, whose partial sums follow the thread count and the rows per block.
  * With the solve beside the terms, the torsion lanes (1, 2, 4, 8), angle lanes (4, 8, 16,
  * 32), angle, H-bond, nonbonded and bond-list blocks are timed again by whole force

@@ -525,17 +525,18 @@ int qeq_impl(reaxff_ctx* ctx, bool side = false) {
   return REAXFF_OK;
 }
 
-// Mixed path with the solve beside the charge-free terms. QEq (k_cg on 512 or 256 threads per
-// SM, with a 164 KB shared-memory carveout) and then the nonbonded kernel, the only
-// charge-dependent term, run on the second stream; the bond list and bond orders (when
-// bonds_pending), their corrections, atom terms, angles, torsions, H-bonds and the chain rule
-// run on the main stream meanwhile. Neither side reads what the other writes (the solve writes charges,
-// solutions and its own state; the terms read positions, bond data and write per-atom
-// quantities, bond accumulators and, like the nonbonded kernel, forces, energies and the
-// virial only through exact fixed-point atomics), so nothing races. The results agree with
-// the serial order to within rounding: with fewer threads each CG thread takes several rows,
-// which changes the order of the FP64 dot-product partials. Fork and join by events (graph
-// edges under stream capture).
+// Mixed path with the solve beside the charge-free terms. QEq (k_cg in the schedule's shape)
+// and then the nonbonded kernel, the only charge-dependent term, run on the second stream;
+// the bond list and bond orders (when bonds_pending), their corrections, atom terms, angles,
+// torsions, H-bonds and the chain rule run on the main and third streams meanwhile. Neither
+// side uses what the other writes: the solve writes charges (also into the fourth word of the
+// packed position records, which the bond-list kernel loads with the positions but does not
+// use), solutions and its own state; the terms read positions and bond data, write per-atom
+// quantities and bond accumulators, and add forces, energies and the virial, like the
+// nonbonded kernel, only through exact fixed-point atomics. So nothing races. The results
+// agree with the serial order to within rounding: the CG thread count and rows per block
+// change the order of the FP64 dot-product partials. Fork and join by events (graph edges
+// under stream capture).
 int forces_overlap(reaxff_ctx* ctx, bool bonds_pending) {
   rx::Launch L = launch_of(ctx);
   const DParams<float>* P = ctx->Pf;
@@ -2462,6 +2463,76 @@ template <typename F> float time_launch(reaxff_ctx* ctx, F&& launch) {
   return ms / 8.0f;
 }
 
+// Where the QEq solve runs (schedule entry 7), timed on MD steps through the captured step
+// graph: whole force evaluations rank the close candidates (512 threads on every SM, or
+// 1024-thread blocks on part of the SMs) differently from the steps they are for. Every
+// candidate starts from the same state (positions, velocities, solution history: the
+// rollback snapshot, kept aside), runs 3 warm-up steps of 0.1 fs and three timed windows of
+// 16, and the state is restored after it; each candidate's fastest window decides (the
+// candidates are a few per cent apart, about the spread of single short windows).
+void tune_solve_placement(reaxff_ctx* ctx) {
+  rx::Tune& T = ctx->tune;
+  rx::Launch L = launch_of(ctx);
+  const size_t nd = (6 + 2 * (size_t)rx::QEQ_HIST) * ctx->n;
+  double* keep = nullptr;
+  int* keep_i = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaMalloc(&keep, nd * sizeof(double)) != cudaSuccess || cudaMalloc(&keep_i, 4 * sizeof(int)) != cudaSuccess ||
+      cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    cudaGetLastError();
+    if (keep) cudaFree(keep);
+    if (keep_i) cudaFree(keep_i);
+    if (a) cudaEventDestroy(a);
+    return;                                               // keeps the default placement
+  }
+  const bool had_forces = ctx->forces_valid;
+  rx::snapshot(L, ctx->sys, ctx->Q.hist_s, 2 * rx::QEQ_HIST * ctx->n, ctx->Q.hst, ctx->snap, ctx->snap_i, 0);
+  cudaMemcpyAsync(keep, ctx->snap, nd * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st);
+  cudaMemcpyAsync(keep_i, ctx->snap_i, 4 * sizeof(int), cudaMemcpyDeviceToDevice, ctx->st);
+  auto restore = [&] {
+    cudaMemcpyAsync(ctx->snap, keep, nd * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st);
+    cudaMemcpyAsync(ctx->snap_i, keep_i, 4 * sizeof(int), cudaMemcpyDeviceToDevice, ctx->st);
+    rx::snapshot(L, ctx->sys, ctx->Q.hist_s, 2 * rx::QEQ_HIST * ctx->n, ctx->Q.hst, ctx->snap, ctx->snap_i, 1);
+    cudaMemsetAsync(ctx->sys.img, 0, 3 * (size_t)ctx->n * sizeof(int), ctx->st);
+    cudaMemsetAsync(ctx->sys.rebuild, 1, sizeof(int), ctx->st);
+    ctx->forces_valid = false;
+    ctx->lists_valid = false;
+  };
+  float best = 1e30f;
+  int arg = T.qeq_overlap;
+  for (int c = 0; c < rx::QEQ_PLACEMENTS; ++c) {
+    T.qeq_overlap = c;
+    drop_graph(ctx);
+    float ms = 1e30f;
+    int flags = 0;
+    if (forces_impl(ctx, true) == REAXFF_OK && run_unchecked(ctx, 3, 0.1, nullptr, &flags) == REAXFF_OK && !flags) {
+      for (int w = 0; w < 3; ++w) {
+        cudaEventRecord(a, ctx->st);
+        const int rc = run_unchecked(ctx, 16, 0.1, nullptr, &flags);
+        cudaEventRecord(b, ctx->st);
+        float t = 1e30f;
+        if (rc != REAXFF_OK || flags || cudaEventSynchronize(b) != cudaSuccess ||
+            cudaEventElapsedTime(&t, a, b) != cudaSuccess) {
+          ms = 1e30f;
+          break;
+        }
+        ms = std::min(ms, t / 16.0f);
+      }
+    }
+    cudaGetLastError();
+    restore();
+    if (ms < best) { best = ms; arg = c; }
+  }
+  T.qeq_overlap = arg;
+  drop_graph(ctx);
+  cudaStreamSynchronize(ctx->st);
+  cudaFree(keep);
+  cudaFree(keep_i);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (had_forces && forces_impl(ctx, true) != REAXFF_OK) cudaGetLastError();
+}
+
 template <typename R> void tune_all(reaxff_ctx* ctx) {
   rx::Launch L = launch_of(ctx);
   const DParams<R>* P = params_ptr<R>(ctx);
@@ -2495,13 +2566,13 @@ template <typename R> void tune_all(reaxff_ctx* ctx) {
   // solve instead starts without history and is capped at 8 SpMVs, about those of an MD step
   // (the capped solves' flags are cleared by the checked evaluation that follows tuning)
   if (!ctx->fp64) {
+    tune_solve_placement(ctx);
     const int mi = ctx->ho.qeq_max_iter;
     ctx->ho.qeq_max_iter = 7;
     auto whole = [&] {
       cudaMemsetAsync(ctx->Q.hst + 2, 0, sizeof(int), ctx->st);
       forces_impl(ctx, true, true, false);
     };
-    pick(T.qeq_overlap, {0, 1, 2, 3, 4, 5}, whole);
     if (T.qeq_overlap != 0) {
       // beside the resident solve the charge-free kernels get fewer registers and warps per
       // SM than when timed alone above: their launch shapes are picked again by whole
@@ -2528,7 +2599,7 @@ bool tune_valid(const rx::Tune& t) {
   };
   return in(t.tors_lanes, {1, 2, 4, 8}) && in(t.ang_lanes, {4, 8, 16, 32}) && in(t.nb_block, {128, 256, 512}) &&
          in(t.cf_block, {128, 256, 512}) && in(t.bl_block, {128, 256, 512}) && in(t.ang_block, {64, 128, 256}) &&
-         in(t.hb_block, {64, 128, 256}) && t.qeq_overlap >= 0 && t.qeq_overlap <= 1 + rx::QEQ_NLAYOUT;
+         in(t.hb_block, {64, 128, 256}) && t.qeq_overlap >= 0 && t.qeq_overlap < rx::QEQ_PLACEMENTS;
 }
 
 std::string tune_key(reaxff_ctx* ctx) {

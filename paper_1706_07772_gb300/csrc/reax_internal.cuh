@@ -491,7 +491,8 @@ struct Tune {
   int hb_block = 128;          //   H-bonds (warp per hydrogen)
   int qeq_overlap = 0;         // 1 / 2: QEq (CG on 512 / 256 threads per SM) runs beside the
                                //    charge-free bond-order and bonded kernels (mixed path);
-                               //    3.. : beside them on 1024-thread blocks, shape qeq_overlap - 2
+                               //    3..5: beside them on 1024-thread blocks, launch shape
+                               //    qeq_overlap - 2
 };
 struct Launch {
   cudaStream_t st;
@@ -598,6 +599,7 @@ struct QeqLayout {
 };
 // shapes 1.. : grid = QEQ_PART_NUM[k] / 8 of the SMs
 constexpr int QEQ_NLAYOUT = 4;
+constexpr int QEQ_PLACEMENTS = 2 + QEQ_NLAYOUT;   // schedule entry qeq_overlap: 0 .. QEQ_PLACEMENTS - 1
 constexpr int QEQ_PART_NUM[QEQ_NLAYOUT] = {8, 4, 3, 5};
 struct QeqState {
   double *hist_s, *hist_t;     // [QEQ_HIST*n] each: solution rings (s, t); the solver writes

@@ -17,8 +17,13 @@ def test_autotune_schedule_and_cache(params, tmp_path, prec):
     c.forces()
     _, _, q = c.get_state()
     F0, E0, _ = c.forces(q=q)                       # fixed charges: only the schedule changes
+    x0, v0, _ = c.get_state()
     cache = tmp_path / "tune.txt"
     sch = c.autotune(cache)
+    # the solve's placement is timed on MD steps, each candidate's steps rolled back: the
+    # context's positions and velocities are the ones it had
+    x1, v1, _ = c.get_state()
+    assert np.array_equal(x1, x0) and np.array_equal(v1, v0)
     # torsion lanes 1 and angle lanes 4 are candidates of the second, overlapped tuning pass
     assert sch[0] in (1, 2, 4, 8) and sch[1] in (128, 256, 512) and sch[2] in (128, 256, 512)
     assert sch[3] in (128, 256, 512) and sch[4] in (64, 128, 256) and sch[5] in (64, 128, 256)
