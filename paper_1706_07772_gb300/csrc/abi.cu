@@ -550,10 +550,11 @@ int forces_overlap(reaxff_ctx* ctx, bool bonds_pending) {
   if (sp >= 0) record_on(ctx, ctx->ev_pool[sp + 1], ctx->st2);
   cudaEventRecord(ctx->ev_join, ctx->st2);
   if (bonds_pending) bond_lists_impl(ctx, L);      // the solve reads only the far list
-  rx::bo_correct_atom_terms<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
+  rx::bo_correct<float>(L, ctx->sys, ctx->bond, ctx->aq, P);
+  rx::atom_terms<float>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
   // over/under-coordination with the bond energy, the S gather and the torsions on a third
   // stream beside the angle and H-bond kernels. The angle, torsion and H-bond kernels read
-  // only the corrected bond orders and the atom quantities of the kernel above; the
+  // only the corrected bond orders and the atom quantities of the kernels above; the
   // over/under kernel's own outputs (dE/dS) are read by the S gather after it on the same
   // stream. Everything else they write (forces, energies, the virial, the dE/dBO and dE/dDelta
   // accumulators) is added through exact fixed-point atomics or owner-written per term, so
@@ -577,12 +578,8 @@ int forces_overlap(reaxff_ctx* ctx, bool bonds_pending) {
 template <typename R> void terms_impl(reaxff_ctx* ctx) {
   rx::Launch L = launch_of(ctx);
   const DParams<R>* P = params_of<R>(ctx);
-  if (ctx->prof == 1) {                                   // stage timers: one kernel per stage
-    { Stage st(ctx, 5); rx::bo_correct<R>(L, ctx->sys, ctx->bond, ctx->aq, P); }
-    { Stage st(ctx, 6); rx::atom_terms<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
-  } else {
-    rx::bo_correct_atom_terms<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask);
-  }
+  { Stage st(ctx, 5); rx::bo_correct<R>(L, ctx->sys, ctx->bond, ctx->aq, P); }
+  { Stage st(ctx, 6); rx::atom_terms<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
   { Stage st(ctx, 7); rx::over_under_bond<R>(L, ctx->sys, ctx->bond, ctx->aq, ctx->acc, P, ctx->mask); }
   { Stage st(ctx, 8); rx::s_gather<R>(L, ctx->sys, ctx->bond, ctx->aq); }
   if (sizeof(R) == 4 && ctx->prof != 1) {

@@ -44,24 +44,18 @@ template <typename R> __device__ __forceinline__ R wbit(unsigned mask, int t) {
   return ((mask >> t) & 1u) ? R(1) : R(0);
 }
 
-template <typename R>
-__device__ __forceinline__ void atom_terms_of(int i, const Sys& s, const BondList& bl, const AtomQ& aq,
-                                              const Accum& acc, const DParams<R>* __restrict__ P, unsigned mask);
-
 // ------------------------------------------------------------------ BO correction
 // Evaluated in the path's precision R from FP64 Delta' and BO'; the factors and their
-// partials are stored in FP64 for the chain rule, BO, BO_pi and BO_pp in R. Every entry of
-// row i is corrected by thread i (a bond's two entries by the two atoms' threads, with the
-// same operands in the same order), so with ATOM the thread goes on to atom i's terms, which
-// read only row i's corrected orders: the same values, written and read back by the same
-// thread, as the separate kernel reads.
-template <typename R, bool ATOM = false>
-__global__ void k_bo_correct(Sys s, BondList bl, AtomQ aq, const DParams<R>* __restrict__ P, Accum acc,
-                             unsigned mask) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s.n) return;
-  const int ti = s.type[i];
-  const int nb = bl.cnt[i];
+// partials are stored in FP64 for the chain rule, BO, BO_pi and BO_pp in R. One thread per
+// unordered bond writes both directed entries: the canonical entry e of atom i and its
+// mirror m in atom j's row. f1, F = f1 f4 f5 and G = f1^2 f4 f5 are symmetric; f4/f5 (stored
+// as the entry's own factor fo and the other atom's ft), their BO' derivatives and the
+// Delta' derivatives df1, dfo_d belong to one atom each, so the mirror holds them with the
+// roles swapped. Every value comes from the same operands, in the same order, as an
+// evaluation of that entry alone.
+template <typename R>
+__global__ void k_bo_correct(Sys s, BondList bl, AtomQ aq, const DParams<R>* __restrict__ P) {
+  const int nc = *bl.ncanon;
   const double* BOp = bl.bop;
   const double* BOpi = bl.bopi;
   const double* BOpp = bl.bopp;
@@ -69,19 +63,19 @@ __global__ void k_bo_correct(Sys s, BondList bl, AtomQ aq, const DParams<R>* __r
   double* f1a = (double*)bl.f1; double* foa = (double*)bl.fo; double* fta = (double*)bl.ft;
   double* df1a = (double*)bl.df1; double* dfoba = (double*)bl.dfo_bo; double* dftba = (double*)bl.dft_bo;
   double* dfoda = (double*)bl.dfo_d;
-  const R dpo = (R)aq.dp[i], dpbo = (R)aq.dpboc[i];
-  for (int k = 0; k < nb; ++k) {
-    const int e = i * bl.cap + k;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += gridDim.x * blockDim.x) {
+    const int e = bl.canon[t];
+    const int i = e / bl.cap;
     const int j = bl.j[e];
-    const int tj = s.type[j];
+    const int m = bl.mirror[e];
+    const int ti = s.type[i], tj = s.type[j];
     const int pt = ti * MAXT + tj;
-    const bool own_lo = (i < j) || (i == j && bl.s[e] > 13);
-    const R dpt = (R)aq.dp[j], dptb = (R)aq.dpboc[j];
     const R bp = (R)BOp[e];
-    R f1 = 1, df1 = 0;
+    R f1 = 1, df1i = 0, df1j = 0;
     if (P->ovc[pt] > R(0)) {
-      const R dlo = own_lo ? dpo : dpt, dhi = own_lo ? dpt : dpo;
-      const R vlo = own_lo ? P->val[ti] : P->val[tj], vhi = own_lo ? P->val[tj] : P->val[ti];
+      // i is the lower atom of the bond (canonical entry)
+      const R dlo = (R)aq.dp[i], dhi = (R)aq.dp[j];
+      const R vlo = P->val[ti], vhi = P->val[tj];
       const R e1lo = m_expc(-P->p_boc1 * dlo), e1hi = m_expc(-P->p_boc1 * dhi);
       const R f2 = e1lo + e1hi;
       // f3 = -(1/p_boc2) ln((e^a + e^b)/2), a,b = -p_boc2 D'; as a log-sum-exp so that
@@ -93,32 +87,45 @@ __global__ void k_bo_correct(Sys s, BondList bl, AtomQ aq, const DParams<R>* __r
       const R f3 = -(R(1) / P->p_boc2) * (gm + m_log(R(0.5) * wsum));
       const R dlo_den = vlo + f2 + f3, dhi_den = vhi + f2 + f3;
       f1 = R(0.5) * ((vlo + f2) / dlo_den + (vhi + f2) / dhi_den);
-      const R df2 = -P->p_boc1 * (own_lo ? e1lo : e1hi);
-      const R df3 = (own_lo ? wlo : whi) / wsum;
-      const R dAlo = (f3 * df2 - (vlo + f2) * df3) / (dlo_den * dlo_den);
-      const R dAhi = (f3 * df2 - (vhi + f2) * df3) / (dhi_den * dhi_den);
-      df1 = R(0.5) * (dAlo + dAhi);
+      // df1/dDelta'_i (entry e) and df1/dDelta'_j (entry m)
+      {
+        const R df2 = -P->p_boc1 * e1lo;
+        const R df3 = wlo / wsum;
+        const R dAlo = (f3 * df2 - (vlo + f2) * df3) / (dlo_den * dlo_den);
+        const R dAhi = (f3 * df2 - (vhi + f2) * df3) / (dhi_den * dhi_den);
+        df1i = R(0.5) * (dAlo + dAhi);
+      }
+      {
+        const R df2 = -P->p_boc1 * e1hi;
+        const R df3 = whi / wsum;
+        const R dAlo = (f3 * df2 - (vlo + f2) * df3) / (dlo_den * dlo_den);
+        const R dAhi = (f3 * df2 - (vhi + f2) * df3) / (dhi_den * dhi_den);
+        df1j = R(0.5) * (dAlo + dAhi);
+      }
     }
-    R fo = 1, ft = 1, dfo_bo = 0, dft_bo = 0, dfo_d = 0;
+    // f4 (atom i) and f5 (atom j), their BO' and Delta'boc derivatives
+    R fi = 1, fj = 1, dfi_bo = 0, dfj_bo = 0, dfi_d = 0, dfj_d = 0;
     if (P->v13[pt] > R(0)) {
       const R p3 = P->p_boc3[pt], p4 = P->p_boc4[pt], p5 = P->p_boc5[pt];
-      R sdo, sdt;
-      sig_pair<R>(-p3 * (p4 * bp * bp - dpbo) + p5, fo, sdo);
-      sig_pair<R>(-p3 * (p4 * bp * bp - dptb) + p5, ft, sdt);
-      dfo_bo = R(2) * p3 * p4 * bp * sdo;
-      dft_bo = R(2) * p3 * p4 * bp * sdt;
-      dfo_d = -p3 * sdo;
+      R sdi, sdj;
+      sig_pair<R>(-p3 * (p4 * bp * bp - (R)aq.dpboc[i]) + p5, fi, sdi);
+      sig_pair<R>(-p3 * (p4 * bp * bp - (R)aq.dpboc[j]) + p5, fj, sdj);
+      dfi_bo = R(2) * p3 * p4 * bp * sdi;
+      dfj_bo = R(2) * p3 * p4 * bp * sdj;
+      dfi_d = -p3 * sdi;
+      dfj_d = -p3 * sdj;
     }
-    const double flo = own_lo ? fo : ft, fhi = own_lo ? ft : fo;
+    const double flo = fi, fhi = fj;
     const double F = (double)f1 * flo * fhi;
     const double G = (double)f1 * f1 * flo * fhi;
-    bo[e] = (R)(BOp[e] * F);
-    bo_pi[e] = (R)(BOpi[e] * G);
-    bo_pp[e] = (R)(BOpp[e] * G);
-    f1a[e] = f1; foa[e] = fo; fta[e] = ft; df1a[e] = df1;
-    dfoba[e] = dfo_bo; dftba[e] = dft_bo; dfoda[e] = dfo_d;
+    const R b = (R)(BOp[e] * F), bpi = (R)(BOpi[e] * G), bpp = (R)(BOpp[e] * G);
+    bo[e] = b; bo_pi[e] = bpi; bo_pp[e] = bpp;
+    bo[m] = b; bo_pi[m] = bpi; bo_pp[m] = bpp;
+    f1a[e] = f1; foa[e] = fi; fta[e] = fj; df1a[e] = df1i;
+    dfoba[e] = dfi_bo; dftba[e] = dfj_bo; dfoda[e] = dfi_d;
+    f1a[m] = f1; foa[m] = fj; fta[m] = fi; df1a[m] = df1j;
+    dfoba[m] = dfj_bo; dftba[m] = dfi_bo; dfoda[m] = dfj_d;
   }
-  if constexpr (ATOM) atom_terms_of<R>(i, s, bl, aq, acc, P, mask);
 }
 
 // ------------------------------------------------------------------ atom terms + lone pair
@@ -127,12 +134,6 @@ __global__ void k_atom_terms(Sys s, BondList bl, AtomQ aq, Accum acc, const DPar
                              unsigned mask) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
-  atom_terms_of<R>(i, s, bl, aq, acc, P, mask);
-}
-
-template <typename R>
-__device__ __forceinline__ void atom_terms_of(int i, const Sys& s, const BondList& bl, const AtomQ& aq,
-                                              const Accum& acc, const DParams<R>* __restrict__ P, unsigned mask) {
   const int ti = s.type[i];
   const int nb = bl.cnt[i];
   const R* bo = (const R*)bl.bo;
@@ -1182,13 +1183,9 @@ __global__ void k_hbonds(Sys s, BondList bl, HbList hl, Accum acc, const DParams
 namespace rx {
 
 template <typename R> void bo_correct(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<R>* P) {
-  k_bo_correct<R, false><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a, P, Accum{}, 0u);
-  *L.count += 1;
-}
-template <typename R>
-void bo_correct_atom_terms(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P,
-                           unsigned mask) {
-  k_bo_correct<R, true><<<grid_for(s.n, 128), 128, 0, L.st>>>(s, b, a, P, acc, mask);
+  // two threads per atom: about one pass over the canonical bonds of molecular systems (the
+  // loop strides over any more)
+  k_bo_correct<R><<<grid_for(2LL * s.n, 128), 128, 0, L.st>>>(s, b, a, P);
   *L.count += 1;
 }
 template <typename R>
@@ -1248,7 +1245,6 @@ void hbonds(const Launch& L, Sys s, BondList b, HbList h, Accum acc, const DPara
 #define INST(R)                                                                                           \
   template void bo_correct<R>(const Launch&, Sys, BondList, AtomQ, const DParams<R>*);                    \
   template void atom_terms<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned);   \
-  template void bo_correct_atom_terms<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned); \
   template void over_under_bond<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned); \
   template void s_gather<R>(const Launch&, Sys, BondList, AtomQ);                                         \
   template void angles<R>(const Launch&, Sys, BondList, AtomQ, Accum, const DParams<R>*, unsigned);       \

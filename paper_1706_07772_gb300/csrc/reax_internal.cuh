@@ -530,10 +530,6 @@ void bo_correct(const Launch& L, Sys s, BondList b, AtomQ a, const DParams<R>* P
 template <typename R>
 void atom_terms(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P,
                 unsigned mask);
-// the two above in one kernel (thread i corrects row i, then takes atom i's terms)
-template <typename R>
-void bo_correct_atom_terms(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P,
-                           unsigned mask);
 template <typename R>
 void over_under_bond(const Launch& L, Sys s, BondList b, AtomQ a, Accum acc, const DParams<R>* P,
                      unsigned mask);
