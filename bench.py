@@ -3,7 +3,7 @@
 Default (no flags): 1 GPU, the mixed-precision path (FP32 interaction math, FP64 sums)
 with the extrapolated QEq warm start at QEq tolerance 1e-6, dt = 0.1 fs, QEq solved every
 step; the neighbour lists come from a Verlet-skin candidate list (rebuilt once an atom has
-moved more than half the 1 A skin) filtered to the exact cutoffs every step. One JSON line
+moved more than half the 0.7 A skin) filtered to the exact cutoffs every step. One JSON line
 on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -296,7 +296,7 @@ def run_ours(a, rank, world):
         "config": {"workload": a.workload, "atoms": n, "atoms_per_gpu": n, "precision": a.precision,
                    "warm_start": "extrapolated", "qeq_tol": w["options"]["qeq_tol"], "qeq_precond": a.qeq_precond,
                    "dt_fs": a.dt,
-                   "lists": "Verlet-skin candidates (1 A skin, rebuilt on displacement > skin/2), exact cutoff filter every step",
+                   "lists": "Verlet-skin candidates (0.7 A skin, rebuilt on displacement > skin/2), exact cutoff filter every step",
                    "l2": "flushed (256 MB write) before each library call of %d steps; each step streams > 200 MB of lists" % CALL_STEPS,
                    "parallelism": "independent system per GPU" if world > 1 else "single GPU",
                    "schedule": dict(zip(("torsion_lanes", "nonbonded_block", "filter_block", "bond_list_block",

@@ -137,7 +137,7 @@ typedef struct {
   double capacity_margin; /* list capacity headroom factor (>= 1; 0 = default 1.35) */
   double skin;        /* Verlet skin (A) of the neighbour candidate list, rebuilt on the device
                          only when an atom has moved more than skin/2; the far list is still
-                         filtered exactly (r < r_nb) every step. 0 = default 1.0 A,
+                         filtered exactly (r < r_nb) every step. 0 = default 0.7 A,
                          negative = no candidate list (cell stencil every step). A system
                          with a box edge <= r_nb + skin runs the cell stencil instead. */
   int32_t qeq_precond; /* REAXFF_PRECOND_* (0 = Jacobi) */

@@ -96,7 +96,7 @@ struct reaxff_ctx {
   int cap_far = 0, cap_bond = 0, cap_hb = 0, cap_near = 0, cap_cand = 0;
   float near_margin = 0.f, hb_margin = 0.f;
   bool use_skin = true;
-  double skin = 1.0;
+  double skin = 0.7;
   CandList cand{};
   // MD steps without host synchronisation: one CUDA graph per step (captured on first use,
   // dropped when the list buffers, dt or the profiling switch change), flags checked once
@@ -886,7 +886,10 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   const double sph = 4.0 / 3.0 * M_PI;
   ctx->cap_far = std::max(64, round_up(margin * sph * (std::pow(options->r_nb, 3) - std::pow(options->r_bond, 3)) * rho + 16, 32));
   ctx->cap_near = std::max(32, round_up(margin * sph * std::pow(options->r_bond, 3) * rho + 16, 32));
-  ctx->skin = options->skin > 0.0 ? options->skin : 1.0;
+  // default 0.7 A: against 1.0 A, 8 % fewer candidates for the per-step filter outweigh
+  // the more frequent rebuilds (petn32k 0.854 -> 0.844 ms per step, 1,039,360 atoms 22.0 ->
+  // 21.8 ms, steady-state windows)
+  ctx->skin = options->skin > 0.0 ? options->skin : 0.7;
   // candidates need every box edge above r_nb + skin (images beyond the nearest shifts stay
   // out of reach between rebuilds); smaller boxes run the cell stencil every step
   ctx->use_skin = !(options->skin < 0.0);

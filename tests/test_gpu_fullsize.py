@@ -57,7 +57,7 @@ def keyset(i, j, s, n):
 
 def bench_ctx(rx, params, w, prec, **kw):
     """A context as the benchmark makes it (extrapolated warm start, Jacobi QEq, default
-    1 A skin, autotuned schedules)."""
+    0.7 A skin, autotuned schedules)."""
     c = rx.ReaxFF(params, w["types"], w["box"], w["options"], precision=prec, warm_start=rx.WARM_EXTRAP,
                   qeq_precond=rx.PRECOND_JACOBI, **kw)
     c.set_state(w["x"], w["v"])
