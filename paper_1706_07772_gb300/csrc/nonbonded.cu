@@ -160,7 +160,8 @@ __device__ __forceinline__ void nb_pair_far(const Sys& s, const FarAtom& a, cons
 }
 
 template <typename R>
-__global__ void k_nonbonded(Sys s, FarList f, Accum acc, const DParams<R>* __restrict__ P, unsigned mask) {
+__device__ __forceinline__ void nonbonded_atom(const Sys& s, const FarList& f, const Accum& acc,
+                                               const DParams<R>* __restrict__ P, unsigned mask) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   // mixed path: image signs per shift code and the far-pair constants, staged once per block
@@ -254,13 +255,25 @@ __global__ void k_nonbonded(Sys s, FarList f, Accum acc, const DParams<R>* __res
   }
 }
 
+// the FP32 form capped at 64 registers (72 uncapped; 12 bytes of spills): 32 warps per SM
+// instead of 28 for this latency-bound kernel (petn32k 0.152 -> 0.147 ms); the FP64 form
+// keeps its 126 registers
+__global__ void __maxnreg__(64) k_nonbonded_f(Sys s, FarList f, Accum acc, const DParams<float>* __restrict__ P,
+                                             unsigned mask) {
+  nonbonded_atom<float>(s, f, acc, P, mask);
+}
+__global__ void k_nonbonded_d(Sys s, FarList f, Accum acc, const DParams<double>* __restrict__ P, unsigned mask) {
+  nonbonded_atom<double>(s, f, acc, P, mask);
+}
+
 }  // namespace
 
 namespace rx {
 template <typename R>
 void nonbonded(const Launch& L, Sys s, FarList f, Accum acc, const DParams<R>* P, unsigned mask) {
   const int bs = L.t().nb_block;
-  k_nonbonded<R><<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, f, acc, P, mask);
+  if constexpr (sizeof(R) == 4) k_nonbonded_f<<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, f, acc, P, mask);
+  else k_nonbonded_d<<<grid_for((long long)s.n * 32, bs), bs, 0, L.st>>>(s, f, acc, P, mask);
   *L.count += 1;
 }
 template void nonbonded<double>(const Launch&, Sys, FarList, Accum, const DParams<double>*, unsigned);
