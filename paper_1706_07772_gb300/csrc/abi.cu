@@ -953,6 +953,9 @@ int reaxff_create_batch(const reaxff_params* params, int32_t nrep, const int64_t
   int* nc_d = B.alloc<int>(3 * nrep);
   int* coff_d = B.alloc<int>(nrep + 1);
   c.nc = nc_d; c.cell_off = coff_d; c.ncell_total = ncell;
+  // candidate build: about four blocks per SM at least, each home cell's atoms shared by
+  // this many blocks
+  c.slices = std::max(1, std::min(16, (4 * ctx->nsm + ncell - 1) / std::max(ncell, 1)));
   c.count = B.alloc<int>(ncell); c.start = B.alloc<int>(ncell + 1); c.cursor = B.alloc<int>(ncell);
   c.atoms = B.alloc<int>(n); c.atom_cell = B.alloc<int>(n); c.tmp = B.alloc<int>(n);
   AtomQ& a = ctx->aq;

@@ -483,59 +483,102 @@ __global__ void k_skin_check(Sys s, CandList cl) {
 }
 
 // candidate rows: every (j, image) within r_nb + skin (FP32 with a margin: a superset),
-// built from the cell stencil; resets the atom's reference position and crossings
-__global__ void k_cand_build(Sys s, Cells c, CandList cl) {
+// built from the cell stencil; resets the atom's reference position and crossings.
+// c.slices blocks per home cell, each taking a contiguous share of its atoms (several when
+// the system has few cells, so that the grid fills the GPU): each of the 27 stencil cells is
+// staged in shared memory once per block (FP32 positions and atom ids, CB_STAGE atoms per
+// pass) and scanned by the block's home atoms, warp per home atom, 32 candidates per ballot. A row lists its candidates in the same order as a
+// scan of the stencil atom by atom would (stencil cells in order, each cell's atoms in cell
+// order), so the rows do not depend on this blocking; the staging replaces a gather of
+// three coordinates per candidate and home atom by one per candidate and home cell.
+constexpr int CB_THREADS = 256;
+constexpr int CB_STAGE = 512;                 // stencil-cell atoms per staging pass
+constexpr int CB_HOME = 256;                  // home atoms per pass (their row counts in shared memory)
+__global__ void __launch_bounds__(CB_THREADS) k_cand_build(Sys s, Cells c, CandList cl) {
   if (*s.rebuild == 0) return;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= s.n) return;
-  const int i = warp;
-  const int r = s.rep[i];
+  const int cell = blockIdx.x / c.slices, slice = blockIdx.x % c.slices;
+  const int ca = c.start[cell], cb = c.start[cell + 1];
+  const int a = ca + (int)((long long)(cb - ca) * slice / c.slices);
+  const int b = ca + (int)((long long)(cb - ca) * (slice + 1) / c.slices);
+  if (a >= b) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = CB_THREADS / 32;
+  __shared__ float sx[CB_STAGE], sy[CB_STAGE], sz[CB_STAGE];
+  __shared__ int sj[CB_STAGE];
+  __shared__ int scnt[CB_HOME];
+  const int r = s.rep[c.atoms[a]];
   const int* nc = c.nc + 3 * r;
   const float* Lh = s.boxh + 3 * r;
-  int cell = c.atom_cell[i] - c.cell_off[r];
-  int ci[3] = {cell % nc[0], (cell / nc[0]) % nc[1], cell / (nc[0] * nc[1])};
-  const float xi = s.xh[i], yi = s.yh[i], zi = s.zh[i];
-  int count = 0;
-  const int row = i * cl.cap;
-  for (int o = 0; o < 27; ++o) {
-    int oc[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
-    int t[3], sh[3];
-    for (int d = 0; d < 3; ++d) {
-      int v = ci[d] + oc[d];
-      sh[d] = v < 0 ? -1 : (v >= nc[d] ? 1 : 0);
-      t[d] = v - sh[d] * nc[d];
-    }
-    const int code = (sh[0] + 1) * 9 + (sh[1] + 1) * 3 + (sh[2] + 1);
-    const int cid = c.cell_off[r] + (t[2] * nc[1] + t[1]) * nc[0] + t[0];
-    const int a = c.start[cid], b = c.start[cid + 1];
-    const float ox = sh[0] * Lh[0], oy = sh[1] * Lh[1], oz = sh[2] * Lh[2];
-    for (int base = a; base < b; base += 32) {
-      const int k = base + lane;
-      bool ok = false;
-      int j = -1;
-      if (k < b) {
-        j = c.atoms[k];
-        const float dx = (s.xh[j] - xi) + ox, dy = (s.yh[j] - yi) + oy, dz = (s.zh[j] - zi) + oz;
-        ok = !(j == i && code == 13) && dx * dx + dy * dy + dz * dz < cl.rc2;
+  const int lc = cell - c.cell_off[r];
+  const int ci[3] = {lc % nc[0], (lc / nc[0]) % nc[1], lc / (nc[0] * nc[1])};
+  for (int h0 = a; h0 < b; h0 += CB_HOME) {
+    const int h1 = min(b, h0 + CB_HOME);
+    for (int t = threadIdx.x; t < h1 - h0; t += CB_THREADS) scnt[t] = 0;
+    for (int o = 0; o < 27; ++o) {
+      const int oc[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+      int t3[3], sh[3];
+      for (int d = 0; d < 3; ++d) {
+        const int v = ci[d] + oc[d];
+        sh[d] = v < 0 ? -1 : (v >= nc[d] ? 1 : 0);
+        t3[d] = v - sh[d] * nc[d];
       }
-      const unsigned m = __ballot_sync(0xffffffffu, ok);
-      const int pos = count + __popc(m & ((1u << lane) - 1u));
-      if (ok && pos < cl.cap) {
-        cl.j[row + pos] = j;
-        cl.s[row + pos] = (uint8_t)code;
+      const int code = (sh[0] + 1) * 9 + (sh[1] + 1) * 3 + (sh[2] + 1);
+      const int cid = c.cell_off[r] + (t3[2] * nc[1] + t3[1]) * nc[0] + t3[0];
+      const int na = c.start[cid], nb = c.start[cid + 1];
+      const float ox = sh[0] * Lh[0], oy = sh[1] * Lh[1], oz = sh[2] * Lh[2];
+      for (int p0 = na; p0 < nb; p0 += CB_STAGE) {
+        const int np = min(CB_STAGE, nb - p0);
+        __syncthreads();                          // the previous pass's readers are done
+        for (int t = threadIdx.x; t < np; t += CB_THREADS) {
+          const int j = c.atoms[p0 + t];
+          sj[t] = j;
+          sx[t] = s.xh[j];
+          sy[t] = s.yh[j];
+          sz[t] = s.zh[j];
+        }
+        __syncthreads();
+        for (int h = h0 + warp; h < h1; h += nw) {
+          const int i = c.atoms[h];
+          const float xi = s.xh[i], yi = s.yh[i], zi = s.zh[i];
+          const int row = i * cl.cap;
+          int count = scnt[h - h0];                // this warp alone owns home atom h
+          for (int base = 0; base < np; base += 32) {
+            const int k = base + lane;
+            bool ok = false;
+            int j = -1;
+            if (k < np) {
+              j = sj[k];
+              const float dx = (sx[k] - xi) + ox, dy = (sy[k] - yi) + oy, dz = (sz[k] - zi) + oz;
+              ok = !(j == i && code == 13) && dx * dx + dy * dy + dz * dz < cl.rc2;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            const int pos = count + __popc(m & ((1u << lane) - 1u));
+            if (ok && pos < cl.cap) {
+              cl.j[row + pos] = j;
+              cl.s[row + pos] = (uint8_t)code;
+            }
+            count += __popc(m);
+          }
+          __syncwarp();
+          if (lane == 0) scnt[h - h0] = count;
+          __syncwarp();
+        }
       }
-      count += __popc(m);
     }
-  }
-  if (lane == 0) {
-    cl.cnt[i] = count < cl.cap ? count : cl.cap;
-    if (count > cl.cap) atomicOr(s.err, ERR_CAP_CAND);
-  }
-  if (lane < 3) {
-    s.xb[3 * i + lane] = lane == 0 ? s.x[i] : (lane == 1 ? s.y[i] : s.z[i]);
-    s.img[3 * i + lane] = 0;
-    if (lane == 0 && s.pl) ((float*)(s.pl + i))[3] = pack_type_img(s.type[i], 0, 0, 0);
+    __syncthreads();
+    for (int h = h0 + warp; h < h1; h += nw) {
+      const int i = c.atoms[h];
+      const int count = scnt[h - h0];
+      if (lane == 0) {
+        cl.cnt[i] = count < cl.cap ? count : cl.cap;
+        if (count > cl.cap) atomicOr(s.err, ERR_CAP_CAND);
+      }
+      if (lane < 3) {
+        s.xb[3 * i + lane] = lane == 0 ? s.x[i] : (lane == 1 ? s.y[i] : s.z[i]);
+        s.img[3 * i + lane] = 0;
+        if (lane == 0 && s.pl) ((float*)(s.pl + i))[3] = pack_type_img(s.type[i], 0, 0, 0);
+      }
+    }
+    __syncthreads();                              // scnt is reused by the next home pass
   }
 }
 
@@ -821,7 +864,7 @@ void cand_build(const Launch& L, Sys s, Cells c, CandList cl) {
   k_cell_scan<true><<<1, 1024, 0, L.st>>>(c, s.rebuild);
   k_cell_scatter<true><<<grid_for(s.n, 256), 256, 0, L.st>>>(s, c, c.tmp);
   k_cell_sort<true><<<c.ncell_total, 128, 0, L.st>>>(c, c.tmp, s.rebuild);
-  k_cand_build<<<grid_for((long long)s.n * 32, 256), 256, 0, L.st>>>(s, c, cl);
+  k_cand_build<<<c.ncell_total * c.slices, CB_THREADS, 0, L.st>>>(s, c, cl);
   *L.count += 5;
 }
 

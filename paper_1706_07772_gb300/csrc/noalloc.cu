@@ -199,6 +199,7 @@ extern "C" int reaxff_far_list_noalloc(const reaxff_params* params, const reaxff
   c.atom_cell = I(1);
   c.atoms = I(2);
   c.tmp = I(3);
+  c.slices = 1;
   FarList f{};
   f.cap = cap;
   f.cnt = cnt_dev;

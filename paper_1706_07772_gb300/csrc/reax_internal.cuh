@@ -118,6 +118,7 @@ struct Cells {
   int* atoms;                  // [n] atoms sorted by cell
   int* atom_cell;              // [n]
   int* tmp;                    // [n] scatter scratch
+  int slices;                  // blocks per home cell in the candidate build (>= 1)
 };
 
 // Far list. Context path: every row is split into a near part (r < r_bond, the bond
