@@ -309,8 +309,9 @@ int reaxff_step_dev(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot
  * row had more than cap neighbours (that row is truncated). params/options and box are
  * host pointers. Work is enqueued on `stream`; the call waits for it to finish.
  * *err_msg (if not NULL) receives a static description of any error.
- * The first call on each device looks up the scratch array's device address (once per
- * device, with that device current); make that first call before any stream capture.
+ * No call can be captured into a CUDA graph: each one reads its error flags back to the
+ * host and waits for the stream. The first call on each device also looks up the scratch
+ * array's device address (once per device, with that device current).
  * The address is kept for the life of the process, so the entry point must not be used
  * on a device after cudaDeviceReset (a new context would not hold that address).
  * All calls share the one scratch array and each call clears what must start at zero;
