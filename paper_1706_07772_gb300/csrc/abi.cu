@@ -2448,14 +2448,15 @@ template <typename R> const DParams<R>* params_ptr(reaxff_ctx* ctx);
 template <> const DParams<double>* params_ptr<double>(reaxff_ctx* ctx) { return ctx->Pd; }
 template <> const DParams<float>* params_ptr<float>(reaxff_ctx* ctx) { return ctx->Pf; }
 
-// mean device time (ms) of `launch` over 8 runs after 2 warm-up runs; +inf if it fails
-template <typename F> float time_launch(reaxff_ctx* ctx, F&& launch) {
+// mean device time (ms) of `launch` over `runs` runs after `warm` warm-up runs; +inf if it
+// fails
+template <typename F> float time_launch(reaxff_ctx* ctx, F&& launch, int warm = 2, int runs = 8) {
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess) return 1e30f;
   if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return 1e30f; }
-  for (int k = 0; k < 2; ++k) launch();
+  for (int k = 0; k < warm; ++k) launch();
   cudaEventRecord(a, ctx->st);
-  for (int k = 0; k < 8; ++k) launch();
+  for (int k = 0; k < runs; ++k) launch();
   cudaEventRecord(b, ctx->st);
   float ms = 1e30f;
   if (cudaEventSynchronize(b) == cudaSuccess && cudaGetLastError() == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
@@ -2463,7 +2464,7 @@ template <typename F> float time_launch(reaxff_ctx* ctx, F&& launch) {
   cudaGetLastError();
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  return ms / 8.0f;
+  return ms / (float)runs;
 }
 
 // Where the QEq solve runs (schedule entry 7), timed on MD steps through the captured step
@@ -2585,12 +2586,28 @@ template <typename R> void tune_all(reaxff_ctx* ctx) {
       // beside the resident solve the charge-free kernels get fewer registers and warps per
       // SM than when timed alone above: their launch shapes are picked again by whole
       // overlapped force evaluations
-      pick(T.tors_lanes, {1, 2, 4, 8}, whole);
-      pick(T.ang_lanes, {4, 8, 16, 32}, whole);
-      pick(T.ang_block, {64, 128, 256}, whole);
-      pick(T.hb_block, {64, 128, 256}, whole);
-      pick(T.nb_block, {128, 256, 512}, whole);
-      pick(T.bl_block, {128, 256, 512}, whole);
+      // the candidates of each entry interleaved over 4 rounds (a warm-up and 3 timed
+      // evaluations each) and each candidate's fastest round counted, so that a drift of
+      // the GPU's state during the pass favours no candidate by its place in the order
+      auto pick_rounds = [&](int& knob, std::initializer_list<int> cands) {
+        const std::vector<int> cs(cands);
+        std::vector<float> best(cs.size(), 1e30f);
+        for (int round = 0; round < 4; ++round)
+          for (size_t c = 0; c < cs.size(); ++c) {
+            knob = cs[c];
+            best[c] = std::min(best[c], time_launch(ctx, whole, 1, 3));
+          }
+        size_t arg = 0;
+        for (size_t c = 1; c < cs.size(); ++c)
+          if (best[c] < best[arg]) arg = c;
+        knob = cs[arg];
+      };
+      pick_rounds(T.tors_lanes, {1, 2, 4, 8});
+      pick_rounds(T.ang_lanes, {4, 8, 16, 32});
+      pick_rounds(T.ang_block, {64, 128, 256});
+      pick_rounds(T.hb_block, {64, 128, 256});
+      pick_rounds(T.nb_block, {128, 256, 512});
+      pick_rounds(T.bl_block, {128, 256, 512});
     }
     ctx->ho.qeq_max_iter = mi;
     cudaMemsetAsync(ctx->Q.hst + 2, 0, sizeof(int), ctx->st);
