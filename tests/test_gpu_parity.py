@@ -305,6 +305,26 @@ def test_lists_stay_exact_along_md(rx, params, skin):
     c.close()
 
 
+def test_candidate_build_with_crowded_cells(rx, params):
+    """A dense 4,200-atom cluster in a 21 A box has one candidate cell holding every atom. The
+    candidate build then stages each stencil cell in several shared-memory passes (more than
+    512 atoms) and gives each block more home atoms than one pass takes (more than 256 with
+    16 blocks per cell). The far list it yields must be the one the cell stencil builds
+    without candidates (skin < 0), as a set of (i, j, image) entries."""
+    n, L = 4200, 21.0
+    t, x, box = synth.random_cluster(n, (L, L, L), seed=7)
+    o = dict(synth.OPTIONS_DEFAULT)
+    got = []
+    for skin in (0.7, -1.0):
+        c = rx.ReaxFF(params, t, box, o, precision=1, skin=skin, term_mask=rx.NO_TERMS)
+        c.set_state(x)
+        c.build_lists()
+        got.append(keyset(*c.get_lists(rx.LIST_FAR), n))
+        c.close()
+    assert len(got[0]) > 1500 * n
+    assert np.array_equal(got[0], got[1])
+
+
 def test_candidates_cover_pairs_two_cells_apart(rx, params):
     """Two atoms 10.6 A apart across two cell boundaries of a 10.5 A grid (box 31.5 A)
     fly towards each other by 0.35 A each (below the skin/2 rebuild trigger): the
