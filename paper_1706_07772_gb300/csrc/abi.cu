@@ -78,6 +78,7 @@ struct reaxff_ctx {
   rx::QeqState Q{};
   rx::RedPlan red{};
   double *F_out = nullptr, *E_rep = nullptr, *vir_rep = nullptr, *ke_rep = nullptr, *Etot_dev = nullptr;
+  double* h_etot = nullptr;    // pinned copy of Etot_dev for reaxff_step
   int Etot_cap = 0;
   double *chi_t = nullptr, *eta_t = nullptr, *mass_t = nullptr;
   int* h_err_pinned = nullptr;
@@ -1202,6 +1203,7 @@ void reaxff_destroy(reaxff_ctx* ctx) {
   if (ctx->sp.h_changed) cudaFreeHost(ctx->sp.h_changed);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->Etot_dev) cudaFree(ctx->Etot_dev);
+  if (ctx->h_etot) cudaFreeHost(ctx->h_etot);
   ctx->lists.free_all();
   ctx->fixed.free_all();
   if (ctx->h_err_pinned) cudaFreeHost(ctx->h_err_pinned);
@@ -1247,6 +1249,14 @@ __global__ void k_state_in(const double* __restrict__ x, const double* __restric
     if (cmp && __double_as_longlong(p) != __double_as_longlong(cur[d][i])) f |= 2;
   }
   if (f) atomicOr(flag, f);
+}
+// staged rows (x, y, z, vx, vy, vz, n each) into the state
+__global__ void k_state_commit(Sys s, const double* __restrict__ stage) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const size_t n = (size_t)s.n;
+  s.x[i] = stage[i]; s.y[i] = stage[n + i]; s.z[i] = stage[2 * n + i];
+  s.vx[i] = stage[3 * n + i]; s.vy[i] = stage[4 * n + i]; s.vz[i] = stage[5 * n + i];
 }
 // SoA state -> interleaved rows: x[3n], v[3n], q[n] at out, out + 3n, out + 6n
 __global__ void k_state_out(Sys s, int want_x, int want_v, int want_q, double* __restrict__ out) {
@@ -1294,9 +1304,8 @@ static int set_state_device_io(reaxff_ctx* ctx, const double* x, const double* v
   // positions bit for bit those the device holds: forces, lists, candidates and image
   // counters stay valid (the copies below rewrite the same values)
   const bool same = ctx->have_pos && !(flags & 2);
-  double* dst[6] = {ctx->sys.x, ctx->sys.y, ctx->sys.z, ctx->sys.vx, ctx->sys.vy, ctx->sys.vz};
-  for (int k = 0; k < 6; ++k)
-    CK(cudaMemcpyAsync(dst[k], stage + k * (size_t)n, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  k_state_commit<<<(n + 255) / 256, 256, 0, ctx->st>>>(ctx->sys, stage);
+  CK(cudaGetLastError());
   if (!same) {
     CK(cudaMemsetAsync(ctx->sys.img, 0, n3 * sizeof(int), ctx->st));
     CK(cudaMemsetAsync(ctx->sys.rebuild, 1, sizeof(int), ctx->st));   // new positions: rebuild candidates
@@ -1694,8 +1703,11 @@ static void collect_graph_profile(reaxff_ctx* ctx) {
   }
 }
 
-// the steps of one call without host synchronisation; returns the device flags
-static int run_unchecked(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev, int* flags) {
+// the steps of one call without host synchronisation; returns the device flags. With
+// Etot_host (pinned), the energies are copied there before the flags are read, so that the
+// one synchronisation of the flag read covers both
+static int run_unchecked(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev, int* flags,
+                         double* Etot_host = nullptr) {
   rx::Launch L = launch_of(ctx);
   rx::snapshot(L, ctx->sys, ctx->Q.hist_s, 2 * rx::QEQ_HIST * ctx->n, ctx->Q.hst, ctx->snap, ctx->snap_i, 0);
   CK(cudaMemsetAsync(ctx->sys.err, 0, sizeof(int), ctx->st));
@@ -1718,11 +1730,16 @@ static int run_unchecked(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_de
       CK(cudaMemcpyAsync(Etot_dev + (size_t)c0 * ctx->nrep, ctx->etot_buf, (size_t)len * ctx->nrep * sizeof(double),
                          cudaMemcpyDeviceToDevice, ctx->st));
   }
+  if (Etot_dev && Etot_host)
+    CK(cudaMemcpyAsync(Etot_host, Etot_dev, (size_t)nsteps * ctx->nrep * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->st));
   CK(cudaGetLastError());
   return read_err(ctx, flags);
 }
 
-static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev) {
+// Etot_host (pinned, or null): *staged is set when the energies of the call already sit there
+static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev, double* Etot_host = nullptr,
+                     bool* staged = nullptr) {
   if (!ctx->have_pos) return fail(ctx, REAXFF_E_STATE, "positions not set");
   ctx->launches = 0;
   if (nsteps > 0) ctx->h_pos_valid = false;               // the atoms move
@@ -1732,11 +1749,12 @@ static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev) {
   }
   if (nsteps > 0) {
     int flags = 0;
-    if ((rc = run_unchecked(ctx, nsteps, dt, Etot_dev, &flags))) return rc;
+    if ((rc = run_unchecked(ctx, nsteps, dt, Etot_dev, &flags, Etot_host))) return rc;
     const int cap = ERR_CAP_FAR | ERR_CAP_BOND | ERR_CAP_HB | ERR_CAP_NEAR | ERR_CAP_CAND;
     if (!(flags & cap) || (flags & (ERR_NAN | ERR_TIMEOUT))) {
       rc = flags_status(ctx, flags, false);               // the flags were read after the last step
       collect_profile(ctx);
+      if (staged) *staged = Etot_dev && Etot_host;
       return rc;
     }
     // a list overflowed during the call: restore its starting state, regrow, redo it checked
@@ -1763,20 +1781,31 @@ static int step_impl(reaxff_ctx* ctx, int nsteps, double dt, double* Etot_dev) {
 int reaxff_step(reaxff_ctx* ctx, int32_t nsteps, double dt_fs, double* E_tot) {
   if (!ctx || nsteps < 0 || !(dt_fs > 0)) return REAXFF_E_INVALID;
   double* dev = nullptr;
+  const size_t ebytes = (size_t)nsteps * ctx->nrep * sizeof(double);
   if (E_tot && nsteps > 0) {
     if (ctx->Etot_cap < nsteps * ctx->nrep) {
       if (ctx->Etot_dev) cudaFree(ctx->Etot_dev);
+      if (ctx->h_etot) cudaFreeHost(ctx->h_etot);
       ctx->Etot_dev = nullptr;
-      CK(cudaMalloc(&ctx->Etot_dev, (size_t)nsteps * ctx->nrep * sizeof(double)));
+      ctx->h_etot = nullptr;
+      ctx->Etot_cap = 0;
+      CK(cudaMalloc(&ctx->Etot_dev, ebytes));
+      CK(cudaMallocHost(&ctx->h_etot, ebytes));
       ctx->Etot_cap = nsteps * ctx->nrep;
     }
     dev = ctx->Etot_dev;
   }
-  int rc = step_impl(ctx, nsteps, dt_fs, dev);
+  // the energies come back through a pinned buffer, in the synchronisation that reads the
+  // call's error flags
+  bool staged = false;
+  int rc = step_impl(ctx, nsteps, dt_fs, dev, dev ? ctx->h_etot : nullptr, &staged);
   if (rc) return rc;
   if (E_tot && nsteps > 0) {
-    CK(cudaMemcpyAsync(E_tot, dev, (size_t)nsteps * ctx->nrep * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
+    if (!staged) {
+      CK(cudaMemcpyAsync(ctx->h_etot, dev, ebytes, cudaMemcpyDeviceToHost, ctx->st));
+      CK(cudaStreamSynchronize(ctx->st));
+    }
+    std::memcpy(E_tot, ctx->h_etot, ebytes);
   }
   return REAXFF_OK;
 }
